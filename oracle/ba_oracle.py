@@ -1,0 +1,682 @@
+"""FP64 CPU oracle for one Levenberg-Marquardt step of holistic bundle adjustment.
+
+TEST INFRASTRUCTURE ONLY.  This module exists to check the CUDA library; only the
+test-suite, the smoke entry point and the benchmark's CPU-baseline leg may import
+it.  It shares no code with the CUDA path: it is written from the paper's
+definitions, in plain float64 PyTorch (CPU) / numpy / scipy, and is kept slow and
+direct on purpose.  Jacobians are not hand-derived here: each residual is written
+as a function of the minimal local increments through the retraction x (+) delta,
+and forward-mode automatic differentiation at delta = 0 gives J (the definition
+of the derivative); finite differences in the tests pin that.
+
+What follows the paper, and where:
+  * cost             Eq. 1 and Eq. 4 (points, lines), Eq. 6 (VP), Eq. 7 / Eq. 8
+                     (plane-induced point / line), Eq. 11 / Eq. 12 (wireframe
+                     point->line, line->point); weights and Cauchy scales from the
+                     cost-balancing paragraph of Appendix C.  Robust cost is
+                     E = 1/2 sum_r w_r a_r^2 ln(1 + |r|^2 / a_r^2).
+  * plane projection of points and Pluecker lines: Appendix B ("Plane").
+  * VP residual: Eq. 6 / Appendix B, as the 3-vector d_hat x v (same squared norm).
+  * normal equations, augmented set A = C u G, block-diagonal H_ff and the Schur
+    complement S = H_aa - H_af H_ff^-1 H_fa: Eq. 2, Eq. 3, Eq. 5.
+  * termination: relative change of the pixel-space cost only (Section 3.5;
+    Appendix C excludes the angular VP terms).
+Readings where the paper is silent (camera model, the LM rule, PCG, ...) are the
+ones listed in the design notes; each function below states the one it uses.
+
+Parity status: every function here is pinned by a CPU test (finite differences,
+closed forms, dense full-system solve, an independent trust-region minimiser,
+invariants).
+"""
+from __future__ import annotations
+
+import math
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+import torch
+from torch.func import jacfwd, vmap
+
+torch.set_default_dtype(torch.float64)
+DT = torch.float64
+
+KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p")
+# residual dimension, feature type, group type per kind
+RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1}
+FEAT = {"point": "point", "line": "line", "plane_point": "point", "plane_line": "line",
+        "vp": "line", "p2l": "point", "l2p": "line"}
+GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp"}
+HAS_CAM = {k: k != "vp" for k in KINDS}
+FDOF = {"point": 3, "line": 4}
+GDOF = {"plane": 3, "vp": 2}
+CDOF = 6
+
+
+@dataclasses.dataclass
+class Options:
+    """Weights and Cauchy scales (Appendix C) and LM / PCG constants."""
+    w_point: float = 1.0
+    w_line: float = 1.0
+    w_group: float = 0.5
+    w_wire: float = 0.1
+    w_vp: float = 5e3
+    cauchy_px: float = 1.0
+    cauchy_vp: float = 0.2
+    lambda0: float = 1e-4
+    lambda_min: float = 1e-12
+    lambda_max: float = 1e12
+    min_gain: float = 1e-3
+    rel_cost_tol: float = 1e-6
+    pcg_rel_tol: float = 1e-6
+    pcg_max_iters: int = 1000
+    solver: str = "pcg"           # "pcg" (block-Jacobi PCG) or "dense" (Cholesky of S)
+
+    def weight(self, kind):
+        return {"point": self.w_point, "line": self.w_line, "plane_point": self.w_group,
+                "plane_line": self.w_group, "vp": self.w_vp, "p2l": self.w_wire,
+                "l2p": self.w_wire}[kind]
+
+    def scale(self, kind):
+        return self.cauchy_vp if kind == "vp" else self.cauchy_px
+
+
+# ===========================================================================
+# rotations and manifolds
+# ===========================================================================
+def skew(v):
+    z = torch.zeros_like(v[..., 0])
+    return torch.stack([torch.stack([z, -v[..., 2], v[..., 1]], -1),
+                        torch.stack([v[..., 2], z, -v[..., 0]], -1),
+                        torch.stack([-v[..., 1], v[..., 0], z], -1)], -2)
+
+
+def so3_exp(w):
+    """Rodrigues' formula R = I + A [w]x + B [w]x^2 with a series branch near 0."""
+    th2 = (w * w).sum(-1)
+    small = th2 < 1e-12
+    th2s = torch.where(small, torch.ones_like(th2), th2)
+    th = torch.sqrt(th2s)
+    A = torch.where(small, 1 - th2 / 6, torch.sin(th) / th)
+    B = torch.where(small, 0.5 - th2 / 24, (1 - torch.cos(th)) / th2s)
+    K = skew(w)
+    eye = torch.eye(3, dtype=w.dtype).expand(K.shape)
+    return eye + A[..., None, None] * K + B[..., None, None] * (K @ K)
+
+
+def quat_to_R(q):
+    q = q / torch.linalg.norm(q, dim=-1, keepdim=True)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    return torch.stack([
+        torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+
+
+def R_to_quat(R):
+    """Rotation matrix -> unit quaternion (w,x,y,z), w >= 0 (numpy)."""
+    R = np.asarray(R)
+    q = np.empty(R.shape[:-2] + (4,))
+    for i in np.ndindex(R.shape[:-2]):
+        M = R[i]
+        t = np.trace(M)
+        if t > 0:
+            s = math.sqrt(t + 1.0) * 2
+            v = (0.25 * s, (M[2, 1] - M[1, 2]) / s, (M[0, 2] - M[2, 0]) / s, (M[1, 0] - M[0, 1]) / s)
+        elif M[0, 0] > M[1, 1] and M[0, 0] > M[2, 2]:
+            s = math.sqrt(1.0 + M[0, 0] - M[1, 1] - M[2, 2]) * 2
+            v = ((M[2, 1] - M[1, 2]) / s, 0.25 * s, (M[0, 1] + M[1, 0]) / s, (M[0, 2] + M[2, 0]) / s)
+        elif M[1, 1] > M[2, 2]:
+            s = math.sqrt(1.0 + M[1, 1] - M[0, 0] - M[2, 2]) * 2
+            v = ((M[0, 2] - M[2, 0]) / s, (M[0, 1] + M[1, 0]) / s, 0.25 * s, (M[1, 2] + M[2, 1]) / s)
+        else:
+            s = math.sqrt(1.0 + M[2, 2] - M[0, 0] - M[1, 1]) * 2
+            v = ((M[1, 0] - M[0, 1]) / s, (M[0, 2] + M[2, 0]) / s, (M[1, 2] + M[2, 1]) / s, 0.25 * s)
+        q[i] = v
+    q *= np.where(q[..., :1] < 0, -1.0, 1.0)
+    return q / np.linalg.norm(q, axis=-1, keepdims=True)
+
+
+def tangent_basis(n):
+    """Orthonormal (b1, b2) spanning the tangent plane of the unit vector n:
+    a = e_x unless |n_x| >= 0.9 (then e_y); b1 = unit(a - (a.n) n); b2 = n x b1."""
+    ex = torch.zeros_like(n); ex[..., 0] = 1.0
+    ey = torch.zeros_like(n); ey[..., 1] = 1.0
+    a = torch.where((n[..., 0].abs() < 0.9)[..., None], ex, ey)
+    b1 = a - (a * n).sum(-1, keepdim=True) * n
+    b1 = b1 / torch.linalg.norm(b1, dim=-1, keepdim=True)
+    b2 = torch.linalg.cross(n, b1)
+    return b1, b2
+
+
+def s2_exp(n, v):
+    """Exponential map of the unit sphere at n along the tangent vector v."""
+    th2 = (v * v).sum(-1)
+    small = th2 < 1e-12
+    th = torch.sqrt(torch.where(small, torch.ones_like(th2), th2))
+    c = torch.where(small, 1 - th2 / 2, torch.cos(th))
+    s = torch.where(small, 1 - th2 / 6, torch.sin(th) / th)
+    return c[..., None] * n + s[..., None] * v
+
+
+# ---------------------------------------------------------------------------
+# retractions x (+) delta (the minimal increments the normal equations use)
+# ---------------------------------------------------------------------------
+def pose_plus(q, t, dp):
+    """R <- Exp(dw) R, t <- t + dt; dp = (dw, dt)."""
+    return so3_exp(dp[..., :3]) @ quat_to_R(q), t + dp[..., 3:6]
+
+
+def line_frame(L):
+    """Orthonormal representation (Bartoli-Sturm) of a Pluecker line with |d| = 1:
+    U = [m/|m|, d, (m x d)/|m x d|] and the angle phi with (cos, sin) ~ (|m|, |d|)."""
+    d, m = L[..., :3], L[..., 3:6]
+    dn = torch.linalg.norm(d, dim=-1, keepdim=True)
+    d = d / dn
+    m = m / dn
+    r = torch.linalg.norm(m, dim=-1)
+    tiny = r < 1e-12
+    b1, _ = tangent_basis(d)
+    u1 = torch.where(tiny[..., None], b1, m / torch.where(tiny, torch.ones_like(r), r)[..., None])
+    u3 = torch.linalg.cross(u1, d)
+    U = torch.stack([u1, d, u3], -1)
+    phi = torch.atan2(torch.ones_like(r), r)
+    return U, phi
+
+
+def line_plus(L, dl):
+    """U <- U Exp(dl[0:3]), phi <- phi + dl[3]; d = u2, m = cot(phi) u1 (|d| stays 1)."""
+    U, phi = line_frame(L)
+    U2 = U @ so3_exp(dl[..., :3])
+    ph = phi + dl[..., 3]
+    return torch.cat([U2[..., :, 1], (torch.cos(ph) / torch.sin(ph))[..., None] * U2[..., :, 0]], -1)
+
+
+def plane_plus(P, dp):
+    """n <- Exp_n(b1 d0 + b2 d1) on S^2, w <- w + d2."""
+    n = P[..., :3] / torch.linalg.norm(P[..., :3], dim=-1, keepdim=True)
+    b1, b2 = tangent_basis(n)
+    v = dp[..., 0:1] * b1 + dp[..., 1:2] * b2
+    return torch.cat([s2_exp(n, v), P[..., 3:4] + dp[..., 2:3]], -1)
+
+
+def vp_plus(v, dv):
+    v = v / torch.linalg.norm(v, dim=-1, keepdim=True)
+    b1, b2 = tangent_basis(v)
+    return s2_exp(v, dv[..., 0:1] * b1 + dv[..., 1:2] * b2)
+
+
+# ===========================================================================
+# projections (Section 3.1-3.4) and the plane projections (Appendix B)
+# ===========================================================================
+def to_cam(R, t, X):
+    return (R @ X[..., None])[..., 0] + t
+
+
+def pi_point(R, t, cam, X):
+    """Point projection with radial distortion: pp + f (1 + k1 r^2 + k2 r^4) (x/z, y/z)."""
+    xc = to_cam(R, t, X)
+    u = xc[..., :2] / xc[..., 2:3]
+    r2 = (u * u).sum(-1, keepdim=True)
+    s = 1 + cam[..., 8:9] * r2 + cam[..., 9:10] * r2 * r2
+    return cam[..., 10:12] + cam[..., 7:8] * s * u, xc[..., 2]
+
+
+def pi_point_pinhole(R, t, cam, X):
+    xc = to_cam(R, t, X)
+    return cam[..., 10:12] + cam[..., 7:8] * xc[..., :2] / xc[..., 2:3], xc[..., 2]
+
+
+def pi_line(R, t, cam, L):
+    """Image line (homogeneous, pixels) of a Pluecker line: d_c = R d,
+    m_c = R m + t x d_c, l = (m_c0, m_c1, f m_c2 - ppx m_c0 - ppy m_c1)."""
+    dc = (R @ L[..., :3, None])[..., 0]
+    mc = (R @ L[..., 3:6, None])[..., 0] + torch.linalg.cross(t, dc)
+    f, px, py = cam[..., 7], cam[..., 10], cam[..., 11]
+    return torch.stack([mc[..., 0], mc[..., 1], f * mc[..., 2] - px * mc[..., 0] - py * mc[..., 1]], -1)
+
+
+def rho(l, seg):
+    """Eq. 4: perpendicular displacement vectors of the two observed endpoints to the line l."""
+    n12 = torch.sqrt(l[..., 0] ** 2 + l[..., 1] ** 2)
+    nrm = l[..., :2] / n12[..., None]
+    out = []
+    for e in (seg[..., 0:2], seg[..., 2:4]):
+        s = (l[..., 0] * e[..., 0] + l[..., 1] * e[..., 1] + l[..., 2]) / n12
+        out.append(s[..., None] * nrm)
+    return torch.cat(out, -1), n12
+
+
+def plane_project_point(P, X):
+    """Appendix B: p_proj = p - (n.p + w) n."""
+    n, w = P[..., :3], P[..., 3]
+    return X - ((n * X).sum(-1) + w)[..., None] * n
+
+
+def plane_project_line(P, L):
+    """Appendix B: d' = d - (d.n) n;  m' = (1 - a^2/|d|^2) m + (a g/|d|^2) d + (w - dl/|d|^2)(d x n),
+    a = d.n, g = m.n, dl = (d x n).m."""
+    n, w = P[..., :3], P[..., 3:4]
+    d, m = L[..., :3], L[..., 3:6]
+    a = (d * n).sum(-1, keepdim=True)
+    g = (m * n).sum(-1, keepdim=True)
+    dxn = torch.linalg.cross(d, n)
+    dl = (dxn * m).sum(-1, keepdim=True)
+    dd = (d * d).sum(-1, keepdim=True)
+    return torch.cat([d - a * n, (1 - a * a / dd) * m + (a * g / dd) * d + (w - dl / dd) * dxn], -1)
+
+
+# ===========================================================================
+# residuals as functions of the local increments (one record, vmapped)
+#   cam = [q(4) t(3) f k1 k2 ppx ppy] (12), feat = point (3) or line (6),
+#   grp = plane (4) or vp (3, padded to 4), meas (4, padded)
+# each returns (r, valid)
+# ===========================================================================
+def _pose(cam, dc):
+    return pose_plus(cam[:4], cam[4:7], dc)
+
+
+def res_point(dc, df, dg, cam, feat, grp, meas):            # Eq. 1 / Eq. 4 (points)
+    R, t = _pose(cam, dc)
+    x, z = pi_point(R, t, cam, feat[:3] + df)
+    return x - meas[:2], z > 1e-6
+
+
+def res_line(dc, df, dg, cam, feat, grp, meas):             # Eq. 4 (lines)
+    R, t = _pose(cam, dc)
+    l = pi_line(R, t, cam, line_plus(feat, df))
+    r, n12 = rho(l, meas)
+    return r, n12 > 1e-12
+
+
+def res_plane_point(dc, df, dg, cam, feat, grp, meas):      # Eq. 7
+    R, t = _pose(cam, dc)
+    X = feat[:3] + df
+    P = plane_plus(grp, dg)
+    x1, z1 = pi_point(R, t, cam, X)
+    x2, z2 = pi_point(R, t, cam, plane_project_point(P, X))
+    return x1 - x2, (z1 > 1e-6) & (z2 > 1e-6)
+
+
+def res_plane_line(dc, df, dg, cam, feat, grp, meas):       # Eq. 8
+    R, t = _pose(cam, dc)
+    L = line_plus(feat, df)
+    P = plane_plus(grp, dg)
+    r1, n1 = rho(pi_line(R, t, cam, L), meas)
+    r2, n2 = rho(pi_line(R, t, cam, plane_project_line(P, L)), meas)
+    return r1 - r2, (n1 > 1e-12) & (n2 > 1e-12)
+
+
+def res_vp(dc, df, dg, cam, feat, grp, meas):               # Eq. 6 as d_hat x v
+    L = line_plus(feat, df)
+    d = L[:3] / torch.linalg.norm(L[:3])
+    v = vp_plus(grp[:3], dg[:2])
+    return torch.linalg.cross(d, v), torch.ones((), dtype=torch.bool)
+
+
+def res_p2l(dc, df, dg, cam, feat, grp, meas):              # Eq. 11
+    R, t = _pose(cam, dc)
+    x, z = pi_point_pinhole(R, t, cam, feat[:3] + df)
+    e1 = torch.cat([meas[0:2], torch.ones(1, dtype=DT)])
+    e2 = torch.cat([meas[2:4], torch.ones(1, dtype=DT)])
+    lh = torch.linalg.cross(e1, e2)
+    lh = lh / torch.sqrt(lh[0] ** 2 + lh[1] ** 2)
+    return (lh[:2] * x).sum(-1, keepdim=True) + lh[2:3], z > 1e-6
+
+
+def res_l2p(dc, df, dg, cam, feat, grp, meas):              # Eq. 12
+    R, t = _pose(cam, dc)
+    l = pi_line(R, t, cam, line_plus(feat, df))
+    n12 = torch.sqrt(l[0] ** 2 + l[1] ** 2)
+    return ((l[0] * meas[0] + l[1] * meas[1] + l[2]) / n12)[None], n12 > 1e-12
+
+
+RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
+          "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p}
+
+
+# ===========================================================================
+# problem state
+# ===========================================================================
+def normalize_lines(L):
+    L = np.array(L, dtype=np.float64, copy=True)
+    dn = np.linalg.norm(L[:, :3], axis=1, keepdims=True)
+    return L / dn
+
+
+def state_from_scene(scene):
+    c = scene["cams"]
+    st = dict(
+        cams=np.concatenate([c["q"] / np.linalg.norm(c["q"], axis=1, keepdims=True), c["t"],
+                             c["intr"], c["pp"]], 1).astype(np.float64),
+        points=np.array(scene["points"], np.float64),
+        lines=normalize_lines(scene["lines"]) if len(scene["lines"]) else np.zeros((0, 6)),
+        planes=np.array(scene["planes"], np.float64).reshape(-1, 4),
+        vps=np.array(scene["vps"], np.float64).reshape(-1, 3),
+    )
+    if len(st["planes"]):
+        st["planes"][:, :3] /= np.linalg.norm(st["planes"][:, :3], axis=1, keepdims=True)
+    if len(st["vps"]):
+        st["vps"] /= np.linalg.norm(st["vps"], axis=1, keepdims=True)
+    return st
+
+
+def _records(state, obs, kind):
+    """Gather the per-residual inputs of one kind as float64 tensors."""
+    o = obs[kind]
+    n = len(o["feat"])
+    cam = torch.zeros((n, 12), dtype=DT)
+    if HAS_CAM[kind] and n:
+        cam = torch.from_numpy(state["cams"][o["cam"]])
+    ft = FEAT[kind]
+    src = state["points"] if ft == "point" else state["lines"]
+    feat = torch.zeros((n, 6), dtype=DT)
+    if n:
+        feat[:, : src.shape[1]] = torch.from_numpy(src[o["feat"]])
+    grp = torch.zeros((n, 4), dtype=DT)
+    gk = GROUP.get(kind)
+    if gk and n:
+        g = state["planes"] if gk == "plane" else state["vps"]
+        grp[:, : g.shape[1]] = torch.from_numpy(g[o["other"]])
+    meas = torch.zeros((n, 4), dtype=DT)
+    m = np.asarray(o["meas"]).reshape(n, -1)
+    if m.shape[1]:
+        meas[:, : m.shape[1]] = torch.from_numpy(m)
+    return cam, feat, grp, meas
+
+
+def residuals(state, obs, kind, with_jac=False, chunk=200_000):
+    """r [n, rdim], valid [n] and, with with_jac, J w.r.t. (cam 6, feature k, group 3) increments."""
+    cam, feat, grp, meas = _records(state, obs, kind)
+    n = cam.shape[0]
+    kf = FDOF[FEAT[kind]]
+    fn = RES_FN[kind]
+    rd = RDIM[kind]
+    if n == 0:
+        z = torch.zeros((0, rd))
+        out = (z, torch.zeros(0, dtype=torch.bool))
+        if with_jac:
+            out = out + (torch.zeros((0, rd, 6)), torch.zeros((0, rd, kf)), torch.zeros((0, rd, 3)))
+        return out
+    dc = torch.zeros((n, 6)); df = torch.zeros((n, kf)); dg = torch.zeros((n, 3))
+    rs, vs, Jc, Jf, Jg = [], [], [], [], []
+    for s in range(0, n, chunk):
+        sl = slice(s, s + chunk)
+        args = (dc[sl], df[sl], dg[sl], cam[sl], feat[sl], grp[sl], meas[sl])
+        if with_jac:
+            def f2(*a):
+                r, v = fn(*a)
+                return r, (r, v)
+            jac, (r, v) = vmap(jacfwd(f2, argnums=(0, 1, 2), has_aux=True))(*args)
+            Jc.append(jac[0]); Jf.append(jac[1]); Jg.append(jac[2])
+        else:
+            r, v = vmap(fn)(*args)
+        rs.append(r); vs.append(v)
+    out = (torch.cat(rs), torch.cat(vs))
+    if with_jac:
+        out = out + (torch.cat(Jc), torch.cat(Jf), torch.cat(Jg))
+    return out
+
+
+def cost(state, obs, opt: Options):
+    """(E, E_px): E = 1/2 sum w a^2 ln(1 + |r|^2/a^2); E_px omits the VP (angular) terms."""
+    E = 0.0
+    Epx = 0.0
+    for k in KINDS:
+        if len(obs[k]["feat"]) == 0:
+            continue
+        r, v = residuals(state, obs, k)
+        a = opt.scale(k)
+        s = (r * r).sum(-1)
+        e = 0.5 * opt.weight(k) * a * a * torch.log1p(s / (a * a))
+        e = torch.where(v, e, torch.zeros_like(e))
+        tot = float(e.sum())
+        E += tot
+        if k != "vp":
+            Epx += tot
+    return E, Epx
+
+
+# ===========================================================================
+# the normal equations (Eq. 2 / Eq. 5) and the Schur complement (Eq. 3)
+# ===========================================================================
+class Layout:
+    """Column layout of the full system: [cameras | planes | VPs | points | lines]."""
+
+    def __init__(self, state, fixed=None):
+        self.nc = state["cams"].shape[0]
+        self.npl = state["planes"].shape[0]
+        self.nv = state["vps"].shape[0]
+        self.np_ = state["points"].shape[0]
+        self.nl = state["lines"].shape[0]
+        self.fixed = np.zeros(self.nc, bool) if fixed is None else np.asarray(fixed, bool)
+        free = ~self.fixed
+        self.cam_col = np.full(self.nc, -1, np.int64)
+        self.cam_col[free] = 6 * np.arange(free.sum())
+        o = 6 * int(free.sum())
+        self.plane_col = o + 3 * np.arange(self.npl); o += 3 * self.npl
+        self.vp_col = o + 2 * np.arange(self.nv); o += 2 * self.nv
+        self.na = o
+        self.point_col = o + 3 * np.arange(self.np_); o += 3 * self.np_
+        self.line_col = o + 4 * np.arange(self.nl); o += 4 * self.nl
+        self.n = o
+        # entity blocks of A (for block-Jacobi): (start, size)
+        self.a_blocks = ([(int(c), 6) for c in self.cam_col[free]] +
+                         [(int(c), 3) for c in self.plane_col] + [(int(c), 2) for c in self.vp_col])
+        self.f_blocks = [(int(c), 3) for c in self.point_col] + [(int(c), 4) for c in self.line_col]
+
+
+def linearize(state, obs, opt: Options, lay: Layout):
+    """Weighted Jacobian J~ = sqrt(w) J (sparse) and r~ = sqrt(w) r with IRLS weights
+    w = weight / (1 + |r|^2/a^2) (plain IRLS, no second-order correction)."""
+    rows, cols, vals, rt = [], [], [], []
+    row0 = 0
+    for k in KINDS:
+        o = obs[k]
+        n = len(o["feat"])
+        if n == 0:
+            continue
+        r, v, Jc, Jf, Jg = residuals(state, obs, k, with_jac=True)
+        a = opt.scale(k)
+        s = (r * r).sum(-1)
+        om = opt.weight(k) / (1 + s / (a * a))
+        om = torch.where(v, om, torch.zeros_like(om))
+        sq = torch.sqrt(om).numpy()
+        rd = RDIM[k]
+        ridx = row0 + np.arange(n)[:, None] * rd + np.arange(rd)[None, :]          # [n, rd]
+        blocks = []
+        if HAS_CAM[k]:
+            cc = lay.cam_col[o["cam"]]
+            ok = cc >= 0
+            blocks.append((Jc.numpy(), np.where(ok, cc, 0), ok, 6))
+        ft = FEAT[k]
+        fc = (lay.point_col if ft == "point" else lay.line_col)[o["feat"]]
+        blocks.append((Jf.numpy(), fc, np.ones(n, bool), FDOF[ft]))
+        gk = GROUP.get(k)
+        if gk:
+            gc = (lay.plane_col if gk == "plane" else lay.vp_col)[o["other"]]
+            blocks.append((Jg.numpy()[:, :, : GDOF[gk]], gc, np.ones(n, bool), GDOF[gk]))
+        for J, c0, ok, w in blocks:
+            J = J * sq[:, None, None]
+            R_ = np.broadcast_to(ridx[:, :, None], (n, rd, w))
+            C_ = c0[:, None, None] + np.arange(w)[None, None, :]
+            m = np.broadcast_to(ok[:, None, None], (n, rd, w))
+            rows.append(R_[m]); cols.append(np.broadcast_to(C_, (n, rd, w))[m]); vals.append(J[m])
+        rt.append((r.numpy() * sq[:, None]).reshape(-1))
+        row0 += n * rd
+    Jt = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(row0, lay.n))
+    return Jt, np.concatenate(rt)
+
+
+def _block_diag_inverse(H, blocks):
+    """Inverse of the block-diagonal part of H on the given (start, size) blocks, as sparse."""
+    rows, cols, vals = [], [], []
+    for size in sorted({s for _, s in blocks}):
+        starts = np.array([b for b, s in blocks if s == size], np.int64)
+        if len(starts) == 0:
+            continue
+        idx = starts[:, None] + np.arange(size)[None, :]
+        ri = np.broadcast_to(idx[:, :, None], (len(starts), size, size)).ravel()
+        ci = np.broadcast_to(idx[:, None, :], (len(starts), size, size)).ravel()
+        B = np.asarray(H[ri, ci]).reshape(len(starts), size, size)          # [nb, s, s]
+        Bi = np.linalg.inv(B)
+        rows.append(np.broadcast_to(idx[:, :, None], Bi.shape).ravel())
+        cols.append(np.broadcast_to(idx[:, None, :], Bi.shape).ravel())
+        vals.append(Bi.ravel())
+    n = H.shape[0]
+    if not rows:
+        return sp.csr_matrix((n, n))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def normal_equations(Jt, rt):
+    """H = J~^T J~ and g = J~^T r~ (Eq. 2 / Eq. 5)."""
+    H = (Jt.T @ Jt).tocsr()
+    g = Jt.T @ rt
+    return H, g
+
+
+def damping_diag(H):
+    """D = clamp(diag H, 1e-6, 1e32)."""
+    return np.clip(H.diagonal(), 1e-6, 1e32)
+
+
+def reduced_system(H, g, lam, lay: Layout):
+    """Damp both blocks by lam*D, eliminate the features:
+    S = H_aa + lam D_a - H_af (H_ff + lam D_f)^-1 H_fa,  b = -g_a + H_af (H_ff + lam D_f)^-1 g_f (Eq. 3 / Eq. 5)."""
+    D = damping_diag(H)
+    Hl = (H + sp.diags(lam * D)).tocsr()
+    na = lay.na
+    Haa = Hl[:na, :na]
+    Haf = Hl[:na, na:]
+    Hff = Hl[na:, na:]
+    fb = [(s - na, k) for s, k in lay.f_blocks]
+    Hffi = _block_diag_inverse(Hff, fb)
+    S = (Haa - Haf @ Hffi @ Haf.T).tocsr()
+    b = -g[:na] + Haf @ (Hffi @ g[na:])
+    return S, b, Hffi, Haf, D
+
+
+def pcg(S, b, blocks, tol, max_iters):
+    """Block-Jacobi preconditioned CG from x0 = 0; stops when |r_k| <= tol |b| (recurrence residual)."""
+    Minv = _block_diag_inverse(S.tocsr(), blocks)
+    x = np.zeros_like(b)
+    bn = float(np.sqrt(b @ b))
+    if bn == 0.0:
+        return x, 0, 0.0
+    r = b.copy()
+    z = Minv @ r
+    p = z.copy()
+    rz = float(r @ z)
+    it = 0
+    rn = bn
+    while it < max_iters:
+        Ap = S @ p
+        alpha = rz / float(p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        it += 1
+        rn = float(np.sqrt(r @ r))
+        if rn <= tol * bn:
+            break
+        z = Minv @ r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return x, it, rn / bn
+
+
+def apply_step(state, delta, lay: Layout):
+    """x (+) delta with the retractions above; returns a new state."""
+    new = {k: v.copy() for k, v in state.items()}
+    free = np.nonzero(~lay.fixed)[0]
+    if len(free):
+        dp = torch.from_numpy(np.stack([delta[lay.cam_col[i]: lay.cam_col[i] + 6] for i in free]))
+        c = torch.from_numpy(state["cams"][free])
+        R, t = pose_plus(c[:, :4], c[:, 4:7], dp)
+        new["cams"][free, :4] = R_to_quat(R.numpy())
+        new["cams"][free, 4:7] = t.numpy()
+    if lay.npl:
+        d = delta[lay.plane_col[:, None] + np.arange(3)]
+        new["planes"] = plane_plus(torch.from_numpy(state["planes"]), torch.from_numpy(d)).numpy()
+    if lay.nv:
+        d = delta[lay.vp_col[:, None] + np.arange(2)]
+        new["vps"] = vp_plus(torch.from_numpy(state["vps"]), torch.from_numpy(d)).numpy()
+    if lay.np_:
+        new["points"] = state["points"] + delta[lay.point_col[:, None] + np.arange(3)]
+    if lay.nl:
+        d = delta[lay.line_col[:, None] + np.arange(4)]
+        new["lines"] = line_plus(torch.from_numpy(state["lines"]), torch.from_numpy(d)).numpy()
+    return new
+
+
+def solve_step(state, obs, opt: Options, lam, lay: Layout, lin=None):
+    """The full-system step at damping lam: returns (delta, info)."""
+    Jt, rt = lin if lin is not None else linearize(state, obs, opt, lay)
+    H, g = normal_equations(Jt, rt)
+    S, b, Hffi, Haf, D = reduced_system(H, g, lam, lay)
+    if opt.solver == "dense":
+        da = np.linalg.solve(S.toarray(), b) if lay.na else np.zeros(0)
+        it, rel = 0, 0.0
+    else:
+        da, it, rel = pcg(S, b, lay.a_blocks, opt.pcg_rel_tol, opt.pcg_max_iters)
+    na = lay.na
+    df = -(Hffi @ (g[na:] + Haf.T @ da))
+    delta = np.concatenate([da, df])
+    Jd = Jt @ delta
+    pred = -float(g @ delta) - 0.5 * float(Jd @ Jd)
+    return delta, dict(pcg_iters=it, pcg_rel=rel, pred=pred, S=S, b=b, g=g, H=H, D=D)
+
+
+@dataclasses.dataclass
+class LMState:
+    lam: float
+    nu: float = 2.0
+
+
+def lm_step(state, obs, opt: Options, lm: LMState, lay: Layout, cur=None, lin=None):
+    """One LM iteration (build, damp, eliminate, solve, back-substitute, evaluate, decide).
+    Acceptance: gain ratio > min_gain; lambda update by Nielsen's rule
+    (Madsen, Nielsen & Tingleff 2004, Sec. 3.2), lambda clamped to [lambda_min, lambda_max]."""
+    E, Epx = cur if cur is not None else cost(state, obs, opt)
+    delta, info = solve_step(state, obs, opt, lm.lam, lay, lin)
+    cand = apply_step(state, delta, lay)
+    E2, Epx2 = cost(cand, obs, opt)
+    pred = info["pred"]
+    gain = (E - E2) / pred if pred > 0 else -np.inf
+    accepted = bool(np.isfinite(E2) and gain > opt.min_gain)
+    lam_used = lm.lam
+    if accepted:
+        lm.lam = min(max(lm.lam * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3), opt.lambda_min), opt.lambda_max)
+        lm.nu = 2.0
+    else:
+        lm.lam = min(lm.lam * lm.nu, opt.lambda_max)
+        lm.nu *= 2.0
+    rep = dict(E=E, Epx=Epx, E_new=E2, Epx_new=Epx2, gain=gain, accepted=accepted, lam=lam_used,
+               pcg_iters=info["pcg_iters"], pcg_rel=info["pcg_rel"], pred=pred, delta=delta)
+    return (cand if accepted else state), rep
+
+
+def solve(scene_or_state, obs, opt: Options = None, max_iters=20, fixed=None, history=False):
+    """LM until an accepted step with |dE_px|/E_px < rel_cost_tol (Section 3.5) or max_iters."""
+    opt = opt or Options()
+    state = scene_or_state if "cams" in scene_or_state and isinstance(scene_or_state["cams"], np.ndarray) \
+        else state_from_scene(scene_or_state)
+    lay = Layout(state, fixed)
+    lm = LMState(opt.lambda0)
+    cur = cost(state, obs, opt)
+    reps = []
+    converged = False
+    for _ in range(max_iters):
+        state, rep = lm_step(state, obs, opt, lm, lay, cur)
+        rep.pop("delta")
+        reps.append(rep)
+        if rep["accepted"]:
+            rel = abs(rep["Epx"] - rep["Epx_new"]) / max(rep["Epx"], 1e-300)
+            cur = (rep["E_new"], rep["Epx_new"])
+            if rel < opt.rel_cost_tol:
+                converged = True
+                break
+    return state, dict(iters=len(reps), converged=converged, reports=reps, E=cur[0], Epx=cur[1])

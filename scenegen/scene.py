@@ -1,0 +1,458 @@
+"""Seeded synthetic holistic-BA scenes (inputs only).
+
+This module draws cameras, points, lines, planes, vanishing points, wireframe
+edges and their observation lists, shaped like the synthetic benchmark of the
+paper's appendix (A.3): a cube of half-extent 3 with Manhattan-aligned planes,
+cameras on a sphere (or a ring) looking inwards, features on planes and free,
+wireframe grids on planes, pixel noise, outliers and perturbed initial values.
+
+It is shared by the CPU oracle and the CUDA path as *input* only.  To create
+measurements it needs to project ground-truth geometry into the images; it does
+so with its own small projection helpers below, which neither the oracle nor
+the CUDA library uses.  Nothing here linearises, weights or solves anything.
+
+Conventions (all float64):
+  cameras:  q [Nc,4] unit quaternion (w,x,y,z) world->camera, t [Nc,3],
+            intr [Nc,3] = (f, k1, k2), pp [Nc,2] principal point (pixels).
+            x_cam = R(q) X + t, +z forward.
+  points:   [Np,3]
+  lines:    [Nl,6] Pluecker (d, m), |d| = 1, m = p x d for any p on the line.
+  planes:   [Npl,4] (n, w), |n| = 1, plane n.x + w = 0.
+  vps:      [Nv,3] unit directions.
+Observation kinds (one record per residual):
+  point      (cam, point, -, meas 2 distorted pixels)                 Eq. 1/4
+  line       (cam, line,  -, meas 4 undistorted segment endpoints)    Eq. 4
+  plane_point(cam, point, plane, no meas)                             Eq. 7
+  plane_line (cam, line,  plane, meas 4 segment)                      Eq. 8
+  vp         (-1,  line,  vp,    no meas)                             Eq. 6
+  p2l        (cam, point, line id of partner, meas 4 partner segment) Eq. 11
+  l2p        (cam, line,  point id of partner, meas 2 undistorted pt) Eq. 12
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+IMG_W, IMG_H = 800.0, 600.0
+HALF = 3.0
+
+KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p")
+MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2}
+
+
+@dataclasses.dataclass
+class SceneConfig:
+    name: str = "tiny"
+    n_cams: int = 10
+    ring: bool = True
+    n_points: int = 500
+    n_lines: int = 100
+    n_planes: int = 4
+    n_vps: int = 2
+    track_min: int = 3
+    track_max: int = 6
+    track_mean: float = 0.0          # >0: truncated geometric on [track_min, track_max]
+    k_near: int = 64
+    frac_points_on_plane: float = 0.5
+    frac_lines_on_plane: float = 0.5
+    frac_lines_vp: float = 0.6
+    n_wire_edges: int = 100
+    sigma_px: float = 1.0
+    outlier_frac: float = 0.05
+    rot_noise_deg: float = 1.0
+    trans_noise: float = 0.05
+    feat_noise: float = 0.1
+    group_rot_noise_deg: float = 2.0
+    group_off_noise: float = 0.05
+    seed: int = 1
+
+
+def config(name: str, seed: int | None = None, **over) -> SceneConfig:
+    """Named workloads.  Sizes follow the five benchmark configurations."""
+    if name == "tiny":         # 10 ring cameras, 500 pts, 100 lines, 4 planes, 2 VPs
+        c = SceneConfig(name="tiny", seed=1)
+    elif name == "small":      # a parity case a few tiles wide with ragged sizes
+        c = SceneConfig(name="small", n_cams=37, ring=False, n_points=5003, n_lines=611,
+                        n_planes=7, n_vps=4, track_min=2, track_max=9, track_mean=4.5,
+                        k_near=20, n_wire_edges=301, sigma_px=0.7, outlier_frac=0.03, seed=7)
+    elif name == "medium":     # 200 cams, 100k pts, 20k lines, 30 planes + 20 VPs
+        c = SceneConfig(name="medium", n_cams=200, ring=False, n_points=100_000, n_lines=20_000,
+                        n_planes=30, n_vps=20, track_min=2, track_max=12, track_mean=5.0,
+                        k_near=40, n_wire_edges=3000, sigma_px=0.5, outlier_frac=0.03, seed=2)
+    elif name == "large":      # 2000 cams, 2M pts, 200k lines, 300 planes + 200 VPs
+        c = SceneConfig(name="large", n_cams=2000, ring=False, n_points=2_000_000,
+                        n_lines=200_000, n_planes=300, n_vps=200, track_min=2, track_max=12,
+                        track_mean=6.0, k_near=64, n_wire_edges=34_000, sigma_px=0.5,
+                        outlier_frac=0.03, seed=3)
+    else:
+        raise ValueError(name)
+    if seed is not None:
+        c.seed = seed
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+# --------------------------------------------------------------------------
+# small geometric helpers used only to synthesise data
+# --------------------------------------------------------------------------
+def _quat_to_mat(q):
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z); R[..., 0, 1] = 2 * (x * y - w * z); R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z); R[..., 1, 1] = 1 - 2 * (x * x + z * z); R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y); R[..., 2, 1] = 2 * (y * z + w * x); R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def _mat_to_quat(R):
+    q = np.empty(R.shape[:-2] + (4,))
+    tr = R[..., 0, 0] + R[..., 1, 1] + R[..., 2, 2]
+    for i in np.ndindex(R.shape[:-2]):
+        M = R[i]
+        t = tr[i]
+        if t > 0:
+            s = math.sqrt(t + 1.0) * 2
+            q[i] = ((0.25 * s), (M[2, 1] - M[1, 2]) / s, (M[0, 2] - M[2, 0]) / s, (M[1, 0] - M[0, 1]) / s)
+        elif M[0, 0] > M[1, 1] and M[0, 0] > M[2, 2]:
+            s = math.sqrt(1.0 + M[0, 0] - M[1, 1] - M[2, 2]) * 2
+            q[i] = ((M[2, 1] - M[1, 2]) / s, 0.25 * s, (M[0, 1] + M[1, 0]) / s, (M[0, 2] + M[2, 0]) / s)
+        elif M[1, 1] > M[2, 2]:
+            s = math.sqrt(1.0 + M[1, 1] - M[0, 0] - M[2, 2]) * 2
+            q[i] = ((M[0, 2] - M[2, 0]) / s, (M[0, 1] + M[1, 0]) / s, 0.25 * s, (M[1, 2] + M[2, 1]) / s)
+        else:
+            s = math.sqrt(1.0 + M[2, 2] - M[0, 0] - M[1, 1]) * 2
+            q[i] = ((M[1, 0] - M[0, 1]) / s, (M[0, 2] + M[2, 0]) / s, (M[1, 2] + M[2, 1]) / s, 0.25 * s)
+    q *= np.sign(q[..., :1] + 1e-300)
+    return q / np.linalg.norm(q, axis=-1, keepdims=True)
+
+
+def _axis_angle_mat(axis, ang):
+    axis = axis / np.linalg.norm(axis, axis=-1, keepdims=True)
+    K = np.zeros(axis.shape[:-1] + (3, 3))
+    K[..., 0, 1] = -axis[..., 2]; K[..., 0, 2] = axis[..., 1]
+    K[..., 1, 0] = axis[..., 2]; K[..., 1, 2] = -axis[..., 0]
+    K[..., 2, 0] = -axis[..., 1]; K[..., 2, 1] = axis[..., 0]
+    s = np.sin(ang)[..., None, None]
+    c = np.cos(ang)[..., None, None]
+    return np.eye(3) + s * K + (1 - c) * (K @ K)
+
+
+def _rand_unit(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _to_cam(R, t, X):
+    return np.einsum("...ij,...j->...i", R, X) + t
+
+
+def _pix_pinhole(f, pp, xc):
+    return pp + f[..., None] * xc[..., :2] / xc[..., 2:3]
+
+
+def _pix_dist(f, k1, k2, pp, xc):
+    u = xc[..., :2] / xc[..., 2:3]
+    r2 = (u * u).sum(-1)
+    s = 1 + k1 * r2 + k2 * r2 * r2
+    return pp + (f * s)[..., None] * u
+
+
+def _visible(xy, z):
+    return (z > 0.5) & (xy[..., 0] > 2) & (xy[..., 0] < IMG_W - 2) & (xy[..., 1] > 2) & (xy[..., 1] < IMG_H - 2)
+
+
+def _track_lengths(rng, cfg: SceneConfig, n):
+    lo, hi = cfg.track_min, cfg.track_max
+    if cfg.track_mean <= 0:
+        return rng.integers(lo, hi + 1, size=n)
+    ks = np.arange(lo, hi + 1)
+    best = None
+    for p in np.linspace(0.01, 0.99, 981):       # pick the geometric rate whose truncated mean fits
+        w = p * (1 - p) ** (ks - lo)
+        m = (w * ks).sum() / w.sum()
+        if best is None or abs(m - cfg.track_mean) < best[0]:
+            best = (abs(m - cfg.track_mean), w / w.sum())
+    return rng.choice(ks, size=n, p=best[1])
+
+
+# --------------------------------------------------------------------------
+def make_scene(cfg: SceneConfig) -> dict:
+    rng = np.random.default_rng(cfg.seed)
+    Nc = cfg.n_cams
+    # ---- cameras on a ring (horizontal, y up) or a sphere, looking at the origin with 2 deg jitter
+    if cfg.ring:
+        a = 2 * np.pi * np.arange(Nc) / Nc + rng.uniform(0, 0.1, Nc)
+        dirs = np.stack([np.cos(a), 0.15 * rng.normal(size=Nc), np.sin(a)], 1)
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    else:
+        dirs = _rand_unit(rng, Nc)
+    centers = 8.0 * dirs
+    fwd = -dirs
+    jit = _axis_angle_mat(_rand_unit(rng, Nc), np.deg2rad(2.0) * rng.normal(size=Nc))
+    fwd = np.einsum("nij,nj->ni", jit, fwd)
+    up = np.where(np.abs(fwd[:, 1:2]) > 0.99, np.array([[1.0, 0, 0]]), np.array([[0, 1.0, 0]]))
+    xax = np.cross(up, fwd); xax /= np.linalg.norm(xax, axis=1, keepdims=True)
+    yax = np.cross(fwd, xax)
+    Rgt = np.stack([xax, yax, fwd], 1)                 # rows = camera axes in world
+    tgt = -np.einsum("nij,nj->ni", Rgt, centers)
+    f = rng.uniform(550, 650, Nc)
+    k1 = rng.uniform(-0.1, 0.1, Nc)
+    k2 = rng.uniform(-0.02, 0.02, Nc)
+    pp = np.tile([IMG_W / 2, IMG_H / 2], (Nc, 1)) + rng.uniform(-5, 5, (Nc, 2))
+
+    # ---- k nearest cameras (by angle) of each camera, itself included
+    K = min(cfg.k_near, Nc)
+    near = np.argsort(-(dirs @ dirs.T), axis=1)[:, :K]
+
+    # ---- groups
+    npl = cfg.n_planes
+    pl_axis = rng.integers(0, 3, npl)
+    pl_sign = rng.choice([-1.0, 1.0], npl)
+    pl_n = np.zeros((npl, 3)); pl_n[np.arange(npl), pl_axis] = pl_sign
+    pl_w = rng.uniform(-2.5, 2.5, npl)
+    nv = cfg.n_vps
+    vp = np.zeros((nv, 3))
+    for i in range(min(nv, 3)):
+        vp[i, i] = 1.0
+    if nv > 3:
+        vp[3:] = _rand_unit(rng, nv - 3)
+    vp_axis = np.full(nv, -1); vp_axis[: min(nv, 3)] = np.arange(min(nv, 3))
+
+    def sample_on_plane(pidx):
+        n = len(pidx)
+        X = rng.uniform(-HALF, HALF, (n, 3))
+        ax = pl_axis[pidx]
+        X[np.arange(n), ax] = -pl_w[pidx] / pl_sign[pidx]
+        return X
+
+    # ---- wireframe grids: junction points on planes joined by row / column lines
+    n_edges = cfg.n_wire_edges if npl > 0 else 0
+    n_junc = n_edges // 2
+    wf_pts, wf_pl, wf_lines_c, wf_lines_d, wf_lines_len, wf_lines_pl, edges = [], [], [], [], [], [], []
+    if n_junc > 0:
+        per_plane = np.full(npl, n_junc // npl); per_plane[: n_junc % npl] += 1
+        lid = 0
+        for p in range(npl):
+            g = int(math.ceil(math.sqrt(max(per_plane[p], 1))))
+            if per_plane[p] == 0:
+                continue
+            ax = pl_axis[p]; o = [i for i in range(3) if i != ax]
+            c0 = rng.uniform(-2.0, 2.0, 2); step = rng.uniform(0.15, 0.3)
+            coords = [(i, j) for i in range(g) for j in range(g)][: per_plane[p]]
+            rows = sorted({i for i, _ in coords}); cols = sorted({j for _, j in coords})
+            row_id, col_id = {}, {}
+            for i in rows:
+                d = np.zeros(3); d[o[1]] = 1.0
+                c = np.zeros(3); c[ax] = -pl_w[p] / pl_sign[p]; c[o[0]] = c0[0] + i * step; c[o[1]] = c0[1] + (g - 1) * step / 2
+                wf_lines_c.append(c); wf_lines_d.append(d); wf_lines_len.append(max(g - 1, 1) * step + 0.2); wf_lines_pl.append(p)
+                row_id[i] = lid; lid += 1
+            for j in cols:
+                d = np.zeros(3); d[o[0]] = 1.0
+                c = np.zeros(3); c[ax] = -pl_w[p] / pl_sign[p]; c[o[0]] = c0[0] + (g - 1) * step / 2; c[o[1]] = c0[1] + j * step
+                wf_lines_c.append(c); wf_lines_d.append(d); wf_lines_len.append(max(g - 1, 1) * step + 0.2); wf_lines_pl.append(p)
+                col_id[j] = lid; lid += 1
+            for i, j in coords:
+                X = np.zeros(3); X[ax] = -pl_w[p] / pl_sign[p]; X[o[0]] = c0[0] + i * step; X[o[1]] = c0[1] + j * step
+                k = len(wf_pts)
+                wf_pts.append(X); wf_pl.append(p)
+                edges.append((k, row_id[i])); edges.append((k, col_id[j]))
+    n_wf_pts = len(wf_pts)
+    n_wf_lines = len(wf_lines_c)
+
+    # ---- points: wireframe junctions first, then plane points, then free points
+    Np = max(cfg.n_points, n_wf_pts)
+    P = np.empty((Np, 3))
+    p_plane = np.full(Np, -1)
+    if n_wf_pts:
+        P[:n_wf_pts] = np.array(wf_pts); p_plane[:n_wf_pts] = np.array(wf_pl)
+    rest = np.arange(n_wf_pts, Np)
+    on = rest[rng.random(len(rest)) < cfg.frac_points_on_plane] if npl else rest[:0]
+    if len(on):
+        p_plane[on] = rng.integers(0, npl, len(on))
+        P[on] = sample_on_plane(p_plane[on])
+    free = np.setdiff1d(rest, on)
+    P[free] = rng.uniform(-HALF, HALF, (len(free), 3))
+
+    # ---- lines: wireframe lines first, then plane lines, then free lines
+    Nl = max(cfg.n_lines, n_wf_lines)
+    Lc = np.empty((Nl, 3)); Ld = np.empty((Nl, 3)); Llen = rng.uniform(0.5, 2.0, Nl)
+    l_plane = np.full(Nl, -1); l_vp = np.full(Nl, -1)
+    if n_wf_lines:
+        Lc[:n_wf_lines] = np.array(wf_lines_c); Ld[:n_wf_lines] = np.array(wf_lines_d)
+        Llen[:n_wf_lines] = np.array(wf_lines_len); l_plane[:n_wf_lines] = np.array(wf_lines_pl)
+    rest = np.arange(n_wf_lines, Nl)
+    on = rest[rng.random(len(rest)) < cfg.frac_lines_on_plane] if npl else rest[:0]
+    if len(on):
+        l_plane[on] = rng.integers(0, npl, len(on))
+        Lc[on] = sample_on_plane(l_plane[on]) * 0.8
+        Lc[on, pl_axis[l_plane[on]]] = -pl_w[l_plane[on]] / pl_sign[l_plane[on]]
+        # in-plane direction: an axis (Manhattan) or a random in-plane direction
+        for i in on:
+            ax = pl_axis[l_plane[i]]
+            if rng.random() < 0.7:
+                d = np.zeros(3); d[rng.choice([k for k in range(3) if k != ax])] = 1.0
+            else:
+                d = rng.normal(size=3); d[ax] = 0.0; d /= np.linalg.norm(d)
+            Ld[i] = d
+    free = np.setdiff1d(rest, on)
+    Lc[free] = rng.uniform(-HALF * 0.8, HALF * 0.8, (len(free), 3))
+    Ld[free] = _rand_unit(rng, len(free))
+    if nv > 0:
+        # free lines: a share takes a VP direction
+        take = free[rng.random(len(free)) < cfg.frac_lines_vp]
+        Ld[take] = vp[rng.integers(0, nv, len(take))]
+    # VP associations: a line whose direction is (up to sign) a VP direction
+    if nv > 0:
+        dots = np.abs(Ld @ vp.T)
+        best = dots.argmax(1)
+        assoc = dots[np.arange(Nl), best] > 1 - 1e-12
+        keep = assoc & (rng.random(Nl) < max(cfg.frac_lines_vp, 0.8))
+        l_vp[keep] = best[keep]
+    Ld = Ld * np.where(rng.random(Nl) < 0.5, 1.0, -1.0)[:, None]
+    E1 = Lc - 0.5 * Llen[:, None] * Ld
+    E2 = Lc + 0.5 * Llen[:, None] * Ld
+
+    # ---- tracks: anchor camera uniform, views among its K nearest where the feature is visible
+    def draw_tracks(pts_list, n):
+        anchor = rng.integers(0, Nc, n)
+        cand = near[anchor]                              # [n, K]
+        ok = np.ones((n, K), bool)
+        for X in pts_list:
+            xc = _to_cam(Rgt[cand], tgt[cand], X[:, None, :])
+            xy = _pix_pinhole(f[cand], pp[cand], xc)
+            ok &= _visible(xy, xc[..., 2])
+        L = _track_lengths(rng, cfg, n)
+        key = rng.random((n, K)) + np.where(ok, 0.0, 2.0)
+        order = np.argsort(key, axis=1)
+        nvis = ok.sum(1)
+        L = np.minimum(L, nvis)
+        sel = np.take_along_axis(cand, order, 1)
+        mask = np.arange(K)[None, :] < L[:, None]
+        return sel, mask
+
+    p_sel, p_mask = draw_tracks([P], Np)
+    l_sel, l_mask = draw_tracks([E1, E2], Nl)
+
+    def pack(sel, mask):
+        fid = np.repeat(np.arange(sel.shape[0]), mask.sum(1))
+        cam = sel[mask]
+        return cam.astype(np.int32), fid.astype(np.int32)
+
+    pc, pf = pack(p_sel, p_mask)
+    lc, lf = pack(l_sel, l_mask)
+    # drop features seen fewer than 2 times from the observation lists (they keep their params)
+    def pt_obs(cam, fid):
+        xc = _to_cam(Rgt[cam], tgt[cam], P[fid])
+        clean_d = _pix_dist(f[cam], k1[cam], k2[cam], pp[cam], xc)
+        clean_u = _pix_pinhole(f[cam], pp[cam], xc)
+        n = rng.normal(0, cfg.sigma_px, (len(cam), 2))
+        md, mu = clean_d + n, clean_u + n
+        out = rng.random(len(cam)) < cfg.outlier_frac
+        rnd = np.stack([rng.uniform(0, IMG_W, out.sum()), rng.uniform(0, IMG_H, out.sum())], 1)
+        md[out] = rnd; mu[out] = rnd
+        return md, mu
+
+    def ln_obs(cam, fid):
+        a = _pix_pinhole(f[cam], pp[cam], _to_cam(Rgt[cam], tgt[cam], E1[fid]))
+        b = _pix_pinhole(f[cam], pp[cam], _to_cam(Rgt[cam], tgt[cam], E2[fid]))
+        m = np.concatenate([a, b], 1) + rng.normal(0, cfg.sigma_px, (len(cam), 4))
+        out = rng.random(len(cam)) < cfg.outlier_frac
+        m[out] = np.stack([rng.uniform(0, IMG_W, out.sum()), rng.uniform(0, IMG_H, out.sum()),
+                           rng.uniform(0, IMG_W, out.sum()), rng.uniform(0, IMG_H, out.sum())], 1)
+        return m
+
+    pm_d, pm_u = pt_obs(pc, pf)
+    lm = ln_obs(lc, lf)
+
+    obs = {}
+    neg = lambda n: np.full(n, -1, np.int32)
+    obs["point"] = dict(cam=pc, feat=pf, other=neg(len(pc)), meas=pm_d)
+    obs["line"] = dict(cam=lc, feat=lf, other=neg(len(lc)), meas=lm)
+    sel = p_plane[pf] >= 0
+    obs["plane_point"] = dict(cam=pc[sel], feat=pf[sel], other=p_plane[pf[sel]].astype(np.int32),
+                              meas=np.zeros((sel.sum(), 0)))
+    sel = l_plane[lf] >= 0
+    obs["plane_line"] = dict(cam=lc[sel], feat=lf[sel], other=l_plane[lf[sel]].astype(np.int32), meas=lm[sel])
+    vl = np.nonzero(l_vp >= 0)[0]
+    obs["vp"] = dict(cam=neg(len(vl)), feat=vl.astype(np.int32), other=l_vp[vl].astype(np.int32),
+                     meas=np.zeros((len(vl), 0)))
+    # cross-feature residuals of each wireframe edge (point j on line k)
+    p2l = {"cam": [], "feat": [], "other": [], "meas": []}
+    l2p = {"cam": [], "feat": [], "other": [], "meas": []}
+    if edges:
+        # index observation rows by (feature, cam)
+        prow = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(pf, pc)) if a < n_wf_pts}
+        lrow = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(lf, lc)) if a < n_wf_lines}
+        pv = {}
+        for (j, c), i in prow.items():
+            pv.setdefault(j, []).append(c)
+        lv = {}
+        for (k, c), i in lrow.items():
+            lv.setdefault(k, []).append(c)
+        for j, k in edges:
+            vp_, vl_ = set(pv.get(j, [])), set(lv.get(k, []))
+            for c in sorted(vl_ - vp_):          # line seen, point not: point -> observed line
+                p2l["cam"].append(c); p2l["feat"].append(j); p2l["other"].append(k)
+                p2l["meas"].append(lm[lrow[(k, c)]])
+            for c in sorted(vp_ - vl_):          # point seen, line not: observed point -> line
+                l2p["cam"].append(c); l2p["feat"].append(k); l2p["other"].append(j)
+                l2p["meas"].append(pm_u[prow[(j, c)]])
+    for name, d in (("p2l", p2l), ("l2p", l2p)):
+        md = MEAS_DIM[name]
+        obs[name] = dict(cam=np.array(d["cam"], np.int32), feat=np.array(d["feat"], np.int32),
+                         other=np.array(d["other"], np.int32),
+                         meas=np.array(d["meas"], np.float64).reshape(-1, md))
+
+    # ---- ground truth and perturbed initial values
+    qgt = _mat_to_quat(Rgt)
+    gt_lines = np.concatenate([Ld, np.cross(E1, Ld)], 1)
+    gt_planes = np.concatenate([pl_n, pl_w[:, None]], 1)
+    dR = _axis_angle_mat(_rand_unit(rng, Nc), np.deg2rad(cfg.rot_noise_deg) * rng.normal(size=Nc))
+    R0 = dR @ Rgt
+    t0 = tgt + rng.normal(0, cfg.trans_noise, (Nc, 3))
+    P0 = P + rng.normal(0, cfg.feat_noise, P.shape)
+    e1 = E1 + rng.normal(0, cfg.feat_noise, E1.shape)
+    e2 = E2 + rng.normal(0, cfg.feat_noise, E2.shape)
+    d0 = e2 - e1; d0 /= np.linalg.norm(d0, axis=1, keepdims=True)
+    lines0 = np.concatenate([d0, np.cross(e1, d0)], 1)
+    if npl:
+        n0 = np.einsum("nij,nj->ni", _axis_angle_mat(_rand_unit(rng, npl), np.deg2rad(cfg.group_rot_noise_deg) * rng.normal(size=npl)), pl_n)
+        planes0 = np.concatenate([n0, (pl_w + rng.normal(0, cfg.group_off_noise, npl))[:, None]], 1)
+    else:
+        planes0 = np.zeros((0, 4))
+    if nv:
+        vps0 = np.einsum("nij,nj->ni", _axis_angle_mat(_rand_unit(rng, nv), np.deg2rad(cfg.group_rot_noise_deg) * rng.normal(size=nv)), vp)
+    else:
+        vps0 = np.zeros((0, 3))
+    intr = np.stack([f, k1, k2], 1)
+    fixed = np.zeros(Nc, bool)
+    fixed[0] = True                                    # gauge: camera 0's pose is held
+    scene = dict(
+        name=cfg.name, seed=cfg.seed, fixed=fixed,
+        cams=dict(q=_mat_to_quat(R0), t=t0, intr=intr, pp=pp),
+        points=P0, lines=lines0, planes=planes0, vps=vps0,
+        obs=obs,
+        gt=dict(cams=dict(q=qgt, t=tgt.copy(), intr=intr.copy(), pp=pp.copy()), points=P.copy(),
+                lines=gt_lines, planes=gt_planes, vps=vp.copy()),
+        info=dict(n_wf_points=n_wf_pts, n_wf_lines=n_wf_lines, n_edges=len(edges),
+                  point_plane=p_plane, line_plane=l_plane, line_vp=l_vp),
+    )
+    return scene
+
+
+def noise_free(cfg: SceneConfig) -> dict:
+    """The same scene with zero pixel noise, no outliers, and initial values at ground truth."""
+    c = dataclasses.replace(cfg, sigma_px=0.0, outlier_frac=0.0, rot_noise_deg=0.0, trans_noise=0.0,
+                            feat_noise=0.0, group_rot_noise_deg=0.0, group_off_noise=0.0)
+    s = make_scene(c)
+    s["cams"] = {k: v.copy() for k, v in s["gt"]["cams"].items()}
+    s["points"] = s["gt"]["points"].copy(); s["lines"] = s["gt"]["lines"].copy()
+    s["planes"] = s["gt"]["planes"].copy(); s["vps"] = s["gt"]["vps"].copy()
+    return s
+
+
+def counts(scene: dict) -> dict:
+    return {k: int(len(v["cam"])) for k, v in scene["obs"].items()}

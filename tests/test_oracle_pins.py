@@ -1,0 +1,353 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test ties an oracle function to the paper or to mathematics: hand-worked
+closed forms (tests/golden/closed_forms.json), finite differences, algebraic
+identities from Appendix B, the first-order expansion of Eq. 9, the dense full
+normal-equation solve (the Schur step must equal it, Eq. 3 / Eq. 5), an
+independent minimiser (scipy's trust-region Newton method), and invariants (monotone accepted
+cost, zero residual at noise-free ground truth, similarity invariance).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize
+import scipy.spatial.transform
+import torch
+
+from oracle import ba_oracle as O
+from scenegen import config, make_scene, noise_free
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+def _case(name):
+    return next(c for c in GOLD["cases"] if c["name"] == name)
+
+
+def _cam_vec(c):
+    return torch.tensor(c["q"] + c["t"] + [c["f"], c["k1"], c["k2"]] + c["pp"], dtype=torch.float64)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = make_scene(config("tiny"))
+    st = O.state_from_scene(s)
+    fixed = np.zeros(len(st["cams"]), bool); fixed[0] = True
+    return s, st, fixed
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("name", ["point_projection_radial", "point_projection_translated"])
+def test_point_projection_closed_form(name):
+    c = _case(name)
+    cam = _cam_vec(c["cam"])
+    R = O.quat_to_R(cam[:4])
+    x, z = O.pi_point(R, cam[4:7], cam, torch.tensor(c["X"]))
+    np.testing.assert_allclose(x.numpy(), c["pi"], rtol=0, atol=1e-10)
+
+
+def test_line_rho_closed_form():
+    c = _case("line_reprojection_rho")
+    cam = _cam_vec(c["cam"])
+    R = O.quat_to_R(cam[:4])
+    l = O.pi_line(R, cam[4:7], cam, torch.tensor(c["line"]))
+    r, _ = O.rho(l, torch.tensor(c["seg"]))
+    np.testing.assert_allclose(r.numpy(), c["rho"], atol=1e-10)
+    # the displacement vectors do not change when the line's sign flips (Eq. 8 difference well defined)
+    r2, _ = O.rho(-l, torch.tensor(c["seg"]))
+    np.testing.assert_allclose(r2.numpy(), c["rho"], atol=1e-10)
+
+
+def test_plane_point_closed_form():
+    c = _case("plane_point_projection")
+    p = O.plane_project_point(torch.tensor(c["plane"]), torch.tensor(c["X"]))
+    np.testing.assert_allclose(p.numpy(), c["proj"], atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["plane_line_projection", "plane_line_projection_offset"])
+def test_plane_line_closed_form(name):
+    c = _case(name)
+    L = O.plane_project_line(torch.tensor(c["plane"]), torch.tensor(c["line"]))
+    np.testing.assert_allclose(L.numpy(), c["proj"], atol=1e-14)
+
+
+def test_vp_closed_form():
+    c = _case("vp_angle")
+    r = torch.linalg.cross(torch.tensor(c["d"]), torch.tensor(c["v"]))
+    assert abs(float(torch.linalg.norm(r)) - c["abs"]) < 1e-15
+
+
+# ---------------------------------------------------------------- Appendix B identities
+def test_vp_identity_random():
+    """|d x v| = |v - (v.d) d| = sin(theta) for unit d, v (Appendix B, VP)."""
+    g = np.random.default_rng(0)
+    d = g.normal(size=(200, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+    v = g.normal(size=(200, 3)); v /= np.linalg.norm(v, axis=1, keepdims=True)
+    a = np.linalg.norm(np.cross(d, v), axis=1)
+    b = np.linalg.norm(v - (v * d).sum(1, keepdims=True) * d, axis=1)
+    th = np.arccos(np.clip((d * v).sum(1), -1, 1))
+    np.testing.assert_allclose(a, b, atol=1e-14)
+    np.testing.assert_allclose(a, np.sin(th), atol=1e-12)
+    r = O.res_vp(torch.zeros(6), torch.zeros(4), torch.zeros(3), torch.zeros(12),
+                 torch.tensor(np.concatenate([d[0], np.cross(np.array([0.3, -1.0, 2.0]), d[0])])),
+                 torch.tensor(np.concatenate([v[0], [0.0]])), torch.zeros(4))[0]
+    assert abs(float(torch.linalg.norm(r)) - a[0]) < 1e-14
+
+
+def test_plane_line_projection_properties():
+    """m'.d' = 0 (Pluecker constraint), n.d' = 0, points of the projected line lie on the plane, and
+    m' = p' x d' for the orthogonal projection p' of a point of the line (Appendix B)."""
+    g = np.random.default_rng(1)
+    for _ in range(100):
+        n = g.normal(size=3); n /= np.linalg.norm(n)
+        w = g.normal()
+        p = g.normal(size=3) * 2
+        d = g.normal(size=3) * g.uniform(0.3, 3)
+        m = np.cross(p, d)
+        Lp = O.plane_project_line(torch.tensor(np.r_[n, w]), torch.tensor(np.r_[d, m])).numpy()
+        d2, m2 = Lp[:3], Lp[3:]
+        assert abs(m2 @ d2) < 1e-10 * (1 + np.linalg.norm(m2) * np.linalg.norm(d2))
+        assert abs(n @ d2) < 1e-12 * np.linalg.norm(d)
+        pp = p - (n @ p + w) * n
+        np.testing.assert_allclose(m2, np.cross(pp, d2), atol=1e-10 * (1 + np.linalg.norm(m2)))
+        # a point of the projected line: p0 = d' x m' / |d'|^2 satisfies the plane equation
+        p0 = np.cross(d2, m2) / (d2 @ d2)
+        assert abs(n @ p0 + w) < 1e-9 * (1 + abs(w) + np.linalg.norm(p0))
+
+
+# ---------------------------------------------------------------- residuals vanish on groups
+def test_group_residuals_vanish_on_group():
+    """Eq. 7 / Eq. 8: a point or line that lies on its plane gives r_g = 0; Eq. 6: an associated
+    line parallel to its VP gives 0; Eq. 11 / 12 vanish for exact junction observations."""
+    s = noise_free(config("tiny"))
+    st = O.state_from_scene(s)
+    for k in ("plane_point", "plane_line", "vp", "p2l", "l2p", "point", "line"):
+        r, v = O.residuals(st, s["obs"], k)
+        assert v.all()
+        assert float(r.abs().max()) < 1e-9, k
+
+
+def test_noise_free_zero_cost_and_zero_step():
+    s = noise_free(config("tiny"))
+    st = O.state_from_scene(s)
+    opt = O.Options()
+    E, Epx = O.cost(st, s["obs"], opt)
+    assert E <= 1e-18
+    fixed = np.zeros(len(st["cams"]), bool); fixed[0] = True
+    lay = O.Layout(st, fixed)
+    delta, info = O.solve_step(st, s["obs"], opt, 1e-4, lay)
+    assert np.abs(delta).max() < 1e-9
+
+
+# ---------------------------------------------------------------- Jacobians by finite differences
+@pytest.mark.parametrize("kind", O.KINDS)
+def test_jacobian_finite_differences(tiny, kind):
+    """Central differences through the retraction x (+) delta agree with the oracle's J."""
+    s, st, _ = tiny
+    o = s["obs"][kind]
+    n = min(40, len(o["feat"]))
+    sub = {k: {kk: vv[:n] for kk, vv in o.items()} for k, o in s["obs"].items()}
+    r, v, Jc, Jf, Jg = O.residuals(st, sub, kind, with_jac=True)
+    cam, feat, grp, meas = O._records(st, sub, kind)
+    kf = O.FDOF[O.FEAT[kind]]
+    fn = O.RES_FN[kind]
+    h = 1e-6
+    for blk, dim, J in ((0, 6, Jc), (1, kf, Jf), (2, 3, Jg)):
+        for j in range(dim):
+            def ev(sgn):
+                out = []
+                for i in range(n):
+                    d = [torch.zeros(6), torch.zeros(kf), torch.zeros(3)]
+                    d[blk] = d[blk].clone(); d[blk][j] = sgn * h
+                    out.append(fn(d[0], d[1], d[2], cam[i], feat[i], grp[i], meas[i])[0])
+                return torch.stack(out)
+            fd = (ev(1) - ev(-1)) / (2 * h)
+            scale = float(J.abs().max()) + 1e-12
+            err = float((fd - J[:, :, j]).abs().max())
+            assert err <= 2e-6 * scale + 1e-7, (kind, blk, j, err, scale)
+
+
+def test_first_order_group_residual():
+    """Eq. 9: r_g^(p) = J_i delta + O(|delta|^2) with delta = X - Proj(X), J_i = d pi / d X."""
+    s = noise_free(config("tiny"))
+    st = O.state_from_scene(s)
+    o = s["obs"]["plane_point"]
+    i = 3
+    cam = torch.tensor(st["cams"][o["cam"][i]])
+    P = torch.tensor(st["planes"][o["other"][i]])
+    X0 = torch.tensor(st["points"][o["feat"][i]])          # on the plane
+    R = O.quat_to_R(cam[:4])
+    J = torch.func.jacfwd(lambda X: O.pi_point(R, cam[4:7], cam, X)[0])(X0)
+    errs = []
+    for eps in (1e-1, 1e-2, 1e-3):
+        X = X0 + eps * P[:3]                               # move off the plane along the normal
+        delta = X - O.plane_project_point(P, X)
+        r = O.pi_point(R, cam[4:7], cam, X)[0] - O.pi_point(R, cam[4:7], cam, O.plane_project_point(P, X))[0]
+        lin = J @ delta
+        errs.append(float(torch.linalg.norm(r - lin) / torch.linalg.norm(lin)))
+    # relative error shrinks linearly with |delta|
+    assert errs[1] < errs[0] * 0.2 and errs[2] < errs[1] * 0.2, errs
+
+
+# ---------------------------------------------------------------- the Schur step equals the full solve
+def test_schur_equals_dense_full_solve(tiny):
+    s, st, fixed = tiny
+    opt = O.Options(solver="dense")
+    lay = O.Layout(st, fixed)
+    lam = 1e-3
+    Jt, rt = O.linearize(st, s["obs"], opt, lay)
+    H, g = O.normal_equations(Jt, rt)
+    D = O.damping_diag(H)
+    full = np.linalg.solve(H.toarray() + np.diag(lam * D), -g)
+    delta, info = O.solve_step(st, s["obs"], opt, lam, lay, (Jt, rt))
+    rel = np.linalg.norm(delta - full) / np.linalg.norm(full)
+    assert rel < 1e-10, rel
+    # predicted decrease: -g.d - 1/2 d^T H d computed two ways
+    pred2 = -g @ full - 0.5 * full @ (H @ full)
+    assert abs(info["pred"] - pred2) <= 1e-9 * abs(pred2)
+
+
+def test_pcg_matches_dense_cholesky(tiny):
+    s, st, fixed = tiny
+    lay = O.Layout(st, fixed)
+    Jt, rt = O.linearize(st, s["obs"], O.Options(), lay)
+    H, g = O.normal_equations(Jt, rt)
+    S, b, *_ = O.reduced_system(H, g, 1e-2, lay)
+    Sd = S.toarray()
+    assert np.allclose(Sd, Sd.T, atol=1e-9 * np.abs(Sd).max())
+    L = np.linalg.cholesky(Sd)                      # S is SPD
+    x_chol = np.linalg.solve(L.T, np.linalg.solve(L, b))
+    x, it, rel = O.pcg(S, b, lay.a_blocks, 1e-12, 5000)
+    assert rel <= 1e-12
+    assert np.linalg.norm(b - Sd @ x) <= 1e-11 * np.linalg.norm(b)
+    np.testing.assert_allclose(x, x_chol, rtol=0, atol=1e-9 * np.abs(x_chol).max())
+
+
+# ---------------------------------------------------------------- S sparsity (Section 3.3 / 3.4)
+def test_schur_pattern_matches_visibility(tiny):
+    """A camera-group block of S is non-zero iff the camera sees a feature associated with the group;
+    a camera-camera block iff the two cameras share a feature through any residual (Section 3.3, 3.4)."""
+    s, st, fixed = tiny
+    lay = O.Layout(st, fixed)
+    Jt, rt = O.linearize(st, s["obs"], O.Options(), lay)
+    H, g = O.normal_equations(Jt, rt)
+    S, *_ = O.reduced_system(H, g, 1e-3, lay)
+    Sd = np.abs(S.toarray())
+    nc, npl = lay.nc, lay.npl
+    # entity sets per feature from the raw observation lists (brute force)
+    ent = {}
+    for k in O.KINDS:
+        o = s["obs"][k]
+        ft = O.FEAT[k]
+        for i in range(len(o["feat"])):
+            key = (ft, int(o["feat"][i]))
+            e = ent.setdefault(key, set())
+            if O.HAS_CAM[k]:
+                e.add(("c", int(o["cam"][i])))
+            if k in ("plane_point", "plane_line"):
+                e.add(("p", int(o["other"][i])))
+            if k == "vp":
+                e.add(("v", int(o["other"][i])))
+    def col(e):
+        t, i = e
+        if t == "c":
+            return None if fixed[i] else int(lay.cam_col[i]), 6
+        if t == "p":
+            return int(lay.plane_col[i]), 3
+        return int(lay.vp_col[i]), 2
+    expect = set()
+    for es in ent.values():
+        for a in es:
+            for b in es:
+                expect.add((a, b))
+    ents = [("c", i) for i in range(nc)] + [("p", i) for i in range(npl)] + [("v", i) for i in range(lay.nv)]
+    for a in ents:
+        ca = col(a)
+        if ca[0] is None:
+            continue
+        for b in ents:
+            cb = col(b)
+            if cb[0] is None:
+                continue
+            blk = Sd[ca[0]:ca[0] + ca[1], cb[0]:cb[0] + cb[1]]
+            nz = blk.max() > 0
+            if a == b:
+                continue
+            assert nz == ((a, b) in expect), (a, b)
+
+
+# ---------------------------------------------------------------- invariants of the LM
+def test_lm_accepted_cost_monotone(tiny):
+    s, st, fixed = tiny
+    _, info = O.solve(st, s["obs"], O.Options(), max_iters=8, fixed=fixed)
+    E = [r["E"] for r in info["reports"]]
+    assert all(b <= a for a, b in zip(E, E[1:]))
+    for r in info["reports"]:
+        if r["accepted"]:
+            assert r["E_new"] < r["E"]
+
+
+def _similarity(st, s_, Rs, tp):
+    """X -> s R X + t' applied to the whole scene; poses (R_i R^T, s t_i - R_i R^T t')."""
+    new = {k: v.copy() for k, v in st.items()}
+    new["points"] = s_ * st["points"] @ Rs.T + tp
+    Rc = O.quat_to_R(torch.tensor(st["cams"][:, :4])).numpy()
+    Rn = Rc @ Rs.T
+    new["cams"][:, :4] = O.R_to_quat(Rn)
+    new["cams"][:, 4:7] = s_ * st["cams"][:, 4:7] - np.einsum("nij,j->ni", Rn, tp)
+    d = st["lines"][:, :3] @ Rs.T
+    m = s_ * st["lines"][:, 3:] @ Rs.T + np.cross(tp, d)
+    new["lines"] = np.concatenate([d, m], 1)
+    n = st["planes"][:, :3] @ Rs.T
+    new["planes"] = np.concatenate([n, (s_ * st["planes"][:, 3] - n @ tp)[:, None]], 1)
+    new["vps"] = st["vps"] @ Rs.T
+    return new
+
+
+def test_cost_similarity_invariant(tiny):
+    """Every residual kind is pixel- or angle-based, so E is unchanged by a similarity of the scene
+    (Section 1 / Section 3.3: no scale-dependent 3D terms)."""
+    s, st, _ = tiny
+    opt = O.Options()
+    E0 = O.cost(st, s["obs"], opt)
+    Rs = scipy.spatial.transform.Rotation.from_rotvec([0.3, -0.7, 0.2]).as_matrix()
+    st2 = _similarity(st, 2.7, Rs, np.array([1.0, -3.0, 0.5]))
+    E1 = O.cost(st2, s["obs"], opt)
+    assert abs(E1[0] - E0[0]) <= 1e-11 * E0[0]
+    assert abs(E1[1] - E0[1]) <= 1e-11 * E0[1]
+
+
+def test_classical_ba_matches_independent_minimiser():
+    """Point-only special case (Eq. 1): the LM's converged cost equals the minimum that scipy's
+    trust-region Newton method (exact Hessian) finds for the same robust cost, written directly over
+    rotation vectors, translations and points.  Two cameras are held fixed in both, so the
+    minimum is isolated."""
+    cfg = config("tiny", n_cams=5, n_points=40, n_lines=0, n_planes=0, n_vps=0, n_wire_edges=0,
+                 outlier_frac=0.0, seed=11)
+    s = make_scene(cfg)
+    obs = s["obs"]
+    st = O.state_from_scene(s)
+    fixed = np.zeros(5, bool); fixed[:2] = True
+    st_lm, info = O.solve(st, obs, O.Options(rel_cost_tol=1e-13, solver="dense"), max_iters=300, fixed=fixed)
+    assert info["converged"]
+    o = obs["point"]
+    cam = torch.tensor(st["cams"][o["cam"]]); meas = torch.tensor(o["meas"])
+    ci = torch.tensor(o["cam"]).long(); fi = torch.tensor(o["feat"]).long()
+    R0 = O.quat_to_R(torch.tensor(st["cams"][:, :4]))
+    t0 = torch.tensor(st["cams"][:, 4:7])
+
+    def E(x):
+        Rf = torch.linalg.matrix_exp(O.skew(x[:9].reshape(3, 3))) @ R0[2:]
+        R = torch.cat([R0[:2], Rf]); t = torch.cat([t0[:2], x[9:18].reshape(3, 3)])
+        pi, _ = O.pi_point(R[ci], t[ci], cam, x[18:].reshape(-1, 3)[fi])
+        return 0.5 * torch.log1p(((pi - meas) ** 2).sum(-1)).sum()     # w = 1, a = 1
+
+    fg = lambda xn: (float(E(torch.tensor(xn))), torch.func.grad(E)(torch.tensor(xn)).numpy())
+    hs = lambda xn: torch.func.hessian(E)(torch.tensor(xn)).numpy()
+    x0 = np.concatenate([np.zeros(9), st["cams"][2:, 4:7].ravel(), st["points"].ravel()])
+    res = scipy.optimize.minimize(fg, x0, jac=True, hess=hs, method="trust-exact",
+                                  options=dict(gtol=1e-11, maxiter=500))
+    assert abs(info["E"] - res.fun) <= 1e-8 * res.fun, (info["E"], res.fun)
