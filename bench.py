@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the holistic-BA LM step on one B300 (per process; N processes = N independent replicas).
+
+A "step" is one Levenberg-Marquardt iteration of the library: linearise every residual, damp and invert the
+landmark blocks, accumulate the Schur complement over cameras and groups, solve it by block-Jacobi PCG,
+back-substitute, evaluate the FP64 cost of the candidate and accept or reject.  The one-time structure
+build (the analogue of a sparse solver's symbolic analysis) runs before the timed region and is reported
+separately.
+
+Workload (default "large"): 2000 cameras, 2M points, 200k lines, 300 planes and 200 VPs, about 20.5M
+residuals, mixed precision (FP32 Jacobians / Schur / S storage, FP64 landmark inverses, PCG vectors, cost
+and accept test).  Inputs are synthetic and seeded (scenegen), shaped like the paper's synthetic benchmark.
+
+Printed JSON (rank 0, one line): value = LM iterations per second of device time over K timed steps (max
+over ranks; N ranks = N replicas, so the value is the sum of their iterations over the slowest rank's time);
+e2e = the same metric through the public API with host buffers (problem creation, host->device copies,
+structure build, the solve to convergence and the read-back of the parameters inside the timed region);
+roofline of the dominant kernel; cpu_baseline = the FP64 oracle on a bounded sample of the same scene.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config large]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LM iter/s & time-to-converge (cost rel 1e-6) at 2k cams; PCG iters vs Jacobi"
+UNIT = "LM iter/s"
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12     # SMs x FP32 lanes x 2 (FMA) x max SM clock
+
+
+# ------------------------------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock / power / throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def scene_counts(s):
+    return {k: int(len(v["feat"])) for k, v in s["obs"].items()}
+
+
+def workload_desc(s, name):
+    c = scene_counts(s)
+    return (f"{name}: {len(s['cams']['q'])} cams, {len(s['points'])} points, {len(s['lines'])} lines, "
+            f"{len(s['planes'])} planes + {len(s['vps'])} VPs, {sum(c.values())} residuals "
+            f"({c['point']} point, {c['line']} line, {c['plane_point']}+{c['plane_line']} plane-induced, "
+            f"{c['vp']} VP, {c['p2l'] + c['l2p']} wireframe)")
+
+
+# per-unit algorithmic FP32 flops of the linearisation (residual + Jacobian + IRLS-weighted accumulation of
+# V_f, g_f and the per-slot blocks), counted from the formulas of each residual kind
+LIN_FLOPS = {"point": 354, "line": 1100, "plane_point": 660, "plane_line": 2700, "vp": 280, "p2l": 210, "l2p": 440}
+
+
+def roofline_models(n, dims):
+    """Algorithmic work per launch of each stage.  n = residual counts per kind; dims from the library."""
+    pairs_pt, pairs_ln = dims["pairs_point"], dims["pairs_line"]
+    return {
+        "linearize": ("alu", sum(LIN_FLOPS[k] * v for k, v in n.items()), "TFLOP/s"),
+        # S_ab -= Y_a^T W_b: 36 k FMA per slot pair (k = 3 point, 4 line)
+        "schur_items": ("alu", 2 * 36 * (3 * pairs_pt + 4 * pairs_ln), "TFLOP/s"),
+        # PCG: every iteration streams the stored blocks of S (36 values + a 4-byte column index) and touches
+        # the FP64 vectors (SpMV gather of p, x, r, z, Ap, p updates: ~10 reads/writes of 6 doubles per row)
+        "pcg": ("hbm", dims["pcg_iters_mean"] * (dims["stored_blocks"] * (36 * dims["Tbytes"] + 4)
+                                                  + dims["block_rows"] * 6 * 8 * 10), "GB/s"),
+    }
+
+
+# ------------------------------------------------------------------------------------------ oracle baseline
+def subsample(scene, frac):
+    """The scene restricted to the first `frac` of its points and lines (all cameras and groups)."""
+    import copy
+    s = copy.copy(scene)
+    npk = max(1, int(len(scene["points"]) * frac))
+    nlk = max(1, int(len(scene["lines"]) * frac))
+    obs = {}
+    for k, o in scene["obs"].items():
+        is_pt = k in ("point", "plane_point", "p2l")
+        keep = o["feat"] < (npk if is_pt else nlk)
+        obs[k] = {kk: vv[keep] for kk, vv in o.items()}
+    s["obs"] = obs
+    s["points"] = scene["points"][:npk]
+    s["lines"] = scene["lines"][:nlk]
+    return s
+
+
+def oracle_step_time(scene, frac):
+    """Seconds of one oracle LM iteration on the sub-sample, and the fraction of residuals it covers."""
+    import torch
+    from oracle import ba_oracle as O
+    sub = subsample(scene, frac)
+    n_all = sum(scene_counts(scene).values())
+    n_sub = sum(scene_counts(sub).values())
+    st = O.state_from_scene(sub)
+    lay = O.Layout(st, sub["fixed"])
+    opt = O.Options()
+    lm = O.LMState(opt.lambda0)
+    t = time.perf_counter()
+    O.lm_step(st, sub["obs"], opt, lm, lay)
+    dt = time.perf_counter() - t
+    return dt, n_sub / n_all, torch.get_num_threads()
+
+
+# ------------------------------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-frac", type=float, default=0.04)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-iters", type=int, default=200, help="LM cap of the end-to-end solve")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from scenegen import config as scfg, make_scene
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args, scfg, make_scene)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2609_04026_b300 as B
+
+    scene = make_scene(scfg(args.config, seed=scfg(args.config).seed + rank))
+    counts = scene_counts(scene)
+    prec = B.BA_MIXED if args.precision == "mixed" else B.BA_FP64
+    stream = torch.cuda.Stream()
+    opts = B.ba_default_options(precision=prec, cuda_stream=stream.cuda_stream)
+    p = B.ba_create(opts)
+    B.load_scene(p, scene)
+    t0 = time.perf_counter()
+    reps = [B.ba_lm_step(p)]                        # first step freezes the structure (built once)
+    first_step_s = time.perf_counter() - t0
+    for _ in range(args.warmup - 1):
+        reps.append(B.ba_lm_step(p))
+
+    smi = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                       os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+    smi.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    timed = [B.ba_lm_step(p) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = smi.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    na, nbf = B.ba_reduced_size(p)
+    B.ba_destroy(p)
+
+    kern = {k: float(np.mean([r.as_dict()["ms_kernel"][k] for r in timed])) for k in timed[0].KERNELS}
+    launches = int(sum(r.n_launches for r in timed))
+    pcg_iters = [r.pcg_iters for r in timed]
+    pcg_rel = [float("%.3g" % r.pcg_rel) for r in timed]
+    dims_S = {"block_rows": na, "stored_blocks": nbf, "block_density": round(nbf / max(na * na, 1), 4)}
+    value = world * args.steps / (ms / 1e3)
+
+    # ---------------- roofline of the dominant kernel stage (live CUDA-event times of the timed steps)
+    dims = pair_counts(scene)
+    dims.update(dims_S)
+    dims["pcg_iters_mean"] = float(np.mean(pcg_iters))
+    dims["Tbytes"] = 4 if prec == B.BA_MIXED else 8
+    models = roofline_models(counts, dims)
+    dom = max(kern, key=kern.get)
+    roof = None
+    if dom in models:
+        bound, work, unit = models[dom]
+        if bound == "hbm":
+            achieved = work / (kern[dom] / 1e3) / 1e9
+            pk = measured_peaks()
+            peak = pk["hbm_gbs"] if pk else 6400.0
+            src = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6.4 TB/s"
+        else:
+            achieved = work / (kern[dom] / 1e3) / 1e12
+            peak = FP32_PEAK_TFLOPS
+            src = "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"
+        roof = {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src}
+    else:
+        roof = {"bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "note": "no algorithmic model for this stage"}
+
+    # ---------------- end to end through the public API (host buffers) to convergence
+    e2e = None
+    ttc = None
+    if not args.no_e2e:
+        h2d = host_bytes(scene)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        o2 = B.ba_default_options(precision=prec, max_lm_iters=args.max_iters)
+        q = B.ba_create(o2)
+        B.load_scene(q, scene)
+        sr = B.ba_solve(q)
+        cams = B.ba_get_cameras(q, len(scene["cams"]["q"]))
+        pts = B.ba_get_features(q, B.BA_POINT, len(scene["points"]))
+        lns = B.ba_get_features(q, B.BA_LINE, len(scene["lines"]))
+        pl = B.ba_get_groups(q, B.BA_PLANE, len(scene["planes"]))
+        vp = B.ba_get_groups(q, B.BA_VP, len(scene["vps"]))
+        B.ba_destroy(q)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+        d2h = sum(a.nbytes for a in (cams, pts, lns, pl, vp))
+        e2e = {"value": round(sr.iters / wall, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d / max(sr.iters, 1)),
+               "d2h_bytes_per_step": int(d2h / max(sr.iters, 1)),
+               "note": "one job = create, host->device inputs, structure build, ba_solve to convergence, "
+                       "parameters read back; bytes per step = job bytes / iterations"}
+        ttc = {"seconds_wall": round(wall, 3), "seconds_solve": round((sr.ms_total - sr.ms_structure) / 1e3, 3),
+               "structure_ms": round(sr.ms_structure, 1), "iters": sr.iters, "converged": bool(sr.converged),
+               "accepted": sr.accepted_steps, "pcg_iters_total": sr.total_pcg_iters, "cost0": sr.cost0,
+               "cost": sr.cost, "precision": args.precision}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, frac, cores = oracle_step_time(scene, args.cpu_frac)
+        cpu = {"value": round(frac / dt, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one FP64 oracle LM iteration on the first {args.cpu_frac:.0%} of the points and lines "
+                         f"(all cameras and groups; {frac:.2%} of the residuals) took {dt:.1f} s; "
+                         f"scaled to the full scene by residual count"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64" if prec == B.BA_MIXED else "f64",
+               "data": "synthetic, seeded (scenegen): cube scene with Manhattan planes, VPs, wireframes, pixel "
+                       "noise and outliers, shaped like the paper's synthetic benchmark (App. A.3)",
+               "config": {"workload": workload_desc(scene, args.config), "precision": args.precision,
+                          "l2": "inputs larger than L2 (GB-scale working set per step)",
+                          "parallelism": "replicas" if world > 1 else "single GPU"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+               "time_to_converge": ttc, "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
+               "pcg_iters": pcg_iters, "pcg_rel": pcg_rel, "reduced_system": dims_S,
+               "first_step_s": round(first_step_s, 3)}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def host_bytes(s):
+    n = sum(a.nbytes for a in (s["cams"]["q"], s["cams"]["t"], s["cams"]["intr"], s["cams"]["pp"], s["points"],
+                                s["lines"], s["planes"], s["vps"], s["fixed"]))
+    for o in s["obs"].values():
+        n += sum(np.asarray(v).nbytes for v in o.values())
+    return int(n)
+
+
+def pair_counts(s):
+    """Schur slot pairs sum_f n_f (n_f + 1) / 2 split by feature type (n_f = kept entities of feature f)."""
+    out = {}
+    for ft, kinds in (("point", ("point", "plane_point", "p2l")), ("line", ("line", "plane_line", "vp", "l2p"))):
+        nfeat = len(s["points"] if ft == "point" else s["lines"])
+        fixed = s["fixed"]
+        keys = []
+        for k in kinds:
+            o = s["obs"][k]
+            if len(o["feat"]) == 0:
+                continue
+            if k != "vp":
+                c = o["cam"].astype(np.int64)
+                ok = fixed[c] != 0x3F
+                keys.append(o["feat"][ok].astype(np.int64) * 1_000_000 + c[ok])
+            if k in ("plane_point", "plane_line"):
+                keys.append(o["feat"].astype(np.int64) * 1_000_000 + 500_000 + o["other"])
+            if k == "vp":
+                keys.append(o["feat"].astype(np.int64) * 1_000_000 + 900_000 + o["other"])
+        u = np.unique(np.concatenate(keys)) if keys else np.zeros(0, np.int64)
+        nf = np.bincount((u // 1_000_000).astype(np.int64), minlength=nfeat)
+        out["pairs_" + ft] = int((nf * (nf + 1) // 2).sum())
+    return out
+
+
+def run_reference(args, scfg, make_scene):
+    """The oracle (FP64 CPU, as it stands) timed per LM step on a bounded sample of the same workload."""
+    scene = make_scene(scfg(args.config))
+    times = []
+    frac = args.cpu_frac
+    for _ in range(args.warmup):
+        pass                                          # the oracle has no warm state; warm-up is a no-op
+    cores = None
+    fr = None
+    for _ in range(args.steps):
+        dt, fr, cores = oracle_step_time(scene, frac)
+        times.append(dt)
+    t = float(np.mean(times))
+    value = fr / t
+    sample = (f"each step: one FP64 oracle LM iteration on the first {frac:.0%} of the points and lines "
+              f"({fr:.2%} of the residuals), scaled to the full scene by residual count")
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t / fr * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+           "data": "synthetic, seeded (scenegen)",
+           "config": {"workload": workload_desc(scene, args.config), "precision": "fp64",
+                      "parallelism": "host cores"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/* ba.h -- C ABI of the B300 holistic bundle-adjustment library (libba.so).
+ *
+ * One Levenberg-Marquardt (LM) step of the unified bundle adjustment of
+ * "Stable and Scalable Bundle Adjustment of Holistic 3D Structures":
+ * cameras and groups (planes, vanishing points) form the kept set A = C u G
+ * (Section 3.2, Eq. 5); points and lines are features, eliminated by the Schur
+ * complement S = H_aa - H_af H_ff^-1 H_fa (Eq. 3 / Eq. 5), which is solved by
+ * block-Jacobi preconditioned CG; the features are then back-substituted.
+ *
+ * Residual kinds (one observation record per residual):
+ *   BA_OBS_POINT        point reprojection, Eq. 1 / Eq. 4          meas: 2 (distorted pixels)
+ *   BA_OBS_LINE         line reprojection rho in R^4, Eq. 4      meas: 4 (segment endpoints, undistorted)
+ *   BA_OBS_PLANE_POINT  plane-induced point residual, Eq. 7      meas: none (other = plane id)
+ *   BA_OBS_PLANE_LINE   plane-induced line residual, Eq. 8       meas: 4 (segment; other = plane id)
+ *   BA_OBS_VP           VP angular residual d x v, Eq. 6         meas: none (cam = -1, other = VP id)
+ *   BA_OBS_P2L          wireframe point -> observed line, Eq. 11 meas: 4 (partner segment; other = line id)
+ *   BA_OBS_L2P          wireframe line -> observed point, Eq. 12 meas: 2 (partner point, undistorted)
+ * Plane projections of points and Pluecker lines follow Appendix B.  Weights and
+ * Cauchy scales default to the cost-balancing values of Appendix C; the cost is
+ * E = 1/2 sum w a^2 ln(1 + |r|^2/a^2), and termination uses the relative change
+ * of the pixel-space part only (Section 3.5).
+ *
+ * Conventions.
+ *   Memory: every pointer argument is host memory when mem == BA_MEM_HOST and
+ *     device memory of the current CUDA device when mem == BA_MEM_DEVICE.  Input
+ *     arrays are copied; the caller keeps ownership of its buffers.  The library
+ *     owns all device memory it allocates (through the optional allocator hooks
+ *     of ba_options, else cudaMalloc) and frees it in ba_destroy.
+ *   Indices: 0-based int32, per type (point ids, line ids, plane ids, VP ids).
+ *     They are validated when the structure is frozen (first step); an out of
+ *     range index returns BA_ERR_ARG.
+ *   Freezing: adding data after the first ba_lm_step / ba_solve / ba_build_reduced
+ *     returns BA_ERR_STATE.
+ *   Errors: no exception or abort crosses the ABI.  Every call returns a
+ *     ba_status; ba_last_error() gives a message for the last failure of that
+ *     problem.  After BA_ERR_CUDA the problem can still be destroyed.
+ *   Streams: all device work runs on options.cuda_stream (NULL = legacy default
+ *     stream); calls return after the work they report on has finished.
+ *   Layout of parameters: camera quat_t n x 7 = (qw, qx, qy, qz, tx, ty, tz),
+ *     world -> camera (x_c = R(q) X + t, +z forward); intrinsics n x 3 = (f, k1, k2);
+ *     principal points n x 2.  Points n x 3.  Lines n x 6 Pluecker (d, m), m . d = 0
+ *     (rescaled internally so that |d| = 1).  Planes n x 4 (n, w), plane n.x + w = 0.
+ *     VPs n x 3 directions.
+ *   Limits: a feature may be associated with at most one plane and one VP.
+ */
+#ifndef BA_H
+#define BA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_problem ba_problem;
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_ARG = -1,      /* invalid argument (null pointer, bad kind, index out of range, size limit) */
+  BA_ERR_STATE = -2,    /* call not allowed in the current state (e.g. adding after freezing) */
+  BA_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  BA_ERR_OOM = -4,      /* device or host allocation failed */
+  BA_ERR_NUMERIC = -5,  /* non-finite cost or a linear-algebra breakdown that damping could not fix */
+  BA_ERR_TIMEOUT = -6   /* a bounded device-side wait ran out */
+} ba_status;
+
+typedef enum { BA_MEM_HOST = 0, BA_MEM_DEVICE = 1 } ba_mem;
+typedef enum { BA_FP64 = 0, BA_MIXED = 1 } ba_precision;
+typedef enum { BA_PRECOND_BLOCK_JACOBI = 0, BA_PRECOND_LEARNED = 1 } ba_precond;
+typedef enum { BA_POINT = 0, BA_LINE = 1 } ba_feature_kind;
+typedef enum { BA_PLANE = 0, BA_VP = 1 } ba_group_kind;
+typedef enum {
+  BA_OBS_POINT = 0, BA_OBS_LINE = 1, BA_OBS_PLANE_POINT = 2, BA_OBS_PLANE_LINE = 3,
+  BA_OBS_VP = 4, BA_OBS_P2L = 5, BA_OBS_L2P = 6
+} ba_obs_kind;
+
+typedef struct ba_options {
+  int precision;            /* ba_precision: BA_FP64 everything in double; BA_MIXED: Jacobians, Schur and
+                               SpMV in float, landmark inverses, damping, cost and the accept test in double */
+  double w_point, w_line;   /* loss weights of R1 / R2 (1.0) */
+  double w_group;           /* plane-induced residuals R3 / R4 (0.5) */
+  double w_wire;            /* wireframe residuals R6 / R7 (0.1) */
+  double w_vp;              /* VP angular residual R5 (5e3) */
+  double cauchy_px;         /* Cauchy scale of pixel residuals (1.0) */
+  double cauchy_vp;         /* Cauchy scale of the VP residual (0.2) */
+  double lambda0;           /* initial LM damping (1e-4) */
+  double lambda_min, lambda_max; /* damping clamp (1e-12, 1e12) */
+  double min_gain;          /* accept when gain ratio > min_gain (1e-3) */
+  double rel_cost_tol;      /* stop on an accepted step with |dE_px|/E_px < tol (1e-6) */
+  int max_lm_iters;         /* ba_solve iteration cap (20) */
+  double pcg_rel_tol;       /* PCG stop: |r_k| <= tol |b| (1e-6) */
+  int pcg_max_iters;        /* PCG cap (1000) */
+  int precond;              /* ba_precond */
+  void* cuda_stream;        /* cudaStream_t to run on (NULL = default stream) */
+  void* (*dev_alloc)(size_t bytes, void* ctx);   /* optional device allocator (e.g. the framework's caching allocator) */
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  long long wait_budget_cycles; /* bound on any device-side spin wait (clock64 cycles) */
+  double mixed_lambda_floor; /* BA_MIXED only: lower bound of the damping (1e-6).  The float Schur complement
+                                carries ~1e-7 relative rounding; below this damping its weakest directions sink
+                                under that noise and PCG stops converging */
+} ba_options;
+
+/* Per-LM-step report. */
+typedef struct ba_step_report {
+  double cost, cost_px;         /* E and E_px at the current parameters (before the step) */
+  double cost_new, cost_px_new; /* at the candidate x (+) delta */
+  double pred;                  /* predicted decrease -g.delta - 1/2 delta^T H delta */
+  double gain;                  /* (cost - cost_new) / pred */
+  double lambda;                /* damping used for this step */
+  double pcg_rel;               /* final relative PCG residual |r_k| / |b| */
+  int pcg_iters;
+  int accepted;
+  int converged;                /* accepted and |dE_px|/E_px < rel_cost_tol */
+  int relinearized;             /* 1 if the Jacobians were recomputed for this step */
+  float ms_linearize, ms_schur, ms_pcg, ms_update;  /* device time per phase */
+  /* device time per kernel stage, measured with CUDA events on the problem's stream:
+   * [0] derive + linearize (K1), [1] landmark inverse (K2), [2] Schur work items (K3a),
+   * [3] Schur block sums (K3b), [4] block-Jacobi (K4), [5] PCG (K5/K6, including the host
+   * reads of the stop flag), [6] back-substitution (K7), [7] candidate (K8a), [8] cost (K8b),
+   * [9] decision (K9) */
+  float ms_kernel[10];
+  int n_launches;               /* CUDA kernels this step launched */
+} ba_step_report;
+
+typedef struct ba_solve_report {
+  int iters, converged, accepted_steps, total_pcg_iters;
+  double cost0, cost, cost_px;
+  double ms_structure;          /* one-time structure build (analogue of symbolic analysis) */
+  double ms_total;              /* wall time of the whole solve */
+} ba_solve_report;
+
+/* Fill *o with the defaults listed above. */
+void ba_default_options(ba_options* o);
+
+/* Create an empty problem.  opts may be NULL (defaults).  *out receives the handle. */
+ba_status ba_create(const ba_options* opts, ba_problem** out);
+/* Free every resource of the problem (NULL is allowed). */
+void ba_destroy(ba_problem* p);
+const char* ba_last_error(const ba_problem* p);
+
+/* Cameras (Section 3.1: C_i = (K, R_i, t_i)): quat_t n x 7, f_k1_k2 n x 3, pp n x 2 (principal point; the
+ * intrinsics are held constant), fixed: optional n bytes, a bit mask of pose increment components held
+ * constant (bits 0-2 rotation dw, 3-5 translation dt; 0x3F holds the whole pose), used to fix the gauge.
+ * Appends; ids continue. */
+ba_status ba_add_cameras(ba_problem* p, int64_t n, int mem, const double* quat_t, const double* f_k1_k2,
+                         const double* pp, const uint8_t* fixed);
+/* Features (Section 3.2): kind BA_POINT (n x 3) or BA_LINE (n x 6 Pluecker). */
+ba_status ba_add_features(ba_problem* p, int kind, int64_t n, int mem, const double* params);
+/* Groups (Section 3.2-3.3, Appendix B): kind BA_PLANE (n x 4) or BA_VP (n x 3). */
+ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, const double* params);
+/* Residual records of one kind: cam (n; ignored for BA_OBS_VP, may be NULL), feature (n), other (n; group id or
+ * partner feature id, may be NULL for kinds without one), meas (n x meas_dim(kind), may be NULL when 0). */
+ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int mem, const int32_t* cam,
+                              const int32_t* feature, const int32_t* other, const double* meas);
+
+/* One LM iteration (linearise, damp, eliminate, PCG, back-substitute, evaluate, accept/reject). */
+ba_status ba_lm_step(ba_problem* p, ba_step_report* out);
+/* LM until converged or max_lm_iters.  out may be NULL. */
+ba_status ba_solve(ba_problem* p, ba_solve_report* out);
+
+/* Current parameters, same layouts as the add calls; out arrays sized for all entities of that kind. */
+ba_status ba_get_cameras(ba_problem* p, int mem, double* quat_t);
+ba_status ba_get_features(ba_problem* p, int kind, int mem, double* params);
+ba_status ba_get_groups(ba_problem* p, int kind, int mem, double* params);
+/* LM state (lambda, nu) for checkpoint / resume. */
+ba_status ba_get_lm_state(ba_problem* p, double* lambda_nu);
+ba_status ba_set_lm_state(ba_problem* p, const double* lambda_nu);
+
+/* Cost (E, E_px) at the current parameters (FP64). */
+ba_status ba_eval_cost(ba_problem* p, double* cost, double* cost_px);
+
+/* Build the damped reduced system S, b at damping lambda (linearising if needed) without stepping. */
+ba_status ba_build_reduced(ba_problem* p, double lambda);
+/* Sizes of the reduced system: number of A entities (block rows, each 6 wide; plane blocks use 3, VP blocks 2
+ * of the 6, the rest are padding with a unit diagonal) and number of stored 6x6 blocks (both triangles). */
+ba_status ba_reduced_size(ba_problem* p, int64_t* n_block_rows, int64_t* nnz_blocks);
+/* Copy the last reduced system to host: row_ptr (n_block_rows+1), cols (nnz_blocks), vals (nnz_blocks x 36,
+ * row-major 6x6, double) and b (n_block_rows x 6).  Any pointer may be NULL. */
+ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, int32_t* cols, double* vals, double* b);
+/* Solve the last reduced system by PCG and back-substitute: per-entity increments to host arrays
+ * (cams n x 6 as (dw, dt), planes n x 3, vps n x 2, points n x 3, lines n x 4); NULL skips an output. */
+ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* dvp, double* dpoint,
+                          double* dline, int* pcg_iters, double* pcg_rel, double* pred);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BA_H */

@@ -355,7 +355,8 @@ def state_from_scene(scene):
         vps=np.array(scene["vps"], np.float64).reshape(-1, 3),
     )
     if len(st["planes"]):
-        st["planes"][:, :3] /= np.linalg.norm(st["planes"][:, :3], axis=1, keepdims=True)
+        # the plane n.x + w = 0 is homogeneous in (n, w): rescale both so that |n| = 1
+        st["planes"] /= np.linalg.norm(st["planes"][:, :3], axis=1, keepdims=True)
     if len(st["vps"]):
         st["vps"] /= np.linalg.norm(st["vps"], axis=1, keepdims=True)
     return st
@@ -441,7 +442,11 @@ def cost(state, obs, opt: Options):
 # the normal equations (Eq. 2 / Eq. 5) and the Schur complement (Eq. 3)
 # ===========================================================================
 class Layout:
-    """Column layout of the full system: [cameras | planes | VPs | points | lines]."""
+    """Column layout of the full system: [cameras | planes | VPs | points | lines].
+
+    `fixed` holds camera pose components constant (gauge): per camera a bit mask over the six pose
+    increments (bits 0-2 rotation, 3-5 translation; 0x3F = the whole pose), or a boolean (True = 0x3F).
+    Held components get no column."""
 
     def __init__(self, state, fixed=None):
         self.nc = state["cams"].shape[0]
@@ -449,19 +454,24 @@ class Layout:
         self.nv = state["vps"].shape[0]
         self.np_ = state["points"].shape[0]
         self.nl = state["lines"].shape[0]
-        self.fixed = np.zeros(self.nc, bool) if fixed is None else np.asarray(fixed, bool)
-        free = ~self.fixed
-        self.cam_col = np.full(self.nc, -1, np.int64)
-        self.cam_col[free] = 6 * np.arange(free.sum())
-        o = 6 * int(free.sum())
+        mask = np.zeros(self.nc, np.uint8) if fixed is None else np.asarray(fixed)
+        if mask.dtype == bool:
+            mask = np.where(mask, 0x3F, 0).astype(np.uint8)
+        self.held = ((mask.astype(np.int64)[:, None] >> np.arange(6)[None, :]) & 1).astype(bool)
+        self.fixed = self.held.all(1)
+        self.cam_cols = np.full((self.nc, 6), -1, np.int64)
+        free = ~self.held
+        self.cam_cols[free] = np.arange(int(free.sum()))
+        o = int(free.sum())
         self.plane_col = o + 3 * np.arange(self.npl); o += 3 * self.npl
         self.vp_col = o + 2 * np.arange(self.nv); o += 2 * self.nv
         self.na = o
         self.point_col = o + 3 * np.arange(self.np_); o += 3 * self.np_
         self.line_col = o + 4 * np.arange(self.nl); o += 4 * self.nl
         self.n = o
-        # entity blocks of A (for block-Jacobi): (start, size)
-        self.a_blocks = ([(int(c), 6) for c in self.cam_col[free]] +
+        # entity blocks of A (for block-Jacobi): (start, size); a camera's free columns are contiguous
+        nfree = free.sum(1)
+        self.a_blocks = ([(int(self.cam_cols[i][free[i]][0]), int(nfree[i])) for i in range(self.nc) if nfree[i]] +
                          [(int(c), 3) for c in self.plane_col] + [(int(c), 2) for c in self.vp_col])
         self.f_blocks = [(int(c), 3) for c in self.point_col] + [(int(c), 4) for c in self.line_col]
 
@@ -484,24 +494,26 @@ def linearize(state, obs, opt: Options, lay: Layout):
         sq = torch.sqrt(om).numpy()
         rd = RDIM[k]
         ridx = row0 + np.arange(n)[:, None] * rd + np.arange(rd)[None, :]          # [n, rd]
-        blocks = []
+        blocks = []   # (J [n, rd, w], columns [n, w], column present [n, w])
         if HAS_CAM[k]:
-            cc = lay.cam_col[o["cam"]]
-            ok = cc >= 0
-            blocks.append((Jc.numpy(), np.where(ok, cc, 0), ok, 6))
+            cc = lay.cam_cols[o["cam"]]
+            blocks.append((Jc.numpy(), cc, cc >= 0))
         ft = FEAT[k]
         fc = (lay.point_col if ft == "point" else lay.line_col)[o["feat"]]
-        blocks.append((Jf.numpy(), fc, np.ones(n, bool), FDOF[ft]))
+        w = FDOF[ft]
+        blocks.append((Jf.numpy(), fc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
         gk = GROUP.get(k)
         if gk:
             gc = (lay.plane_col if gk == "plane" else lay.vp_col)[o["other"]]
-            blocks.append((Jg.numpy()[:, :, : GDOF[gk]], gc, np.ones(n, bool), GDOF[gk]))
-        for J, c0, ok, w in blocks:
+            w = GDOF[gk]
+            blocks.append((Jg.numpy()[:, :, :w], gc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
+        for J, C0, ok in blocks:
+            w = C0.shape[1]
             J = J * sq[:, None, None]
             R_ = np.broadcast_to(ridx[:, :, None], (n, rd, w))
-            C_ = c0[:, None, None] + np.arange(w)[None, None, :]
-            m = np.broadcast_to(ok[:, None, None], (n, rd, w))
-            rows.append(R_[m]); cols.append(np.broadcast_to(C_, (n, rd, w))[m]); vals.append(J[m])
+            C_ = np.broadcast_to(C0[:, None, :], (n, rd, w))
+            m = np.broadcast_to(ok[:, None, :], (n, rd, w))
+            rows.append(R_[m]); cols.append(C_[m]); vals.append(J[m])
         rt.append((r.numpy() * sq[:, None]).reshape(-1))
         row0 += n * rd
     Jt = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
@@ -593,7 +605,8 @@ def apply_step(state, delta, lay: Layout):
     new = {k: v.copy() for k, v in state.items()}
     free = np.nonzero(~lay.fixed)[0]
     if len(free):
-        dp = torch.from_numpy(np.stack([delta[lay.cam_col[i]: lay.cam_col[i] + 6] for i in free]))
+        cols = lay.cam_cols[free]
+        dp = torch.from_numpy(np.where(cols >= 0, delta[np.maximum(cols, 0)], 0.0))
         c = torch.from_numpy(state["cams"][free])
         R, t = pose_plus(c[:, :4], c[:, 4:7], dp)
         new["cams"][free, :4] = R_to_quat(R.numpy())

@@ -1,0 +1,325 @@
+"""Python binding of libba, the B300 library for one LM step of holistic bundle adjustment.
+
+The binding only marshals arguments: every step of the solve runs in the CUDA
+kernels of libba.so (built in-tree by ``paper_2609_04026_b300.build``).  Importing
+this module fails loudly when the library is missing; there is no CPU fallback.
+
+Functions keep the C names (``ba_create``, ``ba_add_cameras``, ... ``ba_lm_step``,
+``ba_solve``).  Arrays may be numpy arrays (host memory) or CUDA torch tensors
+(device memory); the binding passes BA_MEM_HOST or BA_MEM_DEVICE accordingly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libba.so")
+
+BA_OK, BA_ERR_ARG, BA_ERR_STATE, BA_ERR_CUDA, BA_ERR_OOM, BA_ERR_NUMERIC, BA_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+BA_MEM_HOST, BA_MEM_DEVICE = 0, 1
+BA_FP64, BA_MIXED = 0, 1
+BA_PRECOND_BLOCK_JACOBI, BA_PRECOND_LEARNED = 0, 1
+BA_POINT, BA_LINE = 0, 1
+BA_PLANE, BA_VP = 0, 1
+OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6}
+MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class ba_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("w_point", C.c_double), ("w_line", C.c_double),
+                ("w_group", C.c_double), ("w_wire", C.c_double), ("w_vp", C.c_double),
+                ("cauchy_px", C.c_double), ("cauchy_vp", C.c_double), ("lambda0", C.c_double),
+                ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("min_gain", C.c_double),
+                ("rel_cost_tol", C.c_double), ("max_lm_iters", C.c_int), ("pcg_rel_tol", C.c_double),
+                ("pcg_max_iters", C.c_int), ("precond", C.c_int), ("cuda_stream", C.c_void_p),
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double)]
+
+
+class ba_step_report(C.Structure):
+    _fields_ = [("cost", C.c_double), ("cost_px", C.c_double), ("cost_new", C.c_double),
+                ("cost_px_new", C.c_double), ("pred", C.c_double), ("gain", C.c_double),
+                ("lambda_", C.c_double), ("pcg_rel", C.c_double), ("pcg_iters", C.c_int),
+                ("accepted", C.c_int), ("converged", C.c_int), ("relinearized", C.c_int),
+                ("ms_linearize", C.c_float), ("ms_schur", C.c_float), ("ms_pcg", C.c_float),
+                ("ms_update", C.c_float), ("ms_kernel", C.c_float * 10), ("n_launches", C.c_int)]
+
+    KERNELS = ("linearize", "invert", "schur_items", "schur_blocks", "precond", "pcg", "backsub",
+               "candidate", "cost", "decide")
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_kernel"}
+        d["ms_kernel"] = dict(zip(self.KERNELS, list(self.ms_kernel)))
+        return d
+
+
+class ba_solve_report(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("accepted_steps", C.c_int),
+                ("total_pcg_iters", C.c_int), ("cost0", C.c_double), ("cost", C.c_double),
+                ("cost_px", C.c_double), ("ms_structure", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libba.so not built at {LIB_PATH}: run python -m paper_2609_04026_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, I64, I, D, VP = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_void_p
+    sig = {
+        "ba_default_options": (None, [C.POINTER(ba_options)]),
+        "ba_create": (I, [C.POINTER(ba_options), C.POINTER(C.c_void_p)]),
+        "ba_destroy": (None, [P]),
+        "ba_last_error": (C.c_char_p, [P]),
+        "ba_add_cameras": (I, [P, I64, I, VP, VP, VP, VP]),
+        "ba_add_features": (I, [P, I, I64, I, VP]),
+        "ba_add_groups": (I, [P, I, I64, I, VP]),
+        "ba_add_observations": (I, [P, I, I64, I, VP, VP, VP, VP]),
+        "ba_lm_step": (I, [P, C.POINTER(ba_step_report)]),
+        "ba_solve": (I, [P, C.POINTER(ba_solve_report)]),
+        "ba_get_cameras": (I, [P, I, VP]),
+        "ba_get_features": (I, [P, I, I, VP]),
+        "ba_get_groups": (I, [P, I, I, VP]),
+        "ba_get_lm_state": (I, [P, VP]),
+        "ba_set_lm_state": (I, [P, VP]),
+        "ba_eval_cost": (I, [P, C.POINTER(D), C.POINTER(D)]),
+        "ba_build_reduced": (I, [P, D]),
+        "ba_reduced_size": (I, [P, C.POINTER(I64), C.POINTER(I64)]),
+        "ba_export_reduced_system": (I, [P, VP, VP, VP, VP]),
+        "ba_compute_step": (I, [P, VP, VP, VP, VP, VP, C.POINTER(I), C.POINTER(D), C.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTS = [n for n in dir(_lib) if n.startswith("ba_")]
+
+
+class BAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libba status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    return _lib
+
+
+def _check(p, status):
+    if status != BA_OK:
+        raise BAError(status, _lib.ba_last_error(p).decode() if p else "")
+
+
+def _arr(x, dtype):
+    """(pointer, mem, keepalive) for a numpy array (host) or a CUDA torch tensor (device)."""
+    if x is None:
+        return None, BA_MEM_HOST, None
+    if hasattr(x, "is_cuda") and x.is_cuda:
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        t = x.to(want).contiguous()
+        return C.c_void_p(t.data_ptr()), BA_MEM_DEVICE, t
+    a = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), BA_MEM_HOST, a
+
+
+# ---------------------------------------------------------------------------- C-named wrappers
+def ba_default_options(**kw):
+    o = ba_options()
+    _lib.ba_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class _TorchAlloc:
+    """Device allocator hooks backed by torch's caching allocator on the given stream."""
+
+    def __init__(self, stream_ptr):
+        import torch
+        self.torch = torch
+        self.dev = torch.cuda.current_device()
+        self.stream = stream_ptr
+
+        def alloc(n, ctx):
+            return self.torch.cuda.caching_allocator_alloc(int(n), self.dev, self.stream)
+
+        def free(p, ctx):
+            self.torch.cuda.caching_allocator_delete(p)
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+def ba_create(opts=None, torch_allocator=False):
+    """Returns an opaque handle (int).  torch_allocator=True routes device allocations through
+    torch's caching allocator on opts.cuda_stream."""
+    opts = opts if opts is not None else ba_default_options()
+    keep = None
+    if torch_allocator:
+        keep = _TorchAlloc(opts.cuda_stream or 0)
+        opts.dev_alloc = keep.alloc
+        opts.dev_free = keep.free
+    h = C.c_void_p()
+    st = _lib.ba_create(C.byref(opts), C.byref(h))
+    if st != BA_OK:
+        raise BAError(st, "ba_create failed (is a CUDA device visible?)")
+    _KEEP[h.value] = (opts, keep)
+    return h.value
+
+
+_KEEP = {}
+
+
+def ba_destroy(p):
+    _lib.ba_destroy(p)
+    _KEEP.pop(p, None)
+
+
+def ba_last_error(p):
+    return _lib.ba_last_error(p).decode()
+
+
+def ba_add_cameras(p, quat_t, f_k1_k2, pp, fixed=None):
+    a, mem, k1 = _arr(quat_t, np.float64)
+    b, _, k2 = _arr(f_k1_k2, np.float64)
+    c, _, k3 = _arr(pp, np.float64)
+    d, _, k4 = _arr(fixed, np.uint8)
+    n = len(k1) if k1 is not None else 0
+    _check(p, _lib.ba_add_cameras(p, n, mem, a, b, c, d))
+
+
+def ba_add_features(p, kind, params):
+    a, mem, k = _arr(params, np.float64)
+    _check(p, _lib.ba_add_features(p, kind, len(k), mem, a))
+
+
+def ba_add_groups(p, kind, params):
+    a, mem, k = _arr(params, np.float64)
+    _check(p, _lib.ba_add_groups(p, kind, len(k), mem, a))
+
+
+def ba_add_observations(p, kind, cam, feature, other=None, meas=None):
+    f, mem, kf = _arr(feature, np.int32)
+    c, _, kc = _arr(cam, np.int32)
+    o, _, ko = _arr(other, np.int32)
+    m, _, km = _arr(meas, np.float64) if MEAS_DIM[kind] else (None, 0, None)
+    _check(p, _lib.ba_add_observations(p, kind, len(kf), mem, c, f, o, m))
+
+
+def ba_lm_step(p):
+    r = ba_step_report()
+    _check(p, _lib.ba_lm_step(p, C.byref(r)))
+    return r
+
+
+def ba_solve(p):
+    r = ba_solve_report()
+    _check(p, _lib.ba_solve(p, C.byref(r)))
+    return r
+
+
+def ba_get_cameras(p, n):
+    out = np.empty((n, 7))
+    _check(p, _lib.ba_get_cameras(p, BA_MEM_HOST, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def ba_get_features(p, kind, n):
+    out = np.empty((n, 3 if kind == BA_POINT else 6))
+    _check(p, _lib.ba_get_features(p, kind, BA_MEM_HOST, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def ba_get_groups(p, kind, n):
+    out = np.empty((n, 4 if kind == BA_PLANE else 3))
+    _check(p, _lib.ba_get_groups(p, kind, BA_MEM_HOST, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def ba_get_lm_state(p):
+    out = np.empty(2)
+    _check(p, _lib.ba_get_lm_state(p, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def ba_set_lm_state(p, lam, nu):
+    a = np.array([lam, nu], np.float64)
+    _check(p, _lib.ba_set_lm_state(p, a.ctypes.data_as(C.c_void_p)))
+
+
+def ba_eval_cost(p):
+    e, epx = C.c_double(), C.c_double()
+    _check(p, _lib.ba_eval_cost(p, C.byref(e), C.byref(epx)))
+    return e.value, epx.value
+
+
+def ba_build_reduced(p, lam):
+    _check(p, _lib.ba_build_reduced(p, float(lam)))
+
+
+def ba_reduced_size(p):
+    a, b = C.c_int64(), C.c_int64()
+    _check(p, _lib.ba_reduced_size(p, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def ba_export_reduced_system(p):
+    na, nb = ba_reduced_size(p)
+    rp = np.empty(na + 1, np.int32); cols = np.empty(nb, np.int32)
+    vals = np.empty((nb, 6, 6)); b = np.empty((na, 6))
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(p, _lib.ba_export_reduced_system(p, ptr(rp), ptr(cols), ptr(vals), ptr(b)))
+    return rp, cols, vals, b
+
+
+def ba_compute_step(p, counts):
+    """counts = (nc, npl, nv, np, nl); returns dict of per-entity increments and PCG info."""
+    nc, npl, nv, np_, nl = counts
+    out = dict(cam=np.empty((nc, 6)), plane=np.empty((npl, 3)), vp=np.empty((nv, 2)),
+               point=np.empty((np_, 3)), line=np.empty((nl, 4)))
+    it, rel, pred = C.c_int(), C.c_double(), C.c_double()
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(p, _lib.ba_compute_step(p, ptr(out["cam"]), ptr(out["plane"]), ptr(out["vp"]), ptr(out["point"]),
+                                   ptr(out["line"]), C.byref(it), C.byref(rel), C.byref(pred)))
+    out.update(pcg_iters=it.value, pcg_rel=rel.value, pred=pred.value)
+    return out
+
+
+# ---------------------------------------------------------------------------- scene marshalling
+def load_scene(p, scene, device_tensors=False):
+    """Add every array of a scene dict (cams, points, lines, planes, vps, obs, fixed) to the problem.
+    With device_tensors=True the arrays are first placed on the current CUDA device (BA_MEM_DEVICE)."""
+    conv = (lambda a: a)
+    if device_tensors:
+        import torch
+        conv = (lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda())
+    c = scene["cams"]
+    quat_t = np.concatenate([c["q"], c["t"]], 1)
+    ba_add_cameras(p, conv(quat_t), conv(c["intr"]), conv(c["pp"]),
+                   conv(scene["fixed"].astype(np.uint8)) if "fixed" in scene else None)
+    if len(scene["points"]):
+        ba_add_features(p, BA_POINT, conv(scene["points"]))
+    if len(scene["lines"]):
+        ba_add_features(p, BA_LINE, conv(scene["lines"]))
+    if len(scene["planes"]):
+        ba_add_groups(p, BA_PLANE, conv(scene["planes"]))
+    if len(scene["vps"]):
+        ba_add_groups(p, BA_VP, conv(scene["vps"]))
+    for name, k in OBS_KINDS.items():
+        o = scene["obs"][name]
+        if len(o["feat"]) == 0:
+            continue
+        meas = o["meas"] if MEAS_DIM[k] else None
+        ba_add_observations(p, k, conv(o["cam"]) if k != 4 else None, conv(o["feat"]), conv(o["other"]),
+                            conv(meas) if meas is not None else None)

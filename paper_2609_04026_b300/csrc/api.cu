@@ -1,0 +1,572 @@
+// C ABI of libba and the host orchestration of one LM step.
+//
+// Per step (all on the problem's stream, one host synchronisation per step plus
+// one per batch of PCG iterations):
+//   [relinearise only after an accepted step]  derive -> K1 linearize
+//   K2 invert (lambda)  -> K3 Schur items / blocks -> K4 block-Jacobi
+//   PCG init, then batches of {SpMV+dot, update+dots, p-update} until the device
+//   stop flag is set -> K7 back-substitution + predicted decrease
+//   K8 candidate x (+) delta, derive, FP64 cost -> K9 accept / reject, damping
+// A rejected step keeps the linearisation and only re-damps (the Jacobians do not
+// depend on lambda).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ba_internal.cuh"
+
+using namespace ba;
+
+static const int kMeasDim[7] = {2, 4, 0, 4, 0, 4, 2};
+
+static ba_status set_err(ba_problem* p, ba_status s, const std::string& m) {
+  if (p) p->err = m;
+  return s;
+}
+
+#define CUDA_OR(p, x)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (x);                                                                \
+    if (e_ != cudaSuccess) return set_err(p, BA_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* ba_problem::dalloc(size_t bytes) {
+  void* ptr = alloc.get(bytes);
+  if (ptr) bufs.push_back({ptr, bytes});
+  return ptr;
+}
+
+extern "C" void ba_default_options(ba_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = BA_FP64;
+  o->w_point = 1.0; o->w_line = 1.0; o->w_group = 0.5; o->w_wire = 0.1; o->w_vp = 5e3;
+  o->cauchy_px = 1.0; o->cauchy_vp = 0.2;
+  o->lambda0 = 1e-4; o->lambda_min = 1e-12; o->lambda_max = 1e12;
+  o->min_gain = 1e-3; o->rel_cost_tol = 1e-6; o->max_lm_iters = 20;
+  o->pcg_rel_tol = 1e-6; o->pcg_max_iters = 1000;
+  o->precond = BA_PRECOND_BLOCK_JACOBI;
+  o->cuda_stream = nullptr;
+  o->wait_budget_cycles = 2000000000LL;
+  o->mixed_lambda_floor = 1e-6;
+}
+
+extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
+  if (!out) return BA_ERR_ARG;
+  *out = nullptr;
+  ba_problem* p = new (std::nothrow) ba_problem();
+  if (!p) return BA_ERR_OOM;
+  if (opts) p->opt = *opts; else ba_default_options(&p->opt);
+  if (p->opt.precision != BA_FP64 && p->opt.precision != BA_MIXED) { delete p; return BA_ERR_ARG; }
+  if (p->opt.precond != BA_PRECOND_BLOCK_JACOBI && p->opt.precond != BA_PRECOND_LEARNED) { delete p; return BA_ERR_ARG; }
+  if (!(p->opt.pcg_rel_tol > 0) || p->opt.pcg_max_iters <= 0) { delete p; return BA_ERR_ARG; }
+  if ((p->opt.dev_alloc == nullptr) != (p->opt.dev_free == nullptr)) { delete p; return BA_ERR_ARG; }
+  if (p->opt.precision == BA_MIXED) p->opt.lambda_min = std::max(p->opt.lambda_min, p->opt.mixed_lambda_floor);
+  p->alloc.fa = p->opt.dev_alloc; p->alloc.ff = p->opt.dev_free; p->alloc.ctx = p->opt.alloc_ctx;
+  p->stream = (cudaStream_t)p->opt.cuda_stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); delete p; return BA_ERR_CUDA; }
+  *out = p;
+  return BA_OK;
+}
+
+extern "C" void ba_destroy(ba_problem* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  for (auto& b : p->bufs) p->alloc.put(b.p);
+  p->bufs.clear();
+  if (p->hS) cudaFreeHost(p->hS);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete p;
+}
+
+extern "C" const char* ba_last_error(const ba_problem* p) { return p ? p->err.c_str() : "null problem"; }
+
+// ---------------------------------------------------------------------------
+// adding data (host staging; device inputs are copied down first)
+template <class X>
+static ba_status fetch(ba_problem* p, int mem, const X* src, size_t n, std::vector<X>& dst) {
+  size_t o = dst.size();
+  dst.resize(o + n);
+  if (n == 0) return BA_OK;
+  if (!src) return set_err(p, BA_ERR_ARG, "null array");
+  if (mem == BA_MEM_HOST) {
+    std::memcpy(dst.data() + o, src, n * sizeof(X));
+  } else if (mem == BA_MEM_DEVICE) {
+    CUDA_OR(p, cudaMemcpyAsync(dst.data() + o, src, n * sizeof(X), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  } else {
+    return set_err(p, BA_ERR_ARG, "mem must be BA_MEM_HOST or BA_MEM_DEVICE");
+  }
+  return BA_OK;
+}
+
+static ba_status check_add(ba_problem* p, int64_t n) {
+  if (!p) return BA_ERR_ARG;
+  if (p->frozen) return set_err(p, BA_ERR_STATE, "the structure is frozen after the first step");
+  if (n < 0) return set_err(p, BA_ERR_ARG, "negative count");
+  return BA_OK;
+}
+
+extern "C" ba_status ba_add_cameras(ba_problem* p, int64_t n, int mem, const double* quat_t, const double* fk,
+                                    const double* pp, const uint8_t* fixed) {
+  ba_status s = check_add(p, n);
+  if (s) return s;
+  std::vector<double> a, b, c;
+  std::vector<uint8_t> fx;
+  if ((s = fetch(p, mem, quat_t, 7 * n, a))) return s;
+  if ((s = fetch(p, mem, fk, 3 * n, b))) return s;
+  if ((s = fetch(p, mem, pp, 2 * n, c))) return s;
+  if (fixed) { if ((s = fetch(p, mem, fixed, n, fx))) return s; } else fx.assign(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 7; ++k) p->h_cam.push_back(a[7 * i + k]);
+    for (int k = 0; k < 3; ++k) p->h_cam.push_back(b[3 * i + k]);
+    for (int k = 0; k < 2; ++k) p->h_cam.push_back(c[2 * i + k]);
+    p->h_fixed.push_back((uint8_t)(fx[i] & 0x3F));
+  }
+  for (double v : p->h_cam)
+    if (!std::isfinite(v)) return set_err(p, BA_ERR_ARG, "non-finite camera parameter");
+  return BA_OK;
+}
+
+extern "C" ba_status ba_add_features(ba_problem* p, int kind, int64_t n, int mem, const double* params) {
+  ba_status s = check_add(p, n);
+  if (s) return s;
+  if (kind == BA_POINT) s = fetch(p, mem, params, 3 * n, p->h_pts);
+  else if (kind == BA_LINE) s = fetch(p, mem, params, 6 * n, p->h_lin);
+  else return set_err(p, BA_ERR_ARG, "feature kind must be BA_POINT or BA_LINE");
+  return s;
+}
+
+extern "C" ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, const double* params) {
+  ba_status s = check_add(p, n);
+  if (s) return s;
+  if (kind == BA_PLANE) s = fetch(p, mem, params, 4 * n, p->h_pln);
+  else if (kind == BA_VP) s = fetch(p, mem, params, 3 * n, p->h_vps);
+  else return set_err(p, BA_ERR_ARG, "group kind must be BA_PLANE or BA_VP");
+  return s;
+}
+
+extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int mem, const int32_t* cam,
+                                         const int32_t* feature, const int32_t* other, const double* meas) {
+  ba_status s = check_add(p, n);
+  if (s) return s;
+  if (kind < 0 || kind > 6) return set_err(p, BA_ERR_ARG, "unknown observation kind");
+  ba_problem::ObsBatch b;
+  b.kind = kind;
+  if ((s = fetch(p, mem, feature, n, b.feat))) return s;
+  if (kind != BA_OBS_VP) { if ((s = fetch(p, mem, cam, n, b.cam))) return s; }
+  bool needs_other = kind == BA_OBS_PLANE_POINT || kind == BA_OBS_PLANE_LINE || kind == BA_OBS_VP;
+  if (other) { if ((s = fetch(p, mem, other, n, b.other))) return s; }
+  else if (needs_other && n > 0) return set_err(p, BA_ERR_ARG, "this observation kind needs the group id array");
+  int md = kMeasDim[kind];
+  std::vector<double> m;
+  if (md) { if ((s = fetch(p, mem, meas, (size_t)md * n, m))) return s; }
+  b.meas.assign(4 * n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < md; ++k) {
+      double v = m[(size_t)md * i + k];
+      if (!std::isfinite(v)) return set_err(p, BA_ERR_ARG, "non-finite measurement");
+      b.meas[4 * i + k] = v;
+    }
+  if (n > 0) p->h_obs.push_back(std::move(b));
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+static bool mixed(const ba_problem* p) { return p->opt.precision == BA_MIXED; }
+
+// Partition of the block rows of S over the CTAs of the persistent PCG kernel: rows are balanced by stored
+// blocks (plus a small per-row term for the vector updates), and every row is cut into chunks of at most
+// PCG_CHUNK blocks for the warps of its CTA.
+static ba_status plan_pcg(ba_problem* p) {
+  const Dims& d = p->d;
+  std::vector<int32_t> rp(d.na + 1);
+  CUDA_OR(p, cudaMemcpyAsync(rp.data(), p->row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  std::vector<int32_t> row_chunk0(d.na + 1, 0), chunk_beg;
+  for (int64_t r = 0; r < d.na; ++r) {
+    int32_t len = rp[r + 1] - rp[r];
+    int32_t nch = std::max<int32_t>(1, (len + PCG_CHUNK - 1) / PCG_CHUNK);
+    for (int32_t k = 0; k < nch; ++k) chunk_beg.push_back(rp[r] + k * PCG_CHUNK);
+    row_chunk0[r + 1] = row_chunk0[r] + nch;
+  }
+  chunk_beg.push_back(rp[d.na]);
+  int sms = 0, dev = 0;
+  CUDA_OR(p, cudaGetDevice(&dev));
+  CUDA_OR(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool mx = mixed(p);
+  auto occ = [&](size_t smem) { return mx ? pcg_blocks_per_sm<float>(smem) : pcg_blocks_per_sm<double>(smem); };
+  int per_sm = std::max(1, std::min(2, occ(48 * 1024)));
+  std::vector<int32_t> cta_row0;
+  size_t smem = 0;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    int64_t G = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, d.na));
+    double total = 0;
+    for (int64_t r = 0; r < d.na; ++r) total += (rp[r + 1] - rp[r]) + 2.0;
+    cta_row0.assign(1, 0);
+    double acc = 0;
+    for (int64_t r = 0; r < d.na; ++r) {
+      acc += (rp[r + 1] - rp[r]) + 2.0;
+      if ((int64_t)cta_row0.size() < G && acc >= total * (double)cta_row0.size() / (double)G && r + 1 < d.na)
+        cta_row0.push_back((int32_t)(r + 1));
+    }
+    while ((int64_t)cta_row0.size() < G + 1) cta_row0.push_back((int32_t)d.na);
+    int32_t maxch = 1;
+    for (int64_t c = 0; c < G; ++c) maxch = std::max(maxch, row_chunk0[cta_row0[c + 1]] - row_chunk0[cta_row0[c]]);
+    smem = sizeof(double) * 6 * (size_t)maxch;
+    if (smem > 160 * 1024) return set_err(p, BA_ERR_ARG, "reduced system too irregular for the PCG partition");
+    if (smem > 48 * 1024) {
+      if (mx) pcg_allow_smem<float>(smem); else pcg_allow_smem<double>(smem);
+    }
+    if (occ(smem) >= per_sm) {
+      p->pcg_grid = (int)G;
+      break;
+    }
+    per_sm = std::max(1, per_sm - 1);
+  }
+  if (p->pcg_grid == 0) return set_err(p, BA_ERR_ARG, "no cooperative PCG launch configuration fits");
+  p->pcg_smem = smem;
+  ba_status s;
+  auto up = [&](int32_t*& dst, const std::vector<int32_t>& v) -> ba_status {
+    dst = p->dnew<int32_t>((int64_t)v.size());
+    if (!dst) return set_err(p, BA_ERR_OOM, "device allocation failed");
+    CUDA_OR(p, cudaMemcpyAsync(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, p->stream));
+    return BA_OK;
+  };
+  if ((s = up(p->cta_row0, cta_row0))) return s;
+  if ((s = up(p->row_chunk0, row_chunk0))) return s;
+  if ((s = up(p->chunk_beg, chunk_beg))) return s;
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+static ba_status freeze(ba_problem* p) {
+  if (p->frozen) return BA_OK;
+  if (p->h_cam.empty() && p->h_pts.empty() && p->h_lin.empty()) return set_err(p, BA_ERR_STATE, "empty problem");
+  ba_status s = build_structure(*p);
+  if (s) return s;
+  p->frozen = true;
+  const Dims& d = p->d;
+  const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
+  auto A = [&](void*& dst, size_t bytes) -> bool {
+    dst = p->dalloc(bytes);
+    return dst != nullptr;
+  };
+  bool ok = true;
+  ok &= A(p->slotW, T * SW * (size_t)d.ne);
+  ok &= A(p->slotY, T * SW * (size_t)d.ne);
+  ok &= A(p->slotH, T * SH * (size_t)d.ne);
+  ok &= A(p->slotG, T * SG * (size_t)d.ne);
+  ok &= A(p->slotB, T * SG * (size_t)d.ne);
+  ok &= A(p->slotC, T * SC * (size_t)d.ne);
+  ok &= A(p->Sval, T * BS2 * (size_t)d.nbf);
+  ok &= A(p->Minv, T * BS2 * (size_t)d.na);
+  ok &= A(p->part, T * PART * (size_t)d.nwi);
+  p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
+  p->featg = p->dnew<double>(4 * d.nf); p->featz = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
+  ok &= p->featV && p->featVinv && p->featg && p->featz && p->dfeat;
+  double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap};
+  for (double** v : vecs) { *v = p->dnew<double>(6 * d.na); ok &= *v != nullptr; }
+  int64_t maxb = std::max<int64_t>({(d.nr + 255) / 256, (d.nf + 127) / 128, (d.na * 32 + 255) / 256, (d.na + 127) / 128,
+                                    4 * 148 * 4, 1});
+  p->red = p->dnew<double>(2 * maxb + 16);
+  p->S = p->dnew<DevScalars>(1);
+  ok &= p->red && p->S;
+  if (mixed(p)) {
+    ok &= A(p->camT, sizeof(float) * CAM_STRIDE * (size_t)d.nc);
+    ok &= A(p->grpT, sizeof(float) * GRP_STRIDE * (size_t)(d.npl + d.nv));
+    ok &= A(p->ptsT, sizeof(float) * 3 * (size_t)d.np);
+    ok &= A(p->linT, sizeof(float) * 6 * (size_t)d.nl);
+    ok &= A(p->measT, sizeof(float) * 4 * (size_t)d.nr);
+  }
+  if (!ok) return set_err(p, BA_ERR_OOM, "device allocation failed");
+  // one-time zero fill of the slot and feature arrays
+  CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
+  CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
+  CUDA_OR(p, cudaMemsetAsync(p->Sval, 0, T * BS2 * (size_t)d.nbf, p->stream));
+  CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
+  CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
+  if (mixed(p) && d.nr) {
+    // float copy of the measurements for the mixed-precision linearisation
+    std::vector<double> hm(4 * (size_t)d.nr);
+    CUDA_OR(p, cudaMemcpyAsync(hm.data(), p->meas64, sizeof(double) * hm.size(), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_OR(p, cudaStreamSynchronize(p->stream));
+    std::vector<float> hf(hm.begin(), hm.end());
+    CUDA_OR(p, cudaMemcpyAsync(p->measT, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, p->stream));
+    CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  }
+  if ((s = plan_pcg(p))) return s;
+  CUDA_OR(p, cudaMallocHost((void**)&p->hS, sizeof(DevScalars)));
+  std::memset(p->hS, 0, sizeof(DevScalars));
+  p->hS->lambda = p->opt.lambda0;
+  p->hS->nu = 2.0;
+  p->hS->max_iters = p->opt.pcg_max_iters;
+  CUDA_OR(p, cudaMemcpyAsync(p->S, p->hS, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  for (auto& e : p->ev) CUDA_OR(p, cudaEventCreate(&e));
+  // cost at the initial parameters
+  if (mixed(p)) launch_prepare<float>(*p, false); else launch_prepare<double>(*p, false);
+  launch_cost(*p, false);
+  CUDA_OR(p, cudaGetLastError());
+  CUDA_OR(p, cudaMemcpyAsync(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+static ba_status sync_scalars(ba_problem* p) {
+  CUDA_OR(p, cudaGetLastError());
+  CUDA_OR(p, cudaMemcpyAsync(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+// events: ev[0] start, ev[1+k] end of kernel stage k (k = 0..9, see ba_step_report.ms_kernel)
+#define MARK(k) CUDA_OR(p, cudaEventRecord(p->ev[1 + (k)], p->stream))
+
+template <class T>
+static ba_status build_reduced_t(ba_problem* p, double lambda, bool* relin) {
+  if (!p->have_lin) {
+    launch_prepare<T>(*p, false);
+    launch_linearize<T>(*p);
+    p->have_lin = true;
+    if (relin) *relin = true;
+  }
+  MARK(0);
+  launch_invert<T>(*p, lambda);
+  MARK(1);
+  launch_schur<T>(*p, lambda);  // records ev[3] between the item and the block pass
+  MARK(3);
+  CUDA_OR(p, cudaGetLastError());
+  p->have_reduced = true;
+  p->last_lambda = lambda;
+  return BA_OK;
+}
+
+template <class T>
+static ba_status solve_reduced_t(ba_problem* p) {
+  launch_precond<T>(*p);
+  MARK(4);
+  launch_pcg<T>(*p);
+  if (p->pcg_err != cudaSuccess) return set_err(p, BA_ERR_CUDA, std::string("PCG launch: ") + cudaGetErrorString(p->pcg_err));
+  MARK(5);
+  launch_backsub<T>(*p);
+  MARK(6);
+  CUDA_OR(p, cudaGetLastError());
+  return BA_OK;
+}
+
+template <class T>
+static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
+  const double lam = p->hS->lambda;
+  bool relin = false;
+  p->launches = 0;
+  CUDA_OR(p, cudaEventRecord(p->ev[0], p->stream));
+  ba_status s = build_reduced_t<T>(p, lam, &relin);
+  if (s) return s;
+  if ((s = solve_reduced_t<T>(p))) return s;
+  launch_candidate(*p);
+  launch_prepare<T>(*p, true);
+  MARK(7);
+  launch_cost(*p, true);
+  MARK(8);
+  launch_decide(*p);
+  MARK(9);
+  if ((s = sync_scalars(p))) return s;
+  DevScalars& h = *p->hS;
+  ba_step_report r;
+  std::memset(&r, 0, sizeof(r));
+  r.cost = h.E; r.cost_px = h.Epx; r.cost_new = h.Enew; r.cost_px_new = h.Epxnew;
+  r.pred = h.pred; r.gain = h.gain; r.lambda = lam;
+  r.pcg_iters = h.iters; r.pcg_rel = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
+  r.accepted = h.accepted; r.relinearized = relin ? 1 : 0;
+  r.n_launches = p->launches;
+  for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&r.ms_kernel[k], p->ev[k], p->ev[k + 1]);
+  r.ms_linearize = r.ms_kernel[0];
+  r.ms_schur = r.ms_kernel[1] + r.ms_kernel[2] + r.ms_kernel[3] + r.ms_kernel[4];
+  r.ms_pcg = r.ms_kernel[5];
+  r.ms_update = r.ms_kernel[6] + r.ms_kernel[7] + r.ms_kernel[8] + r.ms_kernel[9];
+  if (h.accepted) {
+    double rel = std::fabs(h.Epx - h.Epxnew) / std::max(h.Epx, 1e-300);
+    r.converged = rel < p->opt.rel_cost_tol ? 1 : 0;
+    p->cur ^= 1;
+    p->have_lin = false;
+    p->have_reduced = false;
+    // the accepted cost becomes the current cost
+    h.E = h.Enew; h.Epx = h.Epxnew;
+    CUDA_OR(p, cudaMemcpyAsync(&p->S->E, &h.E, 2 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  }
+  if (rep) *rep = r;
+  if (!std::isfinite(h.E)) return set_err(p, BA_ERR_NUMERIC, "non-finite cost");
+  return BA_OK;
+}
+
+extern "C" ba_status ba_lm_step(ba_problem* p, ba_step_report* out) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  return mixed(p) ? lm_step_t<float>(p, out) : lm_step_t<double>(p, out);
+}
+
+extern "C" ba_status ba_solve(ba_problem* p, ba_solve_report* out) {
+  if (!p) return BA_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  ba_status s = freeze(p);
+  if (s) return s;
+  auto t1 = std::chrono::steady_clock::now();
+  ba_solve_report r;
+  std::memset(&r, 0, sizeof(r));
+  r.cost0 = p->hS->E;
+  for (int it = 0; it < p->opt.max_lm_iters; ++it) {
+    ba_step_report sr;
+    if ((s = ba_lm_step(p, &sr))) return s;
+    r.iters++;
+    r.total_pcg_iters += sr.pcg_iters;
+    if (sr.accepted) r.accepted_steps++;
+    if (sr.converged) { r.converged = 1; break; }
+  }
+  r.cost = p->hS->E;
+  r.cost_px = p->hS->Epx;
+  auto t2 = std::chrono::steady_clock::now();
+  r.ms_structure = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  r.ms_total = std::chrono::duration<double, std::milli>(t2 - t0).count();
+  if (out) *out = r;
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+template <class X>
+static ba_status put_out(ba_problem* p, int mem, X* dst, const X* src, size_t n) {
+  if (n == 0) return BA_OK;
+  if (!dst) return set_err(p, BA_ERR_ARG, "null output");
+  cudaMemcpyKind k = mem == BA_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_OR(p, cudaMemcpyAsync(dst, src, n * sizeof(X), k, p->stream));
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+extern "C" ba_status ba_get_cameras(ba_problem* p, int mem, double* quat_t) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  const int64_t n = p->d.nc;
+  std::vector<double> h(12 * n);
+  if ((s = put_out(p, BA_MEM_HOST, h.data(), p->ps[p->cur].cam, h.size()))) return s;
+  std::vector<double> o(7 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 7; ++k) o[7 * i + k] = h[12 * i + k];
+  if (mem == BA_MEM_HOST) { if (n) std::memcpy(quat_t, o.data(), o.size() * sizeof(double)); return BA_OK; }
+  CUDA_OR(p, cudaMemcpy(quat_t, o.data(), o.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return BA_OK;
+}
+
+extern "C" ba_status ba_get_features(ba_problem* p, int kind, int mem, double* params) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  if (kind == BA_POINT) return put_out(p, mem, params, (const double*)p->ps[p->cur].pts, 3 * (size_t)p->d.np);
+  if (kind == BA_LINE) return put_out(p, mem, params, (const double*)p->ps[p->cur].lin, 6 * (size_t)p->d.nl);
+  return set_err(p, BA_ERR_ARG, "bad feature kind");
+}
+
+extern "C" ba_status ba_get_groups(ba_problem* p, int kind, int mem, double* params) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  if (kind == BA_PLANE) return put_out(p, mem, params, (const double*)p->ps[p->cur].pln, 4 * (size_t)p->d.npl);
+  if (kind == BA_VP) return put_out(p, mem, params, (const double*)p->ps[p->cur].vps, 3 * (size_t)p->d.nv);
+  return set_err(p, BA_ERR_ARG, "bad group kind");
+}
+
+extern "C" ba_status ba_get_lm_state(ba_problem* p, double* ln) {
+  if (!p || !ln) return BA_ERR_ARG;
+  if (!p->frozen) { ln[0] = p->opt.lambda0; ln[1] = 2.0; return BA_OK; }
+  ln[0] = p->hS->lambda; ln[1] = p->hS->nu;
+  return BA_OK;
+}
+
+extern "C" ba_status ba_set_lm_state(ba_problem* p, const double* ln) {
+  if (!p || !ln || !(ln[0] > 0) || !(ln[1] > 0)) return p ? set_err(p, BA_ERR_ARG, "lambda and nu must be positive") : BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  p->hS->lambda = ln[0]; p->hS->nu = ln[1];
+  CUDA_OR(p, cudaMemcpyAsync(&p->S->lambda, &p->hS->lambda, 2 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+extern "C" ba_status ba_eval_cost(ba_problem* p, double* cost, double* cost_px) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  if (cost) *cost = p->hS->E;
+  if (cost_px) *cost_px = p->hS->Epx;
+  return BA_OK;
+}
+
+extern "C" ba_status ba_build_reduced(ba_problem* p, double lambda) {
+  if (!p) return BA_ERR_ARG;
+  if (!(lambda >= 0) || !std::isfinite(lambda)) return set_err(p, BA_ERR_ARG, "lambda must be finite and >= 0");
+  ba_status s = freeze(p);
+  if (s) return s;
+  s = mixed(p) ? build_reduced_t<float>(p, lambda, nullptr) : build_reduced_t<double>(p, lambda, nullptr);
+  if (s) return s;
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+extern "C" ba_status ba_reduced_size(ba_problem* p, int64_t* nrows, int64_t* nnzb) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  if (nrows) *nrows = p->d.na;
+  if (nnzb) *nnzb = p->d.nbf;
+  return BA_OK;
+}
+
+extern "C" ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, int32_t* cols, double* vals, double* b) {
+  if (!p) return BA_ERR_ARG;
+  if (!p->have_reduced) return set_err(p, BA_ERR_STATE, "no reduced system built (call ba_build_reduced)");
+  const Dims& d = p->d;
+  ba_status s;
+  if (row_ptr && (s = put_out(p, BA_MEM_HOST, row_ptr, (const int32_t*)p->row_ptr, d.na + 1))) return s;
+  if (cols && (s = put_out(p, BA_MEM_HOST, cols, (const int32_t*)p->col, d.nbf))) return s;
+  if (vals) {
+    size_t n = (size_t)BS2 * d.nbf;
+    if (mixed(p)) {
+      std::vector<float> h(n);
+      if ((s = put_out(p, BA_MEM_HOST, h.data(), (const float*)p->Sval, n))) return s;
+      for (size_t i = 0; i < n; ++i) vals[i] = h[i];
+    } else if ((s = put_out(p, BA_MEM_HOST, vals, (const double*)p->Sval, n))) {
+      return s;
+    }
+  }
+  if (b && (s = put_out(p, BA_MEM_HOST, b, (const double*)p->bvec, 6 * (size_t)d.na))) return s;
+  return BA_OK;
+}
+
+extern "C" ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* dvp, double* dpoint,
+                                     double* dline, int* pcg_iters, double* pcg_rel, double* pred) {
+  if (!p) return BA_ERR_ARG;
+  if (!p->have_reduced) return set_err(p, BA_ERR_STATE, "no reduced system built (call ba_build_reduced)");
+  ba_status s = mixed(p) ? solve_reduced_t<float>(p) : solve_reduced_t<double>(p);
+  if (s) return s;
+  if ((s = sync_scalars(p))) return s;
+  const Dims& d = p->d;
+  std::vector<double> x(6 * d.na), df(4 * d.nf);
+  if ((s = put_out(p, BA_MEM_HOST, x.data(), (const double*)p->x, x.size()))) return s;
+  if ((s = put_out(p, BA_MEM_HOST, df.data(), (const double*)p->dfeat, df.size()))) return s;
+  if (dcam) for (int64_t i = 0; i < d.nc; ++i) for (int k = 0; k < 6; ++k) dcam[6 * i + k] = x[6 * i + k];
+  if (dplane) for (int64_t i = 0; i < d.npl; ++i) for (int k = 0; k < 3; ++k) dplane[3 * i + k] = x[6 * (d.nc + i) + k];
+  if (dvp) for (int64_t i = 0; i < d.nv; ++i) for (int k = 0; k < 2; ++k) dvp[2 * i + k] = x[6 * (d.nc + d.npl + i) + k];
+  if (dpoint) for (int64_t i = 0; i < d.np; ++i) for (int k = 0; k < 3; ++k) dpoint[3 * i + k] = df[4 * i + k];
+  if (dline) for (int64_t i = 0; i < d.nl; ++i) for (int k = 0; k < 4; ++k) dline[4 * i + k] = df[4 * (d.np + i) + k];
+  if (pcg_iters) *pcg_iters = p->hS->iters;
+  if (pcg_rel) *pcg_rel = p->hS->bnorm2 > 0 ? std::sqrt(p->hS->rr / p->hS->bnorm2) : 0.0;
+  if (pred) *pred = p->hS->pred;
+  return BA_OK;
+}

@@ -1,0 +1,164 @@
+// Internal declarations of libba: device buffers, the frozen problem structure,
+// kernel launchers.  Host orchestration lives in api.cu, kernels in kernels.cu,
+// the one-time structure build (the analogue of a sparse solver's symbolic
+// analysis) in structure.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ba.h"
+#include "residuals.cuh"
+
+namespace ba {
+
+// ---------------------------------------------------------------------------
+// device memory: allocated through the caller's hooks (e.g. the framework's
+// caching allocator) when given, else cudaMalloc; freed in the destructor
+struct Alloc {
+  void* (*fa)(size_t, void*) = nullptr;
+  void (*ff)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (fa) return fa(bytes, ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    if (ff) ff(p, ctx); else cudaFree(p);
+  }
+};
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// block sizes of the padded reduced system: every entity of A occupies a 6-wide block
+constexpr int BS = 6;
+constexpr int BS2 = BS * BS;
+// per-slot record strides (in elements of the slot type)
+constexpr int SW = 24;  // W^T (k x 6), k = 3 (point) or 4 (line)
+constexpr int SH = 21;  // upper triangle of the direct 6x6 block J_a^T w J_a
+constexpr int SG = 6;   // J_a^T w r
+constexpr int SC = 18;  // camera slot: J_cam^T w J_plane (6 x 3)
+constexpr int PART = BS2 + 12;  // partial of one Schur work item: 36 S + 6 b + 6 diag(H)
+
+enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
+
+// scalars kept on the device so that PCG and the LM decision need no host round trip
+struct DevScalars {
+  double rz, rz_new, pAp, rr, bnorm2, alpha, beta, tol2;
+  double E, Epx, Enew, Epxnew, pred, gTd, dHd;
+  double lambda, nu, gain;
+  int iters, max_iters, done, accepted;
+  int flags;                 // bit 0: a landmark block needed extra damping; bit 1: non-finite value
+  unsigned int counter[8];   // arrival counters of the last-block reductions
+};
+
+// the frozen problem structure (built once, K0) plus every device array
+using Problem = ::ba_problem;
+
+struct Dims {
+  int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
+  int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, npair = 0, nwi = 0;
+  int64_t n_points_res_end = 0;  // residuals of points are [0, this); lines follow
+};
+
+// kernel launchers (kernels.cu); T = double (FP64 path) or float (mixed path)
+template <class T> void launch_prepare(Problem& P, bool candidate_only);
+template <class T> void launch_linearize(Problem& P);
+template <class T> void launch_invert(Problem& P, double lambda);
+template <class T> void launch_schur(Problem& P, double lambda);
+template <class T> void launch_precond(Problem& P);
+template <class T> void launch_pcg(Problem& P);
+template <class T> int pcg_blocks_per_sm(size_t smem);
+template <class T> void pcg_allow_smem(size_t smem);
+constexpr int PCG_CHUNK = 64;   // stored blocks per SpMV chunk
+template <class T> void launch_backsub(Problem& P);
+void launch_candidate(Problem& P);
+void launch_cost(Problem& P, bool candidate);
+void launch_decide(Problem& P);
+
+}  // namespace ba
+
+// The problem object (opaque to the ABI).
+struct ba_problem {
+  ba_options opt;
+  std::string err;
+  ba::Alloc alloc;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool frozen = false;
+  bool have_lin = false;     // linearisation valid for the current parameters
+  bool have_reduced = false;
+  double last_lambda = 0;
+
+  // host staging of inputs until the structure is frozen
+  std::vector<double> h_cam;      // n x 12: q(4) t(3) f k1 k2 ppx ppy
+  std::vector<uint8_t> h_fixed;
+  std::vector<double> h_pts, h_lin, h_pln, h_vps;
+  struct ObsBatch {
+    int kind;
+    std::vector<int32_t> cam, feat, other;
+    std::vector<double> meas;  // n x 4 padded
+  };
+  std::vector<ObsBatch> h_obs;
+
+  ba::Dims d;
+  std::vector<ba::DBuf> bufs;
+  void* dalloc(size_t bytes);
+  template <class X> X* dnew(int64_t n) { return (X*)dalloc(sizeof(X) * (size_t)(n > 0 ? n : 1)); }
+
+  // ---- device arrays
+  // parameters: two FP64 sets (current / candidate), each with its FP64 derived per-entity data
+  struct ParamSet {
+    double *cam = nullptr, *pts = nullptr, *lin = nullptr, *pln = nullptr, *vps = nullptr;
+    double *camD = nullptr, *grpD = nullptr;   // rotation matrices / tangent bases (CAM_STRIDE / GRP_STRIDE)
+  } ps[2];
+  int cur = 0;
+  // working-type (double or float) copies of the current parameters used by the linearisation
+  void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr;
+  uint8_t* cam_fixed = nullptr;
+  // residuals, feature-major
+  int8_t* rkind = nullptr;
+  int32_t *rcam = nullptr, *rfeat = nullptr, *rgrp = nullptr, *rslot_c = nullptr, *rslot_g = nullptr;
+  double* meas64 = nullptr;
+  void* measT = nullptr;
+  int32_t *fres_off = nullptr, *fslot_off = nullptr;
+  int32_t *slot_ent = nullptr, *slot_feat = nullptr;
+  uint8_t* slot_type = nullptr;
+  int32_t* feat_plane_slot = nullptr;
+  uint8_t* ent_type = nullptr;
+  // reduced system pattern
+  int32_t *row_ptr = nullptr, *col = nullptr;
+  int32_t *up_row = nullptr, *up_full = nullptr, *up_mirror = nullptr, *up_wi = nullptr;
+  int32_t *pair_a = nullptr, *pair_b = nullptr, *wi_start = nullptr;
+  // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are
+  // cut into chunks [chunk_beg[q], chunk_beg[q+1]) for q in [row_chunk0[r], row_chunk0[r+1])
+  int32_t *cta_row0 = nullptr, *row_chunk0 = nullptr, *chunk_beg = nullptr;
+  int pcg_grid = 0;
+  size_t pcg_smem = 0;
+  cudaError_t pcg_err = cudaSuccess;
+  // numeric arrays
+  void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotY = nullptr, *slotB = nullptr;
+  double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featz = nullptr, *dfeat = nullptr;
+  void *Sval = nullptr, *Minv = nullptr, *part = nullptr;
+  double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
+  double* red = nullptr;        // per-block partial sums of reductions
+  int red_cap = 0;
+  ba::DevScalars* S = nullptr;  // device scalars
+  ba::DevScalars* hS = nullptr; // pinned host mirror
+
+  cudaEvent_t ev[16] = {};
+  int launches = 0;              // kernel launches since the start of the current step
+};
+
+namespace ba {
+ba_status build_structure(Problem& P);   // structure.cu
+}

@@ -1,0 +1,1403 @@
+// CUDA kernels of one LM step of holistic BA (sm_103a).
+//
+//   k_derive        per-entity data of a parameter set (rotation matrices, tangent bases)
+//   k_linearize     K1: every residual of a feature and its IRLS weight; per-feature
+//                   reduction of V_f = sum J_f^T w J_f, g_f, and per (feature, entity)
+//                   slot W^T, the direct J_a^T w J_a block, J_a^T w r and, for cameras
+//                   of a plane feature, J_cam^T w J_plane (thread per feature)
+//   k_invert        K2: (V_f + lambda D_f)^-1 by FP64 Cholesky, z_f = V^-1 g_f, and per
+//                   slot Y^T = V^-1 W^T and b-part -g_a + W z_f
+//   k_schur_items   K3: atomic-free Schur accumulation.  Every upper block of S owns a
+//                   list of slot pairs; each work item (<= 64 pairs) sums
+//                   direct terms - Y_a^T W_b in a fixed order into a partial
+//   k_schur_blocks  K3: sums the partials of each block in order, adds lambda D on the
+//                   diagonal, writes both triangles of the full block-CSR S and b
+//   k_precond       K4: block-Jacobi inverse of the diagonal blocks of S (FP64 Cholesky)
+//   k_pcg_*         K5/K6: PCG with a warp-per-block-row SpMV, FP64 vectors and dots, and
+//                   a device-side stop flag so the host never waits inside the loop
+//   k_backsub       K7: delta_f = -V^-1 (g_f + W^T delta_a) and the predicted decrease
+//                   -g.delta - 1/2 delta^T H delta from the stored blocks
+//   k_candidate     K8: x (+) delta with the manifold retractions
+//   k_cost          K8: FP64 robust cost of every residual, E and E_px
+//   k_decide        K9: gain ratio, accept / reject, damping update
+// All reductions are deterministic: warp shuffles in a fixed tree, per-block
+// partials, and a last-arriving block that sums the partials in index order.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ba_internal.cuh"
+
+namespace ba {
+
+// ============================================================================
+// deterministic reductions
+// ============================================================================
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce NV values over the grid.  Returns true in the last block to arrive (all
+// of whose threads then hold the totals in `tot`).  `red` holds gridDim.x * NV doubles.
+template <int NV>
+__device__ bool grid_reduce(double (&v)[NV], double* red, unsigned int* counter, double (&tot)[NV]) {
+  __shared__ double sh[32][NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid][i] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = 0;
+    for (int w = 0; w < nw; ++w)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) s[i] += sh[w][i];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[(size_t)blockIdx.x * NV + i] = s[i];
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) s[i] = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] += __ldcg(&red[(size_t)b * NV + i]);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) s[i] = warp_sum(s[i]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid][i] = s[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double a = 0;
+    for (int w = 0; w < nw; ++w) a += sh[w][i];
+    tot[i] = a;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ============================================================================
+// small dense helpers
+// ============================================================================
+__host__ __device__ constexpr int up_idx(int i, int j, int k) { return i * k - i * (i - 1) / 2 + (j - i); }
+
+// Cholesky inverse of an n x n SPD matrix given by its upper triangle (up_idx layout).
+// Returns false if a pivot is not positive.
+template <int N>
+__device__ bool chol_inverse(const double* Aup, double (&Ainv)[N][N]) {
+  double L[N][N];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) L[i][j] = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    double s = Aup[up_idx(j, j, N)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > 0)) return false;
+    double ljj = sqrt(s);
+    L[j][j] = ljj;
+    double il = 1.0 / ljj;
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      double t = Aup[up_idx(j, i, N)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t * il;
+    }
+  }
+  // invert L (lower triangular)
+  double Li[N][N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) Li[i][j] = 0;
+    Li[i][i] = 1.0 / L[i][i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      double s = 0;
+#pragma unroll
+      for (int k = j; k < i; ++k) s += L[i][k] * Li[k][j];
+      Li[i][j] = -s * Li[i][i];
+    }
+  }
+  // A^-1 = L^-T L^-1
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      double s = 0;
+#pragma unroll
+      for (int k = j; k < N; ++k) s += Li[k][i] * Li[k][j];
+      Ainv[i][j] = s;
+      Ainv[j][i] = s;
+    }
+  return true;
+}
+
+// ============================================================================
+// derived per-entity data
+// ============================================================================
+__device__ void quat_to_R(const double* q, double* R) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double n = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+  w *= n; x *= n; y *= n; z *= n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+__device__ void tangent_basis_d(const double* n, double* b1, double* b2) {
+  tangent_b1<double>(n, b1);
+  cross3(n, b1, b2);
+}
+
+// cams: src n x 12 -> D (double) and optionally W (working type) with CAM_STRIDE
+template <class T>
+__global__ void k_derive_cams(int64_t nc, const double* __restrict__ src, double* __restrict__ D, T* __restrict__ W) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  const double* c = src + 12 * i;
+  double o[17];
+  quat_to_R(c, o);
+  o[9] = c[4]; o[10] = c[5]; o[11] = c[6];
+  o[12] = c[7]; o[13] = c[8]; o[14] = c[9]; o[15] = c[10]; o[16] = c[11];
+  for (int k = 0; k < 17; ++k) D[CAM_STRIDE * i + k] = o[k];
+  if (W)
+    for (int k = 0; k < 17; ++k) W[CAM_STRIDE * i + k] = (T)o[k];
+}
+
+// groups: planes (n, w) then VPs v -> [n|v (3), w|0, b1 (3), b2 (3)] with GRP_STRIDE
+template <class T>
+__global__ void k_derive_groups(int64_t npl, int64_t nv, const double* __restrict__ pln, const double* __restrict__ vps,
+                                double* __restrict__ D, T* __restrict__ W) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npl + nv) return;
+  double o[10];
+  if (i < npl) {
+    const double* q = pln + 4 * i;
+    o[0] = q[0]; o[1] = q[1]; o[2] = q[2]; o[3] = q[3];
+  } else {
+    const double* v = vps + 3 * (i - npl);
+    o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = 0;
+  }
+  tangent_basis_d(o, o + 4, o + 7);
+  for (int k = 0; k < 10; ++k) D[GRP_STRIDE * i + k] = o[k];
+  if (W)
+    for (int k = 0; k < 10; ++k) W[GRP_STRIDE * i + k] = (T)o[k];
+}
+
+__global__ void k_convert(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ============================================================================
+// K1: linearise and reduce per feature
+// ============================================================================
+struct LossW {
+  double w[7];
+  double a2[7];
+};
+
+template <class T>
+struct LinArgs {
+  const int8_t* rkind;
+  const uint8_t* cam_mask;   // held pose components per camera (bit k = increment k)
+  const int32_t *rcam, *rgrp, *rslot_c, *rslot_g, *fres_off, *feat_plane_slot;
+  const T* meas;
+  const T *cam, *pts, *lin, *grp;
+  int64_t npl, np;
+  T *W, *H, *G, *C;
+  double *V, *g;
+  LossW loss;
+};
+
+template <class T, int KF>
+__global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int64_t f1) {
+  int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= f1) return;
+  const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
+  constexpr int NV = KF * (KF + 1) / 2;
+  T V[NV], gf[KF];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) V[i] = 0;
+#pragma unroll
+  for (int i = 0; i < KF; ++i) gf[i] = 0;
+  // current camera slot accumulators
+  T Wc[KF][6], Hc[21], Gc[6], Cc[6][3];
+  int cur = -1;
+  // group slot accumulators: plane (3 dof), VP (2 dof, lines only)
+  T Wp[KF][3], Hp[6], Gp[3];
+  T Wv[KF][2], Hv[3], Gv[2];
+  int ps = -1, vs = -1;
+#pragma unroll
+  for (int i = 0; i < KF; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Wp[i][j] = 0;
+    Wv[i][0] = 0; Wv[i][1] = 0;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Hp[i] = 0;
+  Gp[0] = Gp[1] = Gp[2] = 0;
+  Hv[0] = Hv[1] = Hv[2] = 0;
+  Gv[0] = Gv[1] = 0;
+  const int plane_slot = a.feat_plane_slot[f];
+
+  T F[6];
+  if (KF == 3) {
+    const T* X = a.pts + 3 * f;
+    F[0] = X[0]; F[1] = X[1]; F[2] = X[2];
+  } else {
+    const T* L = a.lin + 6 * (f - a.np);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) F[i] = L[i];
+  }
+
+  auto flush = [&](int e) {
+    T* W = a.W + (size_t)e * SW;
+#pragma unroll
+    for (int i = 0; i < KF; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) W[i * 6 + j] = Wc[i][j];
+    T* H = a.H + (size_t)e * SH;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) H[i] = Hc[i];
+    T* G = a.G + (size_t)e * SG;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) G[i] = Gc[i];
+    if (plane_slot >= 0) {
+      T* C = a.C + (size_t)e * SC;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) C[i * 3 + j] = Cc[i][j];
+    }
+  };
+  auto zero_cam = [&]() {
+#pragma unroll
+    for (int i = 0; i < KF; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) Wc[i][j] = 0;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) Hc[i] = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      Gc[i] = 0;
+      Cc[i][0] = Cc[i][1] = Cc[i][2] = 0;
+    }
+  };
+  zero_cam();
+
+  for (int rr = r0; rr < r1; ++rr) {
+    const int kind = a.rkind[rr];
+    const int sc = a.rslot_c[rr];
+    if (sc != cur) {
+      if (cur >= 0) flush(cur);
+      zero_cam();
+      cur = sc;
+    }
+    const int camid = a.rcam[rr];
+    const int gid = a.rgrp[rr];
+    const T* meas = a.meas + 4 * (size_t)rr;
+    Cam<T> c;
+    if (camid >= 0) load_cam(a.cam + (size_t)CAM_STRIDE * camid, c);
+    ResJ<T> o;
+    int rd = res_dim(kind);
+    bool has_plane = false, has_vp = false;
+    if (KF == 3) {
+      if (kind == R_POINT) res_point<T, true>(c, F, meas, o);
+      else if (kind == R_PLANE_POINT) { res_plane_point<T, true>(c, F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
+      else if (kind == R_P2L) res_p2l<T, true>(c, F, meas, o);
+      else continue;
+    } else {
+      if (kind == R_LINE) res_line<T, true>(c, F, meas, o);
+      else if (kind == R_PLANE_LINE) { res_plane_line<T, true>(c, F, a.grp + (size_t)GRP_STRIDE * gid, meas, o); has_plane = true; }
+      else if (kind == R_VP) { res_vp<T, true>(F, a.grp + (size_t)GRP_STRIDE * (a.npl + gid), o); has_vp = true; }
+      else if (kind == R_L2P) res_l2p<T, true>(c, F, meas, o);
+      else continue;
+    }
+    if (!o.valid) continue;
+    if (camid >= 0) {
+      const unsigned held = a.cam_mask[camid];
+      if (held)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 6; ++k)
+            if ((held >> k) & 1u) o.Jc[i][k] = 0;
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < rd) s += o.r[i] * o.r[i];
+    const T om = (T)a.loss.w[kind] / (T(1) + s / (T)a.loss.a2[kind]);
+    if (has_plane) ps = a.rslot_g[rr];
+    if (has_vp) vs = a.rslot_g[rr];
+    const bool camslot = sc >= 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= rd) break;
+      T wf[KF], wc[6], wg[3];
+#pragma unroll
+      for (int k = 0; k < KF; ++k) wf[k] = om * o.Jf[i][k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wc[k] = om * o.Jc[i][k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) wg[k] = om * o.Jg[i][k];
+      const T ri = o.r[i];
+      // V_f and g_f
+#pragma unroll
+      for (int p = 0; p < KF; ++p) {
+        gf[p] += wf[p] * ri;
+#pragma unroll
+        for (int q = p; q < KF; ++q) V[up_idx(p, q, KF)] += wf[p] * o.Jf[i][q];
+      }
+      if (camslot) {
+#pragma unroll
+        for (int p = 0; p < KF; ++p)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Wc[p][q] += wf[p] * o.Jc[i][q];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          Gc[p] += wc[p] * ri;
+#pragma unroll
+          for (int q = p; q < 6; ++q) Hc[up_idx(p, q, 6)] += wc[p] * o.Jc[i][q];
+        }
+        if (has_plane)
+#pragma unroll
+          for (int p = 0; p < 6; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Cc[p][q] += wc[p] * o.Jg[i][q];
+      }
+      if (has_plane) {
+#pragma unroll
+        for (int p = 0; p < KF; ++p)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) Wp[p][q] += wf[p] * o.Jg[i][q];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          Gp[p] += wg[p] * ri;
+#pragma unroll
+          for (int q = p; q < 3; ++q) Hp[up_idx(p, q, 3)] += wg[p] * o.Jg[i][q];
+        }
+      }
+      if (KF == 4 && has_vp) {
+#pragma unroll
+        for (int p = 0; p < KF; ++p)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) Wv[p][q] += wf[p] * o.Jg[i][q];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          Gv[p] += wg[p] * ri;
+#pragma unroll
+          for (int q = p; q < 2; ++q) Hv[up_idx(p, q, 2)] += wg[p] * o.Jg[i][q];
+        }
+      }
+    }
+  }
+  if (cur >= 0) flush(cur);
+  // group slots, padded to the 6-wide block of the reduced system
+  auto put_group = [&](int e, int nd, const T* Wg, const T* Hg, const T* Gg) {
+    T* W = a.W + (size_t)e * SW;
+    for (int i = 0; i < KF; ++i)
+      for (int j = 0; j < 6; ++j) W[i * 6 + j] = j < nd ? Wg[i * nd + j] : T(0);
+    T* H = a.H + (size_t)e * SH;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i; j < 6; ++j) H[up_idx(i, j, 6)] = (j < nd) ? Hg[up_idx(i, j, nd)] : T(0);
+    T* G = a.G + (size_t)e * SG;
+    for (int i = 0; i < 6; ++i) G[i] = i < nd ? Gg[i] : T(0);
+  };
+  if (ps < 0) ps = plane_slot;  // a plane slot whose residuals were all invalid
+  if (ps >= 0) put_group(ps, 3, &Wp[0][0], Hp, Gp);
+  if (KF == 4) {
+    if (vs < 0) {
+      // find the VP slot (if any) among this feature's residuals
+      for (int rr = r0; rr < r1; ++rr)
+        if (a.rkind[rr] == R_VP) { vs = a.rslot_g[rr]; break; }
+    }
+    if (vs >= 0) put_group(vs, 2, &Wv[0][0], Hv, Gv);
+  }
+  double* Vo = a.V + 10 * f;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) Vo[i] = (double)V[i];
+  double* go = a.g + 4 * f;
+#pragma unroll
+  for (int i = 0; i < KF; ++i) go[i] = (double)gf[i];
+}
+
+// ============================================================================
+// K2: damped landmark inverse and the per-slot Y, b parts
+// ============================================================================
+template <class T>
+struct InvArgs {
+  const int32_t* fslot_off;
+  const double *V, *g;
+  const T *W, *G;
+  double *Vinv, *z;
+  T *Y, *B;
+  int64_t np, nf;
+  double lambda;
+  DevScalars* S;
+};
+
+template <int K>
+__device__ void invert_damped(const double* Vup, double lambda, double (&Vi)[K][K], int* flag) {
+  double A[K * (K + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < K * (K + 1) / 2; ++i) A[i] = Vup[i];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    double dgi = fmin(fmax(A[up_idx(i, i, K)], 1e-6), 1e32);
+    A[up_idx(i, i, K)] += lambda * dgi;
+  }
+  if (!chol_inverse<K>(A, Vi)) {
+    // rounding made the damped block indefinite: add damping until it factorises
+    *flag = 1;
+    double tr = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) tr += fabs(A[up_idx(i, i, K)]);
+    double extra = 1e-12 * tr + 1e-300;
+    for (int t = 0; t < 60; ++t) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) A[up_idx(i, i, K)] += extra;
+      if (chol_inverse<K>(A, Vi)) return;
+      extra *= 10;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j < K; ++j) Vi[i][j] = 0;
+  }
+}
+
+template <class T, int K>
+__device__ void invert_feature(const InvArgs<T>& a, int64_t f) {
+  double Vi[K][K];
+  int flag = 0;
+  invert_damped<K>(a.V + 10 * f, a.lambda, Vi, &flag);
+  if (flag) atomicOr(&a.S->flags, 1);
+  double gz[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    double s = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s += Vi[i][j] * a.g[4 * f + j];
+    gz[i] = s;
+  }
+  double* vo = a.Vinv + 10 * f;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = i; j < K; ++j) vo[up_idx(i, j, K)] = Vi[i][j];
+#pragma unroll
+  for (int i = 0; i < K; ++i) a.z[4 * f + i] = gz[i];
+  T Vt[K][K], zt[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    zt[i] = (T)gz[i];
+#pragma unroll
+    for (int j = 0; j < K; ++j) Vt[i][j] = (T)Vi[i][j];
+  }
+  for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
+    const T* W = a.W + (size_t)e * SW;
+    T w[K][6];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) w[i][j] = W[i * 6 + j];
+    T* Y = a.Y + (size_t)e * SW;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        T s = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) s += Vt[i][k] * w[k][j];
+        Y[i * 6 + j] = s;
+      }
+    const T* G = a.G + (size_t)e * SG;
+    T* B = a.B + (size_t)e * SG;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      T s = -G[j];
+#pragma unroll
+      for (int k = 0; k < K; ++k) s += w[k][j] * zt[k];
+      B[j] = s;
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_invert(InvArgs<T> a) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= a.nf) return;
+  if (f < a.np) invert_feature<T, 3>(a, f);
+  else invert_feature<T, 4>(a, f);
+}
+
+// ============================================================================
+// K3: Schur complement, atomic-free
+// ============================================================================
+template <class T>
+struct SchurArgs {
+  const int32_t *pair_a, *pair_b, *wi_se, *slot_feat;
+  const uint8_t* slot_type;
+  const T *W, *Y, *H, *B, *C;
+  T* part;
+  int64_t np, nwi;
+};
+
+template <class T>
+__global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
+  int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= a.nwi) return;
+  const int s0 = a.wi_se[2 * w], s1 = a.wi_se[2 * w + 1];
+  T acc[6][6], bacc[6], hacc[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    bacc[i] = 0; hacc[i] = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[i][j] = 0;
+  }
+  for (int q = s0; q < s1; ++q) {
+    const int ea = a.pair_a[q], eb = a.pair_b[q];
+    const int k = a.slot_feat[ea] < a.np ? 3 : 4;
+    const T* Ya = a.Y + (size_t)ea * SW;
+    const T* Wb = a.W + (size_t)eb * SW;
+    // S_ab -= Y_a^T W_b   (rows: feature dof c)
+    for (int c = 0; c < k; ++c) {
+      T y[6], wv[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) { y[i] = Ya[c * 6 + i]; wv[i] = Wb[c * 6 + i]; }
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[i][j] -= y[i] * wv[j];
+    }
+    if (ea == eb) {
+      const T* H = a.H + (size_t)ea * SH;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+          T h = H[up_idx(i, j, 6)];
+          acc[i][j] += h;
+          if (j != i) acc[j][i] += h;
+        }
+      const T* B = a.B + (size_t)ea * SG;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        bacc[i] += B[i];
+        hacc[i] += H[up_idx(i, i, 6)];
+      }
+    } else if (a.slot_type[ea] == ENT_CAM && a.slot_type[eb] == ENT_PLANE) {
+      const T* Cm = a.C + (size_t)ea * SC;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[i][j] += Cm[i * 3 + j];
+    }
+  }
+  T* o = a.part + (size_t)w * PART;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) o[i * 6 + j] = acc[i][j];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) { o[36 + i] = bacc[i]; o[42 + i] = hacc[i]; }
+}
+
+template <class T>
+struct BlockArgs {
+  const int32_t *up_row, *up_full, *up_mirror, *up_wi, *col;
+  const uint8_t *ent_type, *cam_fixed;
+  const T* part;
+  T* Sval;
+  double *b, *Dg;
+  int64_t nbu, nc;
+  double lambda;
+};
+
+template <class T>
+__global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= a.nbu) return;
+  const int row = a.up_row[u];
+  const int fpos = a.up_full[u];
+  const bool diag = a.col[fpos] == row;
+  T s[36];
+  double bb[6], hh[6];
+#pragma unroll
+  for (int i = 0; i < 36; ++i) s[i] = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) { bb[i] = 0; hh[i] = 0; }
+  for (int w = a.up_wi[u]; w < a.up_wi[u + 1]; ++w) {
+    const T* p = a.part + (size_t)w * PART;
+#pragma unroll
+    for (int i = 0; i < 36; ++i) s[i] += p[i];
+    if (diag)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) { bb[i] += (double)p[36 + i]; hh[i] += (double)p[42 + i]; }
+  }
+  T* out = a.Sval + (size_t)fpos * BS2;
+  if (diag) {
+    const int et = a.ent_type[row];
+    const int nd = et == ENT_CAM ? 6 : (et == ENT_PLANE ? 3 : 2);
+    const unsigned held = (row < a.nc) ? a.cam_fixed[row] : 0u;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      bool real = i < nd && !((held >> i) & 1u);
+      double Di = real ? fmin(fmax(hh[i], 1e-6), 1e32) : 1.0;
+      a.Dg[6 * (size_t)row + i] = Di;
+      if (real) {
+        s[i * 6 + i] += (T)(a.lambda * Di);
+        a.b[6 * (size_t)row + i] = bb[i];
+      } else {
+        // padding (or a held camera): unit diagonal, no coupling, zero right-hand side
+#pragma unroll
+        for (int j = 0; j < 6; ++j) { s[i * 6 + j] = 0; s[j * 6 + i] = 0; }
+        s[i * 6 + i] = 1;
+        a.b[6 * (size_t)row + i] = 0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 36; ++i) out[i] = s[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 36; ++i) out[i] = s[i];
+    T* mir = a.Sval + (size_t)a.up_mirror[u] * BS2;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) mir[j * 6 + i] = s[i * 6 + j];
+  }
+}
+
+// ============================================================================
+// K4: block-Jacobi preconditioner
+// ============================================================================
+template <class T>
+__global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                          const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S) {
+  int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= na) return;
+  int pos = -1;
+  for (int q = row_ptr[a]; q < row_ptr[a + 1]; ++q)
+    if (col[q] == a) { pos = q; break; }
+  double Aup[21];
+  const T* B = Sval + (size_t)pos * BS2;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j) Aup[up_idx(i, j, 6)] = (double)B[i * 6 + j];
+  double Mi[6][6];
+  if (!chol_inverse<6>(Aup, Mi)) {
+    atomicOr(&S->flags, 4);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) Mi[i][j] = (i == j && Aup[up_idx(i, i, 6)] > 0) ? 1.0 / Aup[up_idx(i, i, 6)] : (i == j ? 1.0 : 0.0);
+  }
+  T* o = Minv + (size_t)a * BS2;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) o[i * 6 + j] = (T)Mi[i][j];
+}
+
+// ============================================================================
+// K5/K6: preconditioned conjugate gradients
+// ============================================================================
+template <class T>
+__device__ __forceinline__ void apply_block(const T* __restrict__ M, const double* __restrict__ v, double* o) {
+  T vv[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) vv[j] = (T)v[j];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += M[i * 6 + j] * vv[j];
+    o[i] = (double)s;
+  }
+}
+
+// Persistent PCG: one cooperative launch runs the whole solve.  Every CTA owns a
+// contiguous range of block rows (balanced by stored blocks); rows are cut into
+// chunks of <= PCG_CHUNK blocks that the CTA's warps multiply (FP32 / working-type
+// products, FP64 sums of the block results), and a warp sums a row's chunk partials
+// in order, so y = S p is deterministic.  Three grid-wide barriers per iteration:
+// after the SpMV (alpha needs p.Ap), after the update (beta and the stop test need
+// r.r and r.z), and after p = z + beta p (the next SpMV reads every p).  Every CTA
+// forms the global sums from the same per-CTA partials in the same order, so all
+// CTAs take the same stop decision.
+template <class T>
+struct PcgArgs {
+  int64_t na;
+  const int32_t *col, *cta_row0, *row_chunk0, *chunk_beg;
+  const T *Sval, *Minv;
+  const double* b;
+  double *x, *r, *z, *p, *Ap;
+  double* part;  // 3 x G x 2 per-CTA partial sums
+  DevScalars* S;
+  double tol;
+  int max_iters;
+};
+
+template <int NT>
+__device__ __forceinline__ void cta_sum2(double v0, double v1, double* out2) {
+  __shared__ double sh[NT / 32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  if (lane == 0) { sh[w][0] = v0; sh[w][1] = v1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int i = 0; i < NT / 32; ++i) { a += sh[i][0]; c += sh[i][1]; }
+    out2[0] = a; out2[1] = c;
+  }
+  __syncthreads();
+}
+
+// sum of the G per-CTA partials (2 values), identical in every CTA; result broadcast in bc
+__device__ __forceinline__ void grid_partials2(const double* part, int G, double* bc) {
+  if (threadIdx.x < 32) {
+    double a = 0, c = 0;
+    for (int g = threadIdx.x; g < G; g += 32) { a += __ldcg(&part[2 * g]); c += __ldcg(&part[2 * g + 1]); }
+    a = warp_sum(a);
+    c = warp_sum(c);
+    if (threadIdx.x == 0) { bc[0] = a; bc[1] = c; }
+  }
+  __syncthreads();
+}
+
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_persistent(PcgArgs<T> a) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double chunk_y[];   // [chunks of this CTA][6]
+  __shared__ double bc[2];
+  __shared__ double cta_out[2];
+  const int G = gridDim.x, c = blockIdx.x;
+  const int r0 = a.cta_row0[c], r1 = a.cta_row0[c + 1];
+  const int q0 = a.row_chunk0[r0], q1 = a.row_chunk0[r1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = NT / 32;
+  double* partA = a.part;
+  double* partB = a.part + 2 * G;
+  double* partC = a.part + 4 * G;
+
+  // ---- init: x = 0, r = b, z = M^-1 r, p = z
+  double v0 = 0, v1 = 0;
+  for (int row = r0 + threadIdx.x; row < r1; row += NT) {
+    double rv[6], zv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { rv[i] = a.b[6 * row + i]; a.x[6 * row + i] = 0; a.r[6 * row + i] = rv[i]; }
+    apply_block(a.Minv + (size_t)row * BS2, rv, zv);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      a.z[6 * row + i] = zv[i];
+      a.p[6 * row + i] = zv[i];
+      v0 += rv[i] * zv[i];
+      v1 += rv[i] * rv[i];
+    }
+  }
+  cta_sum2<NT>(v0, v1, cta_out);
+  if (threadIdx.x == 0) { partC[2 * c] = cta_out[0]; partC[2 * c + 1] = cta_out[1]; }
+  grid.sync();
+  grid_partials2(partC, G, bc);
+  double rz = bc[0];
+  const double bb = bc[1];
+  const double tol2 = a.tol * a.tol * bb;
+  double rr = bb;
+  int it = 0;
+  bool done = !(bb > 0);
+  while (!done) {
+    // ---- A: Ap = S p by chunks, then per row in chunk order; partial p.Ap
+    for (int q = q0 + warp; q < q1; q += NW) {
+      T acc[6] = {0, 0, 0, 0, 0, 0};
+      const int e = a.chunk_beg[q + 1];
+      for (int blk = a.chunk_beg[q] + lane; blk < e; blk += 32) {
+        const T* B = a.Sval + (size_t)blk * BS2;
+        const double* pb = a.p + 6 * (size_t)a.col[blk];
+        T xv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) xv[j] = (T)__ldcg(&pb[j]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[i] += B[i * 6 + j] * xv[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        double y = warp_sum((double)acc[i]);
+        if (lane == 0) chunk_y[6 * (q - q0) + i] = y;
+      }
+    }
+    __syncthreads();
+    double pap = 0;
+    for (int row = r0 + threadIdx.x; row < r1; row += NT) {
+      double y[6] = {0, 0, 0, 0, 0, 0};
+      for (int q = a.row_chunk0[row]; q < a.row_chunk0[row + 1]; ++q)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] += chunk_y[6 * (q - q0) + i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        a.Ap[6 * row + i] = y[i];
+        pap += y[i] * a.p[6 * row + i];
+      }
+    }
+    cta_sum2<NT>(pap, 0.0, cta_out);
+    if (threadIdx.x == 0) { partA[2 * c] = cta_out[0]; partA[2 * c + 1] = 0; }
+    grid.sync();
+    grid_partials2(partA, G, bc);
+    const double alpha = rz / bc[0];
+    // ---- B: x += alpha p, r -= alpha Ap, z = M^-1 r; partial r.r, r.z
+    v0 = 0; v1 = 0;
+    for (int row = r0 + threadIdx.x; row < r1; row += NT) {
+      double rv[6], zv[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        a.x[6 * row + i] += alpha * a.p[6 * row + i];
+        rv[i] = a.r[6 * row + i] - alpha * a.Ap[6 * row + i];
+        a.r[6 * row + i] = rv[i];
+      }
+      apply_block(a.Minv + (size_t)row * BS2, rv, zv);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        a.z[6 * row + i] = zv[i];
+        v0 += rv[i] * rv[i];
+        v1 += rv[i] * zv[i];
+      }
+    }
+    cta_sum2<NT>(v0, v1, cta_out);
+    if (threadIdx.x == 0) { partB[2 * c] = cta_out[0]; partB[2 * c + 1] = cta_out[1]; }
+    grid.sync();
+    grid_partials2(partB, G, bc);
+    rr = bc[0];
+    const double rz_new = bc[1];
+    ++it;
+    if (rr <= tol2 || it >= a.max_iters || !(rr == rr)) break;
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    // ---- C: p = z + beta p
+    for (int k = 6 * r0 + threadIdx.x; k < 6 * r1; k += NT) a.p[k] = a.z[k] + beta * a.p[k];
+    grid.sync();
+  }
+  if (c == 0 && threadIdx.x == 0) {
+    a.S->iters = it;
+    a.S->rr = rr;
+    a.S->bnorm2 = bb;
+    a.S->rz = rz;
+    a.S->done = 1;
+  }
+}
+
+// ============================================================================
+// K7: back-substitution and the predicted decrease
+// ============================================================================
+template <class T>
+struct BackArgs {
+  const int32_t *fslot_off, *slot_ent, *feat_plane_slot;
+  const uint8_t* slot_type;
+  const double *V, *Vinv, *g, *x;
+  const T *W, *H, *G, *C;
+  double* df;
+  int64_t np, nf;
+  DevScalars* S;
+  double* red;
+};
+
+template <class T, int K>
+__device__ void backsub_feature(const BackArgs<T>& a, int64_t f, double& gTd, double& dHd) {
+  double t[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) t[i] = a.g[4 * f + i];
+  const int e0 = a.fslot_off[f], e1 = a.fslot_off[f + 1];
+  T gd = 0, hq = 0;  // sum_e g_e . da  and  sum_e da^T H_e da
+  for (int e = e0; e < e1; ++e) {
+    const double* da = a.x + 6 * (size_t)a.slot_ent[e];
+    T dv[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
+    const T* W = a.W + (size_t)e * SW;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      T s = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
+      t[i] += (double)s;
+    }
+    const T* G = a.G + (size_t)e * SG;
+    const T* H = a.H + (size_t)e * SH;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      gd += G[i] * dv[i];
+      T hv = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) hv += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] * dv[j];
+      hq += dv[i] * hv;
+    }
+  }
+  // delta_f = -V^-1 t
+  double dfv[K];
+  const double* Vi = a.Vinv + 10 * f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    double s = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s += Vi[i <= j ? up_idx(i, j, K) : up_idx(j, i, K)] * t[j];
+    dfv[i] = -s;
+    a.df[4 * f + i] = -s;
+  }
+  // cross terms: 2 sum_e (W_e da) . df  and camera-plane direct blocks
+  T cross = 0, cpl = 0;
+  T dft[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) dft[i] = (T)dfv[i];
+  const int pslot = a.feat_plane_slot[f];
+  T dpl[3] = {0, 0, 0};
+  if (pslot >= 0) {
+    const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
+    dpl[0] = (T)dp[0]; dpl[1] = (T)dp[1]; dpl[2] = (T)dp[2];
+  }
+  for (int e = e0; e < e1; ++e) {
+    const double* da = a.x + 6 * (size_t)a.slot_ent[e];
+    T dv[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
+    const T* W = a.W + (size_t)e * SW;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      T s = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
+      cross += s * dft[i];
+    }
+    if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {
+      const T* Cm = a.C + (size_t)e * SC;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
+    }
+  }
+  // df^T V df and g_f . df
+  const double* Vf = a.V + 10 * f;
+  double vq = 0, gfd = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    gfd += a.g[4 * f + i] * dfv[i];
+#pragma unroll
+    for (int j = 0; j < K; ++j) vq += dfv[i] * Vf[i <= j ? up_idx(i, j, K) : up_idx(j, i, K)] * dfv[j];
+  }
+  gTd = gfd + (double)gd;
+  dHd = vq + 2.0 * (double)cross + (double)hq + 2.0 * (double)cpl;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_backsub(BackArgs<T> a) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v[2] = {0, 0};
+  if (f < a.nf) {
+    if (f < a.np) backsub_feature<T, 3>(a, f, v[0], v[1]);
+    else backsub_feature<T, 4>(a, f, v[0], v[1]);
+  }
+  double tot[2];
+  if (grid_reduce<2>(v, a.red, &a.S->counter[3], tot) && threadIdx.x == 0) {
+    a.S->gTd = tot[0];
+    a.S->dHd = tot[1];
+    a.S->pred = -tot[0] - 0.5 * tot[1];
+  }
+}
+
+// ============================================================================
+// K8: candidate parameters (retractions) and the FP64 cost
+// ============================================================================
+__device__ void so3_exp(const double* w, double* R) {
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double A, B;
+  if (th2 < 1e-12) {
+    A = 1 - th2 / 6;
+    B = 0.5 - th2 / 24;
+  } else {
+    double th = sqrt(th2);
+    A = sin(th) / th;
+    B = (1 - cos(th)) / th2;
+  }
+  double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += K[3 * i + k] * K[3 * k + j];
+      K2[3 * i + j] = s;
+    }
+  for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + A * K[i] + B * K2[i];
+}
+
+__device__ void s2_exp(const double* n, const double* v, double* o) {
+  double th2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double c, s;
+  if (th2 < 1e-12) {
+    c = 1 - th2 / 2;
+    s = 1 - th2 / 6;
+  } else {
+    double th = sqrt(th2);
+    c = cos(th);
+    s = sin(th) / th;
+  }
+  for (int i = 0; i < 3; ++i) o[i] = c * n[i] + s * v[i];
+}
+
+struct CandArgs {
+  const double *cam, *pts, *lin, *pln, *vps, *x, *df;
+  const uint8_t* fixed;
+  double *cam2, *pts2, *lin2, *pln2, *vps2;
+  int64_t nc, np, nl, npl, nv;
+};
+
+__global__ void k_candidate(CandArgs a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n0 = a.nc, n1 = n0 + a.npl, n2 = n1 + a.nv, n3 = n2 + a.np, n4 = n3 + a.nl;
+  if (i >= n4) return;
+  if (i < n0) {
+    const double* c = a.cam + 12 * i;
+    double* o = a.cam2 + 12 * i;
+    for (int k = 0; k < 12; ++k) o[k] = c[k];
+    if (a.fixed[i] == 0x3F) return;
+    const double* dl = a.x + 6 * i;   // held components have zero increments
+    double Rd[9], R[9], Rn[9];
+    so3_exp(dl, Rd);
+    quat_to_R(c, R);
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s) Rn[3 * r + s] = Rd[3 * r] * R[s] + Rd[3 * r + 1] * R[3 + s] + Rd[3 * r + 2] * R[6 + s];
+    // rotation matrix -> quaternion (w >= 0)
+    double q[4];
+    double tr = Rn[0] + Rn[4] + Rn[8];
+    if (tr > 0) {
+      double s = sqrt(tr + 1.0) * 2;
+      q[0] = 0.25 * s; q[1] = (Rn[7] - Rn[5]) / s; q[2] = (Rn[2] - Rn[6]) / s; q[3] = (Rn[3] - Rn[1]) / s;
+    } else if (Rn[0] > Rn[4] && Rn[0] > Rn[8]) {
+      double s = sqrt(1.0 + Rn[0] - Rn[4] - Rn[8]) * 2;
+      q[0] = (Rn[7] - Rn[5]) / s; q[1] = 0.25 * s; q[2] = (Rn[1] + Rn[3]) / s; q[3] = (Rn[2] + Rn[6]) / s;
+    } else if (Rn[4] > Rn[8]) {
+      double s = sqrt(1.0 + Rn[4] - Rn[0] - Rn[8]) * 2;
+      q[0] = (Rn[2] - Rn[6]) / s; q[1] = (Rn[1] + Rn[3]) / s; q[2] = 0.25 * s; q[3] = (Rn[5] + Rn[7]) / s;
+    } else {
+      double s = sqrt(1.0 + Rn[8] - Rn[0] - Rn[4]) * 2;
+      q[0] = (Rn[3] - Rn[1]) / s; q[1] = (Rn[2] + Rn[6]) / s; q[2] = (Rn[5] + Rn[7]) / s; q[3] = 0.25 * s;
+    }
+    double sg = q[0] < 0 ? -1.0 : 1.0;
+    double qn = sg / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int k = 0; k < 4; ++k) o[k] = q[k] * qn;
+    o[4] = c[4] + dl[3]; o[5] = c[5] + dl[4]; o[6] = c[6] + dl[5];
+  } else if (i < n1) {
+    int64_t g = i - n0;
+    const double* P = a.pln + 4 * g;
+    const double* dl = a.x + 6 * i;
+    double b1[3], b2[3], v[3];
+    tangent_basis_d(P, b1, b2);
+    for (int k = 0; k < 3; ++k) v[k] = dl[0] * b1[k] + dl[1] * b2[k];
+    double* o = a.pln2 + 4 * g;
+    s2_exp(P, v, o);
+    o[3] = P[3] + dl[2];
+  } else if (i < n2) {
+    int64_t g = i - n1;
+    const double* V = a.vps + 3 * g;
+    const double* dl = a.x + 6 * i;
+    double b1[3], b2[3], v[3];
+    tangent_basis_d(V, b1, b2);
+    for (int k = 0; k < 3; ++k) v[k] = dl[0] * b1[k] + dl[1] * b2[k];
+    s2_exp(V, v, a.vps2 + 3 * g);
+  } else if (i < n3) {
+    int64_t f = i - n2;
+    for (int k = 0; k < 3; ++k) a.pts2[3 * f + k] = a.pts[3 * f + k] + a.df[4 * f + k];
+  } else {
+    int64_t l = i - n3;
+    const double* L = a.lin + 6 * l;
+    const double* dl = a.df + 4 * (a.np + l);
+    double u1[3], u3[3], r;
+    line_frame<double>(L, L + 3, u1, u3, r);
+    double E[9];
+    so3_exp(dl, E);
+    // U = [u1, d, u3] (columns); U' = U E
+    double U[9] = {u1[0], L[0], u3[0], u1[1], L[1], u3[1], u1[2], L[2], u3[2]};
+    double Un[9];
+    for (int rr = 0; rr < 3; ++rr)
+      for (int s = 0; s < 3; ++s) Un[3 * rr + s] = U[3 * rr] * E[s] + U[3 * rr + 1] * E[3 + s] + U[3 * rr + 2] * E[6 + s];
+    double phi = atan2(1.0, r) + dl[3];
+    double ct = cos(phi) / sin(phi);
+    double* o = a.lin2 + 6 * l;
+    for (int k = 0; k < 3; ++k) {
+      o[k] = Un[3 * k + 1];
+      o[3 + k] = ct * Un[3 * k + 0];
+    }
+  }
+}
+
+struct CostArgs {
+  const int8_t* rkind;
+  const int32_t *rcam, *rfeat, *rgrp;
+  const double *meas, *camD, *grpD, *pts, *lin;
+  int64_t nr, np, npl;
+  LossW loss;
+  DevScalars* S;
+  double* red;
+  int candidate;
+};
+
+__global__ void __launch_bounds__(256) k_cost(CostArgs a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v[2] = {0, 0};
+  if (i < a.nr) {
+    const int kind = a.rkind[i];
+    const int cid = a.rcam[i];
+    const int64_t f = a.rfeat[i];
+    const int gid = a.rgrp[i];
+    const double* meas = a.meas + 4 * i;
+    Cam<double> c;
+    if (cid >= 0) load_cam(a.camD + (size_t)CAM_STRIDE * cid, c);
+    ResJ<double> o;
+    o.valid = false;
+    const double* X = a.pts + 3 * f;
+    const double* L = a.lin + 6 * (f - a.np);
+    int rd = res_dim(kind);
+    switch (kind) {
+      case R_POINT: res_point<double, false>(c, X, meas, o); break;
+      case R_LINE: res_line<double, false>(c, L, meas, o); break;
+      case R_PLANE_POINT: res_plane_point<double, false>(c, X, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
+      case R_PLANE_LINE: res_plane_line<double, false>(c, L, a.grpD + (size_t)GRP_STRIDE * gid, meas, o); break;
+      case R_VP: res_vp<double, false>(L, a.grpD + (size_t)GRP_STRIDE * (a.npl + gid), o); break;
+      case R_P2L: res_p2l<double, false>(c, X, meas, o); break;
+      case R_L2P: res_l2p<double, false>(c, L, meas, o); break;
+    }
+    if (o.valid) {
+      double s = 0;
+      for (int k = 0; k < rd; ++k) s += o.r[k] * o.r[k];
+      double a2 = a.loss.a2[kind];
+      double e = 0.5 * a.loss.w[kind] * a2 * log1p(s / a2);
+      v[0] = e;
+      v[1] = kind == R_VP ? 0.0 : e;
+    }
+  }
+  double tot[2];
+  if (grid_reduce<2>(v, a.red, &a.S->counter[4], tot) && threadIdx.x == 0) {
+    if (a.candidate) { a.S->Enew = tot[0]; a.S->Epxnew = tot[1]; }
+    else { a.S->E = tot[0]; a.S->Epx = tot[1]; }
+  }
+}
+
+// ============================================================================
+// K9: LM decision
+// ============================================================================
+struct DecideArgs {
+  DevScalars* S;
+  double min_gain, lmin, lmax;
+};
+
+__global__ void k_decide(DecideArgs a) {
+  DevScalars* S = a.S;
+  double pred = S->pred;
+  double gain = pred > 0 ? (S->E - S->Enew) / pred : -INFINITY;
+  bool ok = isfinite(S->Enew) && gain > a.min_gain;
+  S->gain = gain;
+  S->accepted = ok ? 1 : 0;
+  if (ok) {
+    double t = 2.0 * gain - 1.0;
+    double fct = fmax(1.0 / 3.0, 1.0 - t * t * t);
+    S->lambda = fmin(fmax(S->lambda * fct, a.lmin), a.lmax);
+    S->nu = 2.0;
+  } else {
+    S->lambda = fmin(S->lambda * S->nu, a.lmax);
+    S->nu *= 2.0;
+  }
+}
+
+// ============================================================================
+// launchers
+// ============================================================================
+static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+static LossW make_loss(const ba_options& o) {
+  LossW L;
+  double w[7] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire};
+  for (int k = 0; k < 7; ++k) {
+    L.w[k] = w[k];
+    double s = (k == R_VP) ? o.cauchy_vp : o.cauchy_px;
+    L.a2[k] = s * s;
+  }
+  return L;
+}
+
+
+template <class T>
+void launch_prepare(Problem& P, bool candidate_only) {
+  const Dims& d = P.d;
+  auto& cs = P.ps[candidate_only ? 1 - P.cur : P.cur];
+  T* camW = candidate_only ? nullptr : (T*)P.camT;
+  T* grpW = candidate_only ? nullptr : (T*)P.grpT;
+  if (sizeof(T) == sizeof(double)) { camW = nullptr; grpW = nullptr; }
+  if (d.nc) { ++P.launches; k_derive_cams<T><<<nblk(d.nc, 128), 128, 0, P.stream>>>(d.nc, cs.cam, cs.camD, camW); }
+  if (d.npl + d.nv) { ++P.launches; k_derive_groups<T><<<nblk(d.npl + d.nv, 128), 128, 0, P.stream>>>(d.npl, d.nv, cs.pln, cs.vps, cs.grpD, grpW); }
+  if (!candidate_only && sizeof(T) == sizeof(float)) {
+    if (d.np) { ++P.launches; k_convert<<<nblk(3 * d.np, 256), 256, 0, P.stream>>>(3 * d.np, cs.pts, (float*)P.ptsT); }
+    if (d.nl) { ++P.launches; k_convert<<<nblk(6 * d.nl, 256), 256, 0, P.stream>>>(6 * d.nl, cs.lin, (float*)P.linT); }
+  }
+}
+
+template <class T>
+void launch_linearize(Problem& P) {
+  const Dims& d = P.d;
+  auto& cs = P.ps[P.cur];
+  LinArgs<T> a;
+  a.rkind = P.rkind; a.cam_mask = P.cam_fixed; a.rcam = P.rcam; a.rgrp = P.rgrp; a.rslot_c = P.rslot_c; a.rslot_g = P.rslot_g;
+  a.fres_off = P.fres_off; a.feat_plane_slot = P.feat_plane_slot;
+  const bool dbl = sizeof(T) == sizeof(double);
+  a.meas = dbl ? (const T*)P.meas64 : (const T*)P.measT;
+  a.cam = dbl ? (const T*)cs.camD : (const T*)P.camT;
+  a.grp = dbl ? (const T*)cs.grpD : (const T*)P.grpT;
+  a.pts = dbl ? (const T*)cs.pts : (const T*)P.ptsT;
+  a.lin = dbl ? (const T*)cs.lin : (const T*)P.linT;
+  a.npl = d.npl; a.np = d.np;
+  a.W = (T*)P.slotW; a.H = (T*)P.slotH; a.G = (T*)P.slotG; a.C = (T*)P.slotC;
+  a.V = P.featV; a.g = P.featg;
+  a.loss = make_loss(P.opt);
+  if (d.np) { ++P.launches; k_linearize<T, 3><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
+  if (d.nl) { ++P.launches; k_linearize<T, 4><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
+}
+
+template <class T>
+void launch_invert(Problem& P, double lambda) {
+  const Dims& d = P.d;
+  InvArgs<T> a;
+  a.fslot_off = P.fslot_off; a.V = P.featV; a.g = P.featg; a.W = (const T*)P.slotW; a.G = (const T*)P.slotG;
+  a.Vinv = P.featVinv; a.z = P.featz; a.Y = (T*)P.slotY; a.B = (T*)P.slotB;
+  a.np = d.np; a.nf = d.nf; a.lambda = lambda; a.S = P.S;
+  if (d.nf) { ++P.launches; k_invert<T><<<nblk(d.nf, 128), 128, 0, P.stream>>>(a); }
+}
+
+template <class T>
+void launch_schur(Problem& P, double lambda) {
+  const Dims& d = P.d;
+  SchurArgs<T> a;
+  a.pair_a = P.pair_a; a.pair_b = P.pair_b; a.wi_se = P.wi_start; a.slot_feat = P.slot_feat; a.slot_type = P.slot_type;
+  a.W = (const T*)P.slotW; a.Y = (const T*)P.slotY; a.H = (const T*)P.slotH; a.B = (const T*)P.slotB;
+  a.C = (const T*)P.slotC; a.part = (T*)P.part; a.np = d.np; a.nwi = d.nwi;
+  if (d.nwi) { ++P.launches; k_schur_items<T><<<nblk(d.nwi, 128), 128, 0, P.stream>>>(a); }
+  if (P.ev[3]) cudaEventRecord(P.ev[3], P.stream);
+  BlockArgs<T> b;
+  b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.up_wi = P.up_wi; b.col = P.col;
+  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.part = (const T*)P.part; b.Sval = (T*)P.Sval;
+  b.b = P.bvec; b.Dg = P.Dg; b.nbu = d.nbu; b.nc = d.nc; b.lambda = lambda;
+  if (d.nbu) { ++P.launches; k_schur_blocks<T><<<nblk(d.nbu, 128), 128, 0, P.stream>>>(b); }
+}
+
+template <class T>
+void launch_precond(Problem& P) {
+  const Dims& d = P.d;
+  if (d.na) { ++P.launches; k_precond<T><<<nblk(d.na, 128), 128, 0, P.stream>>>(d.na, P.row_ptr, P.col, (const T*)P.Sval, (T*)P.Minv, P.S); }
+}
+
+constexpr int PCG_THREADS = 512;
+
+template <class T>
+int pcg_blocks_per_sm(size_t smem) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_persistent<T, PCG_THREADS>, PCG_THREADS, smem);
+  return nb;
+}
+
+template <class T>
+void pcg_allow_smem(size_t smem) {
+  cudaFuncSetAttribute(k_pcg_persistent<T, PCG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <class T>
+void launch_pcg(Problem& P) {
+  const Dims& d = P.d;
+  PcgArgs<T> a;
+  a.na = d.na; a.col = P.col; a.cta_row0 = P.cta_row0; a.row_chunk0 = P.row_chunk0; a.chunk_beg = P.chunk_beg;
+  a.Sval = (const T*)P.Sval; a.Minv = (const T*)P.Minv; a.b = P.bvec;
+  a.x = P.x; a.r = P.r; a.z = P.z; a.p = P.p; a.Ap = P.Ap; a.part = P.red; a.S = P.S;
+  a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
+  void* args[] = {&a};
+  ++P.launches;
+  P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, PCG_THREADS>, dim3(P.pcg_grid),
+                                          dim3(PCG_THREADS), args, P.pcg_smem, P.stream);
+}
+
+template <class T>
+void launch_backsub(Problem& P) {
+  const Dims& d = P.d;
+  BackArgs<T> a;
+  a.fslot_off = P.fslot_off; a.slot_ent = P.slot_ent; a.feat_plane_slot = P.feat_plane_slot; a.slot_type = P.slot_type;
+  a.V = P.featV; a.Vinv = P.featVinv; a.g = P.featg; a.x = P.x;
+  a.W = (const T*)P.slotW; a.H = (const T*)P.slotH; a.G = (const T*)P.slotG; a.C = (const T*)P.slotC;
+  a.df = P.dfeat; a.np = d.np; a.nf = d.nf; a.S = P.S; a.red = P.red;
+  ++P.launches;
+  k_backsub<T><<<nblk(d.nf > 0 ? d.nf : 1, 128), 128, 0, P.stream>>>(a);
+}
+
+void launch_candidate(Problem& P) {
+  const Dims& d = P.d;
+  auto& c = P.ps[P.cur];
+  auto& n = P.ps[1 - P.cur];
+  CandArgs a;
+  a.cam = c.cam; a.pts = c.pts; a.lin = c.lin; a.pln = c.pln; a.vps = c.vps; a.x = P.x; a.df = P.dfeat;
+  a.fixed = P.cam_fixed; a.cam2 = n.cam; a.pts2 = n.pts; a.lin2 = n.lin; a.pln2 = n.pln; a.vps2 = n.vps;
+  a.nc = d.nc; a.np = d.np; a.nl = d.nl; a.npl = d.npl; a.nv = d.nv;
+  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl;
+  if (tot) { ++P.launches; k_candidate<<<nblk(tot, 128), 128, 0, P.stream>>>(a); }
+}
+
+void launch_cost(Problem& P, bool candidate) {
+  const Dims& d = P.d;
+  auto& s = P.ps[candidate ? 1 - P.cur : P.cur];
+  CostArgs a;
+  a.rkind = P.rkind; a.rcam = P.rcam; a.rfeat = P.rfeat; a.rgrp = P.rgrp; a.meas = P.meas64;
+  a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin;
+  a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
+  a.candidate = candidate ? 1 : 0;
+  ++P.launches;
+  k_cost<<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
+}
+
+void launch_decide(Problem& P) {
+  DecideArgs a{P.S, P.opt.min_gain, P.opt.lambda_min, P.opt.lambda_max};
+  ++P.launches;
+  k_decide<<<1, 1, 0, P.stream>>>(a);
+}
+
+#define INST(T)                                         \
+  template void launch_prepare<T>(Problem&, bool);      \
+  template void launch_linearize<T>(Problem&);          \
+  template void launch_invert<T>(Problem&, double);     \
+  template void launch_schur<T>(Problem&, double);      \
+  template void launch_precond<T>(Problem&);            \
+  template void launch_pcg<T>(Problem&);                \
+  template int pcg_blocks_per_sm<T>(size_t);            \
+  template void pcg_allow_smem<T>(size_t);              \
+  template void launch_backsub<T>(Problem&);
+INST(double)
+INST(float)
+
+}  // namespace ba

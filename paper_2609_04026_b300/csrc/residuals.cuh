@@ -1,0 +1,528 @@
+// Residuals and analytic Jacobians of the seven residual kinds of holistic BA.
+//
+// Every function is templated on the arithmetic type T (double for the FP64
+// path, float for the mixed path) and on JAC (false: value only, used by the
+// FP64 cost pass).  Jacobians are taken with respect to the minimal local
+// increments of each parameter block:
+//   camera pose  R <- Exp(dw) R, t <- t + dt                       (6)
+//   point        X <- X + dX                                        (3)
+//   line         orthonormal (Bartoli-Sturm) update of Pluecker (d, m), |d| = 1:
+//                U = [m/|m|, d, u1 x d] <- U Exp(dl0..2), phi <- phi + dl3,
+//                d = u2, m = cot(phi) u1                            (4)
+//   plane (n,w)  n <- Exp_n(b1 dg0 + b2 dg1) on S^2, w <- w + dg2    (3)
+//   VP v         v <- Exp_v(b1 dg0 + b2 dg1)                        (2)
+// with (b1, b2) the tangent basis: a = e_x unless |n_x| >= 0.9 (then e_y),
+// b1 = unit(a - (a.n) n), b2 = n x b1.
+//
+// Residuals (Section 3 of the paper):
+//   R1 point reprojection       Eq. 1 / Eq. 4, radial distortion (f, k1, k2)
+//   R2 line reprojection        Eq. 4, rho = perpendicular displacement vectors
+//   R3 plane-induced point      Eq. 7, plane projection of Appendix B
+//   R4 plane-induced line       Eq. 8, Pluecker plane projection of Appendix B
+//   R5 VP angular               Eq. 6 written as the 3-vector d x v
+//   R6 wireframe point->line    Eq. 11 (pinhole pixels)
+//   R7 wireframe line->point    Eq. 12 (pinhole pixels)
+// Lines and the wireframe terms live in undistorted pixel coordinates; only R1
+// and R3 use k1, k2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ba {
+
+enum ResKind : int { R_POINT = 0, R_LINE = 1, R_PLANE_POINT = 2, R_PLANE_LINE = 3, R_VP = 4, R_P2L = 5, R_L2P = 6 };
+
+__host__ __device__ constexpr int res_dim(int k) {
+  return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3 : 1;
+}
+
+// per-camera data precomputed from the FP64 master parameters each time they change
+// layout (stride CAM_STRIDE): R row-major (9), t (3), f, k1, k2, ppx, ppy
+constexpr int CAM_STRIDE = 20;
+// per-plane data: n (3), w, b1 (3), b2 (3) ; per-VP data: v (3), 0, b1 (3), b2 (3)
+constexpr int GRP_STRIDE = 12;
+
+template <class T>
+struct Cam {
+  T R[9], t[3], f, k1, k2, px, py;
+};
+
+template <class T>
+__device__ __forceinline__ void load_cam(const T* __restrict__ c, Cam<T>& o) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) o.R[i] = c[i];
+  o.t[0] = c[9]; o.t[1] = c[10]; o.t[2] = c[11];
+  o.f = c[12]; o.k1 = c[13]; o.k2 = c[14]; o.px = c[15]; o.py = c[16];
+}
+
+template <class T> __device__ __forceinline__ T dot3(const T* a, const T* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <class T> __device__ __forceinline__ void cross3(const T* a, const T* b, T* o) {
+  T x = a[1] * b[2] - a[2] * b[1], y = a[2] * b[0] - a[0] * b[2], z = a[0] * b[1] - a[1] * b[0];
+  o[0] = x; o[1] = y; o[2] = z;
+}
+template <class T> __device__ __forceinline__ void matvec3(const T* R, const T* v, T* o) {
+  T x = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+  T y = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+  T z = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+  o[0] = x; o[1] = y; o[2] = z;
+}
+template <class T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
+template <class T> __device__ __forceinline__ T sqrt_t(T x);
+template <> __device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
+
+// Output of one residual: r (rd values) and Jacobian rows w.r.t. camera (6),
+// feature (3 or 4) and group (3; VP uses the first 2).
+template <class T>
+struct ResJ {
+  T r[4];
+  T Jc[4][6];
+  T Jf[4][4];
+  T Jg[4][3];
+  bool valid;
+};
+
+// ---------------------------------------------------------------- camera / point pieces
+// rotation columns of the pose Jacobian for one row g of d(res)/d(x_cam):
+//   d x_cam / d dw = -[R X]x  =>  row contribution  (R X) x g ; translation part = g
+template <class T>
+__device__ __forceinline__ void pose_row_point(const T* p, const T* g, T* out6) {
+  T c[3];
+  cross3(p, g, c);
+  out6[0] = c[0]; out6[1] = c[1]; out6[2] = c[2];
+  out6[3] = g[0]; out6[4] = g[1]; out6[5] = g[2];
+}
+
+// distorted projection of x_cam: pi = pp + f s (u, v); Jxc = d pi / d x_cam (2x3)
+template <class T, bool JAC>
+__device__ __forceinline__ void project_dist(const Cam<T>& c, const T* xc, T* pi, T Jxc[2][3]) {
+  T iz = T(1) / xc[2];
+  T u = xc[0] * iz, v = xc[1] * iz;
+  T r2 = u * u + v * v;
+  T s = T(1) + c.k1 * r2 + c.k2 * r2 * r2;
+  pi[0] = c.px + c.f * s * u;
+  pi[1] = c.py + c.f * s * v;
+  if (JAC) {
+    T ds = T(2) * (c.k1 + T(2) * c.k2 * r2);
+    T a00 = c.f * (s + ds * u * u), a01 = c.f * ds * u * v, a11 = c.f * (s + ds * v * v);
+    // d(u,v)/d x_cam = iz [[1,0,-u],[0,1,-v]]
+    Jxc[0][0] = a00 * iz; Jxc[0][1] = a01 * iz; Jxc[0][2] = -(a00 * u + a01 * v) * iz;
+    Jxc[1][0] = a01 * iz; Jxc[1][1] = a11 * iz; Jxc[1][2] = -(a01 * u + a11 * v) * iz;
+  }
+}
+
+template <class T, bool JAC>
+__device__ __forceinline__ void project_pin(const Cam<T>& c, const T* xc, T* pi, T Jxc[2][3]) {
+  T iz = T(1) / xc[2];
+  T u = xc[0] * iz, v = xc[1] * iz;
+  pi[0] = c.px + c.f * u;
+  pi[1] = c.py + c.f * v;
+  if (JAC) {
+    T fz = c.f * iz;
+    Jxc[0][0] = fz; Jxc[0][1] = 0; Jxc[0][2] = -fz * u;
+    Jxc[1][0] = 0; Jxc[1][1] = fz; Jxc[1][2] = -fz * v;
+  }
+}
+
+// ---------------------------------------------------------------- line pieces
+// orthonormal frame of a Pluecker line with |d| = 1: u1 = m/|m| (or the tangent
+// basis vector b1(d) when |m| ~ 0), u3 = u1 x d, r = |m|
+template <class T>
+__device__ __forceinline__ void tangent_b1(const T* n, T* b1) {
+  T a[3] = {T(0), T(0), T(0)};
+  if (fabs((double)n[0]) < 0.9) a[0] = T(1); else a[1] = T(1);
+  T an = dot3(a, n);
+  b1[0] = a[0] - an * n[0]; b1[1] = a[1] - an * n[1]; b1[2] = a[2] - an * n[2];
+  T s = rsqrt_t(dot3(b1, b1));
+  b1[0] *= s; b1[1] *= s; b1[2] *= s;
+}
+
+template <class T>
+__device__ __forceinline__ void line_frame(const T* d, const T* m, T* u1, T* u3, T& r) {
+  r = sqrt_t(dot3(m, m));
+  if ((double)r < 1e-12) {
+    tangent_b1(d, u1);
+  } else {
+    T ir = T(1) / r;
+    u1[0] = m[0] * ir; u1[1] = m[1] * ir; u1[2] = m[2] * ir;
+  }
+  cross3(u1, d, u3);
+}
+
+// partial derivatives of (d, m) w.r.t. the 4 line increments, as directions:
+//   dd/dl = [u3, 0, -u1, 0],  dm/dl = [0, -r u3, r u2, -(1 + r^2) u1]   (u2 = d)
+template <class T>
+__device__ __forceinline__ void line_dirs(const T* d, const T* u1, const T* u3, T r, T dd[4][3], T dm[4][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dd[0][i] = u3[i]; dd[1][i] = 0; dd[2][i] = -u1[i]; dd[3][i] = 0;
+    dm[0][i] = 0; dm[1][i] = -r * u3[i]; dm[2][i] = r * d[i]; dm[3][i] = -(T(1) + r * r) * u1[i];
+  }
+}
+
+// camera-frame moment m_c = R m + t x (R d), d_c = R d; image line l = K_l m_c
+template <class T>
+__device__ __forceinline__ void line_to_cam(const Cam<T>& c, const T* d, const T* m, T* dc, T* Rm, T* mc) {
+  matvec3(c.R, d, dc);
+  matvec3(c.R, m, Rm);
+  T tx[3];
+  cross3(c.t, dc, tx);
+  mc[0] = Rm[0] + tx[0]; mc[1] = Rm[1] + tx[1]; mc[2] = Rm[2] + tx[2];
+}
+
+template <class T>
+__device__ __forceinline__ void image_line(const Cam<T>& c, const T* mc, T* l) {
+  l[0] = mc[0]; l[1] = mc[1]; l[2] = c.f * mc[2] - c.px * mc[0] - c.py * mc[1];
+}
+
+// rho(l, seg) (Eq. 4): per endpoint e, v_e = (l . [e;1]) (l0,l1) / |(l0,l1)|^2.
+// J (4x3) = d rho / d l, then G = J K_l (chain to m_c).  Returns |(l0,l1)|^2.
+template <class T, bool JAC>
+__device__ __forceinline__ T rho_line(const Cam<T>& c, const T* l, const T* seg, T* r4, T G[4][3]) {
+  T A2 = l[0] * l[0] + l[1] * l[1];
+  T iA = T(1) / A2;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    T ex = seg[2 * e], ey = seg[2 * e + 1];
+    T q = l[0] * ex + l[1] * ey + l[2];
+    T s = q * iA;
+    r4[2 * e] = s * l[0];
+    r4[2 * e + 1] = s * l[1];
+    if (JAC) {
+      T k = T(2) * q * iA * iA;
+      T J[2][3];
+      // d v / d l0 = (ex a + q e0)/A2 - 2 q l0 a / A2^2, similarly l1; d v / d l2 = a / A2
+      J[0][0] = (ex * l[0] + q) * iA - k * l[0] * l[0];
+      J[1][0] = (ex * l[1]) * iA - k * l[0] * l[1];
+      J[0][1] = (ey * l[0]) * iA - k * l[1] * l[0];
+      J[1][1] = (ey * l[1] + q) * iA - k * l[1] * l[1];
+      J[0][2] = l[0] * iA;
+      J[1][2] = l[1] * iA;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        G[2 * e + i][0] = J[i][0] - c.px * J[i][2];
+        G[2 * e + i][1] = J[i][1] - c.py * J[i][2];
+        G[2 * e + i][2] = c.f * J[i][2];
+      }
+    }
+  }
+  return A2;
+}
+
+// for one row g (3) of d(res)/d(m_c): pose columns of a line with camera-frame
+// direction dc and rotated moment Rm:  rot = Rm x g + dc x (g x t),  trans = dc x g
+template <class T>
+__device__ __forceinline__ void pose_row_line(const Cam<T>& c, const T* dc, const T* Rm, const T* g, T* out6) {
+  T a[3], gt[3], b[3], tr[3];
+  cross3(Rm, g, a);
+  cross3(g, c.t, gt);
+  cross3(dc, gt, b);
+  cross3(dc, g, tr);
+  out6[0] = a[0] + b[0]; out6[1] = a[1] + b[1]; out6[2] = a[2] + b[2];
+  out6[3] = tr[0]; out6[4] = tr[1]; out6[5] = tr[2];
+}
+
+// d m_c along a perturbation (zeta of d, mu of m):  t x (R zeta) + R mu
+template <class T>
+__device__ __forceinline__ void dmc_dir(const Cam<T>& c, const T* zeta, const T* mu, T* o) {
+  T Rz[3], Rmu[3], tx[3];
+  matvec3(c.R, zeta, Rz);
+  matvec3(c.R, mu, Rmu);
+  cross3(c.t, Rz, tx);
+  o[0] = tx[0] + Rmu[0]; o[1] = tx[1] + Rmu[1]; o[2] = tx[2] + Rmu[2];
+}
+
+// ---------------------------------------------------------------- plane projections (Appendix B)
+template <class T>
+__device__ __forceinline__ void plane_proj_point(const T* n, T w, const T* X, T* Xp, T& cdist) {
+  cdist = dot3(n, X) + w;
+  Xp[0] = X[0] - cdist * n[0]; Xp[1] = X[1] - cdist * n[1]; Xp[2] = X[2] - cdist * n[2];
+}
+
+// d' = d - (d.n) n ; m' = (1 - a^2/|d|^2) m + (a g/|d|^2) d + (w - dl/|d|^2)(d x n)
+template <class T>
+__device__ __forceinline__ void plane_proj_line(const T* n, T w, const T* d, const T* m, T* dp, T* mp) {
+  T a = dot3(d, n), g = dot3(m, n), dd = dot3(d, d);
+  T dxn[3];
+  cross3(d, n, dxn);
+  T dl = dot3(dxn, m);
+  T idd = T(1) / dd;
+  T A = T(1) - a * a * idd, B = a * g * idd, C = w - dl * idd;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dp[i] = d[i] - a * n[i];
+    mp[i] = A * m[i] + B * d[i] + C * dxn[i];
+  }
+}
+
+// directional derivative of (d', m') for perturbations zeta (of d), mu (of m),
+// eta (of n) and dw (of w)
+template <class T>
+__device__ __forceinline__ void plane_proj_line_dir(const T* n, T w, const T* d, const T* m, const T* zeta,
+                                                    const T* mu, const T* eta, T dw, T* ddp, T* dmp) {
+  T a = dot3(d, n), g = dot3(m, n), dd = dot3(d, d);
+  T dxn[3];
+  cross3(d, n, dxn);
+  T dl = dot3(dxn, m);
+  T idd = T(1) / dd;
+  T A = T(1) - a * a * idd, B = a * g * idd, C = w - dl * idd;
+  // first-order changes of the scalars
+  T da = dot3(zeta, n) + dot3(d, eta);
+  T dg = dot3(mu, n) + dot3(m, eta);
+  T zxn[3], dxe[3];
+  cross3(zeta, n, zxn);
+  cross3(d, eta, dxe);
+  T ddxn[3] = {zxn[0] + dxe[0], zxn[1] + dxe[1], zxn[2] + dxe[2]};
+  T ddl = dot3(ddxn, m) + dot3(dxn, mu);
+  T ddd = T(2) * dot3(d, zeta);
+  T dA = -(T(2) * a * da) * idd + a * a * ddd * idd * idd;
+  T dB = (da * g + a * dg) * idd - a * g * ddd * idd * idd;
+  T dC = dw - ddl * idd + dl * ddd * idd * idd;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ddp[i] = zeta[i] - da * n[i] - a * eta[i];
+    dmp[i] = dA * m[i] + A * mu[i] + dB * d[i] + B * zeta[i] + dC * dxn[i] + C * ddxn[i];
+  }
+}
+
+// ---------------------------------------------------------------- the seven residuals
+// R1: pi(C, X) - x_ij
+template <class T, bool JAC>
+__device__ void res_point(const Cam<T>& c, const T* X, const T* meas, ResJ<T>& o) {
+  T p[3], xc[3], pi[2], J[2][3];
+  matvec3(c.R, X, p);
+  xc[0] = p[0] + c.t[0]; xc[1] = p[1] + c.t[1]; xc[2] = p[2] + c.t[2];
+  o.valid = (double)xc[2] > 1e-6;
+  if (!o.valid) return;
+  project_dist<T, JAC>(c, xc, pi, J);
+  o.r[0] = pi[0] - meas[0];
+  o.r[1] = pi[1] - meas[1];
+  if (JAC) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      pose_row_point(p, J[i], o.Jc[i]);
+      // d/dX = J R
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o.Jf[i][k] = J[i][0] * c.R[k] + J[i][1] * c.R[3 + k] + J[i][2] * c.R[6 + k];
+    }
+  }
+}
+
+// R2: rho(pi_l(C, L), segment)
+template <class T, bool JAC>
+__device__ void res_line(const Cam<T>& c, const T* L, const T* seg, ResJ<T>& o) {
+  T dc[3], Rm[3], mc[3], l[3], G[4][3];
+  line_to_cam(c, L, L + 3, dc, Rm, mc);
+  image_line(c, mc, l);
+  T A2 = rho_line<T, JAC>(c, l, seg, o.r, G);
+  o.valid = (double)A2 > 1e-24;
+  if (!JAC || !o.valid) return;
+  T u1[3], u3[3], r;
+  line_frame(L, L + 3, u1, u3, r);
+  T ddir[4][3], mdir[4][3], dmc[4][3];
+  line_dirs(L, u1, u3, r, ddir, mdir);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dmc_dir(c, ddir[k], mdir[k], dmc[k]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    pose_row_line(c, dc, Rm, G[i], o.Jc[i]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o.Jf[i][k] = dot3(G[i], dmc[k]);
+  }
+}
+
+// R3: pi(C, X) - pi(C, Proj_plane(X))  (Eq. 7)
+template <class T, bool JAC>
+__device__ void res_plane_point(const Cam<T>& c, const T* X, const T* P, ResJ<T>& o) {
+  const T* n = P;
+  T w = P[3];
+  T Xp[3], cd;
+  plane_proj_point(n, w, X, Xp, cd);
+  T p1[3], p2[3], x1[3], x2[3], pi1[2], pi2[2], J1[2][3], J2[2][3];
+  matvec3(c.R, X, p1);
+  matvec3(c.R, Xp, p2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { x1[i] = p1[i] + c.t[i]; x2[i] = p2[i] + c.t[i]; }
+  o.valid = (double)x1[2] > 1e-6 && (double)x2[2] > 1e-6;
+  if (!o.valid) return;
+  project_dist<T, JAC>(c, x1, pi1, J1);
+  project_dist<T, JAC>(c, x2, pi2, J2);
+  o.r[0] = pi1[0] - pi2[0];
+  o.r[1] = pi1[1] - pi2[1];
+  if (JAC) {
+    const T* b1 = P + 4;
+    const T* b2 = P + 7;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      T a6[6], b6[6];
+      pose_row_point(p1, J1[i], a6);
+      pose_row_point(p2, J2[i], b6);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) o.Jc[i][k] = a6[k] - b6[k];
+      // g1 = J1 R, g2 = J2 R  (rows as 3-vectors in world frame)
+      T g1[3], g2[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        g1[k] = J1[i][0] * c.R[k] + J1[i][1] * c.R[3 + k] + J1[i][2] * c.R[6 + k];
+        g2[k] = J2[i][0] * c.R[k] + J2[i][1] * c.R[3 + k] + J2[i][2] * c.R[6 + k];
+      }
+      // d Xp / d X = I - n n^T
+      T g2n = dot3(g2, n);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o.Jf[i][k] = g1[k] - (g2[k] - g2n * n[k]);
+      // d Xp along eta (of n) = -((X.eta) n + cd eta);  along w: -n
+      T gX = dot3(g2, X);
+      (void)gX;
+      T e1 = dot3(X, b1), e2 = dot3(X, b2);
+      o.Jg[i][0] = (e1 * g2n + cd * dot3(g2, b1));
+      o.Jg[i][1] = (e2 * g2n + cd * dot3(g2, b2));
+      o.Jg[i][2] = g2n;
+    }
+  }
+}
+
+// R4: rho(pi_l(C, L)) - rho(pi_l(C, Proj_plane(L)))  (Eq. 8)
+template <class T, bool JAC>
+__device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T* seg, ResJ<T>& o) {
+  const T* n = P;
+  T w = P[3];
+  const T* d = L;
+  const T* m = L + 3;
+  T dp[3], mp[3];
+  plane_proj_line(n, w, d, m, dp, mp);
+  T dc1[3], Rm1[3], mc1[3], l1[3], G1[4][3], r1[4];
+  T dc2[3], Rm2[3], mc2[3], l2[3], G2[4][3], r2[4];
+  line_to_cam(c, d, m, dc1, Rm1, mc1);
+  line_to_cam(c, dp, mp, dc2, Rm2, mc2);
+  image_line(c, mc1, l1);
+  image_line(c, mc2, l2);
+  T A1 = rho_line<T, JAC>(c, l1, seg, r1, G1);
+  T A2 = rho_line<T, JAC>(c, l2, seg, r2, G2);
+  o.valid = (double)A1 > 1e-24 && (double)A2 > 1e-24;
+  if (!o.valid) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o.r[i] = r1[i] - r2[i];
+  if (!JAC) return;
+  T u1[3], u3[3], r;
+  line_frame(d, m, u1, u3, r);
+  T ddir[4][3], mdir[4][3], dmc1[4][3], dmc2[4][3];
+  line_dirs(d, u1, u3, r, ddir, mdir);
+  const T zero3[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    dmc_dir(c, ddir[k], mdir[k], dmc1[k]);
+    T ddp[3], dmp[3];
+    plane_proj_line_dir(n, w, d, m, ddir[k], mdir[k], zero3, T(0), ddp, dmp);
+    dmc_dir(c, ddp, dmp, dmc2[k]);
+  }
+  T dmcg[3][3];
+  {
+    const T* b1 = P + 4;
+    const T* b2 = P + 7;
+    T ddp[3], dmp[3];
+    plane_proj_line_dir(n, w, d, m, zero3, zero3, b1, T(0), ddp, dmp);
+    dmc_dir(c, ddp, dmp, dmcg[0]);
+    plane_proj_line_dir(n, w, d, m, zero3, zero3, b2, T(0), ddp, dmp);
+    dmc_dir(c, ddp, dmp, dmcg[1]);
+    plane_proj_line_dir(n, w, d, m, zero3, zero3, zero3, T(1), ddp, dmp);
+    dmc_dir(c, ddp, dmp, dmcg[2]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T a6[6], b6[6];
+    pose_row_line(c, dc1, Rm1, G1[i], a6);
+    pose_row_line(c, dc2, Rm2, G2[i], b6);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.Jc[i][k] = a6[k] - b6[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o.Jf[i][k] = dot3(G1[i], dmc1[k]) - dot3(G2[i], dmc2[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o.Jg[i][k] = -dot3(G2[i], dmcg[k]);
+  }
+}
+
+// R5: d x v (Eq. 6 as a 3-vector; |d| = 1)
+template <class T, bool JAC>
+__device__ void res_vp(const T* L, const T* V, ResJ<T>& o) {
+  const T* d = L;
+  T dn = rsqrt_t(dot3(d, d));
+  T dh[3] = {d[0] * dn, d[1] * dn, d[2] * dn};
+  const T* v = V;
+  cross3(dh, v, o.r);
+  o.valid = true;
+  if (!JAC) return;
+  T u1[3], u3[3], r;
+  line_frame(L, L + 3, u1, u3, r);
+  // d(d x v)/d d = -[v]x ; increments of d: [u3, 0, -u1, 0] (all orthogonal to d)
+  T c0[3], c2[3];
+  cross3(u3, v, c0);
+  cross3(u1, v, c2);
+  const T* b1 = V + 4;
+  const T* b2 = V + 7;
+  T g0[3], g1[3];
+  cross3(dh, b1, g0);
+  cross3(dh, b2, g1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    o.Jf[i][0] = c0[i] * dn; o.Jf[i][1] = 0; o.Jf[i][2] = -c2[i] * dn; o.Jf[i][3] = 0;
+    o.Jg[i][0] = g0[i]; o.Jg[i][1] = g1[i]; o.Jg[i][2] = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.Jc[i][k] = 0;
+  }
+}
+
+// R6: lhat . [pi_pinhole(C, X); 1], lhat = e1 x e2 scaled to |lhat_12| = 1 (Eq. 11)
+template <class T, bool JAC>
+__device__ void res_p2l(const Cam<T>& c, const T* X, const T* seg, ResJ<T>& o) {
+  T e1[3] = {seg[0], seg[1], T(1)}, e2[3] = {seg[2], seg[3], T(1)}, lh[3];
+  cross3(e1, e2, lh);
+  T s = rsqrt_t(lh[0] * lh[0] + lh[1] * lh[1]);
+  lh[0] *= s; lh[1] *= s; lh[2] *= s;
+  T p[3], xc[3], pi[2], J[2][3];
+  matvec3(c.R, X, p);
+  xc[0] = p[0] + c.t[0]; xc[1] = p[1] + c.t[1]; xc[2] = p[2] + c.t[2];
+  o.valid = (double)xc[2] > 1e-6;
+  if (!o.valid) return;
+  project_pin<T, JAC>(c, xc, pi, J);
+  o.r[0] = lh[0] * pi[0] + lh[1] * pi[1] + lh[2];
+  if (JAC) {
+    T g[3] = {lh[0] * J[0][0] + lh[1] * J[1][0], lh[0] * J[0][1] + lh[1] * J[1][1], lh[0] * J[0][2] + lh[1] * J[1][2]};
+    pose_row_point(p, g, o.Jc[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o.Jf[0][k] = g[0] * c.R[k] + g[1] * c.R[3 + k] + g[2] * c.R[6 + k];
+  }
+}
+
+// R7: (l . [x;1]) / |l_12| with l = pi_l(C, L) (Eq. 12)
+template <class T, bool JAC>
+__device__ void res_l2p(const Cam<T>& c, const T* L, const T* x, ResJ<T>& o) {
+  T dc[3], Rm[3], mc[3], l[3];
+  line_to_cam(c, L, L + 3, dc, Rm, mc);
+  image_line(c, mc, l);
+  T A2 = l[0] * l[0] + l[1] * l[1];
+  o.valid = (double)A2 > 1e-24;
+  if (!o.valid) return;
+  T in = rsqrt_t(A2);
+  T q = l[0] * x[0] + l[1] * x[1] + l[2];
+  o.r[0] = q * in;
+  if (!JAC) return;
+  // d r / d l = [x0, x1, 1]/n - q (l0, l1, 0)/n^3, then G = (d r / d l) K_l
+  T in3 = in * in * in;
+  T h0 = x[0] * in - q * l[0] * in3, h1 = x[1] * in - q * l[1] * in3, h2 = in;
+  T G[3] = {h0 - c.px * h2, h1 - c.py * h2, c.f * h2};
+  pose_row_line(c, dc, Rm, G, o.Jc[0]);
+  T u1[3], u3[3], r;
+  line_frame(L, L + 3, u1, u3, r);
+  T ddir[4][3], mdir[4][3];
+  line_dirs(L, u1, u3, r, ddir, mdir);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T dm[3];
+    dmc_dir(c, ddir[k], mdir[k], dm);
+    o.Jf[0][k] = dot3(G, dm);
+  }
+}
+
+}  // namespace ba

@@ -428,8 +428,15 @@ def make_scene(cfg: SceneConfig) -> dict:
     else:
         vps0 = np.zeros((0, 3))
     intr = np.stack([f, k1, k2], 1)
-    fixed = np.zeros(Nc, bool)
-    fixed[0] = True                                    # gauge: camera 0's pose is held
+    # gauge (7-DoF similarity): camera 0's pose is held (mask 0x3F) and, for the scale, the translation
+    # component of camera 1 that moves most when the scene is scaled about camera 0's centre
+    fixed = np.zeros(Nc, np.uint8)
+    fixed[0] = 0x3F
+    if Nc > 1:
+        C0 = -R0[0].T @ t0[0]
+        C1 = -R0[1].T @ t0[1]
+        j = int(np.argmax(np.abs(R0[1] @ (C1 - C0))))
+        fixed[1] = 1 << (3 + j)
     scene = dict(
         name=cfg.name, seed=cfg.seed, fixed=fixed,
         cams=dict(q=_mat_to_quat(R0), t=t0, intr=intr, pp=pp),

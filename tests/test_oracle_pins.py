@@ -35,8 +35,7 @@ def _cam_vec(c):
 def tiny():
     s = make_scene(config("tiny"))
     st = O.state_from_scene(s)
-    fixed = np.zeros(len(st["cams"]), bool); fixed[0] = True
-    return s, st, fixed
+    return s, st, s["fixed"]
 
 
 # ---------------------------------------------------------------- closed forms
@@ -254,7 +253,8 @@ def test_schur_pattern_matches_visibility(tiny):
     def col(e):
         t, i = e
         if t == "c":
-            return None if fixed[i] else int(lay.cam_col[i]), 6
+            c = lay.cam_cols[i][lay.cam_cols[i] >= 0]
+            return (None, 0) if len(c) == 0 else (int(c[0]), len(c))
         if t == "p":
             return int(lay.plane_col[i]), 3
         return int(lay.vp_col[i]), 2
