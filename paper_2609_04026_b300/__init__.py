@@ -1,8 +1,9 @@
 """Python binding of libba, the B300 library for one LM step of holistic bundle adjustment.
 
 The binding only marshals arguments: every step of the solve runs in the CUDA
-kernels of libba.so (built in-tree by ``paper_2609_04026_b300.build``).  Importing
-this module fails loudly when the library is missing; there is no CPU fallback.
+kernels of libba.so (built in-tree by ``paper_2609_04026_b300.build``).  The first
+call into the library raises ImportError when libba.so is missing; there is no CPU
+fallback.
 
 Functions keep the C names (``ba_create``, ``ba_add_cameras``, ... ``ba_lm_step``,
 ``ba_solve``).  Arrays may be numpy arrays (host memory) or CUDA torch tensors
@@ -102,8 +103,17 @@ def _load():
     return lib
 
 
-_lib = _load()
-EXPORTS = [n for n in dir(_lib) if n.startswith("ba_")]
+class _Lazy:
+    """libba.so, loaded (and its signatures declared) on first use; a missing library raises ImportError."""
+    _h = None
+
+    def __getattr__(self, name):
+        if _Lazy._h is None:
+            _Lazy._h = _load()
+        return getattr(_Lazy._h, name)
+
+
+_lib = _Lazy()
 
 
 class BAError(RuntimeError):
@@ -113,7 +123,8 @@ class BAError(RuntimeError):
 
 
 def lib():
-    return _lib
+    _lib.ba_default_options   # force the load
+    return _Lazy._h
 
 
 def _check(p, status):
@@ -323,3 +334,4 @@ def load_scene(p, scene, device_tensors=False):
         meas = o["meas"] if MEAS_DIM[k] else None
         ba_add_observations(p, k, conv(o["cam"]) if k != 4 else None, conv(o["feat"]), conv(o["other"]),
                             conv(meas) if meas is not None else None)
+

@@ -161,4 +161,5 @@ struct ba_problem {
 
 namespace ba {
 ba_status build_structure(Problem& P);   // structure.cu
+
 }

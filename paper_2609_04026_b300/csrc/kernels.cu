@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
   const int row = a.up_row[u];
   const int fpos = a.up_full[u];
   const bool diag = a.col[fpos] == row;
-  T s[36];
+  double s[36];   // partials summed in double, rounded to the storage type once
   double bb[6], hh[6];
 #pragma unroll
   for (int i = 0; i < 36; ++i) s[i] = 0;
@@ -651,13 +651,24 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
   for (int w = a.up_wi[u]; w < a.up_wi[u + 1]; ++w) {
     const T* p = a.part + (size_t)w * PART;
 #pragma unroll
-    for (int i = 0; i < 36; ++i) s[i] += p[i];
+    for (int i = 0; i < 36; ++i) s[i] += (double)p[i];
     if (diag)
 #pragma unroll
       for (int i = 0; i < 6; ++i) { bb[i] += (double)p[36 + i]; hh[i] += (double)p[42 + i]; }
   }
   T* out = a.Sval + (size_t)fpos * BS2;
   if (diag) {
+    // a diagonal block sums -Y_e^T W_e with Y_e = V^-1 W_e rounded to the working type; that product is
+    // symmetric only up to rounding, which the strong cancellation against H_aa amplifies.  CG needs an
+    // exactly symmetric S, so the block keeps its symmetric part.
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const double m = 0.5 * (s[i * 6 + j] + s[j * 6 + i]);
+        s[i * 6 + j] = m;
+        s[j * 6 + i] = m;
+      }
     const int et = a.ent_type[row];
     const int nd = et == ENT_CAM ? 6 : (et == ENT_PLANE ? 3 : 2);
     const unsigned held = (row < a.nc) ? a.cam_fixed[row] : 0u;
@@ -667,7 +678,7 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
       double Di = real ? fmin(fmax(hh[i], 1e-6), 1e32) : 1.0;
       a.Dg[6 * (size_t)row + i] = Di;
       if (real) {
-        s[i * 6 + i] += (T)(a.lambda * Di);
+        s[i * 6 + i] += a.lambda * Di;
         a.b[6 * (size_t)row + i] = bb[i];
       } else {
         // padding (or a held camera): unit diagonal, no coupling, zero right-hand side
@@ -678,15 +689,15 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
       }
     }
 #pragma unroll
-    for (int i = 0; i < 36; ++i) out[i] = s[i];
+    for (int i = 0; i < 36; ++i) out[i] = (T)s[i];
   } else {
 #pragma unroll
-    for (int i = 0; i < 36; ++i) out[i] = s[i];
+    for (int i = 0; i < 36; ++i) out[i] = (T)s[i];
     T* mir = a.Sval + (size_t)a.up_mirror[u] * BS2;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) mir[j * 6 + i] = s[i * 6 + j];
+      for (int j = 0; j < 6; ++j) mir[j * 6 + i] = (T)s[i * 6 + j];
   }
 }
 
@@ -748,6 +759,61 @@ __device__ __forceinline__ void apply_block(const T* __restrict__ M, const doubl
 // r.r and r.z), and after p = z + beta p (the next SpMV reads every p).  Every CTA
 // forms the global sums from the same per-CTA partials in the same order, so all
 // CTAs take the same stop decision.
+// Accumulator of the SpMV products S_ij p_j.  With double S (FP64 path) it is a plain
+// double.  With float S (mixed path) it is a double-single pair (hi, lo) of floats:
+// p_j is split into hi + lo floats, S_ij * hi is formed exactly as a product and its
+// FMA-recovered rounding error (TwoProduct, Dekker 1971), and the sum is kept with
+// Knuth's TwoSum, so the float pipes deliver products accurate to ~1e-14 relative.
+// Plain float products lose the strong cancellation of S p (a Laplacian-like operator
+// whose row sums nearly vanish) and CG then stops converging.
+template <class T>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+  double s = 0;
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct DotAcc<float> {
+  float hi = 0, lo = 0;
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ void block_dot6(const double* __restrict__ B, const double* x, DotAcc<double> (&acc)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[i].s = fma(B[i * 6 + j], x[j], acc[i].s);
+}
+
+__device__ __forceinline__ void block_dot6(const float* __restrict__ B, const double* x, DotAcc<float> (&acc)[6]) {
+  float xh[6], xl[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    xh[j] = (float)x[j];
+    xl[j] = (float)(x[j] - (double)xh[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float hi = acc[i].hi, lo = acc[i].lo;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float b = B[i * 6 + j];
+      const float ph = b * xh[j];
+      const float pe = fmaf(b, xh[j], -ph);      // exact error of the product
+      const float s = hi + ph;                   // TwoSum(hi, ph)
+      const float bp = s - hi;
+      const float err = (hi - (s - bp)) + (ph - bp);
+      hi = s;
+      lo += err + fmaf(b, xl[j], pe);
+    }
+    acc[i].hi = hi;
+    acc[i].lo = lo;
+  }
+}
+
 template <class T>
 struct PcgArgs {
   int64_t na;
@@ -833,22 +899,19 @@ __global__ void __launch_bounds__(NT) k_pcg_persistent(PcgArgs<T> a) {
   while (!done) {
     // ---- A: Ap = S p by chunks, then per row in chunk order; partial p.Ap
     for (int q = q0 + warp; q < q1; q += NW) {
-      T acc[6] = {0, 0, 0, 0, 0, 0};
+      DotAcc<T> acc[6];
       const int e = a.chunk_beg[q + 1];
       for (int blk = a.chunk_beg[q] + lane; blk < e; blk += 32) {
         const T* B = a.Sval + (size_t)blk * BS2;
         const double* pb = a.p + 6 * (size_t)a.col[blk];
-        T xv[6];
+        double xv[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) xv[j] = (T)__ldcg(&pb[j]);
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[i] += B[i * 6 + j] * xv[j];
+        for (int j = 0; j < 6; ++j) xv[j] = __ldcg(&pb[j]);
+        block_dot6(B, xv, acc);
       }
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        double y = warp_sum((double)acc[i]);
+        double y = warp_sum(acc[i].value());
         if (lane == 0) chunk_y[6 * (q - q0) + i] = y;
       }
     }

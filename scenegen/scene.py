@@ -76,15 +76,15 @@ def config(name: str, seed: int | None = None, **over) -> SceneConfig:
     elif name == "small":      # a parity case a few tiles wide with ragged sizes
         c = SceneConfig(name="small", n_cams=37, ring=False, n_points=5003, n_lines=611,
                         n_planes=7, n_vps=4, track_min=2, track_max=9, track_mean=4.5,
-                        k_near=20, n_wire_edges=301, sigma_px=0.7, outlier_frac=0.03, seed=7)
+                        k_near=20, n_wire_edges=601, sigma_px=0.7, outlier_frac=0.03, seed=7)
     elif name == "medium":     # 200 cams, 100k pts, 20k lines, 30 planes + 20 VPs
         c = SceneConfig(name="medium", n_cams=200, ring=False, n_points=100_000, n_lines=20_000,
                         n_planes=30, n_vps=20, track_min=2, track_max=12, track_mean=5.0,
-                        k_near=40, n_wire_edges=3000, sigma_px=0.5, outlier_frac=0.03, seed=2)
+                        k_near=40, n_wire_edges=6000, sigma_px=0.5, outlier_frac=0.03, seed=2)
     elif name == "large":      # 2000 cams, 2M pts, 200k lines, 300 planes + 200 VPs
         c = SceneConfig(name="large", n_cams=2000, ring=False, n_points=2_000_000,
                         n_lines=200_000, n_planes=300, n_vps=200, track_min=2, track_max=12,
-                        track_mean=6.0, k_near=64, n_wire_edges=34_000, sigma_px=0.5,
+                        track_mean=6.0, k_near=64, n_wire_edges=68_000, sigma_px=0.5,
                         outlier_frac=0.03, seed=3)
     else:
         raise ValueError(name)
@@ -232,6 +232,7 @@ def make_scene(cfg: SceneConfig) -> dict:
     n_edges = cfg.n_wire_edges if npl > 0 else 0
     n_junc = n_edges // 2
     wf_pts, wf_pl, wf_lines_c, wf_lines_d, wf_lines_len, wf_lines_pl, edges = [], [], [], [], [], [], []
+    grid_center = {}
     if n_junc > 0:
         per_plane = np.full(npl, n_junc // npl); per_plane[: n_junc % npl] += 1
         lid = 0
@@ -242,6 +243,9 @@ def make_scene(cfg: SceneConfig) -> dict:
             ax = pl_axis[p]; o = [i for i in range(3) if i != ax]
             c0 = rng.uniform(-2.0, 2.0, 2); step = rng.uniform(0.15, 0.3)
             coords = [(i, j) for i in range(g) for j in range(g)][: per_plane[p]]
+            gc = np.zeros(3); gc[ax] = -pl_w[p] / pl_sign[p]
+            gc[o[0]] = c0[0] + (g - 1) * step / 2; gc[o[1]] = c0[1] + (g - 1) * step / 2
+            grid_center[p] = gc
             rows = sorted({i for i, _ in coords}); cols = sorted({j for _, j in coords})
             row_id, col_id = {}, {}
             for i in rows:
@@ -316,10 +320,15 @@ def make_scene(cfg: SceneConfig) -> dict:
     E2 = Lc + 0.5 * Llen[:, None] * Ld
 
     # ---- tracks: anchor camera uniform, views among its K nearest where the feature is visible
-    def draw_tracks(pts_list, n):
+    def draw_tracks(pts_list, n, wf_anchor):
+        """Views among the K nearest cameras of an anchor.  Wireframe features (the first len(wf_anchor))
+        use their grid's anchor camera and only its K_WIRE nearest cameras, so that the points and lines
+        of one junction grid share about half of their views."""
         anchor = rng.integers(0, Nc, n)
+        anchor[: len(wf_anchor)] = wf_anchor
         cand = near[anchor]                              # [n, K]
         ok = np.ones((n, K), bool)
+        ok[: len(wf_anchor), min(K_WIRE, K):] = False
         for X in pts_list:
             xc = _to_cam(Rgt[cand], tgt[cand], X[:, None, :])
             xy = _pix_pinhole(f[cand], pp[cand], xc)
@@ -333,8 +342,11 @@ def make_scene(cfg: SceneConfig) -> dict:
         mask = np.arange(K)[None, :] < L[:, None]
         return sel, mask
 
-    p_sel, p_mask = draw_tracks([P], Np)
-    l_sel, l_mask = draw_tracks([E1, E2], Nl)
+    # anchor camera of each junction grid: the camera that looks most directly at the grid centre
+    K_WIRE = 12
+    grid_anchor = {pl: int(np.argmax(dirs @ (c / max(np.linalg.norm(c), 1e-9)))) for pl, c in grid_center.items()}
+    p_sel, p_mask = draw_tracks([P], Np, np.array([grid_anchor[q] for q in wf_pl], np.int64))
+    l_sel, l_mask = draw_tracks([E1, E2], Nl, np.array([grid_anchor[q] for q in wf_lines_pl], np.int64))
 
     def pack(sel, mask):
         fid = np.repeat(np.arange(sel.shape[0]), mask.sum(1))
