@@ -184,6 +184,35 @@ ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, int32_t* col
 ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* dvp, double* dpoint,
                           double* dline, int* pcg_iters, double* pcg_rel, double* pred);
 
+/* Allocation-free PCG (no counterpart in the paper; an addition for embedding the solver).
+ *
+ * Solves S x = b by the library's block-Jacobi PCG for callers that must not allocate device memory while
+ * they run -- for example a solver inside an application whose GPU memory is handed out once by its own
+ * arena, or a per-frame loop that is not allowed to call cudaMalloc.  The call performs no cudaMalloc,
+ * cudaFree or allocating library routine: every scratch vector lives in one fixed device array inside
+ * libba (about 2.3 MB, held by every GPU that loads the library until the process exits).
+ *
+ *   n_block_rows   block rows of S, each 6 wide, 1 <= n <= 4096
+ *   nnz_blocks     stored 6x6 blocks (both triangles), n <= nnz <= 4194304
+ *   row_ptr        HOST array (n + 1) of the block-CSR row offsets; every row holds its diagonal block
+ *   cols           DEVICE array (nnz) of block column indices
+ *   vals           DEVICE array (nnz x 36) of row-major 6x6 blocks, double; S symmetric positive definite
+ *   b              DEVICE array (6 n), right-hand side
+ *   x              DEVICE array (6 n), output: the PCG iterate when |r_k| <= rel_tol |b| or max_iters is reached
+ *   cuda_stream    stream to run on (NULL = default stream); the call returns after the work has finished
+ *   iters, rel     optional outputs: PCG iterations and final |r_k| / |b|
+ *   err, err_len   optional buffer for a message on failure
+ * Returns BA_ERR_ARG (with a message) for sizes beyond the limits above, a missing diagonal block or an
+ * out-of-range column, BA_ERR_CUDA if a CUDA call fails.
+ * The first call on a device finds the device address of the scratch array (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call shares the scratch array and
+ * leaves the previous call's contents in it (the call initialises everything it reads), so calls whose GPU
+ * work overlaps -- from two host threads, or on two streams of one device -- race on it. */
+ba_status ba_pcg_solve_static(int64_t n_block_rows, int64_t nnz_blocks, const int32_t* row_ptr,
+                              const int32_t* cols, const double* vals, const double* b, double* x,
+                              double rel_tol, int max_iters, void* cuda_stream, int* iters, double* rel,
+                              char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,8 @@ def _load():
         "ba_reduced_size": (I, [P, C.POINTER(I64), C.POINTER(I64)]),
         "ba_export_reduced_system": (I, [P, VP, VP, VP, VP]),
         "ba_compute_step": (I, [P, VP, VP, VP, VP, VP, C.POINTER(I), C.POINTER(D), C.POINTER(D)]),
+        "ba_pcg_solve_static": (I, [I64, I64, VP, VP, VP, VP, VP, D, I, VP, C.POINTER(I), C.POINTER(D),
+                                    C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -335,3 +337,18 @@ def load_scene(p, scene, device_tensors=False):
         ba_add_observations(p, k, conv(o["cam"]) if k != 4 else None, conv(o["feat"]), conv(o["other"]),
                             conv(meas) if meas is not None else None)
 
+
+def ba_pcg_solve_static(row_ptr, cols, vals, b, x, rel_tol=1e-6, max_iters=1000, stream=None):
+    """Allocation-free PCG on a reduced system: row_ptr a host int32 array, cols / vals / b / x CUDA tensors
+    (int32, float64 [nnz, 6, 6], float64 [6n], float64 [6n] output).  Returns (iterations, relative residual)."""
+    n = len(row_ptr) - 1
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    it, rel = C.c_int(), C.c_double()
+    err = C.create_string_buffer(256)
+    st = _lib.ba_pcg_solve_static(n, int(rp[-1]), rp.ctypes.data_as(C.c_void_p), C.c_void_p(cols.data_ptr()),
+                                  C.c_void_p(vals.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                  float(rel_tol), int(max_iters), C.c_void_p(stream or 0), C.byref(it), C.byref(rel),
+                                  err, 256)
+    if st != BA_OK:
+        raise BAError(st, err.value.decode())
+    return it.value, rel.value

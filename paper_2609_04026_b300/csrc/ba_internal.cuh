@@ -162,4 +162,13 @@ struct ba_problem {
 namespace ba {
 ba_status build_structure(Problem& P);   // structure.cu
 
+// raw-pointer launchers (kernels.cu) for the allocation-free PCG entry point (noalloc.cu)
+cudaError_t launch_precond_raw_f64(cudaStream_t st, int64_t na, const int32_t* row_ptr, const int32_t* col,
+                                   const double* Sval, double* Minv, DevScalars* S);
+int pcg_occupancy_f64(size_t smem);
+cudaError_t launch_pcg_raw_f64(cudaStream_t st, int grid, size_t smem, int64_t na, const int32_t* col,
+                               const int32_t* cta_row0, const int32_t* row_chunk0, const int32_t* chunk_beg,
+                               const double* Sval, const double* Minv, const double* b, double* x, double* r,
+                               double* z, double* p, double* Ap, double* part, DevScalars* S, double tol,
+                               int max_iters);
 }

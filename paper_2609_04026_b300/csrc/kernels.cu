@@ -1408,6 +1408,29 @@ void launch_pcg(Problem& P) {
                                           dim3(PCG_THREADS), args, P.pcg_smem, P.stream);
 }
 
+// ---- launchers on caller-provided pointers (FP64), used by the allocation-free PCG entry point
+cudaError_t launch_precond_raw_f64(cudaStream_t st, int64_t na, const int32_t* row_ptr, const int32_t* col,
+                                   const double* Sval, double* Minv, DevScalars* S) {
+  if (na > 0) k_precond<double><<<nblk(na, 128), 128, 0, st>>>(na, row_ptr, col, Sval, Minv, S);
+  return cudaGetLastError();
+}
+
+int pcg_occupancy_f64(size_t smem) { return pcg_blocks_per_sm<double>(smem); }
+
+cudaError_t launch_pcg_raw_f64(cudaStream_t st, int grid, size_t smem, int64_t na, const int32_t* col,
+                               const int32_t* cta_row0, const int32_t* row_chunk0, const int32_t* chunk_beg,
+                               const double* Sval, const double* Minv, const double* b, double* x, double* r,
+                               double* z, double* p, double* Ap, double* part, DevScalars* S, double tol,
+                               int max_iters) {
+  PcgArgs<double> a;
+  a.na = na; a.col = col; a.cta_row0 = cta_row0; a.row_chunk0 = row_chunk0; a.chunk_beg = chunk_beg;
+  a.Sval = Sval; a.Minv = Minv; a.b = b; a.x = x; a.r = r; a.z = z; a.p = p; a.Ap = Ap; a.part = part; a.S = S;
+  a.tol = tol; a.max_iters = max_iters;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<double, PCG_THREADS>, dim3(grid),
+                                     dim3(PCG_THREADS), args, smem, st);
+}
+
 template <class T>
 void launch_backsub(Problem& P) {
   const Dims& d = P.d;
