@@ -189,11 +189,11 @@ static ba_status plan_pcg(ba_problem* p) {
   std::vector<int32_t> rp(d.na + 1);
   CUDA_OR(p, cudaMemcpyAsync(rp.data(), p->row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, p->stream));
   CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  // rows are padded to multiples of 32 stored blocks: one chunk per 32 blocks (one block per lane)
   std::vector<int32_t> row_chunk0(d.na + 1, 0), chunk_beg;
   for (int64_t r = 0; r < d.na; ++r) {
-    int32_t len = rp[r + 1] - rp[r];
-    int32_t nch = std::max<int32_t>(1, (len + PCG_CHUNK - 1) / PCG_CHUNK);
-    for (int32_t k = 0; k < nch; ++k) chunk_beg.push_back(rp[r] + k * PCG_CHUNK);
+    int32_t nch = (rp[r + 1] - rp[r]) / 32;
+    for (int32_t k = 0; k < nch; ++k) chunk_beg.push_back(rp[r] + k * 32);
     row_chunk0[r + 1] = row_chunk0[r] + nch;
   }
   chunk_beg.push_back(rp[d.na]);
@@ -202,7 +202,7 @@ static ba_status plan_pcg(ba_problem* p) {
   CUDA_OR(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const bool mx = mixed(p);
   auto occ = [&](size_t smem) { return mx ? pcg_blocks_per_sm<float>(smem) : pcg_blocks_per_sm<double>(smem); };
-  int per_sm = std::max(1, std::min(2, occ(48 * 1024)));
+  int per_sm = std::max(1, std::min(1, occ(48 * 1024)));
   std::vector<int32_t> cta_row0;
   size_t smem = 0;
   for (int attempt = 0; attempt < 8; ++attempt) {
@@ -265,7 +265,7 @@ static ba_status freeze(ba_problem* p) {
   ok &= A(p->slotG, T * SG * (size_t)d.ne);
   ok &= A(p->slotB, T * SG * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
-  ok &= A(p->Sval, T * BS2 * (size_t)d.nbf);
+  ok &= A(p->Sval, T * BS2 * (size_t)d.nbp);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   ok &= A(p->part, T * PART * (size_t)d.nwi);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
@@ -279,6 +279,7 @@ static ba_status freeze(ba_problem* p) {
   p->S = p->dnew<DevScalars>(1);
   ok &= p->red && p->S;
   if (mixed(p)) {
+    ok &= A(*(void**)&p->phl, sizeof(float2) * 6 * (size_t)d.na);
     ok &= A(p->camT, sizeof(float) * CAM_STRIDE * (size_t)d.nc);
     ok &= A(p->grpT, sizeof(float) * GRP_STRIDE * (size_t)(d.npl + d.nv));
     ok &= A(p->ptsT, sizeof(float) * 3 * (size_t)d.np);
@@ -289,7 +290,7 @@ static ba_status freeze(ba_problem* p) {
   // one-time zero fill of the slot and feature arrays
   CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
-  CUDA_OR(p, cudaMemsetAsync(p->Sval, 0, T * BS2 * (size_t)d.nbf, p->stream));
+  CUDA_OR(p, cudaMemsetAsync(p->Sval, 0, T * BS2 * (size_t)d.nbp, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
   if (mixed(p) && d.nr) {
@@ -533,17 +534,30 @@ extern "C" ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, i
   if (!p->have_reduced) return set_err(p, BA_ERR_STATE, "no reduced system built (call ba_build_reduced)");
   const Dims& d = p->d;
   ba_status s;
-  if (row_ptr && (s = put_out(p, BA_MEM_HOST, row_ptr, (const int32_t*)p->row_ptr, d.na + 1))) return s;
-  if (cols && (s = put_out(p, BA_MEM_HOST, cols, (const int32_t*)p->col, d.nbf))) return s;
+  // the device storage is padded and interleaved; the export is plain block-CSR of the stored blocks
+  std::vector<int32_t> pc(d.nbp);
+  if ((s = put_out(p, BA_MEM_HOST, pc.data(), (const int32_t*)p->col, d.nbp))) return s;
+  std::vector<double> pv;
   if (vals) {
-    size_t n = (size_t)BS2 * d.nbf;
+    pv.resize((size_t)BS2 * d.nbp);
     if (mixed(p)) {
-      std::vector<float> h(n);
-      if ((s = put_out(p, BA_MEM_HOST, h.data(), (const float*)p->Sval, n))) return s;
-      for (size_t i = 0; i < n; ++i) vals[i] = h[i];
-    } else if ((s = put_out(p, BA_MEM_HOST, vals, (const double*)p->Sval, n))) {
+      std::vector<float> h(pv.size());
+      if ((s = put_out(p, BA_MEM_HOST, h.data(), (const float*)p->Sval, h.size()))) return s;
+      for (size_t i = 0; i < h.size(); ++i) pv[i] = h[i];
+    } else if ((s = put_out(p, BA_MEM_HOST, pv.data(), (const double*)p->Sval, pv.size()))) {
       return s;
     }
+  }
+  int64_t o = 0;
+  if (row_ptr) row_ptr[0] = 0;
+  for (int64_t a = 0; a < d.na; ++a) {
+    for (int32_t k = 0; k < p->h_row_len[a]; ++k, ++o) {
+      const int64_t q = p->h_prow_ptr[a] + k;
+      if (cols) cols[o] = pc[q];
+      if (vals)
+        for (int e = 0; e < BS2; ++e) vals[(size_t)o * BS2 + e] = pv[s_idx(q, e)];
+    }
+    if (row_ptr) row_ptr[a + 1] = (int32_t)o;
   }
   if (b && (s = put_out(p, BA_MEM_HOST, b, (const double*)p->bvec, 6 * (size_t)d.na))) return s;
   return BA_OK;

@@ -66,7 +66,7 @@ using Problem = ::ba_problem;
 
 struct Dims {
   int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
-  int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, npair = 0, nwi = 0;
+  int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0, nwi = 0;  // nbf stored blocks, nbp padded
   int64_t n_points_res_end = 0;  // residuals of points are [0, this); lines follow
 };
 
@@ -79,7 +79,10 @@ template <class T> void launch_precond(Problem& P);
 template <class T> void launch_pcg(Problem& P);
 template <class T> int pcg_blocks_per_sm(size_t smem);
 template <class T> void pcg_allow_smem(size_t smem);
-constexpr int PCG_CHUNK = 64;   // stored blocks per SpMV chunk
+constexpr int PCG_CHUNK = 64;   // stored blocks per SpMV chunk (caller-layout path)
+
+// position of entry e of the block at padded position q in the interleaved storage of S
+__host__ __device__ __forceinline__ size_t s_idx(int64_t q, int e) { return (size_t)(q >> 5) * 1152 + (size_t)e * 32 + (q & 31); }
 template <class T> void launch_backsub(Problem& P);
 void launch_candidate(Problem& P);
 void launch_cost(Problem& P, bool candidate);
@@ -135,10 +138,12 @@ struct ba_problem {
   uint8_t* slot_type = nullptr;
   int32_t* feat_plane_slot = nullptr;
   uint8_t* ent_type = nullptr;
-  // reduced system pattern
+  // reduced system pattern: padded, interleaved storage (row_ptr / col over padded positions)
   int32_t *row_ptr = nullptr, *col = nullptr;
+  std::vector<int32_t> h_prow_ptr, h_row_len;
   int32_t *up_row = nullptr, *up_full = nullptr, *up_mirror = nullptr, *up_wi = nullptr;
-  int32_t *pair_a = nullptr, *pair_b = nullptr, *wi_start = nullptr;
+  int32_t *pair_a = nullptr, *pair_b = nullptr, *wi_start = nullptr;   // pair_b bit 31: camera-plane pair
+  int line_slot0 = 0;           // first slot of a line feature
   // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are
   // cut into chunks [chunk_beg[q], chunk_beg[q+1]) for q in [row_chunk0[r], row_chunk0[r+1])
   int32_t *cta_row0 = nullptr, *row_chunk0 = nullptr, *chunk_beg = nullptr;
@@ -150,6 +155,7 @@ struct ba_problem {
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featz = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr, *part = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
+  float2* phl = nullptr;        // mixed path: p split into (hi, lo) floats for the SpMV
   double* red = nullptr;        // per-block partial sums of reductions
   int red_cap = 0;
   ba::DevScalars* S = nullptr;  // device scalars

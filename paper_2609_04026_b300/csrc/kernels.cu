@@ -557,13 +557,77 @@ __global__ void __launch_bounds__(128) k_invert(InvArgs<T> a) {
 // ============================================================================
 template <class T>
 struct SchurArgs {
-  const int32_t *pair_a, *pair_b, *wi_se, *slot_feat;
-  const uint8_t* slot_type;
+  const int32_t *pair_a, *pair_b, *wi_se;
   const T *W, *Y, *H, *B, *C;
   T* part;
-  int64_t np, nwi;
+  int64_t nwi;
+  int line_slot0;   // slots of lines start here (slots are stored feature-major, points first)
 };
 
+// one slot record (24 values) with 16-byte vector loads
+__device__ __forceinline__ void load24(const float* __restrict__ p, float (&v)[24]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 t = __ldg(q + k);
+    v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void load24(const double* __restrict__ p, double (&v)[24]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const double2 t = __ldg(q + k);
+    v[2 * k] = t.x; v[2 * k + 1] = t.y;
+  }
+}
+
+// acc -= Y^T W over the first k rows (k = 3 for points, 4 for lines; the 4th row of a point's Y is
+// never written and must not be read into the sum)
+template <class T>
+__device__ __forceinline__ void sub_yw(const T (&y)[24], const T (&w)[24], bool line, T (&acc)[6][6]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (c == 3 && !line) break;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[i][j] -= y[c * 6 + i] * w[c * 6 + j];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void direct_terms(const SchurArgs<T>& a, int ea, int eb, bool cam_plane, T (&acc)[6][6],
+                                             T (&bacc)[6], T (&hacc)[6]) {
+  if (ea == eb) {
+    const T* H = a.H + (size_t)ea * SH;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i; j < 6; ++j) {
+        const T h = H[up_idx(i, j, 6)];
+        acc[i][j] += h;
+        if (j != i) acc[j][i] += h;
+      }
+    const T* B = a.B + (size_t)ea * SG;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      bacc[i] += B[i];
+      hacc[i] += H[up_idx(i, i, 6)];
+    }
+  } else if (cam_plane) {
+    const T* Cm = a.C + (size_t)ea * SC;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc[i][j] += Cm[i * 3 + j];
+  }
+}
+
+// A thread sums one work item (<= 64 slot pairs of one upper block of S).  Pairs are taken two at a
+// time with both pairs' records loaded before either product, so that a thread keeps two pairs of
+// loads in flight.  pair_b carries a flag in bit 31: the pair is (camera slot, plane slot) of one
+// feature and its direct J_cam^T w J_plane block is added.
 template <class T>
 __global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
   int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -576,43 +640,23 @@ __global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) acc[i][j] = 0;
   }
-  for (int q = s0; q < s1; ++q) {
-    const int ea = a.pair_a[q], eb = a.pair_b[q];
-    const int k = a.slot_feat[ea] < a.np ? 3 : 4;
-    const T* Ya = a.Y + (size_t)ea * SW;
-    const T* Wb = a.W + (size_t)eb * SW;
-    // S_ab -= Y_a^T W_b   (rows: feature dof c)
-    for (int c = 0; c < k; ++c) {
-      T y[6], wv[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) { y[i] = Ya[c * 6 + i]; wv[i] = Wb[c * 6 + i]; }
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) acc[i][j] -= y[i] * wv[j];
-    }
-    if (ea == eb) {
-      const T* H = a.H + (size_t)ea * SH;
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = i; j < 6; ++j) {
-          T h = H[up_idx(i, j, 6)];
-          acc[i][j] += h;
-          if (j != i) acc[j][i] += h;
-        }
-      const T* B = a.B + (size_t)ea * SG;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        bacc[i] += B[i];
-        hacc[i] += H[up_idx(i, i, 6)];
-      }
-    } else if (a.slot_type[ea] == ENT_CAM && a.slot_type[eb] == ENT_PLANE) {
-      const T* Cm = a.C + (size_t)ea * SC;
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) acc[i][j] += Cm[i * 3 + j];
+  for (int q = s0; q < s1; q += 2) {
+    const bool two = q + 1 < s1;
+    const int ea0 = a.pair_a[q];
+    const unsigned pb0 = (unsigned)a.pair_b[q];
+    const int ea1 = two ? a.pair_a[q + 1] : ea0;
+    const unsigned pb1 = two ? (unsigned)a.pair_b[q + 1] : pb0;
+    const int eb0 = (int)(pb0 & 0x7fffffffu), eb1 = (int)(pb1 & 0x7fffffffu);
+    T y0[24], w0[24], y1[24], w1[24];
+    load24(a.Y + (size_t)ea0 * SW, y0);
+    load24(a.W + (size_t)eb0 * SW, w0);
+    load24(a.Y + (size_t)ea1 * SW, y1);
+    load24(a.W + (size_t)eb1 * SW, w1);
+    sub_yw(y0, w0, ea0 >= a.line_slot0, acc);
+    direct_terms(a, ea0, eb0, (pb0 >> 31) != 0u, acc, bacc, hacc);
+    if (two) {
+      sub_yw(y1, w1, ea1 >= a.line_slot0, acc);
+      direct_terms(a, ea1, eb1, (pb1 >> 31) != 0u, acc, bacc, hacc);
     }
   }
   T* o = a.part + (size_t)w * PART;
@@ -656,7 +700,6 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
 #pragma unroll
       for (int i = 0; i < 6; ++i) { bb[i] += (double)p[36 + i]; hh[i] += (double)p[42 + i]; }
   }
-  T* out = a.Sval + (size_t)fpos * BS2;
   if (diag) {
     // a diagonal block sums -Y_e^T W_e with Y_e = V^-1 W_e rounded to the working type; that product is
     // symmetric only up to rounding, which the strong cancellation against H_aa amplifies.  CG needs an
@@ -689,22 +732,23 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
       }
     }
 #pragma unroll
-    for (int i = 0; i < 36; ++i) out[i] = (T)s[i];
+    for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
   } else {
 #pragma unroll
-    for (int i = 0; i < 36; ++i) out[i] = (T)s[i];
-    T* mir = a.Sval + (size_t)a.up_mirror[u] * BS2;
+    for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
+    const int mpos = a.up_mirror[u];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) mir[j * 6 + i] = (T)s[i * 6 + j];
+      for (int j = 0; j < 6; ++j) a.Sval[s_idx(mpos, j * 6 + i)] = (T)s[i * 6 + j];
   }
 }
 
 // ============================================================================
 // K4: block-Jacobi preconditioner
 // ============================================================================
-template <class T>
+// SOA: S in the library's padded interleaved storage; otherwise 36 contiguous values per block
+template <class T, bool SOA>
 __global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                           const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S) {
   int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -713,11 +757,11 @@ __global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const
   for (int q = row_ptr[a]; q < row_ptr[a + 1]; ++q)
     if (col[q] == a) { pos = q; break; }
   double Aup[21];
-  const T* B = Sval + (size_t)pos * BS2;
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int j = i; j < 6; ++j) Aup[up_idx(i, j, 6)] = (double)B[i * 6 + j];
+    for (int j = i; j < 6; ++j)
+      Aup[up_idx(i, j, 6)] = (double)(SOA ? Sval[s_idx(pos, i * 6 + j)] : Sval[(size_t)pos * BS2 + i * 6 + j]);
   double Mi[6][6];
   if (!chol_inverse<6>(Aup, Mi)) {
     atomicOr(&S->flags, 4);
@@ -788,13 +832,8 @@ __device__ __forceinline__ void block_dot6(const double* __restrict__ B, const d
     for (int j = 0; j < 6; ++j) acc[i].s = fma(B[i * 6 + j], x[j], acc[i].s);
 }
 
-__device__ __forceinline__ void block_dot6(const float* __restrict__ B, const double* x, DotAcc<float> (&acc)[6]) {
-  float xh[6], xl[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    xh[j] = (float)x[j];
-    xl[j] = (float)(x[j] - (double)xh[j]);
-  }
+__device__ __forceinline__ void block_dot6_split(const float* __restrict__ B, const float* xh, const float* xl,
+                                                 DotAcc<float> (&acc)[6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     float hi = acc[i].hi, lo = acc[i].lo;
@@ -814,6 +853,42 @@ __device__ __forceinline__ void block_dot6(const float* __restrict__ B, const do
   }
 }
 
+__device__ __forceinline__ void block_dot6(const float* __restrict__ B, const double* x, DotAcc<float> (&acc)[6]) {
+  float xh[6], xl[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    xh[j] = (float)x[j];
+    xl[j] = (float)(x[j] - (double)xh[j]);
+  }
+  block_dot6_split(B, xh, xl, acc);
+}
+
+// warp sum of a product accumulator, returned in double to lane 0 (double-single lanes are
+// combined with TwoSum on the float pipes; one conversion to double at the end)
+__device__ __forceinline__ double warp_sum_acc(const DotAcc<double>& a) { return warp_sum(a.s); }
+__device__ __forceinline__ double warp_sum_acc(const DotAcc<float>& a) {
+  float hi = a.hi, lo = a.lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const float sm = hi + h2;
+    const float bp = sm - hi;
+    const float er = (hi - (sm - bp)) + (h2 - bp);
+    hi = sm;
+    lo = lo + l2 + er;
+  }
+  return (double)hi + (double)lo;
+}
+
+__device__ __forceinline__ float2 split2(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+template <class T>
+struct PcgArgs;
+
 template <class T>
 struct PcgArgs {
   int64_t na;
@@ -821,11 +896,34 @@ struct PcgArgs {
   const T *Sval, *Minv;
   const double* b;
   double *x, *r, *z, *p, *Ap;
+  float2* phl;   // float working type: p split into (hi, lo) floats, written where p is written
   double* part;  // 3 x G x 2 per-CTA partial sums
   DevScalars* S;
   double tol;
   int max_iters;
 };
+
+// one stored block times the gathered p block: FP64 FMAs for double S; for float S the pre-split
+// (hi, lo) copy of p feeds the double-single products without any FP64 instruction
+__device__ __forceinline__ void spmv_block(const double* B, const PcgArgs<double>& a, int col, DotAcc<double> (&acc)[6]) {
+  const double* pb = a.p + 6 * (size_t)col;
+  double xv[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) xv[j] = __ldcg(&pb[j]);
+  block_dot6(B, xv, acc);
+}
+
+__device__ __forceinline__ void spmv_block(const float* B, const PcgArgs<float>& a, int col, DotAcc<float> (&acc)[6]) {
+  const float2* pb = a.phl + 6 * (size_t)col;
+  float xh[6], xl[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float2 v = __ldcg(&pb[j]);
+    xh[j] = v.x;
+    xl[j] = v.y;
+  }
+  block_dot6_split(B, xh, xl, acc);
+}
 
 template <int NT>
 __device__ __forceinline__ void cta_sum2(double v0, double v1, double* out2) {
@@ -855,8 +953,10 @@ __device__ __forceinline__ void grid_partials2(const double* part, int G, double
   __syncthreads();
 }
 
-template <class T, int NT>
-__global__ void __launch_bounds__(NT) k_pcg_persistent(PcgArgs<T> a) {
+// SOA: S in the padded interleaved storage, chunks of exactly 32 blocks (one per lane, coalesced
+// loads); otherwise contiguous blocks and chunks of up to PCG_CHUNK blocks strided over the lanes
+template <class T, int NT, bool SOA>
+__global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double chunk_y[];   // [chunks of this CTA][6]
@@ -882,6 +982,7 @@ __global__ void __launch_bounds__(NT) k_pcg_persistent(PcgArgs<T> a) {
     for (int i = 0; i < 6; ++i) {
       a.z[6 * row + i] = zv[i];
       a.p[6 * row + i] = zv[i];
+      if (a.phl) a.phl[6 * row + i] = split2(zv[i]);
       v0 += rv[i] * zv[i];
       v1 += rv[i] * rv[i];
     }
@@ -900,18 +1001,27 @@ __global__ void __launch_bounds__(NT) k_pcg_persistent(PcgArgs<T> a) {
     // ---- A: Ap = S p by chunks, then per row in chunk order; partial p.Ap
     for (int q = q0 + warp; q < q1; q += NW) {
       DotAcc<T> acc[6];
-      const int e = a.chunk_beg[q + 1];
-      for (int blk = a.chunk_beg[q] + lane; blk < e; blk += 32) {
-        const T* B = a.Sval + (size_t)blk * BS2;
-        const double* pb = a.p + 6 * (size_t)a.col[blk];
-        double xv[6];
+      if (SOA) {
+        const int blk = a.chunk_beg[q] + lane;
+        const T* Bg = a.Sval + s_idx(blk, 0);
+        T B[36];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) xv[j] = __ldcg(&pb[j]);
-        block_dot6(B, xv, acc);
+        for (int k = 0; k < 36; ++k) B[k] = Bg[k * 32];
+        spmv_block(B, a, a.col[blk], acc);
+      } else {
+        const int e = a.chunk_beg[q + 1];
+        for (int blk = a.chunk_beg[q] + lane; blk < e; blk += 32) {
+          const T* B = a.Sval + (size_t)blk * BS2;
+          const double* pb = a.p + 6 * (size_t)a.col[blk];
+          double xv[6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) xv[j] = __ldcg(&pb[j]);
+          block_dot6(B, xv, acc);
+        }
       }
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        double y = warp_sum(acc[i].value());
+        const double y = warp_sum_acc(acc[i]);
         if (lane == 0) chunk_y[6 * (q - q0) + i] = y;
       }
     }
@@ -962,7 +1072,11 @@ __global__ void __launch_bounds__(NT) k_pcg_persistent(PcgArgs<T> a) {
     const double beta = rz_new / rz;
     rz = rz_new;
     // ---- C: p = z + beta p
-    for (int k = 6 * r0 + threadIdx.x; k < 6 * r1; k += NT) a.p[k] = a.z[k] + beta * a.p[k];
+    for (int k = 6 * r0 + threadIdx.x; k < 6 * r1; k += NT) {
+      const double pk = a.z[k] + beta * a.p[k];
+      a.p[k] = pk;
+      if (a.phl) a.phl[k] = split2(pk);
+    }
     grid.sync();
   }
   if (c == 0 && threadIdx.x == 0) {
@@ -1362,9 +1476,9 @@ template <class T>
 void launch_schur(Problem& P, double lambda) {
   const Dims& d = P.d;
   SchurArgs<T> a;
-  a.pair_a = P.pair_a; a.pair_b = P.pair_b; a.wi_se = P.wi_start; a.slot_feat = P.slot_feat; a.slot_type = P.slot_type;
+  a.pair_a = P.pair_a; a.pair_b = P.pair_b; a.wi_se = P.wi_start;
   a.W = (const T*)P.slotW; a.Y = (const T*)P.slotY; a.H = (const T*)P.slotH; a.B = (const T*)P.slotB;
-  a.C = (const T*)P.slotC; a.part = (T*)P.part; a.np = d.np; a.nwi = d.nwi;
+  a.C = (const T*)P.slotC; a.part = (T*)P.part; a.nwi = d.nwi; a.line_slot0 = P.line_slot0;
   if (d.nwi) { ++P.launches; k_schur_items<T><<<nblk(d.nwi, 128), 128, 0, P.stream>>>(a); }
   if (P.ev[3]) cudaEventRecord(P.ev[3], P.stream);
   BlockArgs<T> b;
@@ -1377,7 +1491,7 @@ void launch_schur(Problem& P, double lambda) {
 template <class T>
 void launch_precond(Problem& P) {
   const Dims& d = P.d;
-  if (d.na) { ++P.launches; k_precond<T><<<nblk(d.na, 128), 128, 0, P.stream>>>(d.na, P.row_ptr, P.col, (const T*)P.Sval, (T*)P.Minv, P.S); }
+  if (d.na) { ++P.launches; k_precond<T, true><<<nblk(d.na, 128), 128, 0, P.stream>>>(d.na, P.row_ptr, P.col, (const T*)P.Sval, (T*)P.Minv, P.S); }
 }
 
 constexpr int PCG_THREADS = 512;
@@ -1385,13 +1499,13 @@ constexpr int PCG_THREADS = 512;
 template <class T>
 int pcg_blocks_per_sm(size_t smem) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_persistent<T, PCG_THREADS>, PCG_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_persistent<T, PCG_THREADS, true>, PCG_THREADS, smem);
   return nb;
 }
 
 template <class T>
 void pcg_allow_smem(size_t smem) {
-  cudaFuncSetAttribute(k_pcg_persistent<T, PCG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_pcg_persistent<T, PCG_THREADS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <class T>
@@ -1401,21 +1515,26 @@ void launch_pcg(Problem& P) {
   a.na = d.na; a.col = P.col; a.cta_row0 = P.cta_row0; a.row_chunk0 = P.row_chunk0; a.chunk_beg = P.chunk_beg;
   a.Sval = (const T*)P.Sval; a.Minv = (const T*)P.Minv; a.b = P.bvec;
   a.x = P.x; a.r = P.r; a.z = P.z; a.p = P.p; a.Ap = P.Ap; a.part = P.red; a.S = P.S;
+  a.phl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
   a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
   void* args[] = {&a};
   ++P.launches;
-  P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, PCG_THREADS>, dim3(P.pcg_grid),
+  P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, PCG_THREADS, true>, dim3(P.pcg_grid),
                                           dim3(PCG_THREADS), args, P.pcg_smem, P.stream);
 }
 
 // ---- launchers on caller-provided pointers (FP64), used by the allocation-free PCG entry point
 cudaError_t launch_precond_raw_f64(cudaStream_t st, int64_t na, const int32_t* row_ptr, const int32_t* col,
                                    const double* Sval, double* Minv, DevScalars* S) {
-  if (na > 0) k_precond<double><<<nblk(na, 128), 128, 0, st>>>(na, row_ptr, col, Sval, Minv, S);
+  if (na > 0) k_precond<double, false><<<nblk(na, 128), 128, 0, st>>>(na, row_ptr, col, Sval, Minv, S);
   return cudaGetLastError();
 }
 
-int pcg_occupancy_f64(size_t smem) { return pcg_blocks_per_sm<double>(smem); }
+int pcg_occupancy_f64(size_t smem) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_persistent<double, PCG_THREADS, false>, PCG_THREADS, smem);
+  return nb;
+}
 
 cudaError_t launch_pcg_raw_f64(cudaStream_t st, int grid, size_t smem, int64_t na, const int32_t* col,
                                const int32_t* cta_row0, const int32_t* row_chunk0, const int32_t* chunk_beg,
@@ -1425,9 +1544,10 @@ cudaError_t launch_pcg_raw_f64(cudaStream_t st, int grid, size_t smem, int64_t n
   PcgArgs<double> a;
   a.na = na; a.col = col; a.cta_row0 = cta_row0; a.row_chunk0 = row_chunk0; a.chunk_beg = chunk_beg;
   a.Sval = Sval; a.Minv = Minv; a.b = b; a.x = x; a.r = r; a.z = z; a.p = p; a.Ap = Ap; a.part = part; a.S = S;
+  a.phl = nullptr;
   a.tol = tol; a.max_iters = max_iters;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<double, PCG_THREADS>, dim3(grid),
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<double, PCG_THREADS, false>, dim3(grid),
                                      dim3(PCG_THREADS), args, smem, st);
 }
 

@@ -202,6 +202,7 @@ ba_status build_structure(Problem& P) {
     fslot_off[d.nf] = (int32_t)slot_ent.size();
   }
   d.ne = (int64_t)slot_ent.size();
+  P.line_slot0 = fslot_off[d.np];
 
   // ---- upper block pattern of S: all entity pairs that share a feature, plus every diagonal
   const int64_t na = d.na;
@@ -254,6 +255,31 @@ ba_status build_structure(Problem& P) {
     }
   }
 
+  // ---- storage layout of S for the SpMV: every row's stored blocks padded to a multiple of 32 (the pads
+  // have col = row and zero values), and inside each group of 32 blocks the 36 entries are interleaved
+  // (entry e of the group's block l at e * 32 + l), so that a warp reads one entry of 32 blocks per
+  // coalesced 128-byte load.  up_full / up_mirror hold positions in this padded order.
+  std::vector<int32_t> prow_ptr(na + 1, 0), row_len(na);
+  for (int64_t a = 0; a < na; ++a) {
+    row_len[a] = row_ptr[a + 1] - row_ptr[a];
+    prow_ptr[a + 1] = prow_ptr[a] + ((row_len[a] + 31) / 32) * 32;
+  }
+  d.nbp = prow_ptr[na];
+  std::vector<int32_t> pcol(d.nbp);
+  for (int64_t a = 0; a < na; ++a)
+    for (int32_t k = 0; k < prow_ptr[a + 1] - prow_ptr[a]; ++k)
+      pcol[prow_ptr[a] + k] = k < row_len[a] ? col[row_ptr[a] + k] : (int32_t)a;
+  auto to_padded = [&](int32_t fp) {
+    int64_t a = std::upper_bound(row_ptr.begin(), row_ptr.end(), fp) - row_ptr.begin() - 1;
+    return prow_ptr[a] + (fp - row_ptr[a]);
+  };
+  for (int64_t u = 0; u < d.nbu; ++u) {
+    up_full[u] = to_padded(up_full[u]);
+    up_mirror[u] = to_padded(up_mirror[u]);
+  }
+  P.h_prow_ptr = prow_ptr;
+  P.h_row_len = row_len;
+
   // ---- slot pairs per upper block (feature order inside a block), cut into work items
   std::vector<int64_t> pcount(d.nbu + 1, 0);
   auto find_up = [&](int32_t a, int32_t b) {
@@ -274,7 +300,9 @@ ba_status build_structure(Problem& P) {
         for (int32_t j = i; j < fslot_off[f + 1]; ++j) {
           int64_t q = pos[find_up(slot_ent[i], slot_ent[j])]++;
           pair_a[q] = i;
-          pair_b[q] = j;
+          // bit 31 marks a (camera slot, plane slot) pair of one feature: its direct block J_cam^T w J_plane
+          const bool cam_plane = i != j && slot_type[i] == ENT_CAM && slot_type[j] == ENT_PLANE;
+          pair_b[q] = (int32_t)((uint32_t)j | (cam_plane ? 0x80000000u : 0u));
         }
   }
   std::vector<int32_t> up_wi(d.nbu + 1, 0), wi_start;
@@ -316,7 +344,7 @@ ba_status build_structure(Problem& P) {
   UP(P.fres_off, fres_off); UP(P.fslot_off, fslot_off);
   UP(P.slot_ent, slot_ent); UP(P.slot_feat, slot_feat); UP(P.slot_type, slot_type);
   UP(P.feat_plane_slot, feat_plane_slot); UP(P.ent_type, ent_type);
-  UP(P.row_ptr, row_ptr); UP(P.col, col);
+  UP(P.row_ptr, prow_ptr); UP(P.col, pcol);
   UP(P.up_row, up_row); UP(P.up_full, up_full); UP(P.up_mirror, up_mirror); UP(P.up_wi, up_wi);
   UP(P.pair_a, pair_a); UP(P.pair_b, pair_b); UP(P.wi_start, wi_se);
   UP(P.cam_fixed, P.h_fixed);

@@ -86,6 +86,10 @@ def config(name: str, seed: int | None = None, **over) -> SceneConfig:
                         n_lines=200_000, n_planes=300, n_vps=200, track_min=2, track_max=12,
                         track_mean=6.0, k_near=64, n_wire_edges=68_000, sigma_px=0.5,
                         outlier_frac=0.03, seed=3)
+    elif name == "pcgprof":    # the large reduced system (2000 cams, 500 groups) with a tenth of the features
+        c = SceneConfig(name="pcgprof", n_cams=2000, ring=False, n_points=200_000, n_lines=20_000,
+                        n_planes=300, n_vps=200, track_min=2, track_max=12, track_mean=6.0, k_near=64,
+                        n_wire_edges=6800, sigma_px=0.5, outlier_frac=0.03, seed=4)
     else:
         raise ValueError(name)
     if seed is not None:
