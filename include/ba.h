@@ -122,6 +122,7 @@ typedef struct ba_step_report {
    * [9] decision (K9) */
   float ms_kernel[10];
   int n_launches;               /* CUDA kernels this step launched */
+  int precond_fallbacks;        /* learned preconditioner: blocks that fell back to block-Jacobi (-1: not used) */
 } ba_step_report;
 
 typedef struct ba_solve_report {
@@ -183,6 +184,38 @@ ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, int32_t* col
  * (cams n x 6 as (dw, dt), planes n x 3, vps n x 2, points n x 3, lines n x 4); NULL skips an output. */
 ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* dvp, double* dpoint,
                           double* dline, int* pcg_iters, double* pcg_rel, double* pred);
+
+/* Learned correction of the block-Jacobi preconditioner.  The paper solves the reduced system directly; this
+ * optional preconditioner for the PCG solve has no counterpart there.  Per diagonal block b of S (6 wide):
+ *   features x_b (32): the 21 upper entries of D_b^-1/2 S_bb D_b^-1/2 (D_b = diag S_bb); over the row's
+ *     off-diagonal blocks c, with n_bc = |D_b^-1/2 S_bc D_c^-1/2|_F: log(1+count), sum, max, sum of squares;
+ *     the entity type one-hot (camera, plane, VP); zeros.
+ *   network: y = W2^T relu(W1^T ((x - mu)/sigma) + b1) + b2, 32 -> 128 -> 21 (BF16 weights at inference).
+ *   block: M^ = inv(S^_bb) + sym(y) (no correction in padded or held dimensions), M = D^-1/2 M^ D^-1/2, used
+ *     when positive definite, else plain block-Jacobi for that block.
+ * Parameter vector (float): mu (32), sigma (32), W1 (32 x 128, row-major by input), b1 (128), W2 (128 x 21,
+ * row-major by hidden unit), b2 (21); ba_precond_param_count() values.  Active when options.precond is
+ * BA_PRECOND_LEARNED and weights are set. */
+int ba_precond_param_count(void);
+ba_status ba_precond_set_weights(ba_problem* p, const float* params, int64_t n);
+/* Features (na x 32, host) and real-dimension masks (na bytes, bit k = dimension k is real) of the last reduced
+ * system built by ba_build_reduced. */
+ba_status ba_precond_features(ba_problem* p, float* X, uint8_t* mask);
+/* The preconditioner blocks (na x 36, host, row-major 6x6) for the last reduced system: learned when active,
+ * else block-Jacobi; *fallbacks receives the number of learned blocks that fell back. */
+ba_status ba_precond_blocks(ba_problem* p, double* blocks, int* fallbacks);
+/* Training on the GPU (all arrays device memory, FP32).  Samples: X (n x 32), E (n x 21: the upper entries of
+ * T^_b - inv(S^_bb), T^_b = D_b^1/2 [inv(S)]_bb D_b^1/2), mask (n).  Loss = mean_b |sym(y_b) - E_b|_F^2 over real
+ * dimensions.  ba_mlp_grad: loss and gradient (the trained parameters, i.e. all but mu and sigma, in the
+ * parameter order) over all n samples.  ba_precond_train: `steps` Adam steps (Kingma & Ba 2015; beta 0.9 /
+ * 0.999, eps 1e-8) on consecutive mini-batches of `batch` samples, starting at step count t0; updates params and
+ * the moment vectors adam_m / adam_v in place.  work: device scratch of ba_mlp_work_floats(batch) floats. */
+int64_t ba_mlp_work_floats(int64_t batch);
+ba_status ba_mlp_grad(int64_t n, const float* X, const float* E, const uint8_t* mask, const float* params,
+                      float* grad, double* loss, float* work, void* cuda_stream);
+ba_status ba_precond_train(int64_t n, const float* X, const float* E, const uint8_t* mask, float* params,
+                           float* adam_m, float* adam_v, int t0, int steps, int64_t batch, float lr, float* work,
+                           double* loss_last, void* cuda_stream);
 
 /* Allocation-free PCG (no counterpart in the paper; an addition for embedding the solver).
  *

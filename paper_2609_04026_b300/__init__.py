@@ -49,7 +49,8 @@ class ba_step_report(C.Structure):
                 ("lambda_", C.c_double), ("pcg_rel", C.c_double), ("pcg_iters", C.c_int),
                 ("accepted", C.c_int), ("converged", C.c_int), ("relinearized", C.c_int),
                 ("ms_linearize", C.c_float), ("ms_schur", C.c_float), ("ms_pcg", C.c_float),
-                ("ms_update", C.c_float), ("ms_kernel", C.c_float * 10), ("n_launches", C.c_int)]
+                ("ms_update", C.c_float), ("ms_kernel", C.c_float * 10), ("n_launches", C.c_int),
+                ("precond_fallbacks", C.c_int)]
 
     KERNELS = ("linearize", "invert", "schur_items", "schur_blocks", "precond", "pcg", "backsub",
                "candidate", "cost", "decide")
@@ -97,6 +98,13 @@ def _load():
         "ba_compute_step": (I, [P, VP, VP, VP, VP, VP, C.POINTER(I), C.POINTER(D), C.POINTER(D)]),
         "ba_pcg_solve_static": (I, [I64, I64, VP, VP, VP, VP, VP, D, I, VP, C.POINTER(I), C.POINTER(D),
                                     C.c_char_p, C.c_size_t]),
+        "ba_precond_param_count": (I, []),
+        "ba_precond_set_weights": (I, [P, VP, I64]),
+        "ba_precond_features": (I, [P, VP, VP]),
+        "ba_precond_blocks": (I, [P, VP, C.POINTER(I)]),
+        "ba_mlp_work_floats": (I64, [I64]),
+        "ba_mlp_grad": (I, [I64, VP, VP, VP, VP, VP, C.POINTER(D), VP, VP]),
+        "ba_precond_train": (I, [I64, VP, VP, VP, VP, VP, VP, I, I, I64, C.c_float, VP, C.POINTER(D), VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -352,3 +360,58 @@ def ba_pcg_solve_static(row_ptr, cols, vals, b, x, rel_tol=1e-6, max_iters=1000,
     if st != BA_OK:
         raise BAError(st, err.value.decode())
     return it.value, rel.value
+
+
+# ---------------------------------------------------------------------------- learned preconditioner
+def ba_precond_param_count():
+    return _lib.ba_precond_param_count()
+
+
+def ba_precond_set_weights(p, params):
+    a = np.ascontiguousarray(params, np.float32)
+    _check(p, _lib.ba_precond_set_weights(p, a.ctypes.data_as(C.c_void_p), len(a)))
+
+
+def ba_precond_features(p, na):
+    X = np.empty((na, 32), np.float32)
+    m = np.empty(na, np.uint8)
+    _check(p, _lib.ba_precond_features(p, X.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p)))
+    return X, m
+
+
+def ba_precond_blocks(p, na):
+    out = np.empty((na, 6, 6))
+    fb = C.c_int()
+    _check(p, _lib.ba_precond_blocks(p, out.ctypes.data_as(C.c_void_p), C.byref(fb)))
+    return out, fb.value
+
+
+def _dp(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def ba_mlp_grad(X, E, mask, params, stream=None):
+    """X [n,32], E [n,21] float32, mask [n] uint8, params [P] float32: CUDA tensors.  Returns (loss, grad)."""
+    import torch
+    n = X.shape[0]
+    grad = torch.empty(ba_precond_param_count() - 64, dtype=torch.float32, device=X.device)
+    work = torch.empty(int(_lib.ba_mlp_work_floats(n)) + 8, dtype=torch.float32, device=X.device)
+    loss = C.c_double()
+    st = _lib.ba_mlp_grad(n, _dp(X), _dp(E), _dp(mask), _dp(params), _dp(grad), C.byref(loss), _dp(work),
+                          C.c_void_p(stream or 0))
+    if st != BA_OK:
+        raise BAError(st, "ba_mlp_grad failed")
+    return loss.value, grad
+
+
+def ba_precond_train(X, E, mask, params, adam_m, adam_v, t0, steps, batch, lr, stream=None):
+    """In-place Adam training of params (CUDA tensors); returns the last mini-batch loss."""
+    import torch
+    work = torch.empty(int(_lib.ba_mlp_work_floats(batch)) + 8, dtype=torch.float32, device=X.device)
+    loss = C.c_double()
+    st = _lib.ba_precond_train(X.shape[0], _dp(X), _dp(E), _dp(mask), _dp(params), _dp(adam_m), _dp(adam_v),
+                               int(t0), int(steps), int(batch), float(lr), _dp(work), C.byref(loss),
+                               C.c_void_p(stream or 0))
+    if st != BA_OK:
+        raise BAError(st, "ba_precond_train failed")
+    return loss.value

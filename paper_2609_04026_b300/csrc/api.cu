@@ -271,7 +271,7 @@ static ba_status freeze(ba_problem* p) {
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
   p->featg = p->dnew<double>(4 * d.nf); p->featz = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
   ok &= p->featV && p->featVinv && p->featg && p->featz && p->dfeat;
-  double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap};
+  double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap, &p->sdiag};
   for (double** v : vecs) { *v = p->dnew<double>(6 * d.na); ok &= *v != nullptr; }
   int64_t maxb = std::max<int64_t>({(d.nr + 255) / 256, (d.nf + 127) / 128, (d.na * 32 + 255) / 256, (d.na + 127) / 128,
                                     4 * 148 * 4, 1});
@@ -349,8 +349,14 @@ static ba_status build_reduced_t(ba_problem* p, double lambda, bool* relin) {
 }
 
 template <class T>
+static void build_precond_t(ba_problem* p) {
+  if (p->opt.precond == BA_PRECOND_LEARNED && p->pre_ready) launch_pre_learned<T>(*p);
+  else launch_precond<T>(*p);
+}
+
+template <class T>
 static ba_status solve_reduced_t(ba_problem* p) {
-  launch_precond<T>(*p);
+  build_precond_t<T>(p);
   MARK(4);
   launch_pcg<T>(*p);
   if (p->pcg_err != cudaSuccess) return set_err(p, BA_ERR_CUDA, std::string("PCG launch: ") + cudaGetErrorString(p->pcg_err));
@@ -386,6 +392,9 @@ static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
   r.pcg_iters = h.iters; r.pcg_rel = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
   r.accepted = h.accepted; r.relinearized = relin ? 1 : 0;
   r.n_launches = p->launches;
+  r.precond_fallbacks = -1;
+  if (p->opt.precond == BA_PRECOND_LEARNED && p->pre_ready)
+    CUDA_OR(p, cudaMemcpy(&r.precond_fallbacks, p->pre_fallbacks, sizeof(int), cudaMemcpyDeviceToHost));
   for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&r.ms_kernel[k], p->ev[k], p->ev[k + 1]);
   r.ms_linearize = r.ms_kernel[0];
   r.ms_schur = r.ms_kernel[1] + r.ms_kernel[2] + r.ms_kernel[3] + r.ms_kernel[4];
@@ -582,5 +591,55 @@ extern "C" ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane
   if (pcg_iters) *pcg_iters = p->hS->iters;
   if (pcg_rel) *pcg_rel = p->hS->bnorm2 > 0 ? std::sqrt(p->hS->rr / p->hS->bnorm2) : 0.0;
   if (pred) *pred = p->hS->pred;
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned preconditioner
+extern "C" ba_status ba_precond_set_weights(ba_problem* p, const float* params, int64_t n) {
+  if (!p || !params) return BA_ERR_ARG;
+  if (n != ba_precond_param_count()) return set_err(p, BA_ERR_ARG, "wrong number of preconditioner parameters");
+  ba_status s = freeze(p);
+  if (s) return s;
+  if ((s = precond_alloc_features(*p))) return set_err(p, s, "device allocation failed");
+  if ((s = precond_set_weights(*p, params))) return set_err(p, s, "could not upload the preconditioner weights");
+  return BA_OK;
+}
+
+extern "C" ba_status ba_precond_features(ba_problem* p, float* X, uint8_t* mask) {
+  if (!p) return BA_ERR_ARG;
+  if (!p->have_reduced) return set_err(p, BA_ERR_STATE, "no reduced system built (call ba_build_reduced)");
+  ba_status s = precond_alloc_features(*p);
+  if (s) return set_err(p, s, "device allocation failed");
+  if (mixed(p)) launch_pre_features<float>(*p); else launch_pre_features<double>(*p);
+  CUDA_OR(p, cudaGetLastError());
+  if (X && (s = put_out(p, BA_MEM_HOST, X, (const float*)p->pre_X, 32 * (size_t)p->d.na))) return s;
+  if (mask && (s = put_out(p, BA_MEM_HOST, mask, (const uint8_t*)p->pre_mask, (size_t)p->d.na))) return s;
+  return BA_OK;
+}
+
+extern "C" ba_status ba_precond_blocks(ba_problem* p, double* blocks, int* fallbacks) {
+  if (!p || !blocks) return BA_ERR_ARG;
+  if (!p->have_reduced) return set_err(p, BA_ERR_STATE, "no reduced system built (call ba_build_reduced)");
+  if (p->opt.precond == BA_PRECOND_LEARNED && p->pre_ready) {
+    if (mixed(p)) launch_pre_learned<float>(*p); else launch_pre_learned<double>(*p);
+  } else {
+    if (mixed(p)) launch_precond<float>(*p); else launch_precond<double>(*p);
+  }
+  CUDA_OR(p, cudaGetLastError());
+  const size_t n = (size_t)BS2 * p->d.na;
+  ba_status s;
+  if (mixed(p)) {
+    std::vector<float> h(n);
+    if ((s = put_out(p, BA_MEM_HOST, h.data(), (const float*)p->Minv, n))) return s;
+    for (size_t i = 0; i < n; ++i) blocks[i] = h[i];
+  } else if ((s = put_out(p, BA_MEM_HOST, blocks, (const double*)p->Minv, n))) {
+    return s;
+  }
+  if (fallbacks) {
+    *fallbacks = 0;
+    if (p->opt.precond == BA_PRECOND_LEARNED && p->pre_ready)
+      CUDA_OR(p, cudaMemcpy(fallbacks, p->pre_fallbacks, sizeof(int), cudaMemcpyDeviceToHost));
+  }
   return BA_OK;
 }

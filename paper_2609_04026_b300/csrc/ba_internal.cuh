@@ -156,6 +156,15 @@ struct ba_problem {
   void *Sval = nullptr, *Minv = nullptr, *part = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   float2* phl = nullptr;        // mixed path: p split into (hi, lo) floats for the SpMV
+  int32_t* row_len = nullptr;   // stored (non-padding) blocks per row of S
+  double* sdiag = nullptr;      // diagonal of S (after damping), 6 per entity
+  // learned correction of the block-Jacobi preconditioner
+  float* pre_params = nullptr;  // network parameters (float)
+  void *pre_w1 = nullptr, *pre_w2 = nullptr;  // weights as bf16 for inference
+  float* pre_X = nullptr;       // features, 32 per block row
+  uint8_t* pre_mask = nullptr;  // real dimensions per block row
+  int* pre_fallbacks = nullptr; // blocks that fell back to block-Jacobi in the last build
+  bool pre_ready = false;
   double* red = nullptr;        // per-block partial sums of reductions
   int red_cap = 0;
   ba::DevScalars* S = nullptr;  // device scalars
@@ -167,6 +176,11 @@ struct ba_problem {
 
 namespace ba {
 ba_status build_structure(Problem& P);   // structure.cu
+// learned preconditioner (precond.cu)
+ba_status precond_set_weights(Problem& P, const float* host_params);
+ba_status precond_alloc_features(Problem& P);
+template <class T> void launch_pre_features(Problem& P);
+template <class T> void launch_pre_learned(Problem& P);
 
 // raw-pointer launchers (kernels.cu) for the allocation-free PCG entry point (noalloc.cu)
 cudaError_t launch_precond_raw_f64(cudaStream_t st, int64_t na, const int32_t* row_ptr, const int32_t* col,

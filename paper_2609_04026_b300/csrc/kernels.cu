@@ -674,7 +674,7 @@ struct BlockArgs {
   const uint8_t *ent_type, *cam_fixed;
   const T* part;
   T* Sval;
-  double *b, *Dg;
+  double *b, *Dg, *sdiag;
   int64_t nbu, nc;
   double lambda;
 };
@@ -733,6 +733,8 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
     }
 #pragma unroll
     for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) a.sdiag[6 * (size_t)row + i] = (double)(T)s[i * 6 + i];
   } else {
 #pragma unroll
     for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
@@ -1484,7 +1486,7 @@ void launch_schur(Problem& P, double lambda) {
   BlockArgs<T> b;
   b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.up_wi = P.up_wi; b.col = P.col;
   b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.part = (const T*)P.part; b.Sval = (T*)P.Sval;
-  b.b = P.bvec; b.Dg = P.Dg; b.nbu = d.nbu; b.nc = d.nc; b.lambda = lambda;
+  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nbu = d.nbu; b.nc = d.nc; b.lambda = lambda;
   if (d.nbu) { ++P.launches; k_schur_blocks<T><<<nblk(d.nbu, 128), 128, 0, P.stream>>>(b); }
 }
 

@@ -344,7 +344,7 @@ ba_status build_structure(Problem& P) {
   UP(P.fres_off, fres_off); UP(P.fslot_off, fslot_off);
   UP(P.slot_ent, slot_ent); UP(P.slot_feat, slot_feat); UP(P.slot_type, slot_type);
   UP(P.feat_plane_slot, feat_plane_slot); UP(P.ent_type, ent_type);
-  UP(P.row_ptr, prow_ptr); UP(P.col, pcol);
+  UP(P.row_ptr, prow_ptr); UP(P.col, pcol); UP(P.row_len, row_len);
   UP(P.up_row, up_row); UP(P.up_full, up_full); UP(P.up_mirror, up_mirror); UP(P.up_wi, up_wi);
   UP(P.pair_a, pair_a); UP(P.pair_b, pair_b); UP(P.wi_start, wi_se);
   UP(P.cam_fixed, P.h_fixed);
