@@ -185,6 +185,21 @@ ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, int32_t* col
 ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* dvp, double* dpoint,
                           double* dline, int* pcg_iters, double* pcg_rel, double* pred);
 
+/* Batched local windows: solve n independent problems (windows) with lm_iters LM iterations each, all in one
+ * persistent kernel launch captured in a CUDA graph (local bundle adjustment after every registered image
+ * dominates incremental SfM, Section 4 / Appendix A.2).  Every window is a problem built with the calls above;
+ * all windows must use the same precision and device, and run on the stream of windows[0].  A CTA takes the
+ * next window from a device queue (largest first) and runs its iterations on the device (the same linearise /
+ * invert / Schur / PCG / back-substitute / cost / decide steps as ba_lm_step); every window keeps its own
+ * damping and accept / reject state.  A window's `converged` flag reports whether some accepted step met
+ * rel_cost_tol (iteration then continues to lm_iters).  autotune != 0 times one LM step of each candidate launch
+ * shape (threads per CTA, CTAs per SM) from the same state, keeps the fastest and caches it per (GPU,
+ * precision, size class); the chosen shape is readable with ba_batch_launch_shape(windows[0], ...).
+ * reports (n, may be NULL): iters, accepted steps, converged, initial and final cost; ms_total = the graph's
+ * device time for the whole batch. */
+ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_iters, int autotune, ba_solve_report* reports);
+ba_status ba_batch_launch_shape(const ba_problem* p, int* threads, int* grid);
+
 /* Learned correction of the block-Jacobi preconditioner.  The paper solves the reduced system directly; this
  * optional preconditioner for the PCG solve has no counterpart there.  Per diagonal block b of S (6 wide):
  *   features x_b (32): the 21 upper entries of D_b^-1/2 S_bb D_b^-1/2 (D_b = diag S_bb); over the row's

@@ -98,6 +98,8 @@ def _load():
         "ba_compute_step": (I, [P, VP, VP, VP, VP, VP, C.POINTER(I), C.POINTER(D), C.POINTER(D)]),
         "ba_pcg_solve_static": (I, [I64, I64, VP, VP, VP, VP, VP, D, I, VP, C.POINTER(I), C.POINTER(D),
                                     C.c_char_p, C.c_size_t]),
+        "ba_solve_batch": (I, [VP, I, I, I, VP]),
+        "ba_batch_launch_shape": (I, [P, C.POINTER(I), C.POINTER(I)]),
         "ba_precond_param_count": (I, []),
         "ba_precond_set_weights": (I, [P, VP, I64]),
         "ba_precond_features": (I, [P, VP, VP]),
@@ -415,3 +417,20 @@ def ba_precond_train(X, E, mask, params, adam_m, adam_v, t0, steps, batch, lr, s
     if st != BA_OK:
         raise BAError(st, "ba_precond_train failed")
     return loss.value
+
+
+# ---------------------------------------------------------------------------- batched windows
+def ba_solve_batch(problems, lm_iters=10, autotune=True):
+    """Solve independent problems (handles) in one persistent launch; returns their reports."""
+    n = len(problems)
+    arr = (C.c_void_p * n)(*problems)
+    reps = (ba_solve_report * n)()
+    st = _lib.ba_solve_batch(C.cast(arr, C.c_void_p), n, int(lm_iters), 1 if autotune else 0, C.cast(reps, C.c_void_p))
+    _check(problems[0], st)
+    return list(reps)
+
+
+def ba_batch_launch_shape(p):
+    t, g = C.c_int(), C.c_int()
+    _check(p, _lib.ba_batch_launch_shape(p, C.byref(t), C.byref(g)))
+    return t.value, g.value

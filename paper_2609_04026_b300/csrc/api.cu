@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -641,5 +642,203 @@ extern "C" ba_status ba_precond_blocks(ba_problem* p, double* blocks, int* fallb
     if (p->opt.precond == BA_PRECOND_LEARNED && p->pre_ready)
       CUDA_OR(p, cudaMemcpy(fallbacks, p->pre_fallbacks, sizeof(int), cudaMemcpyDeviceToHost));
   }
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched windows: many independent problems, one persistent launch in a CUDA graph
+#include <map>
+#include <mutex>
+
+namespace {
+struct BatchCfg {
+  int threads = 256;
+  int per_sm = 1;
+};
+std::map<std::string, BatchCfg> g_batch_cache;   // (GPU, precision, size class) -> launch shape
+std::mutex g_batch_lock;
+}  // namespace
+
+template <class T>
+static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_report* rep, int autotune) {
+  ba_problem* p0 = w[0];
+  cudaStream_t st = p0->stream;
+  const size_t dsz = window_desc_size<T>();
+  std::vector<unsigned char> host(dsz * (size_t)n);
+  std::vector<std::pair<int64_t, int>> sz;
+  int64_t max_nch = 1, max_work = 1;
+  for (int i = 0; i < n; ++i) {
+    ba_problem* p = w[i];
+    if (!p->win_state) {
+      p->win_state = p->dnew<int>(5);
+      if (!p->win_state) return set_err(p0, BA_ERR_OOM, "device allocation failed");
+    }
+    int s0[5] = {p->cur, p->have_lin ? 1 : 0, 0, 0, 0};
+    CUDA_OR(p0, cudaMemcpyAsync(p->win_state, s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+    CUDA_OR(p0, cudaStreamSynchronize(st));
+    fill_window_desc<T>(*p, host.data() + dsz * i);
+    int32_t nch = 0;
+    CUDA_OR(p0, cudaMemcpy(&nch, p->row_chunk0 + p->d.na, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    max_nch = std::max<int64_t>(max_nch, nch);
+    const int64_t work = p->d.nr + p->d.nf;
+    max_work = std::max(max_work, work);
+    sz.push_back({-work, i});
+  }
+  std::sort(sz.begin(), sz.end());
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = sz[i].second;
+  void* d_desc = p0->alloc.get(host.size());
+  int* d_order = (int*)p0->alloc.get(sizeof(int) * n);
+  int* d_queue = (int*)p0->alloc.get(sizeof(int));
+  if (!d_desc || !d_order || !d_queue) return set_err(p0, BA_ERR_OOM, "device allocation failed");
+  struct Free {
+    ba::Alloc& a; void *x, *y, *z;
+    ~Free() { cudaDeviceSynchronize(); a.put(x); a.put(y); a.put(z); }
+  } guard{p0->alloc, d_desc, d_order, d_queue};
+  CUDA_OR(p0, cudaMemcpyAsync(d_desc, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+  CUDA_OR(p0, cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  const size_t smem = sizeof(double) * 6 * (size_t)max_nch;
+  if (smem > 200 * 1024) return set_err(p0, BA_ERR_ARG, "a window's reduced system is too large for the batched kernel");
+  int dev = 0, sms = 0;
+  CUDA_OR(p0, cudaGetDevice(&dev));
+  CUDA_OR(p0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaDeviceProp prop;
+  CUDA_OR(p0, cudaGetDeviceProperties(&prop, dev));
+  int cls = 0;
+  while ((int64_t(1) << cls) < max_work) ++cls;
+  const std::string key = std::string(prop.name) + "/" + (sizeof(T) == 4 ? "f32" : "f64") + "/" + std::to_string(cls);
+  BatchCfg cfg;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> g(g_batch_lock);
+    auto it = g_batch_cache.find(key);
+    if (it != g_batch_cache.end()) { cfg = it->second; cached = true; }
+  }
+  auto grid_of = [&](const BatchCfg& c) {
+    int occ = windows_per_sm<T>(c.threads, smem);
+    return std::max(1, std::min(n, sms * std::max(1, std::min(occ, c.per_sm))));
+  };
+  // ---- autotuner: time one LM step of every candidate shape from the same state (scalars and per-window
+  // state are restored after each trial; the parameters a trial may change are the candidate set only)
+  if (autotune && !cached) {
+    std::vector<DevScalars> snapS(n);
+    std::vector<std::array<int, 5>> snapW(n);
+    for (int i = 0; i < n; ++i) {
+      CUDA_OR(p0, cudaMemcpy(&snapS[i], w[i]->S, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+      CUDA_OR(p0, cudaMemcpy(snapW[i].data(), w[i]->win_state, sizeof(int) * 5, cudaMemcpyDeviceToHost));
+    }
+    const BatchCfg cands[4] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}};
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    CUDA_OR(p0, cudaEventCreate(&e0));
+    CUDA_OR(p0, cudaEventCreate(&e1));
+    for (const BatchCfg& c : cands) {
+      if (c.per_sm > 1 && windows_per_sm<T>(c.threads, smem) < c.per_sm) continue;
+      CUDA_OR(p0, cudaEventRecord(e0, st));
+      CUDA_OR(p0, launch_windows<T>(st, d_desc, d_order, n, 1, d_queue, c.threads, grid_of(c), smem));
+      CUDA_OR(p0, cudaEventRecord(e1, st));
+      CUDA_OR(p0, cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; cfg = c; }
+      for (int i = 0; i < n; ++i) {
+        CUDA_OR(p0, cudaMemcpy(w[i]->S, &snapS[i], sizeof(DevScalars), cudaMemcpyHostToDevice));
+        CUDA_OR(p0, cudaMemcpy(w[i]->win_state, snapW[i].data(), sizeof(int) * 5, cudaMemcpyHostToDevice));
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> g(g_batch_lock);
+    g_batch_cache[key] = cfg;
+  }
+  // ---- the solve: queue reset + persistent kernel, captured once in a graph and launched
+  // capture is not allowed on the legacy default stream: capture and launch on a private stream that
+  // starts after the caller's stream has drained
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const int grid = grid_of(cfg);
+  CUDA_OR(p0, cudaStreamSynchronize(st));
+  cudaStream_t cap = nullptr;
+  CUDA_OR(p0, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  } sguard{cap};
+  CUDA_OR(p0, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = launch_windows<T>(cap, d_desc, d_order, n, iters, d_queue, cfg.threads, grid, smem);
+  cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return set_err(p0, BA_ERR_CUDA, std::string("batched graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+  }
+  CUDA_OR(p0, cudaGraphInstantiate(&exec, graph, 0));
+  cudaEvent_t e0, e1;
+  CUDA_OR(p0, cudaEventCreate(&e0));
+  CUDA_OR(p0, cudaEventCreate(&e1));
+  CUDA_OR(p0, cudaEventRecord(e0, cap));
+  CUDA_OR(p0, cudaGraphLaunch(exec, cap));
+  CUDA_OR(p0, cudaEventRecord(e1, cap));
+  CUDA_OR(p0, cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  CUDA_OR(p0, cudaGetLastError());
+  p0->batch_threads = cfg.threads;
+  p0->batch_grid = grid;
+  // ---- bring every window's host state up to date
+  for (int i = 0; i < n; ++i) {
+    ba_problem* p = w[i];
+    int sw[5];
+    CUDA_OR(p0, cudaMemcpy(sw, p->win_state, sizeof(sw), cudaMemcpyDeviceToHost));
+    CUDA_OR(p0, cudaMemcpy(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    p->cur = sw[0];
+    p->have_lin = sw[1] != 0;
+    p->have_reduced = false;
+    if (rep) {
+      ba_solve_report& r = rep[i];
+      std::memset(&r, 0, sizeof(r));
+      r.iters = sw[2];
+      r.accepted_steps = sw[3];
+      r.converged = sw[4] > 0;
+      r.cost = p->hS->E;
+      r.cost_px = p->hS->Epx;
+      r.ms_total = ms;
+    }
+  }
+  return BA_OK;
+}
+
+extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_iters, int autotune,
+                                    ba_solve_report* reports) {
+  if (!windows || n <= 0 || lm_iters <= 0) return BA_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!windows[i]) return BA_ERR_ARG;
+  ba_problem* p0 = windows[0];
+  for (int i = 0; i < n; ++i) {
+    ba_problem* p = windows[i];
+    if (p->opt.precision != p0->opt.precision)
+      return set_err(p0, BA_ERR_ARG, "all windows of a batch must use the same precision");
+    if (p->device != p0->device) return set_err(p0, BA_ERR_ARG, "all windows of a batch must be on one device");
+    ba_status s = freeze(p);
+    if (s) return set_err(p0, s, "window " + std::to_string(i) + ": " + p->err);
+    if (reports) reports[i].cost0 = p->hS->E;
+  }
+  std::vector<double> c0(n);
+  for (int i = 0; i < n; ++i) c0[i] = windows[i]->hS->E;
+  ba_status s = mixed(p0) ? solve_batch_t<float>(windows, n, lm_iters, reports, autotune)
+                          : solve_batch_t<double>(windows, n, lm_iters, reports, autotune);
+  if (s == BA_OK && reports)
+    for (int i = 0; i < n; ++i) reports[i].cost0 = c0[i];
+  return s;
+}
+
+extern "C" ba_status ba_batch_launch_shape(const ba_problem* p, int* threads, int* grid) {
+  if (!p) return BA_ERR_ARG;
+  if (threads) *threads = p->batch_threads;
+  if (grid) *grid = p->batch_grid;
   return BA_OK;
 }

@@ -165,6 +165,8 @@ struct ba_problem {
   uint8_t* pre_mask = nullptr;  // real dimensions per block row
   int* pre_fallbacks = nullptr; // blocks that fell back to block-Jacobi in the last build
   bool pre_ready = false;
+  int* win_state = nullptr;     // batched windows: device copy of (set, linearised, steps, accepted, converged)
+  int batch_threads = 0, batch_grid = 0;  // launch shape of the last batched solve started from this problem
   double* red = nullptr;        // per-block partial sums of reductions
   int red_cap = 0;
   ba::DevScalars* S = nullptr;  // device scalars
@@ -176,6 +178,12 @@ struct ba_problem {
 
 namespace ba {
 ba_status build_structure(Problem& P);   // structure.cu
+// batched windows (kernels.cu, launched from batch.cu)
+template <class T> void fill_window_desc(Problem& P, void* out);
+template <class T> size_t window_desc_size();
+template <class T> cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int iters,
+                                              int* queue, int threads, int grid, size_t smem);
+template <class T> int windows_per_sm(int threads, size_t smem);
 // learned preconditioner (precond.cu)
 ba_status precond_set_weights(Problem& P, const float* host_params);
 ba_status precond_alloc_features(Problem& P);

@@ -170,9 +170,7 @@ __device__ void tangent_basis_d(const double* n, double* b1, double* b2) {
 
 // cams: src n x 12 -> D (double) and optionally W (working type) with CAM_STRIDE
 template <class T>
-__global__ void k_derive_cams(int64_t nc, const double* __restrict__ src, double* __restrict__ D, T* __restrict__ W) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nc) return;
+__device__ void derive_cam(const double* __restrict__ src, double* __restrict__ D, T* __restrict__ W, int64_t i) {
   const double* c = src + 12 * i;
   double o[17];
   quat_to_R(c, o);
@@ -183,12 +181,16 @@ __global__ void k_derive_cams(int64_t nc, const double* __restrict__ src, double
     for (int k = 0; k < 17; ++k) W[CAM_STRIDE * i + k] = (T)o[k];
 }
 
+template <class T>
+__global__ void k_derive_cams(int64_t nc, const double* __restrict__ src, double* __restrict__ D, T* __restrict__ W) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nc) derive_cam<T>(src, D, W, i);
+}
+
 // groups: planes (n, w) then VPs v -> [n|v (3), w|0, b1 (3), b2 (3)] with GRP_STRIDE
 template <class T>
-__global__ void k_derive_groups(int64_t npl, int64_t nv, const double* __restrict__ pln, const double* __restrict__ vps,
-                                double* __restrict__ D, T* __restrict__ W) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= npl + nv) return;
+__device__ void derive_group(int64_t npl, const double* __restrict__ pln, const double* __restrict__ vps,
+                             double* __restrict__ D, T* __restrict__ W, int64_t i) {
   double o[10];
   if (i < npl) {
     const double* q = pln + 4 * i;
@@ -201,6 +203,13 @@ __global__ void k_derive_groups(int64_t npl, int64_t nv, const double* __restric
   for (int k = 0; k < 10; ++k) D[GRP_STRIDE * i + k] = o[k];
   if (W)
     for (int k = 0; k < 10; ++k) W[GRP_STRIDE * i + k] = (T)o[k];
+}
+
+template <class T>
+__global__ void k_derive_groups(int64_t npl, int64_t nv, const double* __restrict__ pln, const double* __restrict__ vps,
+                                double* __restrict__ D, T* __restrict__ W) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < npl + nv) derive_group<T>(npl, pln, vps, D, W, i);
 }
 
 __global__ void k_convert(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -230,9 +239,7 @@ struct LinArgs {
 };
 
 template <class T, int KF>
-__global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int64_t f1) {
-  int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= f1) return;
+__device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   constexpr int NV = KF * (KF + 1) / 2;
   T V[NV], gf[KF];
@@ -442,6 +449,12 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int
   for (int i = 0; i < KF; ++i) go[i] = (double)gf[i];
 }
 
+template <class T, int KF>
+__global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int64_t f1) {
+  int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f < f1) linearize_feature<T, KF>(a, f);
+}
+
 // ============================================================================
 // K2: damped landmark inverse and the per-slot Y, b parts
 // ============================================================================
@@ -629,9 +642,7 @@ __device__ __forceinline__ void direct_terms(const SchurArgs<T>& a, int ea, int 
 // loads in flight.  pair_b carries a flag in bit 31: the pair is (camera slot, plane slot) of one
 // feature and its direct J_cam^T w J_plane block is added.
 template <class T>
-__global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
-  int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (w >= a.nwi) return;
+__device__ void schur_item(const SchurArgs<T>& a, int64_t w) {
   const int s0 = a.wi_se[2 * w], s1 = a.wi_se[2 * w + 1];
   T acc[6][6], bacc[6], hacc[6];
 #pragma unroll
@@ -669,6 +680,12 @@ __global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
 }
 
 template <class T>
+__global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
+  int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w < a.nwi) schur_item<T>(a, w);
+}
+
+template <class T>
 struct BlockArgs {
   const int32_t *up_row, *up_full, *up_mirror, *up_wi, *col;
   const uint8_t *ent_type, *cam_fixed;
@@ -680,9 +697,7 @@ struct BlockArgs {
 };
 
 template <class T>
-__global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
-  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (u >= a.nbu) return;
+__device__ void schur_block(const BlockArgs<T>& a, int64_t u) {
   const int row = a.up_row[u];
   const int fpos = a.up_full[u];
   const bool diag = a.col[fpos] == row;
@@ -746,15 +761,19 @@ __global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u < a.nbu) schur_block<T>(a, u);
+}
+
 // ============================================================================
 // K4: block-Jacobi preconditioner
 // ============================================================================
 // SOA: S in the library's padded interleaved storage; otherwise 36 contiguous values per block
 template <class T, bool SOA>
-__global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                          const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S) {
-  int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= na) return;
+__device__ void precond_row(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S, int64_t a) {
   int pos = -1;
   for (int q = row_ptr[a]; q < row_ptr[a + 1]; ++q)
     if (col[q] == a) { pos = q; break; }
@@ -777,6 +796,13 @@ __global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < 6; ++j) o[i * 6 + j] = (T)Mi[i][j];
+}
+
+template <class T, bool SOA>
+__global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                          const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S) {
+  int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a < na) precond_row<T, SOA>(row_ptr, col, Sval, Minv, S, a);
 }
 
 // ============================================================================
@@ -1254,10 +1280,8 @@ struct CandArgs {
   int64_t nc, np, nl, npl, nv;
 };
 
-__global__ void k_candidate(CandArgs a) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t n0 = a.nc, n1 = n0 + a.npl, n2 = n1 + a.nv, n3 = n2 + a.np, n4 = n3 + a.nl;
-  if (i >= n4) return;
+__device__ void candidate_item(const CandArgs& a, int64_t i) {
+  const int64_t n0 = a.nc, n1 = n0 + a.npl, n2 = n1 + a.nv, n3 = n2 + a.np;
   if (i < n0) {
     const double* c = a.cam + 12 * i;
     double* o = a.cam2 + 12 * i;
@@ -1333,6 +1357,11 @@ __global__ void k_candidate(CandArgs a) {
   }
 }
 
+__global__ void k_candidate(CandArgs a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.nc + a.npl + a.nv + a.np + a.nl) candidate_item(a, i);
+}
+
 struct CostArgs {
   const int8_t* rkind;
   const int32_t *rcam, *rfeat, *rgrp;
@@ -1344,10 +1373,8 @@ struct CostArgs {
   int candidate;
 };
 
-__global__ void __launch_bounds__(256) k_cost(CostArgs a) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double v[2] = {0, 0};
-  if (i < a.nr) {
+__device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
+  {
     const int kind = a.rkind[i];
     const int cid = a.rcam[i];
     const int64_t f = a.rfeat[i];
@@ -1378,6 +1405,12 @@ __global__ void __launch_bounds__(256) k_cost(CostArgs a) {
       v[1] = kind == R_VP ? 0.0 : e;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_cost(CostArgs a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v[2] = {0, 0};
+  if (i < a.nr) cost_residual(a, i, v);
   double tot[2];
   if (grid_reduce<2>(v, a.red, &a.S->counter[4], tot) && threadIdx.x == 0) {
     if (a.candidate) { a.S->Enew = tot[0]; a.S->Epxnew = tot[1]; }
@@ -1393,7 +1426,7 @@ struct DecideArgs {
   double min_gain, lmin, lmax;
 };
 
-__global__ void k_decide(DecideArgs a) {
+__device__ void decide(const DecideArgs& a) {
   DevScalars* S = a.S;
   double pred = S->pred;
   double gain = pred > 0 ? (S->E - S->Enew) / pred : -INFINITY;
@@ -1410,6 +1443,8 @@ __global__ void k_decide(DecideArgs a) {
     S->nu *= 2.0;
   }
 }
+
+__global__ void k_decide(DecideArgs a) { decide(a); }
 
 // ============================================================================
 // launchers
@@ -1594,6 +1629,345 @@ void launch_decide(Problem& P) {
   ++P.launches;
   k_decide<<<1, 1, 0, P.stream>>>(a);
 }
+
+// ============================================================================
+// K10: many independent windows, one persistent launch
+// ============================================================================
+// Every window is a frozen problem of its own (structure, slots, S pattern, PCG chunking).  A CTA takes
+// the next window from a queue (largest first) and runs all its LM iterations on the device: the same
+// per-item bodies as the grid kernels above, strided over the CTA's threads, with CTA barriers between
+// phases, a single-CTA PCG, and the accept / reject decision on thread 0.
+template <class T>
+struct WinDesc {
+  int64_t nc, npl, nv, np, nl, nf, na, nr, nwi, nbu, nch;
+  LinArgs<T> lin;
+  InvArgs<T> inv;
+  SchurArgs<T> schur;
+  BlockArgs<T> blocks;
+  BackArgs<T> back;
+  CandArgs cand;
+  CostArgs cost;
+  DecideArgs dec;
+  double *cam[2], *pts[2], *lin_[2], *pln[2], *vps[2], *camD[2], *grpD[2];
+  T *camT, *grpT, *ptsT, *linT;
+  const int32_t *row_ptr, *col, *row_chunk0, *chunk_beg;
+  const T* Sval;
+  T* Minv;
+  const double* b;
+  double *x, *r, *z, *p, *Ap;
+  float2* phl;
+  DevScalars* S;
+  int* state;          // [0] current parameter set, [1] linearisation valid, [2] steps, [3] accepted, [4] converged
+  double pcg_tol, rel_cost_tol;
+  int pcg_max_iters;
+};
+
+template <class T, int NT>
+__device__ void window_pcg(const WinDesc<T>& W, double* chunk_y, double* red2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  PcgArgs<T> a;
+  a.p = W.p;
+  a.phl = W.phl;
+  const int64_t na = W.na;
+  double v0 = 0, v1 = 0;
+  for (int64_t row = threadIdx.x; row < na; row += NT) {
+    double rv[6], zv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { rv[i] = W.b[6 * row + i]; W.x[6 * row + i] = 0; W.r[6 * row + i] = rv[i]; }
+    apply_block(W.Minv + (size_t)row * BS2, rv, zv);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      W.z[6 * row + i] = zv[i];
+      W.p[6 * row + i] = zv[i];
+      if (W.phl) W.phl[6 * row + i] = split2(zv[i]);
+      v0 += rv[i] * zv[i];
+      v1 += rv[i] * rv[i];
+    }
+  }
+  cta_sum2<NT>(v0, v1, red2);
+  double rz = red2[0];
+  const double bb = red2[1];
+  const double tol2 = W.pcg_tol * W.pcg_tol * bb;
+  double rr = bb;
+  int it = 0;
+  bool go = bb > 0;
+  while (go) {
+    for (int64_t q = warp; q < W.nch; q += NW) {
+      DotAcc<T> acc[6];
+      const int blk = W.chunk_beg[q] + lane;
+      const T* Bg = W.Sval + s_idx(blk, 0);
+      T B[36];
+#pragma unroll
+      for (int k = 0; k < 36; ++k) B[k] = Bg[k * 32];
+      spmv_block(B, a, W.col[blk], acc);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double y = warp_sum_acc(acc[i]);
+        if (lane == 0) chunk_y[6 * q + i] = y;
+      }
+    }
+    __syncthreads();
+    double pap = 0;
+    for (int64_t row = threadIdx.x; row < na; row += NT) {
+      double y[6] = {0, 0, 0, 0, 0, 0};
+      for (int q = W.row_chunk0[row]; q < W.row_chunk0[row + 1]; ++q)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] += chunk_y[6 * q + i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        W.Ap[6 * row + i] = y[i];
+        pap += y[i] * W.p[6 * row + i];
+      }
+    }
+    cta_sum2<NT>(pap, 0.0, red2);
+    const double alpha = rz / red2[0];
+    v0 = 0; v1 = 0;
+    for (int64_t row = threadIdx.x; row < na; row += NT) {
+      double rv[6], zv[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        W.x[6 * row + i] += alpha * W.p[6 * row + i];
+        rv[i] = W.r[6 * row + i] - alpha * W.Ap[6 * row + i];
+        W.r[6 * row + i] = rv[i];
+      }
+      apply_block(W.Minv + (size_t)row * BS2, rv, zv);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        W.z[6 * row + i] = zv[i];
+        v0 += rv[i] * rv[i];
+        v1 += rv[i] * zv[i];
+      }
+    }
+    cta_sum2<NT>(v0, v1, red2);
+    rr = red2[0];
+    const double rz_new = red2[1];
+    ++it;
+    if (rr <= tol2 || it >= W.pcg_max_iters || !(rr == rr)) break;
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int64_t k = threadIdx.x; k < 6 * na; k += NT) {
+      const double pk = W.z[k] + beta * W.p[k];
+      W.p[k] = pk;
+      if (W.phl) W.phl[k] = split2(pk);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    W.S->iters = it;
+    W.S->rr = rr;
+    W.S->bnorm2 = bb;
+  }
+  __syncthreads();
+}
+
+template <class T, int NT>
+__device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
+  __shared__ double red2[2];
+  __shared__ int s_cur, s_lin;
+  if (threadIdx.x == 0) { s_cur = W.state[0]; s_lin = W.state[1]; }
+  __syncthreads();
+  const int cur = s_cur, nxt = 1 - s_cur;
+  const bool flt = sizeof(T) == sizeof(float);
+  // ---- linearise at the current parameters (after an accepted step only)
+  if (!s_lin) {
+    for (int64_t i = threadIdx.x; i < W.nc; i += NT) derive_cam<T>(W.cam[cur], W.camD[cur], flt ? W.camT : nullptr, i);
+    for (int64_t i = threadIdx.x; i < W.npl + W.nv; i += NT)
+      derive_group<T>(W.npl, W.pln[cur], W.vps[cur], W.grpD[cur], flt ? W.grpT : nullptr, i);
+    if (flt) {
+      for (int64_t i = threadIdx.x; i < 3 * W.np; i += NT) ((float*)W.ptsT)[i] = (float)W.pts[cur][i];
+      for (int64_t i = threadIdx.x; i < 6 * W.nl; i += NT) ((float*)W.linT)[i] = (float)W.lin_[cur][i];
+    }
+    __syncthreads();
+    LinArgs<T> la = W.lin;
+    if (!flt) {
+      la.cam = (const T*)W.camD[cur]; la.grp = (const T*)W.grpD[cur];
+      la.pts = (const T*)W.pts[cur]; la.lin = (const T*)W.lin_[cur];
+    }
+    for (int64_t f = threadIdx.x; f < W.np; f += NT) linearize_feature<T, 3>(la, f);
+    for (int64_t f = W.np + threadIdx.x; f < W.nf; f += NT) linearize_feature<T, 4>(la, f);
+    __syncthreads();
+  }
+  const double lam = W.S->lambda;
+  // ---- damp + invert the landmark blocks, Schur complement, block-Jacobi
+  {
+    InvArgs<T> ia = W.inv;
+    ia.lambda = lam;
+    for (int64_t f = threadIdx.x; f < W.nf; f += NT) {
+      if (f < W.np) invert_feature<T, 3>(ia, f);
+      else invert_feature<T, 4>(ia, f);
+    }
+  }
+  __syncthreads();
+  for (int64_t w = threadIdx.x; w < W.nwi; w += NT) schur_item<T>(W.schur, w);
+  __syncthreads();
+  {
+    BlockArgs<T> ba = W.blocks;
+    ba.lambda = lam;
+    for (int64_t u = threadIdx.x; u < W.nbu; u += NT) schur_block<T>(ba, u);
+  }
+  __syncthreads();
+  for (int64_t r = threadIdx.x; r < W.na; r += NT) precond_row<T, true>(W.row_ptr, W.col, W.Sval, W.Minv, W.S, r);
+  __syncthreads();
+  // ---- PCG, back-substitution and predicted decrease
+  window_pcg<T, NT>(W, chunk_y, red2);
+  double g = 0, h = 0;
+  for (int64_t f = threadIdx.x; f < W.nf; f += NT) {
+    double gi = 0, hi = 0;
+    if (f < W.np) backsub_feature<T, 3>(W.back, f, gi, hi);
+    else backsub_feature<T, 4>(W.back, f, gi, hi);
+    g += gi; h += hi;
+  }
+  cta_sum2<NT>(g, h, red2);
+  if (threadIdx.x == 0) { W.S->gTd = red2[0]; W.S->dHd = red2[1]; W.S->pred = -red2[0] - 0.5 * red2[1]; }
+  // ---- candidate, its FP64 cost, decision
+  {
+    CandArgs ca = W.cand;
+    ca.cam = W.cam[cur]; ca.pts = W.pts[cur]; ca.lin = W.lin_[cur]; ca.pln = W.pln[cur]; ca.vps = W.vps[cur];
+    ca.cam2 = W.cam[nxt]; ca.pts2 = W.pts[nxt]; ca.lin2 = W.lin_[nxt]; ca.pln2 = W.pln[nxt]; ca.vps2 = W.vps[nxt];
+    const int64_t tot = W.nc + W.npl + W.nv + W.np + W.nl;
+    for (int64_t i = threadIdx.x; i < tot; i += NT) candidate_item(ca, i);
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < W.nc; i += NT) derive_cam<T>(W.cam[nxt], W.camD[nxt], nullptr, i);
+  for (int64_t i = threadIdx.x; i < W.npl + W.nv; i += NT)
+    derive_group<T>(W.npl, W.pln[nxt], W.vps[nxt], W.grpD[nxt], nullptr, i);
+  __syncthreads();
+  {
+    CostArgs co = W.cost;
+    co.camD = W.camD[nxt]; co.grpD = W.grpD[nxt]; co.pts = W.pts[nxt]; co.lin = W.lin_[nxt];
+    double e = 0, epx = 0;
+    for (int64_t i = threadIdx.x; i < W.nr; i += NT) {
+      double v[2] = {0, 0};
+      cost_residual(co, i, v);
+      e += v[0]; epx += v[1];
+    }
+    cta_sum2<NT>(e, epx, red2);
+  }
+  if (threadIdx.x == 0) {
+    DevScalars* S = W.S;
+    S->Enew = red2[0];
+    S->Epxnew = red2[1];
+    decide(W.dec);
+    W.state[2] += 1;
+    if (S->accepted) {
+      const double rel = fabs(S->Epx - S->Epxnew) / fmax(S->Epx, 1e-300);
+      if (rel < W.rel_cost_tol && !W.state[4]) W.state[4] = W.state[2];
+      S->E = S->Enew;
+      S->Epx = S->Epxnew;
+      W.state[0] = nxt;
+      W.state[1] = 0;
+      W.state[3] += 1;
+    } else {
+      W.state[1] = 1;
+    }
+  }
+  __syncthreads();
+}
+
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, 1) k_windows(const WinDesc<T>* __restrict__ descs, const int* __restrict__ order,
+                                                   int nwin, int iters, int* queue) {
+  extern __shared__ double chunk_y[];
+  __shared__ int s_w;
+  for (;;) {
+    if (threadIdx.x == 0) s_w = atomicAdd(queue, 1);
+    __syncthreads();
+    const int w = s_w;
+    __syncthreads();
+    if (w >= nwin) break;
+    const WinDesc<T>& W = descs[order[w]];
+    for (int it = 0; it < iters; ++it) window_step<T, NT>(W, chunk_y);
+  }
+}
+
+template <class T>
+void fill_window_desc(Problem& P, void* out) {
+  WinDesc<T>& W = *(WinDesc<T>*)out;
+  const Dims& d = P.d;
+  W.nc = d.nc; W.npl = d.npl; W.nv = d.nv; W.np = d.np; W.nl = d.nl; W.nf = d.nf; W.na = d.na; W.nr = d.nr;
+  W.nwi = d.nwi; W.nbu = d.nbu;
+  std::vector<int32_t> rc(1);
+  W.nch = 0;
+  cudaMemcpy(&rc[0], P.row_chunk0 + d.na, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  W.nch = rc[0];
+  const bool flt = sizeof(T) == sizeof(float);
+  LinArgs<T>& a = W.lin;
+  a.rkind = P.rkind; a.cam_mask = P.cam_fixed; a.rcam = P.rcam; a.rgrp = P.rgrp; a.rslot_c = P.rslot_c;
+  a.rslot_g = P.rslot_g; a.fres_off = P.fres_off; a.feat_plane_slot = P.feat_plane_slot;
+  a.meas = flt ? (const T*)P.measT : (const T*)P.meas64;
+  a.cam = (const T*)P.camT; a.grp = (const T*)P.grpT; a.pts = (const T*)P.ptsT; a.lin = (const T*)P.linT;
+  a.npl = d.npl; a.np = d.np;
+  a.W = (T*)P.slotW; a.H = (T*)P.slotH; a.G = (T*)P.slotG; a.C = (T*)P.slotC; a.V = P.featV; a.g = P.featg;
+  a.loss = make_loss(P.opt);
+  InvArgs<T>& ia = W.inv;
+  ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
+  ia.Vinv = P.featVinv; ia.z = P.featz; ia.Y = (T*)P.slotY; ia.B = (T*)P.slotB; ia.np = d.np; ia.nf = d.nf;
+  ia.lambda = 0; ia.S = P.S;
+  SchurArgs<T>& sa = W.schur;
+  sa.pair_a = P.pair_a; sa.pair_b = P.pair_b; sa.wi_se = P.wi_start; sa.W = (const T*)P.slotW; sa.Y = (const T*)P.slotY;
+  sa.H = (const T*)P.slotH; sa.B = (const T*)P.slotB; sa.C = (const T*)P.slotC; sa.part = (T*)P.part; sa.nwi = d.nwi;
+  sa.line_slot0 = P.line_slot0;
+  BlockArgs<T>& b = W.blocks;
+  b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.up_wi = P.up_wi; b.col = P.col;
+  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.part = (const T*)P.part; b.Sval = (T*)P.Sval;
+  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nbu = d.nbu; b.nc = d.nc; b.lambda = 0;
+  BackArgs<T>& k = W.back;
+  k.fslot_off = P.fslot_off; k.slot_ent = P.slot_ent; k.feat_plane_slot = P.feat_plane_slot; k.slot_type = P.slot_type;
+  k.V = P.featV; k.Vinv = P.featVinv; k.g = P.featg; k.x = P.x; k.W = (const T*)P.slotW; k.H = (const T*)P.slotH;
+  k.G = (const T*)P.slotG; k.C = (const T*)P.slotC; k.df = P.dfeat; k.np = d.np; k.nf = d.nf; k.S = P.S; k.red = P.red;
+  CandArgs& c = W.cand;
+  c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
+  CostArgs& co = W.cost;
+  co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64;
+  co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;
+  W.dec = DecideArgs{P.S, P.opt.min_gain, P.opt.lambda_min, P.opt.lambda_max};
+  for (int s = 0; s < 2; ++s) {
+    W.cam[s] = P.ps[s].cam; W.pts[s] = P.ps[s].pts; W.lin_[s] = P.ps[s].lin; W.pln[s] = P.ps[s].pln;
+    W.vps[s] = P.ps[s].vps; W.camD[s] = P.ps[s].camD; W.grpD[s] = P.ps[s].grpD;
+  }
+  W.camT = (T*)P.camT; W.grpT = (T*)P.grpT; W.ptsT = (T*)P.ptsT; W.linT = (T*)P.linT;
+  W.row_ptr = P.row_ptr; W.col = P.col; W.row_chunk0 = P.row_chunk0; W.chunk_beg = P.chunk_beg;
+  W.Sval = (const T*)P.Sval; W.Minv = (T*)P.Minv; W.b = P.bvec; W.x = P.x; W.r = P.r; W.z = P.z; W.p = P.p;
+  W.Ap = P.Ap; W.phl = flt ? P.phl : nullptr; W.S = P.S; W.state = P.win_state;
+  W.pcg_tol = P.opt.pcg_rel_tol; W.rel_cost_tol = P.opt.rel_cost_tol; W.pcg_max_iters = P.opt.pcg_max_iters;
+}
+
+template <class T>
+size_t window_desc_size() { return sizeof(WinDesc<T>); }
+
+template <class T, int NT>
+cudaError_t launch_windows_nt(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
+                              int grid, size_t smem) {
+  cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaMemsetAsync(queue, 0, sizeof(int), st);
+  k_windows<T, NT><<<grid, NT, smem, st>>>((const WinDesc<T>*)descs, order, nwin, iters, queue);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
+                           int threads, int grid, size_t smem) {
+  if (threads == 128) return launch_windows_nt<T, 128>(st, descs, order, nwin, iters, queue, grid, smem);
+  return launch_windows_nt<T, 256>(st, descs, order, nwin, iters, queue, grid, smem);
+}
+
+template <class T>
+int windows_per_sm(int threads, size_t smem) {
+  int nb = 0;
+  if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_windows<T, 128>, 128, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_windows<T, 256>, 256, smem);
+  return nb;
+}
+
+template void fill_window_desc<float>(Problem&, void*);
+template void fill_window_desc<double>(Problem&, void*);
+template size_t window_desc_size<float>();
+template size_t window_desc_size<double>();
+template cudaError_t launch_windows<float>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t);
+template cudaError_t launch_windows<double>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t);
+template int windows_per_sm<float>(int, size_t);
+template int windows_per_sm<double>(int, size_t);
 
 #define INST(T)                                         \
   template void launch_prepare<T>(Problem&, bool);      \

@@ -99,6 +99,21 @@ def config(name: str, seed: int | None = None, **over) -> SceneConfig:
     return c
 
 
+def window_config(i: int, seed: int = 4000, max_features: int = 20_000) -> SceneConfig:
+    """The i-th local-BA window of the batched workload: cameras uniform in 5..40, features log-uniform in
+    200..max_features (70 % points, 30 % lines), 0..8 groups split between planes and VPs."""
+    rng = np.random.default_rng(seed * 100_003 + i)
+    nc = int(rng.integers(5, 41))
+    nfeat = int(np.exp(rng.uniform(np.log(200), np.log(max_features))))
+    ng = int(rng.integers(0, 9))
+    npl = int(rng.integers(0, ng + 1))
+    return SceneConfig(name=f"window{i}", n_cams=nc, ring=False, n_points=int(0.7 * nfeat),
+                       n_lines=max(nfeat - int(0.7 * nfeat), 1), n_planes=npl, n_vps=ng - npl, track_min=2,
+                       track_max=8, track_mean=4.0, k_near=min(12, nc),
+                       n_wire_edges=(max(2, nfeat // 40) if npl > 0 else 0), sigma_px=0.7, outlier_frac=0.03,
+                       seed=seed * 7919 + i)
+
+
 # --------------------------------------------------------------------------
 # small geometric helpers used only to synthesise data
 # --------------------------------------------------------------------------
