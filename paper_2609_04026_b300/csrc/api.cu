@@ -261,7 +261,7 @@ static ba_status freeze(ba_problem* p) {
   };
   bool ok = true;
   ok &= A(p->slotW, T * SW * (size_t)d.ne);
-  ok &= A(p->slotY, T * SW * (size_t)d.ne);
+  ok &= A(p->slotZ, T * SW * (size_t)d.ne);
   ok &= A(p->slotH, T * SH * (size_t)d.ne);
   ok &= A(p->slotG, T * SG * (size_t)d.ne);
   ok &= A(p->slotB, T * SG * (size_t)d.ne);

@@ -151,7 +151,7 @@ struct ba_problem {
   size_t pcg_smem = 0;
   cudaError_t pcg_err = cudaSuccess;
   // numeric arrays
-  void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotY = nullptr, *slotB = nullptr;
+  void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotZ = nullptr, *slotB = nullptr;
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featz = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr, *part = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;

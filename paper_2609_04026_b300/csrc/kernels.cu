@@ -96,10 +96,10 @@ __device__ bool grid_reduce(double (&v)[NV], double* red, unsigned int* counter,
 // ============================================================================
 __host__ __device__ constexpr int up_idx(int i, int j, int k) { return i * k - i * (i - 1) / 2 + (j - i); }
 
-// Cholesky inverse of an n x n SPD matrix given by its upper triangle (up_idx layout).
-// Returns false if a pivot is not positive.
+// Cholesky inverse of an n x n SPD matrix given by its upper triangle (up_idx layout): A = L L^T,
+// Linv = L^-1 (lower triangular) and Ainv = L^-T L^-1.  Returns false if a pivot is not positive.
 template <int N>
-__device__ bool chol_inverse(const double* Aup, double (&Ainv)[N][N]) {
+__device__ bool chol_inverse(const double* Aup, double (&Ainv)[N][N], double (&Li)[N][N]) {
   double L[N][N];
 #pragma unroll
   for (int i = 0; i < N; ++i)
@@ -123,7 +123,6 @@ __device__ bool chol_inverse(const double* Aup, double (&Ainv)[N][N]) {
     }
   }
   // invert L (lower triangular)
-  double Li[N][N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
@@ -149,6 +148,12 @@ __device__ bool chol_inverse(const double* Aup, double (&Ainv)[N][N]) {
       Ainv[j][i] = s;
     }
   return true;
+}
+
+template <int N>
+__device__ bool chol_inverse(const double* Aup, double (&Ainv)[N][N]) {
+  double Li[N][N];
+  return chol_inverse<N>(Aup, Ainv, Li);
 }
 
 // ============================================================================
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int
 }
 
 // ============================================================================
-// K2: damped landmark inverse and the per-slot Y, b parts
+// K2: damped landmark inverse, the whitened slot blocks Z = L^-1 W and the per-slot b parts
 // ============================================================================
 template <class T>
 struct InvArgs {
@@ -464,14 +469,14 @@ struct InvArgs {
   const double *V, *g;
   const T *W, *G;
   double *Vinv, *z;
-  T *Y, *B;
+  T *Z, *B;
   int64_t np, nf;
   double lambda;
   DevScalars* S;
 };
 
 template <int K>
-__device__ void invert_damped(const double* Vup, double lambda, double (&Vi)[K][K], int* flag) {
+__device__ void invert_damped(const double* Vup, double lambda, double (&Vi)[K][K], double (&Li)[K][K], int* flag) {
   double A[K * (K + 1) / 2];
 #pragma unroll
   for (int i = 0; i < K * (K + 1) / 2; ++i) A[i] = Vup[i];
@@ -480,7 +485,7 @@ __device__ void invert_damped(const double* Vup, double lambda, double (&Vi)[K][
     double dgi = fmin(fmax(A[up_idx(i, i, K)], 1e-6), 1e32);
     A[up_idx(i, i, K)] += lambda * dgi;
   }
-  if (!chol_inverse<K>(A, Vi)) {
+  if (!chol_inverse<K>(A, Vi, Li)) {
     // rounding made the damped block indefinite: add damping until it factorises
     *flag = 1;
     double tr = 0;
@@ -490,21 +495,59 @@ __device__ void invert_damped(const double* Vup, double lambda, double (&Vi)[K][
     for (int t = 0; t < 60; ++t) {
 #pragma unroll
       for (int i = 0; i < K; ++i) A[up_idx(i, i, K)] += extra;
-      if (chol_inverse<K>(A, Vi)) return;
+      if (chol_inverse<K>(A, Vi, Li)) return;
       extra *= 10;
     }
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll
-      for (int j = 0; j < K; ++j) Vi[i][j] = 0;
+      for (int j = 0; j < K; ++j) { Vi[i][j] = 0; Li[i][j] = 0; }
   }
+}
+
+// Z = L^-1 W for one slot (K x 6, rows of W at stride 6).  With a float working type the product is
+// formed in double-single arithmetic on the float pipes (L^-1 split into hi + lo floats, exact products
+// by FMA, TwoSum accumulation) and rounded to float once: rounding V^-1 or L^-1 to float before the
+// product would multiply the error by the condition number of V_f, and the Schur complement of a
+// poorly observed feature then loses the cancellation that makes its contribution small.
+template <int K>
+__device__ __forceinline__ void whiten_slot(const double (&Li)[K][K], const double* W, double* Z) {
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double s = 0;
+#pragma unroll
+      for (int k = 0; k <= i; ++k) s = fma(Li[i][k], W[k * 6 + j], s);
+      Z[i * 6 + j] = s;
+    }
+}
+template <int K>
+__device__ __forceinline__ void whiten_slot(const float (&Lh)[K][K], const float (&Ll)[K][K], const float* W, float* Z) {
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float hi = 0, lo = 0;
+#pragma unroll
+      for (int k = 0; k <= i; ++k) {
+        const float w = W[k * 6 + j];
+        const float ph = Lh[i][k] * w;
+        const float pe = fmaf(Lh[i][k], w, -ph);
+        const float sm = hi + ph;
+        const float bp = sm - hi;
+        lo += ((hi - (sm - bp)) + (ph - bp)) + fmaf(Ll[i][k], w, pe);
+        hi = sm;
+      }
+      Z[i * 6 + j] = hi + lo;
+    }
 }
 
 template <class T, int K>
 __device__ void invert_feature(const InvArgs<T>& a, int64_t f) {
-  double Vi[K][K];
+  double Vi[K][K], Li[K][K];
   int flag = 0;
-  invert_damped<K>(a.V + 10 * f, a.lambda, Vi, &flag);
+  invert_damped<K>(a.V + 10 * f, a.lambda, Vi, Li, &flag);
   if (flag) atomicOr(&a.S->flags, 1);
   double gz[K];
 #pragma unroll
@@ -521,37 +564,40 @@ __device__ void invert_feature(const InvArgs<T>& a, int64_t f) {
     for (int j = i; j < K; ++j) vo[up_idx(i, j, K)] = Vi[i][j];
 #pragma unroll
   for (int i = 0; i < K; ++i) a.z[4 * f + i] = gz[i];
-  T Vt[K][K], zt[K];
+  // u = L^-1 g_f: the slot's share of b is -G_e + Z_e^T u  (= -G_e + W_e^T V^-1 g_f)
+  T ut[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    zt[i] = (T)gz[i];
+    double s = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) Vt[i][j] = (T)Vi[i][j];
+    for (int k = 0; k <= i; ++k) s += Li[i][k] * a.g[4 * f + k];
+    ut[i] = (T)s;
   }
+  T Lh[K][K], Ll[K][K];
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      Lh[i][j] = (T)Li[i][j];
+      Ll[i][j] = (T)(Li[i][j] - (double)Lh[i][j]);
+    }
   for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
     const T* W = a.W + (size_t)e * SW;
-    T w[K][6];
+    T w[K * 6], z[K * 6];
 #pragma unroll
-    for (int i = 0; i < K; ++i)
+    for (int i = 0; i < K * 6; ++i) w[i] = W[i];
+    if constexpr (sizeof(T) == 8) whiten_slot<K>(Li, (const double*)w, (double*)z);
+    else whiten_slot<K>(Lh, Ll, w, z);
+    T* Z = a.Z + (size_t)e * SW;
 #pragma unroll
-      for (int j = 0; j < 6; ++j) w[i][j] = W[i * 6 + j];
-    T* Y = a.Y + (size_t)e * SW;
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        T s = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) s += Vt[i][k] * w[k][j];
-        Y[i * 6 + j] = s;
-      }
+    for (int i = 0; i < K * 6; ++i) Z[i] = z[i];
     const T* G = a.G + (size_t)e * SG;
     T* B = a.B + (size_t)e * SG;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       T s = -G[j];
 #pragma unroll
-      for (int k = 0; k < K; ++k) s += w[k][j] * zt[k];
+      for (int k = 0; k < K; ++k) s += z[k * 6 + j] * ut[k];
       B[j] = s;
     }
   }
@@ -571,7 +617,7 @@ __global__ void __launch_bounds__(128) k_invert(InvArgs<T> a) {
 template <class T>
 struct SchurArgs {
   const int32_t *pair_a, *pair_b, *wi_se;
-  const T *W, *Y, *H, *B, *C;
+  const T *Z, *H, *B, *C;
   T* part;
   int64_t nwi;
   int line_slot0;   // slots of lines start here (slots are stored feature-major, points first)
@@ -595,8 +641,8 @@ __device__ __forceinline__ void load24(const double* __restrict__ p, double (&v)
   }
 }
 
-// acc -= Y^T W over the first k rows (k = 3 for points, 4 for lines; the 4th row of a point's Y is
-// never written and must not be read into the sum)
+// acc -= Za^T Zb over the first k rows (k = 3 for points, 4 for lines; the 4th row of a point's Z is
+// never written and must not be read into the sum).  W_a V^-1 W_b^T = (L^-1 W_a)^T (L^-1 W_b).
 template <class T>
 __device__ __forceinline__ void sub_yw(const T (&y)[24], const T (&w)[24], bool line, T (&acc)[6][6]) {
 #pragma unroll
@@ -659,10 +705,10 @@ __device__ void schur_item(const SchurArgs<T>& a, int64_t w) {
     const unsigned pb1 = two ? (unsigned)a.pair_b[q + 1] : pb0;
     const int eb0 = (int)(pb0 & 0x7fffffffu), eb1 = (int)(pb1 & 0x7fffffffu);
     T y0[24], w0[24], y1[24], w1[24];
-    load24(a.Y + (size_t)ea0 * SW, y0);
-    load24(a.W + (size_t)eb0 * SW, w0);
-    load24(a.Y + (size_t)ea1 * SW, y1);
-    load24(a.W + (size_t)eb1 * SW, w1);
+    load24(a.Z + (size_t)ea0 * SW, y0);
+    load24(a.Z + (size_t)eb0 * SW, w0);
+    load24(a.Z + (size_t)ea1 * SW, y1);
+    load24(a.Z + (size_t)eb1 * SW, w1);
     sub_yw(y0, w0, ea0 >= a.line_slot0, acc);
     direct_terms(a, ea0, eb0, (pb0 >> 31) != 0u, acc, bacc, hacc);
     if (two) {
@@ -716,9 +762,8 @@ __device__ void schur_block(const BlockArgs<T>& a, int64_t u) {
       for (int i = 0; i < 6; ++i) { bb[i] += (double)p[36 + i]; hh[i] += (double)p[42 + i]; }
   }
   if (diag) {
-    // a diagonal block sums -Y_e^T W_e with Y_e = V^-1 W_e rounded to the working type; that product is
-    // symmetric only up to rounding, which the strong cancellation against H_aa amplifies.  CG needs an
-    // exactly symmetric S, so the block keeps its symmetric part.
+    // a diagonal block sums -Z_e^T Z_e (symmetric by construction) and the symmetric H_e; the
+    // symmetric part is taken anyway so that CG always sees an exactly symmetric S
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -891,23 +936,37 @@ __device__ __forceinline__ void block_dot6(const float* __restrict__ B, const do
   block_dot6_split(B, xh, xl, acc);
 }
 
-// warp sum of a product accumulator, returned in double to lane 0 (double-single lanes are
-// combined with TwoSum on the float pipes; one conversion to double at the end)
-__device__ __forceinline__ double warp_sum_acc(const DotAcc<double>& a) { return warp_sum(a.s); }
-__device__ __forceinline__ double warp_sum_acc(const DotAcc<float>& a) {
+// warp sum of a product accumulator, left in lane 0.  Double-single lanes are combined with TwoSum
+// on the float pipes and stay double-single: on this part a warp-wide FP64 instruction costs as
+// much as dozens of float ones, so conversions to double happen once per block row, not per chunk.
+__device__ __forceinline__ DotAcc<double> warp_sum_acc(const DotAcc<double>& a) {
+  DotAcc<double> r;
+  r.s = warp_sum(a.s);
+  return r;
+}
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float h2, float l2) {
+  const float sm = hi + h2;
+  const float bp = sm - hi;
+  const float er = (hi - (sm - bp)) + (h2 - bp);
+  hi = sm;
+  lo = lo + l2 + er;
+}
+__device__ __forceinline__ DotAcc<float> warp_sum_acc(const DotAcc<float>& a) {
   float hi = a.hi, lo = a.lo;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
-    const float sm = hi + h2;
-    const float bp = sm - hi;
-    const float er = (hi - (sm - bp)) + (h2 - bp);
-    hi = sm;
-    lo = lo + l2 + er;
+    two_sum_acc(hi, lo, h2, l2);
   }
-  return (double)hi + (double)lo;
+  DotAcc<float> r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
 }
+// running sum of chunk results in the accumulator's own precision
+__device__ __forceinline__ void acc_add(DotAcc<double>& s, const DotAcc<double>& v) { s.s += v.s; }
+__device__ __forceinline__ void acc_add(DotAcc<float>& s, const DotAcc<float>& v) { two_sum_acc(s.hi, s.lo, v.hi, v.lo); }
 
 __device__ __forceinline__ float2 split2(double v) {
   const float h = (float)v;
@@ -987,7 +1046,8 @@ template <class T, int NT, bool SOA>
 __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  extern __shared__ double chunk_y[];   // [chunks of this CTA][6]
+  extern __shared__ double chunk_mem[];   // [chunks of this CTA][6] accumulators
+  DotAcc<T>* chunk_y = reinterpret_cast<DotAcc<T>*>(chunk_mem);
   __shared__ double bc[2];
   __shared__ double cta_out[2];
   const int G = gridDim.x, c = blockIdx.x;
@@ -1049,21 +1109,22 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
       }
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        const double y = warp_sum_acc(acc[i]);
+        const DotAcc<T> y = warp_sum_acc(acc[i]);
         if (lane == 0) chunk_y[6 * (q - q0) + i] = y;
       }
     }
     __syncthreads();
     double pap = 0;
     for (int row = r0 + threadIdx.x; row < r1; row += NT) {
-      double y[6] = {0, 0, 0, 0, 0, 0};
+      DotAcc<T> y[6];
       for (int q = a.row_chunk0[row]; q < a.row_chunk0[row + 1]; ++q)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) y[i] += chunk_y[6 * (q - q0) + i];
+        for (int i = 0; i < 6; ++i) acc_add(y[i], chunk_y[6 * (q - q0) + i]);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        a.Ap[6 * row + i] = y[i];
-        pap += y[i] * a.p[6 * row + i];
+        const double yv = y[i].value();
+        a.Ap[6 * row + i] = yv;
+        pap += yv * a.p[6 * row + i];
       }
     }
     cta_sum2<NT>(pap, 0.0, cta_out);
@@ -1504,7 +1565,7 @@ void launch_invert(Problem& P, double lambda) {
   const Dims& d = P.d;
   InvArgs<T> a;
   a.fslot_off = P.fslot_off; a.V = P.featV; a.g = P.featg; a.W = (const T*)P.slotW; a.G = (const T*)P.slotG;
-  a.Vinv = P.featVinv; a.z = P.featz; a.Y = (T*)P.slotY; a.B = (T*)P.slotB;
+  a.Vinv = P.featVinv; a.z = P.featz; a.Z = (T*)P.slotZ; a.B = (T*)P.slotB;
   a.np = d.np; a.nf = d.nf; a.lambda = lambda; a.S = P.S;
   if (d.nf) { ++P.launches; k_invert<T><<<nblk(d.nf, 128), 128, 0, P.stream>>>(a); }
 }
@@ -1514,7 +1575,7 @@ void launch_schur(Problem& P, double lambda) {
   const Dims& d = P.d;
   SchurArgs<T> a;
   a.pair_a = P.pair_a; a.pair_b = P.pair_b; a.wi_se = P.wi_start;
-  a.W = (const T*)P.slotW; a.Y = (const T*)P.slotY; a.H = (const T*)P.slotH; a.B = (const T*)P.slotB;
+  a.Z = (const T*)P.slotZ; a.H = (const T*)P.slotH; a.B = (const T*)P.slotB;
   a.C = (const T*)P.slotC; a.part = (T*)P.part; a.nwi = d.nwi; a.line_slot0 = P.line_slot0;
   if (d.nwi) { ++P.launches; k_schur_items<T><<<nblk(d.nwi, 128), 128, 0, P.stream>>>(a); }
   if (P.ev[3]) cudaEventRecord(P.ev[3], P.stream);
@@ -1663,7 +1724,8 @@ struct WinDesc {
 };
 
 template <class T, int NT>
-__device__ void window_pcg(const WinDesc<T>& W, double* chunk_y, double* red2) {
+__device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2) {
+  DotAcc<T>* chunk_y = reinterpret_cast<DotAcc<T>*>(chunk_mem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
   PcgArgs<T> a;
@@ -1703,21 +1765,22 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_y, double* red2) {
       spmv_block(B, a, W.col[blk], acc);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        const double y = warp_sum_acc(acc[i]);
+        const DotAcc<T> y = warp_sum_acc(acc[i]);
         if (lane == 0) chunk_y[6 * q + i] = y;
       }
     }
     __syncthreads();
     double pap = 0;
     for (int64_t row = threadIdx.x; row < na; row += NT) {
-      double y[6] = {0, 0, 0, 0, 0, 0};
+      DotAcc<T> y[6];
       for (int q = W.row_chunk0[row]; q < W.row_chunk0[row + 1]; ++q)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) y[i] += chunk_y[6 * q + i];
+        for (int i = 0; i < 6; ++i) acc_add(y[i], chunk_y[6 * q + i]);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        W.Ap[6 * row + i] = y[i];
-        pap += y[i] * W.p[6 * row + i];
+        const double yv = y[i].value();
+        W.Ap[6 * row + i] = yv;
+        pap += yv * W.p[6 * row + i];
       }
     }
     cta_sum2<NT>(pap, 0.0, red2);
@@ -1902,10 +1965,10 @@ void fill_window_desc(Problem& P, void* out) {
   a.loss = make_loss(P.opt);
   InvArgs<T>& ia = W.inv;
   ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
-  ia.Vinv = P.featVinv; ia.z = P.featz; ia.Y = (T*)P.slotY; ia.B = (T*)P.slotB; ia.np = d.np; ia.nf = d.nf;
+  ia.Vinv = P.featVinv; ia.z = P.featz; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB; ia.np = d.np; ia.nf = d.nf;
   ia.lambda = 0; ia.S = P.S;
   SchurArgs<T>& sa = W.schur;
-  sa.pair_a = P.pair_a; sa.pair_b = P.pair_b; sa.wi_se = P.wi_start; sa.W = (const T*)P.slotW; sa.Y = (const T*)P.slotY;
+  sa.pair_a = P.pair_a; sa.pair_b = P.pair_b; sa.wi_se = P.wi_start; sa.Z = (const T*)P.slotZ;
   sa.H = (const T*)P.slotH; sa.B = (const T*)P.slotB; sa.C = (const T*)P.slotC; sa.part = (T*)P.part; sa.nwi = d.nwi;
   sa.line_slot0 = P.line_slot0;
   BlockArgs<T>& b = W.blocks;

@@ -1,8 +1,8 @@
 """Batched windows (one persistent launch in a CUDA graph) against the per-window oracle and against the
 library's own sequential step.
 
-FP64: every window's accept/reject sequence and final cost equal its own oracle run of the same number of LM
-iterations (1e-9 relative).  Mixed: one batched step equals the sequential mixed step (1e-5 relative).
+FP64: every batched iteration of every window equals the oracle's iteration from the same state (accept
+decision, cost at 1e-9 relative), and six batched iterations equal six sequential library steps.  Mixed: one batched step equals the sequential mixed step (1e-5 relative).
 """
 import numpy as np
 import pytest
@@ -29,35 +29,73 @@ def windows(n, max_features, seed):
     return [make_scene(window_config(i, seed=seed, max_features=max_features)) for i in range(n)]
 
 
-def oracle_run(s, iters):
-    st = O.state_from_scene(s)
-    lay = O.Layout(st, s["fixed"])
-    opt = O.Options()
-    lm = O.LMState(opt.lambda0)
-    cur = O.cost(st, s["obs"], opt)
-    acc = []
-    for _ in range(iters):
-        st, rep = O.lm_step(st, s["obs"], opt, lm, lay, cur)
-        acc.append(rep["accepted"])
-        if rep["accepted"]:
-            cur = (rep["E_new"], rep["Epx_new"])
-    return cur[0], acc
+# Multi-iteration trajectories are compared with PCG run far below its default tolerance on both sides:
+# at 1e-6 a step whose PCG residual lands within rounding of the threshold stops one iteration earlier on
+# one side, and the two trajectories then differ by up to the PCG tolerance instead of by rounding.
+TIGHT_PCG = 1e-11
+
+
+def gpu_state(B, p, s):
+    """The window's current parameters and LM state read back from the library, as an oracle scene."""
+    cams = B.ba_get_cameras(p, len(s["cams"]["q"]))
+    s2 = dict(s)
+    s2["cams"] = dict(s["cams"], q=cams[:, :4], t=cams[:, 4:7])
+    s2["points"] = B.ba_get_features(p, B.BA_POINT, len(s["points"]))
+    s2["lines"] = B.ba_get_features(p, B.BA_LINE, len(s["lines"]))
+    s2["planes"] = B.ba_get_groups(p, B.BA_PLANE, len(s["planes"]))
+    s2["vps"] = B.ba_get_groups(p, B.BA_VP, len(s["vps"]))
+    lam, nu = B.ba_get_lm_state(p)
+    return s2, lam, nu
 
 
 def test_batch_fp64_matches_oracle(B):
+    """Every batched LM iteration of every window equals the oracle's LM iteration from the same state
+    and LM damping: the same accept decision and the same resulting cost (1e-9 relative).  Comparing
+    step by step keeps the check at rounding level: two correct trajectories of a window with a weakly
+    determined direction drift apart by far more than rounding over several iterations."""
     iters = 6
     ws = windows(3, 600, seed=11)
-    ps = [gpu_problem(B, s, precision=B.BA_FP64) for s in ws]
+    ps = [gpu_problem(B, s, precision=B.BA_FP64, pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000) for s in ws]
     try:
-        reps = B.ba_solve_batch(ps, lm_iters=iters, autotune=False)
+        for _ in range(iters):
+            start = [gpu_state(B, p, s) for p, s in zip(ps, ws)]
+            reps = B.ba_solve_batch(ps, lm_iters=1, autotune=False)
+            for (s2, lam, nu), r in zip(start, reps):
+                st = O.state_from_scene(s2)
+                lay = O.Layout(st, s2["fixed"])
+                opt = O.Options(pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000)
+                _, rep = O.lm_step(st, s2["obs"], opt, O.LMState(lam, nu), lay)
+                E = rep["E_new"] if rep["accepted"] else rep["E"]
+                assert r.accepted_steps == int(rep["accepted"])
+                assert abs(r.cost - E) <= 1e-9 * E, (r.cost, E)
     finally:
         for p in ps:
             B.ba_destroy(p)
-    for s, r in zip(ws, reps):
-        E, acc = oracle_run(s, iters)
-        assert r.iters == iters
-        assert r.accepted_steps == sum(acc), (r.accepted_steps, acc)
-        assert abs(r.cost - E) <= 1e-9 * E, (r.cost, E)
+
+
+def test_batch_fp64_equals_sequential_path(B):
+    """Six batched iterations in one launch give every window the same costs as six ba_lm_step calls of
+    the library's sequential path (1e-10 relative).  The per-feature, per-item and per-row device
+    functions are shared; only the order of the PCG dot-product sums differs (one CTA against a grid)."""
+    ws = windows(3, 600, seed=11)
+    seq = []
+    for s in ws:
+        p = gpu_problem(B, s, precision=B.BA_FP64)
+        try:
+            for _ in range(6):
+                r = B.ba_lm_step(p)
+            seq.append(r.cost_new if r.accepted else r.cost)
+        finally:
+            B.ba_destroy(p)
+    ps = [gpu_problem(B, s, precision=B.BA_FP64) for s in ws]
+    try:
+        reps = B.ba_solve_batch(ps, lm_iters=6, autotune=False)
+    finally:
+        for p in ps:
+            B.ba_destroy(p)
+    for E, r in zip(seq, reps):
+        assert r.iters == 6
+        assert abs(r.cost - E) <= 1e-10 * E, (r.cost, E)
 
 
 def test_batch_mixed_step_matches_sequential(B):
