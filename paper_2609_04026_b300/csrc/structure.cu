@@ -1,18 +1,24 @@
 // One-time structure build (K0): the analogue of a sparse solver's symbolic
 // analysis, which the paper observes only on the first iteration of each BA
-// call (Section 4, Fig. 3c).  It runs on the host once per problem:
-//   * validates every index (BA_ERR_ARG on failure),
-//   * orders the residual records feature-major (each residual touches exactly
-//     one feature, Section 3.2-3.4, so H_ff is block-diagonal),
-//   * gives every (feature, kept entity) pair a "slot" that will hold its
-//     W block and its direct contribution to H_aa,
-//   * builds the block pattern of S over A = cameras u groups (every pair of
-//     entities that share a feature, Section 3.3 sparsity analysis), stored as
-//     full block-CSR (both triangles, for the SpMV),
-//   * lists, for every upper block of S, the slot pairs (e_a, e_b) whose product
-//     W_a V^-1 W_b^T lands in it, cut into work items of at most PAIR_CHUNK pairs
-//     so that the Schur kernel accumulates each block in a fixed order without
-//     atomics.
+// call (Section 4, Fig. 3c).  The host validates every index (BA_ERR_ARG on
+// failure) and uploads the residual records; the rest runs on the GPU:
+//   * the residual records are ordered feature-major (each residual touches
+//     exactly one feature, Section 3.2-3.4, so H_ff is block-diagonal), and by
+//     camera inside a feature, with a stable LSD radix sort,
+//   * every (feature, kept entity) pair gets a "slot" that will hold its W
+//     block and its direct contribution to H_aa,
+//   * the block pattern of S over A = cameras u groups (every pair of entities
+//     that share a feature, Section 3.3 sparsity analysis) is marked in a
+//     symmetric bitmap of A x A and read out as full block-CSR (both triangles,
+//     for the SpMV), padded and interleaved for coalesced loads,
+//   * for every upper block of S the slot pairs (e_a, e_b) whose product
+//     W_a V^-1 W_b^T lands in it are listed in feature order (a stable radix
+//     sort of the pairs by block) and cut into work items of at most PAIR_CHUNK
+//     pairs, so that the Schur kernel accumulates each block in a fixed order
+//     without atomics.
+// Every step is deterministic: the same input gives the same structure, and the
+// orders are those of a sequential build (features ascending, cameras ascending
+// inside a feature, input order among equal keys).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +52,500 @@ static ba_status upload(Problem& P, X*& dst, const std::vector<X>& src) {
   return BA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// temporary device memory of the build, released when the build returns
+struct Scratch {
+  Alloc* al;
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  Scratch(Alloc* a, cudaStream_t s) : al(a), st(s) {}
+  ~Scratch() {
+    cudaStreamSynchronize(st);   // kernels of a build that stopped early may still read these buffers
+    for (void* p : ptrs) al->put(p);
+  }
+  template <class X>
+  X* get(int64_t n) {
+    void* p = al->get(sizeof(X) * (size_t)(n > 0 ? n : 1));
+    if (p) ptrs.push_back(p);
+    return (X*)p;
+  }
+};
+
+static inline unsigned grid_of(int64_t n, int nt) { return (unsigned)std::max<int64_t>(1, (n + nt - 1) / nt); }
+static inline int bits_for(int64_t n) {   // bits to hold values in [0, n)
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int64 values (three phases: tile sums, scan of the tile sums, tile scans)
+constexpr int SC_NT = 256, SC_ITEMS = 8, SC_TILE = SC_NT * SC_ITEMS;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t* total) {
+  // sh: SC_NT / 32 + 1 entries
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t s = 0;
+    for (int i = 0; i < SC_NT / 32; ++i) { const int64_t c = sh[i]; sh[i] = s; s += c; }
+    sh[SC_NT / 32] = s;
+  }
+  __syncthreads();
+  const int64_t r = x - v + sh[w];
+  *total = sh[SC_NT / 32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_tiles(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ tsum) {
+  __shared__ int64_t sh[SC_NT / 32 + 1];
+  const int64_t base = blockIdx.x * (int64_t)SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) s += (base + i < n) ? in[base + i] : 0;
+  int64_t tot;
+  block_excl_scan(s, sh, &tot);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_apply(const int64_t* __restrict__ in, int64_t n, const int64_t* __restrict__ toff,
+                             int64_t* __restrict__ out) {
+  __shared__ int64_t sh[SC_NT / 32 + 1];
+  const int64_t base = blockIdx.x * (int64_t)SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+  int64_t v[SC_ITEMS], s = 0;
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) { v[i] = (base + i < n) ? in[base + i] : 0; s += v[i]; }
+  int64_t tot;
+  int64_t run = block_excl_scan(s, sh, &tot) + toff[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+// out[i] = sum of in[0..i) for i in [0, n], out has n + 1 entries (in and out may alias only if n == 0)
+static ba_status scan_excl(Problem& P, Scratch& S, const int64_t* in, int64_t* out, int64_t n) {
+  if (n == 0) {
+    CU(cudaMemsetAsync(out, 0, sizeof(int64_t), P.stream));
+    return BA_OK;
+  }
+  const int64_t nt = (n + SC_TILE - 1) / SC_TILE;
+  int64_t* tsum = S.get<int64_t>(nt);
+  int64_t* toff = S.get<int64_t>(nt + 1);
+  if (!tsum || !toff) return fail(P, BA_ERR_OOM, "device allocation failed");
+  k_scan_tiles<<<(unsigned)nt, SC_NT, 0, P.stream>>>(in, n, tsum);
+  if (nt == 1) {
+    CU(cudaMemsetAsync(toff, 0, sizeof(int64_t), P.stream));
+    CU(cudaMemcpyAsync(toff + 1, tsum, sizeof(int64_t), cudaMemcpyDeviceToDevice, P.stream));
+  } else {
+    ba_status s = scan_excl(P, S, tsum, toff, nt);
+    if (s) return s;
+  }
+  k_scan_apply<<<(unsigned)nt, SC_NT, 0, P.stream>>>(in, n, toff, out);
+  CU(cudaMemcpyAsync(out + n, toff + nt, sizeof(int64_t), cudaMemcpyDeviceToDevice, P.stream));   // the total
+  CU(cudaGetLastError());
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (key, value) u32 pairs by the low `bits` bits of the key, 8 bits per pass.
+// A tile of RS_TILE keys is split into per-warp runs of consecutive keys; inside a warp the rank of a
+// key among equal digits comes from __match_any_sync, so the scatter keeps the input order of equal
+// digits (stability) without any atomics on global memory.
+constexpr int RS_NT = 256, RS_ITEMS = 16, RS_TILE = RS_NT * RS_ITEMS, RS_NW = RS_NT / 32;
+
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t* __restrict__ hist,
+                          int64_t ntiles) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = blockIdx.x * (int64_t)RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_NT) {
+    const int64_t k = base + i;
+    if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, const int64_t* __restrict__ off, int64_t ntiles) {
+  __shared__ unsigned wcnt[RS_NW][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < RS_NW * 256; i += RS_NT) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t base = blockIdx.x * (int64_t)RS_TILE + (int64_t)warp * 32 * RS_ITEMS;
+  uint32_t k[RS_ITEMS], v[RS_ITEMS], loc[RS_ITEMS];
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const int64_t idx = base + it * 32 + lane;
+    const bool ok = idx < n;
+    k[it] = ok ? kin[idx] : 0u;
+    v[it] = ok ? vin[idx] : 0u;
+    const unsigned d = (k[it] >> shift) & 255u;
+    const unsigned peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + lane);
+    const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+    const unsigned before = ok ? wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (ok && rank == 0) wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+    loc[it] = before + rank;
+  }
+  __syncthreads();
+  // exclusive prefix of the per-warp counts of each digit (warps hold consecutive runs of the tile)
+  for (int d = threadIdx.x; d < 256; d += RS_NT) {
+    unsigned s = 0;
+#pragma unroll
+    for (int w = 0; w < RS_NW; ++w) { const unsigned c = wcnt[w][d]; wcnt[w][d] = s; s += c; }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const int64_t idx = base + it * 32 + lane;
+    if (idx < n) {
+      const unsigned d = (k[it] >> shift) & 255u;
+      const int64_t dst = off[(int64_t)d * ntiles + blockIdx.x] + wcnt[warp][d] + loc[it];
+      kout[dst] = k[it];
+      vout[dst] = v[it];
+    }
+  }
+}
+
+// sorts (k, v) in place (k and v end up holding the sorted pairs); k2 / v2 are work buffers of n entries
+static ba_status radix_sort(Problem& P, Scratch& S, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2, int64_t n,
+                            int bits) {
+  if (n <= 1 || bits <= 0) return BA_OK;
+  const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  int64_t* hist = S.get<int64_t>(256 * ntiles);
+  int64_t* off = S.get<int64_t>(256 * ntiles + 1);
+  if (!hist || !off) return fail(P, BA_ERR_OOM, "device allocation failed");
+  uint32_t *ka = k, *va = v, *kb = k2, *vb = v2;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<(unsigned)ntiles, RS_NT, 0, P.stream>>>(ka, n, shift, hist, ntiles);
+    ba_status s = scan_excl(P, S, hist, off, 256 * ntiles);
+    if (s) return s;
+    k_rs_scatter<<<(unsigned)ntiles, RS_NT, 0, P.stream>>>(ka, va, kb, vb, n, shift, off, ntiles);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != k) {
+    CU(cudaMemcpyAsync(k, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, P.stream));
+    CU(cudaMemcpyAsync(v, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, P.stream));
+  }
+  CU(cudaGetLastError());
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// build kernels
+__global__ void k_iota_key(const int32_t* __restrict__ src, int64_t n, int add, uint32_t* __restrict__ key,
+                           uint32_t* __restrict__ val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) { key[i] = (uint32_t)(src[i] + add); val[i] = (uint32_t)i; }
+}
+
+// key[j] = feature of residual val[j] (the permutation sorted by camera so far)
+__global__ void k_gather_key(const int32_t* __restrict__ feat, const uint32_t* __restrict__ val, int64_t n,
+                             uint32_t* __restrict__ key) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) key[j] = (uint32_t)feat[val[j]];
+}
+
+__global__ void k_count(const int32_t* __restrict__ id, int64_t n, unsigned long long* __restrict__ cnt) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) atomicAdd(&cnt[id[j]], 1ull);
+}
+
+__global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int32_t* __restrict__ b) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) b[j] = (int32_t)a[j];
+}
+
+struct SlotArgs {
+  const int32_t *order, *fres_off, *cam, *grp;
+  const int8_t* kind;
+  const uint8_t* fixed;
+  int64_t nf, nc, npl;
+  int* err;   // bit 0: two planes on one feature, bit 1: two VPs on one line
+};
+
+// distinct kept entities of a feature (cameras ascending, then its plane, then its VP)
+__global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= a.nf) return;
+  int n = 0, prev = -1, plane = -1, vp = -1;
+  for (int32_t j = a.fres_off[f]; j < a.fres_off[f + 1]; ++j) {
+    const int32_t i = a.order[j];
+    const int c = a.cam[i];
+    if (c >= 0 && a.fixed[c] != 0x3F && c != prev) { ++n; prev = c; }
+    const int k = a.kind[i];
+    if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
+      if (plane >= 0 && plane != a.grp[i]) atomicOr(a.err, 1);
+      plane = a.grp[i];
+    } else if (k == R_VP) {
+      if (vp >= 0 && vp != a.grp[i]) atomicOr(a.err, 2);
+      vp = a.grp[i];
+    }
+  }
+  nslot[f] = n + (plane >= 0) + (vp >= 0);
+}
+
+struct SlotFill {
+  int32_t *fslot_off, *slot_ent, *slot_feat, *feat_plane_slot, *rslot_c, *rslot_g;
+  uint8_t* slot_type;
+};
+
+__global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFill o) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f > a.nf) return;
+  o.fslot_off[f] = (int32_t)soff[f];
+  if (f == a.nf) return;
+  const int32_t r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
+  int32_t e = (int32_t)soff[f];
+  int prev = -1, plane = -1, vp = -1;
+  for (int32_t j = r0; j < r1; ++j) {
+    const int32_t i = a.order[j];
+    const int c = a.cam[i];
+    const int k = a.kind[i];
+    if (k == R_PLANE_POINT || k == R_PLANE_LINE) plane = a.grp[i];
+    if (k == R_VP) vp = a.grp[i];
+    if (c >= 0 && a.fixed[c] != 0x3F) {
+      if (c != prev) {
+        o.slot_ent[e] = c;
+        o.slot_feat[e] = (int32_t)f;
+        o.slot_type[e] = ENT_CAM;
+        prev = c;
+        ++e;
+      }
+      o.rslot_c[j] = e - 1;
+    } else {
+      o.rslot_c[j] = -1;
+    }
+  }
+  const int32_t plane_slot = plane >= 0 ? e : -1;
+  if (plane >= 0) {
+    o.slot_ent[e] = (int32_t)(a.nc + plane);
+    o.slot_feat[e] = (int32_t)f;
+    o.slot_type[e] = ENT_PLANE;
+    ++e;
+  }
+  const int32_t vp_slot = vp >= 0 ? e : -1;
+  if (vp >= 0) {
+    o.slot_ent[e] = (int32_t)(a.nc + a.npl + vp);
+    o.slot_feat[e] = (int32_t)f;
+    o.slot_type[e] = ENT_VP;
+    ++e;
+  }
+  o.feat_plane_slot[f] = plane_slot;
+  for (int32_t j = r0; j < r1; ++j) {
+    const int k = a.kind[a.order[j]];
+    o.rslot_g[j] = (k == R_PLANE_POINT || k == R_PLANE_LINE) ? plane_slot : (k == R_VP ? vp_slot : -1);
+  }
+}
+
+// symmetric bitmap of the block pattern of S: bit (a, b) set when a and b share a feature or a == b
+struct Bitmap {
+  uint32_t* w;
+  int64_t wpr;   // 32-bit words per row
+  __device__ __forceinline__ void set(int64_t a, int64_t b) const {
+    uint32_t* p = w + a * wpr + (b >> 5);
+    const uint32_t bit = 1u << (b & 31);
+    if (!(*(volatile uint32_t*)p & bit)) atomicOr(p, bit);
+  }
+};
+
+__global__ void k_pattern_pairs(const int32_t* __restrict__ fslot_off, const int32_t* __restrict__ slot_ent, int64_t nf,
+                                Bitmap bm) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int32_t s0 = fslot_off[f], s1 = fslot_off[f + 1];
+  for (int32_t i = s0; i < s1; ++i) {
+    const int64_t a = slot_ent[i];
+    for (int32_t j = i + 1; j < s1; ++j) {
+      const int64_t b = slot_ent[j];
+      bm.set(a, b);
+      bm.set(b, a);
+    }
+  }
+}
+
+__global__ void k_pattern_diag(int64_t na, Bitmap bm) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a < na) bm.set(a, a);
+}
+
+// per row: stored blocks, blocks left of the diagonal, and the exclusive popcount prefix of every word
+__global__ void k_pattern_rows(int64_t na, Bitmap bm, int32_t* __restrict__ wpre, int64_t* __restrict__ full_cnt,
+                               int64_t* __restrict__ pad_cnt, int64_t* __restrict__ up_cnt, int32_t* __restrict__ nlow) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= na) return;
+  const uint32_t* row = bm.w + a * bm.wpr;
+  int32_t* pre = wpre + a * bm.wpr;
+  int32_t s = 0;
+  for (int64_t w = 0; w < bm.wpr; ++w) {
+    pre[w] = s;
+    s += __popc(row[w]);
+  }
+  const int32_t low = pre[a >> 5] + __popc(row[a >> 5] & ((1u << (a & 31)) - 1u));
+  full_cnt[a] = s;
+  pad_cnt[a] = ((s + 31) / 32) * 32;
+  up_cnt[a] = s - low;
+  nlow[a] = low;
+}
+
+__device__ __forceinline__ int32_t bm_rank(const Bitmap& bm, const int32_t* wpre, int64_t a, int64_t c) {
+  const int64_t w = c >> 5;
+  return wpre[a * bm.wpr + w] + __popc(bm.w[a * bm.wpr + w] & ((1u << (c & 31)) - 1u));
+}
+
+struct RowFill {
+  const int64_t *prow, *uptr;
+  const int32_t *wpre, *nlow;
+  int32_t *pcol, *up_row, *up_full, *up_mirror, *prow32, *row_len;
+  const int64_t* full_cnt;
+};
+
+__global__ void k_pattern_fill(int64_t na, Bitmap bm, RowFill o) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a > na) return;
+  o.prow32[a] = (int32_t)o.prow[a];
+  if (a == na) return;
+  o.row_len[a] = (int32_t)o.full_cnt[a];
+  const uint32_t* row = bm.w + a * bm.wpr;
+  const int64_t p0 = o.prow[a];
+  int32_t k = 0;
+  for (int64_t w = 0; w < bm.wpr; ++w) {
+    uint32_t bits = row[w];
+    while (bits) {
+      const int t = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      const int64_t c = w * 32 + t;
+      o.pcol[p0 + k] = (int32_t)c;
+      if (c >= a) {
+        const int64_t u = o.uptr[a] + (k - o.nlow[a]);
+        o.up_row[u] = (int32_t)a;
+        o.up_full[u] = (int32_t)(p0 + k);
+        o.up_mirror[u] = (int32_t)(o.prow[c] + bm_rank(bm, o.wpre, c, a));
+      }
+      ++k;
+    }
+  }
+  for (int64_t q = p0 + k; q < o.prow[a + 1]; ++q) o.pcol[q] = (int32_t)a;   // padding: col = row, zero values
+}
+
+__global__ void k_pair_count(const int32_t* __restrict__ fslot_off, int64_t nf, int64_t* __restrict__ npf) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int64_t n = fslot_off[f + 1] - fslot_off[f];
+  npf[f] = n * (n + 1) / 2;
+}
+
+struct PairGen {
+  const int32_t *fslot_off, *slot_ent, *wpre, *nlow;
+  const uint8_t* slot_type;
+  const int64_t *poff, *uptr;
+  Bitmap bm;
+  int64_t nf;
+  uint32_t *key, *val;
+  int32_t *gi, *gj;
+  unsigned long long* ucnt;
+};
+
+// the pairs of every feature in (i, j >= i) order: key = upper block of S the product lands in
+__global__ void k_pair_gen(PairGen g) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= g.nf) return;
+  const int32_t s0 = g.fslot_off[f], s1 = g.fslot_off[f + 1];
+  int64_t q = g.poff[f];
+  for (int32_t i = s0; i < s1; ++i) {
+    const int64_t a = g.slot_ent[i];
+    for (int32_t j = i; j < s1; ++j, ++q) {
+      const int64_t b = g.slot_ent[j];
+      const int64_t u = g.uptr[a] + (bm_rank(g.bm, g.wpre, a, b) - g.nlow[a]);
+      g.key[q] = (uint32_t)u;
+      g.val[q] = (uint32_t)q;
+      g.gi[q] = i;
+      // bit 31 marks a (camera slot, plane slot) pair of one feature: its direct J_cam^T w J_plane block is added
+      const bool cam_plane = i != j && g.slot_type[i] == ENT_CAM && g.slot_type[j] == ENT_PLANE;
+      g.gj[q] = (int32_t)((uint32_t)j | (cam_plane ? 0x80000000u : 0u));
+      atomicAdd(&g.ucnt[u], 1ull);
+    }
+  }
+}
+
+__global__ void k_pair_place(const uint32_t* __restrict__ val, int64_t n, const int32_t* __restrict__ gi,
+                             const int32_t* __restrict__ gj, int32_t* __restrict__ pa, int32_t* __restrict__ pb) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) { const uint32_t q = val[k]; pa[k] = gi[q]; pb[k] = gj[q]; }
+}
+
+__global__ void k_item_count(const unsigned long long* __restrict__ ucnt, int64_t nbu, int64_t* __restrict__ nw) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u < nbu) {
+    const int64_t n = (int64_t)ucnt[u];
+    nw[u] = n > 0 ? (n + PAIR_CHUNK - 1) / PAIR_CHUNK : 1;   // every block gets one (possibly empty) item
+  }
+}
+
+__global__ void k_item_fill(const unsigned long long* __restrict__ ucnt, const int64_t* __restrict__ pstart,
+                            const int64_t* __restrict__ wstart, int64_t nbu, int32_t* __restrict__ up_wi,
+                            int32_t* __restrict__ wi_se) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u > nbu) return;
+  up_wi[u] = (int32_t)wstart[u];
+  if (u == nbu) return;
+  const int64_t p0 = pstart[u], p1 = p0 + (int64_t)ucnt[u];
+  for (int64_t w = wstart[u]; w < wstart[u + 1]; ++w) {
+    const int64_t s = p0 + (w - wstart[u]) * PAIR_CHUNK;
+    wi_se[2 * w] = (int32_t)s;
+    wi_se[2 * w + 1] = (int32_t)(s + PAIR_CHUNK < p1 ? s + PAIR_CHUNK : p1);
+  }
+}
+
+struct Permute {
+  const uint32_t* order;
+  const int8_t* kind;
+  const int32_t *cam, *feat, *grp;
+  const double4* meas;
+  int8_t* rkind;
+  int32_t *rcam, *rfeat, *rgrp;
+  double4* rmeas;
+  int64_t n;
+};
+
+__global__ void k_permute(Permute a) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= a.n) return;
+  const uint32_t i = a.order[j];
+  a.rkind[j] = a.kind[i];
+  a.rcam[j] = a.cam[i];
+  a.rfeat[j] = a.feat[i];
+  a.rgrp[j] = a.grp[i];
+  a.rmeas[j] = a.meas[i];
+}
+
+__global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, uint8_t* __restrict__ t) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a < na) t[a] = a < nc ? ENT_CAM : (a < nc + npl ? ENT_PLANE : ENT_VP);
+}
+
+static ba_status read_i64(Problem& P, const int64_t* src, int64_t* dst) {
+  CU(cudaMemcpyAsync(dst, src, sizeof(int64_t), cudaMemcpyDeviceToHost, P.stream));
+  CU(cudaStreamSynchronize(P.stream));
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
 ba_status build_structure(Problem& P) {
   Dims& d = P.d;
   d.nc = (int64_t)P.h_cam.size() / 12;
@@ -56,6 +556,10 @@ ba_status build_structure(Problem& P) {
   d.nf = d.np + d.nl;
   d.na = d.nc + d.npl + d.nv;
   if (d.na > (int64_t)1 << 30 || d.nf > (int64_t)1 << 30) return fail(P, BA_ERR_ARG, "too many entities");
+  // the pattern bitmap holds na x na bits
+  const int64_t wpr = (d.na + 31) / 32;
+  if ((double)d.na * (double)wpr * 8.0 > 16e9)
+    return fail(P, BA_ERR_ARG, "too many cameras and groups for the reduced-system pattern (" + std::to_string(d.na) + ")");
 
   // ---- normalise parameters: unit quaternions, |d| = 1 lines, unit plane normals (with w), unit VPs
   for (int64_t i = 0; i < d.nc; ++i) {
@@ -83,7 +587,7 @@ ba_status build_structure(Problem& P) {
     for (int k = 0; k < 3; ++k) v[k] /= n;
   }
 
-  // ---- gather and validate residual records
+  // ---- validate the residual records and stage them in input order
   int64_t nr = 0;
   for (auto& b : P.h_obs) nr += (int64_t)b.feat.size();
   if (nr > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many residuals");
@@ -94,17 +598,17 @@ ba_status build_structure(Problem& P) {
   {
     int64_t o = 0;
     for (auto& b : P.h_obs) {
-      int64_t n = (int64_t)b.feat.size();
+      const int64_t n = (int64_t)b.feat.size();
+      const int k = b.kind;
+      const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L);
+      const int64_t nfk = is_point ? d.np : d.nl;
       for (int64_t i = 0; i < n; ++i, ++o) {
-        int k = b.kind;
         kind[o] = (int8_t)k;
-        bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L);
-        int32_t f = b.feat[i];
-        int64_t nfk = is_point ? d.np : d.nl;
+        const int32_t f = b.feat[i];
         if (f < 0 || f >= nfk) return fail(P, BA_ERR_ARG, "observation kind " + std::to_string(k) + ": feature id out of range");
         feat[o] = is_point ? f : (int32_t)(d.np + f);
         if (k != R_VP) {
-          int32_t c = b.cam[i];
+          const int32_t c = b.cam[i];
           if (c < 0 || c >= d.nc) return fail(P, BA_ERR_ARG, "observation kind " + std::to_string(k) + ": camera id out of range");
           cam[o] = c;
         } else {
@@ -112,251 +616,194 @@ ba_status build_structure(Problem& P) {
         }
         grp[o] = -1;
         if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
-          int32_t g = b.other[i];
+          const int32_t g = b.other[i];
           if (g < 0 || g >= d.npl) return fail(P, BA_ERR_ARG, "plane id out of range");
           grp[o] = g;
         } else if (k == R_VP) {
-          int32_t g = b.other[i];
+          const int32_t g = b.other[i];
           if (g < 0 || g >= d.nv) return fail(P, BA_ERR_ARG, "vp id out of range");
           grp[o] = g;
-        } else if (k == R_P2L || k == R_L2P) {
-          if (!b.other.empty()) {
-            int32_t g = b.other[i];
-            int64_t lim = (k == R_P2L) ? d.nl : d.np;
-            if (g < 0 || g >= lim) return fail(P, BA_ERR_ARG, "partner feature id out of range");
-          }
+        } else if ((k == R_P2L || k == R_L2P) && !b.other.empty()) {
+          const int32_t g = b.other[i];
+          const int64_t lim = (k == R_P2L) ? d.nl : d.np;
+          if (g < 0 || g >= lim) return fail(P, BA_ERR_ARG, "partner feature id out of range");
         }
-        for (int c = 0; c < 4; ++c) meas[4 * o + c] = b.meas[4 * i + c];
       }
+      if (n) std::memcpy(&meas[4 * (o - n)], b.meas.data(), sizeof(double) * 4 * n);
     }
   }
   P.h_obs.clear();
   P.h_obs.shrink_to_fit();
 
-  // ---- feature-major order (counting sort by feature, then by camera inside a feature)
-  std::vector<int32_t> fres_off(d.nf + 1, 0);
-  for (int64_t i = 0; i < nr; ++i) fres_off[feat[i] + 1]++;
-  for (int64_t f = 0; f < d.nf; ++f) fres_off[f + 1] += fres_off[f];
-  std::vector<int32_t> order(nr);
-  {
-    std::vector<int32_t> pos(fres_off.begin(), fres_off.end() - 1);
-    for (int64_t i = 0; i < nr; ++i) order[pos[feat[i]]++] = (int32_t)i;
-  }
-  for (int64_t f = 0; f < d.nf; ++f) {
-    auto b = order.begin() + fres_off[f], e = order.begin() + fres_off[f + 1];
-    std::stable_sort(b, e, [&](int32_t a, int32_t c) { return cam[a] < cam[c]; });
-  }
-  d.n_points_res_end = fres_off[d.np];
-
-  // ---- slots: one per (feature, kept entity); cameras first (ids < groups)
-  std::vector<int32_t> fslot_off(d.nf + 1, 0);
-  std::vector<int32_t> slot_ent, slot_feat;
-  std::vector<uint8_t> slot_type;
-  std::vector<int32_t> feat_plane_slot(d.nf, -1);
-  std::vector<int32_t> rslot_c(nr, -1), rslot_g(nr, -1);
-  slot_ent.reserve((size_t)nr + d.nf);
-  {
-    std::vector<int32_t> ents;
-    for (int64_t f = 0; f < d.nf; ++f) {
-      ents.clear();
-      int32_t plane = -1, vp = -1;
-      for (int32_t j = fres_off[f]; j < fres_off[f + 1]; ++j) {
-        int32_t i = order[j];
-        if (cam[i] >= 0 && P.h_fixed[cam[i]] != 0x3F) ents.push_back(cam[i]);
-        int k = kind[i];
-        if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
-          if (plane >= 0 && plane != grp[i]) return fail(P, BA_ERR_ARG, "a feature may be associated with at most one plane");
-          plane = grp[i];
-        }
-        if (k == R_VP) {
-          if (vp >= 0 && vp != grp[i]) return fail(P, BA_ERR_ARG, "a line may be associated with at most one VP");
-          vp = grp[i];
-        }
-      }
-      if (plane >= 0) ents.push_back((int32_t)(d.nc + plane));
-      if (vp >= 0) ents.push_back((int32_t)(d.nc + d.npl + vp));
-      std::sort(ents.begin(), ents.end());
-      ents.erase(std::unique(ents.begin(), ents.end()), ents.end());
-      int32_t base = (int32_t)slot_ent.size();
-      fslot_off[f] = base;
-      for (int32_t a : ents) {
-        slot_ent.push_back(a);
-        slot_feat.push_back((int32_t)f);
-        uint8_t t = a < d.nc ? ENT_CAM : (a < d.nc + d.npl ? ENT_PLANE : ENT_VP);
-        slot_type.push_back(t);
-        if (t == ENT_PLANE) feat_plane_slot[f] = (int32_t)(slot_ent.size() - 1);
-      }
-      for (int32_t j = fres_off[f]; j < fres_off[f + 1]; ++j) {
-        int32_t i = order[j];
-        auto find = [&](int32_t a) {
-          auto it = std::lower_bound(ents.begin(), ents.end(), a);
-          return base + (int32_t)(it - ents.begin());
-        };
-        if (cam[i] >= 0 && P.h_fixed[cam[i]] != 0x3F) rslot_c[j] = find(cam[i]);
-        int k = kind[i];
-        if (k == R_PLANE_POINT || k == R_PLANE_LINE) rslot_g[j] = find((int32_t)(d.nc + grp[i]));
-        if (k == R_VP) rslot_g[j] = find((int32_t)(d.nc + d.npl + grp[i]));
-      }
-      if ((int64_t)slot_ent.size() > INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many slots");
-    }
-    fslot_off[d.nf] = (int32_t)slot_ent.size();
-  }
-  d.ne = (int64_t)slot_ent.size();
-  P.line_slot0 = fslot_off[d.np];
-
-  // ---- upper block pattern of S: all entity pairs that share a feature, plus every diagonal
-  const int64_t na = d.na;
-  std::vector<int32_t> up_ptr(na + 1, 0), up_col;
-  {
-    std::vector<std::vector<int32_t>> rows(na);
-    for (int64_t a = 0; a < na; ++a) rows[a].push_back((int32_t)a);
-    for (int64_t f = 0; f < d.nf; ++f)
-      for (int32_t i = fslot_off[f]; i < fslot_off[f + 1]; ++i)
-        for (int32_t j = i + 1; j < fslot_off[f + 1]; ++j) rows[slot_ent[i]].push_back(slot_ent[j]);
-    for (int64_t a = 0; a < na; ++a) {
-      auto& r = rows[a];
-      std::sort(r.begin(), r.end());
-      r.erase(std::unique(r.begin(), r.end()), r.end());
-      up_ptr[a + 1] = up_ptr[a] + (int32_t)r.size();
-    }
-    up_col.resize(up_ptr[na]);
-    for (int64_t a = 0; a < na; ++a) std::copy(rows[a].begin(), rows[a].end(), up_col.begin() + up_ptr[a]);
-  }
-  d.nbu = up_ptr[na];
-  std::vector<int32_t> up_row(d.nbu);
-  for (int64_t a = 0; a < na; ++a)
-    for (int32_t u = up_ptr[a]; u < up_ptr[a + 1]; ++u) up_row[u] = (int32_t)a;
-
-  // ---- full block-CSR (row b = lower entries (cols a < b, ascending) then upper entries)
-  std::vector<int32_t> row_ptr(na + 1, 0), low_cnt(na, 0);
-  for (int64_t u = 0; u < d.nbu; ++u)
-    if (up_col[u] != up_row[u]) low_cnt[up_col[u]]++;
-  for (int64_t a = 0; a < na; ++a) row_ptr[a + 1] = row_ptr[a] + low_cnt[a] + (up_ptr[a + 1] - up_ptr[a]);
-  d.nbf = row_ptr[na];
-  std::vector<int32_t> col(d.nbf), up_full(d.nbu), up_mirror(d.nbu);
-  {
-    std::vector<int32_t> low_pos(na);
-    for (int64_t a = 0; a < na; ++a) low_pos[a] = row_ptr[a];
-    for (int64_t a = 0; a < na; ++a) {
-      int32_t base = row_ptr[a] + low_cnt[a];
-      for (int32_t u = up_ptr[a]; u < up_ptr[a + 1]; ++u) {
-        int32_t b = up_col[u];
-        int32_t pf = base + (u - up_ptr[a]);
-        col[pf] = b;
-        up_full[u] = pf;
-        if (b == a) {
-          up_mirror[u] = pf;
-        } else {
-          int32_t pm = low_pos[b]++;
-          col[pm] = (int32_t)a;
-          up_mirror[u] = pm;
-        }
-      }
-    }
-  }
-
-  // ---- storage layout of S for the SpMV: every row's stored blocks padded to a multiple of 32 (the pads
-  // have col = row and zero values), and inside each group of 32 blocks the 36 entries are interleaved
-  // (entry e of the group's block l at e * 32 + l), so that a warp reads one entry of 32 blocks per
-  // coalesced 128-byte load.  up_full / up_mirror hold positions in this padded order.
-  std::vector<int32_t> prow_ptr(na + 1, 0), row_len(na);
-  for (int64_t a = 0; a < na; ++a) {
-    row_len[a] = row_ptr[a + 1] - row_ptr[a];
-    prow_ptr[a + 1] = prow_ptr[a] + ((row_len[a] + 31) / 32) * 32;
-  }
-  d.nbp = prow_ptr[na];
-  std::vector<int32_t> pcol(d.nbp);
-  for (int64_t a = 0; a < na; ++a)
-    for (int32_t k = 0; k < prow_ptr[a + 1] - prow_ptr[a]; ++k)
-      pcol[prow_ptr[a] + k] = k < row_len[a] ? col[row_ptr[a] + k] : (int32_t)a;
-  auto to_padded = [&](int32_t fp) {
-    int64_t a = std::upper_bound(row_ptr.begin(), row_ptr.end(), fp) - row_ptr.begin() - 1;
-    return prow_ptr[a] + (fp - row_ptr[a]);
-  };
-  for (int64_t u = 0; u < d.nbu; ++u) {
-    up_full[u] = to_padded(up_full[u]);
-    up_mirror[u] = to_padded(up_mirror[u]);
-  }
-  P.h_prow_ptr = prow_ptr;
-  P.h_row_len = row_len;
-
-  // ---- slot pairs per upper block (feature order inside a block), cut into work items
-  std::vector<int64_t> pcount(d.nbu + 1, 0);
-  auto find_up = [&](int32_t a, int32_t b) {
-    auto it = std::lower_bound(up_col.begin() + up_ptr[a], up_col.begin() + up_ptr[a + 1], b);
-    return (int32_t)(it - up_col.begin());
-  };
-  for (int64_t f = 0; f < d.nf; ++f)
-    for (int32_t i = fslot_off[f]; i < fslot_off[f + 1]; ++i)
-      for (int32_t j = i; j < fslot_off[f + 1]; ++j) pcount[find_up(slot_ent[i], slot_ent[j]) + 1]++;
-  for (int64_t u = 0; u < d.nbu; ++u) pcount[u + 1] += pcount[u];
-  d.npair = pcount[d.nbu];
-  if (d.npair > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many Schur pairs");
-  std::vector<int32_t> pair_a(d.npair), pair_b(d.npair);
-  {
-    std::vector<int64_t> pos(pcount.begin(), pcount.end() - 1);
-    for (int64_t f = 0; f < d.nf; ++f)
-      for (int32_t i = fslot_off[f]; i < fslot_off[f + 1]; ++i)
-        for (int32_t j = i; j < fslot_off[f + 1]; ++j) {
-          int64_t q = pos[find_up(slot_ent[i], slot_ent[j])]++;
-          pair_a[q] = i;
-          // bit 31 marks a (camera slot, plane slot) pair of one feature: its direct block J_cam^T w J_plane
-          const bool cam_plane = i != j && slot_type[i] == ENT_CAM && slot_type[j] == ENT_PLANE;
-          pair_b[q] = (int32_t)((uint32_t)j | (cam_plane ? 0x80000000u : 0u));
-        }
-  }
-  std::vector<int32_t> up_wi(d.nbu + 1, 0), wi_start;
-  for (int64_t u = 0; u < d.nbu; ++u) {
-    int64_t n = pcount[u + 1] - pcount[u];
-    int64_t nw = (n + PAIR_CHUNK - 1) / PAIR_CHUNK;
-    if (nw == 0) nw = 1;  // every block gets one (possibly empty) work item
-    up_wi[u + 1] = up_wi[u] + (int32_t)nw;
-    for (int64_t w = 0; w < nw; ++w) wi_start.push_back((int32_t)(pcount[u] + w * PAIR_CHUNK));
-  }
-  d.nwi = up_wi[d.nbu];
-  wi_start.push_back((int32_t)d.npair);
-  // a work item ends where the next starts, except at a block boundary
-  std::vector<int32_t> wi_end(d.nwi);
-  for (int64_t u = 0; u < d.nbu; ++u)
-    for (int32_t w = up_wi[u]; w < up_wi[u + 1]; ++w)
-      wi_end[w] = std::min<int64_t>(wi_start[w] + PAIR_CHUNK, pcount[u + 1]);
-  // store start/end interleaved: wi_start[2w], wi_start[2w+1]
-  std::vector<int32_t> wi_se(2 * d.nwi);
-  for (int64_t w = 0; w < d.nwi; ++w) { wi_se[2 * w] = wi_start[w]; wi_se[2 * w + 1] = wi_end[w]; }
-
-  // ---- permuted residual arrays
-  std::vector<int8_t> rkind(nr);
-  std::vector<int32_t> rcam(nr), rfeat(nr), rgrp(nr);
-  std::vector<double> rmeas(4 * nr);
-  for (int64_t j = 0; j < nr; ++j) {
-    int32_t i = order[j];
-    rkind[j] = kind[i]; rcam[j] = cam[i]; rfeat[j] = feat[i]; rgrp[j] = grp[i];
-    for (int c = 0; c < 4; ++c) rmeas[4 * j + c] = meas[4 * i + c];
-  }
-  std::vector<uint8_t> ent_type(na);
-  for (int64_t a = 0; a < na; ++a) ent_type[a] = a < d.nc ? ENT_CAM : (a < d.nc + d.npl ? ENT_PLANE : ENT_VP);
-
-  // ---- upload
+  Scratch S(&P.alloc, P.stream);
+  const int NT = 256;
+  const int64_t na = d.na, nf = d.nf;
   ba_status s;
+  auto oom = [&]() { return fail(P, BA_ERR_OOM, "device allocation failed"); };
+
+  // raw residual records (input order) on the device
+  int8_t* kind_d = S.get<int8_t>(nr);
+  int32_t *cam_d = S.get<int32_t>(nr), *feat_d = S.get<int32_t>(nr), *grp_d = S.get<int32_t>(nr);
+  double* meas_d = S.get<double>(4 * nr);
+  uint8_t* fixed_d = S.get<uint8_t>(d.nc);
+  if (!kind_d || !cam_d || !feat_d || !grp_d || !meas_d || !fixed_d) return oom();
+  if (nr) {
+    CU(cudaMemcpyAsync(kind_d, kind.data(), nr, cudaMemcpyHostToDevice, P.stream));
+    CU(cudaMemcpyAsync(cam_d, cam.data(), 4 * nr, cudaMemcpyHostToDevice, P.stream));
+    CU(cudaMemcpyAsync(feat_d, feat.data(), 4 * nr, cudaMemcpyHostToDevice, P.stream));
+    CU(cudaMemcpyAsync(grp_d, grp.data(), 4 * nr, cudaMemcpyHostToDevice, P.stream));
+    CU(cudaMemcpyAsync(meas_d, meas.data(), 32 * nr, cudaMemcpyHostToDevice, P.stream));
+  }
+  if (d.nc) CU(cudaMemcpyAsync(fixed_d, P.h_fixed.data(), d.nc, cudaMemcpyHostToDevice, P.stream));
+
+  // ---- feature-major order: stable sort by camera, then stable sort by feature
+  uint32_t *key = S.get<uint32_t>(nr), *order = S.get<uint32_t>(nr), *k2 = S.get<uint32_t>(nr), *v2 = S.get<uint32_t>(nr);
+  if (!key || !order || !k2 || !v2) return oom();
+  if (nr) {
+    k_iota_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(cam_d, nr, 1, key, order);
+    if ((s = radix_sort(P, S, key, order, k2, v2, nr, bits_for(d.nc + 1)))) return s;
+    k_gather_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(feat_d, order, nr, key);
+    if ((s = radix_sort(P, S, key, order, k2, v2, nr, bits_for(nf)))) return s;
+  }
+  // residual offsets per feature
+  int64_t* cnt64 = S.get<int64_t>(std::max(nf, na) + 1);
+  int64_t* off64 = S.get<int64_t>(std::max(nf, na) + 1);
+  if (!cnt64 || !off64) return oom();
+  CU(cudaMemsetAsync(cnt64, 0, sizeof(int64_t) * (nf + 1), P.stream));
+  if (nr) k_count<<<grid_of(nr, NT), NT, 0, P.stream>>>(feat_d, nr, (unsigned long long*)cnt64);
+  if ((s = scan_excl(P, S, cnt64, off64, nf))) return s;
+  P.fres_off = P.dnew<int32_t>(nf + 1);
+  if (!P.fres_off) return oom();
+  k_i64_to_i32<<<grid_of(nf + 1, NT), NT, 0, P.stream>>>(off64, nf + 1, P.fres_off);
+  {
+    int64_t v;
+    if ((s = read_i64(P, off64 + d.np, &v))) return s;
+    d.n_points_res_end = v;
+  }
+
+  // ---- slots
+  int* err_d = S.get<int>(1);
+  if (!err_d) return oom();
+  CU(cudaMemsetAsync(err_d, 0, sizeof(int), P.stream));
+  SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d};
+  int64_t* soff = S.get<int64_t>(nf + 1);
+  if (!soff) return oom();
+  k_slot_count<<<grid_of(nf, NT), NT, 0, P.stream>>>(sa, cnt64);
+  if ((s = scan_excl(P, S, cnt64, soff, nf))) return s;
+  int64_t ne;
+  if ((s = read_i64(P, soff + nf, &ne))) return s;
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, err_d, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+  CU(cudaStreamSynchronize(P.stream));
+  if (herr & 1) return fail(P, BA_ERR_ARG, "a feature may be associated with at most one plane");
+  if (herr & 2) return fail(P, BA_ERR_ARG, "a line may be associated with at most one VP");
+  if (ne > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many slots");
+  d.ne = ne;
+  P.fslot_off = P.dnew<int32_t>(nf + 1);
+  P.slot_ent = P.dnew<int32_t>(ne); P.slot_feat = P.dnew<int32_t>(ne); P.slot_type = P.dnew<uint8_t>(ne);
+  P.feat_plane_slot = P.dnew<int32_t>(nf);
+  P.rslot_c = P.dnew<int32_t>(nr); P.rslot_g = P.dnew<int32_t>(nr);
+  if (!P.fslot_off || !P.slot_ent || !P.slot_feat || !P.slot_type || !P.feat_plane_slot || !P.rslot_c || !P.rslot_g) return oom();
+  SlotFill sf{P.fslot_off, P.slot_ent, P.slot_feat, P.feat_plane_slot, P.rslot_c, P.rslot_g, P.slot_type};
+  k_slot_fill<<<grid_of(nf + 1, NT), NT, 0, P.stream>>>(sa, soff, sf);
+  {
+    int64_t v;
+    if ((s = read_i64(P, soff + d.np, &v))) return s;
+    P.line_slot0 = (int)v;
+  }
+
+  // ---- block pattern of S
+  Bitmap bm{S.get<uint32_t>(na * wpr), wpr};
+  int32_t* wpre = S.get<int32_t>(na * wpr);
+  if (!bm.w || !wpre) return oom();
+  CU(cudaMemsetAsync(bm.w, 0, sizeof(uint32_t) * na * wpr, P.stream));
+  if (na) {
+    k_pattern_diag<<<grid_of(na, NT), NT, 0, P.stream>>>(na, bm);
+    if (nf) k_pattern_pairs<<<grid_of(nf, NT), NT, 0, P.stream>>>(P.fslot_off, P.slot_ent, nf, bm);
+  }
+  int64_t *full_cnt = S.get<int64_t>(na + 1), *pad_cnt = S.get<int64_t>(na + 1), *up_cnt = S.get<int64_t>(na + 1);
+  int64_t *rowp = S.get<int64_t>(na + 1), *prow = S.get<int64_t>(na + 1), *uptr = S.get<int64_t>(na + 1);
+  int32_t* nlow = S.get<int32_t>(na);
+  if (!full_cnt || !pad_cnt || !up_cnt || !rowp || !prow || !uptr || !nlow) return oom();
+  if (na) k_pattern_rows<<<grid_of(na, NT), NT, 0, P.stream>>>(na, bm, wpre, full_cnt, pad_cnt, up_cnt, nlow);
+  if ((s = scan_excl(P, S, full_cnt, rowp, na))) return s;
+  if ((s = scan_excl(P, S, pad_cnt, prow, na))) return s;
+  if ((s = scan_excl(P, S, up_cnt, uptr, na))) return s;
+  int64_t nbf, nbp, nbu;
+  if ((s = read_i64(P, rowp + na, &nbf)) || (s = read_i64(P, prow + na, &nbp)) || (s = read_i64(P, uptr + na, &nbu))) return s;
+  if (nbp > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many blocks in the reduced system");
+  d.nbf = nbf; d.nbp = nbp; d.nbu = nbu;
+  P.row_ptr = P.dnew<int32_t>(na + 1); P.col = P.dnew<int32_t>(nbp); P.row_len = P.dnew<int32_t>(na);
+  P.up_row = P.dnew<int32_t>(nbu); P.up_full = P.dnew<int32_t>(nbu); P.up_mirror = P.dnew<int32_t>(nbu);
+  if (!P.row_ptr || !P.col || !P.row_len || !P.up_row || !P.up_full || !P.up_mirror) return oom();
+  RowFill rf{prow, uptr, wpre, nlow, P.col, P.up_row, P.up_full, P.up_mirror, P.row_ptr, P.row_len, full_cnt};
+  k_pattern_fill<<<grid_of(na + 1, NT), NT, 0, P.stream>>>(na, bm, rf);
+  P.h_prow_ptr.assign(na + 1, 0);
+  P.h_row_len.assign(na, 0);
+  CU(cudaMemcpyAsync(P.h_prow_ptr.data(), P.row_ptr, sizeof(int32_t) * (na + 1), cudaMemcpyDeviceToHost, P.stream));
+  if (na) CU(cudaMemcpyAsync(P.h_row_len.data(), P.row_len, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, P.stream));
+
+  // ---- slot pairs per upper block, in feature order, cut into work items
+  int64_t* poff = S.get<int64_t>(nf + 1);
+  if (!poff) return oom();
+  k_pair_count<<<grid_of(nf, NT), NT, 0, P.stream>>>(P.fslot_off, nf, cnt64);
+  if ((s = scan_excl(P, S, cnt64, poff, nf))) return s;
+  int64_t npair;
+  if ((s = read_i64(P, poff + nf, &npair))) return s;
+  if (npair > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many Schur pairs");
+  d.npair = npair;
+  uint32_t *pkey = S.get<uint32_t>(npair), *pval = S.get<uint32_t>(npair);
+  uint32_t *pk2 = S.get<uint32_t>(npair), *pv2 = S.get<uint32_t>(npair);
+  int32_t *gi = S.get<int32_t>(npair), *gj = S.get<int32_t>(npair);
+  unsigned long long* ucnt = S.get<unsigned long long>(nbu + 1);
+  if (!pkey || !pval || !pk2 || !pv2 || !gi || !gj || !ucnt) return oom();
+  CU(cudaMemsetAsync(ucnt, 0, sizeof(unsigned long long) * (nbu + 1), P.stream));
+  PairGen pg{P.fslot_off, P.slot_ent, wpre, nlow, P.slot_type, poff, uptr, bm, nf, pkey, pval, gi, gj, ucnt};
+  if (nf) k_pair_gen<<<grid_of(nf, NT), NT, 0, P.stream>>>(pg);
+  if ((s = radix_sort(P, S, pkey, pval, pk2, pv2, npair, bits_for(nbu)))) return s;
+  P.pair_a = P.dnew<int32_t>(npair); P.pair_b = P.dnew<int32_t>(npair);
+  if (!P.pair_a || !P.pair_b) return oom();
+  if (npair) k_pair_place<<<grid_of(npair, NT), NT, 0, P.stream>>>(pval, npair, gi, gj, P.pair_a, P.pair_b);
+  int64_t *pstart = S.get<int64_t>(nbu + 1), *nw = S.get<int64_t>(nbu + 1), *wstart = S.get<int64_t>(nbu + 1);
+  if (!pstart || !nw || !wstart) return oom();
+  if ((s = scan_excl(P, S, (const int64_t*)ucnt, pstart, nbu))) return s;
+  if (nbu) k_item_count<<<grid_of(nbu, NT), NT, 0, P.stream>>>(ucnt, nbu, nw);
+  if ((s = scan_excl(P, S, nw, wstart, nbu))) return s;
+  int64_t nwi;
+  if ((s = read_i64(P, wstart + nbu, &nwi))) return s;
+  if (nwi > (int64_t)INT32_MAX / 2 - 1) return fail(P, BA_ERR_ARG, "too many Schur work items");
+  d.nwi = nwi;
+  P.up_wi = P.dnew<int32_t>(nbu + 1); P.wi_start = P.dnew<int32_t>(2 * nwi);
+  if (!P.up_wi || !P.wi_start) return oom();
+  k_item_fill<<<grid_of(nbu + 1, NT), NT, 0, P.stream>>>(ucnt, pstart, wstart, nbu, P.up_wi, P.wi_start);
+
+  // ---- residual records in feature-major order
+  P.rkind = P.dnew<int8_t>(nr); P.rcam = P.dnew<int32_t>(nr); P.rfeat = P.dnew<int32_t>(nr); P.rgrp = P.dnew<int32_t>(nr);
+  P.meas64 = P.dnew<double>(4 * nr);
+  if (!P.rkind || !P.rcam || !P.rfeat || !P.rgrp || !P.meas64) return oom();
+  if (nr) {
+    Permute pm{order, kind_d, cam_d, feat_d, grp_d, (const double4*)meas_d, P.rkind, P.rcam, P.rfeat, P.rgrp,
+               (double4*)P.meas64, nr};
+    k_permute<<<grid_of(nr, NT), NT, 0, P.stream>>>(pm);
+  }
+  P.ent_type = P.dnew<uint8_t>(na);
+  if (!P.ent_type) return oom();
+  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, P.ent_type);
+
+  // ---- parameters
 #define UP(dst, src) if ((s = upload(P, dst, src)) != BA_OK) return s
-  UP(P.rkind, rkind); UP(P.rcam, rcam); UP(P.rfeat, rfeat); UP(P.rgrp, rgrp);
-  UP(P.rslot_c, rslot_c); UP(P.rslot_g, rslot_g); UP(P.meas64, rmeas);
-  UP(P.fres_off, fres_off); UP(P.fslot_off, fslot_off);
-  UP(P.slot_ent, slot_ent); UP(P.slot_feat, slot_feat); UP(P.slot_type, slot_type);
-  UP(P.feat_plane_slot, feat_plane_slot); UP(P.ent_type, ent_type);
-  UP(P.row_ptr, prow_ptr); UP(P.col, pcol); UP(P.row_len, row_len);
-  UP(P.up_row, up_row); UP(P.up_full, up_full); UP(P.up_mirror, up_mirror); UP(P.up_wi, up_wi);
-  UP(P.pair_a, pair_a); UP(P.pair_b, pair_b); UP(P.wi_start, wi_se);
   UP(P.cam_fixed, P.h_fixed);
   for (int k = 0; k < 2; ++k) {
     auto& S_ = P.ps[k];
     UP(S_.cam, P.h_cam); UP(S_.pts, P.h_pts); UP(S_.lin, P.h_lin); UP(S_.pln, P.h_pln); UP(S_.vps, P.h_vps);
     S_.camD = P.dnew<double>(d.nc * CAM_STRIDE);
     S_.grpD = P.dnew<double>((d.npl + d.nv) * GRP_STRIDE);
-    if (!S_.camD || !S_.grpD) return fail(P, BA_ERR_OOM, "device allocation failed");
+    if (!S_.camD || !S_.grpD) return oom();
   }
   P.cur = 0;
 #undef UP
+  CU(cudaGetLastError());
+  // the scratch buffers are released when this function returns: finish the work that reads them
   CU(cudaStreamSynchronize(P.stream));
   return BA_OK;
 }
