@@ -270,8 +270,9 @@ static ba_status freeze(ba_problem* p) {
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   ok &= A(p->part, T * PART * (size_t)d.nwi);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
-  p->featg = p->dnew<double>(4 * d.nf); p->featz = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
-  ok &= p->featV && p->featVinv && p->featg && p->featz && p->dfeat;
+  p->featg = p->dnew<double>(4 * d.nf); p->featu = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
+  p->featL = p->dnew<double>(10 * d.nf);
+  ok &= p->featV && p->featVinv && p->featg && p->featu && p->dfeat && p->featL;
   double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap, &p->sdiag};
   for (double** v : vecs) { *v = p->dnew<double>(6 * d.na); ok &= *v != nullptr; }
   int64_t maxb = std::max<int64_t>({(d.nr + 255) / 256, (d.nf + 127) / 128, (d.na * 32 + 255) / 256, (d.na + 127) / 128,

@@ -132,6 +132,7 @@ struct ba_problem {
   int8_t* rkind = nullptr;
   int32_t *rcam = nullptr, *rfeat = nullptr, *rgrp = nullptr, *rslot_c = nullptr, *rslot_g = nullptr;
   double* meas64 = nullptr;
+  int32_t* cost_order = nullptr;   // residual indices sorted by kind (feature-major inside a kind)
   void* measT = nullptr;
   int32_t *fres_off = nullptr, *fslot_off = nullptr;
   int32_t *slot_ent = nullptr, *slot_feat = nullptr;
@@ -152,7 +153,7 @@ struct ba_problem {
   cudaError_t pcg_err = cudaSuccess;
   // numeric arrays
   void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotZ = nullptr, *slotB = nullptr;
-  double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featz = nullptr, *dfeat = nullptr;
+  double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featu = nullptr, *featL = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr, *part = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   float2* phl = nullptr;        // mixed path: p split into (hi, lo) floats for the SpMV

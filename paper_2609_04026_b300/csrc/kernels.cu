@@ -5,11 +5,11 @@
 //                   reduction of V_f = sum J_f^T w J_f, g_f, and per (feature, entity)
 //                   slot W^T, the direct J_a^T w J_a block, J_a^T w r and, for cameras
 //                   of a plane feature, J_cam^T w J_plane (thread per feature)
-//   k_invert        K2: (V_f + lambda D_f)^-1 by FP64 Cholesky, z_f = V^-1 g_f, and per
-//                   slot Y^T = V^-1 W^T and b-part -g_a + W z_f
+//   k_invert        K2: (V_f + lambda D_f) = L L^T by FP64 Cholesky; V^-1, L^-1, u_f = L^-1 g_f
+//   k_whiten        K2: per slot Z = L^-1 W (double-single products) and b-part -G_e + Z^T u_f
 //   k_schur_items   K3: atomic-free Schur accumulation.  Every upper block of S owns a
 //                   list of slot pairs; each work item (<= 64 pairs) sums
-//                   direct terms - Y_a^T W_b in a fixed order into a partial
+//                   direct terms - Z_a^T Z_b in a fixed order into a partial
 //   k_schur_blocks  K3: sums the partials of each block in order, adds lambda D on the
 //                   diagonal, writes both triangles of the full block-CSR S and b
 //   k_precond       K4: block-Jacobi inverse of the diagonal blocks of S (FP64 Cholesky)
@@ -465,12 +465,12 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int
 // ============================================================================
 template <class T>
 struct InvArgs {
-  const int32_t* fslot_off;
+  const int32_t *fslot_off, *slot_feat;
   const double *V, *g;
   const T *W, *G;
-  double *Vinv, *z;
+  double *Vinv, *u, *L;
   T *Z, *B;
-  int64_t np, nf;
+  int64_t np, nf, ne;
   double lambda;
   DevScalars* S;
 };
@@ -543,37 +543,31 @@ __device__ __forceinline__ void whiten_slot(const float (&Lh)[K][K], const float
     }
 }
 
+// the damped landmark inverse of one feature: V^-1 (for the back-substitution), L^-1 and u = L^-1 g_f
 template <class T, int K>
-__device__ void invert_feature(const InvArgs<T>& a, int64_t f) {
-  double Vi[K][K], Li[K][K];
+__device__ void invert_core(const InvArgs<T>& a, int64_t f, double (&Li)[K][K], T (&ut)[K]) {
+  double Vi[K][K];
   int flag = 0;
   invert_damped<K>(a.V + 10 * f, a.lambda, Vi, Li, &flag);
   if (flag) atomicOr(&a.S->flags, 1);
-  double gz[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    double s = 0;
-#pragma unroll
-    for (int j = 0; j < K; ++j) s += Vi[i][j] * a.g[4 * f + j];
-    gz[i] = s;
-  }
   double* vo = a.Vinv + 10 * f;
 #pragma unroll
   for (int i = 0; i < K; ++i)
 #pragma unroll
     for (int j = i; j < K; ++j) vo[up_idx(i, j, K)] = Vi[i][j];
-#pragma unroll
-  for (int i = 0; i < K; ++i) a.z[4 * f + i] = gz[i];
   // u = L^-1 g_f: the slot's share of b is -G_e + Z_e^T u  (= -G_e + W_e^T V^-1 g_f)
-  T ut[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     double s = 0;
 #pragma unroll
     for (int k = 0; k <= i; ++k) s += Li[i][k] * a.g[4 * f + k];
+    a.u[4 * f + i] = s;
     ut[i] = (T)s;
   }
-  T Lh[K][K], Ll[K][K];
+}
+
+template <class T, int K>
+__device__ __forceinline__ void split_L(const double (&Li)[K][K], T (&Lh)[K][K], T (&Ll)[K][K]) {
 #pragma unroll
   for (int i = 0; i < K; ++i)
 #pragma unroll
@@ -581,34 +575,86 @@ __device__ void invert_feature(const InvArgs<T>& a, int64_t f) {
       Lh[i][j] = (T)Li[i][j];
       Ll[i][j] = (T)(Li[i][j] - (double)Lh[i][j]);
     }
-  for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
-    const T* W = a.W + (size_t)e * SW;
-    T w[K * 6], z[K * 6];
+}
+
+// one slot: Z_e = L^-1 W_e and the slot's share of b
+template <class T, int K>
+__device__ __forceinline__ void whiten_record(const InvArgs<T>& a, int64_t e, const double (&Li)[K][K], const T (&Lh)[K][K],
+                                              const T (&Ll)[K][K], const T (&ut)[K]) {
+  const T* W = a.W + (size_t)e * SW;
+  T w[K * 6], z[K * 6];
 #pragma unroll
-    for (int i = 0; i < K * 6; ++i) w[i] = W[i];
-    if constexpr (sizeof(T) == 8) whiten_slot<K>(Li, (const double*)w, (double*)z);
-    else whiten_slot<K>(Lh, Ll, w, z);
-    T* Z = a.Z + (size_t)e * SW;
+  for (int i = 0; i < K * 6; ++i) w[i] = W[i];
+  if constexpr (sizeof(T) == 8) whiten_slot<K>(Li, (const double*)w, (double*)z);
+  else whiten_slot<K>(Lh, Ll, w, z);
+  T* Z = a.Z + (size_t)e * SW;
 #pragma unroll
-    for (int i = 0; i < K * 6; ++i) Z[i] = z[i];
-    const T* G = a.G + (size_t)e * SG;
-    T* B = a.B + (size_t)e * SG;
+  for (int i = 0; i < K * 6; ++i) Z[i] = z[i];
+  const T* G = a.G + (size_t)e * SG;
+  T* B = a.B + (size_t)e * SG;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      T s = -G[j];
+  for (int j = 0; j < 6; ++j) {
+    T s = -G[j];
 #pragma unroll
-      for (int k = 0; k < K; ++k) s += z[k * 6 + j] * ut[k];
-      B[j] = s;
-    }
+    for (int k = 0; k < K; ++k) s += z[k * 6 + j] * ut[k];
+    B[j] = s;
   }
+}
+
+// a whole feature in one thread (the batched-window kernel)
+template <class T, int K>
+__device__ void invert_feature(const InvArgs<T>& a, int64_t f) {
+  double Li[K][K];
+  T ut[K], Lh[K][K], Ll[K][K];
+  invert_core<T, K>(a, f, Li, ut);
+  split_L<T, K>(Li, Lh, Ll);
+  for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) whiten_record<T, K>(a, e, Li, Lh, Ll, ut);
+}
+
+// grid path: a thread per feature factors the block and stores L^-1 (lower triangle, up_idx of the
+// transpose), then a thread per slot whitens that slot, so that slot records stream coalesced
+template <class T, int K>
+__device__ void invert_store(const InvArgs<T>& a, int64_t f) {
+  double Li[K][K];
+  T ut[K];
+  invert_core<T, K>(a, f, Li, ut);
+  double* lo = a.L + 10 * f;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) lo[up_idx(j, i, K)] = Li[i][j];
 }
 
 template <class T>
 __global__ void __launch_bounds__(128) k_invert(InvArgs<T> a) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.nf) return;
-  if (f < a.np) invert_feature<T, 3>(a, f);
-  else invert_feature<T, 4>(a, f);
+  if (f < a.np) invert_store<T, 3>(a, f);
+  else invert_store<T, 4>(a, f);
+}
+
+template <class T, int K>
+__device__ __forceinline__ void whiten_from_store(const InvArgs<T>& a, int64_t e, int64_t f) {
+  double Li[K][K];
+  T ut[K], Lh[K][K], Ll[K][K];
+  const double* lo = a.L + 10 * f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    ut[i] = (T)a.u[4 * f + i];
+#pragma unroll
+    for (int j = 0; j < K; ++j) Li[i][j] = j <= i ? lo[up_idx(j, i, K)] : 0.0;
+  }
+  split_L<T, K>(Li, Lh, Ll);
+  whiten_record<T, K>(a, e, Li, Lh, Ll, ut);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_whiten(InvArgs<T> a) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= a.ne) return;
+  const int64_t f = a.slot_feat[e];
+  if (f < a.np) whiten_from_store<T, 3>(a, e, f);
+  else whiten_from_store<T, 4>(a, e, f);
 }
 
 // ============================================================================
@@ -742,24 +788,68 @@ struct BlockArgs {
   double lambda;
 };
 
+// sum of work-item partials: FP64 for a double working type; for float partials a double-single
+// (hi, lo) pair of floats with TwoSum, since a warp-wide FP64 add or conversion costs dozens of float
+// instructions on this part.  value() rounds once to double.
+template <class T>
+struct PartSum;
+template <>
+struct PartSum<double> {
+  double s = 0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ double rounded() const { return s; }
+};
+template <>
+struct PartSum<float> {
+  float hi = 0, lo = 0;
+  __device__ __forceinline__ void add(float v) {
+    const float sm = hi + v;
+    const float bp = sm - hi;
+    lo += (hi - (sm - bp)) + (v - bp);
+    hi = sm;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ float rounded() const { return hi + lo; }
+};
+
 template <class T>
 __device__ void schur_block(const BlockArgs<T>& a, int64_t u) {
   const int row = a.up_row[u];
   const int fpos = a.up_full[u];
   const bool diag = a.col[fpos] == row;
-  double s[36];   // partials summed in double, rounded to the storage type once
-  double bb[6], hh[6];
-#pragma unroll
-  for (int i = 0; i < 36; ++i) s[i] = 0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) { bb[i] = 0; hh[i] = 0; }
+  PartSum<T> ps[36];
   for (int w = a.up_wi[u]; w < a.up_wi[u + 1]; ++w) {
     const T* p = a.part + (size_t)w * PART;
 #pragma unroll
-    for (int i = 0; i < 36; ++i) s[i] += (double)p[i];
-    if (diag)
+    for (int i = 0; i < 36; ++i) ps[i].add(p[i]);
+  }
+  if (!diag) {
+    // an off-diagonal block: rounded once to the storage type and written with its mirror
 #pragma unroll
-      for (int i = 0; i < 6; ++i) { bb[i] += (double)p[36 + i]; hh[i] += (double)p[42 + i]; }
+    for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)ps[i].rounded();
+    const int mpos = a.up_mirror[u];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) a.Sval[s_idx(mpos, j * 6 + i)] = (T)ps[i * 6 + j].rounded();
+    return;
+  }
+  double s[36];
+#pragma unroll
+  for (int i = 0; i < 36; ++i) s[i] = ps[i].value();
+  double bb[6], hh[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) { bb[i] = 0; hh[i] = 0; }
+  if (diag) {
+    PartSum<T> pb[6], ph[6];
+    for (int w = a.up_wi[u]; w < a.up_wi[u + 1]; ++w) {
+      const T* p = a.part + (size_t)w * PART;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) { pb[i].add(p[36 + i]); ph[i].add(p[42 + i]); }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { bb[i] = pb[i].value(); hh[i] = ph[i].value(); }
   }
   if (diag) {
     // a diagonal block sums -Z_e^T Z_e (symmetric by construction) and the symmetric H_e; the
@@ -795,14 +885,6 @@ __device__ void schur_block(const BlockArgs<T>& a, int64_t u) {
     for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
 #pragma unroll
     for (int i = 0; i < 6; ++i) a.sdiag[6 * (size_t)row + i] = (double)(T)s[i * 6 + i];
-  } else {
-#pragma unroll
-    for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
-    const int mpos = a.up_mirror[u];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) a.Sval[s_idx(mpos, j * 6 + i)] = (T)s[i * 6 + j];
   }
 }
 
@@ -1425,7 +1507,7 @@ __global__ void k_candidate(CandArgs a) {
 
 struct CostArgs {
   const int8_t* rkind;
-  const int32_t *rcam, *rfeat, *rgrp;
+  const int32_t *rcam, *rfeat, *rgrp, *order;
   const double *meas, *camD, *grpD, *pts, *lin;
   int64_t nr, np, npl;
   LossW loss;
@@ -1469,9 +1551,9 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
 }
 
 __global__ void __launch_bounds__(256) k_cost(CostArgs a) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double v[2] = {0, 0};
-  if (i < a.nr) cost_residual(a, i, v);
+  if (t < a.nr) cost_residual(a, a.order[t], v);
   double tot[2];
   if (grid_reduce<2>(v, a.red, &a.S->counter[4], tot) && threadIdx.x == 0) {
     if (a.candidate) { a.S->Enew = tot[0]; a.S->Epxnew = tot[1]; }
@@ -1564,10 +1646,11 @@ template <class T>
 void launch_invert(Problem& P, double lambda) {
   const Dims& d = P.d;
   InvArgs<T> a;
-  a.fslot_off = P.fslot_off; a.V = P.featV; a.g = P.featg; a.W = (const T*)P.slotW; a.G = (const T*)P.slotG;
-  a.Vinv = P.featVinv; a.z = P.featz; a.Z = (T*)P.slotZ; a.B = (T*)P.slotB;
-  a.np = d.np; a.nf = d.nf; a.lambda = lambda; a.S = P.S;
+  a.fslot_off = P.fslot_off; a.slot_feat = P.slot_feat; a.V = P.featV; a.g = P.featg; a.W = (const T*)P.slotW;
+  a.G = (const T*)P.slotG; a.Vinv = P.featVinv; a.u = P.featu; a.L = P.featL; a.Z = (T*)P.slotZ; a.B = (T*)P.slotB;
+  a.np = d.np; a.nf = d.nf; a.ne = d.ne; a.lambda = lambda; a.S = P.S;
   if (d.nf) { ++P.launches; k_invert<T><<<nblk(d.nf, 128), 128, 0, P.stream>>>(a); }
+  if (d.ne) { ++P.launches; k_whiten<T><<<nblk(d.ne, 128), 128, 0, P.stream>>>(a); }
 }
 
 template <class T>
@@ -1677,7 +1760,7 @@ void launch_cost(Problem& P, bool candidate) {
   const Dims& d = P.d;
   auto& s = P.ps[candidate ? 1 - P.cur : P.cur];
   CostArgs a;
-  a.rkind = P.rkind; a.rcam = P.rcam; a.rfeat = P.rfeat; a.rgrp = P.rgrp; a.meas = P.meas64;
+  a.rkind = P.rkind; a.rcam = P.rcam; a.rfeat = P.rfeat; a.rgrp = P.rgrp; a.meas = P.meas64; a.order = P.cost_order;
   a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin;
   a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
   a.candidate = candidate ? 1 : 0;
@@ -1902,7 +1985,7 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
     double e = 0, epx = 0;
     for (int64_t i = threadIdx.x; i < W.nr; i += NT) {
       double v[2] = {0, 0};
-      cost_residual(co, i, v);
+      cost_residual(co, co.order[i], v);
       e += v[0]; epx += v[1];
     }
     cta_sum2<NT>(e, epx, red2);
@@ -1965,7 +2048,8 @@ void fill_window_desc(Problem& P, void* out) {
   a.loss = make_loss(P.opt);
   InvArgs<T>& ia = W.inv;
   ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
-  ia.Vinv = P.featVinv; ia.z = P.featz; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB; ia.np = d.np; ia.nf = d.nf;
+  ia.slot_feat = P.slot_feat; ia.Vinv = P.featVinv; ia.u = P.featu; ia.L = P.featL; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB;
+  ia.np = d.np; ia.nf = d.nf; ia.ne = d.ne;
   ia.lambda = 0; ia.S = P.S;
   SchurArgs<T>& sa = W.schur;
   sa.pair_a = P.pair_a; sa.pair_b = P.pair_b; sa.wi_se = P.wi_start; sa.Z = (const T*)P.slotZ;
@@ -1982,7 +2066,7 @@ void fill_window_desc(Problem& P, void* out) {
   CandArgs& c = W.cand;
   c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
   CostArgs& co = W.cost;
-  co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64;
+  co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64; co.order = P.cost_order;
   co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;
   W.dec = DecideArgs{P.S, P.opt.min_gain, P.opt.lambda_min, P.opt.lambda_max};
   for (int s = 0; s < 2; ++s) {

@@ -534,6 +534,11 @@ __global__ void k_permute(Permute a) {
   a.rmeas[j] = a.meas[i];
 }
 
+__global__ void k_kind_key(const int8_t* __restrict__ kind, int64_t n, uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) { key[j] = (uint32_t)kind[j]; val[j] = (uint32_t)j; }
+}
+
 __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, uint8_t* __restrict__ t) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a < na) t[a] = a < nc ? ENT_CAM : (a < nc + npl ? ENT_PLANE : ENT_VP);
@@ -785,6 +790,14 @@ ba_status build_structure(Problem& P) {
     Permute pm{order, kind_d, cam_d, feat_d, grp_d, (const double4*)meas_d, P.rkind, P.rcam, P.rfeat, P.rgrp,
                (double4*)P.meas64, nr};
     k_permute<<<grid_of(nr, NT), NT, 0, P.stream>>>(pm);
+  }
+  // the cost pass visits the residuals kind by kind (feature-major inside a kind), so that the lanes of a
+  // warp evaluate the same residual formula
+  P.cost_order = P.dnew<int32_t>(nr);
+  if (!P.cost_order) return oom();
+  if (nr) {
+    k_kind_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(P.rkind, nr, key, (uint32_t*)P.cost_order);
+    if ((s = radix_sort(P, S, key, (uint32_t*)P.cost_order, k2, v2, nr, 8))) return s;
   }
   P.ent_type = P.dnew<uint8_t>(na);
   if (!P.ent_type) return oom();
