@@ -112,12 +112,13 @@ typedef struct ba_step_report {
   double pcg_rel;               /* final relative PCG residual |r_k| / |b| */
   int pcg_iters;
   int accepted;
-  int converged;                /* accepted and |dE_px|/E_px < rel_cost_tol */
+  int converged;                /* accepted with |dE_px|/E_px < rel_cost_tol, or rejected at lambda_max (no step
+                                   lowers the cost at the working precision) */
   int relinearized;             /* 1 if the Jacobians were recomputed for this step */
   float ms_linearize, ms_schur, ms_pcg, ms_update;  /* device time per phase */
   /* device time per kernel stage, measured with CUDA events on the problem's stream:
-   * [0] derive + linearize (K1), [1] landmark inverse (K2), [2] Schur work items (K3a),
-   * [3] Schur block sums (K3b), [4] block-Jacobi (K4), [5] PCG (K5/K6, including the host
+   * [0] derive + linearize (K1), [1] landmark inverse (K2), [2] Schur work units (K3a),
+   * [3] Schur diagonal / split-block sums (K3b), [4] block-Jacobi (K4), [5] PCG (K5/K6, including the host
    * reads of the stop flag), [6] back-substitution (K7), [7] candidate (K8a), [8] cost (K8b),
    * [9] decision (K9) */
   float ms_kernel[10];
@@ -192,7 +193,7 @@ ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* d
  * next window from a device queue (largest first) and runs its iterations on the device (the same linearise /
  * invert / Schur / PCG / back-substitute / cost / decide steps as ba_lm_step); every window keeps its own
  * damping and accept / reject state.  A window's `converged` flag reports whether some accepted step met
- * rel_cost_tol (iteration then continues to lm_iters).  autotune != 0 times one LM step of each candidate launch
+ * rel_cost_tol or some step was rejected at lambda_max (iteration then continues to lm_iters).  autotune != 0 times one LM step of each candidate launch
  * shape (threads per CTA, CTAs per SM) from the same state, keeps the fastest and caches it per (GPU,
  * precision, size class); the chosen shape is readable with ba_batch_launch_shape(windows[0], ...).
  * reports (n, may be NULL): iters, accepted steps, converged, initial and final cost; ms_total = the graph's

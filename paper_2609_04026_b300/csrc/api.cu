@@ -268,7 +268,6 @@ static ba_status freeze(ba_problem* p) {
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
   ok &= A(p->Sval, T * BS2 * (size_t)d.nbp);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
-  ok &= A(p->part, T * PART * (size_t)d.nwi);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
   p->featg = p->dnew<double>(4 * d.nf); p->featu = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
   p->featL = p->dnew<double>(10 * d.nf);
@@ -411,6 +410,10 @@ static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
     // the accepted cost becomes the current cost
     h.E = h.Enew; h.Epx = h.Epxnew;
     CUDA_OR(p, cudaMemcpyAsync(&p->S->E, &h.E, 2 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  } else if (lam >= p->opt.lambda_max) {
+    // rejected at the largest damping: no step lowers the cost at the working precision (the analogue of
+    // a trust region shrunk to its minimum radius), so the iteration has converged
+    r.converged = 1;
   }
   if (rep) *rep = r;
   if (!std::isfinite(h.E)) return set_err(p, BA_ERR_NUMERIC, "non-finite cost");

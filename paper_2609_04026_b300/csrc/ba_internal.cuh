@@ -47,7 +47,6 @@ constexpr int SW = 24;  // W^T (k x 6), k = 3 (point) or 4 (line)
 constexpr int SH = 21;  // upper triangle of the direct 6x6 block J_a^T w J_a
 constexpr int SG = 6;   // J_a^T w r
 constexpr int SC = 18;  // camera slot: J_cam^T w J_plane (6 x 3)
-constexpr int PART = BS2 + 12;  // partial of one Schur work item: 36 S + 6 b + 6 diag(H)
 
 enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
 
@@ -66,7 +65,8 @@ using Problem = ::ba_problem;
 
 struct Dims {
   int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
-  int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0, nwi = 0;  // nbf stored blocks, nbp padded
+  int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0;  // nbf stored blocks, nbp padded
+  int64_t nun = 0, nmulti = 0;   // Schur work units of the grid path; blocks split over several units
   int64_t n_points_res_end = 0;  // residuals of points are [0, this); lines follow
 };
 
@@ -142,8 +142,12 @@ struct ba_problem {
   // reduced system pattern: padded, interleaved storage (row_ptr / col over padded positions)
   int32_t *row_ptr = nullptr, *col = nullptr;
   std::vector<int32_t> h_prow_ptr, h_row_len;
-  int32_t *up_row = nullptr, *up_full = nullptr, *up_mirror = nullptr, *up_wi = nullptr;
-  int32_t *pair_a = nullptr, *pair_b = nullptr, *wi_start = nullptr;   // pair_b bit 31: camera-plane pair
+  int32_t *up_row = nullptr, *up_full = nullptr, *up_mirror = nullptr;
+  int32_t *pair_a = nullptr, *pair_b = nullptr;   // pair_b bit 31: camera-plane pair
+  // grid-path Schur work units: pair range, block, processing order (long units first), first unit of
+  // every block, and the blocks whose units leave FP64 partials (48 per unit in upart)
+  int32_t *un_se = nullptr, *un_blk = nullptr, *un_order = nullptr, *up_un = nullptr, *multi_blk = nullptr;
+  double* upart = nullptr;
   int line_slot0 = 0;           // first slot of a line feature
   // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are
   // cut into chunks [chunk_beg[q], chunk_beg[q+1]) for q in [row_chunk0[r], row_chunk0[r+1])
@@ -154,7 +158,7 @@ struct ba_problem {
   // numeric arrays
   void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotZ = nullptr, *slotB = nullptr;
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featu = nullptr, *featL = nullptr, *dfeat = nullptr;
-  void *Sval = nullptr, *Minv = nullptr, *part = nullptr;
+  void *Sval = nullptr, *Minv = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   float2* phl = nullptr;        // mixed path: p split into (hi, lo) floats for the SpMV
   int32_t* row_len = nullptr;   // stored (non-padding) blocks per row of S

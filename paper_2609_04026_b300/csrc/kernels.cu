@@ -660,137 +660,38 @@ __global__ void __launch_bounds__(128) k_whiten(InvArgs<T> a) {
 // ============================================================================
 // K3: Schur complement, atomic-free
 // ============================================================================
-template <class T>
-struct SchurArgs {
-  const int32_t *pair_a, *pair_b, *wi_se;
-  const T *Z, *H, *B, *C;
-  T* part;
-  int64_t nwi;
-  int line_slot0;   // slots of lines start here (slots are stored feature-major, points first)
-};
-
-// one slot record (24 values) with 16-byte vector loads
-__device__ __forceinline__ void load24(const float* __restrict__ p, float (&v)[24]) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float4 t = __ldg(q + k);
-    v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
-  }
-}
-__device__ __forceinline__ void load24(const double* __restrict__ p, double (&v)[24]) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const double2 t = __ldg(q + k);
-    v[2 * k] = t.x; v[2 * k + 1] = t.y;
-  }
-}
-
-// acc -= Za^T Zb over the first k rows (k = 3 for points, 4 for lines; the 4th row of a point's Z is
-// never written and must not be read into the sum).  W_a V^-1 W_b^T = (L^-1 W_a)^T (L^-1 W_b).
-template <class T>
-__device__ __forceinline__ void sub_yw(const T (&y)[24], const T (&w)[24], bool line, T (&acc)[6][6]) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    if (c == 3 && !line) break;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) acc[i][j] -= y[c * 6 + i] * w[c * 6 + j];
-  }
-}
-
-template <class T>
-__device__ __forceinline__ void direct_terms(const SchurArgs<T>& a, int ea, int eb, bool cam_plane, T (&acc)[6][6],
-                                             T (&bacc)[6], T (&hacc)[6]) {
-  if (ea == eb) {
-    const T* H = a.H + (size_t)ea * SH;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = i; j < 6; ++j) {
-        const T h = H[up_idx(i, j, 6)];
-        acc[i][j] += h;
-        if (j != i) acc[j][i] += h;
-      }
-    const T* B = a.B + (size_t)ea * SG;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      bacc[i] += B[i];
-      hacc[i] += H[up_idx(i, i, 6)];
-    }
-  } else if (cam_plane) {
-    const T* Cm = a.C + (size_t)ea * SC;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) acc[i][j] += Cm[i * 3 + j];
-  }
-}
-
-// A thread sums one work item (<= 64 slot pairs of one upper block of S).  Pairs are taken two at a
-// time with both pairs' records loaded before either product, so that a thread keeps two pairs of
-// loads in flight.  pair_b carries a flag in bit 31: the pair is (camera slot, plane slot) of one
-// feature and its direct J_cam^T w J_plane block is added.
-template <class T>
-__device__ void schur_item(const SchurArgs<T>& a, int64_t w) {
-  const int s0 = a.wi_se[2 * w], s1 = a.wi_se[2 * w + 1];
-  T acc[6][6], bacc[6], hacc[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    bacc[i] = 0; hacc[i] = 0;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) acc[i][j] = 0;
-  }
-  for (int q = s0; q < s1; q += 2) {
-    const bool two = q + 1 < s1;
-    const int ea0 = a.pair_a[q];
-    const unsigned pb0 = (unsigned)a.pair_b[q];
-    const int ea1 = two ? a.pair_a[q + 1] : ea0;
-    const unsigned pb1 = two ? (unsigned)a.pair_b[q + 1] : pb0;
-    const int eb0 = (int)(pb0 & 0x7fffffffu), eb1 = (int)(pb1 & 0x7fffffffu);
-    T y0[24], w0[24], y1[24], w1[24];
-    load24(a.Z + (size_t)ea0 * SW, y0);
-    load24(a.Z + (size_t)eb0 * SW, w0);
-    load24(a.Z + (size_t)ea1 * SW, y1);
-    load24(a.Z + (size_t)eb1 * SW, w1);
-    sub_yw(y0, w0, ea0 >= a.line_slot0, acc);
-    direct_terms(a, ea0, eb0, (pb0 >> 31) != 0u, acc, bacc, hacc);
-    if (two) {
-      sub_yw(y1, w1, ea1 >= a.line_slot0, acc);
-      direct_terms(a, ea1, eb1, (pb1 >> 31) != 0u, acc, bacc, hacc);
-    }
-  }
-  T* o = a.part + (size_t)w * PART;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) o[i * 6 + j] = acc[i][j];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) { o[36 + i] = bacc[i]; o[42 + i] = hacc[i]; }
-}
-
-template <class T>
-__global__ void __launch_bounds__(128) k_schur_items(SchurArgs<T> a) {
-  int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (w < a.nwi) schur_item<T>(a, w);
-}
-
+// Every upper block of S owns the list of slot pairs (e_a, e_b) of the features that see both of its
+// entities, in feature order; the list is cut into work units of at most UNIT_MAX pairs.  A unit sums
+//   sum over its pairs of  direct(e_a, e_b) - Z_a^T Z_b        (W_a V^-1 W_b^T = (L^-1 W_a)^T (L^-1 W_b))
+// entry by entry in pair order, where direct() is the slot's J_a^T w J_a block on the diagonal and the
+// camera-plane block J_cam^T w J_plane of a plane feature (pair_b bit 31).  A float working type sums in
+// double-single arithmetic across lanes.  An off-diagonal block that fits one unit is written to S with
+// its mirror directly; the units of a diagonal block or of a longer block leave FP64 partials that a
+// finishing pass adds in unit order before the damping.  The grid path and the batched-window path run
+// the same warp-level unit code, so both form every entry with the same operations in the same order.
 template <class T>
 struct BlockArgs {
-  const int32_t *up_row, *up_full, *up_mirror, *up_wi, *col;
+  const int32_t *up_row, *up_full, *up_mirror, *col;
   const uint8_t *ent_type, *cam_fixed;
-  const T* part;
   T* Sval;
   double *b, *Dg, *sdiag;
-  int64_t nbu, nc;
+  int64_t nc;
   double lambda;
 };
 
-// sum of work-item partials: FP64 for a double working type; for float partials a double-single
-// (hi, lo) pair of floats with TwoSum, since a warp-wide FP64 add or conversion costs dozens of float
-// instructions on this part.  value() rounds once to double.
+template <class T>
+struct UnitArgs {
+  const int32_t *un_se, *un_blk, *un_order, *up_un, *pair_a, *pair_b, *multi;
+  const T *Z, *H, *B, *C;
+  double* upart;   // 48 per unit: 36 S, 6 b, 6 diag(H)
+  int64_t nun, nmulti;
+  int line_slot0;
+  BlockArgs<T> fb;
+};
+
+// running sum of a unit's terms: FP64 for a double working type; for float a double-single (hi, lo)
+// pair with TwoSum, since a warp-wide FP64 add or conversion costs dozens of float instructions on
+// this part.  value() rounds once to double, rounded() once to float.
 template <class T>
 struct PartSum;
 template <>
@@ -813,85 +714,244 @@ struct PartSum<float> {
   __device__ __forceinline__ float rounded() const { return hi + lo; }
 };
 
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// entry (i, j) of Z_a^T Z_b (rows at stride 6; three rows for a point, four for a line), with explicit
+// operations so that every kernel forms it identically
 template <class T>
-__device__ void schur_block(const BlockArgs<T>& a, int64_t u) {
-  const int row = a.up_row[u];
-  const int fpos = a.up_full[u];
-  const bool diag = a.col[fpos] == row;
-  PartSum<T> ps[36];
-  for (int w = a.up_wi[u]; w < a.up_wi[u + 1]; ++w) {
-    const T* p = a.part + (size_t)w * PART;
+__device__ __forceinline__ T pair_dot(const T* za, const T* zb, int i, int j, bool line) {
+  T t = mul_rn(za[i], zb[j]);
+  t = fma(za[6 + i], zb[6 + j], t);
+  t = fma(za[12 + i], zb[12 + j], t);
+  if (line) t = fma(za[18 + i], zb[18 + j], t);
+  return t;
+}
+
+// direct term of entry (i, j) for a pair of a diagonal block or a camera-plane pair
+template <class T>
+__device__ __forceinline__ T pair_direct(const UnitArgs<T>& a, int ea, bool diag, bool cam_plane, int i, int j) {
+  if (diag) return a.H[(size_t)ea * SH + (i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6))];
+  if (cam_plane && j < 3) return a.C[(size_t)ea * SC + i * 3 + j];
+  return T(0);
+}
+
+// a diagonal block of S from its sums: symmetric part, damping lambda D on the real dimensions, a unit
+// diagonal on padding and held camera components; writes S, b, D and the diagonal of S
+template <class T>
+__device__ void finish_diag(const BlockArgs<T>& a, int row, int fpos, double (&s)[36], const double (&bb)[6],
+                            const double (&hh)[6]) {
+  // Z_e^T Z_e is symmetric by construction and so is H_e; the symmetric part is taken anyway so
+  // that CG always sees an exactly symmetric S
 #pragma unroll
-    for (int i = 0; i < 36; ++i) ps[i].add(p[i]);
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      const double m = 0.5 * (s[i * 6 + j] + s[j * 6 + i]);
+      s[i * 6 + j] = m;
+      s[j * 6 + i] = m;
+    }
+  const int et = a.ent_type[row];
+  const int nd = et == ENT_CAM ? 6 : (et == ENT_PLANE ? 3 : 2);
+  const unsigned held = (row < a.nc) ? a.cam_fixed[row] : 0u;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    bool real = i < nd && !((held >> i) & 1u);
+    double Di = real ? fmin(fmax(hh[i], 1e-6), 1e32) : 1.0;
+    a.Dg[6 * (size_t)row + i] = Di;
+    if (real) {
+      s[i * 6 + i] += a.lambda * Di;
+      a.b[6 * (size_t)row + i] = bb[i];
+    } else {
+      // padding (or a held camera): unit diagonal, no coupling, zero right-hand side
+#pragma unroll
+      for (int j = 0; j < 6; ++j) { s[i * 6 + j] = 0; s[j * 6 + i] = 0; }
+      s[i * 6 + i] = 1;
+      a.b[6 * (size_t)row + i] = 0;
+    }
   }
-  if (!diag) {
-    // an off-diagonal block: rounded once to the storage type and written with its mirror
 #pragma unroll
-    for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)ps[i].rounded();
-    const int mpos = a.up_mirror[u];
+  for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 6; ++i) a.sdiag[6 * (size_t)row + i] = (double)(T)s[i * 6 + i];
+}
+
+// a diagonal block, or a block split over several units: FP64 sum of the unit partials in unit order
+template <class T>
+__device__ void unit_finish(const UnitArgs<T>& a, int u) {
+  const int row = a.fb.up_row[u], fpos = a.fb.up_full[u];
+  const bool diag = a.fb.col[fpos] == row;
+  double s[36], bb[6], hh[6];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) a.Sval[s_idx(mpos, j * 6 + i)] = (T)ps[i * 6 + j].rounded();
-    return;
-  }
-  double s[36];
-#pragma unroll
-  for (int i = 0; i < 36; ++i) s[i] = ps[i].value();
-  double bb[6], hh[6];
+  for (int i = 0; i < 36; ++i) s[i] = 0;
 #pragma unroll
   for (int i = 0; i < 6; ++i) { bb[i] = 0; hh[i] = 0; }
-  if (diag) {
-    PartSum<T> pb[6], ph[6];
-    for (int w = a.up_wi[u]; w < a.up_wi[u + 1]; ++w) {
-      const T* p = a.part + (size_t)w * PART;
+  for (int w = a.up_un[u]; w < a.up_un[u + 1]; ++w) {
+    const double* p = a.upart + (size_t)w * 48;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) { pb[i].add(p[36 + i]); ph[i].add(p[42 + i]); }
-    }
+    for (int i = 0; i < 36; ++i) s[i] += p[i];
+    if (diag)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) { bb[i] = pb[i].value(); hh[i] = ph[i].value(); }
+      for (int i = 0; i < 6; ++i) { bb[i] += p[36 + i]; hh[i] += p[42 + i]; }
   }
   if (diag) {
-    // a diagonal block sums -Z_e^T Z_e (symmetric by construction) and the symmetric H_e; the
-    // symmetric part is taken anyway so that CG always sees an exactly symmetric S
+    finish_diag<T>(a.fb, row, fpos, s, bb, hh);
+    return;
+  }
+  const int mpos = a.fb.up_mirror[u];
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = i + 1; j < 6; ++j) {
-        const double m = 0.5 * (s[i * 6 + j] + s[j * 6 + i]);
-        s[i * 6 + j] = m;
-        s[j * 6 + i] = m;
-      }
-    const int et = a.ent_type[row];
-    const int nd = et == ENT_CAM ? 6 : (et == ENT_PLANE ? 3 : 2);
-    const unsigned held = (row < a.nc) ? a.cam_fixed[row] : 0u;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      bool real = i < nd && !((held >> i) & 1u);
-      double Di = real ? fmin(fmax(hh[i], 1e-6), 1e32) : 1.0;
-      a.Dg[6 * (size_t)row + i] = Di;
-      if (real) {
-        s[i * 6 + i] += a.lambda * Di;
-        a.b[6 * (size_t)row + i] = bb[i];
-      } else {
-        // padding (or a held camera): unit diagonal, no coupling, zero right-hand side
-#pragma unroll
-        for (int j = 0; j < 6; ++j) { s[i * 6 + j] = 0; s[j * 6 + i] = 0; }
-        s[i * 6 + i] = 1;
-        a.b[6 * (size_t)row + i] = 0;
-      }
+    for (int j = 0; j < 6; ++j) {
+      const T v = (T)s[i * 6 + j];
+      a.fb.Sval[s_idx(fpos, i * 6 + j)] = v;
+      a.fb.Sval[s_idx(mpos, j * 6 + i)] = v;
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_schur_finish(UnitArgs<T> a) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < a.nmulti) unit_finish<T>(a, a.multi[k]);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// A warp per work unit; lane l takes pairs l, l + 32, ... of the unit.  For each stage of 32 pairs the
+// warp gathers both Z records of every pair into shared memory with 16-byte cp.async copies (each lane
+// keeps up to a dozen copies in flight); every lane then adds the full 6 x 6 term of its pair to its own
+// accumulators in the working type.  At the end the lanes' accumulators are summed across lanes in lane
+// order (double-single for float), and lane l writes entry l (and 32 + l) of the block.
+// Shared memory per warp: 32 staged pairs at a padded stride (conflict-free 16-byte loads) and the pair
+// indices; the stage area is reused for the cross-lane sums.
+template <class T>
+struct UnitSmem {
+  static constexpr int stride = sizeof(T) == 4 ? 52 : 50;   // elements per staged pair: Z_a | Z_b | pad
+  static constexpr int red = 49;                            // row stride of the cross-lane sums (36 + 12 + 1)
+  static constexpr size_t bytes = sizeof(T) * 32 * stride + 2 * 32 * sizeof(int);
+};
+
+template <class T>
+__device__ __forceinline__ void load_rec(const T* src, T (&z)[24], bool line) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(src);
 #pragma unroll
-    for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
+    for (int k = 0; k < 6; ++k) {
+      if (k == 5 && !line) { z[20] = 0; z[21] = 0; z[22] = 0; z[23] = 0; continue; }   // a point has 3 rows
+      const float4 t = q[k];
+      z[4 * k] = t.x; z[4 * k + 1] = t.y; z[4 * k + 2] = t.z; z[4 * k + 3] = t.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(src);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) a.sdiag[6 * (size_t)row + i] = (double)(T)s[i * 6 + i];
+    for (int k = 0; k < 12; ++k) {
+      if (k >= 9 && !line) { z[2 * k] = 0; z[2 * k + 1] = 0; continue; }
+      const double2 t = q[k];
+      z[2 * k] = t.x; z[2 * k + 1] = t.y;
+    }
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_schur_blocks(BlockArgs<T> a) {
-  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (u < a.nbu) schur_block<T>(a, u);
+__device__ void unit_warp(const UnitArgs<T>& a, int w, char* smem, int lane) {
+  constexpr int ST = UnitSmem<T>::stride, RS = UnitSmem<T>::red;
+  constexpr int CH = SW * (int)sizeof(T) / 16;   // 16-byte pieces of one Z record
+  T* stage = reinterpret_cast<T*>(smem);
+  int* sa_ = reinterpret_cast<int*>(smem + sizeof(T) * 32 * ST);
+  int* sb_ = sa_ + 32;
+  const int s0 = a.un_se[2 * w], s1 = a.un_se[2 * w + 1];
+  const int u = a.un_blk[w];
+  const int row = a.fb.up_row[u], fpos = a.fb.up_full[u];
+  const bool diag = a.fb.col[fpos] == row;
+  const bool direct = !diag && a.up_un[u + 1] - a.up_un[u] == 1;   // written to S here
+  T acc[36], bacc[6], hacc[6];
+#pragma unroll
+  for (int e = 0; e < 36; ++e) acc[e] = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) { bacc[i] = 0; hacc[i] = 0; }
+  for (int base = s0; base < s1; base += 32) {
+    const int n = min(32, s1 - base);
+    if (lane < n) { sa_[lane] = a.pair_a[base + lane]; sb_[lane] = a.pair_b[base + lane]; }
+    __syncwarp();
+    for (int t = lane; t < n * 2 * CH; t += 32) {
+      const int p = t / (2 * CH), r = t - p * 2 * CH;
+      const int which = r / CH, ch = r - which * CH;
+      const int e = which == 0 ? sa_[p] : (sb_[p] & 0x7fffffff);
+      cp_async16(reinterpret_cast<char*>(stage + p * ST + which * SW) + 16 * ch,
+                 reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * ch);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    if (lane < n) {
+      const int ea = sa_[lane];
+      const bool cp = ((unsigned)sb_[lane] >> 31) != 0u;
+      const bool line = ea >= a.line_slot0;
+      T za[24], zb[24];
+      load_rec(stage + lane * ST, za, line);
+      load_rec(stage + lane * ST + SW, zb, line);
+      if (diag) {
+        const T* H = a.H + (size_t)ea * SH;
+        const T* Bv = a.B + (size_t)ea * SG;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          bacc[i] += Bv[i];
+          hacc[i] += H[up_idx(i, i, 6)];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] - pair_dot(za, zb, i, j, line);
+        }
+      } else if (cp) {
+        const T* Cm = a.C + (size_t)ea * SC;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 36; ++e) acc[e] -= pair_dot(za, zb, e / 6, e % 6, line);
+      }
+    }
+    __syncwarp();   // the next stage overwrites the staged records
+  }
+  // cross-lane sums in lane order
+  T* red = stage;
+#pragma unroll
+  for (int e = 0; e < 36; ++e) red[lane * RS + e] = acc[e];
+  if (diag)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { red[lane * RS + 36 + i] = bacc[i]; red[lane * RS + 42 + i] = hacc[i]; }
+  __syncwarp();
+  const int ne = diag ? 48 : 36;
+  const int mpos = direct ? a.fb.up_mirror[u] : 0;
+  for (int e = lane; e < ne; e += 32) {
+    PartSum<T> sm;
+    for (int k = 0; k < 32; ++k) sm.add(red[k * RS + e]);
+    if (!direct) {
+      a.upart[(size_t)w * 48 + e] = sm.value();
+    } else {
+      const T v = (T)sm.rounded();
+      a.fb.Sval[s_idx(fpos, e)] = v;
+      a.fb.Sval[s_idx(mpos, (e % 6) * 6 + e / 6)] = v;
+    }
+  }
+  __syncwarp();   // the next unit of this warp reuses the shared memory
+}
+
+template <class T>
+struct UnitWarps { static constexpr int n = sizeof(T) == 4 ? 4 : 2; };
+
+// grid path: a warp per unit, in the unit order (long units first)
+template <class T>
+__global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_units(UnitArgs<T> a) {
+  constexpr int NW = UnitWarps<T>::n;
+  __shared__ __align__(16) char smem[NW][UnitSmem<T>::bytes];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = blockIdx.x * (int64_t)NW + warp;
+  if (g >= a.nun) return;   // the whole warp leaves together
+  unit_warp<T>(a, a.un_order[g], smem[warp], lane);
 }
 
 // ============================================================================
@@ -1654,19 +1714,31 @@ void launch_invert(Problem& P, double lambda) {
 }
 
 template <class T>
+UnitArgs<T> unit_args(Problem& P, double lambda) {
+  const Dims& d = P.d;
+  BlockArgs<T> b;
+  b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.col = P.col;
+  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.Sval = (T*)P.Sval;
+  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nc = d.nc; b.lambda = lambda;
+  UnitArgs<T> un;
+  un.un_se = P.un_se; un.un_blk = P.un_blk; un.un_order = P.un_order; un.up_un = P.up_un; un.multi = P.multi_blk;
+  un.pair_a = P.pair_a; un.pair_b = P.pair_b; un.Z = (const T*)P.slotZ; un.H = (const T*)P.slotH;
+  un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.upart = P.upart; un.nun = d.nun; un.nmulti = d.nmulti;
+  un.line_slot0 = P.line_slot0; un.fb = b;
+  return un;
+}
+
+template <class T>
 void launch_schur(Problem& P, double lambda) {
   const Dims& d = P.d;
-  SchurArgs<T> a;
-  a.pair_a = P.pair_a; a.pair_b = P.pair_b; a.wi_se = P.wi_start;
-  a.Z = (const T*)P.slotZ; a.H = (const T*)P.slotH; a.B = (const T*)P.slotB;
-  a.C = (const T*)P.slotC; a.part = (T*)P.part; a.nwi = d.nwi; a.line_slot0 = P.line_slot0;
-  if (d.nwi) { ++P.launches; k_schur_items<T><<<nblk(d.nwi, 128), 128, 0, P.stream>>>(a); }
+  const UnitArgs<T> un = unit_args<T>(P, lambda);
+  if (d.nun) {
+    ++P.launches;
+    constexpr int NW = UnitWarps<T>::n;
+    k_schur_units<T><<<nblk(d.nun, NW), NW * 32, 0, P.stream>>>(un);
+  }
   if (P.ev[3]) cudaEventRecord(P.ev[3], P.stream);
-  BlockArgs<T> b;
-  b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.up_wi = P.up_wi; b.col = P.col;
-  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.part = (const T*)P.part; b.Sval = (T*)P.Sval;
-  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nbu = d.nbu; b.nc = d.nc; b.lambda = lambda;
-  if (d.nbu) { ++P.launches; k_schur_blocks<T><<<nblk(d.nbu, 128), 128, 0, P.stream>>>(b); }
+  if (d.nmulti) { ++P.launches; k_schur_finish<T><<<nblk(d.nmulti, 128), 128, 0, P.stream>>>(un); }
 }
 
 template <class T>
@@ -1783,11 +1855,10 @@ void launch_decide(Problem& P) {
 // phases, a single-CTA PCG, and the accept / reject decision on thread 0.
 template <class T>
 struct WinDesc {
-  int64_t nc, npl, nv, np, nl, nf, na, nr, nwi, nbu, nch;
+  int64_t nc, npl, nv, np, nl, nf, na, nr, nbu, nch;
   LinArgs<T> lin;
   InvArgs<T> inv;
-  SchurArgs<T> schur;
-  BlockArgs<T> blocks;
+  UnitArgs<T> units;
   BackArgs<T> back;
   CandArgs cand;
   CostArgs cost;
@@ -1945,12 +2016,14 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
     }
   }
   __syncthreads();
-  for (int64_t w = threadIdx.x; w < W.nwi; w += NT) schur_item<T>(W.schur, w);
-  __syncthreads();
   {
-    BlockArgs<T> ba = W.blocks;
-    ba.lambda = lam;
-    for (int64_t u = threadIdx.x; u < W.nbu; u += NT) schur_block<T>(ba, u);
+    UnitArgs<T> ua = W.units;
+    ua.fb.lambda = lam;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    char* mine = reinterpret_cast<char*>(chunk_y) + (size_t)warp * UnitSmem<T>::bytes;
+    for (int64_t w = warp; w < ua.nun; w += NT / 32) unit_warp<T>(ua, (int)w, mine, lane);
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < ua.nmulti; k += NT) unit_finish<T>(ua, ua.multi[k]);
   }
   __syncthreads();
   for (int64_t r = threadIdx.x; r < W.na; r += NT) precond_row<T, true>(W.row_ptr, W.col, W.Sval, W.Minv, W.S, r);
@@ -1994,8 +2067,10 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
     DevScalars* S = W.S;
     S->Enew = red2[0];
     S->Epxnew = red2[1];
+    const double lam_used = S->lambda;
     decide(W.dec);
     W.state[2] += 1;
+    if (!S->accepted && lam_used >= W.dec.lmax && !W.state[4]) W.state[4] = W.state[2];   // no step helps any more
     if (S->accepted) {
       const double rel = fabs(S->Epx - S->Epxnew) / fmax(S->Epx, 1e-300);
       if (rel < W.rel_cost_tol && !W.state[4]) W.state[4] = W.state[2];
@@ -2014,7 +2089,7 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
 template <class T, int NT>
 __global__ void __launch_bounds__(NT, 1) k_windows(const WinDesc<T>* __restrict__ descs, const int* __restrict__ order,
                                                    int nwin, int iters, int* queue) {
-  extern __shared__ double chunk_y[];
+  extern __shared__ __align__(16) double chunk_y[];
   __shared__ int s_w;
   for (;;) {
     if (threadIdx.x == 0) s_w = atomicAdd(queue, 1);
@@ -2032,7 +2107,7 @@ void fill_window_desc(Problem& P, void* out) {
   WinDesc<T>& W = *(WinDesc<T>*)out;
   const Dims& d = P.d;
   W.nc = d.nc; W.npl = d.npl; W.nv = d.nv; W.np = d.np; W.nl = d.nl; W.nf = d.nf; W.na = d.na; W.nr = d.nr;
-  W.nwi = d.nwi; W.nbu = d.nbu;
+  W.nbu = d.nbu;
   std::vector<int32_t> rc(1);
   W.nch = 0;
   cudaMemcpy(&rc[0], P.row_chunk0 + d.na, sizeof(int32_t), cudaMemcpyDeviceToHost);
@@ -2051,14 +2126,7 @@ void fill_window_desc(Problem& P, void* out) {
   ia.slot_feat = P.slot_feat; ia.Vinv = P.featVinv; ia.u = P.featu; ia.L = P.featL; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB;
   ia.np = d.np; ia.nf = d.nf; ia.ne = d.ne;
   ia.lambda = 0; ia.S = P.S;
-  SchurArgs<T>& sa = W.schur;
-  sa.pair_a = P.pair_a; sa.pair_b = P.pair_b; sa.wi_se = P.wi_start; sa.Z = (const T*)P.slotZ;
-  sa.H = (const T*)P.slotH; sa.B = (const T*)P.slotB; sa.C = (const T*)P.slotC; sa.part = (T*)P.part; sa.nwi = d.nwi;
-  sa.line_slot0 = P.line_slot0;
-  BlockArgs<T>& b = W.blocks;
-  b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.up_wi = P.up_wi; b.col = P.col;
-  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.part = (const T*)P.part; b.Sval = (T*)P.Sval;
-  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nbu = d.nbu; b.nc = d.nc; b.lambda = 0;
+  W.units = unit_args<T>(P, 0.0);
   BackArgs<T>& k = W.back;
   k.fslot_off = P.fslot_off; k.slot_ent = P.slot_ent; k.feat_plane_slot = P.feat_plane_slot; k.slot_type = P.slot_type;
   k.V = P.featV; k.Vinv = P.featVinv; k.g = P.featg; k.x = P.x; k.W = (const T*)P.slotW; k.H = (const T*)P.slotH;
@@ -2083,9 +2151,18 @@ void fill_window_desc(Problem& P, void* out) {
 template <class T>
 size_t window_desc_size() { return sizeof(WinDesc<T>); }
 
+// dynamic shared memory of a window CTA: the PCG chunk sums (smem_pcg bytes, from the host) or the Schur
+// stage areas of its warps, whichever is larger (the two phases never overlap)
+template <class T, int NT>
+size_t window_smem(size_t smem_pcg) {
+  const size_t su = (size_t)(NT / 32) * UnitSmem<T>::bytes;
+  return smem_pcg > su ? smem_pcg : su;
+}
+
 template <class T, int NT>
 cudaError_t launch_windows_nt(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
-                              int grid, size_t smem) {
+                              int grid, size_t smem_pcg) {
+  const size_t smem = window_smem<T, NT>(smem_pcg);
   cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaMemsetAsync(queue, 0, sizeof(int), st);
   k_windows<T, NT><<<grid, NT, smem, st>>>((const WinDesc<T>*)descs, order, nwin, iters, queue);
@@ -2099,12 +2176,18 @@ cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order,
   return launch_windows_nt<T, 256>(st, descs, order, nwin, iters, queue, grid, smem);
 }
 
-template <class T>
-int windows_per_sm(int threads, size_t smem) {
+template <class T, int NT>
+int windows_per_sm_nt(size_t smem_pcg) {
+  const size_t smem = window_smem<T, NT>(smem_pcg);
+  cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
-  if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_windows<T, 128>, 128, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_windows<T, 256>, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_windows<T, NT>, NT, smem);
   return nb;
+}
+
+template <class T>
+int windows_per_sm(int threads, size_t smem_pcg) {
+  return threads == 128 ? windows_per_sm_nt<T, 128>(smem_pcg) : windows_per_sm_nt<T, 256>(smem_pcg);
 }
 
 template void fill_window_desc<float>(Problem&, void*);

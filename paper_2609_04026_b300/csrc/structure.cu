@@ -13,8 +13,8 @@
 //     for the SpMV), padded and interleaved for coalesced loads,
 //   * for every upper block of S the slot pairs (e_a, e_b) whose product
 //     W_a V^-1 W_b^T lands in it are listed in feature order (a stable radix
-//     sort of the pairs by block) and cut into work items of at most PAIR_CHUNK
-//     pairs, so that the Schur kernel accumulates each block in a fixed order
+//     sort of the pairs by block) and cut into work units of at most UNIT_MAX
+//     pairs, so that the Schur kernels accumulate each block in a fixed order
 //     without atomics.
 // Every step is deterministic: the same input gives the same structure, and the
 // orders are those of a sequential build (features ascending, cameras ascending
@@ -30,7 +30,8 @@
 
 namespace ba {
 
-static constexpr int PAIR_CHUNK = 64;
+static constexpr int UNIT_MAX = 1024;     // pairs per Schur work unit
+static constexpr int UNIT_LONG = 128;     // units with more pairs are scheduled first
 
 static ba_status fail(Problem& P, ba_status s, const std::string& m) {
   P.err = m;
@@ -489,26 +490,47 @@ __global__ void k_pair_place(const uint32_t* __restrict__ val, int64_t n, const 
   if (k < n) { const uint32_t q = val[k]; pa[k] = gi[q]; pb[k] = gj[q]; }
 }
 
-__global__ void k_item_count(const unsigned long long* __restrict__ ucnt, int64_t nbu, int64_t* __restrict__ nw) {
+__global__ void k_unit_count(const unsigned long long* __restrict__ ucnt, int64_t nbu, int64_t* __restrict__ nu) {
   const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (u < nbu) {
     const int64_t n = (int64_t)ucnt[u];
-    nw[u] = n > 0 ? (n + PAIR_CHUNK - 1) / PAIR_CHUNK : 1;   // every block gets one (possibly empty) item
+    nu[u] = n > 0 ? (n + UNIT_MAX - 1) / UNIT_MAX : 1;
   }
 }
 
-__global__ void k_item_fill(const unsigned long long* __restrict__ ucnt, const int64_t* __restrict__ pstart,
-                            const int64_t* __restrict__ wstart, int64_t nbu, int32_t* __restrict__ up_wi,
-                            int32_t* __restrict__ wi_se) {
+// multi[u] = 1 for the blocks that k_schur_finish completes: blocks split over several units, and every
+// diagonal block (its damping and padding are applied there)
+__global__ void k_unit_fill(const unsigned long long* __restrict__ ucnt, const int64_t* __restrict__ pstart,
+                            const int64_t* __restrict__ ustart, int64_t nbu, const int32_t* __restrict__ up_row,
+                            const int32_t* __restrict__ up_full, const int32_t* __restrict__ pcol,
+                            int32_t* __restrict__ up_un, int32_t* __restrict__ un_se, int32_t* __restrict__ un_blk,
+                            int64_t* __restrict__ multi) {
   const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (u > nbu) return;
-  up_wi[u] = (int32_t)wstart[u];
+  up_un[u] = (int32_t)ustart[u];
   if (u == nbu) return;
   const int64_t p0 = pstart[u], p1 = p0 + (int64_t)ucnt[u];
-  for (int64_t w = wstart[u]; w < wstart[u + 1]; ++w) {
-    const int64_t s = p0 + (w - wstart[u]) * PAIR_CHUNK;
-    wi_se[2 * w] = (int32_t)s;
-    wi_se[2 * w + 1] = (int32_t)(s + PAIR_CHUNK < p1 ? s + PAIR_CHUNK : p1);
+  for (int64_t w = ustart[u]; w < ustart[u + 1]; ++w) {
+    const int64_t s = p0 + (w - ustart[u]) * UNIT_MAX;
+    un_se[2 * w] = (int32_t)s;
+    un_se[2 * w + 1] = (int32_t)(s + UNIT_MAX < p1 ? s + UNIT_MAX : p1);
+    un_blk[w] = (int32_t)u;
+  }
+  multi[u] = (ustart[u + 1] - ustart[u] > 1 || pcol[up_full[u]] == up_row[u]) ? 1 : 0;
+}
+
+__global__ void k_multi_fill(const int64_t* __restrict__ flag, const int64_t* __restrict__ off, int64_t nbu,
+                             int32_t* __restrict__ list) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u < nbu && flag[u]) list[off[u]] = (int32_t)u;
+}
+
+__global__ void k_unit_key(const int32_t* __restrict__ un_se, int64_t nun, uint32_t* __restrict__ key,
+                           uint32_t* __restrict__ val) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w < nun) {
+    key[w] = un_se[2 * w + 1] - un_se[2 * w] > UNIT_LONG ? 0u : 1u;
+    val[w] = (uint32_t)w;
   }
 }
 
@@ -516,10 +538,10 @@ struct Permute {
   const uint32_t* order;
   const int8_t* kind;
   const int32_t *cam, *feat, *grp;
-  const double4* meas;
+  const double4_32a* meas;
   int8_t* rkind;
   int32_t *rcam, *rfeat, *rgrp;
-  double4* rmeas;
+  double4_32a* rmeas;
   int64_t n;
 };
 
@@ -769,26 +791,47 @@ ba_status build_structure(Problem& P) {
   P.pair_a = P.dnew<int32_t>(npair); P.pair_b = P.dnew<int32_t>(npair);
   if (!P.pair_a || !P.pair_b) return oom();
   if (npair) k_pair_place<<<grid_of(npair, NT), NT, 0, P.stream>>>(pval, npair, gi, gj, P.pair_a, P.pair_b);
-  int64_t *pstart = S.get<int64_t>(nbu + 1), *nw = S.get<int64_t>(nbu + 1), *wstart = S.get<int64_t>(nbu + 1);
-  if (!pstart || !nw || !wstart) return oom();
+  int64_t* pstart = S.get<int64_t>(nbu + 1);
+  if (!pstart) return oom();
   if ((s = scan_excl(P, S, (const int64_t*)ucnt, pstart, nbu))) return s;
-  if (nbu) k_item_count<<<grid_of(nbu, NT), NT, 0, P.stream>>>(ucnt, nbu, nw);
-  if ((s = scan_excl(P, S, nw, wstart, nbu))) return s;
-  int64_t nwi;
-  if ((s = read_i64(P, wstart + nbu, &nwi))) return s;
-  if (nwi > (int64_t)INT32_MAX / 2 - 1) return fail(P, BA_ERR_ARG, "too many Schur work items");
-  d.nwi = nwi;
-  P.up_wi = P.dnew<int32_t>(nbu + 1); P.wi_start = P.dnew<int32_t>(2 * nwi);
-  if (!P.up_wi || !P.wi_start) return oom();
-  k_item_fill<<<grid_of(nbu + 1, NT), NT, 0, P.stream>>>(ucnt, pstart, wstart, nbu, P.up_wi, P.wi_start);
+
+  // ---- Schur work units: <= UNIT_MAX pairs of one block, long units first
+  {
+    int64_t *nuc = S.get<int64_t>(nbu + 1), *ustart = S.get<int64_t>(nbu + 1);
+    int64_t *mflag = S.get<int64_t>(nbu + 1), *moff = S.get<int64_t>(nbu + 1);
+    if (!nuc || !ustart || !mflag || !moff) return oom();
+    if (nbu) k_unit_count<<<grid_of(nbu, NT), NT, 0, P.stream>>>(ucnt, nbu, nuc);
+    if ((s = scan_excl(P, S, nuc, ustart, nbu))) return s;
+    int64_t nun;
+    if ((s = read_i64(P, ustart + nbu, &nun))) return s;
+    d.nun = nun;
+    P.up_un = P.dnew<int32_t>(nbu + 1); P.un_se = P.dnew<int32_t>(2 * nun); P.un_blk = P.dnew<int32_t>(nun);
+    P.un_order = P.dnew<int32_t>(nun); P.upart = P.dnew<double>(48 * nun);
+    if (!P.up_un || !P.un_se || !P.un_blk || !P.un_order || !P.upart) return oom();
+    k_unit_fill<<<grid_of(nbu + 1, NT), NT, 0, P.stream>>>(ucnt, pstart, ustart, nbu, P.up_row, P.up_full, P.col,
+                                                            P.up_un, P.un_se, P.un_blk, mflag);
+    if ((s = scan_excl(P, S, mflag, moff, nbu))) return s;
+    int64_t nmulti;
+    if ((s = read_i64(P, moff + nbu, &nmulti))) return s;
+    d.nmulti = nmulti;
+    P.multi_blk = P.dnew<int32_t>(nmulti);
+    if (!P.multi_blk) return oom();
+    if (nbu) k_multi_fill<<<grid_of(nbu, NT), NT, 0, P.stream>>>(mflag, moff, nbu, P.multi_blk);
+    uint32_t *uk = S.get<uint32_t>(nun), *uk2 = S.get<uint32_t>(nun), *uv2 = S.get<uint32_t>(nun);
+    if (!uk || !uk2 || !uv2) return oom();
+    if (nun) {
+      k_unit_key<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_se, nun, uk, (uint32_t*)P.un_order);
+      if ((s = radix_sort(P, S, uk, (uint32_t*)P.un_order, uk2, uv2, nun, 8))) return s;
+    }
+  }
 
   // ---- residual records in feature-major order
   P.rkind = P.dnew<int8_t>(nr); P.rcam = P.dnew<int32_t>(nr); P.rfeat = P.dnew<int32_t>(nr); P.rgrp = P.dnew<int32_t>(nr);
   P.meas64 = P.dnew<double>(4 * nr);
   if (!P.rkind || !P.rcam || !P.rfeat || !P.rgrp || !P.meas64) return oom();
   if (nr) {
-    Permute pm{order, kind_d, cam_d, feat_d, grp_d, (const double4*)meas_d, P.rkind, P.rcam, P.rfeat, P.rgrp,
-               (double4*)P.meas64, nr};
+    Permute pm{order, kind_d, cam_d, feat_d, grp_d, (const double4_32a*)meas_d, P.rkind, P.rcam, P.rfeat, P.rgrp,
+               (double4_32a*)P.meas64, nr};
     k_permute<<<grid_of(nr, NT), NT, 0, P.stream>>>(pm);
   }
   // the cost pass visits the residuals kind by kind (feature-major inside a kind), so that the lanes of a

@@ -143,31 +143,61 @@ def test_lm_trajectory_fp64_tiny(B):
     assert rel(cams[:, 4:7], st2["cams"][:, 4:7]) <= 1e-8
 
 
+def _solve_state(B, s, prec):
+    """Solve to a relative cost change of 1e-9 (or until no step helps); the result as (report, scene)."""
+    p = gpu_problem(B, s, precision=prec, max_lm_iters=600, rel_cost_tol=1e-9)
+    try:
+        rep = B.ba_solve(p)
+        out = dict(s)
+        cams = B.ba_get_cameras(p, len(s["cams"]["q"]))
+        out["cams"] = dict(s["cams"], q=cams[:, :4], t=cams[:, 4:7])
+        out["points"] = B.ba_get_features(p, B.BA_POINT, len(s["points"]))
+        out["lines"] = B.ba_get_features(p, B.BA_LINE, len(s["lines"]))
+        out["planes"] = B.ba_get_groups(p, B.BA_PLANE, len(s["planes"]))
+        out["vps"] = B.ba_get_groups(p, B.BA_VP, len(s["vps"]))
+    finally:
+        B.ba_destroy(p)
+    return rep, out
+
+
+def _point_rms(s):
+    r, v = O.residuals(O.state_from_scene(s), s["obs"], "point")
+    n = np.sqrt((r.numpy() ** 2).sum(1))
+    return n
+
+
 def test_mixed_matches_fp64(B):
     """Mixed path (FP32 Jacobians / Schur / S storage, FP64 inverses, cost and accept test): at convergence
     the final cost is within 1e-5 relative, and the reprojection RMS over inlier point observations within
-    1e-4 px, of the FP64 path's.  Both run to a relative cost change of 1e-9 so that they reach the same
-    minimum rather than two points of plain IRLS's slow tail."""
-    s = scene("small")
-    res = {}
-    for prec in (0, 1):
-        p = gpu_problem(B, s, precision=prec, max_lm_iters=600, rel_cost_tol=1e-9)
-        try:
-            rep = B.ba_solve(p)
-            st = O.state_from_scene(s)
-            st["points"] = B.ba_get_features(p, B.BA_POINT, len(s["points"]))
-            st["cams"][:, :7] = B.ba_get_cameras(p, len(s["cams"]["q"]))
-        finally:
-            B.ba_destroy(p)
-        r, v = O.residuals(st, s["obs"], "point")
-        res[prec] = (rep.cost, np.sqrt((r.numpy() ** 2).sum(1)), rep.iters, rep.converged)
-    (E64, n64, it64, c64), (E32, n32, it32, c32) = res[0], res[1]
-    assert c64 and c32, (it64, it32)
+    1e-4 px, of the FP64 path's.  The scene has no outliers, so both paths descend into the same minimum;
+    both run to a relative cost change of 1e-9 so that they reach it rather than two points of plain
+    IRLS's slow tail."""
+    s = make_scene(config("small", outlier_frac=0.0))
+    (r64, s64), (r32, s32) = _solve_state(B, s, 0), _solve_state(B, s, 1)
+    assert r64.converged and r32.converged, (r64.iters, r32.iters)
+    n64, n32 = _point_rms(s64), _point_rms(s32)
     inl = n64 < 5.0
     rms64 = float(np.sqrt((n64[inl] ** 2).mean()))
     rms32 = float(np.sqrt((n32[inl] ** 2).mean()))
-    assert abs(E32 - E64) <= 1e-5 * E64, (E32, E64)
+    assert abs(r32.cost - r64.cost) <= 1e-5 * r64.cost, (r32.cost, r64.cost)
     assert abs(rms32 - rms64) <= 1e-4, (rms32, rms64)
+
+
+def test_mixed_solution_is_fp64_minimum(B):
+    """With 3% outliers under the Cauchy loss the cost has nearby local minima, and which one a path
+    reaches depends on rounding.  The mixed path's end point must still be a minimum by the FP64 path's
+    standard: FP64 iterations started there lower the cost by at most 1e-5 relative and move the inlier
+    reprojection RMS by at most 1e-4 px."""
+    s = scene("small")
+    r32, s32 = _solve_state(B, s, 1)
+    assert r32.converged, r32.iters
+    r64, s64 = _solve_state(B, s32, 0)
+    assert r64.converged, r64.iters
+    assert r64.cost <= r32.cost * (1 + 1e-12)
+    assert r32.cost - r64.cost <= 1e-5 * r64.cost, (r32.cost, r64.cost)
+    n64, n32 = _point_rms(s64), _point_rms(s32)
+    inl = n64 < 5.0
+    assert abs(float(np.sqrt((n32[inl] ** 2).mean())) - float(np.sqrt((n64[inl] ** 2).mean()))) <= 1e-4
 
 
 # ------------------------------------------------------------------ degenerate cases
