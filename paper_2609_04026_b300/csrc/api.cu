@@ -218,13 +218,12 @@ static ba_status plan_pcg(ba_problem* p) {
         cta_row0.push_back((int32_t)(r + 1));
     }
     while ((int64_t)cta_row0.size() < G + 1) cta_row0.push_back((int32_t)d.na);
-    int32_t maxch = 1;
-    for (int64_t c = 0; c < G; ++c) maxch = std::max(maxch, row_chunk0[cta_row0[c + 1]] - row_chunk0[cta_row0[c]]);
-    smem = sizeof(double) * 6 * (size_t)maxch;
-    if (smem > 160 * 1024) return set_err(p, BA_ERR_ARG, "reduced system too irregular for the PCG partition");
-    if (smem > 48 * 1024) {
-      if (mx) pcg_allow_smem<float>(smem); else pcg_allow_smem<double>(smem);
-    }
+    // shared memory of the row sums: one segment of 6 double-width sums per (warp, row it touches)
+    int32_t maxrows = 1;
+    for (int64_t c = 0; c < G; ++c) maxrows = std::max(maxrows, cta_row0[c + 1] - cta_row0[c]);
+    smem = sizeof(double) * 6 * ((size_t)maxrows + 16);
+    if (smem > 72 * 1024) return set_err(p, BA_ERR_ARG, "reduced system too large or irregular for the PCG partition");
+    if (mx) pcg_allow_smem<float>(smem); else pcg_allow_smem<double>(smem);
     if (occ(smem) >= per_sm) {
       p->pcg_grid = (int)G;
       break;
@@ -272,7 +271,7 @@ static ba_status freeze(ba_problem* p) {
   p->featg = p->dnew<double>(4 * d.nf); p->featu = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
   p->featL = p->dnew<double>(10 * d.nf);
   ok &= p->featV && p->featVinv && p->featg && p->featu && p->dfeat && p->featL;
-  double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap, &p->sdiag};
+  double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap, &p->sdiag, &p->svec};
   for (double** v : vecs) { *v = p->dnew<double>(6 * d.na); ok &= *v != nullptr; }
   int64_t maxb = std::max<int64_t>({(d.nr + 255) / 256, (d.nf + 127) / 128, (d.na * 32 + 255) / 256, (d.na + 127) / 128,
                                     4 * 148 * 4, 1});
@@ -324,6 +323,12 @@ static ba_status sync_scalars(ba_problem* p) {
   CUDA_OR(p, cudaGetLastError());
   CUDA_OR(p, cudaMemcpyAsync(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
   CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  if (p->hS->flags & PCG_FLAG_TIMEOUT) {
+    // a bulk copy of S into shared memory did not complete within the PCG kernel's bounded wait
+    const int cleared = p->hS->flags & ~PCG_FLAG_TIMEOUT;
+    CUDA_OR(p, cudaMemcpy(&p->S->flags, &cleared, sizeof(int), cudaMemcpyHostToDevice));
+    return set_err(p, BA_ERR_TIMEOUT, "PCG: a shared-memory copy of S timed out");
+  }
   return BA_OK;
 }
 

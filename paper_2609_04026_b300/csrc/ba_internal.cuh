@@ -50,13 +50,16 @@ constexpr int SC = 18;  // camera slot: J_cam^T w J_plane (6 x 3)
 
 enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
 
+constexpr int PCG_FLAG_TIMEOUT = 8;   // DevScalars::flags bit: a TMA copy of S did not complete in time
+
 // scalars kept on the device so that PCG and the LM decision need no host round trip
 struct DevScalars {
   double rz, rz_new, pAp, rr, bnorm2, alpha, beta, tol2;
   double E, Epx, Enew, Epxnew, pred, gTd, dHd;
   double lambda, nu, gain;
   int iters, max_iters, done, accepted;
-  int flags;                 // bit 0: a landmark block needed extra damping; bit 1: non-finite value
+  int flags;                 // bit 0: a landmark block needed extra damping; bit 1: non-finite value;
+                             // bit 2: a block-Jacobi block fell back to its diagonal; bit 3: PCG copy timeout
   unsigned int counter[8];   // arrival counters of the last-block reductions
 };
 
@@ -81,8 +84,9 @@ template <class T> int pcg_blocks_per_sm(size_t smem);
 template <class T> void pcg_allow_smem(size_t smem);
 constexpr int PCG_CHUNK = 64;   // stored blocks per SpMV chunk (caller-layout path)
 
-// position of entry e of the block at padded position q in the interleaved storage of S
-__host__ __device__ __forceinline__ size_t s_idx(int64_t q, int e) { return (size_t)(q >> 5) * 1152 + (size_t)e * 32 + (q & 31); }
+// position of entry e (row-major 6 x 6) of the block at padded position q in the storage of S: blocks are
+// stored whole and in order, so a 32-block chunk is one contiguous run of 1152 values
+__host__ __device__ __forceinline__ size_t s_idx(int64_t q, int e) { return (size_t)q * 36 + (size_t)e; }
 template <class T> void launch_backsub(Problem& P);
 void launch_candidate(Problem& P);
 void launch_cost(Problem& P, bool candidate);
@@ -160,6 +164,7 @@ struct ba_problem {
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featu = nullptr, *featL = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
+  double* svec = nullptr;       // PCG: s = S p (Chronopoulos-Gear form)
   float2* phl = nullptr;        // mixed path: p split into (hi, lo) floats for the SpMV
   int32_t* row_len = nullptr;   // stored (non-padding) blocks per row of S
   double* sdiag = nullptr;      // diagonal of S (after damping), 6 per entity

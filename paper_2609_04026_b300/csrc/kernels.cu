@@ -1115,6 +1115,24 @@ __device__ __forceinline__ float2 split2(double v) {
   return make_float2(h, (float)(v - (double)h));
 }
 
+// the 36 values of one stored block (16-byte aligned: a block is 144 or 288 bytes)
+__device__ __forceinline__ void load_block36(const float* p, float (&B)[36]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float4 t = q[k];
+    B[4 * k] = t.x; B[4 * k + 1] = t.y; B[4 * k + 2] = t.z; B[4 * k + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void load_block36(const double* p, double (&B)[36]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    const double2 t = q[k];
+    B[2 * k] = t.x; B[2 * k + 1] = t.y;
+  }
+}
+
 template <class T>
 struct PcgArgs;
 
@@ -1233,10 +1251,8 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
       DotAcc<T> acc[6];
       if (SOA) {
         const int blk = a.chunk_beg[q] + lane;
-        const T* Bg = a.Sval + s_idx(blk, 0);
         T B[36];
-#pragma unroll
-        for (int k = 0; k < 36; ++k) B[k] = Bg[k * 32];
+        load_block36(a.Sval + s_idx(blk, 0), B);
         spmv_block(B, a, a.col[blk], acc);
       } else {
         const int e = a.chunk_beg[q + 1];
@@ -1315,6 +1331,329 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
     a.S->rr = rr;
     a.S->bnorm2 = bb;
     a.S->rz = rz;
+    a.S->done = 1;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Grid path of K5/K6: S streamed by the Tensor Memory Accelerator, CG in the Chronopoulos-Gear form.
+//
+// A CTA owns a contiguous range of block rows, hence a contiguous run of 32-block chunks of the padded
+// storage (one chunk = 32 whole blocks, 4.6 KB in float).  The run is split into NW contiguous pieces,
+// one per warp; a warp keeps NBUF chunks of its piece in flight in shared memory, each fetched by two
+// bulk copies (cp.async.bulk: the values and the 32 column indices, completion counted on an mbarrier
+// per buffer), so the stream of S never waits on the products.  Every wait on an mbarrier is bounded: if a copy has not landed after a very long
+// spin the kernel records PCG_FLAG_TIMEOUT, finishes the iteration and stops; the host then returns
+// BA_ERR_TIMEOUT.
+//
+// CG in the Chronopoulos-Gear form (one fused reduction per iteration) needs two grid barriers per
+// iteration instead of three: u = M^-1 r must be complete before w = S u, and the partial dots
+// (r, u), (r, r) and (w, u) must be complete before alpha and beta.  With s = S p carried as a vector:
+//   x += alpha p;  r -= alpha s;  u = M^-1 r;  w = S u;  gamma' = (r, u);  delta = (w, u)
+//   beta = gamma' / gamma;  alpha = gamma' / (delta - beta gamma' / alpha);  p = u + beta p;  s = w + beta s
+// which produces the iterates of the standard preconditioned CG (the oracle's) in exact arithmetic.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// true once the barrier's phase with the given parity has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit) {
+  const unsigned a = smem_u32(bar);
+  for (int i = 0; i < limit; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <class T>
+struct PcgStreamArgs {
+  int64_t na;
+  const int32_t *col, *cta_row0, *row_chunk0, *chunk_beg;
+  const T *Sval, *Minv;
+  const double* b;
+  double *x, *r, *u, *p, *w, *s;
+  float2* uhl;   // float working type: u split into (hi, lo) floats for the products
+  double* part;  // per-CTA partial sums, two parity slots of 3 x G
+  DevScalars* S;
+  double tol;
+  int max_iters;
+};
+
+template <class T>
+struct StreamCfg;
+template <>
+struct StreamCfg<float> { static constexpr int NT = 256, NBUF = 3; };
+template <>
+struct StreamCfg<double> { static constexpr int NT = 256, NBUF = 2; };
+template <class T>
+constexpr size_t stream_chunk_bytes() { return (size_t)BS2 * 32 * sizeof(T); }
+template <class T>
+constexpr size_t stream_stage_bytes() { return (size_t)(StreamCfg<T>::NT / 32) * StreamCfg<T>::NBUF * stream_chunk_bytes<T>(); }
+
+// the u block a lane multiplies: the pre-split (hi, lo) floats (float S), or the FP64 values
+template <class T>
+struct UVal;
+template <>
+struct UVal<float> {
+  float xh[6], xl[6];
+  __device__ __forceinline__ void gather(const PcgStreamArgs<float>& a, int col) {
+    const float2* pb = a.uhl + 6 * (size_t)col;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float2 v = __ldcg(&pb[j]);
+      xh[j] = v.x;
+      xl[j] = v.y;
+    }
+  }
+  __device__ __forceinline__ void product(const float (&B)[36], DotAcc<float> (&acc)[6]) const {
+    block_dot6_split(B, xh, xl, acc);
+  }
+};
+template <>
+struct UVal<double> {
+  double xv[6];
+  __device__ __forceinline__ void gather(const PcgStreamArgs<double>& a, int col) {
+    const double* pb = a.u + 6 * (size_t)col;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) xv[j] = __ldcg(&pb[j]);
+  }
+  __device__ __forceinline__ void product(const double (&B)[36], DotAcc<double> (&acc)[6]) const {
+    block_dot6(B, xv, acc);
+  }
+};
+
+template <class T, int NT, int NBUF>
+__global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  constexpr int NW = NT / 32;
+  constexpr unsigned CHB = (unsigned)stream_chunk_bytes<T>();
+  constexpr int SPIN = 1 << 22;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  T* stage = reinterpret_cast<T*>(dyn);                                          // [NW][NBUF][32 blocks x 36]
+  DotAcc<T>* seg = reinterpret_cast<DotAcc<T>*>(dyn + stream_stage_bytes<T>());  // [row segments][6]
+  __shared__ __align__(8) uint64_t bars[NW][NBUF];
+  __shared__ __align__(128) int cols[NW][NBUF][32];
+  __shared__ int wfirst[NW], wlast[NW], wbase[NW + 1];
+  __shared__ double bc[4];
+  __shared__ double cta_out[2];
+  const int G = gridDim.x, c = blockIdx.x;
+  const int r0 = a.cta_row0[c], r1 = a.cta_row0[c + 1];
+  const int q0 = a.row_chunk0[r0], q1 = a.row_chunk0[r1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // warp w multiplies the contiguous chunks [c0, c1) of the CTA's run; a lane accumulates its block
+  // position over all chunks of one block row and the warp sums the lanes once per row it touches,
+  // leaving one "row segment" (6 sums) per (warp, row)
+  const int ntot = q1 - q0;
+  const int c0 = q0 + (int)((int64_t)ntot * warp / NW), c1 = q0 + (int)((int64_t)ntot * (warp + 1) / NW);
+  const int nk = c1 - c0;
+  auto row_of = [&](int q) {   // the block row holding chunk q (r0 <= row < r1)
+    int lo = r0, hi = r1 - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.row_chunk0[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  if (lane == 0) {
+    for (int bi = 0; bi < NBUF; ++bi) mbar_init(&bars[warp][bi], 1);
+    wfirst[warp] = nk > 0 ? row_of(c0) : 0;
+    wlast[warp] = nk > 0 ? row_of(c1 - 1) : -1;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int w = 0; w < NW; ++w) { wbase[w] = b; b += wlast[w] - wfirst[w] + 1; }
+    wbase[NW] = b;
+  }
+  __syncthreads();
+  unsigned phase = 0;   // bit bi: parity of the next completion of buffer bi
+  bool timed_out = false;
+
+  // w = S u over this CTA's rows; returns (w, u) over the CTA's rows.  Software pipeline per warp: the
+  // values and column indices of chunk k + NBUF are in flight (TMA) while chunk k is multiplied, and the
+  // u values of chunk k + 1 are gathered (L2) before the products of chunk k are formed.
+  auto spmv = [&](double& wu) {
+    auto issue = [&](int k) {
+      const int q = c0 + k;
+      const int bi = k % NBUF;
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect_tx(&bars[warp][bi], CHB + 128u);
+      bulk_g2s(stage + ((size_t)warp * NBUF + bi) * (BS2 * 32), a.Sval + s_idx(a.chunk_beg[q], 0), CHB, &bars[warp][bi]);
+      bulk_g2s(&cols[warp][bi][0], a.col + a.chunk_beg[q], 128u, &bars[warp][bi]);
+    };
+    auto arrive = [&](int k) {   // wait for chunk k's copies
+      const int bi = k % NBUF;
+      if (!mbar_wait(&bars[warp][bi], (phase >> bi) & 1u, SPIN)) timed_out = true;
+      phase ^= 1u << bi;
+    };
+    if (lane == 0)
+      for (int k = 0; k < NBUF && k < nk; ++k) issue(k);
+    DotAcc<T> acc[6];
+    int row = wfirst[warp];
+    int rend = nk > 0 ? a.row_chunk0[row + 1] : 0;
+    auto flush = [&]() {   // the warp's sums of `row` into its segment, then a fresh accumulator
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const DotAcc<T> y = warp_sum_acc(acc[i]);
+        if (lane == 0) seg[6 * (wbase[warp] + row - wfirst[warp]) + i] = y;
+        acc[i] = DotAcc<T>();
+      }
+    };
+    UVal<T> un;   // u of this lane's column in the next chunk
+    if (nk > 0) {
+      arrive(0);
+      un.gather(a, cols[warp][0][lane]);
+    }
+    for (int k = 0; k < nk; ++k) {
+      const int q = c0 + k;
+      while (q >= rend) {
+        flush();
+        ++row;
+        rend = a.row_chunk0[row + 1];
+      }
+      const int bi = k % NBUF;
+      T B[36];
+      load_block36(stage + ((size_t)warp * NBUF + bi) * (BS2 * 32) + lane * 36, B);
+      const UVal<T> uc = un;
+      if (k + 1 < nk) {
+        arrive(k + 1);
+        un.gather(a, cols[warp][(k + 1) % NBUF][lane]);
+      }
+      __syncwarp();   // every lane holds its block: the buffer may be refilled while the products run
+      if (lane == 0 && k + NBUF < nk) issue(k + NBUF);
+      uc.product(B, acc);
+    }
+    if (nk > 0) flush();
+    __syncthreads();
+    double v = 0;
+    for (int r = r0 + threadIdx.x; r < r1; r += NT) {
+      DotAcc<T> y[6];
+      for (int w = 0; w < NW; ++w)
+        if (wfirst[w] <= r && r <= wlast[w])
+#pragma unroll
+          for (int i = 0; i < 6; ++i) acc_add(y[i], seg[6 * (wbase[w] + r - wfirst[w]) + i]);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double yv = y[i].value();
+        a.w[6 * r + i] = yv;
+        v += yv * a.u[6 * r + i];
+      }
+    }
+    wu = v;
+  };
+  // u = M^-1 r for the CTA's rows (and its split copy); partial (r, u) and (r, r)
+  auto precondition = [&](double& ru, double& rr_) {
+    double v0 = 0, v1 = 0;
+    for (int row = r0 + threadIdx.x; row < r1; row += NT) {
+      double rv[6], zv[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) rv[i] = a.r[6 * row + i];
+      apply_block(a.Minv + (size_t)row * BS2, rv, zv);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        a.u[6 * row + i] = zv[i];
+        if (a.uhl) a.uhl[6 * row + i] = split2(zv[i]);
+        v0 += rv[i] * zv[i];
+        v1 += rv[i] * rv[i];
+      }
+    }
+    ru = v0;
+    rr_ = v1;
+  };
+  auto slot = [&](int par, int k) { return a.part + (size_t)par * 3 * G + (size_t)k * G; };
+
+  // ---- start: x = 0, r = b, u = M^-1 r, w = S u
+  for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) { a.x[k] = 0; a.r[k] = a.b[k]; }
+  __syncthreads();
+  double ru, rrl, wu;
+  precondition(ru, rrl);
+  cta_sum2<NT>(ru, rrl, cta_out);
+  if (threadIdx.x == 0) { slot(0, 0)[c] = cta_out[0]; slot(0, 1)[c] = cta_out[1]; }
+  grid.sync();
+  spmv(wu);
+  cta_sum2<NT>(wu, 0.0, cta_out);
+  if (threadIdx.x == 0) slot(0, 2)[c] = cta_out[0];
+  if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
+  grid.sync();
+  auto reduce3 = [&](int par) {
+    if (threadIdx.x < 32) {
+      double s0 = 0, s1 = 0, s2 = 0;
+      for (int g = threadIdx.x; g < G; g += 32) {
+        s0 += __ldcg(&slot(par, 0)[g]);
+        s1 += __ldcg(&slot(par, 1)[g]);
+        s2 += __ldcg(&slot(par, 2)[g]);
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      if (threadIdx.x == 0) { bc[0] = s0; bc[1] = s1; bc[2] = s2; }
+    }
+    __syncthreads();
+  };
+  reduce3(0);
+  double gam = bc[0];
+  const double bb = bc[1];
+  double alpha = bc[2] > 0 ? gam / bc[2] : 0.0;
+  const double tol2 = a.tol * a.tol * bb;
+  double rr = bb;
+  int it = 0;
+  bool done = !(bb > 0) || !(bc[2] > 0) || (*(volatile int*)&a.S->flags & PCG_FLAG_TIMEOUT);
+  // p = u, s = w
+  for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) { a.p[k] = a.u[k]; a.s[k] = a.w[k]; }
+  int par = 1;
+  while (!done) {
+    // x += alpha p, r -= alpha s, u = M^-1 r; partial (r, u), (r, r)
+    for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {
+      a.x[k] += alpha * a.p[k];
+      a.r[k] -= alpha * a.s[k];
+    }
+    __syncthreads();
+    precondition(ru, rrl);
+    cta_sum2<NT>(ru, rrl, cta_out);
+    if (threadIdx.x == 0) { slot(par, 0)[c] = cta_out[0]; slot(par, 1)[c] = cta_out[1]; }
+    ++it;
+    grid.sync();
+    spmv(wu);
+    cta_sum2<NT>(wu, 0.0, cta_out);
+    if (threadIdx.x == 0) slot(par, 2)[c] = cta_out[0];
+    if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
+    grid.sync();
+    reduce3(par);
+    const double gam_new = bc[0], delta = bc[2];
+    rr = bc[1];
+    if (rr <= tol2 || it >= a.max_iters || !(rr == rr) || (*(volatile int*)&a.S->flags & PCG_FLAG_TIMEOUT)) break;
+    const double beta = gam_new / gam;
+    const double den = delta - beta * gam_new / alpha;
+    alpha = gam_new / den;
+    gam = gam_new;
+    if (!(den > 0)) break;   // S not positive definite along p (rounding): keep the current x
+    for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {
+      a.p[k] = a.u[k] + beta * a.p[k];
+      a.s[k] = a.w[k] + beta * a.s[k];
+    }
+    par ^= 1;
+  }
+  if (c == 0 && threadIdx.x == 0) {
+    a.S->iters = it;
+    a.S->rr = rr;
+    a.S->bnorm2 = bb;
+    a.S->rz = gam;
     a.S->done = 1;
   }
 }
@@ -1749,31 +2088,39 @@ void launch_precond(Problem& P) {
 
 constexpr int PCG_THREADS = 512;
 
+// occupancy and shared-memory opt-in of the streaming PCG for `smem` bytes of chunk sums (the stage
+// buffers come on top)
 template <class T>
 int pcg_blocks_per_sm(size_t smem) {
+  constexpr int NT = StreamCfg<T>::NT, NB = StreamCfg<T>::NBUF;
+  const size_t tot = smem + stream_stage_bytes<T>();
+  cudaFuncSetAttribute(k_pcg_stream<T, NT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_persistent<T, PCG_THREADS, true>, PCG_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_stream<T, NT, NB>, NT, tot);
   return nb;
 }
 
 template <class T>
 void pcg_allow_smem(size_t smem) {
-  cudaFuncSetAttribute(k_pcg_persistent<T, PCG_THREADS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int NT = StreamCfg<T>::NT, NB = StreamCfg<T>::NBUF;
+  cudaFuncSetAttribute(k_pcg_stream<T, NT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(smem + stream_stage_bytes<T>()));
 }
 
 template <class T>
 void launch_pcg(Problem& P) {
   const Dims& d = P.d;
-  PcgArgs<T> a;
+  constexpr int NT = StreamCfg<T>::NT, NB = StreamCfg<T>::NBUF;
+  PcgStreamArgs<T> a;
   a.na = d.na; a.col = P.col; a.cta_row0 = P.cta_row0; a.row_chunk0 = P.row_chunk0; a.chunk_beg = P.chunk_beg;
   a.Sval = (const T*)P.Sval; a.Minv = (const T*)P.Minv; a.b = P.bvec;
-  a.x = P.x; a.r = P.r; a.z = P.z; a.p = P.p; a.Ap = P.Ap; a.part = P.red; a.S = P.S;
-  a.phl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
+  a.x = P.x; a.r = P.r; a.u = P.z; a.p = P.p; a.w = P.Ap; a.s = P.svec; a.part = P.red; a.S = P.S;
+  a.uhl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
   a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
   void* args[] = {&a};
   ++P.launches;
-  P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, PCG_THREADS, true>, dim3(P.pcg_grid),
-                                          dim3(PCG_THREADS), args, P.pcg_smem, P.stream);
+  P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_stream<T, NT, NB>, dim3(P.pcg_grid), dim3(NT), args,
+                                          P.pcg_smem + stream_stage_bytes<T>(), P.stream);
 }
 
 // ---- launchers on caller-provided pointers (FP64), used by the allocation-free PCG entry point
@@ -1912,10 +2259,8 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2)
     for (int64_t q = warp; q < W.nch; q += NW) {
       DotAcc<T> acc[6];
       const int blk = W.chunk_beg[q] + lane;
-      const T* Bg = W.Sval + s_idx(blk, 0);
       T B[36];
-#pragma unroll
-      for (int k = 0; k < 36; ++k) B[k] = Bg[k * 32];
+      load_block36(W.Sval + s_idx(blk, 0), B);
       spmv_block(B, a, W.col[blk], acc);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
