@@ -1396,7 +1396,7 @@ struct PcgStreamArgs {
 template <class T>
 struct StreamCfg;
 template <>
-struct StreamCfg<float> { static constexpr int NT = 256, NBUF = 3; };
+struct StreamCfg<float> { static constexpr int NT = 256, NBUF = 4; };
 template <>
 struct StreamCfg<double> { static constexpr int NT = 256, NBUF = 2; };
 template <class T>
@@ -1451,6 +1451,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   __shared__ int wfirst[NW], wlast[NW], wbase[NW + 1];
   __shared__ double bc[4];
   __shared__ double cta_out[2];
+  __shared__ double red3[NW][3];
   const int G = gridDim.x, c = blockIdx.x;
   const int r0 = a.cta_row0[c], r1 = a.cta_row0[c + 1];
   const int q0 = a.row_chunk0[r0], q1 = a.row_chunk0[r1];
@@ -1484,6 +1485,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   __syncthreads();
   unsigned phase = 0;   // bit bi: parity of the next completion of buffer bi
   bool timed_out = false;
+  bool prefetched = false;   // the first NBUF chunks of the next product are already in flight
 
   // w = S u over this CTA's rows; returns (w, u) over the CTA's rows.  Software pipeline per warp: the
   // values and column indices of chunk k + NBUF are in flight (TMA) while chunk k is multiplied, and the
@@ -1502,8 +1504,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
       if (!mbar_wait(&bars[warp][bi], (phase >> bi) & 1u, SPIN)) timed_out = true;
       phase ^= 1u << bi;
     };
-    if (lane == 0)
+    if (lane == 0 && !prefetched)
       for (int k = 0; k < NBUF && k < nk; ++k) issue(k);
+    prefetched = false;
     DotAcc<T> acc[6];
     int row = wfirst[warp];
     int rend = nk > 0 ? a.row_chunk0[row + 1] : 0;
@@ -1540,6 +1543,12 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
       uc.product(B, acc);
     }
     if (nk > 0) flush();
+    // S is the same in every iteration: start the next product's first chunks now, so that they stream
+    // in while the vectors are updated and the grid waits at its barriers
+    __syncwarp();
+    if (lane == 0)
+      for (int k = 0; k < NBUF && k < nk; ++k) issue(k);
+    prefetched = true;
     __syncthreads();
     double v = 0;
     for (int r = r0 + threadIdx.x; r < r1; r += NT) {
@@ -1558,20 +1567,29 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     wu = v;
   };
   // u = M^-1 r for the CTA's rows (and its split copy); partial (r, u) and (r, r)
+  auto drain = [&]() {   // wait for prefetched copies before the kernel ends
+    if (!prefetched) return;
+    for (int k = 0; k < NBUF && k < nk; ++k) {
+      const int bi = k % NBUF;
+      if (!mbar_wait(&bars[warp][bi], (phase >> bi) & 1u, SPIN)) timed_out = true;
+      phase ^= 1u << bi;
+    }
+    prefetched = false;
+  };
   auto precondition = [&](double& ru, double& rr_) {
     double v0 = 0, v1 = 0;
-    for (int row = r0 + threadIdx.x; row < r1; row += NT) {
-      double rv[6], zv[6];
+    for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {   // one output per thread
+      const int row = k / 6, i = k - 6 * row;
+      const T* M = a.Minv + (size_t)row * BS2 + 6 * i;
+      const double* rv = a.r + 6 * (size_t)row;
+      T zs = 0;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) rv[i] = a.r[6 * row + i];
-      apply_block(a.Minv + (size_t)row * BS2, rv, zv);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        a.u[6 * row + i] = zv[i];
-        if (a.uhl) a.uhl[6 * row + i] = split2(zv[i]);
-        v0 += rv[i] * zv[i];
-        v1 += rv[i] * rv[i];
-      }
+      for (int j = 0; j < 6; ++j) zs += M[j] * (T)rv[j];
+      const double z = (double)zs, ri = rv[i];
+      a.u[k] = z;
+      if (a.uhl) a.uhl[k] = split2(z);
+      v0 += ri * z;
+      v1 += ri * ri;
     }
     ru = v0;
     rr_ = v1;
@@ -1591,18 +1609,22 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   if (threadIdx.x == 0) slot(0, 2)[c] = cta_out[0];
   if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
   grid.sync();
-  auto reduce3 = [&](int par) {
-    if (threadIdx.x < 32) {
-      double s0 = 0, s1 = 0, s2 = 0;
-      for (int g = threadIdx.x; g < G; g += 32) {
-        s0 += __ldcg(&slot(par, 0)[g]);
-        s1 += __ldcg(&slot(par, 1)[g]);
-        s2 += __ldcg(&slot(par, 2)[g]);
-      }
-      s0 = warp_sum(s0);
-      s1 = warp_sum(s1);
-      s2 = warp_sum(s2);
-      if (threadIdx.x == 0) { bc[0] = s0; bc[1] = s1; bc[2] = s2; }
+  auto reduce3 = [&](int par) {   // the three global sums, formed identically in every CTA
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int g = threadIdx.x; g < G; g += NT) {
+      s0 += __ldcg(&slot(par, 0)[g]);
+      s1 += __ldcg(&slot(par, 1)[g]);
+      s2 += __ldcg(&slot(par, 2)[g]);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) { red3[warp][0] = s0; red3[warp][1] = s1; red3[warp][2] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t0 = 0, t1 = 0, t2 = 0;
+      for (int w = 0; w < NW; ++w) { t0 += red3[w][0]; t1 += red3[w][1]; t2 += red3[w][2]; }
+      bc[0] = t0; bc[1] = t1; bc[2] = t2;
     }
     __syncthreads();
   };
@@ -1614,14 +1636,19 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   double rr = bb;
   int it = 0;
   bool done = !(bb > 0) || !(bc[2] > 0) || (*(volatile int*)&a.S->flags & PCG_FLAG_TIMEOUT);
-  // p = u, s = w
-  for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) { a.p[k] = a.u[k]; a.s[k] = a.w[k]; }
+  double beta = 0;
   int par = 1;
   while (!done) {
-    // x += alpha p, r -= alpha s, u = M^-1 r; partial (r, u), (r, r)
+    // p = u + beta p, s = w + beta s (p = u, s = w on the first pass: p and s hold no values yet),
+    // x += alpha p, r -= alpha s; then u = M^-1 r; partial (r, u), (r, r)
+    const bool first = it == 0;
     for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {
-      a.x[k] += alpha * a.p[k];
-      a.r[k] -= alpha * a.s[k];
+      const double pk = first ? a.u[k] : a.u[k] + beta * a.p[k];
+      const double sk = first ? a.w[k] : a.w[k] + beta * a.s[k];
+      a.p[k] = pk;
+      a.s[k] = sk;
+      a.x[k] += alpha * pk;
+      a.r[k] -= alpha * sk;
     }
     __syncthreads();
     precondition(ru, rrl);
@@ -1638,17 +1665,15 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     const double gam_new = bc[0], delta = bc[2];
     rr = bc[1];
     if (rr <= tol2 || it >= a.max_iters || !(rr == rr) || (*(volatile int*)&a.S->flags & PCG_FLAG_TIMEOUT)) break;
-    const double beta = gam_new / gam;
+    beta = gam_new / gam;
     const double den = delta - beta * gam_new / alpha;
     alpha = gam_new / den;
     gam = gam_new;
     if (!(den > 0)) break;   // S not positive definite along p (rounding): keep the current x
-    for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {
-      a.p[k] = a.u[k] + beta * a.p[k];
-      a.s[k] = a.w[k] + beta * a.s[k];
-    }
     par ^= 1;
   }
+  drain();
+  if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
   if (c == 0 && threadIdx.x == 0) {
     a.S->iters = it;
     a.S->rr = rr;
