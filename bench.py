@@ -110,6 +110,12 @@ def workload_desc(s, name):
             f"{c['vp']} VP, {c['p2l'] + c['l2p']} wireframe)")
 
 
+# DRAM bytes per stored block of S and PCG iteration of the streaming PCG kernel (float S), from
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of that kernel on the 2000-camera,
+# 200k-point scene (130 iterations, 1.285M stored blocks); the kernel streams every block once per
+# iteration, so a launch's traffic is this figure times its blocks and iterations
+PCG_DRAM_BYTES_PER_BLOCK_ITER = 153.3
+
 # per-unit algorithmic FP32 flops of the linearisation (residual + Jacobian + IRLS-weighted accumulation of
 # V_f, g_f and the per-slot blocks), counted from the formulas of each residual kind
 LIN_FLOPS = {"point": 354, "line": 1100, "plane_point": 660, "plane_line": 2700, "vp": 280, "p2l": 210, "l2p": 440}
@@ -263,8 +269,13 @@ def main():
             achieved = work / (kern[dom] / 1e3) / 1e12
             peak = FP32_PEAK_TFLOPS
             src = "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"
+        traffic = None
+        if dom == "pcg" and prec == B.BA_MIXED:
+            traffic = int(PCG_DRAM_BYTES_PER_BLOCK_ITER * dims["stored_blocks"] * dims["pcg_iters_mean"])
         roof = {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": unit,
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src}
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
+                "work": "algorithmic bytes per launch: PCG iterations x (stored blocks x (36 values + 4-byte column) "
+                        "+ block rows x 6 x 8 bytes x 10 vector accesses)"}
     else:
         roof = {"bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "note": "no algorithmic model for this stage"}
