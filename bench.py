@@ -310,18 +310,53 @@ def main():
                "accepted": sr.accepted_steps, "pcg_iters_total": sr.total_pcg_iters, "cost0": sr.cost0,
                "cost": sr.cost, "precision": args.precision, "precond": "learned (shipped weights)"}
 
-    # ---------------- the FP64 block-Jacobi form to convergence on the same scene (the comparison form)
+    # ---------------- time to converge at equal final-cost accuracy: the mixed learned form and the plain FP64
+    # block-Jacobi form, each stepped with ba_lm_step (structure built before the clock starts) until its own
+    # stopping rule; the target is the lower of the two final costs plus 1e-5 relative, and a form that stopped
+    # above it keeps iterating (up to --max-iters) until it reaches it
     ttc64 = None
+    equal = None
     if not args.no_fp64_ttc and not args.no_e2e:
-        q = B.ba_create(B.ba_default_options(precision=B.BA_FP64, max_lm_iters=args.max_iters))
-        B.load_scene(q, scene)
-        t = time.perf_counter()
-        sr = B.ba_solve(q)
-        wall = time.perf_counter() - t
-        B.ba_destroy(q)
-        ttc64 = {"seconds_wall": round(wall, 3), "seconds_solve": round((sr.ms_total - sr.ms_structure) / 1e3, 3),
-                 "iters": sr.iters, "converged": bool(sr.converged), "cost": sr.cost,
-                 "cost_rel_to_mixed": (abs(sr.cost - ttc["cost"]) / sr.cost) if ttc else None}
+        forms = {}
+        for name, pr, pc in (("mixed_learned", B.BA_MIXED, B.BA_PRECOND_LEARNED),
+                             ("fp64_block_jacobi", B.BA_FP64, B.BA_PRECOND_BLOCK_JACOBI)):
+            q = B.ba_create(B.ba_default_options(precision=pr, precond=pc))
+            B.load_scene(q, scene)
+            if pc == B.BA_PRECOND_LEARNED:
+                B.ba_precond_set_weights(q, shipped_weights())
+            B.ba_eval_cost(q)                                 # builds the structure
+            f = {"q": q, "t": 0.0, "traj": [], "stop": None, "pcg": 0}
+            while len(f["traj"]) < args.max_iters:
+                t = time.perf_counter()
+                r = B.ba_lm_step(q)
+                f["t"] += time.perf_counter() - t
+                f["pcg"] += r.pcg_iters
+                f["traj"].append((f["t"], r.cost_new if r.accepted else r.cost, f["pcg"]))
+                if r.converged:
+                    f["stop"] = len(f["traj"])
+                    break
+            forms[name] = f
+        target = min(f["traj"][-1][1] for f in forms.values()) * (1 + 1e-5)
+        equal = {"target_cost": target, "rule": "lower final cost of the two forms + 1e-5 relative"}
+        for name, f in forms.items():
+            while f["traj"][-1][1] > target and len(f["traj"]) < args.max_iters:
+                t = time.perf_counter()
+                r = B.ba_lm_step(f["q"])
+                f["t"] += time.perf_counter() - t
+                f["pcg"] += r.pcg_iters
+                f["traj"].append((f["t"], r.cost_new if r.accepted else r.cost, f["pcg"]))
+            hit = next((k for k, row in enumerate(f["traj"]) if row[1] <= target), None)
+            B.ba_destroy(f["q"])
+            equal[name] = {"seconds": round(f["traj"][hit][0], 3) if hit is not None else None,
+                           "lm_iters": hit + 1 if hit is not None else None,
+                           "pcg_iters": f["traj"][hit][2] if hit is not None else None,
+                           "stopped_at_iter": f["stop"], "final_cost_at_stop": f["traj"][(f["stop"] or 1) - 1][1]}
+        if equal["mixed_learned"]["seconds"] and equal["fp64_block_jacobi"]["seconds"]:
+            equal["speedup_mixed_learned_over_fp64"] = round(
+                equal["fp64_block_jacobi"]["seconds"] / equal["mixed_learned"]["seconds"], 2)
+        f64 = equal["fp64_block_jacobi"]
+        ttc64 = {"seconds_solve": round(forms["fp64_block_jacobi"]["traj"][(f64["stopped_at_iter"] or 1) - 1][0], 3),
+                 "iters": f64["stopped_at_iter"], "cost": f64["final_cost_at_stop"]}
 
     # ---------------- batched local windows in one persistent launch (CUDA graph), autotuned
     batched = None
@@ -377,6 +412,7 @@ def main():
                           "parallelism": "replicas" if world > 1 else "single GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "time_to_converge": ttc, "time_to_converge_fp64_block_jacobi": ttc64,
+               "time_to_equal_cost": equal,
                "batched_windows": batched, "learned_precond": learned,
                "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
                "pcg_iters": pcg_iters, "pcg_rel": pcg_rel, "reduced_system": dims_S,

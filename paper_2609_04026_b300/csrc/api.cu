@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "ba_internal.cuh"
@@ -168,13 +169,23 @@ extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int
   int md = kMeasDim[kind];
   std::vector<double> m;
   if (md) { if ((s = fetch(p, mem, meas, (size_t)md * n, m))) return s; }
-  b.meas.assign(4 * n, 0.0);
-  for (int64_t i = 0; i < n; ++i)
-    for (int k = 0; k < md; ++k) {
-      double v = m[(size_t)md * i + k];
-      if (!std::isfinite(v)) return set_err(p, BA_ERR_ARG, "non-finite measurement");
-      b.meas[4 * i + k] = v;
-    }
+  b.meas.resize(4 * n);
+  std::vector<int64_t> bad_at(1, n);
+  {
+    std::mutex mu;
+    host_parallel_for(n, [&](int64_t i0, int64_t i1) {
+      int64_t bad = n;
+      for (int64_t i = i0; i < i1; ++i)
+        for (int k = 0; k < 4; ++k) {
+          const double v = k < md ? m[(size_t)md * i + k] : 0.0;
+          if (!std::isfinite(v) && bad == n) bad = i;
+          b.meas[4 * i + k] = v;
+        }
+      std::lock_guard<std::mutex> g(mu);
+      bad_at[0] = std::min(bad_at[0], bad);
+    });
+  }
+  if (bad_at[0] < n) return set_err(p, BA_ERR_ARG, "non-finite measurement");
   if (n > 0) p->h_obs.push_back(std::move(b));
   return BA_OK;
 }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ba.h"
@@ -187,6 +188,18 @@ struct ba_problem {
 };
 
 namespace ba {
+// fn(begin, end) over [0, n) in contiguous pieces on up to 32 host threads (one piece below 1M items)
+template <class F>
+void host_parallel_for(int64_t n, F fn) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int nt = (int)std::min<int64_t>(hw ? (hw > 32 ? 32 : hw) : 1, (n + (1 << 20) - 1) >> 20);
+  if (nt <= 1) { if (n > 0) fn((int64_t)0, n); return; }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int t = 0; t < nt; ++t) th.emplace_back([&, t]() { fn(n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
 ba_status build_structure(Problem& P);   // structure.cu
 // batched windows (kernels.cu, launched from batch.cu)
 template <class T> void fill_window_desc(Problem& P, void* out);

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "ba_internal.cuh"
@@ -623,40 +624,61 @@ ba_status build_structure(Problem& P) {
   std::vector<int32_t> cam(nr), feat(nr), grp(nr);
   std::vector<double> meas(4 * nr);
   {
+    // every batch is checked and copied on several host threads; the first bad record of a batch (lowest
+    // index) names the error, so the message does not depend on the thread count
     int64_t o = 0;
     for (auto& b : P.h_obs) {
       const int64_t n = (int64_t)b.feat.size();
       const int k = b.kind;
       const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L);
       const int64_t nfk = is_point ? d.np : d.nl;
-      for (int64_t i = 0; i < n; ++i, ++o) {
-        kind[o] = (int8_t)k;
-        const int32_t f = b.feat[i];
-        if (f < 0 || f >= nfk) return fail(P, BA_ERR_ARG, "observation kind " + std::to_string(k) + ": feature id out of range");
-        feat[o] = is_point ? f : (int32_t)(d.np + f);
-        if (k != R_VP) {
-          const int32_t c = b.cam[i];
-          if (c < 0 || c >= d.nc) return fail(P, BA_ERR_ARG, "observation kind " + std::to_string(k) + ": camera id out of range");
-          cam[o] = c;
-        } else {
-          cam[o] = -1;
+      std::vector<std::pair<int64_t, int>> firsts;   // (index, error code) of each piece
+      std::mutex mu;
+      host_parallel_for(n, [&](int64_t i0, int64_t i1) {
+        int code = 0;
+        int64_t at = n;
+        for (int64_t i = i0; i < i1 && !code; ++i) {
+          const int64_t j = o + i;
+          kind[j] = (int8_t)k;
+          const int32_t f = b.feat[i];
+          if (f < 0 || f >= nfk) { code = 1; at = i; break; }
+          feat[j] = is_point ? f : (int32_t)(d.np + f);
+          if (k != R_VP) {
+            const int32_t c = b.cam[i];
+            if (c < 0 || c >= d.nc) { code = 2; at = i; break; }
+            cam[j] = c;
+          } else {
+            cam[j] = -1;
+          }
+          grp[j] = -1;
+          if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
+            const int32_t g = b.other[i];
+            if (g < 0 || g >= d.npl) { code = 3; at = i; break; }
+            grp[j] = g;
+          } else if (k == R_VP) {
+            const int32_t g = b.other[i];
+            if (g < 0 || g >= d.nv) { code = 4; at = i; break; }
+            grp[j] = g;
+          } else if ((k == R_P2L || k == R_L2P) && !b.other.empty()) {
+            const int32_t g = b.other[i];
+            const int64_t lim = (k == R_P2L) ? d.nl : d.np;
+            if (g < 0 || g >= lim) { code = 5; at = i; break; }
+          }
         }
-        grp[o] = -1;
-        if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
-          const int32_t g = b.other[i];
-          if (g < 0 || g >= d.npl) return fail(P, BA_ERR_ARG, "plane id out of range");
-          grp[o] = g;
-        } else if (k == R_VP) {
-          const int32_t g = b.other[i];
-          if (g < 0 || g >= d.nv) return fail(P, BA_ERR_ARG, "vp id out of range");
-          grp[o] = g;
-        } else if ((k == R_P2L || k == R_L2P) && !b.other.empty()) {
-          const int32_t g = b.other[i];
-          const int64_t lim = (k == R_P2L) ? d.nl : d.np;
-          if (g < 0 || g >= lim) return fail(P, BA_ERR_ARG, "partner feature id out of range");
-        }
+        if (!code && i1 > i0) std::memcpy(&meas[4 * (o + i0)], b.meas.data() + 4 * i0, sizeof(double) * 4 * (i1 - i0));
+        std::lock_guard<std::mutex> g(mu);
+        if (code) firsts.emplace_back(at, code);
+      });
+      if (!firsts.empty()) {
+        const int code = std::min_element(firsts.begin(), firsts.end())->second;
+        const std::string ks = std::to_string(k);
+        if (code == 1) return fail(P, BA_ERR_ARG, "observation kind " + ks + ": feature id out of range");
+        if (code == 2) return fail(P, BA_ERR_ARG, "observation kind " + ks + ": camera id out of range");
+        if (code == 3) return fail(P, BA_ERR_ARG, "plane id out of range");
+        if (code == 4) return fail(P, BA_ERR_ARG, "vp id out of range");
+        return fail(P, BA_ERR_ARG, "partner feature id out of range");
       }
-      if (n) std::memcpy(&meas[4 * (o - n)], b.meas.data(), sizeof(double) * 4 * n);
+      o += n;
     }
   }
   P.h_obs.clear();
