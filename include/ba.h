@@ -27,8 +27,9 @@
  *     owns all device memory it allocates (through the optional allocator hooks
  *     of ba_options, else cudaMalloc) and frees it in ba_destroy.
  *   Indices: 0-based int32, per type (point ids, line ids, plane ids, VP ids).
- *     They are validated when the structure is frozen (first step); an out of
- *     range index returns BA_ERR_ARG.
+ *     They, and the finiteness of the measurements, are validated when the
+ *     structure is frozen (first step); an out of range index or a non-finite
+ *     measurement returns BA_ERR_ARG there.
  *   Freezing: adding data after the first ba_lm_step / ba_solve / ba_build_reduced
  *     returns BA_ERR_STATE.
  *   Errors: no exception or abort crosses the ABI.  Every call returns a

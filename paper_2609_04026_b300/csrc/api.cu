@@ -16,8 +16,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "ba_internal.cuh"
 
@@ -78,6 +78,7 @@ extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
 extern "C" void ba_destroy(ba_problem* p) {
   if (!p) return;
   cudaStreamSynchronize(p->stream);
+  p->release_obs();
   for (auto& b : p->bufs) p->alloc.put(b.p);
   p->bufs.clear();
   if (p->hS) cudaFreeHost(p->hS);
@@ -159,34 +160,37 @@ extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int
   ba_status s = check_add(p, n);
   if (s) return s;
   if (kind < 0 || kind > 6) return set_err(p, BA_ERR_ARG, "unknown observation kind");
+  if (mem != BA_MEM_HOST && mem != BA_MEM_DEVICE) return set_err(p, BA_ERR_ARG, "mem must be BA_MEM_HOST or BA_MEM_DEVICE");
+  if (n == 0) return BA_OK;
+  const bool needs_other = kind == BA_OBS_PLANE_POINT || kind == BA_OBS_PLANE_LINE || kind == BA_OBS_VP;
+  const int md = kMeasDim[kind];
+  if (!feature || (kind != BA_OBS_VP && !cam) || (md && !meas)) return set_err(p, BA_ERR_ARG, "null array");
+  if (needs_other && !other) return set_err(p, BA_ERR_ARG, "this observation kind needs the group id array");
+  // the records go straight to device memory: the structure build validates and merges them there
   ba_problem::ObsBatch b;
   b.kind = kind;
-  if ((s = fetch(p, mem, feature, n, b.feat))) return s;
-  if (kind != BA_OBS_VP) { if ((s = fetch(p, mem, cam, n, b.cam))) return s; }
-  bool needs_other = kind == BA_OBS_PLANE_POINT || kind == BA_OBS_PLANE_LINE || kind == BA_OBS_VP;
-  if (other) { if ((s = fetch(p, mem, other, n, b.other))) return s; }
-  else if (needs_other && n > 0) return set_err(p, BA_ERR_ARG, "this observation kind needs the group id array");
-  int md = kMeasDim[kind];
-  std::vector<double> m;
-  if (md) { if ((s = fetch(p, mem, meas, (size_t)md * n, m))) return s; }
-  b.meas.resize(4 * n);
-  std::vector<int64_t> bad_at(1, n);
-  {
-    std::mutex mu;
-    host_parallel_for(n, [&](int64_t i0, int64_t i1) {
-      int64_t bad = n;
-      for (int64_t i = i0; i < i1; ++i)
-        for (int k = 0; k < 4; ++k) {
-          const double v = k < md ? m[(size_t)md * i + k] : 0.0;
-          if (!std::isfinite(v) && bad == n) bad = i;
-          b.meas[4 * i + k] = v;
-        }
-      std::lock_guard<std::mutex> g(mu);
-      bad_at[0] = std::min(bad_at[0], bad);
-    });
+  b.md = md;
+  b.n = n;
+  const cudaMemcpyKind dir = mem == BA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  bool ok = true;
+  auto stage = [&](auto*& dst, const auto* src, size_t count) {
+    if (!ok || !src) return;
+    const size_t bytes = sizeof(*src) * count;
+    dst = (std::remove_const_t<std::remove_reference_t<decltype(*src)>>*)p->alloc.get(bytes);
+    if (!dst || cudaMemcpyAsync(dst, src, bytes, dir, p->stream) != cudaSuccess) ok = false;
+  };
+  stage(b.feat, feature, (size_t)n);
+  if (kind != BA_OBS_VP) stage(b.cam, cam, (size_t)n);
+  stage(b.other, other, (size_t)n);
+  if (md) stage(b.meas, meas, (size_t)md * n);
+  // the caller may reuse its buffers on return (also pinned ones, whose copies are asynchronous)
+  const cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (!ok || e != cudaSuccess) {
+    p->alloc.put(b.feat); p->alloc.put(b.cam); p->alloc.put(b.other); p->alloc.put(b.meas);
+    cudaGetLastError();
+    return set_err(p, ok ? BA_ERR_CUDA : BA_ERR_OOM, "could not copy the observations to the device");
   }
-  if (bad_at[0] < n) return set_err(p, BA_ERR_ARG, "non-finite measurement");
-  if (n > 0) p->h_obs.push_back(std::move(b));
+  p->d_obs.push_back(b);
   return BA_OK;
 }
 

@@ -7,7 +7,6 @@
 #include <stdint.h>
 
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/ba.h"
@@ -111,12 +110,19 @@ struct ba_problem {
   std::vector<double> h_cam;      // n x 12: q(4) t(3) f k1 k2 ppx ppy
   std::vector<uint8_t> h_fixed;
   std::vector<double> h_pts, h_lin, h_pln, h_vps;
+  // residual records as added, copied to the device at add time (validated and merged by the structure build,
+  // which releases them); cam is null for VP records, other may be null, meas holds n x meas_dim values
   struct ObsBatch {
-    int kind;
-    std::vector<int32_t> cam, feat, other;
-    std::vector<double> meas;  // n x 4 padded
+    int kind = 0, md = 0;
+    int64_t n = 0;
+    int32_t *cam = nullptr, *feat = nullptr, *other = nullptr;
+    double* meas = nullptr;
   };
-  std::vector<ObsBatch> h_obs;
+  std::vector<ObsBatch> d_obs;
+  void release_obs() {
+    for (auto& b : d_obs) { alloc.put(b.cam); alloc.put(b.feat); alloc.put(b.other); alloc.put(b.meas); }
+    d_obs.clear();
+  }
 
   ba::Dims d;
   std::vector<ba::DBuf> bufs;
@@ -188,18 +194,6 @@ struct ba_problem {
 };
 
 namespace ba {
-// fn(begin, end) over [0, n) in contiguous pieces on up to 32 host threads (one piece below 1M items)
-template <class F>
-void host_parallel_for(int64_t n, F fn) {
-  unsigned hw = std::thread::hardware_concurrency();
-  int nt = (int)std::min<int64_t>(hw ? (hw > 32 ? 32 : hw) : 1, (n + (1 << 20) - 1) >> 20);
-  if (nt <= 1) { if (n > 0) fn((int64_t)0, n); return; }
-  std::vector<std::thread> th;
-  th.reserve(nt);
-  for (int t = 0; t < nt; ++t) th.emplace_back([&, t]() { fn(n * t / nt, n * (t + 1) / nt); });
-  for (auto& x : th) x.join();
-}
-
 ba_status build_structure(Problem& P);   // structure.cu
 // batched windows (kernels.cu, launched from batch.cu)
 template <class T> void fill_window_desc(Problem& P, void* out);

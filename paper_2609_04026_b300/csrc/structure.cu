@@ -1,7 +1,9 @@
 // One-time structure build (K0): the analogue of a sparse solver's symbolic
 // analysis, which the paper observes only on the first iteration of each BA
-// call (Section 4, Fig. 3c).  The host validates every index (BA_ERR_ARG on
-// failure) and uploads the residual records; the rest runs on the GPU:
+// call (Section 4, Fig. 3c).  It runs on the GPU from the residual records
+// that ba_add_observations copied there:
+//   * every record is validated (an out of range id or a non-finite measurement
+//     gives BA_ERR_ARG naming the first bad record) and merged in input order,
 //   * the residual records are ordered feature-major (each residual touches
 //     exactly one feature, Section 3.2-3.4, so H_ff is block-diagonal), and by
 //     camera inside a feature, with a stable LSD radix sort,
@@ -24,7 +26,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <numeric>
 
 #include "ba_internal.cuh"
@@ -535,6 +536,62 @@ __global__ void k_unit_key(const int32_t* __restrict__ un_se, int64_t nun, uint3
   }
 }
 
+// validation and merge of one batch of residual records into the input-order arrays; a bad record leaves
+// (merged index << 3 | code) in *err (atomicMin: the lowest index wins)
+struct ObsGather {
+  int kind, md;
+  int64_t n, o;
+  const int32_t *cam, *feat, *other;
+  const double* meas;
+  int64_t np, nl, nc, npl, nv;
+  int8_t* kind_d;
+  int32_t *cam_d, *feat_d, *grp_d;
+  double* meas_d;
+  unsigned long long* err;
+};
+
+__global__ void k_gather_obs(ObsGather a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int64_t j = a.o + i;
+  const int k = a.kind;
+  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L);
+  int code = 0;
+  const int32_t f = a.feat[i];
+  if (f < 0 || f >= (is_point ? a.np : a.nl)) code = 1;
+  int32_t c = -1;
+  if (!code && k != R_VP) {
+    c = a.cam[i];
+    if (c < 0 || c >= a.nc) code = 2;
+  }
+  int32_t g = -1;
+  if (!code && (k == R_PLANE_POINT || k == R_PLANE_LINE)) {
+    g = a.other[i];
+    if (g < 0 || g >= a.npl) code = 3;
+  } else if (!code && k == R_VP) {
+    g = a.other[i];
+    if (g < 0 || g >= a.nv) code = 4;
+  } else if (!code && (k == R_P2L || k == R_L2P) && a.other) {
+    const int32_t q = a.other[i];
+    if (q < 0 || q >= (k == R_P2L ? a.nl : a.np)) code = 5;
+  }
+  double m[4] = {0, 0, 0, 0};
+  for (int t = 0; t < a.md; ++t) {
+    m[t] = a.meas[(size_t)a.md * i + t];
+    if (!code && !isfinite(m[t])) code = 6;
+  }
+  if (code) {
+    atomicMin(a.err, ((unsigned long long)j << 3) | (unsigned long long)code);
+    return;
+  }
+  a.kind_d[j] = (int8_t)k;
+  a.feat_d[j] = is_point ? f : (int32_t)(a.np + f);
+  a.cam_d[j] = c;
+  a.grp_d[j] = g;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) a.meas_d[4 * j + t] = m[t];
+}
+
 struct Permute {
   const uint32_t* order;
   const int8_t* kind;
@@ -615,74 +672,11 @@ ba_status build_structure(Problem& P) {
     for (int k = 0; k < 3; ++k) v[k] /= n;
   }
 
-  // ---- validate the residual records and stage them in input order
+  // ---- residual records: validated and merged in input order on the device (below)
   int64_t nr = 0;
-  for (auto& b : P.h_obs) nr += (int64_t)b.feat.size();
+  for (auto& b : P.d_obs) nr += b.n;
   if (nr > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many residuals");
   d.nr = nr;
-  std::vector<int8_t> kind(nr);
-  std::vector<int32_t> cam(nr), feat(nr), grp(nr);
-  std::vector<double> meas(4 * nr);
-  {
-    // every batch is checked and copied on several host threads; the first bad record of a batch (lowest
-    // index) names the error, so the message does not depend on the thread count
-    int64_t o = 0;
-    for (auto& b : P.h_obs) {
-      const int64_t n = (int64_t)b.feat.size();
-      const int k = b.kind;
-      const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L);
-      const int64_t nfk = is_point ? d.np : d.nl;
-      std::vector<std::pair<int64_t, int>> firsts;   // (index, error code) of each piece
-      std::mutex mu;
-      host_parallel_for(n, [&](int64_t i0, int64_t i1) {
-        int code = 0;
-        int64_t at = n;
-        for (int64_t i = i0; i < i1 && !code; ++i) {
-          const int64_t j = o + i;
-          kind[j] = (int8_t)k;
-          const int32_t f = b.feat[i];
-          if (f < 0 || f >= nfk) { code = 1; at = i; break; }
-          feat[j] = is_point ? f : (int32_t)(d.np + f);
-          if (k != R_VP) {
-            const int32_t c = b.cam[i];
-            if (c < 0 || c >= d.nc) { code = 2; at = i; break; }
-            cam[j] = c;
-          } else {
-            cam[j] = -1;
-          }
-          grp[j] = -1;
-          if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
-            const int32_t g = b.other[i];
-            if (g < 0 || g >= d.npl) { code = 3; at = i; break; }
-            grp[j] = g;
-          } else if (k == R_VP) {
-            const int32_t g = b.other[i];
-            if (g < 0 || g >= d.nv) { code = 4; at = i; break; }
-            grp[j] = g;
-          } else if ((k == R_P2L || k == R_L2P) && !b.other.empty()) {
-            const int32_t g = b.other[i];
-            const int64_t lim = (k == R_P2L) ? d.nl : d.np;
-            if (g < 0 || g >= lim) { code = 5; at = i; break; }
-          }
-        }
-        if (!code && i1 > i0) std::memcpy(&meas[4 * (o + i0)], b.meas.data() + 4 * i0, sizeof(double) * 4 * (i1 - i0));
-        std::lock_guard<std::mutex> g(mu);
-        if (code) firsts.emplace_back(at, code);
-      });
-      if (!firsts.empty()) {
-        const int code = std::min_element(firsts.begin(), firsts.end())->second;
-        const std::string ks = std::to_string(k);
-        if (code == 1) return fail(P, BA_ERR_ARG, "observation kind " + ks + ": feature id out of range");
-        if (code == 2) return fail(P, BA_ERR_ARG, "observation kind " + ks + ": camera id out of range");
-        if (code == 3) return fail(P, BA_ERR_ARG, "plane id out of range");
-        if (code == 4) return fail(P, BA_ERR_ARG, "vp id out of range");
-        return fail(P, BA_ERR_ARG, "partner feature id out of range");
-      }
-      o += n;
-    }
-  }
-  P.h_obs.clear();
-  P.h_obs.shrink_to_fit();
 
   Scratch S(&P.alloc, P.stream);
   const int NT = 256;
@@ -696,12 +690,40 @@ ba_status build_structure(Problem& P) {
   double* meas_d = S.get<double>(4 * nr);
   uint8_t* fixed_d = S.get<uint8_t>(d.nc);
   if (!kind_d || !cam_d || !feat_d || !grp_d || !meas_d || !fixed_d) return oom();
-  if (nr) {
-    CU(cudaMemcpyAsync(kind_d, kind.data(), nr, cudaMemcpyHostToDevice, P.stream));
-    CU(cudaMemcpyAsync(cam_d, cam.data(), 4 * nr, cudaMemcpyHostToDevice, P.stream));
-    CU(cudaMemcpyAsync(feat_d, feat.data(), 4 * nr, cudaMemcpyHostToDevice, P.stream));
-    CU(cudaMemcpyAsync(grp_d, grp.data(), 4 * nr, cudaMemcpyHostToDevice, P.stream));
-    CU(cudaMemcpyAsync(meas_d, meas.data(), 32 * nr, cudaMemcpyHostToDevice, P.stream));
+  {
+    unsigned long long* err = S.get<unsigned long long>(1);
+    if (!err) return oom();
+    const unsigned long long none = ~0ull;
+    CU(cudaMemcpyAsync(err, &none, sizeof(none), cudaMemcpyHostToDevice, P.stream));
+    int64_t o = 0;
+    for (auto& b : P.d_obs) {
+      ObsGather g{b.kind, b.md, b.n, o, b.cam, b.feat, b.other, b.meas, d.np, d.nl, d.nc, d.npl, d.nv,
+                  kind_d, cam_d, feat_d, grp_d, meas_d, err};
+      k_gather_obs<<<grid_of(b.n, NT), NT, 0, P.stream>>>(g);
+      o += b.n;
+    }
+    unsigned long long herr = none;
+    CU(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, P.stream));
+    CU(cudaStreamSynchronize(P.stream));
+    if (herr != none) {
+      // the lowest offending record of the merged input order names the error
+      const int code = (int)(herr & 7ull);
+      const int64_t j = (int64_t)(herr >> 3);
+      int kk = 0;
+      int64_t o2 = 0;
+      for (auto& b : P.d_obs) {
+        if (j < o2 + b.n) { kk = b.kind; break; }
+        o2 += b.n;
+      }
+      const std::string ks = std::to_string(kk);
+      if (code == 1) return fail(P, BA_ERR_ARG, "observation kind " + ks + ": feature id out of range");
+      if (code == 2) return fail(P, BA_ERR_ARG, "observation kind " + ks + ": camera id out of range");
+      if (code == 3) return fail(P, BA_ERR_ARG, "plane id out of range");
+      if (code == 4) return fail(P, BA_ERR_ARG, "vp id out of range");
+      if (code == 5) return fail(P, BA_ERR_ARG, "partner feature id out of range");
+      return fail(P, BA_ERR_ARG, "non-finite measurement");
+    }
+    P.release_obs();
   }
   if (d.nc) CU(cudaMemcpyAsync(fixed_d, P.h_fixed.data(), d.nc, cudaMemcpyHostToDevice, P.stream));
 
