@@ -280,6 +280,7 @@ static ba_status freeze(ba_problem* p) {
   ok &= A(p->slotG, T * SG * (size_t)d.ne);
   ok &= A(p->slotB, T * SG * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
+  ok &= A(p->slotBS, T * 6 * (size_t)d.ne);
   ok &= A(p->Sval, T * BS2 * (size_t)d.nbp);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);

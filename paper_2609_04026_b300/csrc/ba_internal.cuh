@@ -168,6 +168,7 @@ struct ba_problem {
   cudaError_t pcg_err = cudaSuccess;
   // numeric arrays
   void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotZ = nullptr, *slotB = nullptr;
+  void* slotBS = nullptr;       // back-substitution: per slot W da (4), G.da, da^T H da + 2 da^T C dplane
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featu = nullptr, *featL = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr;
   double *bvec = nullptr, *Dg = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;

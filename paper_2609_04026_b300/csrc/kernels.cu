@@ -15,7 +15,8 @@
 //   k_precond       K4: block-Jacobi inverse of the diagonal blocks of S (FP64 Cholesky)
 //   k_pcg_*         K5/K6: PCG with a warp-per-block-row SpMV, FP64 vectors and dots, and
 //                   a device-side stop flag so the host never waits inside the loop
-//   k_backsub       K7: delta_f = -V^-1 (g_f + W^T delta_a) and the predicted decrease
+//   k_backsub_slots K7: per slot W delta_a and its shares of g.delta, delta^T H delta
+//   k_backsub       K7: delta_f = -V^-1 (g_f + sum W^T delta_a) and the predicted decrease
 //                   -g.delta - 1/2 delta^T H delta from the stored blocks
 //   k_candidate     K8: x (+) delta with the manifold retractions
 //   k_cost          K8: FP64 robust cost of every residual, E and E_px
@@ -1688,48 +1689,79 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
 // ============================================================================
 template <class T>
 struct BackArgs {
-  const int32_t *fslot_off, *slot_ent, *feat_plane_slot;
+  const int32_t *fslot_off, *slot_ent, *slot_feat, *feat_plane_slot;
   const uint8_t* slot_type;
   const double *V, *Vinv, *g, *x;
   const T *W, *H, *G, *C;
+  T* sv;        // per slot: W_e da (4, zero-padded), G_e . da, da^T H_e da + 2 da^T C_e dplane
   double* df;
-  int64_t np, nf;
+  int64_t np, nf, ne;
   DevScalars* S;
   double* red;
 };
 
+// The slot part (a thread per slot, records read coalesced): the slot's share of t_f = g_f + sum_e W_e da and
+// of the predicted decrease.
+template <class T>
+__device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
+  const int64_t f = a.slot_feat[e];
+  const int K = f < a.np ? 3 : 4;
+  const double* da = a.x + 6 * (size_t)a.slot_ent[e];
+  T dv[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
+  const T* W = a.W + (size_t)e * SW;
+  T* so = a.sv + (size_t)e * 6;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T s = 0;
+    if (i < K)   // a point's W has three rows
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
+    so[i] = s;
+  }
+  const T* G = a.G + (size_t)e * SG;
+  const T* H = a.H + (size_t)e * SH;
+  T gd = 0, hq = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    gd += G[i] * dv[i];
+    T hv = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) hv += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] * dv[j];
+    hq += dv[i] * hv;
+  }
+  T cpl = 0;
+  const int pslot = a.feat_plane_slot[f];
+  if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {   // camera-plane direct block of a plane feature
+    const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
+    const T dpl[3] = {(T)dp[0], (T)dp[1], (T)dp[2]};
+    const T* Cm = a.C + (size_t)e * SC;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
+  }
+  so[4] = gd;
+  so[5] = hq + T(2) * cpl;
+}
+
+// The feature part: delta_f = -V^-1 t_f, and the feature's share of g.delta and delta^T H delta:
+//   g_f.df + sum_e G_e.da   and   df^T V df + 2 (t_f - g_f).df + sum_e (da^T H_e da + 2 da^T C_e dplane)
+// where (t_f - g_f).df = sum_e (W_e da).df is the feature-camera cross term.
 template <class T, int K>
 __device__ void backsub_feature(const BackArgs<T>& a, int64_t f, double& gTd, double& dHd) {
   double t[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) t[i] = a.g[4 * f + i];
-  const int e0 = a.fslot_off[f], e1 = a.fslot_off[f + 1];
-  T gd = 0, hq = 0;  // sum_e g_e . da  and  sum_e da^T H_e da
-  for (int e = e0; e < e1; ++e) {
-    const double* da = a.x + 6 * (size_t)a.slot_ent[e];
-    T dv[6];
+  double gd = 0, hh = 0;
+  for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
+    const T* so = a.sv + (size_t)e * 6;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
-    const T* W = a.W + (size_t)e * SW;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      T s = 0;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
-      t[i] += (double)s;
-    }
-    const T* G = a.G + (size_t)e * SG;
-    const T* H = a.H + (size_t)e * SH;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      gd += G[i] * dv[i];
-      T hv = 0;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) hv += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] * dv[j];
-      hq += dv[i] * hv;
-    }
+    for (int i = 0; i < K; ++i) t[i] += (double)so[i];
+    gd += (double)so[4];
+    hh += (double)so[5];
   }
-  // delta_f = -V^-1 t
   double dfv[K];
   const double* Vi = a.Vinv + 10 * f;
 #pragma unroll
@@ -1740,49 +1772,23 @@ __device__ void backsub_feature(const BackArgs<T>& a, int64_t f, double& gTd, do
     dfv[i] = -s;
     a.df[4 * f + i] = -s;
   }
-  // cross terms: 2 sum_e (W_e da) . df  and camera-plane direct blocks
-  T cross = 0, cpl = 0;
-  T dft[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) dft[i] = (T)dfv[i];
-  const int pslot = a.feat_plane_slot[f];
-  T dpl[3] = {0, 0, 0};
-  if (pslot >= 0) {
-    const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
-    dpl[0] = (T)dp[0]; dpl[1] = (T)dp[1]; dpl[2] = (T)dp[2];
-  }
-  for (int e = e0; e < e1; ++e) {
-    const double* da = a.x + 6 * (size_t)a.slot_ent[e];
-    T dv[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
-    const T* W = a.W + (size_t)e * SW;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      T s = 0;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
-      cross += s * dft[i];
-    }
-    if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {
-      const T* Cm = a.C + (size_t)e * SC;
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
-    }
-  }
-  // df^T V df and g_f . df
   const double* Vf = a.V + 10 * f;
-  double vq = 0, gfd = 0;
+  double vq = 0, gfd = 0, cross = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     gfd += a.g[4 * f + i] * dfv[i];
+    cross += (t[i] - a.g[4 * f + i]) * dfv[i];
 #pragma unroll
     for (int j = 0; j < K; ++j) vq += dfv[i] * Vf[i <= j ? up_idx(i, j, K) : up_idx(j, i, K)] * dfv[j];
   }
-  gTd = gfd + (double)gd;
-  dHd = vq + 2.0 * (double)cross + (double)hq + 2.0 * (double)cpl;
+  gTd = gfd + gd;
+  dHd = vq + 2.0 * cross + hh;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_backsub_slots(BackArgs<T> a) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < a.ne) backsub_slot<T>(a, e);
 }
 
 template <class T>
@@ -2180,10 +2186,11 @@ template <class T>
 void launch_backsub(Problem& P) {
   const Dims& d = P.d;
   BackArgs<T> a;
-  a.fslot_off = P.fslot_off; a.slot_ent = P.slot_ent; a.feat_plane_slot = P.feat_plane_slot; a.slot_type = P.slot_type;
-  a.V = P.featV; a.Vinv = P.featVinv; a.g = P.featg; a.x = P.x;
+  a.fslot_off = P.fslot_off; a.slot_ent = P.slot_ent; a.slot_feat = P.slot_feat; a.feat_plane_slot = P.feat_plane_slot;
+  a.slot_type = P.slot_type; a.V = P.featV; a.Vinv = P.featVinv; a.g = P.featg; a.x = P.x;
   a.W = (const T*)P.slotW; a.H = (const T*)P.slotH; a.G = (const T*)P.slotG; a.C = (const T*)P.slotC;
-  a.df = P.dfeat; a.np = d.np; a.nf = d.nf; a.S = P.S; a.red = P.red;
+  a.sv = (T*)P.slotBS; a.df = P.dfeat; a.np = d.np; a.nf = d.nf; a.ne = d.ne; a.S = P.S; a.red = P.red;
+  if (d.ne) { ++P.launches; k_backsub_slots<T><<<nblk(d.ne, 128), 128, 0, P.stream>>>(a); }
   ++P.launches;
   k_backsub<T><<<nblk(d.nf > 0 ? d.nf : 1, 128), 128, 0, P.stream>>>(a);
 }
@@ -2400,6 +2407,8 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
   __syncthreads();
   // ---- PCG, back-substitution and predicted decrease
   window_pcg<T, NT>(W, chunk_y, red2);
+  for (int64_t e = threadIdx.x; e < W.back.ne; e += NT) backsub_slot<T>(W.back, e);
+  __syncthreads();
   double g = 0, h = 0;
   for (int64_t f = threadIdx.x; f < W.nf; f += NT) {
     double gi = 0, hi = 0;
@@ -2501,6 +2510,7 @@ void fill_window_desc(Problem& P, void* out) {
   k.fslot_off = P.fslot_off; k.slot_ent = P.slot_ent; k.feat_plane_slot = P.feat_plane_slot; k.slot_type = P.slot_type;
   k.V = P.featV; k.Vinv = P.featVinv; k.g = P.featg; k.x = P.x; k.W = (const T*)P.slotW; k.H = (const T*)P.slotH;
   k.G = (const T*)P.slotG; k.C = (const T*)P.slotC; k.df = P.dfeat; k.np = d.np; k.nf = d.nf; k.S = P.S; k.red = P.red;
+  k.slot_feat = P.slot_feat; k.sv = (T*)P.slotBS; k.ne = d.ne;
   CandArgs& c = W.cand;
   c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
   CostArgs& co = W.cost;
