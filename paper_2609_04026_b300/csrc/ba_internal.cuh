@@ -158,6 +158,7 @@ struct ba_problem {
   // grid-path Schur work units: pair range, block, processing order (long units first), first unit of
   // every block, and the blocks whose units leave FP64 partials (48 per unit in upart)
   int32_t *un_se = nullptr, *un_blk = nullptr, *un_order = nullptr, *up_un = nullptr, *multi_blk = nullptr;
+  int32_t *un_desc = nullptr, *un_mflag = nullptr;   // per unit in processing order (4 ints; 1 int)
   double* upart = nullptr;
   int line_slot0 = 0;           // first slot of a line feature
   // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are

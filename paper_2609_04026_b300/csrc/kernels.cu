@@ -683,6 +683,8 @@ struct BlockArgs {
 template <class T>
 struct UnitArgs {
   const int32_t *un_se, *un_blk, *un_order, *up_un, *pair_a, *pair_b, *multi;
+  const int4* un_desc;      // per unit in processing order: first pair, end pair, block position, unit id
+  const int32_t* un_mflag;  // per unit in processing order: mirror position << 2 | written directly << 1 | diagonal
   const T *Z, *H, *B, *C;
   double* upart;   // 48 per unit: 36 S, 6 b, 6 diag(H)
   int64_t nun, nmulti;
@@ -858,17 +860,18 @@ __device__ __forceinline__ void load_rec(const T* src, T (&z)[24], bool line) {
 }
 
 template <class T>
-__device__ void unit_warp(const UnitArgs<T>& a, int w, char* smem, int lane) {
+__device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
   constexpr int ST = UnitSmem<T>::stride, RS = UnitSmem<T>::red;
   constexpr int CH = SW * (int)sizeof(T) / 16;   // 16-byte pieces of one Z record
   T* stage = reinterpret_cast<T*>(smem);
   int* sa_ = reinterpret_cast<int*>(smem + sizeof(T) * 32 * ST);
   int* sb_ = sa_ + 32;
-  const int s0 = a.un_se[2 * w], s1 = a.un_se[2 * w + 1];
-  const int u = a.un_blk[w];
-  const int row = a.fb.up_row[u], fpos = a.fb.up_full[u];
-  const bool diag = a.fb.col[fpos] == row;
-  const bool direct = !diag && a.up_un[u + 1] - a.up_un[u] == 1;   // written to S here
+  // the unit's descriptor (two independent loads instead of a chain through the block's arrays)
+  const int4 dsc = a.un_desc[g];
+  const int mf = a.un_mflag[g];
+  const int s0 = dsc.x, s1 = dsc.y, fpos = dsc.z, w = dsc.w;
+  const bool diag = (mf & 1) != 0;
+  const bool direct = (mf & 2) != 0;   // an off-diagonal block that fits this unit: written to S here
   T acc[36], bacc[6], hacc[6];
 #pragma unroll
   for (int e = 0; e < 36; ++e) acc[e] = 0;
@@ -926,7 +929,7 @@ __device__ void unit_warp(const UnitArgs<T>& a, int w, char* smem, int lane) {
     for (int i = 0; i < 6; ++i) { red[lane * RS + 36 + i] = bacc[i]; red[lane * RS + 42 + i] = hacc[i]; }
   __syncwarp();
   const int ne = diag ? 48 : 36;
-  const int mpos = direct ? a.fb.up_mirror[u] : 0;
+  const int mpos = mf >> 2;
   for (int e = lane; e < ne; e += 32) {
     PartSum<T> sm;
     for (int k = 0; k < 32; ++k) sm.add(red[k * RS + e]);
@@ -952,7 +955,7 @@ __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_units(UnitArgs<T
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g = blockIdx.x * (int64_t)NW + warp;
   if (g >= a.nun) return;   // the whole warp leaves together
-  unit_warp<T>(a, a.un_order[g], smem[warp], lane);
+  unit_warp<T>(a, (int)g, smem[warp], lane);
 }
 
 // ============================================================================
@@ -2092,6 +2095,7 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nc = d.nc; b.lambda = lambda;
   UnitArgs<T> un;
   un.un_se = P.un_se; un.un_blk = P.un_blk; un.un_order = P.un_order; un.up_un = P.up_un; un.multi = P.multi_blk;
+  un.un_desc = reinterpret_cast<const int4*>(P.un_desc); un.un_mflag = P.un_mflag;
   un.pair_a = P.pair_a; un.pair_b = P.pair_b; un.Z = (const T*)P.slotZ; un.H = (const T*)P.slotH;
   un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.upart = P.upart; un.nun = d.nun; un.nmulti = d.nmulti;
   un.line_slot0 = P.line_slot0; un.fb = b;

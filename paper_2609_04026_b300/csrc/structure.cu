@@ -592,6 +592,24 @@ __global__ void k_gather_obs(ObsGather a) {
   for (int t = 0; t < 4; ++t) a.meas_d[4 * j + t] = m[t];
 }
 
+// per unit in processing order: (first pair, end pair, block position, unit id) and
+// (mirror position << 2 | written directly << 1 | diagonal)
+__global__ void k_unit_desc(const int32_t* __restrict__ order, const int32_t* __restrict__ un_se,
+                            const int32_t* __restrict__ un_blk, const int32_t* __restrict__ up_un,
+                            const int32_t* __restrict__ up_row, const int32_t* __restrict__ up_full,
+                            const int32_t* __restrict__ up_mirror, const int32_t* __restrict__ pcol, int64_t nun,
+                            int4* __restrict__ desc, int32_t* __restrict__ mflag) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nun) return;
+  const int w = order[g];
+  const int u = un_blk[w];
+  const int fpos = up_full[u];
+  const bool diag = pcol[fpos] == up_row[u];
+  const bool direct = !diag && up_un[u + 1] - up_un[u] == 1;
+  desc[g] = make_int4(un_se[2 * w], un_se[2 * w + 1], fpos, w);
+  mflag[g] = (up_mirror[u] << 2) | (direct ? 2 : 0) | (diag ? 1 : 0);
+}
+
 struct Permute {
   const uint32_t* order;
   const int8_t* kind;
@@ -867,6 +885,13 @@ ba_status build_structure(Problem& P) {
       k_unit_key<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_se, nun, uk, (uint32_t*)P.un_order);
       if ((s = radix_sort(P, S, uk, (uint32_t*)P.un_order, uk2, uv2, nun, 8))) return s;
     }
+    if (nbp >= ((int64_t)1 << 29)) return fail(P, BA_ERR_ARG, "too many blocks in the reduced system");
+    P.un_desc = P.dnew<int32_t>(4 * nun);
+    P.un_mflag = P.dnew<int32_t>(nun);
+    if (!P.un_desc || !P.un_mflag) return oom();
+    if (nun)
+      k_unit_desc<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_order, P.un_se, P.un_blk, P.up_un, P.up_row, P.up_full,
+                                                        P.up_mirror, P.col, nun, (int4*)P.un_desc, P.un_mflag);
   }
 
   // ---- residual records in feature-major order
