@@ -219,23 +219,41 @@ static ba_status plan_pcg(ba_problem* p) {
   const bool mx = mixed(p);
   auto occ = [&](size_t smem) { return mx ? pcg_blocks_per_sm<float>(smem) : pcg_blocks_per_sm<double>(smem); };
   int per_sm = std::max(1, std::min(1, occ(48 * 1024)));
-  std::vector<int32_t> cta_row0;
+  // CTAs get contiguous runs of chunks of equal weight (32 blocks a chunk, 2 more for a chunk that opens
+  // a row: the row's sums and vector updates); a long row may be cut between CTAs
+  const int64_t Q = row_chunk0[d.na];
+  std::vector<int32_t> cta_part;
   size_t smem = 0;
   for (int attempt = 0; attempt < 8; ++attempt) {
-    int64_t G = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, d.na));
-    double total = 0;
-    for (int64_t r = 0; r < d.na; ++r) total += (rp[r + 1] - rp[r]) + 2.0;
-    cta_row0.assign(1, 0);
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, Q));
+    const double total = 32.0 * (double)Q + 2.0 * (double)d.na;
+    std::vector<int32_t> q0s(1, 0);
     double acc = 0;
-    for (int64_t r = 0; r < d.na; ++r) {
-      acc += (rp[r + 1] - rp[r]) + 2.0;
-      if ((int64_t)cta_row0.size() < G && acc >= total * (double)cta_row0.size() / (double)G && r + 1 < d.na)
-        cta_row0.push_back((int32_t)(r + 1));
+    int64_t row = 0;
+    for (int64_t q = 0; q < Q; ++q) {
+      while (row_chunk0[row + 1] <= q) ++row;
+      acc += 32.0 + (row_chunk0[row] == q ? 2.0 : 0.0);
+      if ((int64_t)q0s.size() < G && acc >= total * (double)q0s.size() / (double)G && q + 1 < Q)
+        q0s.push_back((int32_t)(q + 1));
     }
-    while ((int64_t)cta_row0.size() < G + 1) cta_row0.push_back((int32_t)d.na);
-    // shared memory of the row sums: one segment of 6 double-width sums per (warp, row it touches)
+    while ((int64_t)q0s.size() < G + 1) q0s.push_back((int32_t)Q);
+    cta_part.assign(4 * G, 0);
     int32_t maxrows = 1;
-    for (int64_t c = 0; c < G; ++c) maxrows = std::max(maxrows, cta_row0[c + 1] - cta_row0[c]);
+    int64_t rr = 0;
+    for (int64_t c = 0; c < G; ++c) {
+      const int32_t q0 = q0s[c], q1 = q0s[c + 1];
+      int32_t t0 = 0, t1 = 0;
+      if (q1 > q0) {
+        while (row_chunk0[rr + 1] <= q0) ++rr;
+        t0 = (int32_t)rr;
+        int64_t re = rr;
+        while (row_chunk0[re + 1] <= q1 - 1) ++re;
+        t1 = (int32_t)(re + 1);
+      }
+      cta_part[4 * c] = q0; cta_part[4 * c + 1] = q1; cta_part[4 * c + 2] = t0; cta_part[4 * c + 3] = t1;
+      maxrows = std::max(maxrows, t1 - t0);
+    }
+    // shared memory of the row sums: one segment of 6 double-width sums per (warp, row it touches)
     smem = sizeof(double) * 6 * ((size_t)maxrows + 16);
     if (smem > 72 * 1024) return set_err(p, BA_ERR_ARG, "reduced system too large or irregular for the PCG partition");
     if (mx) pcg_allow_smem<float>(smem); else pcg_allow_smem<double>(smem);
@@ -254,7 +272,9 @@ static ba_status plan_pcg(ba_problem* p) {
     CUDA_OR(p, cudaMemcpyAsync(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, p->stream));
     return BA_OK;
   };
-  if ((s = up(p->cta_row0, cta_row0))) return s;
+  p->pcg_carry = p->dnew<double>(6 * (int64_t)p->pcg_grid);
+  if (!p->pcg_carry) return set_err(p, BA_ERR_OOM, "device allocation failed");
+  if ((s = up(p->cta_part, cta_part))) return s;
   if ((s = up(p->row_chunk0, row_chunk0))) return s;
   if ((s = up(p->chunk_beg, chunk_beg))) return s;
   CUDA_OR(p, cudaStreamSynchronize(p->stream));

@@ -164,6 +164,11 @@ struct ba_problem {
   // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are
   // cut into chunks [chunk_beg[q], chunk_beg[q+1]) for q in [row_chunk0[r], row_chunk0[r+1])
   int32_t *cta_row0 = nullptr, *row_chunk0 = nullptr, *chunk_beg = nullptr;
+  // streaming PCG partition: CTA c multiplies chunks [q0, q1) touching block rows [t0, t1), stored as
+  // int4 {q0, q1, t0, t1}; a row cut by a CTA boundary belongs to the CTA holding its first chunk, and
+  // the other CTAs leave their partial sums of it in pcg_carry (6 doubles per CTA)
+  int32_t* cta_part = nullptr;
+  double* pcg_carry = nullptr;
   int pcg_grid = 0;
   size_t pcg_smem = 0;
   cudaError_t pcg_err = cudaSuccess;

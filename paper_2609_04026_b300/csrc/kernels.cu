@@ -1342,8 +1342,12 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
 // ----------------------------------------------------------------------------
 // Grid path of K5/K6: S streamed by the Tensor Memory Accelerator, CG in the Chronopoulos-Gear form.
 //
-// A CTA owns a contiguous range of block rows, hence a contiguous run of 32-block chunks of the padded
-// storage (one chunk = 32 whole blocks, 4.6 KB in float).  The run is split into NW contiguous pieces,
+// A CTA multiplies a contiguous run of 32-block chunks of the padded storage (one chunk = 32 whole blocks,
+// 4.6 KB in float), runs of equal length whatever the row lengths: a long row (a plane or a vanishing
+// point seen by many cameras) may be cut between CTAs.  A row belongs to the CTA holding its first chunk,
+// which updates its vector entries; a CTA whose run starts inside a row it does not own leaves its partial
+// product of that row in a carry slot, added by the owner after the grid barrier that follows the product
+// (the partial dot (w, u) needs no carry: it is a sum over the pieces).  The run is split into NW contiguous pieces,
 // one per warp; a warp keeps NBUF chunks of its piece in flight in shared memory, each fetched by two
 // bulk copies (cp.async.bulk: the values and the 32 column indices, completion counted on an mbarrier
 // per buffer), so the stream of S never waits on the products.  Every wait on an mbarrier is bounded: if a copy has not landed after a very long
@@ -1386,7 +1390,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int li
 template <class T>
 struct PcgStreamArgs {
   int64_t na;
-  const int32_t *col, *cta_row0, *row_chunk0, *chunk_beg;
+  const int32_t *col, *row_chunk0, *chunk_beg;
+  const int4* cta_part;   // per CTA {q0, q1, t0, t1}: chunks [q0, q1), touched block rows [t0, t1)
+  double* carry;          // per CTA: its partial w of its first row when another CTA owns that row
   const T *Sval, *Minv;
   const double* b;
   double *x, *r, *u, *p, *w, *s;
@@ -1457,8 +1463,11 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   __shared__ double cta_out[2];
   __shared__ double red3[NW][3];
   const int G = gridDim.x, c = blockIdx.x;
-  const int r0 = a.cta_row0[c], r1 = a.cta_row0[c + 1];
-  const int q0 = a.row_chunk0[r0], q1 = a.row_chunk0[r1];
+  const int4 pc = a.cta_part[c];
+  const int q0 = pc.x, q1 = pc.y;   // chunks [q0, q1)
+  const int r0 = pc.z, r1 = pc.w;   // block rows touched [r0, r1)
+  const int o0 = (r0 < r1 && a.row_chunk0[r0] != q0) ? r0 + 1 : r0;   // block rows owned [o0, r1)
+  const bool tail_cut = o0 < r1 && a.row_chunk0[r1] > q1;            // the last owned row continues
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // warp w multiplies the contiguous chunks [c0, c1) of the CTA's run; a lane accumulates its block
   // position over all chunks of one block row and the warp sums the lanes once per row it touches,
@@ -1561,11 +1570,12 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
         if (wfirst[w] <= r && r <= wlast[w])
 #pragma unroll
           for (int i = 0; i < 6; ++i) acc_add(y[i], seg[6 * (wbase[w] + r - wfirst[w]) + i]);
+      double* dst = r < o0 ? a.carry + 6 * (size_t)c : a.w + 6 * (size_t)r;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         const double yv = y[i].value();
-        a.w[6 * r + i] = yv;
-        v += yv * a.u[6 * r + i];
+        dst[i] = yv;
+        v += yv * __ldcg(&a.u[6 * r + i]);   // u of a row owned by another CTA: not through L1
       }
     }
     wu = v;
@@ -1580,9 +1590,22 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     }
     prefetched = false;
   };
+  // after the grid barrier that follows a product: the partial sums of the last owned row left by the
+  // following CTAs (every CTA whose run starts inside that row)
+  auto add_carries = [&]() {
+    if (!tail_cut || threadIdx.x >= 6) return;
+    const int row = r1 - 1;
+    double v = a.w[6 * (size_t)row + threadIdx.x];
+    for (int c2 = c + 1; c2 < G; ++c2) {
+      const int4 pn = a.cta_part[c2];
+      if (pn.x == pn.y || pn.z != row) break;
+      v += __ldcg(&a.carry[6 * (size_t)c2 + threadIdx.x]);
+    }
+    a.w[6 * (size_t)row + threadIdx.x] = v;
+  };
   auto precondition = [&](double& ru, double& rr_) {
     double v0 = 0, v1 = 0;
-    for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {   // one output per thread
+    for (int k = o0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {   // one output per thread
       const int row = k / 6, i = k - 6 * row;
       const T* M = a.Minv + (size_t)row * BS2 + 6 * i;
       const double* rv = a.r + 6 * (size_t)row;
@@ -1601,7 +1624,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   auto slot = [&](int par, int k) { return a.part + (size_t)par * 3 * G + (size_t)k * G; };
 
   // ---- start: x = 0, r = b, u = M^-1 r, w = S u
-  for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) { a.x[k] = 0; a.r[k] = a.b[k]; }
+  for (int k = o0 * 6 + threadIdx.x; k < r1 * 6; k += NT) { a.x[k] = 0; a.r[k] = a.b[k]; }
   __syncthreads();
   double ru, rrl, wu;
   precondition(ru, rrl);
@@ -1613,6 +1636,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   if (threadIdx.x == 0) slot(0, 2)[c] = cta_out[0];
   if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
   grid.sync();
+  add_carries();   // ordered before the vector updates by the barriers inside reduce3
   auto reduce3 = [&](int par) {   // the three global sums, formed identically in every CTA
     double s0 = 0, s1 = 0, s2 = 0;
     for (int g = threadIdx.x; g < G; g += NT) {
@@ -1646,7 +1670,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     // p = u + beta p, s = w + beta s (p = u, s = w on the first pass: p and s hold no values yet),
     // x += alpha p, r -= alpha s; then u = M^-1 r; partial (r, u), (r, r)
     const bool first = it == 0;
-    for (int k = r0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {
+    for (int k = o0 * 6 + threadIdx.x; k < r1 * 6; k += NT) {
       const double pk = first ? a.u[k] : a.u[k] + beta * a.p[k];
       const double sk = first ? a.w[k] : a.w[k] + beta * a.s[k];
       a.p[k] = pk;
@@ -1665,6 +1689,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     if (threadIdx.x == 0) slot(par, 2)[c] = cta_out[0];
     if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
     grid.sync();
+    add_carries();
     reduce3(par);
     const double gam_new = bc[0], delta = bc[2];
     rr = bc[1];
@@ -2147,7 +2172,8 @@ void launch_pcg(Problem& P) {
   const Dims& d = P.d;
   constexpr int NT = StreamCfg<T>::NT, NB = StreamCfg<T>::NBUF;
   PcgStreamArgs<T> a;
-  a.na = d.na; a.col = P.col; a.cta_row0 = P.cta_row0; a.row_chunk0 = P.row_chunk0; a.chunk_beg = P.chunk_beg;
+  a.na = d.na; a.col = P.col; a.row_chunk0 = P.row_chunk0; a.chunk_beg = P.chunk_beg;
+  a.cta_part = reinterpret_cast<const int4*>(P.cta_part); a.carry = P.pcg_carry;
   a.Sval = (const T*)P.Sval; a.Minv = (const T*)P.Minv; a.b = P.bvec;
   a.x = P.x; a.r = P.r; a.u = P.z; a.p = P.p; a.w = P.Ap; a.s = P.svec; a.part = P.red; a.S = P.S;
   a.uhl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
