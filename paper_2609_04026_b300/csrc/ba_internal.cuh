@@ -42,11 +42,16 @@ struct DBuf {
 // block sizes of the padded reduced system: every entity of A occupies a 6-wide block
 constexpr int BS = 6;
 constexpr int BS2 = BS * BS;
-// per-slot record strides (in elements of the slot type)
+// per-slot record strides (in elements of the slot type), padded to 16-byte multiples so that the
+// linearisation writes whole records with 16-byte stores
 constexpr int SW = 24;  // W^T (k x 6), k = 3 (point) or 4 (line)
-constexpr int SH = 21;  // upper triangle of the direct 6x6 block J_a^T w J_a
-constexpr int SG = 6;   // J_a^T w r
-constexpr int SC = 18;  // camera slot: J_cam^T w J_plane (6 x 3)
+// H and G share one record of SH values: the upper triangle of the direct 6x6 block J_a^T w J_a (21
+// values), then J_a^T w r (6 values) at offset HG_G, then one pad; G is addressed as a view at that offset
+constexpr int SH = 28;
+constexpr int HG_G = 21;
+constexpr int SG = SH;
+constexpr int SB = 6;   // the whitened per-slot b part
+constexpr int SC = 20;  // camera slot: J_cam^T w J_plane (6 x 3, 18 values)
 
 enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
 

@@ -244,6 +244,26 @@ struct LinArgs {
   LossW loss;
 };
 
+// N values to a 16-byte aligned destination with 16-byte stores (a thread writes a whole record: one
+// store instruction of a warp then carries 16 bytes per lane instead of 4)
+template <class T, int N>
+__device__ __forceinline__ void store16(T* __restrict__ dst, const T* src) {
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int NV = N / V * V;
+#pragma unroll
+  for (int i = 0; i < NV; i += V) {
+    if constexpr (sizeof(T) == 4)
+      *reinterpret_cast<float4*>(dst + i) = make_float4(src[i], src[i + 1], src[i + 2], src[i + 3]);
+    else
+      *reinterpret_cast<double2*>(dst + i) = make_double2(src[i], src[i + 1]);
+  }
+  if constexpr (sizeof(T) == 4 && N - NV >= 2)
+    *reinterpret_cast<float2*>(dst + NV) = make_float2(src[NV], src[NV + 1]);
+  constexpr int NT2 = (sizeof(T) == 4 && N - NV >= 2) ? NV + 2 : NV;
+#pragma unroll
+  for (int i = NT2; i < N; ++i) dst[i] = src[i];
+}
+
 template <class T, int KF>
 __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
@@ -284,23 +304,16 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   }
 
   auto flush = [&](int e) {
-    T* W = a.W + (size_t)e * SW;
+    store16<T, KF * 6>(a.W + (size_t)e * SW, &Wc[0][0]);
+    T hg[SH];   // H (21), G (6), pad
 #pragma unroll
-    for (int i = 0; i < KF; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) W[i * 6 + j] = Wc[i][j];
-    T* H = a.H + (size_t)e * SH;
-#pragma unroll
-    for (int i = 0; i < 21; ++i) H[i] = Hc[i];
-    T* G = a.G + (size_t)e * SG;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) G[i] = Gc[i];
+    for (int i = 0; i < SH; ++i) hg[i] = i < HG_G ? Hc[i] : i < HG_G + 6 ? Gc[i - HG_G] : T(0);
+    store16<T, SH>(a.H + (size_t)e * SH, hg);
     if (plane_slot >= 0) {
-      T* C = a.C + (size_t)e * SC;
+      T cb[SC];
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) C[i * 3 + j] = Cc[i][j];
+      for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? Cc[i / 3][i % 3] : T(0);
+      store16<T, SC>(a.C + (size_t)e * SC, cb);
     }
   };
   auto zero_cam = [&]() {
@@ -428,14 +441,22 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   if (cur >= 0) flush(cur);
   // group slots, padded to the 6-wide block of the reduced system
   auto put_group = [&](int e, int nd, const T* Wg, const T* Hg, const T* Gg) {
-    T* W = a.W + (size_t)e * SW;
+    T wb[KF * 6], hg[SH];   // W; H (21), G (6), pad
+#pragma unroll
     for (int i = 0; i < KF; ++i)
-      for (int j = 0; j < 6; ++j) W[i * 6 + j] = j < nd ? Wg[i * nd + j] : T(0);
-    T* H = a.H + (size_t)e * SH;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) wb[i * 6 + j] = j < nd ? Wg[i * nd + j] : T(0);
+#pragma unroll
+    for (int i = 0; i < SH; ++i) hg[i] = T(0);
+#pragma unroll
     for (int i = 0; i < 6; ++i)
-      for (int j = i; j < 6; ++j) H[up_idx(i, j, 6)] = (j < nd) ? Hg[up_idx(i, j, nd)] : T(0);
-    T* G = a.G + (size_t)e * SG;
-    for (int i = 0; i < 6; ++i) G[i] = i < nd ? Gg[i] : T(0);
+#pragma unroll
+      for (int j = i; j < 6; ++j)
+        if (j < nd) hg[up_idx(i, j, 6)] = Hg[up_idx(i, j, nd)];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) hg[HG_G + i] = i < nd ? Gg[i] : T(0);
+    store16<T, KF * 6>(a.W + (size_t)e * SW, wb);
+    store16<T, SH>(a.H + (size_t)e * SH, hg);
   };
   if (ps < 0) ps = plane_slot;  // a plane slot whose residuals were all invalid
   if (ps >= 0) put_group(ps, 3, &Wp[0][0], Hp, Gp);
@@ -447,12 +468,13 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
     }
     if (vs >= 0) put_group(vs, 2, &Wv[0][0], Hv, Gv);
   }
-  double* Vo = a.V + 10 * f;
+  double vb[NV], gbf[KF];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) Vo[i] = (double)V[i];
-  double* go = a.g + 4 * f;
+  for (int i = 0; i < NV; ++i) vb[i] = (double)V[i];
 #pragma unroll
-  for (int i = 0; i < KF; ++i) go[i] = (double)gf[i];
+  for (int i = 0; i < KF; ++i) gbf[i] = (double)gf[i];
+  store16<double, NV>(a.V + 10 * f, vb);
+  store16<double, KF>(a.g + 4 * f, gbf);
 }
 
 template <class T, int KF>
@@ -592,7 +614,7 @@ __device__ __forceinline__ void whiten_record(const InvArgs<T>& a, int64_t e, co
 #pragma unroll
   for (int i = 0; i < K * 6; ++i) Z[i] = z[i];
   const T* G = a.G + (size_t)e * SG;
-  T* B = a.B + (size_t)e * SG;
+  T* B = a.B + (size_t)e * SB;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     T s = -G[j];
@@ -899,7 +921,7 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
       load_rec(stage + lane * ST + SW, zb, line);
       if (diag) {
         const T* H = a.H + (size_t)ea * SH;
-        const T* Bv = a.B + (size_t)ea * SG;
+        const T* Bv = a.B + (size_t)ea * SB;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
           bacc[i] += Bv[i];
