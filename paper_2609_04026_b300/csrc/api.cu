@@ -296,8 +296,8 @@ static ba_status freeze(ba_problem* p) {
   bool ok = true;
   ok &= A(p->slotW, T * SW * (size_t)d.ne);
   ok &= A(p->slotZ, T * SW * (size_t)d.ne);
-  ok &= A(p->slotH, T * SH * (size_t)d.ne);
-  p->slotG = p->slotH ? (void*)((char*)p->slotH + T * HG_G) : nullptr;   // a view into the H|G records
+  ok &= A(p->slotG, T * SG * (size_t)d.ne);
+  p->slotH = p->slotG ? (void*)((char*)p->slotG + T * HG_H) : nullptr;   // a view into the G|H records
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
   ok &= A(p->slotBS, T * 6 * (size_t)d.ne);

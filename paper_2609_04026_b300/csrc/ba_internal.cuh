@@ -45,11 +45,12 @@ constexpr int BS2 = BS * BS;
 // per-slot record strides (in elements of the slot type), padded to 16-byte multiples so that the
 // linearisation writes whole records with 16-byte stores
 constexpr int SW = 24;  // W^T (k x 6), k = 3 (point) or 4 (line)
-// H and G share one record of SH values: the upper triangle of the direct 6x6 block J_a^T w J_a (21
-// values), then J_a^T w r (6 values) at offset HG_G, then one pad; G is addressed as a view at that offset
-constexpr int SH = 28;
-constexpr int HG_G = 21;
-constexpr int SG = SH;
+// G and H share one 16-byte aligned record of SG values: J_a^T w r (6 values), then the upper triangle of
+// the direct 6x6 block J_a^T w J_a (21 values) at offset HG_H, then one pad; H is addressed as a view at
+// that offset with the same stride
+constexpr int SG = 28;
+constexpr int HG_H = 6;
+constexpr int SH = SG;
 constexpr int SB = 6;   // the whitened per-slot b part
 constexpr int SC = 20;  // camera slot: J_cam^T w J_plane (6 x 3, 18 values)
 

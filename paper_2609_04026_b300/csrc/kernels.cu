@@ -229,6 +229,8 @@ __global__ void k_convert(int64_t n, const double* __restrict__ a, float* __rest
 struct LossW {
   double w[7];
   double a2[7];
+  double inv_a2[7];   // 1 / a^2: the scaled squared norm s / a^2 as a product
+  double half_wa2[7]; // w a^2 / 2, the factor of the Cauchy cost
 };
 
 template <class T>
@@ -259,6 +261,30 @@ __device__ __forceinline__ void store16(T* __restrict__ dst, const T* src) {
   }
   if constexpr (sizeof(T) == 4 && N - NV >= 2)
     *reinterpret_cast<float2*>(dst + NV) = make_float2(src[NV], src[NV + 1]);
+  constexpr int NT2 = (sizeof(T) == 4 && N - NV >= 2) ? NV + 2 : NV;
+#pragma unroll
+  for (int i = NT2; i < N; ++i) dst[i] = src[i];
+}
+
+// N values from a 16-byte aligned record with 16-byte loads
+template <class T, int N>
+__device__ __forceinline__ void load16(const T* __restrict__ src, T* dst) {
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int NV = N / V * V;
+#pragma unroll
+  for (int i = 0; i < NV; i += V) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(src + i);
+      dst[i] = t.x; dst[i + 1] = t.y; dst[i + 2] = t.z; dst[i + 3] = t.w;
+    } else {
+      const double2 t = *reinterpret_cast<const double2*>(src + i);
+      dst[i] = t.x; dst[i + 1] = t.y;
+    }
+  }
+  if constexpr (sizeof(T) == 4 && N - NV >= 2) {
+    const float2 t = *reinterpret_cast<const float2*>(src + NV);
+    dst[NV] = t.x; dst[NV + 1] = t.y;
+  }
   constexpr int NT2 = (sizeof(T) == 4 && N - NV >= 2) ? NV + 2 : NV;
 #pragma unroll
   for (int i = NT2; i < N; ++i) dst[i] = src[i];
@@ -305,10 +331,10 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 
   auto flush = [&](int e) {
     store16<T, KF * 6>(a.W + (size_t)e * SW, &Wc[0][0]);
-    T hg[SH];   // H (21), G (6), pad
+    T gh[SG];   // G (6), H (21), pad
 #pragma unroll
-    for (int i = 0; i < SH; ++i) hg[i] = i < HG_G ? Hc[i] : i < HG_G + 6 ? Gc[i - HG_G] : T(0);
-    store16<T, SH>(a.H + (size_t)e * SH, hg);
+    for (int i = 0; i < SG; ++i) gh[i] = i < HG_H ? Gc[i] : i < HG_H + 21 ? Hc[i - HG_H] : T(0);
+    store16<T, SG>(a.G + (size_t)e * SG, gh);
     if (plane_slot >= 0) {
       T cb[SC];
 #pragma unroll
@@ -373,7 +399,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (i < rd) s += o.r[i] * o.r[i];
-    const T om = (T)a.loss.w[kind] / (T(1) + s / (T)a.loss.a2[kind]);
+    const T om = (T)a.loss.w[kind] / (T(1) + s * (T)a.loss.inv_a2[kind]);
     if (has_plane) ps = a.rslot_g[rr];
     if (has_vp) vs = a.rslot_g[rr];
     const bool camslot = sc >= 0;
@@ -441,22 +467,22 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   if (cur >= 0) flush(cur);
   // group slots, padded to the 6-wide block of the reduced system
   auto put_group = [&](int e, int nd, const T* Wg, const T* Hg, const T* Gg) {
-    T wb[KF * 6], hg[SH];   // W; H (21), G (6), pad
+    T wb[KF * 6], gh[SG];   // W; G (6), H (21), pad
 #pragma unroll
     for (int i = 0; i < KF; ++i)
 #pragma unroll
       for (int j = 0; j < 6; ++j) wb[i * 6 + j] = j < nd ? Wg[i * nd + j] : T(0);
 #pragma unroll
-    for (int i = 0; i < SH; ++i) hg[i] = T(0);
+    for (int i = 0; i < SG; ++i) gh[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gh[i] = i < nd ? Gg[i] : T(0);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int j = i; j < 6; ++j)
-        if (j < nd) hg[up_idx(i, j, 6)] = Hg[up_idx(i, j, nd)];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) hg[HG_G + i] = i < nd ? Gg[i] : T(0);
+        if (j < nd) gh[HG_H + up_idx(i, j, 6)] = Hg[up_idx(i, j, nd)];
     store16<T, KF * 6>(a.W + (size_t)e * SW, wb);
-    store16<T, SH>(a.H + (size_t)e * SH, hg);
+    store16<T, SG>(a.G + (size_t)e * SG, gh);
   };
   if (ps < 0) ps = plane_slot;  // a plane slot whose residuals were all invalid
   if (ps >= 0) put_group(ps, 3, &Wp[0][0], Hp, Gp);
@@ -604,16 +630,12 @@ __device__ __forceinline__ void split_L(const double (&Li)[K][K], T (&Lh)[K][K],
 template <class T, int K>
 __device__ __forceinline__ void whiten_record(const InvArgs<T>& a, int64_t e, const double (&Li)[K][K], const T (&Lh)[K][K],
                                               const T (&Ll)[K][K], const T (&ut)[K]) {
-  const T* W = a.W + (size_t)e * SW;
-  T w[K * 6], z[K * 6];
-#pragma unroll
-  for (int i = 0; i < K * 6; ++i) w[i] = W[i];
+  T w[K * 6], z[K * 6], G[6];
+  load16<T, K * 6>(a.W + (size_t)e * SW, w);
   if constexpr (sizeof(T) == 8) whiten_slot<K>(Li, (const double*)w, (double*)z);
   else whiten_slot<K>(Lh, Ll, w, z);
-  T* Z = a.Z + (size_t)e * SW;
-#pragma unroll
-  for (int i = 0; i < K * 6; ++i) Z[i] = z[i];
-  const T* G = a.G + (size_t)e * SG;
+  store16<T, K * 6>(a.Z + (size_t)e * SW, z);
+  load16<T, 6>(a.G + (size_t)e * SG, G);
   T* B = a.B + (size_t)e * SB;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -1760,18 +1782,26 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
   T dv[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
-  const T* W = a.W + (size_t)e * SW;
+  T W[24];
+  if (K == 3) {   // a point's W has three rows
+    load16<T, 18>(a.W + (size_t)e * SW, W);
+#pragma unroll
+    for (int j = 18; j < 24; ++j) W[j] = 0;
+  } else {
+    load16<T, 24>(a.W + (size_t)e * SW, W);
+  }
   T* so = a.sv + (size_t)e * 6;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     T s = 0;
-    if (i < K)   // a point's W has three rows
 #pragma unroll
-      for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
+    for (int j = 0; j < 6; ++j) s += W[i * 6 + j] * dv[j];
     so[i] = s;
   }
-  const T* G = a.G + (size_t)e * SG;
-  const T* H = a.H + (size_t)e * SH;
+  T gh[SG];   // G (6), H (21), pad
+  load16<T, SG>(a.G + (size_t)e * SG, gh);
+  const T* G = gh;
+  const T* H = gh + HG_H;
   T gd = 0, hq = 0;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -1786,7 +1816,8 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
   if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {   // camera-plane direct block of a plane feature
     const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
     const T dpl[3] = {(T)dp[0], (T)dp[1], (T)dp[2]};
-    const T* Cm = a.C + (size_t)e * SC;
+    T Cm[18];
+    load16<T, 18>(a.C + (size_t)e * SC, Cm);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -2022,8 +2053,7 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
     if (o.valid) {
       double s = 0;
       for (int k = 0; k < rd; ++k) s += o.r[k] * o.r[k];
-      double a2 = a.loss.a2[kind];
-      double e = 0.5 * a.loss.w[kind] * a2 * log1p(s / a2);
+      const double e = a.loss.half_wa2[kind] * log1p(s * a.loss.inv_a2[kind]);
       v[0] = e;
       v[1] = kind == R_VP ? 0.0 : e;
     }
@@ -2081,6 +2111,8 @@ static LossW make_loss(const ba_options& o) {
     L.w[k] = w[k];
     double s = (k == R_VP) ? o.cauchy_vp : o.cauchy_px;
     L.a2[k] = s * s;
+    L.inv_a2[k] = 1.0 / L.a2[k];
+    L.half_wa2[k] = 0.5 * w[k] * L.a2[k];
   }
   return L;
 }
