@@ -76,6 +76,7 @@ struct Dims {
   int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
   int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0;  // nbf stored blocks, nbp padded
   int64_t nun = 0, nmulti = 0;   // Schur work units of the grid path; blocks split over several units
+  int64_t nun_main = 0, npack = 0;   // units a warp takes alone (the rest are packed), and the packs
   int64_t n_points_res_end = 0;  // residuals of points are [0, this); lines follow
 };
 
@@ -165,6 +166,10 @@ struct ba_problem {
   // every block, and the blocks whose units leave FP64 partials (48 per unit in upart)
   int32_t *un_se = nullptr, *un_blk = nullptr, *un_order = nullptr, *up_un = nullptr, *multi_blk = nullptr;
   int32_t *un_desc = nullptr, *un_mflag = nullptr;   // per unit in processing order (4 ints; 1 int)
+  // packs of small units (a whole off-diagonal block of at most PACK_MAX pairs each, not camera-plane):
+  // the units [nun_main, nun) of the processing order, several to a warp; per pack int4
+  // {first unit in processing order, units, first pair, pairs}, the pairs contiguous
+  int32_t* pk_desc = nullptr;
   double* upart = nullptr;
   int line_slot0 = 0;           // first slot of a line feature
   // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are

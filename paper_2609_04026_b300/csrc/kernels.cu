@@ -729,9 +729,10 @@ struct UnitArgs {
   const int32_t *un_se, *un_blk, *un_order, *up_un, *pair_a, *pair_b, *multi;
   const int4* un_desc;      // per unit in processing order: first pair, end pair, block position, unit id
   const int32_t* un_mflag;  // per unit in processing order: mirror position << 2 | written directly << 1 | diagonal
+  const int4* pk_desc;      // per pack of small units: first unit (processing order), units, first pair, pairs
   const T *Z, *H, *B, *C;
   double* upart;   // 48 per unit: 36 S, 6 b, 6 diag(H)
-  int64_t nun, nmulti;
+  int64_t nun, nmulti, nun_main, npack;
   int line_slot0;
   BlockArgs<T> fb;
 };
@@ -998,8 +999,84 @@ __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_units(UnitArgs<T
   __shared__ __align__(16) char smem[NW][UnitSmem<T>::bytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g = blockIdx.x * (int64_t)NW + warp;
-  if (g >= a.nun) return;   // the whole warp leaves together
+  if (g >= a.nun_main) return;   // the whole warp leaves together
   unit_warp<T>(a, (int)g, smem[warp], lane);
+}
+
+// Small units, several to a warp: a pack holds whole off-diagonal blocks of a few pairs each (not
+// camera-plane blocks), their pairs contiguous, one pair per lane.  Lane l forms the term of pair l, and
+// each block's 36 entries are summed over its own lanes in lane order, then written to S with the mirror.
+// A lane's term and the order of the sums are those of unit_warp for the same block (which adds only
+// zeros beyond its pairs), so both paths give identical blocks; a warp no longer spends a stage and a
+// 32-lane sum on a block of a handful of pairs.
+template <class T>
+struct PackSmem {
+  static constexpr int stride = UnitSmem<T>::stride;
+  // per warp, a multiple of 16 bytes so that every warp's stage is 16-byte aligned (cp.async, 16-byte loads)
+  static constexpr size_t bytes = (sizeof(T) * 32 * stride + sizeof(int) * (33 + 32 + 32 + 32 + 32) + 15) / 16 * 16;
+  static_assert(sizeof(T) * 32 * stride % 16 == 0, "stage area must keep 16-byte alignment");
+};
+static_assert(PackSmem<float>::bytes % 16 == 0 && PackSmem<double>::bytes % 16 == 0, "warp areas must be 16-byte aligned");
+static_assert(UnitSmem<float>::bytes % 16 == 0 && UnitSmem<double>::bytes % 16 == 0, "warp areas must be 16-byte aligned");
+
+template <class T>
+__global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_packs(UnitArgs<T> a) {
+  constexpr int NW = UnitWarps<T>::n;
+  constexpr int ST = UnitSmem<T>::stride, RS = UnitSmem<T>::red;
+  constexpr int CH = SW * (int)sizeof(T) / 16;
+  __shared__ __align__(16) char smem[NW][PackSmem<T>::bytes];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t pk = blockIdx.x * (int64_t)NW + warp;
+  if (pk >= a.npack) return;   // the whole warp leaves together
+  T* stage = reinterpret_cast<T*>(smem[warp]);
+  int* seg = reinterpret_cast<int*>(smem[warp] + sizeof(T) * 32 * ST);   // first lane of each block (+ end)
+  int* fp = seg + 33;   // block position
+  int* mp = fp + 32;    // mirror position
+  int* sa_ = mp + 32;
+  int* sb_ = sa_ + 32;
+  const int4 pd = a.pk_desc[pk];
+  const int nu = pd.y, p0 = pd.z, n = pd.w;
+  if (lane < nu) {
+    const int4 dd = a.un_desc[pd.x + lane];
+    seg[lane] = dd.x - p0;
+    fp[lane] = dd.z;
+    mp[lane] = a.un_mflag[pd.x + lane] >> 2;
+  }
+  if (lane == 0) seg[nu] = n;
+  if (lane < n) { sa_[lane] = a.pair_a[p0 + lane]; sb_[lane] = a.pair_b[p0 + lane]; }
+  __syncwarp();
+  for (int t = lane; t < n * 2 * CH; t += 32) {
+    const int p = t / (2 * CH), r = t - p * 2 * CH;
+    const int which = r / CH, ch = r - which * CH;
+    const int e = which == 0 ? sa_[p] : sb_[p];
+    cp_async16(reinterpret_cast<char*>(stage + p * ST + which * SW) + 16 * ch,
+               reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * ch);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  T acc[36];
+  if (lane < n) {
+    const bool line = sa_[lane] >= a.line_slot0;
+    T za[24], zb[24];
+    load_rec(stage + lane * ST, za, line);
+    load_rec(stage + lane * ST + SW, zb, line);
+#pragma unroll
+    for (int e = 0; e < 36; ++e) acc[e] = T(0) - pair_dot(za, zb, e / 6, e % 6, line);
+  }
+  __syncwarp();   // the staged records are overwritten by the terms
+  T* red = stage;
+  if (lane < n)
+#pragma unroll
+    for (int e = 0; e < 36; ++e) red[lane * RS + e] = acc[e];
+  __syncwarp();
+  for (int t = lane; t < nu * 36; t += 32) {
+    const int i = t / 36, e = t - 36 * i;
+    PartSum<T> sm;
+    for (int k = seg[i]; k < seg[i + 1]; ++k) sm.add(red[k * RS + e]);
+    const T v = (T)sm.rounded();
+    a.fb.Sval[s_idx(fp[i], e)] = v;
+    a.fb.Sval[s_idx(mp[i], (e % 6) * 6 + e / 6)] = v;
+  }
 }
 
 // ============================================================================
@@ -2177,6 +2254,7 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   un.un_desc = reinterpret_cast<const int4*>(P.un_desc); un.un_mflag = P.un_mflag;
   un.pair_a = P.pair_a; un.pair_b = P.pair_b; un.Z = (const T*)P.slotZ; un.H = (const T*)P.slotH;
   un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.upart = P.upart; un.nun = d.nun; un.nmulti = d.nmulti;
+  un.pk_desc = reinterpret_cast<const int4*>(P.pk_desc); un.nun_main = d.nun_main; un.npack = d.npack;
   un.line_slot0 = P.line_slot0; un.fb = b;
   return un;
 }
@@ -2185,10 +2263,14 @@ template <class T>
 void launch_schur(Problem& P, double lambda) {
   const Dims& d = P.d;
   const UnitArgs<T> un = unit_args<T>(P, lambda);
-  if (d.nun) {
+  constexpr int NW = UnitWarps<T>::n;
+  if (d.nun_main) {
     ++P.launches;
-    constexpr int NW = UnitWarps<T>::n;
-    k_schur_units<T><<<nblk(d.nun, NW), NW * 32, 0, P.stream>>>(un);
+    k_schur_units<T><<<nblk(d.nun_main, NW), NW * 32, 0, P.stream>>>(un);
+  }
+  if (d.npack) {
+    ++P.launches;
+    k_schur_packs<T><<<nblk(d.npack, NW), NW * 32, 0, P.stream>>>(un);
   }
   if (P.ev[3]) cudaEventRecord(P.ev[3], P.stream);
   if (d.nmulti) { ++P.launches; k_schur_finish<T><<<nblk(d.nmulti, 128), 128, 0, P.stream>>>(un); }

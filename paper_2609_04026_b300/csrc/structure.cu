@@ -34,6 +34,7 @@ namespace ba {
 
 static constexpr int UNIT_MAX = 1024;     // pairs per Schur work unit
 static constexpr int UNIT_LONG = 128;     // units with more pairs are scheduled first
+static constexpr int PACK_MAX = 32;       // pairs of a pack of small units (one per lane)
 
 static ba_status fail(Problem& P, ba_status s, const std::string& m) {
   P.err = m;
@@ -527,11 +528,21 @@ __global__ void k_multi_fill(const int64_t* __restrict__ flag, const int64_t* __
   if (u < nbu && flag[u]) list[off[u]] = (int32_t)u;
 }
 
-__global__ void k_unit_key(const int32_t* __restrict__ un_se, int64_t nun, uint32_t* __restrict__ key,
+// processing class of a unit: 0 long (scheduled first), 1 other, 2 packable (a whole off-diagonal block
+// of 1..PACK_MAX pairs, not a camera-plane block: its sums go straight to S)
+__global__ void k_unit_key(const int32_t* __restrict__ un_se, const int32_t* __restrict__ un_blk,
+                           const int32_t* __restrict__ up_un, const int32_t* __restrict__ up_row,
+                           const int32_t* __restrict__ up_full, const int32_t* __restrict__ pcol,
+                           const int32_t* __restrict__ pair_b, int64_t nun, uint32_t* __restrict__ key,
                            uint32_t* __restrict__ val) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (w < nun) {
-    key[w] = un_se[2 * w + 1] - un_se[2 * w] > UNIT_LONG ? 0u : 1u;
+    const int n = un_se[2 * w + 1] - un_se[2 * w];
+    const int u = un_blk[w];
+    const bool diag = pcol[up_full[u]] == up_row[u];
+    const bool single = up_un[u + 1] - up_un[u] == 1;
+    const bool packable = !diag && single && n >= 1 && n <= PACK_MAX && pair_b[un_se[2 * w]] >= 0;
+    key[w] = n > UNIT_LONG ? 0u : (packable ? 2u : 1u);
     val[w] = (uint32_t)w;
   }
 }
@@ -882,7 +893,8 @@ ba_status build_structure(Problem& P) {
     uint32_t *uk = S.get<uint32_t>(nun), *uk2 = S.get<uint32_t>(nun), *uv2 = S.get<uint32_t>(nun);
     if (!uk || !uk2 || !uv2) return oom();
     if (nun) {
-      k_unit_key<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_se, nun, uk, (uint32_t*)P.un_order);
+      k_unit_key<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_se, P.un_blk, P.up_un, P.up_row, P.up_full, P.col,
+                                                       P.pair_b, nun, uk, (uint32_t*)P.un_order);
       if ((s = radix_sort(P, S, uk, (uint32_t*)P.un_order, uk2, uv2, nun, 8))) return s;
     }
     if (nbp >= ((int64_t)1 << 29)) return fail(P, BA_ERR_ARG, "too many blocks in the reduced system");
@@ -892,6 +904,37 @@ ba_status build_structure(Problem& P) {
     if (nun)
       k_unit_desc<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_order, P.un_se, P.un_blk, P.up_un, P.up_row, P.up_full,
                                                         P.up_mirror, P.col, nun, (int4*)P.un_desc, P.un_mflag);
+    // packs: the packable units (the tail of the processing order, in block order) taken greedily while
+    // their pairs stay contiguous and number at most PACK_MAX
+    d.nun_main = nun;
+    d.npack = 0;
+    if (nun) {
+      std::vector<uint32_t> hk(nun);
+      CU(cudaMemcpyAsync(hk.data(), uk, sizeof(uint32_t) * nun, cudaMemcpyDeviceToHost, P.stream));
+      CU(cudaStreamSynchronize(P.stream));
+      const int64_t nmain = std::lower_bound(hk.begin(), hk.end(), 2u) - hk.begin();
+      const int64_t nsm = nun - nmain;
+      if (nsm > 0) {
+        std::vector<int32_t> hd(4 * nsm);
+        CU(cudaMemcpyAsync(hd.data(), P.un_desc + 4 * nmain, sizeof(int32_t) * hd.size(), cudaMemcpyDeviceToHost,
+                           P.stream));
+        CU(cudaStreamSynchronize(P.stream));
+        std::vector<int32_t> pk;
+        for (int64_t i = 0; i < nsm;) {
+          const int64_t i0 = i;
+          const int32_t p0 = hd[4 * i];
+          int32_t end = hd[4 * i + 1];
+          for (++i; i < nsm && hd[4 * i] == end && hd[4 * i + 1] - p0 <= PACK_MAX; ++i) end = hd[4 * i + 1];
+          pk.insert(pk.end(), {(int32_t)(nmain + i0), (int32_t)(i - i0), p0, end - p0});
+        }
+        P.pk_desc = P.dnew<int32_t>((int64_t)pk.size());
+        if (!P.pk_desc) return oom();
+        CU(cudaMemcpyAsync(P.pk_desc, pk.data(), sizeof(int32_t) * pk.size(), cudaMemcpyHostToDevice, P.stream));
+        CU(cudaStreamSynchronize(P.stream));
+        d.nun_main = nmain;
+        d.npack = (int64_t)pk.size() / 4;
+      }
+    }
   }
 
   // ---- residual records in feature-major order
