@@ -272,6 +272,15 @@ static ba_status plan_pcg(ba_problem* p) {
     CUDA_OR(p, cudaMemcpyAsync(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, p->stream));
     return BA_OK;
   };
+  {
+    // share of S kept in L2 across PCG iterations (fetched evict_last; the rest streams evict_first): about
+    // half of the 126 MB L2, so that the vectors and the other kernels keep their share.  No persisting
+    // set-aside is configured: reserving L2 for S slowed the linearisation and the whitening more than it
+    // helped the PCG.
+    constexpr double kKeepBytes = 60.0 * 1048576.0;
+    const double sbytes = (double)Q * 32.0 * BS2 * (mx ? sizeof(float) : sizeof(double)) + (double)Q * 128.0;
+    p->pcg_keep_frac = sbytes > 0 ? (float)std::min(1.0, kKeepBytes / sbytes) : 0.f;
+  }
   p->pcg_carry = p->dnew<double>(6 * (int64_t)p->pcg_grid);
   if (!p->pcg_carry) return set_err(p, BA_ERR_OOM, "device allocation failed");
   if ((s = up(p->cta_part, cta_part))) return s;

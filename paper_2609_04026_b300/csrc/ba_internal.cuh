@@ -180,6 +180,7 @@ struct ba_problem {
   // the other CTAs leave their partial sums of it in pcg_carry (6 doubles per CTA)
   int32_t* cta_part = nullptr;
   double* pcg_carry = nullptr;
+  float pcg_keep_frac = 0.f;   // fraction of S the PCG keeps resident in L2 across iterations
   int pcg_grid = 0;
   size_t pcg_smem = 0;
   cudaError_t pcg_err = cudaSuccess;

@@ -1493,6 +1493,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// the same copy with an L2 eviction-priority policy (createpolicy)
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
 // true once the barrier's phase with the given parity has completed; false after `limit` polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit) {
   const unsigned a = smem_u32(bar);
@@ -1522,6 +1540,7 @@ struct PcgStreamArgs {
   DevScalars* S;
   double tol;
   int max_iters;
+  float keep_frac;   // fraction of every warp's chunks fetched with L2 evict_last (kept across iterations)
 };
 
 template <class T>
@@ -1596,6 +1615,10 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   const int ntot = q1 - q0;
   const int c0 = q0 + (int)((int64_t)ntot * warp / NW), c1 = q0 + (int)((int64_t)ntot * (warp + 1) / NW);
   const int nk = c1 - c0;
+  // S does not fit in L2: the first keep_frac of the warp's chunks are fetched evict_last so that they stay
+  // resident from one iteration to the next, the rest evict_first so that they do not displace them
+  const int nkeep = (int)((float)nk * a.keep_frac);
+  const uint64_t pol_keep = l2_evict_last(), pol_stream = l2_evict_first();
   auto row_of = [&](int q) {   // the block row holding chunk q (r0 <= row < r1)
     int lo = r0, hi = r1 - 1;
     while (lo < hi) {
@@ -1630,8 +1653,10 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
       const int bi = k % NBUF;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_expect_tx(&bars[warp][bi], CHB + 128u);
-      bulk_g2s(stage + ((size_t)warp * NBUF + bi) * (BS2 * 32), a.Sval + s_idx(a.chunk_beg[q], 0), CHB, &bars[warp][bi]);
-      bulk_g2s(&cols[warp][bi][0], a.col + a.chunk_beg[q], 128u, &bars[warp][bi]);
+      const uint64_t pol = k < nkeep ? pol_keep : pol_stream;
+      bulk_g2s_hint(stage + ((size_t)warp * NBUF + bi) * (BS2 * 32), a.Sval + s_idx(a.chunk_beg[q], 0), CHB,
+                    &bars[warp][bi], pol);
+      bulk_g2s_hint(&cols[warp][bi][0], a.col + a.chunk_beg[q], 128u, &bars[warp][bi], pol);
     };
     auto arrive = [&](int k) {   // wait for chunk k's copies
       const int bi = k % NBUF;
@@ -2314,6 +2339,7 @@ void launch_pcg(Problem& P) {
   a.x = P.x; a.r = P.r; a.u = P.z; a.p = P.p; a.w = P.Ap; a.s = P.svec; a.part = P.red; a.S = P.S;
   a.uhl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
   a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
+  a.keep_frac = P.pcg_keep_frac;
   void* args[] = {&a};
   ++P.launches;
   P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_stream<T, NT, NB>, dim3(P.pcg_grid), dim3(NT), args,
