@@ -94,7 +94,9 @@ typedef struct ba_options {
   int pcg_max_iters;        /* PCG cap (1000) */
   int precond;              /* ba_precond */
   void* cuda_stream;        /* cudaStream_t to run on (NULL = default stream) */
-  void* (*dev_alloc)(size_t bytes, void* ctx);   /* optional device allocator (e.g. the framework's caching allocator) */
+  void* (*dev_alloc)(size_t bytes, void* ctx);   /* optional device allocator (e.g. the framework's caching allocator);
+                                                    must return 256-byte aligned blocks, as cudaMalloc does: a
+                                                    misaligned block is freed again and the call fails (BA_ERR_OOM) */
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
   long long wait_budget_cycles; /* bound on any device-side spin wait (clock64 cycles) */

@@ -309,7 +309,7 @@ static ba_status freeze(ba_problem* p) {
   p->slotH = p->slotG ? (void*)((char*)p->slotG + T * HG_H) : nullptr;   // a view into the G|H records
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
-  ok &= A(p->slotBS, T * 6 * (size_t)d.ne);
+  ok &= A(p->slotBS, T * SBS * (size_t)d.ne);
   ok &= A(p->Sval, T * BS2 * (size_t)d.nbp);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);

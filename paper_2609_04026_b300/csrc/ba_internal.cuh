@@ -23,7 +23,16 @@ struct Alloc {
   void* ctx = nullptr;
   void* get(size_t bytes) {
     if (bytes == 0) bytes = 16;
-    if (fa) return fa(bytes, ctx);
+    if (fa) {
+      // the kernels move records with 16-byte accesses and bulk copies: a hook's block must be aligned
+      // like cudaMalloc's (256 bytes); a misaligned block is handed back and the allocation fails
+      void* p = fa(bytes, ctx);
+      if (p && ((uintptr_t)p & 255u)) {
+        if (ff) ff(p, ctx);
+        return nullptr;
+      }
+      return p;
+    }
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
     return p;
@@ -53,6 +62,7 @@ constexpr int HG_H = 6;
 constexpr int SH = SG;
 constexpr int SB = 6;   // the whitened per-slot b part
 constexpr int SC = 20;  // camera slot: J_cam^T w J_plane (6 x 3, 18 values)
+constexpr int SBS = 6;  // back-substitution record per slot (6 values, unpadded: padding cost more than it saved)
 
 enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
 

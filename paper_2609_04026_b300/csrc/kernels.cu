@@ -367,7 +367,8 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
     }
     const int camid = a.rcam[rr];
     const int gid = a.rgrp[rr];
-    const T* meas = a.meas + 4 * (size_t)rr;
+    T meas[4];
+    load16<T, 4>(a.meas + 4 * (size_t)rr, meas);
     Cam<T> c;
     if (camid >= 0) load_cam(a.cam + (size_t)CAM_STRIDE * camid, c);
     ResJ<T> o;
@@ -1892,7 +1893,7 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
   } else {
     load16<T, 24>(a.W + (size_t)e * SW, W);
   }
-  T* so = a.sv + (size_t)e * 6;
+  T* so = a.sv + (size_t)e * SBS;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     T s = 0;
@@ -1939,7 +1940,7 @@ __device__ void backsub_feature(const BackArgs<T>& a, int64_t f, double& gTd, do
   for (int i = 0; i < K; ++i) t[i] = a.g[4 * f + i];
   double gd = 0, hh = 0;
   for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
-    const T* so = a.sv + (size_t)e * 6;
+    const T* so = a.sv + (size_t)e * SBS;
 #pragma unroll
     for (int i = 0; i < K; ++i) t[i] += (double)so[i];
     gd += (double)so[4];

@@ -47,12 +47,27 @@ struct Cam {
   T R[9], t[3], f, k1, k2, px, py;
 };
 
+// a camera record (CAM_STRIDE elements, 16-byte aligned); the float records of the linearisation are read
+// with 16-byte loads, the FP64 ones element by element (the FP64 cost pass runs faster with fewer values live)
 template <class T>
 __device__ __forceinline__ void load_cam(const T* __restrict__ c, Cam<T>& o) {
+  if constexpr (sizeof(T) == 4) {
+    T v[20];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) o.R[i] = c[i];
-  o.t[0] = c[9]; o.t[1] = c[10]; o.t[2] = c[11];
-  o.f = c[12]; o.k1 = c[13]; o.k2 = c[14]; o.px = c[15]; o.py = c[16];
+    for (int k = 0; k < 5; ++k) {
+      const float4 q = reinterpret_cast<const float4*>(c)[k];
+      v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o.R[i] = v[i];
+    o.t[0] = v[9]; o.t[1] = v[10]; o.t[2] = v[11];
+    o.f = v[12]; o.k1 = v[13]; o.k2 = v[14]; o.px = v[15]; o.py = v[16];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o.R[i] = c[i];
+    o.t[0] = c[9]; o.t[1] = c[10]; o.t[2] = c[11];
+    o.f = c[12]; o.k1 = c[13]; o.k2 = c[14]; o.px = c[15]; o.py = c[16];
+  }
 }
 
 template <class T> __device__ __forceinline__ T dot3(const T* a, const T* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
