@@ -263,3 +263,32 @@ def test_device_inputs_match_host_inputs(B):
         assert B.ba_eval_cost(p1) == B.ba_eval_cost(p2)
     finally:
         B.ba_destroy(p1); B.ba_destroy(p2)
+
+
+@pytest.mark.gpu
+def test_misaligned_device_allocator_is_refused(B):
+    """The kernels move slot records with 16-byte accesses and S with bulk copies, so a device allocator hook
+    must hand out blocks aligned like cudaMalloc's: a block 16 bytes off is given back and the call fails with
+    BA_ERR_OOM, and every block the hook handed out is returned by the time the problem is destroyed."""
+    held = {}
+
+    def alloc(n, ctx):
+        base = torch.cuda.caching_allocator_alloc(int(n) + 256)
+        held[base + 16] = base
+        return base + 16
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(held.pop(ptr))
+
+    fa, ff = B.ALLOC_FN(alloc), B.FREE_FN(free)
+    o = B.ba_default_options(precision=B.BA_MIXED)
+    o.dev_alloc, o.dev_free = fa, ff
+    p = None
+    with pytest.raises(B.BAError) as err:
+        p = B.ba_create(o)
+        B.load_scene(p, scene("tiny"))
+        B.ba_lm_step(p)
+    assert err.value.status == B.BA_ERR_OOM
+    if p is not None:
+        B.ba_destroy(p)
+    assert not held
