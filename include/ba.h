@@ -120,10 +120,10 @@ typedef struct ba_step_report {
   int relinearized;             /* 1 if the Jacobians were recomputed for this step */
   float ms_linearize, ms_schur, ms_pcg, ms_update;  /* device time per phase */
   /* device time per kernel stage, measured with CUDA events on the problem's stream:
-   * [0] derive + linearize (K1), [1] landmark inverse (K2), [2] Schur work units (K3a),
-   * [3] Schur diagonal / split-block sums (K3b), [4] block-Jacobi (K4), [5] PCG (K5/K6, including the host
-   * reads of the stop flag), [6] back-substitution (K7), [7] candidate (K8a), [8] cost (K8b),
-   * [9] decision (K9) */
+   * [0] derive + linearize (K1; 0 when the step reuses the Jacobians), [1] landmark inverse and whitening
+   * (K2), [2] Schur work units and packed small blocks (K3a), [3] Schur diagonal / split-block sums (K3b),
+   * [4] block-Jacobi (K4), [5] PCG (K5/K6, one cooperative launch), [6] back-substitution (K7),
+   * [7] candidate (K8a), [8] cost (K8b), [9] decision (K9) */
   float ms_kernel[10];
   int n_launches;               /* CUDA kernels this step launched */
   int precond_fallbacks;        /* learned preconditioner: blocks that fell back to block-Jacobi (-1: not used) */
