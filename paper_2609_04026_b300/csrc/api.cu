@@ -356,6 +356,7 @@ static ba_status freeze(ba_problem* p) {
   CUDA_OR(p, cudaMemcpyAsync(p->S, p->hS, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
   for (auto& e : p->ev) CUDA_OR(p, cudaEventCreate(&e));
   // cost at the initial parameters
+  CUDA_OR(p, ensure_ln1p_table(p->stream));
   if (mixed(p)) launch_prepare<float>(*p, false); else launch_prepare<double>(*p, false);
   launch_cost(*p, false);
   CUDA_OR(p, cudaGetLastError());

@@ -107,6 +107,7 @@ __host__ __device__ __forceinline__ size_t s_idx(int64_t q, int e) { return (siz
 template <class T> void launch_backsub(Problem& P);
 void launch_candidate(Problem& P);
 void launch_cost(Problem& P, bool candidate);
+cudaError_t ensure_ln1p_table(cudaStream_t st);   // the FP64 cost's logarithm table on the current device
 void launch_decide(Problem& P);
 
 }  // namespace ba

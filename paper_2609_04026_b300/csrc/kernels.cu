@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "ba_internal.cuh"
 
 namespace ba {
@@ -2119,6 +2121,68 @@ __global__ void k_candidate(CandArgs a) {
   if (i < a.nc + a.npl + a.nv + a.np + a.nl) candidate_item(a, i);
 }
 
+// ---- ln(1 + x) for the FP64 cost, table-driven after P. T. P. Tang, "Table-driven implementation of the
+// logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990, with D. Goldberg's correction
+// for the rounding of 1 + x.  With u = 1 + x = 2^k m, m in [1, 2), and c_j = 1 + j/64 the left end of m's
+// 1/64 interval: ln u = k ln 2 - ln(rc_j) + ln(1 + d), d = m rc_j - 1 in [0, 2^-6) (rc_j = 1/c_j rounded, and
+// the table holds -ln(rc_j) so that the rounding of rc_j cancels exactly), ln(1 + d) by its Taylor series to
+// degree 9 (remainder below 2^-60 relative).  Every term is non-negative, and for j = 0 the table entries are
+// exactly 1 and 0, so nothing cancels as x -> 0.
+__device__ double g_ln1p_tab[130];   // j < 64: rc_j, -ln(rc_j); then ln 2 split into a 28-bit head and a tail
+
+__global__ void k_ln1p_table() {
+  const int j = threadIdx.x;
+  if (j < 64) {
+    const double rc = 1.0 / (1.0 + j / 64.0);
+    g_ln1p_tab[2 * j] = rc;
+    g_ln1p_tab[2 * j + 1] = -log(rc);
+  } else if (j == 64) {
+    const double l2 = log(2.0);
+    const double hi = __longlong_as_double(__double_as_longlong(l2) & ~0xffffffLL);   // k * hi is exact
+    g_ln1p_tab[128] = hi;
+    g_ln1p_tab[129] = l2 - hi;
+  }
+}
+
+__device__ __forceinline__ double ln1p_tab(double x) {
+  const double u = 1.0 + x;
+  if (!(u >= 1.0 && u <= 1.0e308)) return log1p(x);   // negative arguments, infinity and NaN
+  const double corr = (x - (u - 1.0)) * (double)__frcp_rn((float)u);   // the rounding error of 1 + x, over u
+  const long long b = __double_as_longlong(u);
+  const int k = (int)(b >> 52) - 1023;
+  const int j = (int)((b >> 46) & 63);
+  const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  const double d = fma(m, __ldg(&g_ln1p_tab[2 * j]), -1.0);
+  double p = 1.0 / 9;
+  p = fma(p, d, -1.0 / 8);
+  p = fma(p, d, 1.0 / 7);
+  p = fma(p, d, -1.0 / 6);
+  p = fma(p, d, 1.0 / 5);
+  p = fma(p, d, -1.0 / 4);
+  p = fma(p, d, 1.0 / 3);
+  p = fma(p, d, -1.0 / 2);
+  p = fma(p, d, 1.0);
+  const double kd = (double)k;
+  return fma(kd, __ldg(&g_ln1p_tab[128]), __ldg(&g_ln1p_tab[2 * j + 1]) + fma(kd, __ldg(&g_ln1p_tab[129]), fma(p, d, corr)));
+}
+
+// fills the table once per device (stream-ordered, then synchronised so that every stream sees it)
+cudaError_t ensure_ln1p_table(cudaStream_t st) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (done[dev]) return cudaSuccess;
+  k_ln1p_table<<<1, 96, 0, st>>>();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  done[dev] = true;
+  return cudaSuccess;
+}
+
 struct CostArgs {
   const int8_t* rkind;
   const int32_t *rcam, *rfeat, *rgrp, *order;
@@ -2156,7 +2220,7 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
     if (o.valid) {
       double s = 0;
       for (int k = 0; k < rd; ++k) s += o.r[k] * o.r[k];
-      const double e = a.loss.half_wa2[kind] * log1p(s * a.loss.inv_a2[kind]);
+      const double e = a.loss.half_wa2[kind] * ln1p_tab(s * a.loss.inv_a2[kind]);
       v[0] = e;
       v[1] = kind == R_VP ? 0.0 : e;
     }
