@@ -1467,12 +1467,12 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
 // Grid path of K5/K6: S streamed by the Tensor Memory Accelerator, CG in the Chronopoulos-Gear form.
 //
 // A CTA multiplies a contiguous run of 32-block chunks of the padded storage (one chunk = 32 whole blocks,
-// 4.6 KB in float), runs of equal length whatever the row lengths: a long row (a plane or a vanishing
-// point seen by many cameras) may be cut between CTAs.  A row belongs to the CTA holding its first chunk,
-// which updates its vector entries; a CTA whose run starts inside a row it does not own leaves its partial
-// product of that row in a carry slot, added by the owner after the grid barrier that follows the product
-// (the partial dot (w, u) needs no carry: it is a sum over the pieces).  The run is split into NW contiguous pieces,
-// one per warp; a warp keeps NBUF chunks of its piece in flight in shared memory, each fetched by two
+// 4.6 KB in float), the runs of about equal weight whatever the row lengths: a long row (a plane or a
+// vanishing point seen by many cameras) may be cut between CTAs.  A row belongs to the CTA holding its first
+// chunk, which updates its vector entries; a CTA whose run starts inside a row it does not own leaves its
+// partial product of that row in a carry slot, added by the owner after the grid barrier that follows the
+// product (the partial dot (w, u) needs no carry: it is a sum over the pieces).  The run is split into NW
+// contiguous pieces, one per warp; a warp keeps NBUF chunks of its piece in flight in shared memory, each fetched by two
 // bulk copies (cp.async.bulk: the values and the 32 column indices, completion counted on an mbarrier
 // per buffer), so the stream of S never waits on the products.  Every wait on an mbarrier is bounded: if a copy has not landed after a very long
 // spin the kernel records PCG_FLAG_TIMEOUT, finishes the iteration and stops; the host then returns
