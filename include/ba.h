@@ -176,6 +176,14 @@ ba_status ba_set_lm_state(ba_problem* p, const double* lambda_nu);
 /* Cost (E, E_px) at the current parameters (FP64). */
 ba_status ba_eval_cost(ba_problem* p, double* cost, double* cost_px);
 
+/* ln(1 + x) as the FP64 cost pass evaluates it in the Cauchy loss a^2 ln(1 + |r|^2 / a^2) (Section 3.5,
+ * Appendix C): a table-driven logarithm (Tang, ACM TOMS 1990) whose table the library fills once per device.
+ * x (n values) and y (n values, output) are DEVICE arrays of the current device; runs on cuda_stream (NULL =
+ * default stream) and returns after the work has finished.  x >= 0 is the range the cost uses; other values
+ * go to the CUDA math library's log1p.  BA_ERR_ARG for n < 0 or a null array, BA_ERR_CUDA if a CUDA call fails.
+ * An inspection call for tests of the cost's accuracy. */
+ba_status ba_eval_log1p(int64_t n, const double* x, double* y, void* cuda_stream);
+
 /* Build the damped reduced system S, b at damping lambda (linearising if needed) without stepping. */
 ba_status ba_build_reduced(ba_problem* p, double lambda);
 /* Sizes of the reduced system: number of A entities (block rows, each 6 wide; plane blocks use 3, VP blocks 2
@@ -254,12 +262,17 @@ ba_status ba_precond_train(int64_t n, const float* X, const float* E, const uint
  *   cuda_stream    stream to run on (NULL = default stream); the call returns after the work has finished
  *   iters, rel     optional outputs: PCG iterations and final |r_k| / |b|
  *   err, err_len   optional buffer for a message on failure
- * Returns BA_ERR_ARG (with a message) for sizes beyond the limits above, a missing diagonal block or an
- * out-of-range column, BA_ERR_CUDA if a CUDA call fails.
+ * Returns BA_ERR_ARG (with a message) for sizes beyond the limits above, a missing diagonal block, an
+ * out-of-range column or a diagonal block that is not positive definite (no solve is attempted then),
+ * BA_ERR_CUDA if a CUDA call fails.
+ * The call reads status flags back to the host and synchronises cuda_stream several times, so it cannot be
+ * recorded into a CUDA graph: do not call it while a stream of its device is being captured.
  * The first call on a device finds the device address of the scratch array (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call shares the scratch array and
- * leaves the previous call's contents in it (the call initialises everything it reads), so calls whose GPU
- * work overlaps -- from two host threads, or on two streams of one device -- race on it. */
+ * device current and keeps it for the life of the process; after a cudaDeviceReset of that device in the
+ * calling process the kept address is stale, so do not call this entry point again after such a reset.
+ * Every call shares the scratch array and leaves the previous call's contents in it (the call initialises
+ * everything it reads), so calls whose GPU work overlaps -- from two host threads, or on two streams of one
+ * device -- race on it. */
 ba_status ba_pcg_solve_static(int64_t n_block_rows, int64_t nnz_blocks, const int32_t* row_ptr,
                               const int32_t* cols, const double* vals, const double* b, double* x,
                               double rel_tol, int max_iters, void* cuda_stream, int* iters, double* rel,

@@ -649,6 +649,29 @@ class LMState:
     nu: float = 2.0
 
 
+def lm_update(lm: LMState, gain, E_new, opt: Options):
+    """The accept test and the damping update (Madsen, Nielsen & Tingleff 2004, Sec. 3.2, Nielsen's rule).
+    Accept when the candidate cost is finite and the gain ratio exceeds min_gain (a tie rejects); then
+    lambda <- lambda * max(1/3, 1 - (2 gain - 1)^3), clamped to [lambda_min, lambda_max], and nu <- 2.
+    Otherwise lambda <- min(lambda * nu, lambda_max) and nu <- 2 nu.  Returns the decision."""
+    accepted = bool(np.isfinite(E_new) and gain > opt.min_gain)
+    if accepted:
+        lm.lam = min(max(lm.lam * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3), opt.lambda_min), opt.lambda_max)
+        lm.nu = 2.0
+    else:
+        lm.lam = min(lm.lam * lm.nu, opt.lambda_max)
+        lm.nu *= 2.0
+    return accepted
+
+
+def step_converged(rep, opt: Options):
+    """Termination test of Section 3.5: an accepted step whose relative change of the pixel-space cost
+    E_px (the VP angular terms excluded, Appendix C) is below rel_cost_tol."""
+    if not rep["accepted"]:
+        return False
+    return abs(rep["Epx"] - rep["Epx_new"]) / max(rep["Epx"], 1e-300) < opt.rel_cost_tol
+
+
 def lm_step(state, obs, opt: Options, lm: LMState, lay: Layout, cur=None, lin=None):
     """One LM iteration (build, damp, eliminate, solve, back-substitute, evaluate, decide).
     Acceptance: gain ratio > min_gain; lambda update by Nielsen's rule
@@ -659,14 +682,8 @@ def lm_step(state, obs, opt: Options, lm: LMState, lay: Layout, cur=None, lin=No
     E2, Epx2 = cost(cand, obs, opt)
     pred = info["pred"]
     gain = (E - E2) / pred if pred > 0 else -np.inf
-    accepted = bool(np.isfinite(E2) and gain > opt.min_gain)
     lam_used = lm.lam
-    if accepted:
-        lm.lam = min(max(lm.lam * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3), opt.lambda_min), opt.lambda_max)
-        lm.nu = 2.0
-    else:
-        lm.lam = min(lm.lam * lm.nu, opt.lambda_max)
-        lm.nu *= 2.0
+    accepted = lm_update(lm, gain, E2, opt)
     rep = dict(E=E, Epx=Epx, E_new=E2, Epx_new=Epx2, gain=gain, accepted=accepted, lam=lam_used,
                pcg_iters=info["pcg_iters"], pcg_rel=info["pcg_rel"], pred=pred, delta=delta)
     return (cand if accepted else state), rep
@@ -687,9 +704,8 @@ def solve(scene_or_state, obs, opt: Options = None, max_iters=20, fixed=None, hi
         rep.pop("delta")
         reps.append(rep)
         if rep["accepted"]:
-            rel = abs(rep["Epx"] - rep["Epx_new"]) / max(rep["Epx"], 1e-300)
             cur = (rep["E_new"], rep["Epx_new"])
-            if rel < opt.rel_cost_tol:
+            if step_converged(rep, opt):
                 converged = True
                 break
     return state, dict(iters=len(reps), converged=converged, reports=reps, E=cur[0], Epx=cur[1])

@@ -92,6 +92,7 @@ def _load():
         "ba_get_lm_state": (I, [P, VP]),
         "ba_set_lm_state": (I, [P, VP]),
         "ba_eval_cost": (I, [P, C.POINTER(D), C.POINTER(D)]),
+        "ba_eval_log1p": (I, [I64, VP, VP, VP]),
         "ba_build_reduced": (I, [P, D]),
         "ba_reduced_size": (I, [P, C.POINTER(I64), C.POINTER(I64)]),
         "ba_export_reduced_system": (I, [P, VP, VP, VP, VP]),
@@ -142,6 +143,22 @@ def lib():
 def _check(p, status):
     if status != BA_OK:
         raise BAError(status, _lib.ba_last_error(p).decode() if p else "")
+
+
+def _need_dev(*specs):
+    """Raw device pointers cross the ABI without lengths, so the binding checks what the C side cannot.
+    specs: (tensor, dtype, element count, name) tuples; each must be a contiguous tensor of that dtype and
+    count (checked for all first), and all must be CUDA tensors of one device (BA_ERR_ARG otherwise)."""
+    for t, dtype, numel, name in specs:
+        if getattr(t, "dtype", None) != dtype:
+            raise BAError(BA_ERR_ARG, f"{name}: expected dtype {dtype}, got {getattr(t, 'dtype', type(t).__name__)}")
+        if t.numel() != numel:
+            raise BAError(BA_ERR_ARG, f"{name}: expected {numel} elements, got {t.numel()}")
+        if not t.is_contiguous():
+            raise BAError(BA_ERR_ARG, f"{name}: must be contiguous")
+    for t, _, _, name in specs:
+        if not t.is_cuda or t.device != specs[0][0].device:
+            raise BAError(BA_ERR_ARG, f"{name}: must be a CUDA tensor on the device of {specs[0][3]}")
 
 
 def _arr(x, dtype):
@@ -351,8 +368,15 @@ def load_scene(p, scene, device_tensors=False):
 def ba_pcg_solve_static(row_ptr, cols, vals, b, x, rel_tol=1e-6, max_iters=1000, stream=None):
     """Allocation-free PCG on a reduced system: row_ptr a host int32 array, cols / vals / b / x CUDA tensors
     (int32, float64 [nnz, 6, 6], float64 [6n], float64 [6n] output).  Returns (iterations, relative residual)."""
-    n = len(row_ptr) - 1
-    rp = np.ascontiguousarray(row_ptr, np.int32)
+    import torch
+    rp = np.ascontiguousarray(row_ptr)
+    if rp.dtype != np.int32 or rp.ndim != 1 or len(rp) < 2:
+        raise BAError(BA_ERR_ARG, "row_ptr: expected a 1-D int32 host array of n_block_rows + 1 offsets")
+    n, nnz = len(rp) - 1, int(rp[-1])
+    if rp[0] != 0 or np.any(np.diff(rp) <= 0):
+        raise BAError(BA_ERR_ARG, "row_ptr: must start at 0 and give every block row at least its diagonal block")
+    _need_dev((cols, torch.int32, nnz, "cols"), (vals, torch.float64, 36 * nnz, "vals"),
+              (b, torch.float64, 6 * n, "b"), (x, torch.float64, 6 * n, "x"))
     it, rel = C.c_int(), C.c_double()
     err = C.create_string_buffer(256)
     st = _lib.ba_pcg_solve_static(n, int(rp[-1]), rp.ctypes.data_as(C.c_void_p), C.c_void_p(cols.data_ptr()),
@@ -362,6 +386,17 @@ def ba_pcg_solve_static(row_ptr, cols, vals, b, x, rel_tol=1e-6, max_iters=1000,
     if st != BA_OK:
         raise BAError(st, err.value.decode())
     return it.value, rel.value
+
+
+def ba_eval_log1p(x, stream=None):
+    """ln(1 + x) of a CUDA float64 tensor as the library's cost pass evaluates it; returns a new tensor."""
+    import torch
+    _need_dev((x, torch.float64, x.numel(), "x"))
+    y = torch.empty_like(x)
+    st = _lib.ba_eval_log1p(x.numel(), _dp(x), _dp(y), C.c_void_p(stream or 0))
+    if st != BA_OK:
+        raise BAError(st, "ba_eval_log1p failed")
+    return y
 
 
 # ---------------------------------------------------------------------------- learned preconditioner
@@ -396,6 +431,9 @@ def ba_mlp_grad(X, E, mask, params, stream=None):
     """X [n,32], E [n,21] float32, mask [n] uint8, params [P] float32: CUDA tensors.  Returns (loss, grad)."""
     import torch
     n = X.shape[0]
+    P = ba_precond_param_count()
+    _need_dev((X, torch.float32, 32 * n, "X"), (E, torch.float32, 21 * n, "E"), (mask, torch.uint8, n, "mask"),
+              (params, torch.float32, P, "params"))
     grad = torch.empty(ba_precond_param_count() - 64, dtype=torch.float32, device=X.device)
     work = torch.empty(int(_lib.ba_mlp_work_floats(n)) + 8, dtype=torch.float32, device=X.device)
     loss = C.c_double()
@@ -409,6 +447,13 @@ def ba_mlp_grad(X, E, mask, params, stream=None):
 def ba_precond_train(X, E, mask, params, adam_m, adam_v, t0, steps, batch, lr, stream=None):
     """In-place Adam training of params (CUDA tensors); returns the last mini-batch loss."""
     import torch
+    n = X.shape[0]
+    P = ba_precond_param_count()
+    _need_dev((X, torch.float32, 32 * n, "X"), (E, torch.float32, 21 * n, "E"), (mask, torch.uint8, n, "mask"),
+              (params, torch.float32, P, "params"), (adam_m, torch.float32, P, "adam_m"),
+              (adam_v, torch.float32, P, "adam_v"))
+    if n < 1 or int(batch) < 1 or int(steps) < 0 or int(t0) < 0:
+        raise BAError(BA_ERR_ARG, "need n >= 1, batch >= 1, steps >= 0 and t0 >= 0")
     work = torch.empty(int(_lib.ba_mlp_work_floats(batch)) + 8, dtype=torch.float32, device=X.device)
     loss = C.c_double()
     st = _lib.ba_precond_train(X.shape[0], _dp(X), _dp(E), _dp(mask), _dp(params), _dp(adam_m), _dp(adam_v),

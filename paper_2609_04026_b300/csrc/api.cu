@@ -574,6 +574,17 @@ extern "C" ba_status ba_eval_cost(ba_problem* p, double* cost, double* cost_px) 
   return BA_OK;
 }
 
+extern "C" ba_status ba_eval_log1p(int64_t n, const double* x, double* y, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return BA_ERR_ARG;
+  if (n == 0) return BA_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (launch_ln1p_eval(st, n, x, y) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return BA_ERR_CUDA;
+  }
+  return BA_OK;
+}
+
 extern "C" ba_status ba_build_reduced(ba_problem* p, double lambda) {
   if (!p) return BA_ERR_ARG;
   if (!(lambda >= 0) || !std::isfinite(lambda)) return set_err(p, BA_ERR_ARG, "lambda must be finite and >= 0");

@@ -108,6 +108,7 @@ template <class T> void launch_backsub(Problem& P);
 void launch_candidate(Problem& P);
 void launch_cost(Problem& P, bool candidate);
 cudaError_t ensure_ln1p_table(cudaStream_t st);   // the FP64 cost's logarithm table on the current device
+cudaError_t launch_ln1p_eval(cudaStream_t st, int64_t n, const double* x, double* y);
 void launch_decide(Problem& P);
 
 }  // namespace ba

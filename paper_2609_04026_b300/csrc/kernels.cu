@@ -2183,6 +2183,19 @@ cudaError_t ensure_ln1p_table(cudaStream_t st) {
   return cudaSuccess;
 }
 
+// ln(1 + x) of n device values exactly as the cost pass evaluates it (inspection of the logarithm)
+__global__ void k_ln1p_eval(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = ln1p_tab(x[i]);
+}
+
+cudaError_t launch_ln1p_eval(cudaStream_t st, int64_t n, const double* x, double* y) {
+  cudaError_t e = ensure_ln1p_table(st);
+  if (e != cudaSuccess || n <= 0) return e;
+  k_ln1p_eval<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+
 struct CostArgs {
   const int8_t* rkind;
   const int32_t *rcam, *rfeat, *rgrp, *order;

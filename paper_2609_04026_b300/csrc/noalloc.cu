@@ -191,6 +191,13 @@ extern "C" ba_status ba_pcg_solve_static(int64_t n, int64_t nnz, const int32_t* 
     return BA_ERR_ARG;
   }
   if ((e = launch_precond_raw_f64(st, n, W->row_ptr, cols, vals, W->Minv, &W->S))) return fail_cuda(e);
+  // a diagonal block whose Cholesky factorisation failed: S is not positive definite, and CG is not defined
+  if ((e = cudaMemcpyAsync(&flags, &W->S.flags, sizeof(int), cudaMemcpyDeviceToHost, st))) return fail_cuda(e);
+  if ((e = cudaStreamSynchronize(st))) return fail_cuda(e);
+  if (flags & 4) {
+    set_msg(err, err_len, "ba_pcg_solve_static: a diagonal block is not positive definite");
+    return BA_ERR_ARG;
+  }
   if ((e = launch_pcg_raw_f64(st, (int)G, smem, n, cols, W->cta_row0, W->row_chunk0, W->chunk_beg, vals, W->Minv, b,
                               x, W->r, W->z, W->p, W->Ap, W->part, &W->S, rel_tol, max_iters)))
     return fail_cuda(e);

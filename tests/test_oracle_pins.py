@@ -351,3 +351,84 @@ def test_classical_ba_matches_independent_minimiser():
     res = scipy.optimize.minimize(fg, x0, jac=True, hess=hs, method="trust-exact",
                                   options=dict(gtol=1e-11, maxiter=500))
     assert abs(info["E"] - res.fun) <= 1e-8 * res.fun, (info["E"], res.fun)
+
+
+# ---------------------------------------------------------------- the LM rule (hand-worked values)
+# Madsen, Nielsen & Tingleff 2004, Sec. 3.2 (Nielsen's damping update): on acceptance
+# lambda <- lambda * max(1/3, 1 - (2 rho - 1)^3) and nu <- 2; on rejection lambda <- lambda nu, nu <- 2 nu.
+# Each expected value below is worked by hand from that rule; acceptance needs rho > min_gain (1e-3), and
+# lambda is clamped to [1e-12, 1e12].
+@pytest.mark.parametrize("lam,nu,gain,E_new,acc,lam_exp,nu_exp", [
+    (1e-2, 8.0, 0.75, 1.0, True, 8.75e-3, 2.0),          # 2*0.75-1 = 0.5, cube 0.125 -> factor 0.875; nu reset
+    (1e-2, 2.0, 0.25, 1.0, True, 1.125e-2, 2.0),         # (-0.5)^3 = -0.125 -> factor 1.125
+    (3e-4, 2.0, 1.0, 1.0, True, 1e-4, 2.0),              # 1 - 1 = 0 -> the floor 1/3
+    (1e-2, 2.0, 0.9, 1.0, True, 0.488e-2, 2.0),          # 1 - 0.8^3 = 0.488 (above the floor)
+    (1e-2, 2.0, 0.95, 1.0, True, 1e-2 / 3.0, 2.0),       # 1 - 0.9^3 = 0.271 -> the floor 1/3
+    (1e-2, 2.0, 0.6, 1.0, True, 0.992e-2, 2.0),          # 1 - 0.2^3 = 0.992
+    (1.0, 2.0, 0.0011, 1.0, True, 1.993414509352, 2.0),  # 0.9978^3 = 0.99560484 * 0.9978 = 0.993414509352
+    (1e-2, 4.0, 1e-3, 1.0, False, 4e-2, 8.0),            # a tie with min_gain rejects
+    (1e-2, 2.0, -0.5, 1.0, False, 2e-2, 4.0),            # a cost increase rejects
+    (1e-2, 2.0, 0.8, math.inf, False, 2e-2, 4.0),        # a non-finite candidate rejects whatever the gain
+    (1e-12, 2.0, 1.0, 1.0, True, 1e-12, 2.0),            # lower clamp
+    (6e11, 2.0, 0.0, 1.0, False, 1e12, 4.0),             # upper clamp on rejection
+])
+def test_lm_update_hand_worked(lam, nu, gain, E_new, acc, lam_exp, nu_exp):
+    opt = O.Options()
+    lm = O.LMState(lam, nu)
+    assert O.lm_update(lm, gain, E_new, opt) is acc
+    assert lm.lam == pytest.approx(lam_exp, rel=1e-12)
+    assert lm.nu == nu_exp
+
+
+def test_lm_update_sequence():
+    """Two rejections then an acceptance: nu doubles twice, then the accepted factor applies to the
+    grown lambda and nu resets (1e-4 -> 2e-4 -> 8e-4 -> 8e-4 * 0.875 = 7e-4)."""
+    opt = O.Options()
+    lm = O.LMState(1e-4)
+    assert not O.lm_update(lm, -1.0, 1.0, opt)
+    assert (lm.lam, lm.nu) == (pytest.approx(2e-4), 4.0)
+    assert not O.lm_update(lm, 0.0005, 1.0, opt)
+    assert (lm.lam, lm.nu) == (pytest.approx(8e-4), 8.0)
+    assert O.lm_update(lm, 0.75, 1.0, opt)
+    assert (lm.lam, lm.nu) == (pytest.approx(7e-4, rel=1e-12), 2.0)
+
+
+def test_pixel_cost_excludes_vp_terms(tiny):
+    """E_px is E without the angular VP terms (Section 3.5, Appendix C): moving a VP direction changes E
+    through its VP residuals only and leaves E_px unchanged, while moving a point changes both."""
+    s, st, _ = tiny
+    opt = O.Options()
+    E0, P0 = O.cost(st, s["obs"], opt)
+    vp_only = sum(float(x) for x in _kind_cost(st, s["obs"], opt, "vp"))
+    assert vp_only > 0 and abs((E0 - P0) - vp_only) <= 1e-12 * E0
+    st2 = {k: v.copy() for k, v in st.items()}
+    v = st2["vps"][0] + np.array([0.02, -0.01, 0.015])
+    st2["vps"][0] = v / np.linalg.norm(v)
+    E1, P1 = O.cost(st2, s["obs"], opt)
+    assert abs(E1 - E0) > 1e-6 * E0
+    assert P1 == P0
+    st3 = {k: v.copy() for k, v in st.items()}
+    st3["points"][0] += 0.05
+    E2, P2 = O.cost(st3, s["obs"], opt)
+    assert P2 != P0 and abs((E2 - P2) - (E0 - P0)) <= 1e-12 * E0
+
+
+def _kind_cost(st, obs, opt, kind):
+    r, v = O.residuals(st, obs, kind)
+    a = opt.scale(kind)
+    e = 0.5 * opt.weight(kind) * a * a * torch.log1p((r * r).sum(-1) / (a * a))
+    return torch.where(v, e, torch.zeros_like(e))
+
+
+def test_termination_uses_pixel_cost():
+    """The stopping test reads the relative change of E_px, not of E: a step that moves only the VP
+    terms a lot still stops, and a step that moves E_px by more than the tolerance does not; a rejected
+    step never stops."""
+    opt = O.Options()
+    assert O.step_converged(dict(accepted=True, E=1e3, E_new=5e2, Epx=100.0, Epx_new=100.0 - 5e-5), opt)
+    assert not O.step_converged(dict(accepted=True, E=1e3, E_new=1e3 - 1e-6, Epx=100.0, Epx_new=100.0 - 2e-4), opt)
+    assert not O.step_converged(dict(accepted=False, E=1e3, E_new=1e3, Epx=100.0, Epx_new=100.0), opt)
+    # a relative change of exactly rel_cost_tol does not stop (strict inequality); 2^-20 is exact in binary
+    opt2 = O.Options(rel_cost_tol=2.0 ** -20)
+    assert not O.step_converged(dict(accepted=True, E=1.0, E_new=1.0, Epx=1.0, Epx_new=1.0 - 2.0 ** -20), opt2)
+    assert O.step_converged(dict(accepted=True, E=1.0, E_new=1.0, Epx=1.0, Epx_new=1.0 - 2.0 ** -21), opt2)

@@ -61,3 +61,21 @@ def test_static_pcg_rejects_oversize(B):
     with pytest.raises(B.BAError) as e:
         B.ba_pcg_solve_static(rp, t, t, t, t)
     assert e.value.status == B.BA_ERR_ARG and "4096" in str(e.value)
+
+
+def test_static_pcg_rejects_indefinite_diagonal_block(B):
+    """A diagonal block that is not positive definite makes S indefinite: the call says so (BA_ERR_ARG) and
+    does not run CG on it."""
+    n = 3
+    rp = np.array([0, 2, 4, 5], np.int32)
+    cols = np.array([0, 1, 0, 1, 2], np.int32)
+    vals = np.zeros((5, 6, 6))
+    vals[0] = vals[2] = np.eye(6) * 4.0
+    vals[1] = vals[3] = np.eye(6) * 0.5
+    vals[4] = np.diag([3.0, 2.0, -1.0, 1.0, 1.0, 1.0])    # indefinite
+    dev = torch.device("cuda")
+    x_d = torch.zeros(6 * n, dtype=torch.float64, device=dev)
+    with pytest.raises(B.BAError) as e:
+        B.ba_pcg_solve_static(rp, torch.from_numpy(cols).to(dev), torch.from_numpy(vals.reshape(-1)).to(dev),
+                              torch.ones(6 * n, dtype=torch.float64, device=dev), x_d)
+    assert e.value.status == B.BA_ERR_ARG and "positive definite" in str(e.value)
