@@ -84,7 +84,7 @@ def train(B, X, E, mask, steps=4000, batch=1024, lr=1e-3, seed=0, log_every=500)
     Ed = torch.from_numpy(np.ascontiguousarray(E[perm])).to(dev)
     Md = torch.from_numpy(np.ascontiguousarray(mask[perm])).to(dev)
     prm = torch.from_numpy(init_params(X, seed)).to(dev)
-    m = torch.zeros(prm.numel() - 2 * NF, device=dev)
+    m = torch.zeros(prm.numel() - 2 * NF, dtype=torch.float32, device=dev)
     v = torch.zeros_like(m)
     hist = []
     t = 0

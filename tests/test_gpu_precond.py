@@ -87,7 +87,7 @@ def test_adam_step_matches_oracle(B):
     Xd, Ed, Md = (torch.from_numpy(a).to(dev) for a in (X, E, mask))
     prm = torch.from_numpy(blob.copy()).to(dev)
     loss, grad = B.ba_mlp_grad(Xd, Ed, Md, prm)
-    m = torch.zeros(PO.NTRAIN, device=dev)
+    m = torch.zeros(PO.NTRAIN, dtype=torch.float32, device=dev)
     v = torch.zeros_like(m)
     B.ba_precond_train(Xd, Ed, Md, prm, m, v, 0, 1, n, 1e-3)
     th, _, _ = PO.adam_step(blob[64:].astype(np.float64), np.zeros(PO.NTRAIN), np.zeros(PO.NTRAIN),
