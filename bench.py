@@ -34,7 +34,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LM iter/s & time-to-converge (cost rel 1e-6) at 2k cams; PCG iters vs Jacobi"
 UNIT = "LM iter/s"
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12     # SMs x FP32 lanes x 2 (FMA) x max SM clock
 
 
 # ------------------------------------------------------------------------------------------ helpers
@@ -110,18 +109,33 @@ def workload_desc(s, name):
             f"{c['vp']} VP, {c['p2l'] + c['l2p']} wireframe)")
 
 
-# DRAM traffic model of the streaming PCG kernel (float S), from dram__bytes_read.sum + dram__bytes_write.sum
-# of ncu captures of that kernel on the 2000-camera, 200k-point scene (130 iterations, 1.285M stored blocks):
-# every stored block is streamed once per iteration at 153.3 DRAM bytes per block (measured before S was
-# given an L2 policy), less the share of S that stays resident in L2 between iterations under the
-# evict_last policy, a fixed amount (about 60 MB kept) measured at 62.3 MB per iteration (17.51 GB over 130
-# iterations with the policy against 25.62 GB without)
-PCG_DRAM_BYTES_PER_BLOCK_ITER = 153.3
-PCG_L2_RETAINED_BYTES_PER_ITER = 62.3e6
-
 # per-unit algorithmic FP32 flops of the linearisation (residual + Jacobian + IRLS-weighted accumulation of
 # V_f, g_f and the per-slot blocks), counted from the formulas of each residual kind
 LIN_FLOPS = {"point": 354, "line": 1100, "plane_point": 660, "plane_line": 2700, "vp": 280, "p2l": 210, "l2p": 440}
+
+
+def s_type_counts(rp, cols, nc, npl):
+    """Blocks of the reduced system by storage type: camera-camera (both triangles), camera-plane and
+    camera-VP (upper triangle only), group-group (both triangles), and the camera-camera upper triangle."""
+    na = len(rp) - 1
+    r = np.repeat(np.arange(na), np.diff(rp))
+    c = cols.astype(np.int64)
+    cam_r = r < nc
+    return {"cc": int((cam_r & (c < nc)).sum()), "cp": int((cam_r & (c >= nc) & (c < nc + npl)).sum()),
+            "cv": int((cam_r & (c >= nc + npl)).sum()), "gg": int((~cam_r & (c >= nc)).sum()),
+            "cc_upper": int((cam_r & (c < nc) & (c >= r)).sum()), "gg_upper": int((~cam_r & (c >= r)).sum())}
+
+
+def pcg_bytes_per_iter(t, T, na):
+    """Algorithmic bytes of one PCG iteration on the typed storage: every stored block's values at its real
+    width (camera-camera 36, camera-plane 18, camera-VP 12, group-group 36) and its 4-byte column index, and
+    the FP64 vectors (~10 reads or writes of 6 doubles per block row).  The symmetric minimum stores the
+    camera-camera and group-group blocks once (upper triangle)."""
+    vec = na * 6 * 8 * 10
+    stored = T * (36 * t["cc"] + 18 * t["cp"] + 12 * t["cv"] + 36 * t["gg"]) + 4 * (t["cc"] + t["cp"] + t["cv"] + t["gg"])
+    sym = T * (36 * t["cc_upper"] + 18 * t["cp"] + 12 * t["cv"] + 36 * t["gg_upper"]) + \
+        4 * (t["cc_upper"] + t["cp"] + t["cv"] + t["gg_upper"])
+    return stored + vec, sym + vec
 
 
 def roofline_models(n, dims):
@@ -129,12 +143,10 @@ def roofline_models(n, dims):
     pairs_pt, pairs_ln = dims["pairs_point"], dims["pairs_line"]
     return {
         "linearize": ("alu", sum(LIN_FLOPS[k] * v for k, v in n.items()), "TFLOP/s"),
-        # S_ab -= Y_a^T W_b: 36 k FMA per slot pair (k = 3 point, 4 line)
+        # S_ab -= Z_a^T Z_b: 36 k FMA per slot pair (k = 3 point, 4 line)
         "schur_items": ("alu", 2 * 36 * (3 * pairs_pt + 4 * pairs_ln), "TFLOP/s"),
-        # PCG: every iteration streams the stored blocks of S (36 values + a 4-byte column index) and touches
-        # the FP64 vectors (SpMV gather of p, x, r, z, Ap, p updates: ~10 reads/writes of 6 doubles per row)
-        "pcg": ("hbm", dims["pcg_iters_mean"] * (dims["stored_blocks"] * (36 * dims["Tbytes"] + 4)
-                                                  + dims["block_rows"] * 6 * 8 * 10), "GB/s"),
+        # PCG: every iteration streams the stored blocks of S and touches the FP64 vectors
+        "pcg": ("hbm", dims["pcg_iters_mean"] * dims["pcg_bytes_iter"], "GB/s"),
     }
 
 
@@ -189,6 +201,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-window workload")
     ap.add_argument("--windows", type=int, default=256)
     ap.add_argument("--no-fp64-ttc", action="store_true", help="skip the FP64 block-Jacobi time-to-converge")
+    ap.add_argument("--no-mixed-error", action="store_true", help="skip the per-result mixed-vs-FP64 error")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -244,7 +257,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     na, nbf = B.ba_reduced_size(p)
+    B.ba_build_reduced(p, float(B.ba_get_lm_state(p)[0]))
+    rp_, cols_, _, _ = B.ba_export_reduced_system(p, values=False)
     B.ba_destroy(p)
+    tcounts = s_type_counts(rp_, cols_, len(scene["cams"]["q"]), len(scene["planes"]))
+    peak32 = B.ba_measure_fma_rate(B.BA_MIXED, stream.cuda_stream)
+    peak64 = B.ba_measure_fma_rate(B.BA_FP64, stream.cuda_stream)
 
     kern = {k: float(np.mean([r.as_dict()["ms_kernel"][k] for r in timed])) for k in timed[0].KERNELS}
     launches = int(sum(r.n_launches for r in timed))
@@ -258,31 +276,37 @@ def main():
     dims.update(dims_S)
     dims["pcg_iters_mean"] = float(np.mean(pcg_iters))
     dims["Tbytes"] = 4 if prec == B.BA_MIXED else 8
+    dims["pcg_bytes_iter"], sym_iter = pcg_bytes_per_iter(tcounts, dims["Tbytes"], na)
+    dims_S["blocks_by_type"] = tcounts
     models = roofline_models(counts, dims)
-    dom = max(kern, key=kern.get)
-    roof = None
-    if dom in models:
-        bound, work, unit = models[dom]
+    pk = measured_peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6400.0
+    hbm_src = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6.4 TB/s"
+    alu_peak = peak32 if prec == B.BA_MIXED else peak64
+    alu_src = ("measured FP32 FMA rate of this GPU (ba_measure_fma_rate)" if prec == B.BA_MIXED else
+               "measured FP64 FMA rate of this GPU (ba_measure_fma_rate)")
+
+    def stage_roof(stage):
+        bound, work, unit = models[stage]
         if bound == "hbm":
-            achieved = work / (kern[dom] / 1e3) / 1e9
-            pk = measured_peaks()
-            peak = pk["hbm_gbs"] if pk else 6400.0
-            src = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6.4 TB/s"
+            achieved, peak, src = work / (kern[stage] / 1e3) / 1e9, hbm_peak, hbm_src
         else:
-            achieved = work / (kern[dom] / 1e3) / 1e12
-            peak = FP32_PEAK_TFLOPS
-            src = "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"
-        traffic = None
-        if dom == "pcg" and prec == B.BA_MIXED:
-            per_iter = max(0.0, PCG_DRAM_BYTES_PER_BLOCK_ITER * dims["stored_blocks"] - PCG_L2_RETAINED_BYTES_PER_ITER)
-            traffic = int(per_iter * dims["pcg_iters_mean"])
-        roof = {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": unit,
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
-                "work": "algorithmic bytes per launch: PCG iterations x (stored blocks x (36 values + 4-byte column) "
-                        "+ block rows x 6 x 8 bytes x 10 vector accesses)"}
-    else:
-        roof = {"bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "note": "no algorithmic model for this stage"}
+            achieved, peak, src = work / (kern[stage] / 1e3) / 1e12, alu_peak, alu_src
+        return {"bound": bound, "kernel": stage, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": unit,
+                "frac": round(achieved / peak, 4), "peak_source": src}
+
+    stages = {k: stage_roof(k) for k in models if kern.get(k, 0) > 0}
+    stages["pcg"]["work"] = ("algorithmic bytes per launch: PCG iterations x (typed storage of S: camera-camera blocks "
+                             "36 values (both triangles), camera-plane 18, camera-VP 12, group-group 36, each with a "
+                             "4-byte column index; + block rows x 6 x 8 bytes x 10 vector accesses)")
+    stages["pcg"]["frac_of_symmetric_minimum"] = round(
+        dims["pcg_iters_mean"] * sym_iter / (kern["pcg"] / 1e3) / 1e9 / hbm_peak, 4)
+    stages["pcg"]["traffic"] = None   # the DRAM counters of the current kernel are in profiles/
+    dom = max(kern, key=kern.get)
+    roof = dict(stages[dom]) if dom in stages else {
+        "bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+        "note": "no algorithmic model for this stage"}
+    roof.setdefault("traffic", None)
 
     # ---------------- end to end through the public API (host buffers) to convergence
     e2e = None
@@ -294,7 +318,10 @@ def main():
         o2 = B.ba_default_options(precision=prec, max_lm_iters=args.max_iters, precond=B.BA_PRECOND_LEARNED)
         q = B.ba_create(o2)
         B.load_scene(q, scene)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
         B.ba_precond_set_weights(q, shipped_weights())      # freezes the structure: after the inputs
+        structure_s = time.perf_counter() - ts
         sr = B.ba_solve(q)
         cams = B.ba_get_cameras(q, len(scene["cams"]["q"]))
         pts = B.ba_get_features(q, B.BA_POINT, len(scene["points"]))
@@ -310,7 +337,10 @@ def main():
                "note": "one job = create, host->device inputs, structure build, ba_solve to convergence, "
                        "parameters read back; bytes per step = job bytes / iterations"}
         ttc = {"seconds_wall": round(wall, 3), "seconds_solve": round((sr.ms_total - sr.ms_structure) / 1e3, 3),
-               "structure_ms": round(sr.ms_structure, 1), "iters": sr.iters, "converged": bool(sr.converged),
+               "structure_ms": round(sr.ms_structure + 1e3 * structure_s, 1),
+               "structure_note": "structure build (the freeze inside ba_precond_set_weights, timed on the host) "
+                                 "plus any part of it inside ba_solve",
+               "iters": sr.iters, "converged": bool(sr.converged),
                "accepted": sr.accepted_steps, "pcg_iters_total": sr.total_pcg_iters, "cost0": sr.cost0,
                "cost": sr.cost, "precision": args.precision, "precond": "learned (shipped weights)"}
 
@@ -387,6 +417,35 @@ def main():
                    "note": "cameras 5-40, features log-uniform 200-20k (70% points), 0-8 groups per window; "
                            "device time of the graph launch"}
 
+    # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
+    # at the initial damping (the FP64 path itself is checked against the oracle at 2000 cameras by
+    # tests/test_gpu_scale.py)
+    mixed_err = None
+    if prec == B.BA_MIXED and not args.no_mixed_error:
+        res = {}
+        for name, pr in (("fp64", B.BA_FP64), ("mixed", B.BA_MIXED)):
+            q = B.ba_create(B.ba_default_options(precision=pr))
+            B.load_scene(q, scene)
+            E0, _ = B.ba_eval_cost(q)
+            B.ba_build_reduced(q, 1e-4)
+            _, _, vals, bvec = B.ba_export_reduced_system(q)
+            out = B.ba_compute_step(q, (len(scene["cams"]["q"]), len(scene["planes"]), len(scene["vps"]),
+                                        len(scene["points"]), len(scene["lines"])))
+            st1 = B.ba_lm_step(q)
+            B.ba_destroy(q)
+            res[name] = (E0, vals, bvec, out, st1)
+        (E64, S64, b64, o64, s64), (E32, S32, b32, o32, s32) = res["fp64"], res["mixed"]
+        rel_ = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+        d64 = np.concatenate([o64[k].ravel() for k in ("cam", "plane", "vp", "point", "line")])
+        d32 = np.concatenate([o32[k].ravel() for k in ("cam", "plane", "vp", "point", "line")])
+        mixed_err = {"S": rel_(S32, S64), "b": rel_(b32, b64), "delta": rel_(d32, d64),
+                     "pred": abs(o32["pred"] - o64["pred"]) / abs(o64["pred"]), "cost": abs(E32 - E64) / E64,
+                     "cost_new": abs(s32.cost_new - s64.cost_new) / s64.cost_new,
+                     "pcg_iters": {"fp64": o64["pcg_iters"], "mixed": o32["pcg_iters"]},
+                     "note": "max-norm relative error of the mixed path against the FP64 path, one LM step from "
+                             "the seeded start at damping 1e-4, on the benchmark scene"}
+        del res, S64, S32
+
     learned = None
     try:
         meta = json.load(open(os.path.join(ROOT, "paper_2609_04026_b300", "weights", "precond_mlp.json")))
@@ -419,6 +478,8 @@ def main():
                "time_to_equal_cost": equal,
                "batched_windows": batched, "learned_precond": learned,
                "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
+               "stage_rooflines": stages, "measured_fma_tflops": {"fp32": round(peak32, 2), "fp64": round(peak64, 3)},
+               "mixed_error": mixed_err,
                "pcg_iters": pcg_iters, "pcg_rel": pcg_rel, "reduced_system": dims_S,
                "first_step_s": round(first_step_s, 3)}
         print(json.dumps(out), flush=True)

@@ -99,7 +99,11 @@ typedef struct ba_options {
                                                     misaligned block is freed again and the call fails (BA_ERR_OOM) */
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
-  long long wait_budget_cycles; /* bound on any device-side spin wait (clock64 cycles) */
+  long long wait_budget_cycles; /* bound, in clock64 cycles, on each wait at a grid barrier of the persistent
+                                   PCG (2e9, about a second): a wait that runs out ends the solve, and the step
+                                   returns BA_ERR_TIMEOUT with the problem still usable.  The waits for the bulk
+                                   copies of S into shared memory have a fixed bound instead: a copy always
+                                   completes, and a kernel never leaves while one is in flight */
   double mixed_lambda_floor; /* BA_MIXED only: lower bound of the damping (1e-6).  The float Schur complement
                                 carries ~1e-7 relative rounding; below this damping its weakest directions sink
                                 under that noise and PCG stops converging */
@@ -183,6 +187,14 @@ ba_status ba_eval_cost(ba_problem* p, double* cost, double* cost_px);
  * go to the CUDA math library's log1p.  BA_ERR_ARG for n < 0 or a null array, BA_ERR_CUDA if a CUDA call fails.
  * An inspection call for tests of the cost's accuracy. */
 ba_status ba_eval_log1p(int64_t n, const double* x, double* y, void* cuda_stream);
+
+/* Measured FMA throughput of the current device, the denominator of the ALU rooflines: precision BA_MIXED
+ * measures the FP32 pipe, BA_FP64 the FP64 pipe.  *tflops receives 2 x FMAs per second / 1e12 (the best of
+ * three timed launches after a warm-up launch, each thread running eight independent FMA chains).  Runs on
+ * cuda_stream (NULL = default stream); allocates and frees a small device buffer.  BA_ERR_ARG for a bad
+ * precision or a null pointer, BA_ERR_CUDA if a CUDA call fails.  Not part of the paper's method: a probe for
+ * reporting achieved fractions of the arithmetic pipes. */
+ba_status ba_measure_fma_rate(int precision, double* tflops, void* cuda_stream);
 
 /* Build the damped reduced system S, b at damping lambda (linearising if needed) without stepping. */
 ba_status ba_build_reduced(ba_problem* p, double lambda);

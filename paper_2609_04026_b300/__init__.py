@@ -93,6 +93,7 @@ def _load():
         "ba_set_lm_state": (I, [P, VP]),
         "ba_eval_cost": (I, [P, C.POINTER(D), C.POINTER(D)]),
         "ba_eval_log1p": (I, [I64, VP, VP, VP]),
+        "ba_measure_fma_rate": (I, [I, C.POINTER(D), VP]),
         "ba_build_reduced": (I, [P, D]),
         "ba_reduced_size": (I, [P, C.POINTER(I64), C.POINTER(I64)]),
         "ba_export_reduced_system": (I, [P, VP, VP, VP, VP]),
@@ -314,11 +315,13 @@ def ba_reduced_size(p):
     return a.value, b.value
 
 
-def ba_export_reduced_system(p):
+def ba_export_reduced_system(p, values=True):
+    """(row_ptr, cols, vals [nb, 6, 6] or None when values=False, b [na, 6])."""
     na, nb = ba_reduced_size(p)
     rp = np.empty(na + 1, np.int32); cols = np.empty(nb, np.int32)
-    vals = np.empty((nb, 6, 6)); b = np.empty((na, 6))
-    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    vals = np.empty((nb, 6, 6)) if values else None
+    b = np.empty((na, 6))
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None
     _check(p, _lib.ba_export_reduced_system(p, ptr(rp), ptr(cols), ptr(vals), ptr(b)))
     return rp, cols, vals, b
 
@@ -399,6 +402,15 @@ def ba_eval_log1p(x, stream=None):
     return y
 
 
+def ba_measure_fma_rate(precision, stream=None):
+    """Measured FMA throughput (TFLOP/s, 2 flops per FMA) of the FP32 pipe (BA_MIXED) or FP64 pipe (BA_FP64)."""
+    v = C.c_double()
+    st = _lib.ba_measure_fma_rate(int(precision), C.byref(v), C.c_void_p(stream or 0))
+    if st != BA_OK:
+        raise BAError(st, "ba_measure_fma_rate failed")
+    return v.value
+
+
 # ---------------------------------------------------------------------------- learned preconditioner
 def ba_precond_param_count():
     return _lib.ba_precond_param_count()
@@ -450,8 +462,8 @@ def ba_precond_train(X, E, mask, params, adam_m, adam_v, t0, steps, batch, lr, s
     n = X.shape[0]
     P = ba_precond_param_count()
     _need_dev((X, torch.float32, 32 * n, "X"), (E, torch.float32, 21 * n, "E"), (mask, torch.uint8, n, "mask"),
-              (params, torch.float32, P, "params"), (adam_m, torch.float32, P, "adam_m"),
-              (adam_v, torch.float32, P, "adam_v"))
+              (params, torch.float32, P, "params"), (adam_m, torch.float32, P - 64, "adam_m"),
+              (adam_v, torch.float32, P - 64, "adam_v"))
     if n < 1 or int(batch) < 1 or int(steps) < 0 or int(t0) < 0:
         raise BAError(BA_ERR_ARG, "need n >= 1, batch >= 1, steps >= 0 and t0 >= 0")
     work = torch.empty(int(_lib.ba_mlp_work_floats(batch)) + 8, dtype=torch.float32, device=X.device)

@@ -21,16 +21,29 @@ def nvcc():
 
 
 def build(verbose=False, extra=()):
+    """Compile every source to an object in parallel (the translation units share no device code), then
+    link the shared library."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     deps.append(os.path.join(HERE, "..", "include", "ba.h"))
     if os.path.exists(OUT) and all(os.path.getmtime(d) <= os.path.getmtime(OUT) for d in deps) and not extra:
         return OUT
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "--expt-relaxed-constexpr", "-o", OUT + ".tmp", *srcs, *extra]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *extra]
+    objs, procs = [], []
+    for src in srcs:
+        obj = OUT + "." + os.path.basename(src) + ".o"
+        cmd = [nvcc(), *flags, "-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((cmd, subprocess.Popen(cmd)))
+        objs.append(obj)
+    failed = [cmd for cmd, pr in procs if pr.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
+    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT + ".tmp", *objs]
     subprocess.run(cmd, check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(OUT + ".tmp", OUT)
     return OUT
 

@@ -54,7 +54,7 @@ extern "C" void ba_default_options(ba_options* o) {
   o->precond = BA_PRECOND_BLOCK_JACOBI;
   o->cuda_stream = nullptr;
   o->wait_budget_cycles = 2000000000LL;
-  o->mixed_lambda_floor = 1e-6;
+  o->mixed_lambda_floor = 0.0;
 }
 
 extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
@@ -290,6 +290,107 @@ static ba_status plan_pcg(ba_problem* p) {
   return BA_OK;
 }
 
+// Partition of the typed storage's camera-row chunks over the CTAs of the persistent PCG (contiguous runs of
+// equal arithmetic weight, a long camera row possibly cut between CTAs) and of the group rows (slices of
+// equal size: their products are few, their sums of the CTAs' scatter are what they cost).
+static ba_status plan_pcg_typed(ba_problem* p, const TypedPlan& tp) {
+  const Dims& d = p->d;
+  const int64_t nc = d.nc, ng = d.na - d.nc;
+  int sms = 0, dev = 0;
+  CUDA_OR(p, cudaGetDevice(&dev));
+  CUDA_OR(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool mx = mixed(p);
+  const int64_t Q = (int64_t)tp.chunks.size();
+  const int64_t G = std::max<int64_t>(1, sms);
+  std::vector<double> cw(Q + 1, 0.0);
+  for (int64_t q = 0; q < Q; ++q) cw[q + 1] = cw[q] + tp.chunk_w[q];
+  std::vector<int32_t> q0s(1, 0);
+  for (int64_t q = 0; q < Q; ++q)
+    if ((int64_t)q0s.size() < G && cw[q + 1] >= cw[Q] * (double)q0s.size() / (double)G && q + 1 < Q)
+      q0s.push_back((int32_t)(q + 1));
+  while ((int64_t)q0s.size() < G + 1) q0s.push_back((int32_t)Q);
+  std::vector<int32_t> cta_part(4 * G, 0);
+  int32_t maxrows = 1;
+  int64_t rr = 0;
+  for (int64_t c = 0; c < G; ++c) {
+    const int32_t q0 = q0s[c], q1 = q0s[c + 1];
+    int32_t t0 = 0, t1 = 0;
+    if (q1 > q0) {
+      while (tp.row_chunk0[rr + 1] <= q0) ++rr;
+      t0 = (int32_t)rr;
+      int64_t re = rr;
+      while (tp.row_chunk0[re + 1] <= q1 - 1) ++re;
+      t1 = (int32_t)(re + 1);
+    }
+    cta_part[4 * c] = q0; cta_part[4 * c + 1] = q1; cta_part[4 * c + 2] = t0; cta_part[4 * c + 3] = t1;
+    maxrows = std::max(maxrows, t1 - t0);
+  }
+  // group rows in slices of about equal work: the row's group-group blocks plus its values' sums of the
+  // CTAs' scatter
+  std::vector<int32_t> gs(G + 1, (int32_t)ng);
+  {
+    std::vector<int32_t> ggp(ng + 1);
+    if (ng) CUDA_OR(p, cudaMemcpy(ggp.data(), p->gg_ptr, sizeof(int32_t) * (ng + 1), cudaMemcpyDeviceToHost));
+    else ggp[0] = 0;
+    auto wrow = [&](int64_t g) { return (double)(ggp[g + 1] - ggp[g]) + 4.0; };
+    double tot = 0;
+    for (int64_t g = 0; g < ng; ++g) tot += wrow(g);
+    gs[0] = 0;
+    int64_t c = 1;
+    double acc = 0;
+    for (int64_t g = 0; g < ng && c < G; ++g) {
+      acc += wrow(g);
+      while (c < G && acc >= tot * (double)c / (double)G) gs[c++] = (int32_t)(g + 1);
+    }
+    for (; c <= G; ++c) gs[c] = (int32_t)ng;
+    // the products of a slice's group-group blocks are staged in the group accumulators' shared memory
+    int64_t maxgg = 0;
+    for (int64_t c2 = 0; c2 < G; ++c2) maxgg = std::max<int64_t>(maxgg, ggp[gs[c2 + 1]] - ggp[gs[c2]]);
+    const size_t gacc_bytes = mx ? pcg_typed_gacc_bytes<float>(p->gv) : pcg_typed_gacc_bytes<double>(p->gv);
+    if ((size_t)maxgg * 6 * (mx ? 2 * sizeof(float) : sizeof(double)) > gacc_bytes)
+      return set_err(p, BA_ERR_ARG, "group rows with too many group-group blocks for the typed PCG");
+  }
+  std::vector<int32_t> gvi(std::max(p->gv, 1), 0);
+  for (int64_t g = 0; g < d.npl; ++g)
+    for (int k = 0; k < 3; ++k) gvi[3 * g + k] = (int32_t)(6 * (nc + g) + k);
+  for (int64_t v = 0; v < d.nv; ++v)
+    for (int k = 0; k < 2; ++k) gvi[3 * d.npl + 2 * v + k] = (int32_t)(6 * (nc + d.npl + v) + k);
+  // shared memory: the fixed part (stage, group accumulators and operands) and one segment of 6 sums per
+  // (warp, camera row it touches)
+  const size_t seg = (mx ? sizeof(float) * 2 : sizeof(double)) * 6 * ((size_t)maxrows + 16);
+  const size_t smem = (mx ? pcg_typed_fixed_smem<float>(p->gv) : pcg_typed_fixed_smem<double>(p->gv)) + seg;
+  if (smem > 227 * 1024)
+    return set_err(p, BA_ERR_ARG, "reduced system too large or irregular for the PCG partition");
+  const int per_sm = mx ? pcg_typed_blocks_per_sm<float>(smem) : pcg_typed_blocks_per_sm<double>(smem);
+  if (per_sm < 1) return set_err(p, BA_ERR_ARG, "no cooperative PCG launch configuration fits");
+  p->pcg_grid = (int)G;
+  p->pcg_smem = smem;
+  {
+    // share of S kept in L2 across PCG iterations (fetched evict_last; the rest streams evict_first)
+    constexpr double kKeepBytes = 60.0 * 1048576.0;
+    const double sbytes = (double)p->gg_val0 * (mx ? sizeof(float) : sizeof(double)) + 128.0 * (double)Q;
+    p->pcg_keep_frac = sbytes > 0 ? (float)std::min(1.0, kKeepBytes / sbytes) : 0.f;
+  }
+  ba_status s;
+  auto up = [&](int32_t*& dst, const std::vector<int32_t>& v) -> ba_status {
+    dst = p->dnew<int32_t>((int64_t)v.size());
+    if (!dst) return set_err(p, BA_ERR_OOM, "device allocation failed");
+    CUDA_OR(p, cudaMemcpyAsync(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, p->stream));
+    return BA_OK;
+  };
+  p->pcg_carry = p->dnew<double>(6 * G);
+  p->part_g = p->dnew<double>(G * std::max(p->gv, 1));
+  p->tchunk = p->dnew<int4>(std::max<int64_t>(Q, 1));
+  if (!p->pcg_carry || !p->part_g || !p->tchunk) return set_err(p, BA_ERR_OOM, "device allocation failed");
+  if (Q) CUDA_OR(p, cudaMemcpyAsync(p->tchunk, tp.chunks.data(), sizeof(int4) * Q, cudaMemcpyHostToDevice, p->stream));
+  if ((s = up(p->cta_part, cta_part))) return s;
+  if ((s = up(p->row_chunk0, tp.row_chunk0))) return s;
+  if ((s = up(p->cta_gs, gs))) return s;
+  if ((s = up(p->gv_idx, gvi))) return s;
+  CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
 static ba_status freeze(ba_problem* p) {
   if (p->frozen) return BA_OK;
   if (p->h_cam.empty() && p->h_pts.empty() && p->h_lin.empty()) return set_err(p, BA_ERR_STATE, "empty problem");
@@ -298,6 +399,7 @@ static ba_status freeze(ba_problem* p) {
   p->frozen = true;
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
+  p->gv = (int)(3 * d.npl + 2 * d.nv);
   auto A = [&](void*& dst, size_t bytes) -> bool {
     dst = p->dalloc(bytes);
     return dst != nullptr;
@@ -310,7 +412,6 @@ static ba_status freeze(ba_problem* p) {
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
   ok &= A(p->slotBS, T * SBS * (size_t)d.ne);
-  ok &= A(p->Sval, T * BS2 * (size_t)d.nbp);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
   p->featg = p->dnew<double>(4 * d.nf); p->featu = p->dnew<double>(4 * d.nf); p->dfeat = p->dnew<double>(4 * d.nf);
@@ -335,7 +436,6 @@ static ba_status freeze(ba_problem* p) {
   // one-time zero fill of the slot and feature arrays
   CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
-  CUDA_OR(p, cudaMemsetAsync(p->Sval, 0, T * BS2 * (size_t)d.nbp, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
   if (mixed(p) && d.nr) {
@@ -347,7 +447,6 @@ static ba_status freeze(ba_problem* p) {
     CUDA_OR(p, cudaMemcpyAsync(p->measT, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, p->stream));
     CUDA_OR(p, cudaStreamSynchronize(p->stream));
   }
-  if ((s = plan_pcg(p))) return s;
   CUDA_OR(p, cudaMallocHost((void**)&p->hS, sizeof(DevScalars)));
   std::memset(p->hS, 0, sizeof(DevScalars));
   p->hS->lambda = p->opt.lambda0;
@@ -362,6 +461,34 @@ static ba_status freeze(ba_problem* p) {
   CUDA_OR(p, cudaGetLastError());
   CUDA_OR(p, cudaMemcpyAsync(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
   CUDA_OR(p, cudaStreamSynchronize(p->stream));
+  return BA_OK;
+}
+
+// The storage of S and the PCG partition, made when S is first built.  A window of ba_solve_batch
+// (for_batch), whose single-CTA kernels read S in full (both triangles, 6 x 6), keeps the full storage; a
+// problem stepped on its own takes the typed storage when its group values fit (see TY_CC).
+static ba_status ensure_sstore(ba_problem* p, bool for_batch) {
+  if (p->Sval) return BA_OK;
+  const Dims& d = p->d;
+  const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
+  p->typed = !for_batch && d.nc > 0 && 3 * d.npl + 2 * d.nv <= GV_MAX;
+  ba_status s;
+  if (p->typed) {
+    TypedPlan tplan;
+    if ((s = build_typed_storage(*p, tplan))) return s;
+    // a partition whose shared memory does not fit (very many short camera rows on one CTA) takes the full
+    // storage instead
+    if (plan_pcg_typed(p, tplan) != BA_OK) {
+      if (p->pcg_grid) return BA_ERR_OOM;
+      p->typed = false;
+      p->err.clear();
+    }
+  }
+  if (!p->typed && (s = plan_pcg(p))) return s;
+  const size_t nsval = p->typed ? (size_t)p->tvals : (size_t)BS2 * d.nbp;
+  p->Sval = p->dalloc(T * nsval);
+  if (!p->Sval) return set_err(p, BA_ERR_OOM, "device allocation failed");
+  CUDA_OR(p, cudaMemsetAsync(p->Sval, 0, T * nsval, p->stream));
   return BA_OK;
 }
 
@@ -383,6 +510,8 @@ static ba_status sync_scalars(ba_problem* p) {
 
 template <class T>
 static ba_status build_reduced_t(ba_problem* p, double lambda, bool* relin) {
+  ba_status s0 = ensure_sstore(p, false);
+  if (s0) return s0;
   if (!p->have_lin) {
     launch_prepare<T>(*p, false);
     launch_linearize<T>(*p);
@@ -585,6 +714,15 @@ extern "C" ba_status ba_eval_log1p(int64_t n, const double* x, double* y, void* 
   return BA_OK;
 }
 
+extern "C" ba_status ba_measure_fma_rate(int precision, double* tflops, void* cuda_stream) {
+  if (!tflops || (precision != BA_FP64 && precision != BA_MIXED)) return BA_ERR_ARG;
+  if (fma_probe(precision, tflops, (cudaStream_t)cuda_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BA_ERR_CUDA;
+  }
+  return BA_OK;
+}
+
 extern "C" ba_status ba_build_reduced(ba_problem* p, double lambda) {
   if (!p) return BA_ERR_ARG;
   if (!(lambda >= 0) || !std::isfinite(lambda)) return set_err(p, BA_ERR_ARG, "lambda must be finite and >= 0");
@@ -610,12 +748,14 @@ extern "C" ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, i
   if (!p->have_reduced) return set_err(p, BA_ERR_STATE, "no reduced system built (call ba_build_reduced)");
   const Dims& d = p->d;
   ba_status s;
-  // the device storage is padded and interleaved; the export is plain block-CSR of the stored blocks
-  std::vector<int32_t> pc(d.nbp);
+  // the device storage is padded (full or typed, see SView); the export is plain block-CSR of every block,
+  // both triangles, 6 x 6
+  std::vector<int32_t> pc(d.nbp), hsel;
   if ((s = put_out(p, BA_MEM_HOST, pc.data(), (const int32_t*)p->col, d.nbp))) return s;
   std::vector<double> pv;
+  const size_t nsval = p->typed ? (size_t)p->tvals : (size_t)BS2 * d.nbp;
   if (vals) {
-    pv.resize((size_t)BS2 * d.nbp);
+    pv.resize(nsval);
     if (mixed(p)) {
       std::vector<float> h(pv.size());
       if ((s = put_out(p, BA_MEM_HOST, h.data(), (const float*)p->Sval, h.size()))) return s;
@@ -623,15 +763,24 @@ extern "C" ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, i
     } else if ((s = put_out(p, BA_MEM_HOST, pv.data(), (const double*)p->Sval, pv.size()))) {
       return s;
     }
+    if (p->typed) {
+      hsel.resize(d.nbp);
+      if ((s = put_out(p, BA_MEM_HOST, hsel.data(), (const int32_t*)p->sel, d.nbp))) return s;
+    }
   }
+  SView hv;
+  if (p->typed) { hv.sel = hsel.data(); hv.col = pc.data(); hv.nc = d.nc; hv.npl = d.npl; hv.gg_val0 = p->gg_val0; }
   int64_t o = 0;
   if (row_ptr) row_ptr[0] = 0;
   for (int64_t a = 0; a < d.na; ++a) {
     for (int32_t k = 0; k < p->h_row_len[a]; ++k, ++o) {
       const int64_t q = p->h_prow_ptr[a] + k;
       if (cols) cols[o] = pc[q];
-      if (vals)
-        for (int e = 0; e < BS2; ++e) vals[(size_t)o * BS2 + e] = pv[s_idx(q, e)];
+      if (vals) {
+        double blk[36];
+        sview_load(hv, pv.data(), q, a, blk);
+        for (int e = 0; e < BS2; ++e) vals[(size_t)o * BS2 + e] = blk[e];
+      }
     }
     if (row_ptr) row_ptr[a + 1] = (int32_t)o;
   }
@@ -890,7 +1039,12 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
       return set_err(p0, BA_ERR_ARG, "all windows of a batch must use the same precision");
     if (p->device != p0->device) return set_err(p0, BA_ERR_ARG, "all windows of a batch must be on one device");
     ba_status s = freeze(p);
+    if (!s) s = ensure_sstore(p, true);
     if (s) return set_err(p0, s, "window " + std::to_string(i) + ": " + p->err);
+    if (p->typed)
+      return set_err(p0, BA_ERR_STATE, "window " + std::to_string(i) +
+                                           ": a problem already stepped on its own cannot join a batch (its reduced "
+                                           "system has the typed storage of the grid path)");
     if (reports) reports[i].cost0 = p->hS->E;
   }
   std::vector<double> c0(n);

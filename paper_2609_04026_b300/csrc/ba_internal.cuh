@@ -66,7 +66,66 @@ constexpr int SBS = 6;  // back-substitution record per slot (6 values, unpadded
 
 enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
 
-constexpr int PCG_FLAG_TIMEOUT = 8;   // DevScalars::flags bit: a TMA copy of S did not complete in time
+constexpr int PCG_FLAG_TIMEOUT = 8;   // DevScalars::flags bit: a bounded device-side wait of the PCG ran out
+
+// Typed storage of the reduced system (the main path).  A camera row holds its camera-camera blocks (both
+// triangles, 6 x 6), then its camera-plane blocks (6 x 3) and camera-VP blocks (6 x 2) at their real widths;
+// each of the three runs is padded to whole chunks of 32 blocks.  The camera-group blocks are stored only
+// there: a group row's camera part is the transpose, which the PCG forms from the camera rows (a scatter
+// into per-warp accumulators of the group values).  A group row keeps its few group-group blocks (6 x 6).
+constexpr int TY_CC = 0, TY_CP = 1, TY_CV = 2;
+constexpr int TCHUNK = 32;             // blocks per chunk (one per lane)
+constexpr int GV_MAX = 1400;           // group values (3 per plane, 2 per VP) the typed storage supports
+constexpr int GV_PAD = 4;              // dummy group values behind the real ones (targets of padding blocks)
+constexpr uint32_t SEL_MIRROR = 0x80000000u;   // sel[] flag: only the transposed copy of this block is stored
+__host__ __device__ __forceinline__ int ty_vals(int ty) { return ty == TY_CC ? 36 : (ty == TY_CP ? 18 : 12); }
+
+// Where the blocks of the reduced system live, addressed by their position q in the full padded block-CSR
+// pattern (row_ptr / col).  Full storage (sel == null, batched windows): block q at 36 q, row-major 6 x 6.
+// Typed storage: sel[q] as above; a stored block is 6 x 6 except a camera row's camera-group block, which is
+// 6 x 3 (plane) or 6 x 2 (VP), row-major.
+struct SView {
+  const int32_t* sel = nullptr;
+  const int32_t* col = nullptr;
+  int64_t nc = 0, npl = 0, gg_val0 = 0;
+};
+// width of the stored copy at typed offset o of a block in column c (the copy itself, not a mirror)
+__host__ __device__ __forceinline__ int sview_width(const SView& v, int64_t o, int64_t c) {
+  return (o < v.gg_val0 && c >= v.nc) ? (c < v.nc + v.npl ? 3 : 2) : 6;
+}
+// the padded 6 x 6 block at position q of row r (zeros beyond a narrow block's width; the transpose of the
+// stored copy when only the mirror is stored; all zeros for a padding position)
+template <class T>
+__host__ __device__ __forceinline__ void sview_load(const SView& v, const T* Sval, int64_t q, int64_t r, double (&out)[36]) {
+  if (!v.sel) {
+    for (int e = 0; e < 36; ++e) out[e] = (double)Sval[36 * q + e];
+    return;
+  }
+  for (int e = 0; e < 36; ++e) out[e] = 0.0;
+  const int32_t s = v.sel[q];
+  if (s == -1) return;
+  const int64_t o = (int64_t)(s & 0x7fffffff);
+  if (!((uint32_t)s & SEL_MIRROR)) {
+    const int w = sview_width(v, o, v.col[q]);
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < w; ++j) out[i * 6 + j] = (double)Sval[o + i * w + j];
+  } else {
+    const int w = r < v.nc + v.npl ? 3 : 2;   // the stored copy is camera row col[q]'s block of group r
+    for (int i = 0; i < w; ++i)
+      for (int j = 0; j < 6; ++j) out[i * 6 + j] = (double)Sval[o + j * w + i];
+  }
+}
+// where a writer puts the block at position q: element offset and width, or width 0 when it is not stored there
+struct BlkTarget {
+  int64_t off;
+  int w;
+};
+__host__ __device__ __forceinline__ BlkTarget sview_target(const SView& v, int64_t q) {
+  if (!v.sel) return BlkTarget{36 * q, 6};
+  const int32_t s = v.sel[q];
+  if (s == -1 || ((uint32_t)s & SEL_MIRROR)) return BlkTarget{0, 0};
+  return BlkTarget{(int64_t)s, sview_width(v, s, v.col[q])};
+}
 
 // scalars kept on the device so that PCG and the LM decision need no host round trip
 struct DevScalars {
@@ -75,8 +134,9 @@ struct DevScalars {
   double lambda, nu, gain;
   int iters, max_iters, done, accepted;
   int flags;                 // bit 0: a landmark block needed extra damping; bit 1: non-finite value;
-                             // bit 2: a block-Jacobi block fell back to its diagonal; bit 3: PCG copy timeout
+                             // bit 2: a block-Jacobi block fell back to its diagonal; bit 3: PCG wait timeout
   unsigned int counter[8];   // arrival counters of the last-block reductions
+  unsigned int bar_count, bar_gen;   // grid barrier of the persistent PCG (count reset before every launch)
 };
 
 // the frozen problem structure (built once, K0) plus every device array
@@ -99,6 +159,9 @@ template <class T> void launch_precond(Problem& P);
 template <class T> void launch_pcg(Problem& P);
 template <class T> int pcg_blocks_per_sm(size_t smem);
 template <class T> void pcg_allow_smem(size_t smem);
+template <class T> size_t pcg_typed_fixed_smem(int gv);
+template <class T> size_t pcg_typed_gacc_bytes(int gv);
+template <class T> int pcg_typed_blocks_per_sm(size_t smem);
 constexpr int PCG_CHUNK = 64;   // stored blocks per SpMV chunk (caller-layout path)
 
 // position of entry e (row-major 6 x 6) of the block at padded position q in the storage of S: blocks are
@@ -109,6 +172,7 @@ void launch_candidate(Problem& P);
 void launch_cost(Problem& P, bool candidate);
 cudaError_t ensure_ln1p_table(cudaStream_t st);   // the FP64 cost's logarithm table on the current device
 cudaError_t launch_ln1p_eval(cudaStream_t st, int64_t n, const double* x, double* y);
+cudaError_t fma_probe(int precision, double* tflops, cudaStream_t st);   // FP32 / FP64 FMA throughput
 void launch_decide(Problem& P);
 
 }  // namespace ba
@@ -193,6 +257,16 @@ struct ba_problem {
   int32_t* cta_part = nullptr;
   double* pcg_carry = nullptr;
   float pcg_keep_frac = 0.f;   // fraction of S the PCG keeps resident in L2 across iterations
+  // typed storage (see TY_CC): sel[q] = element offset of the stored copy of the block at full padded position q
+  // (| SEL_MIRROR when only its transpose is stored, -1 for padding); per typed block its column code (camera
+  // entity, or the group value offset of a camera-group block); per chunk {value offset, first block, row,
+  // type}; per group row its group-group blocks; per CTA its slice of group rows; the group-value table
+  bool typed = false;
+  int gv = 0;                    // group values 3 npl + 2 nv
+  int32_t *sel = nullptr, *tcol = nullptr, *gg_ptr = nullptr, *gg_col = nullptr, *cta_gs = nullptr, *gv_idx = nullptr;
+  int4* tchunk = nullptr;
+  int64_t tvals = 0, gg_val0 = 0;   // values of the typed storage; first value of the group-group region
+  double* part_g = nullptr;      // per group value, every CTA's share of the scatter (gv x G)
   int pcg_grid = 0;
   size_t pcg_smem = 0;
   cudaError_t pcg_err = cudaSuccess;
@@ -226,6 +300,15 @@ struct ba_problem {
 
 namespace ba {
 ba_status build_structure(Problem& P);   // structure.cu
+// typed storage of the reduced system (structure.cu): per full position its stored copy, column codes of the
+// typed blocks, and the host plan of chunks; see TY_CC
+struct TypedPlan {
+  std::vector<int32_t> row_chunk0;   // camera row r's chunks [row_chunk0[r], row_chunk0[r + 1])
+  std::vector<int32_t> chunk_w;      // per chunk its arithmetic weight (for the CTA partition)
+  std::vector<int4> chunks;          // per chunk {value offset, first block, camera row, type}
+};
+ba_status build_typed_storage(Problem& P, TypedPlan& plan);
+SView sview_of(const Problem& P);
 // batched windows (kernels.cu, launched from batch.cu)
 template <class T> void fill_window_desc(Problem& P, void* out);
 template <class T> size_t window_desc_size();

@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "ba_internal.cuh"
 
@@ -722,6 +723,7 @@ struct BlockArgs {
   const int32_t *up_row, *up_full, *up_mirror, *col;
   const uint8_t *ent_type, *cam_fixed;
   T* Sval;
+  SView sv;        // where each block of S is stored (full or typed storage)
   double *b, *Dg, *sdiag;
   int64_t nc;
   double lambda;
@@ -821,8 +823,9 @@ __device__ void finish_diag(const BlockArgs<T>& a, int row, int fpos, double (&s
       a.b[6 * (size_t)row + i] = 0;
     }
   }
+  const BlkTarget tg = sview_target(a.sv, fpos);   // a diagonal block is stored whole (6 x 6)
 #pragma unroll
-  for (int i = 0; i < 36; ++i) a.Sval[s_idx(fpos, i)] = (T)s[i];
+  for (int i = 0; i < 36; ++i) a.Sval[tg.off + i] = (T)s[i];
 #pragma unroll
   for (int i = 0; i < 6; ++i) a.sdiag[6 * (size_t)row + i] = (double)(T)s[i * 6 + i];
 }
@@ -850,13 +853,14 @@ __device__ void unit_finish(const UnitArgs<T>& a, int u) {
     return;
   }
   const int mpos = a.fb.up_mirror[u];
+  const BlkTarget tm = sview_target(a.fb.sv, fpos), tt = sview_target(a.fb.sv, mpos);
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const T v = (T)s[i * 6 + j];
-      a.fb.Sval[s_idx(fpos, i * 6 + j)] = v;
-      a.fb.Sval[s_idx(mpos, j * 6 + i)] = v;
+      if (j < tm.w) a.fb.Sval[tm.off + i * tm.w + j] = v;
+      if (i < tt.w) a.fb.Sval[tt.off + j * tt.w + i] = v;
     }
 }
 
@@ -978,6 +982,8 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
   __syncwarp();
   const int ne = diag ? 48 : 36;
   const int mpos = mf >> 2;
+  BlkTarget tm{0, 0}, tt{0, 0};
+  if (direct) { tm = sview_target(a.fb.sv, fpos); tt = sview_target(a.fb.sv, mpos); }
   for (int e = lane; e < ne; e += 32) {
     PartSum<T> sm;
     for (int k = 0; k < 32; ++k) sm.add(red[k * RS + e]);
@@ -985,8 +991,9 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
       a.upart[(size_t)w * 48 + e] = sm.value();
     } else {
       const T v = (T)sm.rounded();
-      a.fb.Sval[s_idx(fpos, e)] = v;
-      a.fb.Sval[s_idx(mpos, (e % 6) * 6 + e / 6)] = v;
+      const int i = e / 6, j = e % 6;
+      if (j < tm.w) a.fb.Sval[tm.off + i * tm.w + j] = v;
+      if (i < tt.w) a.fb.Sval[tt.off + j * tt.w + i] = v;
     }
   }
   __syncwarp();   // the next unit of this warp reuses the shared memory
@@ -1077,8 +1084,10 @@ __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_packs(UnitArgs<T
     PartSum<T> sm;
     for (int k = seg[i]; k < seg[i + 1]; ++k) sm.add(red[k * RS + e]);
     const T v = (T)sm.rounded();
-    a.fb.Sval[s_idx(fp[i], e)] = v;
-    a.fb.Sval[s_idx(mp[i], (e % 6) * 6 + e / 6)] = v;
+    const BlkTarget tm = sview_target(a.fb.sv, fp[i]), tt = sview_target(a.fb.sv, mp[i]);
+    const int ei = e / 6, ej = e % 6;
+    if (ej < tm.w) a.fb.Sval[tm.off + ei * tm.w + ej] = v;
+    if (ei < tt.w) a.fb.Sval[tt.off + ej * tt.w + ei] = v;
   }
 }
 
@@ -1088,16 +1097,18 @@ __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_packs(UnitArgs<T
 // SOA: S in the library's padded interleaved storage; otherwise 36 contiguous values per block
 template <class T, bool SOA>
 __device__ void precond_row(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                            const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S, int64_t a) {
+                            const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S, int64_t a,
+                            const SView& sv) {
   int pos = -1;
   for (int q = row_ptr[a]; q < row_ptr[a + 1]; ++q)
     if (col[q] == a) { pos = q; break; }
+  // the diagonal block is stored whole in either storage
+  const int64_t dof = SOA ? sview_target(sv, pos).off : (int64_t)pos * BS2;
   double Aup[21];
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int j = i; j < 6; ++j)
-      Aup[up_idx(i, j, 6)] = (double)(SOA ? Sval[s_idx(pos, i * 6 + j)] : Sval[(size_t)pos * BS2 + i * 6 + j]);
+    for (int j = i; j < 6; ++j) Aup[up_idx(i, j, 6)] = (double)Sval[dof + i * 6 + j];
   double Mi[6][6];
   if (!chol_inverse<6>(Aup, Mi)) {
     atomicOr(&S->flags, 4);
@@ -1115,9 +1126,9 @@ __device__ void precond_row(const int32_t* __restrict__ row_ptr, const int32_t* 
 
 template <class T, bool SOA>
 __global__ void k_precond(int64_t na, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                          const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S) {
+                          const T* __restrict__ Sval, T* __restrict__ Minv, DevScalars* S, SView sv) {
   int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a < na) precond_row<T, SOA>(row_ptr, col, Sval, Minv, S, a);
+  if (a < na) precond_row<T, SOA>(row_ptr, col, Sval, Minv, S, a, sv);
 }
 
 // ============================================================================
@@ -1276,6 +1287,7 @@ struct PcgArgs {
   DevScalars* S;
   double tol;
   int max_iters;
+  long long budget;   // clock64 cycles a grid barrier may wait
 };
 
 // one stored block times the gathered p block: FP64 FMAs for double S; for float S the pre-split
@@ -1328,12 +1340,41 @@ __device__ __forceinline__ void grid_partials2(const double* part, int G, double
   __syncthreads();
 }
 
+// ---- a grid barrier for the persistent PCG kernels.  The launch is cooperative, so every CTA is resident;
+// the wait is still bounded, by `budget` clock64 cycles (ba_options.wait_budget_cycles).  A CTA whose wait
+// runs out records PCG_FLAG_TIMEOUT.  The result is the same for every thread of the CTA: false when this
+// CTA's wait ran out or any CTA has recorded a timeout, and the kernel then leaves its iteration.  The
+// arrival count is reset on the host before every launch; the generation word only ever advances.
+__device__ __forceinline__ bool grid_barrier(DevScalars* S, unsigned G, long long budget) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* genp = &S->bar_gen;
+    const unsigned g0 = *genp;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&S->bar_count, 1u) == G - 1) {
+      atomicExch(&S->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&S->bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*genp == g0)
+        if (clock64() - t0 > budget) { ok = 0; break; }
+    }
+    __threadfence();
+    if (!ok) atomicOr(&S->flags, PCG_FLAG_TIMEOUT);
+    if (*(volatile int*)&S->flags & PCG_FLAG_TIMEOUT) ok = 0;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
 // SOA: S in the padded interleaved storage, chunks of exactly 32 blocks (one per lane, coalesced
 // loads); otherwise contiguous blocks and chunks of up to PCG_CHUNK blocks strided over the lanes
 template <class T, int NT, bool SOA>
 __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
   extern __shared__ double chunk_mem[];   // [chunks of this CTA][6] accumulators
   DotAcc<T>* chunk_y = reinterpret_cast<DotAcc<T>*>(chunk_mem);
   __shared__ double bc[2];
@@ -1365,14 +1406,14 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
   }
   cta_sum2<NT>(v0, v1, cta_out);
   if (threadIdx.x == 0) { partC[2 * c] = cta_out[0]; partC[2 * c + 1] = cta_out[1]; }
-  grid.sync();
+  const bool go = grid_barrier(a.S, (unsigned)G, a.budget);
   grid_partials2(partC, G, bc);
   double rz = bc[0];
   const double bb = bc[1];
   const double tol2 = a.tol * a.tol * bb;
   double rr = bb;
   int it = 0;
-  bool done = !(bb > 0);
+  bool done = !go || !(bb > 0);
   while (!done) {
     // ---- A: Ap = S p by chunks, then per row in chunk order; partial p.Ap
     for (int q = q0 + warp; q < q1; q += NW) {
@@ -1415,7 +1456,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
     }
     cta_sum2<NT>(pap, 0.0, cta_out);
     if (threadIdx.x == 0) { partA[2 * c] = cta_out[0]; partA[2 * c + 1] = 0; }
-    grid.sync();
+    if (!grid_barrier(a.S, (unsigned)G, a.budget)) break;
     grid_partials2(partA, G, bc);
     const double alpha = rz / bc[0];
     // ---- B: x += alpha p, r -= alpha Ap, z = M^-1 r; partial r.r, r.z
@@ -1438,7 +1479,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
     }
     cta_sum2<NT>(v0, v1, cta_out);
     if (threadIdx.x == 0) { partB[2 * c] = cta_out[0]; partB[2 * c + 1] = cta_out[1]; }
-    grid.sync();
+    if (!grid_barrier(a.S, (unsigned)G, a.budget)) break;
     grid_partials2(partB, G, bc);
     rr = bc[0];
     const double rz_new = bc[1];
@@ -1452,7 +1493,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persistent(PcgArgs<T> a) {
       a.p[k] = pk;
       if (a.phl) a.phl[k] = split2(pk);
     }
-    grid.sync();
+    if (!grid_barrier(a.S, (unsigned)G, a.budget)) break;
   }
   if (c == 0 && threadIdx.x == 0) {
     a.S->iters = it;
@@ -1544,6 +1585,7 @@ struct PcgStreamArgs {
   double tol;
   int max_iters;
   float keep_frac;   // fraction of every warp's chunks fetched with L2 evict_last (kept across iterations)
+  long long budget;  // clock64 cycles a grid barrier may wait
 };
 
 template <class T>
@@ -1591,8 +1633,6 @@ struct UVal<double> {
 
 template <class T, int NT, int NBUF>
 __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
   constexpr int NW = NT / 32;
   constexpr unsigned CHB = (unsigned)stream_chunk_bytes<T>();
   constexpr int SPIN = 1 << 22;
@@ -1779,13 +1819,19 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   precondition(ru, rrl);
   cta_sum2<NT>(ru, rrl, cta_out);
   if (threadIdx.x == 0) { slot(0, 0)[c] = cta_out[0]; slot(0, 1)[c] = cta_out[1]; }
-  grid.sync();
-  spmv(wu);
-  cta_sum2<NT>(wu, 0.0, cta_out);
-  if (threadIdx.x == 0) slot(0, 2)[c] = cta_out[0];
-  if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
-  grid.sync();
-  add_carries();   // ordered before the vector updates by the barriers inside reduce3
+  // a copy wait that ran out (in any warp) is recorded before the barrier; the barrier's answer is uniform
+  auto sync = [&]() -> bool {
+    if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
+    return grid_barrier(a.S, (unsigned)G, a.budget);
+  };
+  bool go = sync();
+  if (go) {
+    spmv(wu);
+    cta_sum2<NT>(wu, 0.0, cta_out);
+    if (threadIdx.x == 0) slot(0, 2)[c] = cta_out[0];
+    go = sync();
+  }
+  if (go) add_carries();   // ordered before the vector updates by the barriers inside reduce3
   auto reduce3 = [&](int par) {   // the three global sums, formed identically in every CTA
     double s0 = 0, s1 = 0, s2 = 0;
     for (int g = threadIdx.x; g < G; g += NT) {
@@ -1805,14 +1851,14 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     }
     __syncthreads();
   };
-  reduce3(0);
-  double gam = bc[0];
-  const double bb = bc[1];
-  double alpha = bc[2] > 0 ? gam / bc[2] : 0.0;
+  if (go) reduce3(0);
+  double gam = go ? bc[0] : 0.0;
+  const double bb = go ? bc[1] : 0.0;
+  double alpha = go && bc[2] > 0 ? gam / bc[2] : 0.0;
   const double tol2 = a.tol * a.tol * bb;
   double rr = bb;
   int it = 0;
-  bool done = !(bb > 0) || !(bc[2] > 0) || (*(volatile int*)&a.S->flags & PCG_FLAG_TIMEOUT);
+  bool done = !go || !(bb > 0) || !(bc[2] > 0);
   double beta = 0;
   int par = 1;
   while (!done) {
@@ -1832,17 +1878,566 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
     cta_sum2<NT>(ru, rrl, cta_out);
     if (threadIdx.x == 0) { slot(par, 0)[c] = cta_out[0]; slot(par, 1)[c] = cta_out[1]; }
     ++it;
-    grid.sync();
+    if (!sync()) break;
     spmv(wu);
     cta_sum2<NT>(wu, 0.0, cta_out);
     if (threadIdx.x == 0) slot(par, 2)[c] = cta_out[0];
-    if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
-    grid.sync();
+    if (!sync()) break;
     add_carries();
     reduce3(par);
     const double gam_new = bc[0], delta = bc[2];
     rr = bc[1];
-    if (rr <= tol2 || it >= a.max_iters || !(rr == rr) || (*(volatile int*)&a.S->flags & PCG_FLAG_TIMEOUT)) break;
+    if (rr <= tol2 || it >= a.max_iters || !(rr == rr)) break;
+    beta = gam_new / gam;
+    const double den = delta - beta * gam_new / alpha;
+    alpha = gam_new / den;
+    gam = gam_new;
+    if (!(den > 0)) break;   // S not positive definite along p (rounding): keep the current x
+    par ^= 1;
+  }
+  drain();
+  if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
+  if (c == 0 && threadIdx.x == 0) {
+    a.S->iters = it;
+    a.S->rr = rr;
+    a.S->bnorm2 = bb;
+    a.S->rz = gam;
+    a.S->done = 1;
+  }
+}
+
+// ============================================================================
+// K5/K6 on the typed storage: camera rows stream their camera-camera, camera-plane and camera-VP chunks;
+// every camera-group block also adds its transpose times the camera's u to the group's values
+// (a per-warp shared-memory accumulator: the blocks of one chunk lie in one camera row and so name
+// distinct groups), and the CTAs' group partials are summed in CTA order after the grid barrier.
+// ============================================================================
+template <class T>
+struct PcgTypedArgs {
+  int64_t na, nc, npl;
+  int gv;                         // group values: 3 per plane, 2 per VP
+  const int32_t *tcol, *row_chunk0, *gg_ptr, *gg_col, *cta_gs, *gv_idx;
+  const int4* tchunk;             // per chunk {value offset, first block, camera row, type}
+  const int4* cta_part;           // per CTA {q0, q1, t0, t1} over the camera rows' chunks
+  double* carry;                  // per CTA: its partial w of its first camera row when another CTA owns it
+  double* part_g;                 // per group value, every CTA's scatter into it (gv x G)
+  const T *Sv, *Minv;
+  int64_t gg_val0;                // first value of the group-group blocks in Sv
+  const double* b;
+  double *x, *r, *u, *p, *w, *s;
+  float2* uhl;                    // float working type: u split into (hi, lo) floats
+  double* part;                   // per-CTA partial sums, two parity slots of 3 x G
+  DevScalars* S;
+  double tol;
+  int max_iters;
+  float keep_frac;
+  long long budget;
+};
+
+// one operand value: the (hi, lo) split of an FP64 value for float S, the value itself for double S
+template <class T>
+struct XV;
+template <>
+struct XV<float> {
+  float h, l;
+  __device__ __forceinline__ void set(const float2 v) { h = v.x; l = v.y; }
+};
+template <>
+struct XV<double> {
+  double v;
+};
+// acc += b * x: for float a double-single step (exact product by FMA, TwoSum into the running sum,
+// the same operations as block_dot6_split); for double one FMA
+__device__ __forceinline__ void ds_madd(DotAcc<float>& a, float b, const XV<float>& x) {
+  const float ph = b * x.h;
+  const float pe = fmaf(b, x.h, -ph);
+  const float sm = a.hi + ph;
+  const float bp = sm - a.hi;
+  const float err = (a.hi - (sm - bp)) + (ph - bp);
+  a.hi = sm;
+  a.lo += err + fmaf(b, x.l, pe);
+}
+__device__ __forceinline__ void ds_madd(DotAcc<double>& a, double b, const XV<double>& x) { a.s = fma(b, x.v, a.s); }
+
+__device__ __forceinline__ void load_xv(const PcgTypedArgs<float>& a, size_t i, XV<float>& x) { x.set(__ldcg(&a.uhl[i])); }
+__device__ __forceinline__ void load_xv(const PcgTypedArgs<double>& a, size_t i, XV<double>& x) { x.v = __ldcg(&a.u[i]); }
+
+// n contiguous values of a lane's block from the stage buffer (16-byte aligned for 36 and 12 floats and for
+// every double block; 8-byte aligned for 18 floats)
+template <int N>
+__device__ __forceinline__ void load_vals(const float* p, float (&B)[N]) {
+  if constexpr (N % 4 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 t = q[k];
+      B[4 * k] = t.x; B[4 * k + 1] = t.y; B[4 * k + 2] = t.z; B[4 * k + 3] = t.w;
+    }
+  } else {
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const float2 t = q[k];
+      B[2 * k] = t.x; B[2 * k + 1] = t.y;
+    }
+  }
+}
+template <int N>
+__device__ __forceinline__ void load_vals(const double* p, double (&B)[N]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < N / 2; ++k) {
+    const double2 t = q[k];
+    B[2 * k] = t.x; B[2 * k + 1] = t.y;
+  }
+}
+
+template <class T>
+struct TypedCfg;
+template <>
+struct TypedCfg<float> { static constexpr int NT = 256, NBUF = 3; };
+template <>
+struct TypedCfg<double> { static constexpr int NT = 128, NBUF = 4; };
+template <class T>
+constexpr size_t typed_stage_bytes() {
+  return (size_t)(TypedCfg<T>::NT / 32) * TypedCfg<T>::NBUF * TCHUNK * 36 * sizeof(T);
+}
+// the operand copy of the group values in shared memory
+template <class T>
+using UGv = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+// dynamic shared memory: stage | per-warp group accumulators | group operand values | camera-row segments
+template <class T>
+__host__ __device__ constexpr size_t typed_gvp(int gv) { return (size_t)((gv + GV_PAD + 1) & ~1); }
+template <class T>
+__host__ __device__ constexpr size_t typed_fixed_smem(int gv) {
+  return typed_stage_bytes<T>() + (size_t)(TypedCfg<T>::NT / 32) * typed_gvp<T>(gv) * sizeof(DotAcc<T>) +
+         typed_gvp<T>(gv) * sizeof(UGv<T>);
+}
+
+template <class T, int NT, int NBUF>
+__global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
+  constexpr int NW = NT / 32;
+  constexpr int SPIN = 1 << 22;   // polls of a bulk copy's completion (the copies always complete)
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int gvp = (int)typed_gvp<T>(a.gv);
+  T* stage = reinterpret_cast<T*>(dyn);                                                    // [NW][NBUF][32 x 36]
+  DotAcc<T>* gacc = reinterpret_cast<DotAcc<T>*>(dyn + typed_stage_bytes<T>());           // [NW][gvp]
+  UGv<T>* ug = reinterpret_cast<UGv<T>*>(reinterpret_cast<unsigned char*>(gacc) + sizeof(DotAcc<T>) * NW * gvp);
+  DotAcc<T>* seg = reinterpret_cast<DotAcc<T>*>(dyn + typed_fixed_smem<T>(a.gv));         // [row segments][6]
+  __shared__ __align__(8) uint64_t bars[NW][NBUF];
+  __shared__ __align__(128) int cols[NW][NBUF][TCHUNK];
+  __shared__ int wfirst[NW], wlast[NW], wbase[NW + 1];
+  __shared__ double bc[4];
+  __shared__ double cta_out[2];
+  __shared__ double red3[NW][3];
+  const int G = gridDim.x, c = blockIdx.x;
+  const int4 pc = a.cta_part[c];
+  const int q0 = pc.x, q1 = pc.y;   // chunks [q0, q1)
+  const int r0 = pc.z, r1 = pc.w;   // camera rows touched [r0, r1)
+  const int o0 = (r0 < r1 && a.row_chunk0[r0] != q0) ? r0 + 1 : r0;   // camera rows owned [o0, r1)
+  const bool tail_cut = o0 < r1 && a.row_chunk0[r1] > q1;            // the last owned row continues
+  const int gs0 = a.cta_gs[c], gs1 = a.cta_gs[c + 1];                 // group rows owned [gs0, gs1)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntot = q1 - q0;
+  const int c0 = q0 + (int)((int64_t)ntot * warp / NW), c1 = q0 + (int)((int64_t)ntot * (warp + 1) / NW);
+  const int nk = c1 - c0;
+  const int nkeep = (int)((float)nk * a.keep_frac);
+  const uint64_t pol_keep = l2_evict_last(), pol_stream = l2_evict_first();
+  DotAcc<T>* ga = gacc + (size_t)warp * gvp;
+  auto row_of = [&](int q) {
+    int lo = r0, hi = r1 - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.row_chunk0[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  if (lane == 0) {
+    for (int bi = 0; bi < NBUF; ++bi) mbar_init(&bars[warp][bi], 1);
+    wfirst[warp] = nk > 0 ? row_of(c0) : 0;
+    wlast[warp] = nk > 0 ? row_of(c1 - 1) : -1;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int w = 0; w < NW; ++w) { wbase[w] = b; b += wlast[w] - wfirst[w] + 1; }
+    wbase[NW] = b;
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  bool timed_out = false;
+  bool prefetched = false;
+  // the owned values: camera rows [o0, r1) and group rows [gs0, gs1) (6 per row)
+  const int64_t cb0 = 6 * (int64_t)o0, cb1 = 6 * (int64_t)r1;
+  const int64_t gb0 = 6 * (a.nc + gs0), gb1 = 6 * (a.nc + gs1);
+  auto owned = [&](auto&& f) {
+    for (int64_t k = cb0 + threadIdx.x; k < cb1; k += NT) f(k);
+    for (int64_t k = gb0 + threadIdx.x; k < gb1; k += NT) f(k);
+  };
+  // group row g's group values: first value offset and count
+  auto gval = [&](int g, int& k0, int& nd) {
+    if (g < a.npl) { k0 = 3 * g; nd = 3; } else { k0 = 3 * (int)a.npl + 2 * (g - (int)a.npl); nd = 2; }
+  };
+
+  auto issue = [&](int k) {
+    const int q = c0 + k;
+    const int bi = k % NBUF;
+    const int4 cd = a.tchunk[q];
+    const unsigned vb = (unsigned)(TCHUNK * ty_vals(cd.w) * sizeof(T));
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&bars[warp][bi], vb + 4u * TCHUNK);
+    const uint64_t pol = k < nkeep ? pol_keep : pol_stream;
+    bulk_g2s_hint(stage + ((size_t)warp * NBUF + bi) * (TCHUNK * 36), a.Sv + cd.x, vb, &bars[warp][bi], pol);
+    bulk_g2s_hint(&cols[warp][bi][0], a.tcol + cd.y, 4u * TCHUNK, &bars[warp][bi], pol);
+  };
+  auto arrive = [&](int k) {
+    const int bi = k % NBUF;
+    if (!mbar_wait(&bars[warp][bi], (phase >> bi) & 1u, SPIN)) timed_out = true;
+    phase ^= 1u << bi;
+  };
+  auto drain = [&]() {
+    if (!prefetched) return;
+    for (int k = 0; k < NBUF && k < nk; ++k) arrive(k);
+    prefetched = false;
+  };
+
+  // w = S u over the owned values (camera rows complete after the carries, group rows after the partials);
+  // returns this CTA's share of (w, u)
+  auto spmv = [&](double& wu) {
+    for (int k = threadIdx.x; k < gvp; k += NT) {
+      if constexpr (sizeof(T) == 4) ug[k] = k < a.gv ? __ldcg(&a.uhl[a.gv_idx[k]]) : make_float2(0.f, 0.f);
+      else ug[k] = k < a.gv ? __ldcg(&a.u[a.gv_idx[k]]) : 0.0;
+    }
+    for (int k = lane; k < gvp; k += 32) ga[k] = DotAcc<T>();
+    if (lane == 0 && !prefetched)
+      for (int k = 0; k < NBUF && k < nk; ++k) issue(k);
+    prefetched = false;
+    __syncthreads();
+    DotAcc<T> acc[6];
+    int row = wfirst[warp];
+    int rend = nk > 0 ? a.row_chunk0[row + 1] : 0;
+    XV<T> ur[6];   // u of the current camera row
+    auto load_ur = [&]() {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) load_xv(a, 6 * (size_t)row + i, ur[i]);
+    };
+    auto flush = [&]() {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const DotAcc<T> y = warp_sum_acc(acc[i]);
+        if (lane == 0) seg[6 * (wbase[warp] + row - wfirst[warp]) + i] = y;
+        acc[i] = DotAcc<T>();
+      }
+    };
+    XV<T> un[6];   // u of this lane's column in the next camera-camera chunk
+    int4 cdn = make_int4(0, 0, 0, -1);
+    if (nk > 0) {
+      load_ur();
+      arrive(0);
+      cdn = a.tchunk[c0];
+      if (cdn.w == TY_CC) {
+        const int cl = cols[warp][0][lane];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) load_xv(a, 6 * (size_t)cl + j, un[j]);
+      }
+    }
+    for (int k = 0; k < nk; ++k) {
+      const int q = c0 + k;
+      const int4 cd = cdn;
+      while (q >= rend) {
+        flush();
+        ++row;
+        rend = a.row_chunk0[row + 1];
+        load_ur();
+      }
+      const int bi = k % NBUF;
+      const T* buf = stage + ((size_t)warp * NBUF + bi) * (TCHUNK * 36);
+      const int col = cols[warp][bi][lane];
+      // the lane's block into registers, then the next chunk's copies and gathers
+      T B[36];
+      XV<T> uc[6];
+      if (cd.w == TY_CC) {
+        load_block36(buf + lane * 36, B);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) uc[j] = un[j];
+      } else if (cd.w == TY_CP) {
+        T b18[18];
+        load_vals<18>(buf + lane * 18, b18);
+#pragma unroll
+        for (int j = 0; j < 18; ++j) B[j] = b18[j];
+      } else {
+        T b12[12];
+        load_vals<12>(buf + lane * 12, b12);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) B[j] = b12[j];
+      }
+      // every lane holds its block and column: the buffer is refilled first, so that NBUF chunks are in
+      // flight while the warp waits for the next one
+      __syncwarp();
+      if (lane == 0 && k + NBUF < nk) issue(k + NBUF);
+      if (k + 1 < nk) {
+        arrive(k + 1);
+        cdn = a.tchunk[q + 1];
+        if (cdn.w == TY_CC) {
+          const int cl = cols[warp][(k + 1) % NBUF][lane];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) load_xv(a, 6 * (size_t)cl + j, un[j]);
+        }
+      }
+      if (cd.w == TY_CC) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) ds_madd(acc[i], B[i * 6 + j], uc[j]);
+      } else {
+        // camera-group block (6 x nd): the row part with the group's u, the transpose into the group values
+        const int nd = cd.w == TY_CP ? 3 : 2;
+        XV<T> xg[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (j < nd) {
+            if constexpr (sizeof(T) == 4) xg[j].set(ug[col + j]); else xg[j].v = ug[col + j];
+          }
+        }
+        if (nd == 3) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) ds_madd(acc[i], B[i * 3 + j], xg[j]);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            DotAcc<T> y;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ds_madd(y, B[i * 3 + j], ur[i]);
+            acc_add(ga[col + j], y);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) ds_madd(acc[i], B[i * 2 + j], xg[j]);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            DotAcc<T> y;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ds_madd(y, B[i * 2 + j], ur[i]);
+            acc_add(ga[col + j], y);
+          }
+        }
+      }
+    }
+    if (nk > 0) flush();
+    __syncwarp();
+    if (lane == 0)
+      for (int k = 0; k < NBUF && k < nk; ++k) issue(k);
+    prefetched = true;
+    __syncthreads();
+    double v = 0;
+    // camera rows: the warps' segments, in warp order
+    for (int rr = r0 + threadIdx.x; rr < r1; rr += NT) {
+      DotAcc<T> y[6];
+      for (int w = 0; w < NW; ++w)
+        if (wfirst[w] <= rr && rr <= wlast[w])
+#pragma unroll
+          for (int i = 0; i < 6; ++i) acc_add(y[i], seg[6 * (wbase[w] + rr - wfirst[w]) + i]);
+      double* dst = rr < o0 ? a.carry + 6 * (size_t)c : a.w + 6 * (size_t)rr;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double yv = y[i].value();
+        dst[i] = yv;
+        v += yv * __ldcg(&a.u[6 * (size_t)rr + i]);
+      }
+    }
+    // the group values of this CTA's scatter, warps in order; their dot with u in the working precision
+    // (the staged operand copy of u), rounded to double once
+    DotAcc<T> vg;
+    for (int k = threadIdx.x; k < a.gv; k += NT) {
+      DotAcc<T> y = gacc[k];
+      for (int w = 1; w < NW; ++w) acc_add(y, gacc[(size_t)w * gvp + k]);
+      const double yv = y.value();
+      a.part_g[(size_t)k * G + c] = yv;   // value-major: the group row's owner reads the CTAs' sums coalesced
+      XV<T> uk;
+      if constexpr (sizeof(T) == 4) uk.set(ug[k]); else uk.v = ug[k];
+      if constexpr (sizeof(T) == 4) {
+        // y u = (hi + lo)(u_hi + u_lo): the lo x lo term is below the working precision
+        ds_madd(vg, y.hi, uk);
+        XV<T> ul;
+        ul.h = uk.h; ul.l = 0.f;
+        ds_madd(vg, y.lo, ul);
+      } else {
+        ds_madd(vg, (T)yv, uk);
+      }
+    }
+    v += vg.value();
+    // the group-group blocks of the owned group rows (a VP parallel to many planes has a long row): a thread
+    // per block, its 6 products into the group accumulators' space (free until the next product), then
+    // every row's blocks summed in block order
+    __syncthreads();
+    DotAcc<T>* ggy = gacc;
+    const int kb0 = a.gg_ptr[gs0], kb1 = a.gg_ptr[gs1];
+    for (int kb = kb0 + threadIdx.x; kb < kb1; kb += NT) {
+      T Bk[36];
+      load_block36(a.Sv + a.gg_val0 + 36 * (size_t)kb, Bk);   // 16-byte aligned: gg_val0 is a chunk boundary
+      const int cl = a.gg_col[kb];
+      XV<T> uv[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) load_xv(a, 6 * (size_t)cl + j, uv[j]);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        DotAcc<T> y;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) ds_madd(y, Bk[6 * i + j], uv[j]);
+        ggy[6 * (size_t)(kb - kb0) + i] = y;
+      }
+    }
+    __syncthreads();
+    // a warp per owned group row: its lanes over the row's blocks in the working precision, then the
+    // warp's shuffle tree
+    for (int g = gs0 + warp; g < gs1; g += NW) {
+      DotAcc<T> y[6];
+      for (int kb = a.gg_ptr[g] + lane; kb < a.gg_ptr[g + 1]; kb += 32)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc_add(y[i], ggy[6 * (size_t)(kb - kb0) + i]);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) y[i] = warp_sum_acc(y[i]);
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const size_t o = 6 * ((size_t)a.nc + g) + i;
+          const double yv = y[i].value();
+          a.w[o] = yv;
+          v += yv * __ldcg(&a.u[o]);
+        }
+      }
+    }
+    wu = v;
+  };
+  // after the grid barrier that follows a product: the carries of the last owned camera row, and the group
+  // rows' sums of every CTA's scatter (in CTA order)
+  auto add_carries = [&]() {
+    if (tail_cut && threadIdx.x < 6) {
+      const int rrow = r1 - 1;
+      double v = a.w[6 * (size_t)rrow + threadIdx.x];
+      for (int c2 = c + 1; c2 < G; ++c2) {
+        const int4 pn = a.cta_part[c2];
+        if (pn.x == pn.y || pn.z != rrow) break;
+        v += __ldcg(&a.carry[6 * (size_t)c2 + threadIdx.x]);
+      }
+      a.w[6 * (size_t)rrow + threadIdx.x] = v;
+    }
+    // a warp per owned group value, its lanes over the CTAs (a fixed order: strided lane sums, then the
+    // warp's shuffle tree)
+    for (int t = warp; t < 3 * (gs1 - gs0); t += NW) {
+      const int g = gs0 + t / 3, d = t % 3;
+      int k0, nd;
+      gval(g, k0, nd);
+      if (d >= nd) continue;
+      double v = 0;
+      for (int c2 = lane; c2 < G; c2 += 32) v += __ldcg(&a.part_g[(size_t)(k0 + d) * G + c2]);
+      v = warp_sum(v);
+      if (lane == 0) a.w[6 * ((size_t)a.nc + g) + d] += v;
+    }
+  };
+  auto precondition = [&](double& ru, double& rr_) {
+    double v0 = 0, v1 = 0;
+    owned([&](int64_t k) {
+      const int64_t rw = k / 6;
+      const int i = (int)(k - 6 * rw);
+      const T* M = a.Minv + (size_t)rw * BS2 + 6 * i;
+      const double* rv = a.r + 6 * (size_t)rw;
+      T zs = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) zs += M[j] * (T)rv[j];
+      const double z = (double)zs, ri = rv[i];
+      a.u[k] = z;
+      if (a.uhl) a.uhl[k] = split2(z);
+      v0 += ri * z;
+      v1 += ri * ri;
+    });
+    ru = v0;
+    rr_ = v1;
+  };
+  auto slot = [&](int par, int k) { return a.part + (size_t)par * 3 * G + (size_t)k * G; };
+  // a copy wait that ran out (in any warp) is recorded before the barrier; the barrier's answer is uniform
+  auto sync = [&]() -> bool {
+    if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
+    return grid_barrier(a.S, (unsigned)G, a.budget);
+  };
+
+  // ---- start: x = 0, r = b, u = M^-1 r, w = S u
+  owned([&](int64_t k) { a.x[k] = 0; a.r[k] = a.b[k]; });
+  __syncthreads();
+  double ru, rrl, wu;
+  precondition(ru, rrl);
+  cta_sum2<NT>(ru, rrl, cta_out);
+  if (threadIdx.x == 0) { slot(0, 0)[c] = cta_out[0]; slot(0, 1)[c] = cta_out[1]; }
+  double rr = 0, gam = 0, bb = 0;
+  int it = 0;
+  bool go = sync();
+  if (go) {
+    spmv(wu);
+    cta_sum2<NT>(wu, 0.0, cta_out);
+    if (threadIdx.x == 0) slot(0, 2)[c] = cta_out[0];
+    go = sync();
+  }
+  auto reduce3 = [&](int par) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int g = threadIdx.x; g < G; g += NT) {
+      s0 += __ldcg(&slot(par, 0)[g]);
+      s1 += __ldcg(&slot(par, 1)[g]);
+      s2 += __ldcg(&slot(par, 2)[g]);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) { red3[warp][0] = s0; red3[warp][1] = s1; red3[warp][2] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t0 = 0, t1 = 0, t2 = 0;
+      for (int w = 0; w < NW; ++w) { t0 += red3[w][0]; t1 += red3[w][1]; t2 += red3[w][2]; }
+      bc[0] = t0; bc[1] = t1; bc[2] = t2;
+    }
+    __syncthreads();
+  };
+  bool done = !go;
+  double alpha = 0, beta = 0;
+  if (!done) {
+    add_carries();   // ordered before the vector updates by the barriers inside reduce3
+    reduce3(0);
+    gam = bc[0];
+    bb = bc[1];
+    alpha = bc[2] > 0 ? gam / bc[2] : 0.0;
+    rr = bb;
+    done = !(bb > 0) || !(bc[2] > 0);
+  }
+  const double tol2 = a.tol * a.tol * bb;
+  int par = 1;
+  while (!done) {
+    const bool first = it == 0;
+    owned([&](int64_t k) {
+      const double pk = first ? a.u[k] : a.u[k] + beta * a.p[k];
+      const double sk = first ? a.w[k] : a.w[k] + beta * a.s[k];
+      a.p[k] = pk;
+      a.s[k] = sk;
+      a.x[k] += alpha * pk;
+      a.r[k] -= alpha * sk;
+    });
+    __syncthreads();
+    precondition(ru, rrl);
+    cta_sum2<NT>(ru, rrl, cta_out);
+    if (threadIdx.x == 0) { slot(par, 0)[c] = cta_out[0]; slot(par, 1)[c] = cta_out[1]; }
+    ++it;
+    if (!sync()) break;
+    spmv(wu);
+    cta_sum2<NT>(wu, 0.0, cta_out);
+    if (threadIdx.x == 0) slot(par, 2)[c] = cta_out[0];
+    if (!sync()) break;
+    add_carries();
+    reduce3(par);
+    const double gam_new = bc[0], delta = bc[2];
+    rr = bc[1];
+    if (rr <= tol2 || it >= a.max_iters || !(rr == rr)) break;
     beta = gam_new / gam;
     const double den = delta - beta * gam_new / alpha;
     alpha = gam_new / den;
@@ -2280,6 +2875,56 @@ __device__ void decide(const DecideArgs& a) {
 __global__ void k_decide(DecideArgs a) { decide(a); }
 
 // ============================================================================
+// FMA throughput probe: the denominators of the ALU rooflines (FP32 and FP64 pipes).  Every thread runs
+// eight independent FMA chains, so the pipes, not the chains' latency, bound the rate.
+// ============================================================================
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T seed, T* sink) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + (T)(threadIdx.x + k);
+  const T m = (T)0.999999, c = (T)1e-7;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  T t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += a[k];
+  if (t == (T)-1) sink[threadIdx.x] = t;   // never true: keeps the chains live
+}
+
+cudaError_t fma_probe(int precision, double* tflops, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  const bool f64 = precision == BA_FP64;
+  const int iters = f64 ? 1 << 12 : 1 << 16;
+  const int grid = sms * 8, nt = 256;
+  void* sink = nullptr;
+  if ((e = cudaMalloc(&sink, 256 * sizeof(double)))) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {   // the first launch warms the clocks up; the best of the rest counts
+    cudaEventRecord(e0, st);
+    if (f64) k_fma_probe<double><<<grid, nt, 0, st>>>(iters, 1.0, (double*)sink);
+    else k_fma_probe<float><<<grid, nt, 0, st>>>(iters, 1.0f, (float*)sink);
+    cudaEventRecord(e1, st);
+    if ((e = cudaEventSynchronize(e1))) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = fminf(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *tflops = 2.0 * 8.0 * iters * (double)grid * nt / (best * 1e-3) / 1e12;
+  return e;
+}
+
+// ============================================================================
 // launchers
 // ============================================================================
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -2350,7 +2995,7 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   const Dims& d = P.d;
   BlockArgs<T> b;
   b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.col = P.col;
-  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.Sval = (T*)P.Sval;
+  b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.Sval = (T*)P.Sval; b.sv = sview_of(P);
   b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nc = d.nc; b.lambda = lambda;
   UnitArgs<T> un;
   un.un_se = P.un_se; un.un_blk = P.un_blk; un.un_order = P.un_order; un.up_un = P.up_un; un.multi = P.multi_blk;
@@ -2382,7 +3027,11 @@ void launch_schur(Problem& P, double lambda) {
 template <class T>
 void launch_precond(Problem& P) {
   const Dims& d = P.d;
-  if (d.na) { ++P.launches; k_precond<T, true><<<nblk(d.na, 128), 128, 0, P.stream>>>(d.na, P.row_ptr, P.col, (const T*)P.Sval, (T*)P.Minv, P.S); }
+  if (d.na) {
+    ++P.launches;
+    k_precond<T, true><<<nblk(d.na, 128), 128, 0, P.stream>>>(d.na, P.row_ptr, P.col, (const T*)P.Sval, (T*)P.Minv,
+                                                              P.S, sview_of(P));
+  }
 }
 
 constexpr int PCG_THREADS = 512;
@@ -2406,8 +3055,52 @@ void pcg_allow_smem(size_t smem) {
                        (int)(smem + stream_stage_bytes<T>()));
 }
 
+// the typed-storage PCG: its fixed shared memory, occupancy (with the opt-in for `smem` bytes in all)
+template <class T>
+size_t pcg_typed_fixed_smem(int gv) { return typed_fixed_smem<T>(gv); }
+
+template <class T>
+size_t pcg_typed_gacc_bytes(int gv) { return (size_t)(TypedCfg<T>::NT / 32) * typed_gvp<T>(gv) * sizeof(DotAcc<T>); }
+
+template <class T>
+int pcg_typed_blocks_per_sm(size_t smem) {
+  constexpr int NT = TypedCfg<T>::NT, NB = TypedCfg<T>::NBUF;
+  cudaFuncSetAttribute(k_pcg_typed<T, NT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_typed<T, NT, NB>, NT, smem);
+  return nb;
+}
+
+template <class T>
+static void launch_pcg_typed(Problem& P) {
+  const Dims& d = P.d;
+  constexpr int NT = TypedCfg<T>::NT, NB = TypedCfg<T>::NBUF;
+  PcgTypedArgs<T> a;
+  a.na = d.na; a.nc = d.nc; a.npl = d.npl; a.gv = P.gv;
+  a.tcol = P.tcol; a.row_chunk0 = P.row_chunk0; a.gg_ptr = P.gg_ptr; a.gg_col = P.gg_col; a.cta_gs = P.cta_gs;
+  a.gv_idx = P.gv_idx; a.tchunk = P.tchunk; a.cta_part = reinterpret_cast<const int4*>(P.cta_part);
+  a.carry = P.pcg_carry; a.part_g = P.part_g;
+  a.Sv = (const T*)P.Sval; a.Minv = (const T*)P.Minv; a.gg_val0 = P.gg_val0; a.b = P.bvec;
+  a.x = P.x; a.r = P.r; a.u = P.z; a.p = P.p; a.w = P.Ap; a.s = P.svec; a.part = P.red; a.S = P.S;
+  a.uhl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
+  a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
+  a.keep_frac = P.pcg_keep_frac;
+  a.budget = P.opt.wait_budget_cycles > 0 ? P.opt.wait_budget_cycles : 1;
+  void* args[] = {&a};
+  ++P.launches;
+  // the grid barrier's arrival count starts at zero (a launch that gave up at a barrier may leave it set)
+  P.pcg_err = cudaMemsetAsync(&P.S->bar_count, 0, sizeof(unsigned), P.stream);
+  if (P.pcg_err != cudaSuccess) return;
+  P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_typed<T, NT, NB>, dim3(P.pcg_grid), dim3(NT), args,
+                                          P.pcg_smem, P.stream);
+}
+
 template <class T>
 void launch_pcg(Problem& P) {
+  if (P.typed) {
+    launch_pcg_typed<T>(P);
+    return;
+  }
   const Dims& d = P.d;
   constexpr int NT = StreamCfg<T>::NT, NB = StreamCfg<T>::NBUF;
   PcgStreamArgs<T> a;
@@ -2418,8 +3111,11 @@ void launch_pcg(Problem& P) {
   a.uhl = sizeof(T) == sizeof(float) ? P.phl : nullptr;
   a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
   a.keep_frac = P.pcg_keep_frac;
+  a.budget = P.opt.wait_budget_cycles > 0 ? P.opt.wait_budget_cycles : 1;
   void* args[] = {&a};
   ++P.launches;
+  P.pcg_err = cudaMemsetAsync(&P.S->bar_count, 0, sizeof(unsigned), P.stream);
+  if (P.pcg_err != cudaSuccess) return;
   P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_stream<T, NT, NB>, dim3(P.pcg_grid), dim3(NT), args,
                                           P.pcg_smem + stream_stage_bytes<T>(), P.stream);
 }
@@ -2427,7 +3123,7 @@ void launch_pcg(Problem& P) {
 // ---- launchers on caller-provided pointers (FP64), used by the allocation-free PCG entry point
 cudaError_t launch_precond_raw_f64(cudaStream_t st, int64_t na, const int32_t* row_ptr, const int32_t* col,
                                    const double* Sval, double* Minv, DevScalars* S) {
-  if (na > 0) k_precond<double, false><<<nblk(na, 128), 128, 0, st>>>(na, row_ptr, col, Sval, Minv, S);
+  if (na > 0) k_precond<double, false><<<nblk(na, 128), 128, 0, st>>>(na, row_ptr, col, Sval, Minv, S, SView());
   return cudaGetLastError();
 }
 
@@ -2447,6 +3143,7 @@ cudaError_t launch_pcg_raw_f64(cudaStream_t st, int grid, size_t smem, int64_t n
   a.Sval = Sval; a.Minv = Minv; a.b = b; a.x = x; a.r = r; a.z = z; a.p = p; a.Ap = Ap; a.part = part; a.S = S;
   a.phl = nullptr;
   a.tol = tol; a.max_iters = max_iters;
+  a.budget = 2000000000LL;   // about a second at the SM clock; the caller's scalars start at zero
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<double, PCG_THREADS, false>, dim3(grid),
                                      dim3(PCG_THREADS), args, smem, st);
@@ -2673,7 +3370,7 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
     for (int64_t k = threadIdx.x; k < ua.nmulti; k += NT) unit_finish<T>(ua, ua.multi[k]);
   }
   __syncthreads();
-  for (int64_t r = threadIdx.x; r < W.na; r += NT) precond_row<T, true>(W.row_ptr, W.col, W.Sval, W.Minv, W.S, r);
+  for (int64_t r = threadIdx.x; r < W.na; r += NT) precond_row<T, true>(W.row_ptr, W.col, W.Sval, W.Minv, W.S, r, SView());
   __syncthreads();
   // ---- PCG, back-substitution and predicted decrease
   window_pcg<T, NT>(W, chunk_y, red2);
@@ -2858,6 +3555,9 @@ template int windows_per_sm<double>(int, size_t);
   template void launch_pcg<T>(Problem&);                \
   template int pcg_blocks_per_sm<T>(size_t);            \
   template void pcg_allow_smem<T>(size_t);              \
+  template size_t pcg_typed_fixed_smem<T>(int);         \
+  template size_t pcg_typed_gacc_bytes<T>(int);         \
+  template int pcg_typed_blocks_per_sm<T>(size_t);      \
   template void launch_backsub<T>(Problem&);
 INST(double)
 INST(float)

@@ -204,6 +204,10 @@ extern "C" ba_status ba_pcg_solve_static(int64_t n, int64_t nnz, const int32_t* 
   DevScalars h;
   if ((e = cudaMemcpyAsync(&h, &W->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, st))) return fail_cuda(e);
   if ((e = cudaStreamSynchronize(st))) return fail_cuda(e);
+  if (h.flags & PCG_FLAG_TIMEOUT) {
+    set_msg(err, err_len, "ba_pcg_solve_static: a grid barrier of the PCG kernel waited too long");
+    return BA_ERR_TIMEOUT;
+  }
   if (iters) *iters = h.iters;
   if (rel) *rel = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
   set_msg(err, err_len, "");

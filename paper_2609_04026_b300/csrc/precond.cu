@@ -57,7 +57,7 @@ __global__ void k_pre_features(int64_t na, int64_t nc, const int32_t* __restrict
                                const int32_t* __restrict__ row_len, const int32_t* __restrict__ col,
                                const T* __restrict__ Sval, const double* __restrict__ sdiag,
                                const uint8_t* __restrict__ ent_type, const uint8_t* __restrict__ held,
-                               float* __restrict__ X, uint8_t* __restrict__ mask) {
+                               float* __restrict__ X, uint8_t* __restrict__ mask, SView sv) {
   const int lane = threadIdx.x & 31;
   const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (a >= na) return;
@@ -68,10 +68,12 @@ __global__ void k_pre_features(int64_t na, int64_t nc, const int32_t* __restrict
   const int q0 = row_ptr[a], q1 = q0 + row_len[a];
   for (int q = q0 + lane; q < q1; q += 32) {
     const int c = col[q];
+    double blk[36];
+    sview_load(sv, Sval, q, a, blk);
     if (c == a) {
       for (int k = 0; k < NO; ++k) {
         const int i = c_iu[k], j = c_ju[k];
-        X[(size_t)a * NF + k] = (float)(sda[i] * (double)Sval[s_idx(q, i * 6 + j)] * sda[j]);
+        X[(size_t)a * NF + k] = (float)(sda[i] * blk[i * 6 + j] * sda[j]);
       }
     } else {
       double sdc[6];
@@ -82,7 +84,7 @@ __global__ void k_pre_features(int64_t na, int64_t nc, const int32_t* __restrict
       for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          const double v = sda[i] * (double)Sval[s_idx(q, i * 6 + j)] * sdc[j];
+          const double v = sda[i] * blk[i * 6 + j] * sdc[j];
           f2 += v * v;
         }
       const double n = sqrt(f2);
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(128) k_pre_learned(int64_t na, const int32_t* 
                                                     const float* __restrict__ X, const uint8_t* __restrict__ mask,
                                                     const float* __restrict__ prm, const __nv_bfloat16* __restrict__ w1h,
                                                     const __nv_bfloat16* __restrict__ w2h, T* __restrict__ Minv,
-                                                    int* __restrict__ fallbacks) {
+                                                    int* __restrict__ fallbacks, SView sv) {
   __shared__ __nv_bfloat16 sW1[NF * NH];
   __shared__ __nv_bfloat16 sW2[NH * NO];
   __shared__ float sB1[NH], sB2[NO], sMu[NF], sSg[NF];
@@ -176,8 +178,9 @@ __global__ void __launch_bounds__(128) k_pre_learned(int64_t na, const int32_t* 
     pos_diag &= sdiag[6 * a + i] > 0;
     sd[i] = 1.0 / sqrt(fmax(sdiag[6 * a + i], 1e-300));
   }
+  const int64_t dof = sview_target(sv, pos).off;   // the diagonal block is stored whole
   for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) Sh[i][j] = sd[i] * (double)Sval[s_idx(pos, i * 6 + j)] * sd[j];
+    for (int j = 0; j < 6; ++j) Sh[i][j] = sd[i] * (double)Sval[dof + i * 6 + j] * sd[j];
   // symmetric part (the stored diagonal block is symmetric already)
   bool ok = pos_diag && chol_inv6(Sh, Shi);
   const unsigned m = mask[a];
@@ -440,7 +443,8 @@ void launch_pre_features(Problem& P) {
   const Dims& d = P.d;
   ++P.launches;
   k_pre_features<T><<<(int)((d.na * 32 + 127) / 128), 128, 0, P.stream>>>(
-      d.na, d.nc, P.row_ptr, P.row_len, P.col, (const T*)P.Sval, P.sdiag, P.ent_type, P.cam_fixed, P.pre_X, P.pre_mask);
+      d.na, d.nc, P.row_ptr, P.row_len, P.col, (const T*)P.Sval, P.sdiag, P.ent_type, P.cam_fixed, P.pre_X, P.pre_mask,
+      sview_of(P));
 }
 
 template <class T>
@@ -451,7 +455,7 @@ void launch_pre_learned(Problem& P) {
   ++P.launches;
   k_pre_learned<T><<<(int)((d.na + 127) / 128), 128, 0, P.stream>>>(
       d.na, P.row_ptr, P.row_len, P.col, (const T*)P.Sval, P.sdiag, P.pre_X, P.pre_mask, P.pre_params,
-      (const __nv_bfloat16*)P.pre_w1, (const __nv_bfloat16*)P.pre_w2, (T*)P.Minv, P.pre_fallbacks);
+      (const __nv_bfloat16*)P.pre_w1, (const __nv_bfloat16*)P.pre_w2, (T*)P.Minv, P.pre_fallbacks, sview_of(P));
 }
 
 template void launch_pre_features<float>(Problem&);

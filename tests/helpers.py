@@ -62,3 +62,29 @@ def rel(a, b):
     a = np.asarray(a, float); b = np.asarray(b, float)
     den = max(np.abs(b).max(), 1e-300) if b.size else 1.0
     return float(np.abs(a - b).max() / den) if a.size else 0.0
+
+
+def gpu_S_sparse(B, p, scene, lay):
+    """The library's reduced system in the oracle's column order as a scipy CSR matrix (padding dimensions
+    dropped), and b in the same order.  For systems too large to hold densely."""
+    import scipy.sparse as sp
+    rp, cols, vals, b = B.ba_export_reduced_system(p)
+    na = len(rp) - 1
+    idx = padded_to_oracle_index(scene, lay)
+    inv = np.full(6 * na, -1, np.int64)
+    inv[idx] = np.arange(len(idx))
+    brow = np.repeat(np.arange(na, dtype=np.int64), np.diff(rp))
+    r = (6 * brow[:, None, None] + np.arange(6)[None, :, None]).repeat(6, 2)
+    c = (6 * cols.astype(np.int64)[:, None, None] + np.arange(6)[None, None, :]).repeat(6, 1)
+    ro, co = inv[r.ravel()], inv[c.ravel()]
+    keep = (ro >= 0) & (co >= 0)
+    n = len(idx)
+    S = sp.csr_matrix((vals.ravel()[keep], (ro[keep], co[keep])), shape=(n, n))
+    return S, b.reshape(-1)[idx]
+
+
+def sparse_rel(A, Bm):
+    """max |A - B| / max |B| over sparse matrices."""
+    d = (A - Bm).tocsr()
+    den = max(abs(Bm).max(), 1e-300)
+    return float(abs(d).max() / den) if d.nnz else 0.0

@@ -80,5 +80,5 @@ def test_raw_pointer_calls_check_their_tensors():
             B.ba_mlp_grad(*args)
         assert e.value.status == B.BA_ERR_ARG
     with pytest.raises(B.BAError) as e:
-        B.ba_precond_train(X, E, m, zp(P), zp(P), zp(P - 2), 0, 1, 4, 1e-3)
+        B.ba_precond_train(X, E, m, zp(P), zp(P - 64), zp(P - 66), 0, 1, 4, 1e-3)
     assert e.value.status == B.BA_ERR_ARG and "adam_v" in str(e.value)

@@ -146,3 +146,38 @@ def test_batch_state_continues_with_lm_step(B):
     finally:
         for p in ps:
             B.ba_destroy(p)
+
+
+def _large_windows(n, seed=4):
+    """The first n windows of the batched workload's generator with 35-40 cameras and 10k-20k features: the
+    largest windows of the config (5-40 cameras, 200-20k features)."""
+    out = []
+    for i in range(5000):
+        c = window_config(i, seed=seed)
+        if 35 <= c.n_cams <= 40 and 10_000 <= c.n_points + c.n_lines <= 20_000:
+            out.append(make_scene(c))
+            if len(out) == n:
+                break
+    return out
+
+
+def test_batch_fp64_matches_oracle_on_largest_windows(B):
+    """One batched FP64 LM iteration of three of the largest windows (35-40 cameras, 10k-20k features)
+    equals the oracle's iteration from the same start: the same accept decision and the same resulting cost
+    (1e-9 relative), with PCG run far below its default tolerance on both sides."""
+    ws = _large_windows(3)
+    assert len(ws) == 3
+    ps = [gpu_problem(B, s, precision=B.BA_FP64, pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000) for s in ws]
+    try:
+        reps = B.ba_solve_batch(ps, lm_iters=1, autotune=False)
+    finally:
+        for p in ps:
+            B.ba_destroy(p)
+    for s, r in zip(ws, reps):
+        st = O.state_from_scene(s)
+        lay = O.Layout(st, s["fixed"])
+        opt = O.Options(pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000)
+        _, rep = O.lm_step(st, s["obs"], opt, O.LMState(opt.lambda0), lay)
+        E = rep["E_new"] if rep["accepted"] else rep["E"]
+        assert r.accepted_steps == int(rep["accepted"])
+        assert abs(r.cost - E) <= 1e-9 * E, (r.cost, E)

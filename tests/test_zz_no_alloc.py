@@ -55,11 +55,15 @@ def test_static_pcg_matches_library_step(B):
 
 
 def test_static_pcg_rejects_oversize(B):
+    """More block rows than the fixed scratch array holds: the library refuses the call (BA_ERR_ARG)."""
     n = 5000
     rp = np.arange(n + 1, dtype=np.int32)
-    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dev = torch.device("cuda")
+    cols = torch.arange(n, dtype=torch.int32, device=dev)
+    vals = torch.zeros(36 * n, dtype=torch.float64, device=dev)
+    v = torch.zeros(6 * n, dtype=torch.float64, device=dev)
     with pytest.raises(B.BAError) as e:
-        B.ba_pcg_solve_static(rp, t, t, t, t)
+        B.ba_pcg_solve_static(rp, cols, vals, v, v.clone())
     assert e.value.status == B.BA_ERR_ARG and "4096" in str(e.value)
 
 
