@@ -71,6 +71,7 @@ typedef enum { BA_FP64 = 0, BA_MIXED = 1 } ba_precision;
 typedef enum { BA_PRECOND_BLOCK_JACOBI = 0, BA_PRECOND_LEARNED = 1 } ba_precond;
 typedef enum { BA_POINT = 0, BA_LINE = 1 } ba_feature_kind;
 typedef enum { BA_PLANE = 0, BA_VP = 1 } ba_group_kind;
+typedef enum { BA_REL_ORTHOGONAL = 0, BA_REL_PARALLEL = 1 } ba_relation_type;
 typedef enum {
   BA_OBS_POINT = 0, BA_OBS_LINE = 1, BA_OBS_PLANE_POINT = 2, BA_OBS_PLANE_LINE = 3,
   BA_OBS_VP = 4, BA_OBS_P2L = 5, BA_OBS_L2P = 6
@@ -104,9 +105,11 @@ typedef struct ba_options {
                                    returns BA_ERR_TIMEOUT with the problem still usable.  The waits for the bulk
                                    copies of S into shared memory have a fixed bound instead: a copy always
                                    completes, and a kernel never leaves while one is in flight */
-  double mixed_lambda_floor; /* BA_MIXED only: lower bound of the damping (1e-6).  The float Schur complement
-                                carries ~1e-7 relative rounding; below this damping its weakest directions sink
-                                under that noise and PCG stops converging */
+  double mixed_lambda_floor; /* BA_MIXED only: an extra lower bound of the damping (0 = none, the default).  An
+                                earlier float Schur form needed 1e-6; with the whitened form the floor only slowed
+                                the slow tail of the iteration (measured at 2000 cameras) */
+  double w_rel;             /* loss weight of the inter-group relations (5e3, the VP term's) */
+  double cauchy_rel;        /* Cauchy scale of the inter-group relations (0.2, the VP term's) */
 } ba_options;
 
 /* Per-LM-step report. */
@@ -159,6 +162,16 @@ ba_status ba_add_cameras(ba_problem* p, int64_t n, int mem, const double* quat_t
 ba_status ba_add_features(ba_problem* p, int kind, int64_t n, int mem, const double* params);
 /* Groups (Section 3.2-3.3, Appendix B): kind BA_PLANE (n x 4) or BA_VP (n x 3). */
 ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, const double* params);
+/* Inter-group relations (Section 3.2, Inter-Group Relations; Appendix C, Manhattan / Atlanta world): n
+ * relations between two group directions, each a plane normal (kind BA_PLANE) or a VP direction (BA_VP).
+ * kind_a, a, kind_b, b, type: n int32 each (type BA_REL_ORTHOGONAL: residual a.b, the cosine of the angle;
+ * BA_REL_PARALLEL: residual a x b, its sine as a vector).  Both are angular: weight w_rel and Cauchy scale
+ * cauchy_rel, in E but not in the pixel cost E_px.  They involve only group parameters, so they add to the
+ * group-group blocks of S (H_gg) and to g_g alone.  Indices are validated when the structure is frozen
+ * (BA_ERR_ARG for an unknown kind or type, an id out of range, or a relation of a group with itself).
+ * Appends; not supported by ba_solve_batch (BA_ERR_ARG there). */
+ba_status ba_add_relations(ba_problem* p, int64_t n, int mem, const int32_t* kind_a, const int32_t* a,
+                           const int32_t* kind_b, const int32_t* b, const int32_t* type);
 /* Residual records of one kind: cam (n; ignored for BA_OBS_VP, may be NULL), feature (n), other (n; group id or
  * partner feature id, may be NULL for kinds without one), meas (n x meas_dim(kind), may be NULL when 0). */
 ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int mem, const int32_t* cam,

@@ -61,6 +61,8 @@ class Options:
     w_group: float = 0.5
     w_wire: float = 0.1
     w_vp: float = 5e3
+    w_rel: float = 5e3        # inter-group relations (angular, like the VP term)
+    cauchy_rel: float = 0.2
     cauchy_px: float = 1.0
     cauchy_vp: float = 0.2
     lambda0: float = 1e-4
@@ -338,6 +340,66 @@ RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
 # ===========================================================================
 # problem state
 # ===========================================================================
+# ---------------------------------------------------------------------------
+# inter-group relations (Section 3.2, "Inter-Group Relations"; Appendix C, Manhattan / Atlanta world):
+# orthogonality or parallelism between two group directions -- VP directions and plane normals.  They involve
+# only kept-set parameters, so they add to H_gg and g_g alone.  Readings (the paper gives no formula): the
+# directions are unit vectors a, b; orthogonality r = a . b (the cosine), parallelism r = a x b (the sine, as
+# a vector, the form of the VP residual); both are angular and scale-free, so they take the VP term's weight
+# and Cauchy scale and stay out of E_px.  Residuals are 3-vectors (an orthogonality residual is padded with
+# zeros, which changes neither the cost nor the normal equations).
+# ---------------------------------------------------------------------------
+REL_ORTH, REL_PAR = 0, 1
+
+
+def _group_direction(g, kind, d):
+    """Unit direction of a group after its increment: a plane's normal (kind 0, d = 3 plane increments;
+    the offset increment does not move it) or a VP (kind 1, d[:2])."""
+    n_plane = plane_plus(g, d)[:3]
+    v = vp_plus(g[:3], d[:2])
+    return torch.where(kind == 0, n_plane, v)
+
+
+def res_relation(da, db, ga, gb, ka, kb, typ):
+    a = _group_direction(ga, ka, da)
+    b = _group_direction(gb, kb, db)
+    orth = torch.stack([(a * b).sum(), torch.zeros((), dtype=a.dtype), torch.zeros((), dtype=a.dtype)])
+    par = torch.linalg.cross(a, b)
+    return torch.where(typ == REL_ORTH, orth, par)
+
+
+def _rel_records(state, rel):
+    n = len(rel["a"])
+    ga = torch.zeros((n, 4)); gb = torch.zeros((n, 4))
+    for side, g in (("a", ga), ("b", gb)):
+        k = np.asarray(rel["k" + side])
+        idx = np.asarray(rel[side])
+        pl = k == 0
+        if pl.any():
+            g[torch.from_numpy(pl)] = torch.from_numpy(state["planes"][idx[pl]])
+        if (~pl).any():
+            g[torch.from_numpy(~pl), :3] = torch.from_numpy(state["vps"][idx[~pl]])
+    to_t = lambda x: torch.from_numpy(np.asarray(x, np.int64))
+    return ga, gb, to_t(rel["ka"]), to_t(rel["kb"]), to_t(rel["type"])
+
+
+def relation_residuals(state, rel, with_jac=False):
+    """r [n, 3] and, with with_jac, J w.r.t. the increments of group a and group b (3 each; a VP uses 2)."""
+    ga, gb, ka, kb, ty = _rel_records(state, rel)
+    n = ga.shape[0]
+    da = torch.zeros((n, 3)); db = torch.zeros((n, 3))
+    if n == 0:
+        z = torch.zeros((0, 3))
+        return (z, torch.zeros((0, 3, 3)), torch.zeros((0, 3, 3))) if with_jac else z
+    if with_jac:
+        def f2(*x):
+            r = res_relation(*x)
+            return r, r
+        jac, r = vmap(jacfwd(f2, argnums=(0, 1), has_aux=True))(da, db, ga, gb, ka, kb, ty)
+        return r, jac[0], jac[1]
+    return vmap(res_relation)(da, db, ga, gb, ka, kb, ty)
+
+
 def normalize_lines(L):
     L = np.array(L, dtype=np.float64, copy=True)
     dn = np.linalg.norm(L[:, :3], axis=1, keepdims=True)
@@ -435,6 +497,11 @@ def cost(state, obs, opt: Options):
         E += tot
         if k != "vp":
             Epx += tot
+    rel = obs.get("relations")
+    if rel is not None and len(rel["a"]):
+        r = relation_residuals(state, rel)
+        a = opt.cauchy_rel
+        E += float((0.5 * opt.w_rel * a * a * torch.log1p((r * r).sum(-1) / (a * a))).sum())
     return E, Epx
 
 
@@ -516,6 +583,28 @@ def linearize(state, obs, opt: Options, lay: Layout):
             rows.append(R_[m]); cols.append(C_[m]); vals.append(J[m])
         rt.append((r.numpy() * sq[:, None]).reshape(-1))
         row0 += n * rd
+    rel = obs.get("relations")
+    if rel is not None and len(rel["a"]):
+        r, Ja, Jb = relation_residuals(state, rel, with_jac=True)
+        n = r.shape[0]
+        a = opt.cauchy_rel
+        om = opt.w_rel / (1 + (r * r).sum(-1) / (a * a))
+        sq = torch.sqrt(om).numpy()
+        ridx = row0 + np.arange(n)[:, None] * 3 + np.arange(3)[None, :]
+        for side, J in (("a", Ja.numpy()), ("b", Jb.numpy())):
+            k = np.asarray(rel["k" + side]); idx = np.asarray(rel[side])
+            for kind, colmap, w in ((0, lay.plane_col, 3), (1, lay.vp_col, 2)):
+                m = k == kind
+                if not m.any():
+                    continue
+                C0 = colmap[idx[m]][:, None] + np.arange(w)[None, :]
+                Jm = J[m][:, :, :w] * sq[m][:, None, None]
+                nm = int(m.sum())
+                R_ = np.broadcast_to(ridx[m][:, :, None], (nm, 3, w))
+                C_ = np.broadcast_to(C0[:, None, :], (nm, 3, w))
+                rows.append(R_.ravel()); cols.append(C_.ravel()); vals.append(Jm.ravel())
+        rt.append((r.numpy() * sq[:, None]).reshape(-1))
+        row0 += 3 * n
     Jt = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                        shape=(row0, lay.n))
     return Jt, np.concatenate(rt)

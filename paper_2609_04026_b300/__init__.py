@@ -25,6 +25,7 @@ BA_FP64, BA_MIXED = 0, 1
 BA_PRECOND_BLOCK_JACOBI, BA_PRECOND_LEARNED = 0, 1
 BA_POINT, BA_LINE = 0, 1
 BA_PLANE, BA_VP = 0, 1
+BA_REL_ORTHOGONAL, BA_REL_PARALLEL = 0, 1
 OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6}
 MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2}
 
@@ -40,7 +41,8 @@ class ba_options(C.Structure):
                 ("rel_cost_tol", C.c_double), ("max_lm_iters", C.c_int), ("pcg_rel_tol", C.c_double),
                 ("pcg_max_iters", C.c_int), ("precond", C.c_int), ("cuda_stream", C.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double)]
+                ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double),
+                ("w_rel", C.c_double), ("cauchy_rel", C.c_double)]
 
 
 class ba_step_report(C.Structure):
@@ -84,6 +86,7 @@ def _load():
         "ba_add_features": (I, [P, I, I64, I, VP]),
         "ba_add_groups": (I, [P, I, I64, I, VP]),
         "ba_add_observations": (I, [P, I, I64, I, VP, VP, VP, VP]),
+        "ba_add_relations": (I, [P, I64, I, VP, VP, VP, VP, VP]),
         "ba_lm_step": (I, [P, C.POINTER(ba_step_report)]),
         "ba_solve": (I, [P, C.POINTER(ba_solve_report)]),
         "ba_get_cameras": (I, [P, I, VP]),
@@ -258,6 +261,17 @@ def ba_add_observations(p, kind, cam, feature, other=None, meas=None):
     _check(p, _lib.ba_add_observations(p, kind, len(kf), mem, c, f, o, m))
 
 
+def ba_add_relations(p, kind_a, a, kind_b, b, type_):
+    """Inter-group relations: per relation the kinds (BA_PLANE / BA_VP) and ids of its two groups and its type
+    (BA_REL_ORTHOGONAL / BA_REL_PARALLEL)."""
+    ka, mem, k1 = _arr(kind_a, np.int32)
+    aa, _, k2 = _arr(a, np.int32)
+    kb, _, k3 = _arr(kind_b, np.int32)
+    bb, _, k4 = _arr(b, np.int32)
+    tt, _, k5 = _arr(type_, np.int32)
+    _check(p, _lib.ba_add_relations(p, len(k2), mem, ka, aa, kb, bb, tt))
+
+
 def ba_lm_step(p):
     r = ba_step_report()
     _check(p, _lib.ba_lm_step(p, C.byref(r)))
@@ -359,6 +373,10 @@ def load_scene(p, scene, device_tensors=False):
         ba_add_groups(p, BA_PLANE, conv(scene["planes"]))
     if len(scene["vps"]):
         ba_add_groups(p, BA_VP, conv(scene["vps"]))
+    rel = scene.get("relations")
+    if rel is not None and len(rel["a"]):
+        ba_add_relations(p, conv(rel["ka"].astype(np.int32)), conv(rel["a"]), conv(rel["kb"].astype(np.int32)),
+                         conv(rel["b"]), conv(rel["type"].astype(np.int32)))
     for name, k in OBS_KINDS.items():
         o = scene["obs"][name]
         if len(o["feat"]) == 0:

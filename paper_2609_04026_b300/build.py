@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libba.so")
-SOURCES = ["api.cu", "structure.cu", "kernels.cu", "noalloc.cu", "precond.cu"]
+SOURCES = ["api.cu", "structure.cu", "kernels.cu", "noalloc.cu", "precond.cu", "relations.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -55,6 +55,8 @@ extern "C" void ba_default_options(ba_options* o) {
   o->cuda_stream = nullptr;
   o->wait_budget_cycles = 2000000000LL;
   o->mixed_lambda_floor = 0.0;
+  o->w_rel = 5e3;
+  o->cauchy_rel = 0.2;
 }
 
 extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
@@ -153,6 +155,23 @@ extern "C" ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, 
   else if (kind == BA_VP) s = fetch(p, mem, params, 3 * n, p->h_vps);
   else return set_err(p, BA_ERR_ARG, "group kind must be BA_PLANE or BA_VP");
   return s;
+}
+
+extern "C" ba_status ba_add_relations(ba_problem* p, int64_t n, int mem, const int32_t* kind_a, const int32_t* a,
+                                      const int32_t* kind_b, const int32_t* b, const int32_t* type) {
+  ba_status s = check_add(p, n);
+  if (s) return s;
+  if (n == 0) return BA_OK;
+  if (!kind_a || !a || !kind_b || !b || !type) return set_err(p, BA_ERR_ARG, "null array");
+  std::vector<int32_t> cols[5];
+  const int32_t* src[5] = {kind_a, a, kind_b, b, type};
+  for (int k = 0; k < 5; ++k)
+    if ((s = fetch(p, mem, src[k], (size_t)n, cols[k]))) return s;
+  const size_t o = p->h_rel.size();
+  p->h_rel.resize(o + 5 * (size_t)n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 5; ++k) p->h_rel[o + 5 * i + k] = cols[k][i];
+  return BA_OK;
 }
 
 extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int mem, const int32_t* cam,
@@ -458,6 +477,7 @@ static ba_status freeze(ba_problem* p) {
   CUDA_OR(p, ensure_ln1p_table(p->stream));
   if (mixed(p)) launch_prepare<float>(*p, false); else launch_prepare<double>(*p, false);
   launch_cost(*p, false);
+  launch_rel_cost(*p, false);
   CUDA_OR(p, cudaGetLastError());
   CUDA_OR(p, cudaMemcpyAsync(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
   CUDA_OR(p, cudaStreamSynchronize(p->stream));
@@ -497,10 +517,10 @@ static ba_status sync_scalars(ba_problem* p) {
   CUDA_OR(p, cudaMemcpyAsync(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
   CUDA_OR(p, cudaStreamSynchronize(p->stream));
   if (p->hS->flags & PCG_FLAG_TIMEOUT) {
-    // a bulk copy of S into shared memory did not complete within the PCG kernel's bounded wait
+    // a bounded wait of the PCG kernel ran out: a grid barrier (wait_budget_cycles) or a bulk copy of S
     const int cleared = p->hS->flags & ~PCG_FLAG_TIMEOUT;
     CUDA_OR(p, cudaMemcpy(&p->S->flags, &cleared, sizeof(int), cudaMemcpyHostToDevice));
-    return set_err(p, BA_ERR_TIMEOUT, "PCG: a shared-memory copy of S timed out");
+    return set_err(p, BA_ERR_TIMEOUT, "PCG: a bounded device wait (grid barrier or copy of S) ran out");
   }
   return BA_OK;
 }
@@ -515,6 +535,7 @@ static ba_status build_reduced_t(ba_problem* p, double lambda, bool* relin) {
   if (!p->have_lin) {
     launch_prepare<T>(*p, false);
     launch_linearize<T>(*p);
+    launch_rel_linearize(*p);
     p->have_lin = true;
     if (relin) *relin = true;
   }
@@ -522,6 +543,7 @@ static ba_status build_reduced_t(ba_problem* p, double lambda, bool* relin) {
   launch_invert<T>(*p, lambda);
   MARK(1);
   launch_schur<T>(*p, lambda);  // records ev[3] between the item and the block pass
+  launch_rel_offdiag<T>(*p);
   MARK(3);
   CUDA_OR(p, cudaGetLastError());
   p->have_reduced = true;
@@ -543,6 +565,7 @@ static ba_status solve_reduced_t(ba_problem* p) {
   if (p->pcg_err != cudaSuccess) return set_err(p, BA_ERR_CUDA, std::string("PCG launch: ") + cudaGetErrorString(p->pcg_err));
   MARK(5);
   launch_backsub<T>(*p);
+  launch_rel_pred(*p);
   MARK(6);
   CUDA_OR(p, cudaGetLastError());
   return BA_OK;
@@ -561,6 +584,7 @@ static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
   launch_prepare<T>(*p, true);
   MARK(7);
   launch_cost(*p, true);
+  launch_rel_cost(*p, true);
   MARK(8);
   launch_decide(*p);
   MARK(9);
@@ -1039,6 +1063,7 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
       return set_err(p0, BA_ERR_ARG, "all windows of a batch must use the same precision");
     if (p->device != p0->device) return set_err(p0, BA_ERR_ARG, "all windows of a batch must be on one device");
     ba_status s = freeze(p);
+    if (!s && p->nrel) s = set_err(p, BA_ERR_ARG, "inter-group relations are not supported in batched windows");
     if (!s) s = ensure_sstore(p, true);
     if (s) return set_err(p0, s, "window " + std::to_string(i) + ": " + p->err);
     if (p->typed)

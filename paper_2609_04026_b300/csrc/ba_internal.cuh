@@ -193,6 +193,7 @@ struct ba_problem {
   std::vector<double> h_cam;      // n x 12: q(4) t(3) f k1 k2 ppx ppy
   std::vector<uint8_t> h_fixed;
   std::vector<double> h_pts, h_lin, h_pln, h_vps;
+  std::vector<int32_t> h_rel;     // inter-group relations as added: 5 per relation (kind_a, a, kind_b, b, type)
   // residual records as added, copied to the device at add time (validated and merged by the structure build,
   // which releases them); cam is null for VP records, other may be null, meas holds n x meas_dim values
   struct ObsBatch {
@@ -267,6 +268,14 @@ struct ba_problem {
   int4* tchunk = nullptr;
   int64_t tvals = 0, gg_val0 = 0;   // values of the typed storage; first value of the group-group region
   double* part_g = nullptr;      // per group value, every CTA's share of the scatter (gv x G)
+  // inter-group relations: per relation its two group entities (A indices) and type; per group entity the
+  // relations it takes part in (relation << 1 | side, in relation order); the distinct pairs of entities with
+  // their relations and the full positions of both blocks; linearisation (double): r (3), J_a, J_b (3 x 6
+  // each, padded), IRLS weight; per group entity the summed J^T w J (36) and J^T w r (6)
+  int64_t nrel = 0, nrelpair = 0;
+  int32_t *rel_ga = nullptr, *rel_gb = nullptr, *rel_type = nullptr, *grel_ptr = nullptr, *grel_idx = nullptr;
+  int32_t *rp_ptr = nullptr, *rp_idx = nullptr, *rp_pos = nullptr;
+  double *rel_lin = nullptr, *relH = nullptr, *relG = nullptr;
   int pcg_grid = 0;
   size_t pcg_smem = 0;
   cudaError_t pcg_err = cudaSuccess;
@@ -300,6 +309,14 @@ struct ba_problem {
 
 namespace ba {
 ba_status build_structure(Problem& P);   // structure.cu
+// inter-group relations (relations.cu): device lists at freeze, linearisation, their share of S, b, the cost
+// and the predicted decrease
+ba_status build_relations(Problem& P);
+ba_status relation_positions(Problem& P);
+void launch_rel_linearize(Problem& P);
+template <class T> void launch_rel_offdiag(Problem& P);
+void launch_rel_cost(Problem& P, bool candidate);
+void launch_rel_pred(Problem& P);
 // typed storage of the reduced system (structure.cu): per full position its stored copy, column codes of the
 // typed blocks, and the host plan of chunks; see TY_CC
 struct TypedPlan {

@@ -725,6 +725,7 @@ struct BlockArgs {
   T* Sval;
   SView sv;        // where each block of S is stored (full or typed storage)
   double *b, *Dg, *sdiag;
+  const double *relH, *relG;   // inter-group relations: per group entity J^T w J (36) and J^T w r (6), or null
   int64_t nc;
   double lambda;
 };
@@ -792,8 +793,17 @@ __device__ __forceinline__ T pair_direct(const UnitArgs<T>& a, int ea, bool diag
 // a diagonal block of S from its sums: symmetric part, damping lambda D on the real dimensions, a unit
 // diagonal on padding and held camera components; writes S, b, D and the diagonal of S
 template <class T>
-__device__ void finish_diag(const BlockArgs<T>& a, int row, int fpos, double (&s)[36], const double (&bb)[6],
-                            const double (&hh)[6]) {
+__device__ void finish_diag(const BlockArgs<T>& a, int row, int fpos, double (&s)[36], double (&bb)[6],
+                            double (&hh)[6]) {
+  // a group's inter-group relations (direct terms of H_gg and g_g, Section 3.2), before the damping
+  if (a.relH && row >= a.nc) {
+    const double* H = a.relH + 36 * (size_t)(row - a.nc);
+    const double* G = a.relG + 6 * (size_t)(row - a.nc);
+#pragma unroll
+    for (int e = 0; e < 36; ++e) s[e] += H[e];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { bb[i] -= G[i]; hh[i] += H[7 * i]; }
+  }
   // Z_e^T Z_e is symmetric by construction and so is H_e; the symmetric part is taken anyway so
   // that CG always sees an exactly symmetric S
 #pragma unroll
@@ -2997,6 +3007,7 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.col = P.col;
   b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.Sval = (T*)P.Sval; b.sv = sview_of(P);
   b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nc = d.nc; b.lambda = lambda;
+  b.relH = P.nrel ? P.relH : nullptr; b.relG = P.nrel ? P.relG : nullptr;
   UnitArgs<T> un;
   un.un_se = P.un_se; un.un_blk = P.un_blk; un.un_order = P.un_order; un.up_un = P.up_un; un.multi = P.multi_blk;
   un.un_desc = reinterpret_cast<const int4*>(P.un_desc); un.un_mflag = P.un_mflag;

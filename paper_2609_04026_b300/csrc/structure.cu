@@ -384,6 +384,12 @@ __global__ void k_pattern_pairs(const int32_t* __restrict__ fslot_off, const int
   }
 }
 
+// inter-group relations couple their two groups directly (H_gg)
+__global__ void k_pattern_rel(int64_t n, const int32_t* __restrict__ ga, const int32_t* __restrict__ gb, Bitmap bm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) { bm.set(ga[i], gb[i]); bm.set(gb[i], ga[i]); }
+}
+
 __global__ void k_pattern_diag(int64_t na, Bitmap bm) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a < na) bm.set(a, a);
@@ -818,9 +824,11 @@ ba_status build_structure(Problem& P) {
   int32_t* wpre = S.get<int32_t>(na * wpr);
   if (!bm.w || !wpre) return oom();
   CU(cudaMemsetAsync(bm.w, 0, sizeof(uint32_t) * na * wpr, P.stream));
+  if ((s = build_relations(P))) return s;
   if (na) {
     k_pattern_diag<<<grid_of(na, NT), NT, 0, P.stream>>>(na, bm);
     if (nf) k_pattern_pairs<<<grid_of(nf, NT), NT, 0, P.stream>>>(P.fslot_off, P.slot_ent, nf, bm);
+    if (P.nrel) k_pattern_rel<<<grid_of(P.nrel, NT), NT, 0, P.stream>>>(P.nrel, P.rel_ga, P.rel_gb, bm);
   }
   int64_t *full_cnt = S.get<int64_t>(na + 1), *pad_cnt = S.get<int64_t>(na + 1), *up_cnt = S.get<int64_t>(na + 1);
   int64_t *rowp = S.get<int64_t>(na + 1), *prow = S.get<int64_t>(na + 1), *uptr = S.get<int64_t>(na + 1);
@@ -839,6 +847,7 @@ ba_status build_structure(Problem& P) {
   if (!P.row_ptr || !P.col || !P.row_len || !P.up_row || !P.up_full || !P.up_mirror) return oom();
   RowFill rf{prow, uptr, wpre, nlow, P.col, P.up_row, P.up_full, P.up_mirror, P.row_ptr, P.row_len, full_cnt};
   k_pattern_fill<<<grid_of(na + 1, NT), NT, 0, P.stream>>>(na, bm, rf);
+  if ((s = relation_positions(P))) return s;
   P.h_prow_ptr.assign(na + 1, 0);
   P.h_row_len.assign(na, 0);
   CU(cudaMemcpyAsync(P.h_prow_ptr.data(), P.row_ptr, sizeof(int32_t) * (na + 1), cudaMemcpyDeviceToHost, P.stream));

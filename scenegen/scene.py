@@ -66,6 +66,7 @@ class SceneConfig:
     feat_noise: float = 0.1
     group_rot_noise_deg: float = 2.0
     group_off_noise: float = 0.05
+    relations: bool = False          # inter-group orthogonality / parallelism that hold in the ground truth
     seed: int = 1
 
 
@@ -459,6 +460,31 @@ def make_scene(cfg: SceneConfig) -> dict:
     else:
         vps0 = np.zeros((0, 3))
     intr = np.stack([f, k1, k2], 1)
+    # ---- inter-group relations (no random draws: the other outputs do not change).  Each plane with the
+    # next one (parallel on the same axis, orthogonal otherwise); the axis VPs pairwise orthogonal; each axis
+    # VP orthogonal to the normal of the first plane of another axis and parallel to that of its own axis.
+    # Group kinds: 0 plane, 1 VP; types: 0 orthogonal, 1 parallel.
+    rel = dict(ka=[], a=[], kb=[], b=[], type=[])
+
+    def add_rel(ka, a, kb, b, t):
+        for k_, v_ in (("ka", ka), ("a", a), ("kb", kb), ("b", b), ("type", t)):
+            rel[k_].append(v_)
+    if cfg.relations:
+        for i in range(npl if npl > 1 else 0):
+            j = (i + 1) % npl
+            add_rel(0, i, 0, j, 1 if pl_axis[i] == pl_axis[j] else 0)
+        na_vp = min(nv, 3)
+        for i in range(na_vp):
+            for j in range(i + 1, na_vp):
+                add_rel(1, i, 1, j, 0)
+        for k_ in range(na_vp):
+            other = np.flatnonzero(pl_axis != k_)
+            same = np.flatnonzero(pl_axis == k_)
+            if len(other):
+                add_rel(1, k_, 0, int(other[0]), 0)
+            if len(same):
+                add_rel(1, k_, 0, int(same[0]), 1)
+    relations = {k_: np.asarray(v_, np.int8 if k_ in ("ka", "kb", "type") else np.int32) for k_, v_ in rel.items()}
     # gauge (7-DoF similarity): camera 0's pose is held (mask 0x3F) and, for the scale, the translation
     # component of camera 1 that moves most when the scene is scaled about camera 0's centre
     fixed = np.zeros(Nc, np.uint8)
@@ -472,7 +498,7 @@ def make_scene(cfg: SceneConfig) -> dict:
         name=cfg.name, seed=cfg.seed, fixed=fixed,
         cams=dict(q=_mat_to_quat(R0), t=t0, intr=intr, pp=pp),
         points=P0, lines=lines0, planes=planes0, vps=vps0,
-        obs=obs,
+        obs=obs, relations=relations,
         gt=dict(cams=dict(q=qgt, t=tgt.copy(), intr=intr.copy(), pp=pp.copy()), points=P.copy(),
                 lines=gt_lines, planes=gt_planes, vps=vp.copy()),
         info=dict(n_wf_points=n_wf_pts, n_wf_lines=n_wf_lines, n_edges=len(edges),

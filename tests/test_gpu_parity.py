@@ -314,3 +314,26 @@ def test_misaligned_device_allocator_is_refused(B):
     if p is not None:
         B.ba_destroy(p)
     assert not held
+
+
+def test_pcg_barrier_wait_budget_runs_out(B):
+    """A grid-barrier wait of the persistent PCG that outlasts ba_options.wait_budget_cycles ends the solve:
+    with a budget of one clock cycle the barriers give up, the step returns BA_ERR_TIMEOUT, and the problem
+    and the CUDA context stay usable (the waits for the bulk copies of S are not shortened: every kernel
+    drains its copies before it ends).  A fresh problem with the default budget then steps normally."""
+    s = scene("small")
+    p = gpu_problem(B, s, precision=B.BA_MIXED, wait_budget_cycles=1)
+    try:
+        with pytest.raises(B.BAError) as e:
+            B.ba_lm_step(p)
+        assert e.value.status == B.BA_ERR_TIMEOUT
+        E, _ = B.ba_eval_cost(p)
+        assert np.isfinite(E)
+    finally:
+        B.ba_destroy(p)
+    q = gpu_problem(B, s, precision=B.BA_MIXED)
+    try:
+        r = B.ba_lm_step(q)
+        assert r.pcg_iters > 0 and np.isfinite(r.cost_new)
+    finally:
+        B.ba_destroy(q)

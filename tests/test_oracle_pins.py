@@ -432,3 +432,98 @@ def test_termination_uses_pixel_cost():
     opt2 = O.Options(rel_cost_tol=2.0 ** -20)
     assert not O.step_converged(dict(accepted=True, E=1.0, E_new=1.0, Epx=1.0, Epx_new=1.0 - 2.0 ** -20), opt2)
     assert O.step_converged(dict(accepted=True, E=1.0, E_new=1.0, Epx=1.0, Epx_new=1.0 - 2.0 ** -21), opt2)
+
+
+# ---------------------------------------------------------------- inter-group relations (Section 3.2)
+def _rel_obs(s):
+    return dict(s["obs"], relations=s["relations"])
+
+
+def test_relation_residual_closed_form():
+    """Two unit directions at a hand-set angle theta: orthogonality r = cos(theta), parallelism
+    r = a x b = (0, 0, sin(theta)) for a = e_x, b = (cos, sin, 0); plane normals and VPs alike."""
+    th = 0.3
+    z3 = torch.zeros(3)
+    a_pl = torch.tensor([1.0, 0.0, 0.0, 2.0])               # plane x = -2 (n, w)
+    b_vp = torch.tensor([math.cos(th), math.sin(th), 0.0, 0.0])
+    for ka, kb, ga, gb in ((0, 1, a_pl, b_vp), (1, 0, torch.tensor([1.0, 0, 0, 0]), torch.tensor([math.cos(th), math.sin(th), 0, -1.0])),
+                           (1, 1, torch.tensor([1.0, 0, 0, 0]), b_vp), (0, 0, a_pl, torch.tensor([math.cos(th), math.sin(th), 0, 0.5]))):
+        r_o = O.res_relation(z3, z3, ga, gb, torch.tensor(ka), torch.tensor(kb), torch.tensor(O.REL_ORTH))
+        r_p = O.res_relation(z3, z3, ga, gb, torch.tensor(ka), torch.tensor(kb), torch.tensor(O.REL_PAR))
+        np.testing.assert_allclose(r_o.numpy(), [math.cos(th), 0, 0], atol=1e-14)
+        np.testing.assert_allclose(r_p.numpy(), [0, 0, math.sin(th)], atol=1e-14)
+
+
+def test_relation_jacobian_finite_differences():
+    """Central differences through the group retractions agree with the relation Jacobians, for every pair of
+    group kinds and both relation types."""
+    s = make_scene(config("small", relations=True))
+    st = O.state_from_scene(s)
+    rel = s["relations"]
+    assert set(zip(rel["ka"].tolist(), rel["kb"].tolist(), rel["type"].tolist())) >= {(0, 0, 0), (0, 0, 1), (1, 1, 0),
+                                                                                       (1, 0, 0), (1, 0, 1)}
+    r, Ja, Jb = O.relation_residuals(st, rel, with_jac=True)
+    ga, gb, ka, kb, ty = O._rel_records(st, rel)
+    h = 1e-6
+    for side, J in ((0, Ja), (1, Jb)):
+        for j in range(3):
+            def ev(sgn):
+                d = torch.zeros((len(ka), 3))
+                d[:, j] = sgn * h
+                z = torch.zeros((len(ka), 3))
+                args = (d, z) if side == 0 else (z, d)
+                return torch.stack([O.res_relation(args[0][i], args[1][i], ga[i], gb[i], ka[i], kb[i], ty[i])
+                                    for i in range(len(ka))])
+            fd = (ev(1) - ev(-1)) / (2 * h)
+            assert float((fd - J[:, :, j]).abs().max()) <= 1e-7, (side, j)
+
+
+def test_relations_vanish_at_ground_truth_and_change_only_group_blocks():
+    """Manhattan relations hold exactly in the noise-free scene (zero residual, zero added cost); in the
+    normal equations they add only to group-group blocks (H_gg) -- the camera and feature blocks of H are
+    those of the scene without relations (Section 3.2: no effect on H_ff or the Schur structure)."""
+    s = noise_free(config("tiny", relations=True))
+    st = O.state_from_scene(s)
+    r = O.relation_residuals(st, s["relations"])
+    assert float(r.abs().max()) < 1e-12
+    s2 = make_scene(config("tiny", relations=True))
+    st2 = O.state_from_scene(s2)
+    lay = O.Layout(st2, s2["fixed"])
+    opt = O.Options()
+    H0, _ = O.normal_equations(*O.linearize(st2, s2["obs"], opt, lay))
+    H1, _ = O.normal_equations(*O.linearize(st2, _rel_obs(s2), opt, lay))
+    d = (H1 - H0).tocoo()
+    g0 = lay.plane_col[0] if lay.npl else lay.vp_col[0]
+    g1 = lay.na
+    nz = np.abs(d.data) > 0
+    assert nz.any()
+    assert ((d.row[nz] >= g0) & (d.row[nz] < g1) & (d.col[nz] >= g0) & (d.col[nz] < g1)).all()
+    E0, P0 = O.cost(st2, s2["obs"], opt)
+    E1, P1 = O.cost(st2, _rel_obs(s2), opt)
+    assert E1 > E0 and P1 == P0     # angular terms: in E, not in E_px
+
+
+def test_schur_with_relations_equals_dense_full_solve():
+    s = make_scene(config("tiny", relations=True))
+    st = O.state_from_scene(s)
+    obs = _rel_obs(s)
+    opt = O.Options(solver="dense")
+    lay = O.Layout(st, s["fixed"])
+    lam = 1e-3
+    Jt, rt = O.linearize(st, obs, opt, lay)
+    H, g = O.normal_equations(Jt, rt)
+    D = O.damping_diag(H)
+    full = np.linalg.solve(H.toarray() + np.diag(lam * D), -g)
+    delta, info = O.solve_step(st, obs, opt, lam, lay, (Jt, rt))
+    assert np.linalg.norm(delta - full) / np.linalg.norm(full) < 1e-10
+
+
+def test_relation_cost_rotation_invariant():
+    """The relation residuals compare directions only: a rotation of the whole scene leaves them unchanged."""
+    s = make_scene(config("small", relations=True))
+    st = O.state_from_scene(s)
+    Rs = scipy.spatial.transform.Rotation.from_rotvec([0.4, -0.2, 0.9]).as_matrix()
+    st2 = _similarity(st, 1.7, Rs, np.array([0.3, 1.0, -2.0]))
+    r1 = O.relation_residuals(st, s["relations"]).norm(dim=-1)
+    r2 = O.relation_residuals(st2, s["relations"]).norm(dim=-1)
+    assert float((r1 - r2).abs().max()) < 1e-12
