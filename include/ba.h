@@ -141,6 +141,7 @@ typedef struct ba_solve_report {
   double cost0, cost, cost_px;
   double ms_structure;          /* one-time structure build (analogue of symbolic analysis) */
   double ms_total;              /* wall time of the whole solve */
+  double ms_window;             /* ba_solve_batch: this window's own device time on its CTA (global timer) */
 } ba_solve_report;
 
 /* Fill *o with the defaults listed above. */
@@ -233,7 +234,9 @@ ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* d
  * shape (threads per CTA, CTAs per SM) from the same state, keeps the fastest and caches it per (GPU,
  * precision, size class); the chosen shape is readable with ba_batch_launch_shape(windows[0], ...).
  * reports (n, may be NULL): iters, accepted steps, converged, initial and final cost; ms_total = the graph's
- * device time for the whole batch. */
+ * device time for the whole batch; ms_window = the window's own time on its CTA.  The instantiated graph is
+ * kept with windows[0] (until it is destroyed) and launched again when the same windows, in the same order,
+ * are solved with the same iteration count. */
 ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_iters, int autotune, ba_solve_report* reports);
 ba_status ba_batch_launch_shape(const ba_problem* p, int* threads, int* grid);
 

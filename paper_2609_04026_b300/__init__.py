@@ -66,7 +66,8 @@ class ba_step_report(C.Structure):
 class ba_solve_report(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("accepted_steps", C.c_int),
                 ("total_pcg_iters", C.c_int), ("cost0", C.c_double), ("cost", C.c_double),
-                ("cost_px", C.c_double), ("ms_structure", C.c_double), ("ms_total", C.c_double)]
+                ("cost_px", C.c_double), ("ms_structure", C.c_double), ("ms_total", C.c_double),
+                ("ms_window", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

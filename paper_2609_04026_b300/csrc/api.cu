@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -73,13 +74,28 @@ extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
   p->alloc.fa = p->opt.dev_alloc; p->alloc.ff = p->opt.dev_free; p->alloc.ctx = p->opt.alloc_ctx;
   p->stream = (cudaStream_t)p->opt.cuda_stream;
   if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); delete p; return BA_ERR_CUDA; }
+  static std::atomic<uint64_t> next_serial{1};
+  p->serial = next_serial++;
   *out = p;
   return BA_OK;
+}
+
+static void release_batch_graph(ba_problem* p) {
+  auto& g = p->bgraph;
+  if (g.stream) cudaStreamSynchronize(g.stream);
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  if (g.stream) cudaStreamDestroy(g.stream);
+  p->alloc.put(g.desc);
+  p->alloc.put(g.order);
+  p->alloc.put(g.queue);
+  g = ba_problem::BatchGraph();
 }
 
 extern "C" void ba_destroy(ba_problem* p) {
   if (!p) return;
   cudaStreamSynchronize(p->stream);
+  release_batch_graph(p);
   p->release_obs();
   for (auto& b : p->bufs) p->alloc.put(b.p);
   p->bufs.clear();
@@ -909,10 +925,10 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   for (int i = 0; i < n; ++i) {
     ba_problem* p = w[i];
     if (!p->win_state) {
-      p->win_state = p->dnew<int>(5);
+      p->win_state = p->dnew<int>(8);
       if (!p->win_state) return set_err(p0, BA_ERR_OOM, "device allocation failed");
     }
-    int s0[5] = {p->cur, p->have_lin ? 1 : 0, 0, 0, 0};
+    int s0[8] = {p->cur, p->have_lin ? 1 : 0, 0, 0, 0, 0, 0, 0};
     CUDA_OR(p0, cudaMemcpyAsync(p->win_state, s0, sizeof(s0), cudaMemcpyHostToDevice, st));
     CUDA_OR(p0, cudaStreamSynchronize(st));
     fill_window_desc<T>(*p, host.data() + dsz * i);
@@ -926,14 +942,24 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   std::sort(sz.begin(), sz.end());
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = sz[i].second;
-  void* d_desc = p0->alloc.get(host.size());
-  int* d_order = (int*)p0->alloc.get(sizeof(int) * n);
-  int* d_queue = (int*)p0->alloc.get(sizeof(int));
-  if (!d_desc || !d_order || !d_queue) return set_err(p0, BA_ERR_OOM, "device allocation failed");
-  struct Free {
-    ba::Alloc& a; void *x, *y, *z;
-    ~Free() { cudaDeviceSynchronize(); a.put(x); a.put(y); a.put(z); }
-  } guard{p0->alloc, d_desc, d_order, d_queue};
+  // the batch's identity: its windows (by serial, in order), the iteration count and the precision; a graph
+  // kept from an earlier call with the same identity is launched again with its buffers
+  std::vector<uint64_t> bkey;
+  bkey.push_back((uint64_t)iters);
+  bkey.push_back(sizeof(T));
+  for (int i = 0; i < n; ++i) bkey.push_back(w[i]->serial);
+  auto& bg = p0->bgraph;
+  const bool reuse = bg.exec && bg.key == bkey;
+  if (!reuse) {
+    release_batch_graph(p0);
+    bg.desc = p0->alloc.get(host.size());
+    bg.order = p0->alloc.get(sizeof(int) * n);
+    bg.queue = p0->alloc.get(sizeof(int));
+    if (!bg.desc || !bg.order || !bg.queue) { release_batch_graph(p0); return set_err(p0, BA_ERR_OOM, "device allocation failed"); }
+  }
+  void* d_desc = bg.desc;
+  int* d_order = (int*)bg.order;
+  int* d_queue = (int*)bg.queue;
   CUDA_OR(p0, cudaMemcpyAsync(d_desc, host.data(), host.size(), cudaMemcpyHostToDevice, st));
   CUDA_OR(p0, cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   const size_t smem = sizeof(double) * 6 * (size_t)max_nch;
@@ -990,49 +1016,49 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
     std::lock_guard<std::mutex> g(g_batch_lock);
     g_batch_cache[key] = cfg;
   }
-  // ---- the solve: queue reset + persistent kernel, captured once in a graph and launched
-  // capture is not allowed on the legacy default stream: capture and launch on a private stream that
-  // starts after the caller's stream has drained
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  // ---- the solve: queue reset + persistent kernel, captured once in a graph (kept for the next call with
+  // the same batch) and launched.  Capture is not allowed on the legacy default stream: capture and launch on a
+  // private stream that starts after the caller's stream has drained
   const int grid = grid_of(cfg);
   CUDA_OR(p0, cudaStreamSynchronize(st));
-  cudaStream_t cap = nullptr;
-  CUDA_OR(p0, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  struct StreamGuard {
-    cudaStream_t s;
-    ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
-  } sguard{cap};
-  CUDA_OR(p0, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t le = launch_windows<T>(cap, d_desc, d_order, n, iters, d_queue, cfg.threads, grid, smem);
-  cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-  if (le != cudaSuccess || ce != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
-    return set_err(p0, BA_ERR_CUDA, std::string("batched graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+  if (!reuse || bg.threads != cfg.threads || bg.grid != grid) {
+    if (bg.exec) { cudaGraphExecDestroy(bg.exec); bg.exec = nullptr; }
+    if (bg.graph) { cudaGraphDestroy(bg.graph); bg.graph = nullptr; }
+    if (!bg.stream) CUDA_OR(p0, cudaStreamCreateWithFlags(&bg.stream, cudaStreamNonBlocking));
+    CUDA_OR(p0, cudaStreamBeginCapture(bg.stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = launch_windows<T>(bg.stream, d_desc, d_order, n, iters, d_queue, cfg.threads, grid, smem);
+    cudaError_t ce = cudaStreamEndCapture(bg.stream, &bg.graph);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      cudaGetLastError();
+      release_batch_graph(p0);
+      return set_err(p0, BA_ERR_CUDA, std::string("batched graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    CUDA_OR(p0, cudaGraphInstantiate(&bg.exec, bg.graph, 0));
+    bg.key = bkey;
+    bg.threads = cfg.threads;
+    bg.grid = grid;
   }
-  CUDA_OR(p0, cudaGraphInstantiate(&exec, graph, 0));
   cudaEvent_t e0, e1;
   CUDA_OR(p0, cudaEventCreate(&e0));
   CUDA_OR(p0, cudaEventCreate(&e1));
-  CUDA_OR(p0, cudaEventRecord(e0, cap));
-  CUDA_OR(p0, cudaGraphLaunch(exec, cap));
-  CUDA_OR(p0, cudaEventRecord(e1, cap));
+  CUDA_OR(p0, cudaEventRecord(e0, bg.stream));
+  CUDA_OR(p0, cudaGraphLaunch(bg.exec, bg.stream));
+  CUDA_OR(p0, cudaEventRecord(e1, bg.stream));
   CUDA_OR(p0, cudaEventSynchronize(e1));
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
   CUDA_OR(p0, cudaGetLastError());
   p0->batch_threads = cfg.threads;
   p0->batch_grid = grid;
   // ---- bring every window's host state up to date
   for (int i = 0; i < n; ++i) {
     ba_problem* p = w[i];
-    int sw[5];
+    int sw[8];
     CUDA_OR(p0, cudaMemcpy(sw, p->win_state, sizeof(sw), cudaMemcpyDeviceToHost));
+    unsigned long long wns = 0;
+    std::memcpy(&wns, sw + 6, sizeof(wns));
     CUDA_OR(p0, cudaMemcpy(p->hS, p->S, sizeof(DevScalars), cudaMemcpyDeviceToHost));
     p->cur = sw[0];
     p->have_lin = sw[1] != 0;
@@ -1046,6 +1072,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
       r.cost = p->hS->E;
       r.cost_px = p->hS->Epx;
       r.ms_total = ms;
+      r.ms_window = (double)wns * 1e-6;
     }
   }
   return BA_OK;

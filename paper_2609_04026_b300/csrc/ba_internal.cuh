@@ -296,7 +296,19 @@ struct ba_problem {
   uint8_t* pre_mask = nullptr;  // real dimensions per block row
   int* pre_fallbacks = nullptr; // blocks that fell back to block-Jacobi in the last build
   bool pre_ready = false;
-  int* win_state = nullptr;     // batched windows: device copy of (set, linearised, steps, accepted, converged)
+  int* win_state = nullptr;     // batched windows: device copy of (set, linearised, steps, accepted, converged,
+                                // pad, then the window's device time in ns as a 64-bit value at int 6)
+  uint64_t serial = 0;          // unique per problem (a batch is identified by its windows' serials)
+  // the last batch started from this problem: its instantiated graph and the buffers the graph's kernel reads,
+  // kept so that the same batch launched again reuses them
+  struct BatchGraph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t stream = nullptr;
+    void *desc = nullptr, *order = nullptr, *queue = nullptr;
+    int threads = 0, grid = 0;
+  } bgraph;
   int batch_threads = 0, batch_grid = 0;  // launch shape of the last batched solve started from this problem
   double* red = nullptr;        // per-block partial sums of reductions
   int red_cap = 0;

@@ -181,3 +181,22 @@ def test_batch_fp64_matches_oracle_on_largest_windows(B):
         E = rep["E_new"] if rep["accepted"] else rep["E"]
         assert r.accepted_steps == int(rep["accepted"])
         assert abs(r.cost - E) <= 1e-9 * E, (r.cost, E)
+
+
+def test_batch_graph_kept_and_relaunched(B):
+    """The instantiated graph of a batch is kept with its first window and launched again when the same windows
+    are solved with the same iteration count: two calls of 3 iterations (the second relaunching the kept graph)
+    end where one call of 6 iterations does, window by window, and every window reports its own device time."""
+    ws = windows(4, 800, seed=14)
+    pa = [gpu_problem(B, s, precision=B.BA_FP64) for s in ws]
+    pb = [gpu_problem(B, s, precision=B.BA_FP64) for s in ws]
+    try:
+        B.ba_solve_batch(pa, lm_iters=3, autotune=False)
+        ra = B.ba_solve_batch(pa, lm_iters=3, autotune=False)
+        rb = B.ba_solve_batch(pb, lm_iters=6, autotune=False)
+        for x, y in zip(ra, rb):
+            assert abs(x.cost - y.cost) <= 1e-12 * y.cost, (x.cost, y.cost)
+            assert x.ms_window > 0 and x.ms_window <= x.ms_total * 1.01
+    finally:
+        for p in pa + pb:
+            B.ba_destroy(p)
