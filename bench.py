@@ -406,18 +406,21 @@ def main():
         B.ba_solve_batch(ps, lm_iters=10, autotune=False)     # captures the batch's graph
         reps = B.ba_solve_batch(ps, lm_iters=10, autotune=False)   # launches the kept graph again
         shape = B.ba_batch_launch_shape(ps[0])
+        nct = B.ba_batch_ctas_per_window(ps[0])
         for h in ps:
             B.ba_destroy(h)
         ms_b = reps[0].ms_total
         nres = sum(sum(int(len(o["feat"])) for o in w_["obs"].values()) for w_ in wins)
         batched = {"windows": args.windows, "lm_iters_each": 10, "ms": round(ms_b, 3),
                    "window_lm_iters_per_s": round(args.windows * 10 / (ms_b / 1e3), 1),
-                   "residuals_total": nres, "launch_shape": {"threads": shape[0], "ctas": shape[1]},
+                   "residuals_total": nres,
+                   "launch_shape": {"threads": shape[0], "ctas": shape[1], "ctas_per_window": nct,
+                                    "note": "chosen by the library's autotuner"},
                    "window_ms": {"max": round(max(r.ms_window for r in reps), 3),
                                  "mean": round(float(np.mean([r.ms_window for r in reps])), 3),
-                                 "sum_over_sms": round(sum(r.ms_window for r in reps) / shape[1], 3),
-                                 "note": "each window's own device time on its CTA; sum_over_sms = the sum divided by "
-                                         "the CTAs of the launch, the makespan of a perfect balance"},
+                                 "balanced": round(sum(r.ms_window for r in reps) * nct / shape[1], 3),
+                                 "note": "each window's own device time on its CTAs; balanced = the sum of window x "
+                                         "CTA times over the launch's CTAs, the makespan of a perfect balance"},
                    "accepted_steps": int(sum(r.accepted_steps for r in reps)),
                    "cost_decreased": int(sum(r.cost < r.cost0 for r in reps)),
                    "note": "cameras 5-40, features log-uniform 200-20k (70% points), 0-8 groups per window; "

@@ -110,6 +110,8 @@ typedef struct ba_options {
                                 the slow tail of the iteration (measured at 2000 cameras) */
   double w_rel;             /* loss weight of the inter-group relations (5e3, the VP term's) */
   double cauchy_rel;        /* Cauchy scale of the inter-group relations (0.2, the VP term's) */
+  int batch_ctas_per_window; /* ba_solve_batch, read from windows[0]: 0 = chosen by the autotuner (or 1); 1, 2 or 4
+                                = every window on a thread-block cluster of that many CTAs (256 threads each) */
 } ba_options;
 
 /* Per-LM-step report. */
@@ -226,12 +228,13 @@ ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* d
 /* Batched local windows: solve n independent problems (windows) with lm_iters LM iterations each, all in one
  * persistent kernel launch captured in a CUDA graph (local bundle adjustment after every registered image
  * dominates incremental SfM, Section 4 / Appendix A.2).  Every window is a problem built with the calls above;
- * all windows must use the same precision and device, and run on the stream of windows[0].  A CTA takes the
- * next window from a device queue (largest first) and runs its iterations on the device (the same linearise /
+ * all windows must use the same precision and device, and run on the stream of windows[0].  A CTA (or a
+ * thread-block cluster of CTAs, which splits the window's features, Schur units and reduced-system rows over
+ * its CTAs) takes the next window from a device queue (largest first) and runs its iterations on the device (the same linearise /
  * invert / Schur / PCG / back-substitute / cost / decide steps as ba_lm_step); every window keeps its own
  * damping and accept / reject state.  A window's `converged` flag reports whether some accepted step met
  * rel_cost_tol or some step was rejected at lambda_max (iteration then continues to lm_iters).  autotune != 0 times one LM step of each candidate launch
- * shape (threads per CTA, CTAs per SM) from the same state, keeps the fastest and caches it per (GPU,
+ * shape (threads per CTA, CTAs per SM, CTAs per window) from the same state, keeps the fastest and caches it per (GPU,
  * precision, size class); the chosen shape is readable with ba_batch_launch_shape(windows[0], ...).
  * reports (n, may be NULL): iters, accepted steps, converged, initial and final cost; ms_total = the graph's
  * device time for the whole batch; ms_window = the window's own time on its CTA.  The instantiated graph is
@@ -239,6 +242,8 @@ ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* d
  * are solved with the same iteration count. */
 ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_iters, int autotune, ba_solve_report* reports);
 ba_status ba_batch_launch_shape(const ba_problem* p, int* threads, int* grid);
+/* CTAs per window (the cluster size) of the last batched solve started from p. */
+ba_status ba_batch_ctas_per_window(const ba_problem* p, int* ctas);
 
 /* Learned correction of the block-Jacobi preconditioner.  The paper solves the reduced system directly; this
  * optional preconditioner for the PCG solve has no counterpart there.  Per diagonal block b of S (6 wide):

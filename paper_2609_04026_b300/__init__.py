@@ -42,7 +42,7 @@ class ba_options(C.Structure):
                 ("pcg_max_iters", C.c_int), ("precond", C.c_int), ("cuda_stream", C.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double),
-                ("w_rel", C.c_double), ("cauchy_rel", C.c_double)]
+                ("w_rel", C.c_double), ("cauchy_rel", C.c_double), ("batch_ctas_per_window", C.c_int)]
 
 
 class ba_step_report(C.Structure):
@@ -106,6 +106,7 @@ def _load():
                                     C.c_char_p, C.c_size_t]),
         "ba_solve_batch": (I, [VP, I, I, I, VP]),
         "ba_batch_launch_shape": (I, [P, C.POINTER(I), C.POINTER(I)]),
+        "ba_batch_ctas_per_window": (I, [P, C.POINTER(I)]),
         "ba_precond_param_count": (I, []),
         "ba_precond_set_weights": (I, [P, VP, I64]),
         "ba_precond_features": (I, [P, VP, VP]),
@@ -504,6 +505,12 @@ def ba_solve_batch(problems, lm_iters=10, autotune=True):
     st = _lib.ba_solve_batch(C.cast(arr, C.c_void_p), n, int(lm_iters), 1 if autotune else 0, C.cast(reps, C.c_void_p))
     _check(problems[0], st)
     return list(reps)
+
+
+def ba_batch_ctas_per_window(p):
+    c = C.c_int()
+    _check(p, _lib.ba_batch_ctas_per_window(p, C.byref(c)))
+    return c.value
 
 
 def ba_batch_launch_shape(p):

@@ -908,7 +908,8 @@ extern "C" ba_status ba_precond_blocks(ba_problem* p, double* blocks, int* fallb
 namespace {
 struct BatchCfg {
   int threads = 256;
-  int per_sm = 1;
+  int per_sm = 1;   // CTAs per SM (windows of one CTA)
+  int nct = 1;      // CTAs per window: a thread-block cluster of nct CTAs works on one window
 };
 std::map<std::string, BatchCfg> g_batch_cache;   // (GPU, precision, size class) -> launch shape
 std::mutex g_batch_lock;
@@ -974,12 +975,24 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   const std::string key = std::string(prop.name) + "/" + (sizeof(T) == 4 ? "f32" : "f64") + "/" + std::to_string(cls);
   BatchCfg cfg;
   bool cached = false;
-  {
+  const int forced = p0->opt.batch_ctas_per_window;
+  if (forced != 0 && forced != 1 && forced != 2 && forced != 4)
+    return set_err(p0, BA_ERR_ARG, "batch_ctas_per_window must be 0, 1, 2 or 4");
+  if (forced > 0) {
+    cfg.nct = forced;
+    cached = true;
+    if (forced > 1 && window_clusters<T>(cfg.threads, smem, forced) < 1)
+      return set_err(p0, BA_ERR_ARG, "no cluster of that many window CTAs fits this GPU");
+  } else {
     std::lock_guard<std::mutex> g(g_batch_lock);
     auto it = g_batch_cache.find(key);
     if (it != g_batch_cache.end()) { cfg = it->second; cached = true; }
   }
   auto grid_of = [&](const BatchCfg& c) {
+    if (c.nct > 1) {
+      const int ncl = window_clusters<T>(c.threads, smem, c.nct);
+      return std::max(1, std::min(n, ncl)) * c.nct;
+    }
     int occ = windows_per_sm<T>(c.threads, smem);
     return std::max(1, std::min(n, sms * std::max(1, std::min(occ, c.per_sm))));
   };
@@ -992,15 +1005,19 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
       CUDA_OR(p0, cudaMemcpy(&snapS[i], w[i]->S, sizeof(DevScalars), cudaMemcpyDeviceToHost));
       CUDA_OR(p0, cudaMemcpy(snapW[i].data(), w[i]->win_state, sizeof(int) * 5, cudaMemcpyDeviceToHost));
     }
-    const BatchCfg cands[4] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}};
+    // launch shapes: threads per CTA, CTAs per SM, and CTAs per window (a cluster splits a window's features,
+    // Schur units and reduced-system rows over its CTAs: the largest windows otherwise set the makespan)
+    const BatchCfg cands[] = {{128, 1, 1}, {128, 2, 1}, {256, 1, 1}, {256, 2, 1}, {128, 1, 2}, {256, 1, 2},
+                              {256, 1, 4}};
     float best = 1e30f;
     cudaEvent_t e0, e1;
     CUDA_OR(p0, cudaEventCreate(&e0));
     CUDA_OR(p0, cudaEventCreate(&e1));
     for (const BatchCfg& c : cands) {
       if (c.per_sm > 1 && windows_per_sm<T>(c.threads, smem) < c.per_sm) continue;
+      if (c.nct > 1 && window_clusters<T>(c.threads, smem, c.nct) < 1) continue;
       CUDA_OR(p0, cudaEventRecord(e0, st));
-      CUDA_OR(p0, launch_windows<T>(st, d_desc, d_order, n, 1, d_queue, c.threads, grid_of(c), smem));
+      CUDA_OR(p0, launch_windows<T>(st, d_desc, d_order, n, 1, d_queue, c.threads, grid_of(c), smem, c.nct));
       CUDA_OR(p0, cudaEventRecord(e1, st));
       CUDA_OR(p0, cudaEventSynchronize(e1));
       float ms = 0;
@@ -1021,12 +1038,12 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   // private stream that starts after the caller's stream has drained
   const int grid = grid_of(cfg);
   CUDA_OR(p0, cudaStreamSynchronize(st));
-  if (!reuse || bg.threads != cfg.threads || bg.grid != grid) {
+  if (!reuse || bg.threads != cfg.threads || bg.grid != grid || bg.nct != cfg.nct) {
     if (bg.exec) { cudaGraphExecDestroy(bg.exec); bg.exec = nullptr; }
     if (bg.graph) { cudaGraphDestroy(bg.graph); bg.graph = nullptr; }
     if (!bg.stream) CUDA_OR(p0, cudaStreamCreateWithFlags(&bg.stream, cudaStreamNonBlocking));
     CUDA_OR(p0, cudaStreamBeginCapture(bg.stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = launch_windows<T>(bg.stream, d_desc, d_order, n, iters, d_queue, cfg.threads, grid, smem);
+    cudaError_t le = launch_windows<T>(bg.stream, d_desc, d_order, n, iters, d_queue, cfg.threads, grid, smem, cfg.nct);
     cudaError_t ce = cudaStreamEndCapture(bg.stream, &bg.graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
       cudaGetLastError();
@@ -1037,6 +1054,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
     bg.key = bkey;
     bg.threads = cfg.threads;
     bg.grid = grid;
+    bg.nct = cfg.nct;
   }
   cudaEvent_t e0, e1;
   CUDA_OR(p0, cudaEventCreate(&e0));
@@ -1051,6 +1069,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   cudaEventDestroy(e1);
   CUDA_OR(p0, cudaGetLastError());
   p0->batch_threads = cfg.threads;
+  p0->batch_nct = cfg.nct;
   p0->batch_grid = grid;
   // ---- bring every window's host state up to date
   for (int i = 0; i < n; ++i) {
@@ -1106,6 +1125,12 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
   if (s == BA_OK && reports)
     for (int i = 0; i < n; ++i) reports[i].cost0 = c0[i];
   return s;
+}
+
+extern "C" ba_status ba_batch_ctas_per_window(const ba_problem* p, int* ctas) {
+  if (!p || !ctas) return BA_ERR_ARG;
+  *ctas = p->batch_nct;
+  return BA_OK;
 }
 
 extern "C" ba_status ba_batch_launch_shape(const ba_problem* p, int* threads, int* grid) {

@@ -3234,8 +3234,49 @@ struct WinDesc {
   int pcg_max_iters;
 };
 
+// The CTAs that work on one window: a thread-block cluster of nct CTAs (nct = 1: a single CTA).  Every phase
+// strides its items over the cluster's threads (or warps) and ends at a cluster barrier, which also orders the
+// global-memory writes of one CTA before the reads of the others; the PCG's rows are split into nct contiguous
+// ranges, one per CTA, so that a row's chunk sums stay in the shared memory of the CTA that formed them.
+struct WinCtx {
+  unsigned rank, nct;
+  __device__ __forceinline__ int64_t t0() const { return (int64_t)rank * blockDim.x + threadIdx.x; }
+  __device__ __forceinline__ int64_t ts() const { return (int64_t)nct * blockDim.x; }
+  __device__ __forceinline__ int64_t w0() const { return (int64_t)rank * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+  __device__ __forceinline__ int64_t ws() const { return (int64_t)nct * (blockDim.x >> 5); }
+  __device__ __forceinline__ void sync() const {
+    if (nct == 1) __syncthreads();
+    else cooperative_groups::this_cluster().sync();
+  }
+};
+
+// cluster-wide sums of two values, the CTA sums added in rank order (identical in every CTA)
+template <int NT>
+__device__ __forceinline__ void win_sum2(const WinCtx& c, double v0, double v1, double* out2) {
+  __shared__ double part[2];
+  cta_sum2<NT>(v0, v1, part);
+  if (c.nct == 1) {
+    out2[0] = part[0];
+    out2[1] = part[1];
+    __syncthreads();
+    return;
+  }
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  cl.sync();
+  double a = 0, b = 0;
+  for (unsigned r = 0; r < c.nct; ++r) {
+    const double* q = cl.map_shared_rank(part, r);
+    a += q[0];
+    b += q[1];
+  }
+  cl.sync();   // every CTA has read the parts before any overwrites its own
+  out2[0] = a;
+  out2[1] = b;
+  __syncthreads();
+}
+
 template <class T, int NT>
-__device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2) {
+__device__ void window_pcg(const WinCtx& cx, const WinDesc<T>& W, double* chunk_mem, double* red2) {
   DotAcc<T>* chunk_y = reinterpret_cast<DotAcc<T>*>(chunk_mem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
@@ -3243,8 +3284,11 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2)
   a.p = W.p;
   a.phl = W.phl;
   const int64_t na = W.na;
+  // this CTA's rows and their chunks
+  const int64_t rb = na * cx.rank / cx.nct, re = na * (cx.rank + 1) / cx.nct;
+  const int qb = W.row_chunk0[rb], qe = W.row_chunk0[re];
   double v0 = 0, v1 = 0;
-  for (int64_t row = threadIdx.x; row < na; row += NT) {
+  for (int64_t row = rb + threadIdx.x; row < re; row += NT) {
     double rv[6], zv[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) { rv[i] = W.b[6 * row + i]; W.x[6 * row + i] = 0; W.r[6 * row + i] = rv[i]; }
@@ -3258,15 +3302,16 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2)
       v1 += rv[i] * rv[i];
     }
   }
-  cta_sum2<NT>(v0, v1, red2);
+  win_sum2<NT>(cx, v0, v1, red2);
   double rz = red2[0];
   const double bb = red2[1];
   const double tol2 = W.pcg_tol * W.pcg_tol * bb;
   double rr = bb;
   int it = 0;
   bool go = bb > 0;
+  if (go) cx.sync();   // p of every row is written before any product reads it
   while (go) {
-    for (int64_t q = warp; q < W.nch; q += NW) {
+    for (int64_t q = qb + warp; q < qe; q += NW) {
       DotAcc<T> acc[6];
       const int blk = W.chunk_beg[q] + lane;
       T B[36];
@@ -3275,16 +3320,16 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2)
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         const DotAcc<T> y = warp_sum_acc(acc[i]);
-        if (lane == 0) chunk_y[6 * q + i] = y;
+        if (lane == 0) chunk_y[6 * (q - qb) + i] = y;
       }
     }
     __syncthreads();
     double pap = 0;
-    for (int64_t row = threadIdx.x; row < na; row += NT) {
+    for (int64_t row = rb + threadIdx.x; row < re; row += NT) {
       DotAcc<T> y[6];
       for (int q = W.row_chunk0[row]; q < W.row_chunk0[row + 1]; ++q)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) acc_add(y[i], chunk_y[6 * q + i]);
+        for (int i = 0; i < 6; ++i) acc_add(y[i], chunk_y[6 * (q - qb) + i]);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         const double yv = y[i].value();
@@ -3292,10 +3337,10 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2)
         pap += yv * W.p[6 * row + i];
       }
     }
-    cta_sum2<NT>(pap, 0.0, red2);
+    win_sum2<NT>(cx, pap, 0.0, red2);
     const double alpha = rz / red2[0];
     v0 = 0; v1 = 0;
-    for (int64_t row = threadIdx.x; row < na; row += NT) {
+    for (int64_t row = rb + threadIdx.x; row < re; row += NT) {
       double rv[6], zv[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -3311,116 +3356,117 @@ __device__ void window_pcg(const WinDesc<T>& W, double* chunk_mem, double* red2)
         v1 += rv[i] * zv[i];
       }
     }
-    cta_sum2<NT>(v0, v1, red2);
+    win_sum2<NT>(cx, v0, v1, red2);
     rr = red2[0];
     const double rz_new = red2[1];
     ++it;
     if (rr <= tol2 || it >= W.pcg_max_iters || !(rr == rr)) break;
     const double beta = rz_new / rz;
     rz = rz_new;
-    for (int64_t k = threadIdx.x; k < 6 * na; k += NT) {
+    for (int64_t k = 6 * rb + threadIdx.x; k < 6 * re; k += NT) {
       const double pk = W.z[k] + beta * W.p[k];
       W.p[k] = pk;
       if (W.phl) W.phl[k] = split2(pk);
     }
-    __syncthreads();
+    cx.sync();
   }
-  if (threadIdx.x == 0) {
+  if (cx.rank == 0 && threadIdx.x == 0) {
     W.S->iters = it;
     W.S->rr = rr;
     W.S->bnorm2 = bb;
   }
-  __syncthreads();
+  cx.sync();
 }
 
 template <class T, int NT>
-__device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
+__device__ void window_step(const WinCtx& cx, const WinDesc<T>& W, double* chunk_y) {
   __shared__ double red2[2];
   __shared__ int s_cur, s_lin;
   if (threadIdx.x == 0) { s_cur = W.state[0]; s_lin = W.state[1]; }
   __syncthreads();
   const int cur = s_cur, nxt = 1 - s_cur;
   const bool flt = sizeof(T) == sizeof(float);
+  const int64_t T0 = cx.t0(), TS = cx.ts();
   // ---- linearise at the current parameters (after an accepted step only)
   if (!s_lin) {
-    for (int64_t i = threadIdx.x; i < W.nc; i += NT) derive_cam<T>(W.cam[cur], W.camD[cur], flt ? W.camT : nullptr, i);
-    for (int64_t i = threadIdx.x; i < W.npl + W.nv; i += NT)
+    for (int64_t i = T0; i < W.nc; i += TS) derive_cam<T>(W.cam[cur], W.camD[cur], flt ? W.camT : nullptr, i);
+    for (int64_t i = T0; i < W.npl + W.nv; i += TS)
       derive_group<T>(W.npl, W.pln[cur], W.vps[cur], W.grpD[cur], flt ? W.grpT : nullptr, i);
     if (flt) {
-      for (int64_t i = threadIdx.x; i < 3 * W.np; i += NT) ((float*)W.ptsT)[i] = (float)W.pts[cur][i];
-      for (int64_t i = threadIdx.x; i < 6 * W.nl; i += NT) ((float*)W.linT)[i] = (float)W.lin_[cur][i];
+      for (int64_t i = T0; i < 3 * W.np; i += TS) ((float*)W.ptsT)[i] = (float)W.pts[cur][i];
+      for (int64_t i = T0; i < 6 * W.nl; i += TS) ((float*)W.linT)[i] = (float)W.lin_[cur][i];
     }
-    __syncthreads();
+    cx.sync();
     LinArgs<T> la = W.lin;
     if (!flt) {
       la.cam = (const T*)W.camD[cur]; la.grp = (const T*)W.grpD[cur];
       la.pts = (const T*)W.pts[cur]; la.lin = (const T*)W.lin_[cur];
     }
-    for (int64_t f = threadIdx.x; f < W.np; f += NT) linearize_feature<T, 3>(la, f);
-    for (int64_t f = W.np + threadIdx.x; f < W.nf; f += NT) linearize_feature<T, 4>(la, f);
-    __syncthreads();
+    for (int64_t f = T0; f < W.np; f += TS) linearize_feature<T, 3>(la, f);
+    for (int64_t f = W.np + T0; f < W.nf; f += TS) linearize_feature<T, 4>(la, f);
+    cx.sync();
   }
   const double lam = W.S->lambda;
   // ---- damp + invert the landmark blocks, Schur complement, block-Jacobi
   {
     InvArgs<T> ia = W.inv;
     ia.lambda = lam;
-    for (int64_t f = threadIdx.x; f < W.nf; f += NT) {
+    for (int64_t f = T0; f < W.nf; f += TS) {
       if (f < W.np) invert_feature<T, 3>(ia, f);
       else invert_feature<T, 4>(ia, f);
     }
   }
-  __syncthreads();
+  cx.sync();
   {
     UnitArgs<T> ua = W.units;
     ua.fb.lambda = lam;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     char* mine = reinterpret_cast<char*>(chunk_y) + (size_t)warp * UnitSmem<T>::bytes;
-    for (int64_t w = warp; w < ua.nun; w += NT / 32) unit_warp<T>(ua, (int)w, mine, lane);
-    __syncthreads();
-    for (int64_t k = threadIdx.x; k < ua.nmulti; k += NT) unit_finish<T>(ua, ua.multi[k]);
+    for (int64_t w = cx.w0(); w < ua.nun; w += cx.ws()) unit_warp<T>(ua, (int)w, mine, lane);
+    cx.sync();
+    for (int64_t k = T0; k < ua.nmulti; k += TS) unit_finish<T>(ua, ua.multi[k]);
   }
-  __syncthreads();
-  for (int64_t r = threadIdx.x; r < W.na; r += NT) precond_row<T, true>(W.row_ptr, W.col, W.Sval, W.Minv, W.S, r, SView());
-  __syncthreads();
+  cx.sync();
+  for (int64_t r = T0; r < W.na; r += TS) precond_row<T, true>(W.row_ptr, W.col, W.Sval, W.Minv, W.S, r, SView());
+  cx.sync();
   // ---- PCG, back-substitution and predicted decrease
-  window_pcg<T, NT>(W, chunk_y, red2);
-  for (int64_t e = threadIdx.x; e < W.back.ne; e += NT) backsub_slot<T>(W.back, e);
-  __syncthreads();
+  window_pcg<T, NT>(cx, W, chunk_y, red2);
+  for (int64_t e = T0; e < W.back.ne; e += TS) backsub_slot<T>(W.back, e);
+  cx.sync();
   double g = 0, h = 0;
-  for (int64_t f = threadIdx.x; f < W.nf; f += NT) {
+  for (int64_t f = T0; f < W.nf; f += TS) {
     double gi = 0, hi = 0;
     if (f < W.np) backsub_feature<T, 3>(W.back, f, gi, hi);
     else backsub_feature<T, 4>(W.back, f, gi, hi);
     g += gi; h += hi;
   }
-  cta_sum2<NT>(g, h, red2);
-  if (threadIdx.x == 0) { W.S->gTd = red2[0]; W.S->dHd = red2[1]; W.S->pred = -red2[0] - 0.5 * red2[1]; }
+  win_sum2<NT>(cx, g, h, red2);
+  if (cx.rank == 0 && threadIdx.x == 0) { W.S->gTd = red2[0]; W.S->dHd = red2[1]; W.S->pred = -red2[0] - 0.5 * red2[1]; }
   // ---- candidate, its FP64 cost, decision
   {
     CandArgs ca = W.cand;
     ca.cam = W.cam[cur]; ca.pts = W.pts[cur]; ca.lin = W.lin_[cur]; ca.pln = W.pln[cur]; ca.vps = W.vps[cur];
     ca.cam2 = W.cam[nxt]; ca.pts2 = W.pts[nxt]; ca.lin2 = W.lin_[nxt]; ca.pln2 = W.pln[nxt]; ca.vps2 = W.vps[nxt];
     const int64_t tot = W.nc + W.npl + W.nv + W.np + W.nl;
-    for (int64_t i = threadIdx.x; i < tot; i += NT) candidate_item(ca, i);
+    for (int64_t i = T0; i < tot; i += TS) candidate_item(ca, i);
   }
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < W.nc; i += NT) derive_cam<T>(W.cam[nxt], W.camD[nxt], nullptr, i);
-  for (int64_t i = threadIdx.x; i < W.npl + W.nv; i += NT)
+  cx.sync();
+  for (int64_t i = T0; i < W.nc; i += TS) derive_cam<T>(W.cam[nxt], W.camD[nxt], nullptr, i);
+  for (int64_t i = T0; i < W.npl + W.nv; i += TS)
     derive_group<T>(W.npl, W.pln[nxt], W.vps[nxt], W.grpD[nxt], nullptr, i);
-  __syncthreads();
+  cx.sync();
   {
     CostArgs co = W.cost;
     co.camD = W.camD[nxt]; co.grpD = W.grpD[nxt]; co.pts = W.pts[nxt]; co.lin = W.lin_[nxt];
     double e = 0, epx = 0;
-    for (int64_t i = threadIdx.x; i < W.nr; i += NT) {
+    for (int64_t i = T0; i < W.nr; i += TS) {
       double v[2] = {0, 0};
       cost_residual(co, co.order[i], v);
       e += v[0]; epx += v[1];
     }
-    cta_sum2<NT>(e, epx, red2);
+    win_sum2<NT>(cx, e, epx, red2);
   }
-  if (threadIdx.x == 0) {
+  if (cx.rank == 0 && threadIdx.x == 0) {
     DevScalars* S = W.S;
     S->Enew = red2[0];
     S->Epxnew = red2[1];
@@ -3440,27 +3486,38 @@ __device__ void window_step(const WinDesc<T>& W, double* chunk_y) {
       W.state[1] = 1;
     }
   }
-  __syncthreads();
+  cx.sync();
 }
 
+// A cluster of nct CTAs takes the next window from the queue (largest first) and runs its iterations; rank
+// 0 draws the window and the other CTAs read it from rank 0's shared memory.
 template <class T, int NT>
 __global__ void __launch_bounds__(NT, 1) k_windows(const WinDesc<T>* __restrict__ descs, const int* __restrict__ order,
                                                    int nwin, int iters, int* queue) {
   extern __shared__ __align__(16) double chunk_y[];
   __shared__ int s_w;
+  const unsigned nct = cooperative_groups::this_cluster().num_blocks();
+  const WinCtx cx{nct > 1 ? cooperative_groups::this_cluster().block_rank() : 0u, nct};
   for (;;) {
-    if (threadIdx.x == 0) s_w = atomicAdd(queue, 1);
-    __syncthreads();
-    const int w = s_w;
-    __syncthreads();
+    if (cx.rank == 0 && threadIdx.x == 0) s_w = atomicAdd(queue, 1);
+    int w;
+    if (nct == 1) {
+      __syncthreads();
+      w = s_w;
+      __syncthreads();
+    } else {
+      cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+      cl.sync();
+      w = *cl.map_shared_rank(&s_w, 0);
+      cl.sync();
+    }
     if (w >= nwin) break;
     const WinDesc<T>& W = descs[order[w]];
     unsigned long long t0 = 0, t1 = 0;
     if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (int it = 0; it < iters; ++it) window_step<T, NT>(W, chunk_y);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // the window's own device time on its CTA (ns of the global timer), for the makespan report
+    for (int it = 0; it < iters; ++it) window_step<T, NT>(cx, W, chunk_y);
+    if (cx.rank == 0 && threadIdx.x == 0) {
+      // the window's own device time on its CTAs (ns of the global timer), for the makespan report
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
       *reinterpret_cast<unsigned long long*>(W.state + 6) = t1 - t0;
     }
@@ -3527,19 +3584,59 @@ size_t window_smem(size_t smem_pcg) {
 
 template <class T, int NT>
 cudaError_t launch_windows_nt(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
-                              int grid, size_t smem_pcg) {
+                              int grid, size_t smem_pcg, int nct) {
   const size_t smem = window_smem<T, NT>(smem_pcg);
   cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaMemsetAsync(queue, 0, sizeof(int), st);
-  k_windows<T, NT><<<grid, NT, smem, st>>>((const WinDesc<T>*)descs, order, nwin, iters, queue);
-  return cudaGetLastError();
+  if (nct > 1) cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nct;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_windows<T, NT>, (const WinDesc<T>*)descs, order, nwin, iters, queue);
 }
 
 template <class T>
 cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
-                           int threads, int grid, size_t smem) {
-  if (threads == 128) return launch_windows_nt<T, 128>(st, descs, order, nwin, iters, queue, grid, smem);
-  return launch_windows_nt<T, 256>(st, descs, order, nwin, iters, queue, grid, smem);
+                           int threads, int grid, size_t smem, int nct) {
+  if (threads == 128) return launch_windows_nt<T, 128>(st, descs, order, nwin, iters, queue, grid, smem, nct);
+  return launch_windows_nt<T, 256>(st, descs, order, nwin, iters, queue, grid, smem, nct);
+}
+
+// clusters of nct window CTAs that can be resident at once (0 if the shape cannot launch)
+template <class T, int NT>
+int window_clusters_nt(size_t smem_pcg, int nct) {
+  const size_t smem = window_smem<T, NT>(smem_pcg);
+  cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (nct > 1) cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nct);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nct;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_windows<T, NT>, &cfg) != cudaSuccess) { cudaGetLastError(); return 0; }
+  return n;
+}
+
+template <class T>
+int window_clusters(int threads, size_t smem_pcg, int nct) {
+  return threads == 128 ? window_clusters_nt<T, 128>(smem_pcg, nct) : window_clusters_nt<T, 256>(smem_pcg, nct);
 }
 
 template <class T, int NT>
@@ -3560,8 +3657,10 @@ template void fill_window_desc<float>(Problem&, void*);
 template void fill_window_desc<double>(Problem&, void*);
 template size_t window_desc_size<float>();
 template size_t window_desc_size<double>();
-template cudaError_t launch_windows<float>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t);
-template cudaError_t launch_windows<double>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t);
+template cudaError_t launch_windows<float>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t, int);
+template cudaError_t launch_windows<double>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t, int);
+template int window_clusters<float>(int, size_t, int);
+template int window_clusters<double>(int, size_t, int);
 template int windows_per_sm<float>(int, size_t);
 template int windows_per_sm<double>(int, size_t);
 

@@ -200,3 +200,31 @@ def test_batch_graph_kept_and_relaunched(B):
     finally:
         for p in pa + pb:
             B.ba_destroy(p)
+
+
+@pytest.mark.parametrize("nct", [2, 4])
+def test_batch_on_clusters_equals_sequential_path(B, nct):
+    """Windows on thread-block clusters of 2 or 4 CTAs (a window's features, Schur units and reduced-system rows
+    split over the cluster): every batched FP64 iteration equals one ba_lm_step of the sequential path from the
+    same state (1e-10 relative cost, same decision), including two of the largest windows."""
+    ws = windows(3, 600, seed=15) + _large_windows(2)
+    ps = [gpu_problem(B, s, precision=B.BA_FP64, pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000,
+                      batch_ctas_per_window=nct) for s in ws]
+    try:
+        for _ in range(3):
+            start = [gpu_state(B, p, s) for p, s in zip(ps, ws)]
+            reps = B.ba_solve_batch(ps, lm_iters=1, autotune=False)
+            assert B.ba_batch_ctas_per_window(ps[0]) == nct
+            for (s2, lam, nu), r in zip(start, reps):
+                q = gpu_problem(B, s2, precision=B.BA_FP64, pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000)
+                try:
+                    B.ba_set_lm_state(q, lam, nu)
+                    st = B.ba_lm_step(q)
+                finally:
+                    B.ba_destroy(q)
+                E = st.cost_new if st.accepted else st.cost
+                assert r.accepted_steps == st.accepted
+                assert abs(r.cost - E) <= 1e-10 * E, (r.cost, E)
+    finally:
+        for p in ps:
+            B.ba_destroy(p)
