@@ -406,7 +406,10 @@ def main():
         B.ba_solve_batch(ps, lm_iters=10, autotune=False)     # captures the batch's graph
         reps = B.ba_solve_batch(ps, lm_iters=10, autotune=False)   # launches the kept graph again
         shape = B.ba_batch_launch_shape(ps[0])
-        nct = B.ba_batch_ctas_per_window(ps[0])
+        nct, nbig = B.ba_batch_ctas_per_window(ps[0])
+        work = [sum(int(len(o["feat"])) for o in w_["obs"].values()) + len(w_["points"]) + len(w_["lines"])
+                for w_ in wins]
+        big = set(np.argsort(-np.asarray(work), kind="stable")[:nbig].tolist())
         for h in ps:
             B.ba_destroy(h)
         ms_b = reps[0].ms_total
@@ -415,10 +418,13 @@ def main():
                    "window_lm_iters_per_s": round(args.windows * 10 / (ms_b / 1e3), 1),
                    "residuals_total": nres,
                    "launch_shape": {"threads": shape[0], "ctas": shape[1], "ctas_per_window": nct,
-                                    "note": "chosen by the library's autotuner"},
+                                    "windows_on_clusters": nbig,
+                                    "note": "chosen by the library's autotuner: the largest windows_on_clusters "
+                                            "windows on clusters of ctas_per_window CTAs, the rest on single CTAs"},
                    "window_ms": {"max": round(max(r.ms_window for r in reps), 3),
                                  "mean": round(float(np.mean([r.ms_window for r in reps])), 3),
-                                 "balanced": round(sum(r.ms_window for r in reps) * nct / shape[1], 3),
+                                 "balanced": round(sum(r.ms_window * (nct if i in big else 1)
+                                                       for i, r in enumerate(reps)) / shape[1], 3),
                                  "note": "each window's own device time on its CTAs; balanced = the sum of window x "
                                          "CTA times over the launch's CTAs, the makespan of a perfect balance"},
                    "accepted_steps": int(sum(r.accepted_steps for r in reps)),

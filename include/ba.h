@@ -111,7 +111,9 @@ typedef struct ba_options {
   double w_rel;             /* loss weight of the inter-group relations (5e3, the VP term's) */
   double cauchy_rel;        /* Cauchy scale of the inter-group relations (0.2, the VP term's) */
   int batch_ctas_per_window; /* ba_solve_batch, read from windows[0]: 0 = chosen by the autotuner (or 1); 1, 2 or 4
-                                = every window on a thread-block cluster of that many CTAs (256 threads each) */
+                                = every window on a thread-block cluster of that many CTAs (256 threads each).  The
+                                autotuner may also run only the largest windows on clusters and the rest on single
+                                CTAs of the same launch */
 } ba_options;
 
 /* Per-LM-step report. */
@@ -242,8 +244,9 @@ ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* d
  * are solved with the same iteration count. */
 ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_iters, int autotune, ba_solve_report* reports);
 ba_status ba_batch_launch_shape(const ba_problem* p, int* threads, int* grid);
-/* CTAs per window (the cluster size) of the last batched solve started from p. */
-ba_status ba_batch_ctas_per_window(const ba_problem* p, int* ctas);
+/* CTAs per window (the cluster size) of the last batched solve started from p, and how many of its windows (the
+ * largest) ran on clusters; the others ran on single CTAs.  Either pointer may be NULL. */
+ba_status ba_batch_ctas_per_window(const ba_problem* p, int* ctas, int* windows_on_clusters);
 
 /* Learned correction of the block-Jacobi preconditioner.  The paper solves the reduced system directly; this
  * optional preconditioner for the PCG solve has no counterpart there.  Per diagonal block b of S (6 wide):

@@ -106,7 +106,7 @@ def _load():
                                     C.c_char_p, C.c_size_t]),
         "ba_solve_batch": (I, [VP, I, I, I, VP]),
         "ba_batch_launch_shape": (I, [P, C.POINTER(I), C.POINTER(I)]),
-        "ba_batch_ctas_per_window": (I, [P, C.POINTER(I)]),
+        "ba_batch_ctas_per_window": (I, [P, C.POINTER(I), C.POINTER(I)]),
         "ba_precond_param_count": (I, []),
         "ba_precond_set_weights": (I, [P, VP, I64]),
         "ba_precond_features": (I, [P, VP, VP]),
@@ -508,9 +508,10 @@ def ba_solve_batch(problems, lm_iters=10, autotune=True):
 
 
 def ba_batch_ctas_per_window(p):
-    c = C.c_int()
-    _check(p, _lib.ba_batch_ctas_per_window(p, C.byref(c)))
-    return c.value
+    """(CTAs per window, number of the largest windows that ran on clusters) of the last batched solve."""
+    c, k = C.c_int(), C.c_int()
+    _check(p, _lib.ba_batch_ctas_per_window(p, C.byref(c), C.byref(k)))
+    return c.value, k.value
 
 
 def ba_batch_launch_shape(p):

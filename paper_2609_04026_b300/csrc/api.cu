@@ -910,6 +910,7 @@ struct BatchCfg {
   int threads = 256;
   int per_sm = 1;   // CTAs per SM (windows of one CTA)
   int nct = 1;      // CTAs per window: a thread-block cluster of nct CTAs works on one window
+  int nbig = 0;     // with nct > 1: the largest nbig windows run on clusters, the others on single CTAs (-1: all)
 };
 std::map<std::string, BatchCfg> g_batch_cache;   // (GPU, precision, size class) -> launch shape
 std::mutex g_batch_lock;
@@ -955,7 +956,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
     release_batch_graph(p0);
     bg.desc = p0->alloc.get(host.size());
     bg.order = p0->alloc.get(sizeof(int) * n);
-    bg.queue = p0->alloc.get(sizeof(int));
+    bg.queue = p0->alloc.get(2 * sizeof(int));
     if (!bg.desc || !bg.order || !bg.queue) { release_batch_graph(p0); return set_err(p0, BA_ERR_OOM, "device allocation failed"); }
   }
   void* d_desc = bg.desc;
@@ -980,6 +981,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
     return set_err(p0, BA_ERR_ARG, "batch_ctas_per_window must be 0, 1, 2 or 4");
   if (forced > 0) {
     cfg.nct = forced;
+    cfg.nbig = -1;
     cached = true;
     if (forced > 1 && window_clusters<T>(cfg.threads, smem, forced) < 1)
       return set_err(p0, BA_ERR_ARG, "no cluster of that many window CTAs fits this GPU");
@@ -1007,8 +1009,8 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
     }
     // launch shapes: threads per CTA, CTAs per SM, and CTAs per window (a cluster splits a window's features,
     // Schur units and reduced-system rows over its CTAs: the largest windows otherwise set the makespan)
-    const BatchCfg cands[] = {{128, 1, 1}, {128, 2, 1}, {256, 1, 1}, {256, 2, 1}, {128, 1, 2}, {256, 1, 2},
-                              {256, 1, 4}};
+    const BatchCfg cands[] = {{128, 1, 1, 0}, {128, 2, 1, 0}, {256, 1, 1, 0}, {256, 2, 1, 0}, {256, 1, 2, -1},
+                              {256, 1, 2, 32}, {256, 1, 4, 16},   {256, 1, 4, 32},  {256, 1, 4, 64}};
     float best = 1e30f;
     cudaEvent_t e0, e1;
     CUDA_OR(p0, cudaEventCreate(&e0));
@@ -1017,7 +1019,8 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
       if (c.per_sm > 1 && windows_per_sm<T>(c.threads, smem) < c.per_sm) continue;
       if (c.nct > 1 && window_clusters<T>(c.threads, smem, c.nct) < 1) continue;
       CUDA_OR(p0, cudaEventRecord(e0, st));
-      CUDA_OR(p0, launch_windows<T>(st, d_desc, d_order, n, 1, d_queue, c.threads, grid_of(c), smem, c.nct));
+      CUDA_OR(p0, launch_windows<T>(st, d_desc, d_order, n, c.nbig < 0 ? n : std::min(n, c.nbig), 1, d_queue,
+                                    c.threads, grid_of(c), smem, c.nct));
       CUDA_OR(p0, cudaEventRecord(e1, st));
       CUDA_OR(p0, cudaEventSynchronize(e1));
       float ms = 0;
@@ -1038,12 +1041,13 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   // private stream that starts after the caller's stream has drained
   const int grid = grid_of(cfg);
   CUDA_OR(p0, cudaStreamSynchronize(st));
-  if (!reuse || bg.threads != cfg.threads || bg.grid != grid || bg.nct != cfg.nct) {
+  if (!reuse || bg.threads != cfg.threads || bg.grid != grid || bg.nct != cfg.nct || bg.nbig != cfg.nbig) {
     if (bg.exec) { cudaGraphExecDestroy(bg.exec); bg.exec = nullptr; }
     if (bg.graph) { cudaGraphDestroy(bg.graph); bg.graph = nullptr; }
     if (!bg.stream) CUDA_OR(p0, cudaStreamCreateWithFlags(&bg.stream, cudaStreamNonBlocking));
     CUDA_OR(p0, cudaStreamBeginCapture(bg.stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = launch_windows<T>(bg.stream, d_desc, d_order, n, iters, d_queue, cfg.threads, grid, smem, cfg.nct);
+    cudaError_t le = launch_windows<T>(bg.stream, d_desc, d_order, n, cfg.nbig < 0 ? n : std::min(n, cfg.nbig), iters,
+                                       d_queue, cfg.threads, grid, smem, cfg.nct);
     cudaError_t ce = cudaStreamEndCapture(bg.stream, &bg.graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
       cudaGetLastError();
@@ -1055,6 +1059,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
     bg.threads = cfg.threads;
     bg.grid = grid;
     bg.nct = cfg.nct;
+    bg.nbig = cfg.nbig;
   }
   cudaEvent_t e0, e1;
   CUDA_OR(p0, cudaEventCreate(&e0));
@@ -1070,6 +1075,7 @@ static ba_status solve_batch_t(ba_problem* const* w, int n, int iters, ba_solve_
   CUDA_OR(p0, cudaGetLastError());
   p0->batch_threads = cfg.threads;
   p0->batch_nct = cfg.nct;
+  p0->batch_nbig = cfg.nct > 1 ? (cfg.nbig < 0 ? n : std::min(n, cfg.nbig)) : 0;
   p0->batch_grid = grid;
   // ---- bring every window's host state up to date
   for (int i = 0; i < n; ++i) {
@@ -1127,9 +1133,10 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
   return s;
 }
 
-extern "C" ba_status ba_batch_ctas_per_window(const ba_problem* p, int* ctas) {
-  if (!p || !ctas) return BA_ERR_ARG;
-  *ctas = p->batch_nct;
+extern "C" ba_status ba_batch_ctas_per_window(const ba_problem* p, int* ctas, int* windows_on_clusters) {
+  if (!p) return BA_ERR_ARG;
+  if (ctas) *ctas = p->batch_nct;
+  if (windows_on_clusters) *windows_on_clusters = p->batch_nbig;
   return BA_OK;
 }
 

@@ -307,10 +307,10 @@ struct ba_problem {
     cudaGraph_t graph = nullptr;
     cudaStream_t stream = nullptr;
     void *desc = nullptr, *order = nullptr, *queue = nullptr;
-    int threads = 0, grid = 0, nct = 0;
+    int threads = 0, grid = 0, nct = 0, nbig = 0;
   } bgraph;
   int batch_threads = 0, batch_grid = 0;  // launch shape of the last batched solve started from this problem
-  int batch_nct = 1;                      // and its CTAs per window
+  int batch_nct = 1, batch_nbig = 0;      // and its CTAs per window, windows run on clusters
   double* red = nullptr;        // per-block partial sums of reductions
   int red_cap = 0;
   ba::DevScalars* S = nullptr;  // device scalars
@@ -342,8 +342,8 @@ SView sview_of(const Problem& P);
 // batched windows (kernels.cu, launched from batch.cu)
 template <class T> void fill_window_desc(Problem& P, void* out);
 template <class T> size_t window_desc_size();
-template <class T> cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int iters,
-                                              int* queue, int threads, int grid, size_t smem, int nct);
+template <class T> cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int nbig,
+                                              int iters, int* queue, int threads, int grid, size_t smem, int nct);
 template <class T> int window_clusters(int threads, size_t smem, int nct);
 template <class T> int windows_per_sm(int threads, size_t smem);
 // learned preconditioner (precond.cu)

@@ -3489,38 +3489,48 @@ __device__ void window_step(const WinCtx& cx, const WinDesc<T>& W, double* chunk
   cx.sync();
 }
 
-// A cluster of nct CTAs takes the next window from the queue (largest first) and runs its iterations; rank
-// 0 draws the window and the other CTAs read it from rank 0's shared memory.
+// The windows in `order` are sorted largest first.  Phase 1: a cluster of nct CTAs takes the next of the first
+// nbig windows and runs its iterations together (rank 0 draws it from queue[0], the other CTAs read it from rank
+// 0's shared memory).  Phase 2: once those are taken, every CTA on its own takes the next of the remaining
+// windows from queue[1].  With nct = 1 (nbig = 0) every window runs on a single CTA.
+template <class T, int NT>
+__device__ __forceinline__ void run_window(const WinCtx& cx, const WinDesc<T>& W, int iters, double* chunk_y) {
+  unsigned long long t0 = 0, t1 = 0;
+  if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0; it < iters; ++it) window_step<T, NT>(cx, W, chunk_y);
+  if (cx.rank == 0 && threadIdx.x == 0) {
+    // the window's own device time on its CTAs (ns of the global timer), for the makespan report
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    *reinterpret_cast<unsigned long long*>(W.state + 6) = t1 - t0;
+  }
+}
+
 template <class T, int NT>
 __global__ void __launch_bounds__(NT, 1) k_windows(const WinDesc<T>* __restrict__ descs, const int* __restrict__ order,
-                                                   int nwin, int iters, int* queue) {
+                                                   int nwin, int nbig, int iters, int* queue) {
   extern __shared__ __align__(16) double chunk_y[];
   __shared__ int s_w;
   const unsigned nct = cooperative_groups::this_cluster().num_blocks();
-  const WinCtx cx{nct > 1 ? cooperative_groups::this_cluster().block_rank() : 0u, nct};
+  if (nct > 1) {
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    const WinCtx cx{cl.block_rank(), nct};
+    for (;;) {
+      if (cx.rank == 0 && threadIdx.x == 0) s_w = atomicAdd(&queue[0], 1);
+      cl.sync();
+      const int w = *cl.map_shared_rank(&s_w, 0);
+      cl.sync();
+      if (w >= nbig) break;
+      run_window<T, NT>(cx, descs[order[w]], iters, chunk_y);
+    }
+  }
+  const WinCtx solo{0u, 1u};
   for (;;) {
-    if (cx.rank == 0 && threadIdx.x == 0) s_w = atomicAdd(queue, 1);
-    int w;
-    if (nct == 1) {
-      __syncthreads();
-      w = s_w;
-      __syncthreads();
-    } else {
-      cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-      cl.sync();
-      w = *cl.map_shared_rank(&s_w, 0);
-      cl.sync();
-    }
+    if (threadIdx.x == 0) s_w = nbig + atomicAdd(&queue[1], 1);
+    __syncthreads();
+    const int w = s_w;
+    __syncthreads();
     if (w >= nwin) break;
-    const WinDesc<T>& W = descs[order[w]];
-    unsigned long long t0 = 0, t1 = 0;
-    if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (int it = 0; it < iters; ++it) window_step<T, NT>(cx, W, chunk_y);
-    if (cx.rank == 0 && threadIdx.x == 0) {
-      // the window's own device time on its CTAs (ns of the global timer), for the makespan report
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-      *reinterpret_cast<unsigned long long*>(W.state + 6) = t1 - t0;
-    }
+    run_window<T, NT>(solo, descs[order[w]], iters, chunk_y);
   }
 }
 
@@ -3583,12 +3593,12 @@ size_t window_smem(size_t smem_pcg) {
 }
 
 template <class T, int NT>
-cudaError_t launch_windows_nt(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
-                              int grid, size_t smem_pcg, int nct) {
+cudaError_t launch_windows_nt(cudaStream_t st, const void* descs, const int* order, int nwin, int nbig, int iters,
+                              int* queue, int grid, size_t smem_pcg, int nct) {
   const size_t smem = window_smem<T, NT>(smem_pcg);
   cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (nct > 1) cudaFuncSetAttribute(k_windows<T, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
@@ -3602,14 +3612,15 @@ cudaError_t launch_windows_nt(cudaStream_t st, const void* descs, const int* ord
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_windows<T, NT>, (const WinDesc<T>*)descs, order, nwin, iters, queue);
+  return cudaLaunchKernelEx(&cfg, k_windows<T, NT>, (const WinDesc<T>*)descs, order, nwin, nct > 1 ? nbig : 0, iters,
+                            queue);
 }
 
 template <class T>
-cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int iters, int* queue,
-                           int threads, int grid, size_t smem, int nct) {
-  if (threads == 128) return launch_windows_nt<T, 128>(st, descs, order, nwin, iters, queue, grid, smem, nct);
-  return launch_windows_nt<T, 256>(st, descs, order, nwin, iters, queue, grid, smem, nct);
+cudaError_t launch_windows(cudaStream_t st, const void* descs, const int* order, int nwin, int nbig, int iters,
+                           int* queue, int threads, int grid, size_t smem, int nct) {
+  if (threads == 128) return launch_windows_nt<T, 128>(st, descs, order, nwin, nbig, iters, queue, grid, smem, nct);
+  return launch_windows_nt<T, 256>(st, descs, order, nwin, nbig, iters, queue, grid, smem, nct);
 }
 
 // clusters of nct window CTAs that can be resident at once (0 if the shape cannot launch)
@@ -3657,8 +3668,8 @@ template void fill_window_desc<float>(Problem&, void*);
 template void fill_window_desc<double>(Problem&, void*);
 template size_t window_desc_size<float>();
 template size_t window_desc_size<double>();
-template cudaError_t launch_windows<float>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t, int);
-template cudaError_t launch_windows<double>(cudaStream_t, const void*, const int*, int, int, int*, int, int, size_t, int);
+template cudaError_t launch_windows<float>(cudaStream_t, const void*, const int*, int, int, int, int*, int, int, size_t, int);
+template cudaError_t launch_windows<double>(cudaStream_t, const void*, const int*, int, int, int, int*, int, int, size_t, int);
 template int window_clusters<float>(int, size_t, int);
 template int window_clusters<double>(int, size_t, int);
 template int windows_per_sm<float>(int, size_t);

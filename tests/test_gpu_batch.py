@@ -214,7 +214,7 @@ def test_batch_on_clusters_equals_sequential_path(B, nct):
         for _ in range(3):
             start = [gpu_state(B, p, s) for p, s in zip(ps, ws)]
             reps = B.ba_solve_batch(ps, lm_iters=1, autotune=False)
-            assert B.ba_batch_ctas_per_window(ps[0]) == nct
+            assert B.ba_batch_ctas_per_window(ps[0]) == (nct, len(ps))
             for (s2, lam, nu), r in zip(start, reps):
                 q = gpu_problem(B, s2, precision=B.BA_FP64, pcg_rel_tol=TIGHT_PCG, pcg_max_iters=3000)
                 try:
