@@ -421,6 +421,13 @@ def state_from_scene(scene):
         st["planes"] /= np.linalg.norm(st["planes"][:, :3], axis=1, keepdims=True)
     if len(st["vps"]):
         st["vps"] /= np.linalg.norm(st["vps"], axis=1, keepdims=True)
+    ik = scene.get("intrinsics")
+    if ik is not None:
+        # refined intrinsics (Section 3.1, K_c(i): image i uses the intrinsics of its camera model c(i)): the
+        # entities' (f, k1, k2) are parameters, and every camera's copy is the value of its entity
+        st["intr"] = np.array(ik["values"], np.float64).reshape(-1, 3)
+        st["cam_k"] = np.asarray(ik["of_cam"], np.int64).copy()
+        st["cams"][:, 7:10] = st["intr"][st["cam_k"]]
     return st
 
 
@@ -448,36 +455,50 @@ def _records(state, obs, kind):
     return cam, feat, grp, meas
 
 
-def residuals(state, obs, kind, with_jac=False, chunk=200_000):
-    """r [n, rdim], valid [n] and, with with_jac, J w.r.t. (cam 6, feature k, group 3) increments."""
+def with_intrinsics_increment(fn):
+    """The residual as a function of an additive increment dk of the camera's (f, k1, k2) as well
+    (refined intrinsics, Section 3.1): fn(dc, df, dg, dk, cam, ...) = fn(dc, df, dg, cam + [0 dk 0], ...)."""
+    def g(dc, df, dg, dk, cam, feat, grp, meas):
+        return fn(dc, df, dg, torch.cat([cam[:7], cam[7:10] + dk, cam[10:]]), feat, grp, meas)
+    return g
+
+
+def residuals(state, obs, kind, with_jac=False, chunk=200_000, with_intr=False):
+    """r [n, rdim], valid [n] and, with with_jac, J w.r.t. (cam 6, feature k, group 3) increments, and with
+    with_intr also J w.r.t. the additive (f, k1, k2) increment of the camera (zero for kinds without one)."""
     cam, feat, grp, meas = _records(state, obs, kind)
     n = cam.shape[0]
     kf = FDOF[FEAT[kind]]
     fn = RES_FN[kind]
     rd = RDIM[kind]
+    nj = 4 if with_intr else 3
     if n == 0:
         z = torch.zeros((0, rd))
         out = (z, torch.zeros(0, dtype=torch.bool))
         if with_jac:
             out = out + (torch.zeros((0, rd, 6)), torch.zeros((0, rd, kf)), torch.zeros((0, rd, 3)))
+            if with_intr:
+                out = out + (torch.zeros((0, rd, 3)),)
         return out
-    dc = torch.zeros((n, 6)); df = torch.zeros((n, kf)); dg = torch.zeros((n, 3))
-    rs, vs, Jc, Jf, Jg = [], [], [], [], []
+    dc = torch.zeros((n, 6)); df = torch.zeros((n, kf)); dg = torch.zeros((n, 3)); dk = torch.zeros((n, 3))
+    rs, vs, Js = [], [], [[] for _ in range(nj)]
+    fk = with_intrinsics_increment(fn) if with_intr else fn
     for s in range(0, n, chunk):
         sl = slice(s, s + chunk)
-        args = (dc[sl], df[sl], dg[sl], cam[sl], feat[sl], grp[sl], meas[sl])
+        args = (dc[sl], df[sl], dg[sl]) + ((dk[sl],) if with_intr else ()) + (cam[sl], feat[sl], grp[sl], meas[sl])
         if with_jac:
             def f2(*a):
-                r, v = fn(*a)
+                r, v = fk(*a)
                 return r, (r, v)
-            jac, (r, v) = vmap(jacfwd(f2, argnums=(0, 1, 2), has_aux=True))(*args)
-            Jc.append(jac[0]); Jf.append(jac[1]); Jg.append(jac[2])
+            jac, (r, v) = vmap(jacfwd(f2, argnums=tuple(range(nj)), has_aux=True))(*args)
+            for i in range(nj):
+                Js[i].append(jac[i])
         else:
-            r, v = vmap(fn)(*args)
+            r, v = vmap(fk)(*args)
         rs.append(r); vs.append(v)
     out = (torch.cat(rs), torch.cat(vs))
     if with_jac:
-        out = out + (torch.cat(Jc), torch.cat(Jf), torch.cat(Jg))
+        out = out + tuple(torch.cat(J) for J in Js)
     return out
 
 
@@ -509,11 +530,12 @@ def cost(state, obs, opt: Options):
 # the normal equations (Eq. 2 / Eq. 5) and the Schur complement (Eq. 3)
 # ===========================================================================
 class Layout:
-    """Column layout of the full system: [cameras | planes | VPs | points | lines].
+    """Column layout of the full system: [cameras | planes | VPs | intrinsics | points | lines].
 
     `fixed` holds camera pose components constant (gauge): per camera a bit mask over the six pose
     increments (bits 0-2 rotation, 3-5 translation; 0x3F = the whole pose), or a boolean (True = 0x3F).
-    Held components get no column."""
+    Held components get no column.  With refined intrinsics (state "intr" / "cam_k") every intrinsics
+    entity K_c (Section 3.1) takes three columns (f, k1, k2), whatever the pose mask of its cameras."""
 
     def __init__(self, state, fixed=None):
         self.nc = state["cams"].shape[0]
@@ -532,6 +554,9 @@ class Layout:
         o = int(free.sum())
         self.plane_col = o + 3 * np.arange(self.npl); o += 3 * self.npl
         self.vp_col = o + 2 * np.arange(self.nv); o += 2 * self.nv
+        self.nk = state["intr"].shape[0] if "intr" in state else 0
+        self.cam_k = state["cam_k"] if self.nk else np.full(self.nc, -1, np.int64)
+        self.intr_col = o + 3 * np.arange(self.nk); o += 3 * self.nk
         self.na = o
         self.point_col = o + 3 * np.arange(self.np_); o += 3 * self.np_
         self.line_col = o + 4 * np.arange(self.nl); o += 4 * self.nl
@@ -539,7 +564,8 @@ class Layout:
         # entity blocks of A (for block-Jacobi): (start, size); a camera's free columns are contiguous
         nfree = free.sum(1)
         self.a_blocks = ([(int(self.cam_cols[i][free[i]][0]), int(nfree[i])) for i in range(self.nc) if nfree[i]] +
-                         [(int(c), 3) for c in self.plane_col] + [(int(c), 2) for c in self.vp_col])
+                         [(int(c), 3) for c in self.plane_col] + [(int(c), 2) for c in self.vp_col] +
+                         [(int(c), 3) for c in self.intr_col])
         self.f_blocks = [(int(c), 3) for c in self.point_col] + [(int(c), 4) for c in self.line_col]
 
 
@@ -553,7 +579,7 @@ def linearize(state, obs, opt: Options, lay: Layout):
         n = len(o["feat"])
         if n == 0:
             continue
-        r, v, Jc, Jf, Jg = residuals(state, obs, k, with_jac=True)
+        r, v, Jc, Jf, Jg, *Jk = residuals(state, obs, k, with_jac=True, with_intr=lay.nk > 0)
         a = opt.scale(k)
         s = (r * r).sum(-1)
         om = opt.weight(k) / (1 + s / (a * a))
@@ -565,6 +591,10 @@ def linearize(state, obs, opt: Options, lay: Layout):
         if HAS_CAM[k]:
             cc = lay.cam_cols[o["cam"]]
             blocks.append((Jc.numpy(), cc, cc >= 0))
+            if lay.nk:
+                ck = lay.cam_k[o["cam"]]
+                kc = np.where(ck >= 0, lay.intr_col[np.maximum(ck, 0)], 0)[:, None] + np.arange(3)[None, :]
+                blocks.append((Jk[0].numpy(), kc, np.broadcast_to((ck >= 0)[:, None], (n, 3))))
         ft = FEAT[k]
         fc = (lay.point_col if ft == "point" else lay.line_col)[o["feat"]]
         w = FDOF[ft]
@@ -706,6 +736,11 @@ def apply_step(state, delta, lay: Layout):
     if lay.nv:
         d = delta[lay.vp_col[:, None] + np.arange(2)]
         new["vps"] = vp_plus(torch.from_numpy(state["vps"]), torch.from_numpy(d)).numpy()
+    if lay.nk:
+        # intrinsics: additive; every camera's copy follows its entity
+        new["intr"] = state["intr"] + delta[lay.intr_col[:, None] + np.arange(3)]
+        has = lay.cam_k >= 0
+        new["cams"][has, 7:10] = new["intr"][lay.cam_k[has]]
     if lay.np_:
         new["points"] = state["points"] + delta[lay.point_col[:, None] + np.arange(3)]
     if lay.nl:

@@ -19,6 +19,8 @@ Conventions (all float64):
   lines:    [Nl,6] Pluecker (d, m), |d| = 1, m = p x d for any p on the line.
   planes:   [Npl,4] (n, w), |n| = 1, plane n.x + w = 0.
   vps:      [Nv,3] unit directions.
+  intrinsics (only with refined intrinsics): of_cam [Nc] int32, the intrinsics entity of every camera, and
+            values [Nk,3] the entities' initial (f, k1, k2); cams.intr then equals values[of_cam].
 Observation kinds (one record per residual):
   point      (cam, point, -, meas 2 distorted pixels)                 Eq. 1/4
   line       (cam, line,  -, meas 4 undistorted segment endpoints)    Eq. 4
@@ -67,6 +69,12 @@ class SceneConfig:
     group_rot_noise_deg: float = 2.0
     group_off_noise: float = 0.05
     relations: bool = False          # inter-group orthogonality / parallelism that hold in the ground truth
+    # refined intrinsics (f, k1, k2 as entities of the reduced system): intr_groups = 0 gives every camera its
+    # own entity; g > 0 makes camera i share entity i % g (its ground-truth intrinsics and principal point are
+    # those of camera i % g); intr_noise perturbs the initial values (f relative, k1 and k2 scaled)
+    intr_refine: bool = False
+    intr_groups: int = 0
+    intr_noise: float = 0.0
     seed: int = 1
 
 
@@ -222,6 +230,10 @@ def make_scene(cfg: SceneConfig) -> dict:
     k1 = rng.uniform(-0.1, 0.1, Nc)
     k2 = rng.uniform(-0.02, 0.02, Nc)
     pp = np.tile([IMG_W / 2, IMG_H / 2], (Nc, 1)) + rng.uniform(-5, 5, (Nc, 2))
+    intr_of_cam = np.arange(Nc, dtype=np.int32)
+    if cfg.intr_refine and cfg.intr_groups > 0:
+        intr_of_cam = (np.arange(Nc) % cfg.intr_groups).astype(np.int32)
+        f, k1, k2, pp = f[intr_of_cam], k1[intr_of_cam], k2[intr_of_cam], pp[intr_of_cam]
 
     # ---- k nearest cameras (by angle) of each camera, itself included
     K = min(cfg.k_near, Nc)
@@ -460,6 +472,20 @@ def make_scene(cfg: SceneConfig) -> dict:
     else:
         vps0 = np.zeros((0, 3))
     intr = np.stack([f, k1, k2], 1)
+    intr_gt = intr.copy()
+    intrinsics = None
+    if cfg.intr_refine:
+        # the refined entities: one per camera, or one per group; initial values perturbed with their own
+        # generator, so that every other output is the scene without refined intrinsics
+        nk = int(intr_of_cam.max()) + 1 if Nc else 0
+        vals = intr_gt[:nk].copy() if cfg.intr_groups > 0 else intr_gt.copy()
+        if cfg.intr_noise > 0 and nk:
+            r2 = np.random.default_rng(cfg.seed * 7 + 12345)
+            vals[:, 0] *= 1 + cfg.intr_noise * r2.normal(size=nk)
+            vals[:, 1] += 0.1 * cfg.intr_noise * r2.normal(size=nk)
+            vals[:, 2] += 0.02 * cfg.intr_noise * r2.normal(size=nk)
+        intrinsics = dict(of_cam=intr_of_cam, values=vals)
+        intr = vals[intr_of_cam]
     # ---- inter-group relations (no random draws: the other outputs do not change).  Each plane with the
     # next one (parallel on the same axis, orthogonal otherwise); the axis VPs pairwise orthogonal; each axis
     # VP orthogonal to the normal of the first plane of another axis and parallel to that of its own axis.
@@ -499,11 +525,13 @@ def make_scene(cfg: SceneConfig) -> dict:
         cams=dict(q=_mat_to_quat(R0), t=t0, intr=intr, pp=pp),
         points=P0, lines=lines0, planes=planes0, vps=vps0,
         obs=obs, relations=relations,
-        gt=dict(cams=dict(q=qgt, t=tgt.copy(), intr=intr.copy(), pp=pp.copy()), points=P.copy(),
+        gt=dict(cams=dict(q=qgt, t=tgt.copy(), intr=intr_gt, pp=pp.copy()), points=P.copy(),
                 lines=gt_lines, planes=gt_planes, vps=vp.copy()),
         info=dict(n_wf_points=n_wf_pts, n_wf_lines=n_wf_lines, n_edges=len(edges),
                   point_plane=p_plane, line_plane=l_plane, line_vp=l_vp),
     )
+    if intrinsics is not None:
+        scene["intrinsics"] = intrinsics
     return scene
 
 
@@ -515,6 +543,11 @@ def noise_free(cfg: SceneConfig) -> dict:
     s["cams"] = {k: v.copy() for k, v in s["gt"]["cams"].items()}
     s["points"] = s["gt"]["points"].copy(); s["lines"] = s["gt"]["lines"].copy()
     s["planes"] = s["gt"]["planes"].copy(); s["vps"] = s["gt"]["vps"].copy()
+    if "intrinsics" in s:
+        ik = s["intrinsics"]
+        nk = len(ik["values"])
+        first = np.array([int(np.flatnonzero(ik["of_cam"] == k)[0]) for k in range(nk)], np.int64)
+        s["intrinsics"] = dict(of_cam=ik["of_cam"], values=s["gt"]["cams"]["intr"][first].copy())
     return s
 
 

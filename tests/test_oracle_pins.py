@@ -527,3 +527,93 @@ def test_relation_cost_rotation_invariant():
     r1 = O.relation_residuals(st, s["relations"]).norm(dim=-1)
     r2 = O.relation_residuals(st2, s["relations"]).norm(dim=-1)
     assert float((r1 - r2).abs().max()) < 1e-12
+
+
+# ---------------------------------------------------------------- refined intrinsics (Section 3.1, K_c(i))
+def test_intrinsics_derivatives_closed_form():
+    """d pi / d (f, k1, k2) of the distorted point projection, and d rho / d (f, k1, k2) of the (undistorted)
+    line reprojection, against hand-worked values."""
+    c = _case("point_projection_intrinsics_derivatives")
+    cam = _cam_vec(c["cam"])
+    X = torch.tensor(c["X"])
+    fk = O.with_intrinsics_increment(O.res_point)
+    z6, z3, z4 = torch.zeros(6), torch.zeros(3), torch.zeros(4)
+    J = torch.func.jacfwd(lambda dk: fk(z6, z3, z3, dk, cam, torch.cat([X, z3]), torch.zeros(4), z4)[0])(z3)
+    np.testing.assert_allclose(J.numpy(), c["dpi_dfk1k2"], rtol=0, atol=1e-10)
+    c = _case("line_reprojection_intrinsics_derivatives")
+    cam = _cam_vec(c["cam"])
+    fk = O.with_intrinsics_increment(O.res_line)
+    seg = torch.tensor(c["seg"])
+    r = fk(z6, z4, z3, z3, cam, torch.tensor(c["line"]), torch.zeros(4), seg)[0]
+    np.testing.assert_allclose(r.numpy(), c["rho"], atol=1e-10)
+    J = torch.func.jacfwd(lambda dk: fk(z6, z4, z3, dk, cam, torch.tensor(c["line"]), torch.zeros(4), seg)[0])(z3)
+    np.testing.assert_allclose(J.numpy(), c["drho_dfk1k2"], rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("kind", [k for k in O.KINDS if O.HAS_CAM[k]])
+def test_intrinsics_jacobian_finite_differences(kind):
+    """Central differences of the residuals in (f, k1, k2) agree with the oracle's intrinsics Jacobian; the
+    line kinds and the wireframe kinds do not depend on k1, k2 (undistorted pinhole pixels)."""
+    s = make_scene(config("tiny", intr_refine=True))
+    st = O.state_from_scene(s)
+    n = min(40, len(s["obs"][kind]["feat"]))
+    sub = {k: {kk: vv[:n] for kk, vv in o.items()} for k, o in s["obs"].items()}
+    r, v, Jc, Jf, Jg, Jk = O.residuals(st, sub, kind, with_jac=True, with_intr=True)
+    cam, feat, grp, meas = O._records(st, sub, kind)
+    fk = O.with_intrinsics_increment(O.RES_FN[kind])
+    kf = O.FDOF[O.FEAT[kind]]
+    # the projections are linear in each of f, k1, k2 alone: central differences are exact up to rounding
+    for j, h in ((0, 1e-1), (1, 1e-3), (2, 1e-3)):
+        def ev(sgn):
+            dk = torch.zeros(3); dk[j] = sgn * h
+            return torch.stack([fk(torch.zeros(6), torch.zeros(kf), torch.zeros(3), dk, cam[i], feat[i], grp[i],
+                                   meas[i])[0] for i in range(n)])
+        fd = (ev(1) - ev(-1)) / (2 * h)
+        scale = float(Jk[:, :, j].abs().max()) + 1e-12
+        assert float((fd - Jk[:, :, j]).abs().max()) <= 2e-6 * scale + 1e-7, (kind, j)
+    if kind not in ("point", "plane_point"):
+        assert float(Jk[:, :, 1:].abs().max()) == 0.0
+
+
+def test_shared_intrinsics_normal_equations():
+    """Sharing one intrinsics entity among cameras is the per-camera system restricted to equal intrinsics:
+    with P the matrix that copies an entity's increment to each of its cameras, H_shared = P^T H_cam P and
+    g_shared = P^T g_cam (a plain identity of the chain rule)."""
+    s = make_scene(config("tiny", intr_refine=True, intr_groups=3))
+    st = O.state_from_scene(s)
+    lay = O.Layout(st, s["fixed"])
+    s1 = dict(s); ik = s["intrinsics"]
+    s1["intrinsics"] = dict(of_cam=np.arange(len(ik["of_cam"]), dtype=np.int32), values=ik["values"][ik["of_cam"]])
+    st1 = O.state_from_scene(s1)
+    lay1 = O.Layout(st1, s["fixed"])
+    assert lay.nk == 3 and lay1.nk == 10
+    H, g = O.normal_equations(*O.linearize(st, s["obs"], O.Options(), lay))
+    H1, g1 = O.normal_equations(*O.linearize(st1, s1["obs"], O.Options(), lay1))
+    P = np.zeros((lay1.n, lay.n))
+    keep = np.ones(lay1.n, bool); keep[lay1.intr_col[:, None] + np.arange(3)] = False
+    other = np.ones(lay.n, bool); other[lay.intr_col[:, None] + np.arange(3)] = False
+    P[np.flatnonzero(keep), np.flatnonzero(other)] = 1.0
+    for cam, k in enumerate(ik["of_cam"]):
+        for j in range(3):
+            P[lay1.intr_col[cam] + j, lay.intr_col[k] + j] = 1.0
+    Hd, H1d = H.toarray(), H1.toarray()
+    np.testing.assert_allclose(Hd, P.T @ H1d @ P, rtol=0, atol=1e-9 * np.abs(Hd).max())
+    np.testing.assert_allclose(g, P.T @ g1, rtol=0, atol=1e-9 * np.abs(g).max())
+
+
+def test_refined_intrinsics_recovered_noise_free():
+    """Noise-free scene, intrinsics perturbed (f by 1%, k1, k2 by 5e-3, 1e-3), one entity per group of
+    cameras: LM drives the cost to zero and returns the ground-truth intrinsics."""
+    s = noise_free(config("tiny", intr_refine=True, intr_groups=3))
+    rng = np.random.default_rng(5)
+    v = s["intrinsics"]["values"]
+    true = v.copy()
+    v[:, 0] *= 1 + 0.01 * rng.normal(size=len(v))
+    v[:, 1] += 0.005 * rng.normal(size=len(v))
+    v[:, 2] += 0.001 * rng.normal(size=len(v))
+    st = O.state_from_scene(s)
+    E0 = O.cost(st, s["obs"], O.Options())[0]
+    st2, info = O.solve(st, s["obs"], O.Options(rel_cost_tol=1e-12), max_iters=12, fixed=s["fixed"])
+    assert E0 > 100 and info["E"] < 1e-12 * E0
+    np.testing.assert_allclose(st2["intr"], true, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(st2["cams"][:, 7:10], true[s["intrinsics"]["of_cam"]], rtol=0, atol=1e-7)
