@@ -114,6 +114,12 @@ typedef struct ba_options {
                                 = every window on a thread-block cluster of that many CTAs (256 threads each).  The
                                 autotuner may also run only the largest windows on clusters and the rest on single
                                 CTAs of the same launch */
+  int cam_dof;              /* 6 (default): camera blocks refine the pose, f, k1, k2 are held constant; 9: f, k1, k2
+                               are refined too (Section 3.1, K_c(i)), as intrinsics entities of the reduced system
+                               (3 values each, one per camera unless ba_set_intrinsics shares them); their
+                               increments are additive, and the principal point stays constant.  Problems with
+                               refined intrinsics keep the full 6 x 6 storage of S and are not supported by
+                               ba_solve_batch (BA_ERR_ARG there) */
 } ba_options;
 
 /* Per-LM-step report. */
@@ -157,8 +163,8 @@ ba_status ba_create(const ba_options* opts, ba_problem** out);
 void ba_destroy(ba_problem* p);
 const char* ba_last_error(const ba_problem* p);
 
-/* Cameras (Section 3.1: C_i = (K, R_i, t_i)): quat_t n x 7, f_k1_k2 n x 3, pp n x 2 (principal point; the
- * intrinsics are held constant), fixed: optional n bytes, a bit mask of pose increment components held
+/* Cameras (Section 3.1: C_i = (K, R_i, t_i)): quat_t n x 7, f_k1_k2 n x 3, pp n x 2 (principal point, always held
+ * constant; f, k1, k2 are held constant too unless cam_dof = 9), fixed: optional n bytes, a bit mask of pose increment components held
  * constant (bits 0-2 rotation dw, 3-5 translation dt; 0x3F holds the whole pose), used to fix the gauge.
  * Appends; ids continue. */
 ba_status ba_add_cameras(ba_problem* p, int64_t n, int mem, const double* quat_t, const double* f_k1_k2,
@@ -177,6 +183,15 @@ ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, const doubl
  * Appends; not supported by ba_solve_batch (BA_ERR_ARG there). */
 ba_status ba_add_relations(ba_problem* p, int64_t n, int mem, const int32_t* kind_a, const int32_t* a,
                            const int32_t* kind_b, const int32_t* b, const int32_t* type);
+/* Refined intrinsics shared by camera model (Section 3.1: image i uses the intrinsics K_c(i) of its camera model
+ * c(i)); only with cam_dof = 9 (BA_ERR_ARG otherwise).  n_intr entities with initial values f_k1_k2 (n_intr x 3)
+ * and, for every camera of the problem (n_cams, which must equal the number of cameras added when the structure
+ * is frozen, else BA_ERR_ARG there), its entity in [0, n_intr) (intr_of_cam, n_cams int32; validated here).  A
+ * camera's own f, k1, k2 from ba_add_cameras are then replaced by its entity's values.  Without this call,
+ * cam_dof = 9 gives every camera its own entity, starting from its ba_add_cameras values.  A later call
+ * replaces an earlier one; not allowed after freezing (BA_ERR_STATE). */
+ba_status ba_set_intrinsics(ba_problem* p, int64_t n_intr, int mem, const double* f_k1_k2,
+                            const int32_t* intr_of_cam, int64_t n_cams);
 /* Residual records of one kind: cam (n; ignored for BA_OBS_VP, may be NULL), feature (n), other (n; group id or
  * partner feature id, may be NULL for kinds without one), meas (n x meas_dim(kind), may be NULL when 0). */
 ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int mem, const int32_t* cam,
@@ -191,6 +206,8 @@ ba_status ba_solve(ba_problem* p, ba_solve_report* out);
 ba_status ba_get_cameras(ba_problem* p, int mem, double* quat_t);
 ba_status ba_get_features(ba_problem* p, int kind, int mem, double* params);
 ba_status ba_get_groups(ba_problem* p, int kind, int mem, double* params);
+/* Current f, k1, k2 of every camera (n_cams x 3; with refined intrinsics, its entity's values). */
+ba_status ba_get_intrinsics(ba_problem* p, int mem, double* f_k1_k2);
 /* LM state (lambda, nu) for checkpoint / resume. */
 ba_status ba_get_lm_state(ba_problem* p, double* lambda_nu);
 ba_status ba_set_lm_state(ba_problem* p, const double* lambda_nu);
@@ -216,8 +233,9 @@ ba_status ba_measure_fma_rate(int precision, double* tflops, void* cuda_stream);
 
 /* Build the damped reduced system S, b at damping lambda (linearising if needed) without stepping. */
 ba_status ba_build_reduced(ba_problem* p, double lambda);
-/* Sizes of the reduced system: number of A entities (block rows, each 6 wide; plane blocks use 3, VP blocks 2
- * of the 6, the rest are padding with a unit diagonal) and number of stored 6x6 blocks (both triangles). */
+/* Sizes of the reduced system: number of A entities (block rows, each 6 wide, in the order cameras, planes,
+ * VPs, intrinsics entities; plane and intrinsics blocks use 3, VP blocks 2 of the 6, the rest are padding with
+ * a unit diagonal) and number of stored 6x6 blocks (both triangles). */
 ba_status ba_reduced_size(ba_problem* p, int64_t* n_block_rows, int64_t* nnz_blocks);
 /* Copy the last reduced system to host: row_ptr (n_block_rows+1), cols (nnz_blocks), vals (nnz_blocks x 36,
  * row-major 6x6, double) and b (n_block_rows x 6).  Any pointer may be NULL. */
@@ -226,6 +244,11 @@ ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, int32_t* col
  * (cams n x 6 as (dw, dt), planes n x 3, vps n x 2, points n x 3, lines n x 4); NULL skips an output. */
 ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane, double* dvp, double* dpoint,
                           double* dline, int* pcg_iters, double* pcg_rel, double* pred);
+/* The intrinsics part of the step that ba_compute_step or ba_lm_step computed last: per intrinsics entity its
+ * (df, dk1, dk2) (n_intr x 3; nothing to copy without refined intrinsics). */
+ba_status ba_get_step_intrinsics(ba_problem* p, double* dk);
+/* Number of intrinsics entities in the reduced system (0 with cam_dof = 6).  Freezes the structure. */
+ba_status ba_intrinsics_count(ba_problem* p, int64_t* n_intr);
 
 /* Batched local windows: solve n independent problems (windows) with lm_iters LM iterations each, all in one
  * persistent kernel launch captured in a CUDA graph (local bundle adjustment after every registered image

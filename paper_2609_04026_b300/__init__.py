@@ -42,7 +42,8 @@ class ba_options(C.Structure):
                 ("pcg_max_iters", C.c_int), ("precond", C.c_int), ("cuda_stream", C.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double),
-                ("w_rel", C.c_double), ("cauchy_rel", C.c_double), ("batch_ctas_per_window", C.c_int)]
+                ("w_rel", C.c_double), ("cauchy_rel", C.c_double), ("batch_ctas_per_window", C.c_int),
+                ("cam_dof", C.c_int)]
 
 
 class ba_step_report(C.Structure):
@@ -88,6 +89,10 @@ def _load():
         "ba_add_groups": (I, [P, I, I64, I, VP]),
         "ba_add_observations": (I, [P, I, I64, I, VP, VP, VP, VP]),
         "ba_add_relations": (I, [P, I64, I, VP, VP, VP, VP, VP]),
+        "ba_set_intrinsics": (I, [P, I64, I, VP, VP, I64]),
+        "ba_get_intrinsics": (I, [P, I, VP]),
+        "ba_get_step_intrinsics": (I, [P, VP]),
+        "ba_intrinsics_count": (I, [P, C.POINTER(I64)]),
         "ba_lm_step": (I, [P, C.POINTER(ba_step_report)]),
         "ba_solve": (I, [P, C.POINTER(ba_solve_report)]),
         "ba_get_cameras": (I, [P, I, VP]),
@@ -274,6 +279,35 @@ def ba_add_relations(p, kind_a, a, kind_b, b, type_):
     _check(p, _lib.ba_add_relations(p, len(k2), mem, ka, aa, kb, bb, tt))
 
 
+def ba_set_intrinsics(p, values, intr_of_cam):
+    """Refined intrinsics shared by camera model (cam_dof = 9): values [n_intr, 3] = (f, k1, k2), intr_of_cam
+    [n_cams] the entity of every camera."""
+    v, mem, kv = _arr(values, np.float64)
+    m, _, km = _arr(intr_of_cam, np.int32)
+    _check(p, _lib.ba_set_intrinsics(p, len(kv) if kv is not None else 0, mem, v, m, len(km) if km is not None else 0))
+
+
+def ba_get_intrinsics(p, n):
+    """Current (f, k1, k2) of every camera, [n, 3]."""
+    out = np.empty((n, 3))
+    _check(p, _lib.ba_get_intrinsics(p, BA_MEM_HOST, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def ba_intrinsics_count(p):
+    n = C.c_int64()
+    _check(p, _lib.ba_intrinsics_count(p, C.byref(n)))
+    return n.value
+
+
+def ba_get_step_intrinsics(p):
+    """The intrinsics part of the last computed step, [n_intr, 3]."""
+    n = ba_intrinsics_count(p)
+    out = np.empty((n, 3))
+    _check(p, _lib.ba_get_step_intrinsics(p, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
 def ba_lm_step(p):
     r = ba_step_report()
     _check(p, _lib.ba_lm_step(p, C.byref(r)))
@@ -375,6 +409,9 @@ def load_scene(p, scene, device_tensors=False):
         ba_add_groups(p, BA_PLANE, conv(scene["planes"]))
     if len(scene["vps"]):
         ba_add_groups(p, BA_VP, conv(scene["vps"]))
+    ik = scene.get("intrinsics")
+    if ik is not None:
+        ba_set_intrinsics(p, conv(np.asarray(ik["values"], np.float64)), conv(np.asarray(ik["of_cam"], np.int32)))
     rel = scene.get("relations")
     if rel is not None and len(rel["a"]):
         ba_add_relations(p, conv(rel["ka"].astype(np.int32)), conv(rel["a"]), conv(rel["kb"].astype(np.int32)),

@@ -58,6 +58,7 @@ extern "C" void ba_default_options(ba_options* o) {
   o->mixed_lambda_floor = 0.0;
   o->w_rel = 5e3;
   o->cauchy_rel = 0.2;
+  o->cam_dof = 6;
 }
 
 extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
@@ -70,6 +71,7 @@ extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
   if (p->opt.precond != BA_PRECOND_BLOCK_JACOBI && p->opt.precond != BA_PRECOND_LEARNED) { delete p; return BA_ERR_ARG; }
   if (!(p->opt.pcg_rel_tol > 0) || p->opt.pcg_max_iters <= 0) { delete p; return BA_ERR_ARG; }
   if ((p->opt.dev_alloc == nullptr) != (p->opt.dev_free == nullptr)) { delete p; return BA_ERR_ARG; }
+  if (p->opt.cam_dof != 6 && p->opt.cam_dof != 9) { delete p; return BA_ERR_ARG; }
   if (p->opt.precision == BA_MIXED) p->opt.lambda_min = std::max(p->opt.lambda_min, p->opt.mixed_lambda_floor);
   p->alloc.fa = p->opt.dev_alloc; p->alloc.ff = p->opt.dev_free; p->alloc.ctx = p->opt.alloc_ctx;
   p->stream = (cudaStream_t)p->opt.cuda_stream;
@@ -187,6 +189,28 @@ extern "C" ba_status ba_add_relations(ba_problem* p, int64_t n, int mem, const i
   p->h_rel.resize(o + 5 * (size_t)n);
   for (int64_t i = 0; i < n; ++i)
     for (int k = 0; k < 5; ++k) p->h_rel[o + 5 * i + k] = cols[k][i];
+  return BA_OK;
+}
+
+extern "C" ba_status ba_set_intrinsics(ba_problem* p, int64_t n_intr, int mem, const double* fk,
+                                      const int32_t* intr_of_cam, int64_t n_cams) {
+  ba_status s = check_add(p, n_intr);
+  if (s) return s;
+  if (p->opt.cam_dof != 9) return set_err(p, BA_ERR_ARG, "ba_set_intrinsics needs cam_dof = 9 (refined intrinsics)");
+  if (n_cams < 0) return set_err(p, BA_ERR_ARG, "negative count");
+  if ((n_intr && !fk) || (n_cams && !intr_of_cam)) return set_err(p, BA_ERR_ARG, "null array");
+  std::vector<double> v;
+  std::vector<int32_t> m;
+  if ((s = fetch(p, mem, fk, 3 * (size_t)n_intr, v))) return s;
+  if ((s = fetch(p, mem, intr_of_cam, (size_t)n_cams, m))) return s;
+  for (double x : v)
+    if (!std::isfinite(x)) return set_err(p, BA_ERR_ARG, "non-finite intrinsics value");
+  for (int64_t i = 0; i < n_cams; ++i)
+    if (m[i] < 0 || m[i] >= n_intr)
+      return set_err(p, BA_ERR_ARG, "intr_of_cam[" + std::to_string(i) + "] out of range");
+  p->h_intr = std::move(v);
+  p->h_cam_k = std::move(m);
+  p->intr_set = true;
   return BA_OK;
 }
 
@@ -446,6 +470,7 @@ static ba_status freeze(ba_problem* p) {
   p->slotH = p->slotG ? (void*)((char*)p->slotG + T * HG_H) : nullptr;   // a view into the G|H records
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
+  if (d.nk) ok &= A(p->slotCK, T * SC * (size_t)d.ne);
   ok &= A(p->slotBS, T * SBS * (size_t)d.ne);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
@@ -471,6 +496,7 @@ static ba_status freeze(ba_problem* p) {
   // one-time zero fill of the slot and feature arrays
   CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
+  if (d.nk) CUDA_OR(p, cudaMemsetAsync(p->slotCK, 0, T * SC * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
   if (mixed(p) && d.nr) {
@@ -507,7 +533,8 @@ static ba_status ensure_sstore(ba_problem* p, bool for_batch) {
   if (p->Sval) return BA_OK;
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
-  p->typed = !for_batch && d.nc > 0 && 3 * d.npl + 2 * d.nv <= GV_MAX;
+  // refined intrinsics keep the full storage: the typed storage knows camera, plane and VP columns only
+  p->typed = !for_batch && d.nc > 0 && d.nk == 0 && 3 * d.npl + 2 * d.nv <= GV_MAX;
   ba_status s;
   if (p->typed) {
     TypedPlan tplan;
@@ -715,6 +742,45 @@ extern "C" ba_status ba_get_groups(ba_problem* p, int kind, int mem, double* par
   if (kind == BA_PLANE) return put_out(p, mem, params, (const double*)p->ps[p->cur].pln, 4 * (size_t)p->d.npl);
   if (kind == BA_VP) return put_out(p, mem, params, (const double*)p->ps[p->cur].vps, 3 * (size_t)p->d.nv);
   return set_err(p, BA_ERR_ARG, "bad group kind");
+}
+
+extern "C" ba_status ba_get_intrinsics(ba_problem* p, int mem, double* fk) {
+  if (!p) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  const int64_t n = p->d.nc;
+  std::vector<double> h(12 * n);
+  if ((s = put_out(p, BA_MEM_HOST, h.data(), p->ps[p->cur].cam, h.size()))) return s;
+  std::vector<double> o(3 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) o[3 * i + k] = h[12 * i + 7 + k];
+  if (n == 0) return BA_OK;
+  if (!fk) return set_err(p, BA_ERR_ARG, "null output");
+  if (mem == BA_MEM_HOST) { std::memcpy(fk, o.data(), o.size() * sizeof(double)); return BA_OK; }
+  CUDA_OR(p, cudaMemcpy(fk, o.data(), o.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return BA_OK;
+}
+
+extern "C" ba_status ba_intrinsics_count(ba_problem* p, int64_t* n) {
+  if (!p || !n) return BA_ERR_ARG;
+  ba_status s = freeze(p);
+  if (s) return s;
+  *n = p->d.nk;
+  return BA_OK;
+}
+
+extern "C" ba_status ba_get_step_intrinsics(ba_problem* p, double* dk) {
+  if (!p) return BA_ERR_ARG;
+  if (!p->frozen) return set_err(p, BA_ERR_STATE, "no step computed");
+  const Dims& d = p->d;
+  if (d.nk == 0) return BA_OK;
+  if (!dk) return set_err(p, BA_ERR_ARG, "null output");
+  std::vector<double> x(6 * (size_t)d.nk);
+  ba_status s;
+  if ((s = put_out(p, BA_MEM_HOST, x.data(), (const double*)p->x + 6 * (d.nc + d.npl + d.nv), x.size()))) return s;
+  for (int64_t k = 0; k < d.nk; ++k)
+    for (int j = 0; j < 3; ++j) dk[3 * k + j] = x[6 * k + j];
+  return BA_OK;
 }
 
 extern "C" ba_status ba_get_lm_state(ba_problem* p, double* ln) {
@@ -1116,6 +1182,7 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
     if (p->device != p0->device) return set_err(p0, BA_ERR_ARG, "all windows of a batch must be on one device");
     ba_status s = freeze(p);
     if (!s && p->nrel) s = set_err(p, BA_ERR_ARG, "inter-group relations are not supported in batched windows");
+    if (!s && p->d.nk) s = set_err(p, BA_ERR_ARG, "refined intrinsics (cam_dof 9) are not supported in batched windows");
     if (!s) s = ensure_sstore(p, true);
     if (s) return set_err(p0, s, "window " + std::to_string(i) + ": " + p->err);
     if (p->typed)

@@ -61,10 +61,20 @@ constexpr int SG = 28;
 constexpr int HG_H = 6;
 constexpr int SH = SG;
 constexpr int SB = 6;   // the whitened per-slot b part
-constexpr int SC = 20;  // camera slot: J_cam^T w J_plane (6 x 3, 18 values)
+constexpr int SC = 20;  // camera slot: J_cam^T w J_plane (6 x 3, 18 values); intrinsics slot: J_K^T w J_plane
+                        // (3 x 3 in the first 9); with refined intrinsics a second camera record of this size
+                        // holds J_cam^T w J_K (6 x 3) of the camera's own intrinsics entity
 constexpr int SBS = 6;  // back-substitution record per slot (6 values, unpadded: padding cost more than it saved)
 
-enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2 };
+enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2, ENT_INTR = 3 };
+// real dimensions of an entity block: camera pose 6, plane 3, VP 2, intrinsics (f, k1, k2) 3
+__host__ __device__ __forceinline__ int ent_dims(int et) { return et == ENT_CAM ? 6 : (et == ENT_VP ? 2 : 3); }
+// direct coupling carried by a slot pair (pair_b bits 30-31): none, camera-plane (the camera slot's C record),
+// camera-intrinsics (the camera slot's CK record, its own entity only), plane-intrinsics (the intrinsics slot's
+// C record, transposed)
+constexpr uint32_t PAIR_CP = 1u, PAIR_CK = 2u, PAIR_PK = 3u;
+constexpr int PAIR_SHIFT = 30;
+constexpr int32_t PAIR_SLOT = 0x3fffffff;
 
 constexpr int PCG_FLAG_TIMEOUT = 8;   // DevScalars::flags bit: a bounded device-side wait of the PCG ran out
 
@@ -144,6 +154,7 @@ using Problem = ::ba_problem;
 
 struct Dims {
   int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
+  int64_t nk = 0;    // intrinsics entities (refined f, k1, k2; A indices nc + npl + nv + k)
   int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0;  // nbf stored blocks, nbp padded
   int64_t nun = 0, nmulti = 0;   // Schur work units of the grid path; blocks split over several units
   int64_t nun_main = 0, npack = 0;   // units a warp takes alone (the rest are packed), and the packs
@@ -194,6 +205,10 @@ struct ba_problem {
   std::vector<uint8_t> h_fixed;
   std::vector<double> h_pts, h_lin, h_pln, h_vps;
   std::vector<int32_t> h_rel;     // inter-group relations as added: 5 per relation (kind_a, a, kind_b, b, type)
+  // shared intrinsics (ba_set_intrinsics): entity values (3 each) and every camera's entity
+  std::vector<double> h_intr;
+  std::vector<int32_t> h_cam_k;
+  bool intr_set = false;
   // residual records as added, copied to the device at add time (validated and merged by the structure build,
   // which releases them); cam is null for VP records, other may be null, meas holds n x meas_dim values
   struct ObsBatch {
@@ -217,15 +232,19 @@ struct ba_problem {
   // parameters: two FP64 sets (current / candidate), each with its FP64 derived per-entity data
   struct ParamSet {
     double *cam = nullptr, *pts = nullptr, *lin = nullptr, *pln = nullptr, *vps = nullptr;
+    double* intr = nullptr;   // intrinsics entities (f, k1, k2), refined intrinsics only; each camera's f, k1, k2
+                              // in cam is a copy of its entity's values
     double *camD = nullptr, *grpD = nullptr;   // rotation matrices / tangent bases (CAM_STRIDE / GRP_STRIDE)
   } ps[2];
   int cur = 0;
   // working-type (double or float) copies of the current parameters used by the linearisation
   void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr;
   uint8_t* cam_fixed = nullptr;
+  int32_t* cam_k = nullptr;   // per camera its intrinsics entity (refined intrinsics only)
   // residuals, feature-major
   int8_t* rkind = nullptr;
   int32_t *rcam = nullptr, *rfeat = nullptr, *rgrp = nullptr, *rslot_c = nullptr, *rslot_g = nullptr;
+  int32_t* rslot_k = nullptr;   // per residual the slot of its camera's intrinsics entity (or -1)
   double* meas64 = nullptr;
   int32_t* cost_order = nullptr;   // residual indices sorted by kind (feature-major inside a kind)
   void* measT = nullptr;
@@ -238,7 +257,7 @@ struct ba_problem {
   int32_t *row_ptr = nullptr, *col = nullptr;
   std::vector<int32_t> h_prow_ptr, h_row_len;
   int32_t *up_row = nullptr, *up_full = nullptr, *up_mirror = nullptr;
-  int32_t *pair_a = nullptr, *pair_b = nullptr;   // pair_b bit 31: camera-plane pair
+  int32_t *pair_a = nullptr, *pair_b = nullptr;   // pair_b bits 30-31: the pair's direct coupling (PAIR_CP ...)
   // grid-path Schur work units: pair range, block, processing order (long units first), first unit of
   // every block, and the blocks whose units leave FP64 partials (48 per unit in upart)
   int32_t *un_se = nullptr, *un_blk = nullptr, *un_order = nullptr, *up_un = nullptr, *multi_blk = nullptr;
@@ -281,6 +300,7 @@ struct ba_problem {
   cudaError_t pcg_err = cudaSuccess;
   // numeric arrays
   void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotZ = nullptr, *slotB = nullptr;
+  void* slotCK = nullptr;       // refined intrinsics: per camera slot J_cam^T w J_K of its own entity (SC)
   void* slotBS = nullptr;       // back-substitution: per slot W da (4), G.da, da^T H da + 2 da^T C dplane
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featu = nullptr, *featL = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr;

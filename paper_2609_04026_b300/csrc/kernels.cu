@@ -241,6 +241,9 @@ struct LinArgs {
   const int8_t* rkind;
   const uint8_t* cam_mask;   // held pose components per camera (bit k = increment k)
   const int32_t *rcam, *rgrp, *rslot_c, *rslot_g, *fres_off, *feat_plane_slot;
+  const int32_t *rslot_k, *fslot_off;   // refined intrinsics: per residual its intrinsics slot; slots per feature
+  const uint8_t* slot_type;
+  T* CK;                                // per camera slot J_cam^T w J_K of its own intrinsics entity
   const T* meas;
   const T *cam, *pts, *lin, *grp;
   int64_t npl, np;
@@ -293,7 +296,7 @@ __device__ __forceinline__ void load16(const T* __restrict__ src, T* dst) {
   for (int i = NT2; i < N; ++i) dst[i] = src[i];
 }
 
-template <class T, int KF>
+template <class T, int KF, bool INTR = false>
 __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   constexpr int NV = KF * (KF + 1) / 2;
@@ -360,13 +363,82 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   };
   zero_cam();
 
+  // refined intrinsics: the accumulators of the current intrinsics slot (W, G, the direct 3 x 3 block and the
+  // coupling with the feature's plane), added into the slot's records whenever the slot changes (a slot may
+  // recur: the residuals are in camera order and cameras may share an entity), and the current camera slot's
+  // coupling with its own entity
+  T Wk[KF][3], Gk[3], Hk[6], KPk[3][3], CKc[6][3];
+  int curk = -1;
+  auto zero_k = [&]() {
+#pragma unroll
+    for (int i = 0; i < KF; ++i) Wk[i][0] = Wk[i][1] = Wk[i][2] = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { Gk[i] = 0; KPk[i][0] = KPk[i][1] = KPk[i][2] = 0; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Hk[i] = 0;
+  };
+  auto zero_ck = [&]() {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) CKc[i][0] = CKc[i][1] = CKc[i][2] = 0;
+  };
+  auto add_k = [&](int e) {
+    T wb[KF * 6], gh[SG], cb[SC];
+    load16<T, KF * 6>(a.W + (size_t)e * SW, wb);
+    load16<T, SG>(a.G + (size_t)e * SG, gh);
+    load16<T, SC>(a.C + (size_t)e * SC, cb);
+#pragma unroll
+    for (int i = 0; i < KF; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) wb[i * 6 + j] += Wk[i][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      gh[i] += Gk[i];
+#pragma unroll
+      for (int j = i; j < 3; ++j) gh[HG_H + up_idx(i, j, 6)] += Hk[up_idx(i, j, 3)];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cb[i * 3 + j] += KPk[i][j];
+    }
+    store16<T, KF * 6>(a.W + (size_t)e * SW, wb);
+    store16<T, SG>(a.G + (size_t)e * SG, gh);
+    store16<T, SC>(a.C + (size_t)e * SC, cb);
+  };
+  if constexpr (INTR) {
+    zero_k();
+    zero_ck();
+    // the feature's intrinsics slots start from zero (they are summed into below)
+    const T z[SG > SC ? SG : SC] = {};
+    for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e)
+      if (a.slot_type[e] == ENT_INTR) {
+        store16<T, KF * 6>(a.W + (size_t)e * SW, z);
+        store16<T, SG>(a.G + (size_t)e * SG, z);
+        store16<T, SC>(a.C + (size_t)e * SC, z);
+      }
+  }
+
   for (int rr = r0; rr < r1; ++rr) {
     const int kind = a.rkind[rr];
     const int sc = a.rslot_c[rr];
     if (sc != cur) {
+      if constexpr (INTR) {
+        if (cur >= 0) {
+          T cb[SC];
+#pragma unroll
+          for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? CKc[i / 3][i % 3] : T(0);
+          store16<T, SC>(a.CK + (size_t)cur * SC, cb);
+        }
+        zero_ck();
+      }
       if (cur >= 0) flush(cur);
       zero_cam();
       cur = sc;
+    }
+    if constexpr (INTR) {
+      const int sk = a.rslot_k[rr];
+      if (sk != curk) {
+        if (curk >= 0) add_k(curk);
+        zero_k();
+        curk = sk;
+      }
     }
     const int camid = a.rcam[rr];
     const int gid = a.rgrp[rr];
@@ -378,15 +450,15 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
     int rd = res_dim(kind);
     bool has_plane = false, has_vp = false;
     if (KF == 3) {
-      if (kind == R_POINT) res_point<T, true>(c, F, meas, o);
-      else if (kind == R_PLANE_POINT) { res_plane_point<T, true>(c, F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
-      else if (kind == R_P2L) res_p2l<T, true>(c, F, meas, o);
+      if (kind == R_POINT) res_point<T, true, INTR>(c, F, meas, o);
+      else if (kind == R_PLANE_POINT) { res_plane_point<T, true, INTR>(c, F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
+      else if (kind == R_P2L) res_p2l<T, true, INTR>(c, F, meas, o);
       else continue;
     } else {
-      if (kind == R_LINE) res_line<T, true>(c, F, meas, o);
-      else if (kind == R_PLANE_LINE) { res_plane_line<T, true>(c, F, a.grp + (size_t)GRP_STRIDE * gid, meas, o); has_plane = true; }
-      else if (kind == R_VP) { res_vp<T, true>(F, a.grp + (size_t)GRP_STRIDE * (a.npl + gid), o); has_vp = true; }
-      else if (kind == R_L2P) res_l2p<T, true>(c, F, meas, o);
+      if (kind == R_LINE) res_line<T, true, INTR>(c, F, meas, o);
+      else if (kind == R_PLANE_LINE) { res_plane_line<T, true, INTR>(c, F, a.grp + (size_t)GRP_STRIDE * gid, meas, o); has_plane = true; }
+      else if (kind == R_VP) { res_vp<T, true, INTR>(F, a.grp + (size_t)GRP_STRIDE * (a.npl + gid), o); has_vp = true; }
+      else if (kind == R_L2P) res_l2p<T, true, INTR>(c, F, meas, o);
       else continue;
     }
     if (!o.valid) continue;
@@ -466,7 +538,43 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
           for (int q = p; q < 2; ++q) Hv[up_idx(p, q, 2)] += wg[p] * o.Jg[i][q];
         }
       }
+      if constexpr (INTR) {
+        if (curk >= 0) {
+          T wk[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) wk[k] = om * o.Jk[i][k];
+#pragma unroll
+          for (int p = 0; p < KF; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Wk[p][q] += wf[p] * o.Jk[i][q];
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            Gk[p] += wk[p] * ri;
+#pragma unroll
+            for (int q = p; q < 3; ++q) Hk[up_idx(p, q, 3)] += wk[p] * o.Jk[i][q];
+          }
+          if (has_plane)
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+              for (int q = 0; q < 3; ++q) KPk[p][q] += wk[p] * o.Jg[i][q];
+          if (camslot)
+#pragma unroll
+            for (int p = 0; p < 6; ++p)
+#pragma unroll
+              for (int q = 0; q < 3; ++q) CKc[p][q] += wc[p] * o.Jk[i][q];
+        }
+      }
     }
+  }
+  if constexpr (INTR) {
+    if (cur >= 0) {
+      T cb[SC];
+#pragma unroll
+      for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? CKc[i / 3][i % 3] : T(0);
+      store16<T, SC>(a.CK + (size_t)cur * SC, cb);
+    }
+    if (curk >= 0) add_k(curk);
   }
   if (cur >= 0) flush(cur);
   // group slots, padded to the 6-wide block of the reduced system
@@ -507,10 +615,10 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   store16<double, KF>(a.g + 4 * f, gbf);
 }
 
-template <class T, int KF>
+template <class T, int KF, bool INTR = false>
 __global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int64_t f1) {
   int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f < f1) linearize_feature<T, KF>(a, f);
+  if (f < f1) linearize_feature<T, KF, INTR>(a, f);
 }
 
 // ============================================================================
@@ -726,7 +834,7 @@ struct BlockArgs {
   SView sv;        // where each block of S is stored (full or typed storage)
   double *b, *Dg, *sdiag;
   const double *relH, *relG;   // inter-group relations: per group entity J^T w J (36) and J^T w r (6), or null
-  int64_t nc;
+  int64_t nc, ngend;           // cameras; end of the group entities (planes and VPs; intrinsics entities follow)
   double lambda;
 };
 
@@ -737,6 +845,7 @@ struct UnitArgs {
   const int32_t* un_mflag;  // per unit in processing order: mirror position << 2 | written directly << 1 | diagonal
   const int4* pk_desc;      // per pack of small units: first unit (processing order), units, first pair, pairs
   const T *Z, *H, *B, *C;
+  const T* CK;     // refined intrinsics: per camera slot J_cam^T w J_K of its own entity (or null)
   double* upart;   // 48 per unit: 36 S, 6 b, 6 diag(H)
   int64_t nun, nmulti, nun_main, npack;
   int line_slot0;
@@ -796,7 +905,7 @@ template <class T>
 __device__ void finish_diag(const BlockArgs<T>& a, int row, int fpos, double (&s)[36], double (&bb)[6],
                             double (&hh)[6]) {
   // a group's inter-group relations (direct terms of H_gg and g_g, Section 3.2), before the damping
-  if (a.relH && row >= a.nc) {
+  if (a.relH && row >= a.nc && row < a.ngend) {
     const double* H = a.relH + 36 * (size_t)(row - a.nc);
     const double* G = a.relG + 6 * (size_t)(row - a.nc);
 #pragma unroll
@@ -814,8 +923,7 @@ __device__ void finish_diag(const BlockArgs<T>& a, int row, int fpos, double (&s
       s[i * 6 + j] = m;
       s[j * 6 + i] = m;
     }
-  const int et = a.ent_type[row];
-  const int nd = et == ENT_CAM ? 6 : (et == ENT_PLANE ? 3 : 2);
+  const int nd = ent_dims(a.ent_type[row]);
   const unsigned held = (row < a.nc) ? a.cam_fixed[row] : 0u;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -946,7 +1054,7 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
     for (int t = lane; t < n * 2 * CH; t += 32) {
       const int p = t / (2 * CH), r = t - p * 2 * CH;
       const int which = r / CH, ch = r - which * CH;
-      const int e = which == 0 ? sa_[p] : (sb_[p] & 0x7fffffff);
+      const int e = which == 0 ? sa_[p] : (sb_[p] & PAIR_SLOT);
       cp_async16(reinterpret_cast<char*>(stage + p * ST + which * SW) + 16 * ch,
                  reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * ch);
     }
@@ -954,7 +1062,7 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
     __syncwarp();
     if (lane < n) {
       const int ea = sa_[lane];
-      const bool cp = ((unsigned)sb_[lane] >> 31) != 0u;
+      const unsigned code = (unsigned)sb_[lane] >> PAIR_SHIFT;
       const bool line = ea >= a.line_slot0;
       T za[24], zb[24];
       load_rec(stage + lane * ST, za, line);
@@ -969,12 +1077,20 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
 #pragma unroll
           for (int j = 0; j < 6; ++j) acc[i * 6 + j] += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] - pair_dot(za, zb, i, j, line);
         }
-      } else if (cp) {
-        const T* Cm = a.C + (size_t)ea * SC;
+      } else if (code == PAIR_CP || code == PAIR_CK) {
+        // the camera's direct block with the plane, or with its own intrinsics entity (6 x 3)
+        const T* Cm = (code == PAIR_CP ? a.C : a.CK) + (size_t)ea * SC;
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
           for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+      } else if (code == PAIR_PK) {
+        // plane-intrinsics: the intrinsics slot holds J_K^T w J_plane (3 x 3); this block is its transpose
+        const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (i < 3 && j < 3 ? Cm[j * 3 + i] : T(0)) - pair_dot(za, zb, i, j, line);
       } else {
 #pragma unroll
         for (int e = 0; e < 36; ++e) acc[e] -= pair_dot(za, zb, e / 6, e % 6, line);
@@ -2475,6 +2591,9 @@ struct BackArgs {
   const uint8_t* slot_type;
   const double *V, *Vinv, *g, *x;
   const T *W, *H, *G, *C;
+  const T* CK;              // refined intrinsics: camera slots' blocks with their own entity (else null)
+  const int32_t* cam_k;     // refined intrinsics: per camera its entity (else null)
+  int64_t kbase;            // A index of intrinsics entity 0
   T* sv;        // per slot: W_e da (4, zero-padded), G_e . da, da^T H_e da + 2 da^T C_e dplane
   double* df;
   int64_t np, nf, ne;
@@ -2532,6 +2651,28 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
+  }
+  if (a.cam_k) {
+    // refined intrinsics: a camera slot's direct block with its own entity, an intrinsics slot's with the plane
+    if (a.slot_type[e] == ENT_CAM) {
+      const double* dk = a.x + 6 * (size_t)(a.kbase + a.cam_k[a.slot_ent[e]]);
+      const T dkv[3] = {(T)dk[0], (T)dk[1], (T)dk[2]};
+      T Ck[18];
+      load16<T, 18>(a.CK + (size_t)e * SC, Ck);
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cpl += dv[i] * Ck[i * 3 + j] * dkv[j];
+    } else if (a.slot_type[e] == ENT_INTR && pslot >= 0) {
+      const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
+      const T dpl[3] = {(T)dp[0], (T)dp[1], (T)dp[2]};
+      T Cm[18];
+      load16<T, 18>(a.C + (size_t)e * SC, Cm);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
+    }
   }
   so[4] = gd;
   so[5] = hq + T(2) * cpl;
@@ -2642,14 +2783,31 @@ struct CandArgs {
   const uint8_t* fixed;
   double *cam2, *pts2, *lin2, *pln2, *vps2;
   int64_t nc, np, nl, npl, nv;
+  // refined intrinsics (else nk = 0): entities, their candidate values, every camera's entity, A index of entity 0
+  const double* intr;
+  double* intr2;
+  const int32_t* cam_k;
+  int64_t nk, kbase;
 };
 
+// items: cameras, planes, VPs, points, lines, then the intrinsics entities
 __device__ void candidate_item(const CandArgs& a, int64_t i) {
   const int64_t n0 = a.nc, n1 = n0 + a.npl, n2 = n1 + a.nv, n3 = n2 + a.np;
+  if (i >= n3 + a.nl) {
+    // intrinsics entity: additive (f, k1, k2)
+    const int64_t k = i - n3 - a.nl;
+    for (int j = 0; j < 3; ++j) a.intr2[3 * k + j] = a.intr[3 * k + j] + a.x[6 * (a.kbase + k) + j];
+    return;
+  }
   if (i < n0) {
     const double* c = a.cam + 12 * i;
     double* o = a.cam2 + 12 * i;
     for (int k = 0; k < 12; ++k) o[k] = c[k];
+    if (a.nk) {
+      // the camera's f, k1, k2: its entity's candidate values (the same sums as the entity's item)
+      const int64_t k = a.cam_k[i];
+      for (int j = 0; j < 3; ++j) o[7 + j] = a.intr[3 * k + j] + a.x[6 * (a.kbase + k) + j];
+    }
     if (a.fixed[i] == 0x3F) return;
     const double* dl = a.x + 6 * i;   // held components have zero increments
     double Rd[9], R[9], Rn[9];
@@ -2985,6 +3143,13 @@ void launch_linearize(Problem& P) {
   a.W = (T*)P.slotW; a.H = (T*)P.slotH; a.G = (T*)P.slotG; a.C = (T*)P.slotC;
   a.V = P.featV; a.g = P.featg;
   a.loss = make_loss(P.opt);
+  a.rslot_k = P.rslot_k; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = (T*)P.slotCK;
+  if (d.nk) {
+    // refined intrinsics: the feature's intrinsics slots and the camera slots' couplings with them too
+    if (d.np) { ++P.launches; k_linearize<T, 3, true><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
+    if (d.nl) { ++P.launches; k_linearize<T, 4, true><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
+    return;
+  }
   if (d.np) { ++P.launches; k_linearize<T, 3><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
   if (d.nl) { ++P.launches; k_linearize<T, 4><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
 }
@@ -3006,13 +3171,14 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   BlockArgs<T> b;
   b.up_row = P.up_row; b.up_full = P.up_full; b.up_mirror = P.up_mirror; b.col = P.col;
   b.ent_type = P.ent_type; b.cam_fixed = P.cam_fixed; b.Sval = (T*)P.Sval; b.sv = sview_of(P);
-  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nc = d.nc; b.lambda = lambda;
+  b.b = P.bvec; b.Dg = P.Dg; b.sdiag = P.sdiag; b.nc = d.nc; b.ngend = d.nc + d.npl + d.nv; b.lambda = lambda;
   b.relH = P.nrel ? P.relH : nullptr; b.relG = P.nrel ? P.relG : nullptr;
   UnitArgs<T> un;
   un.un_se = P.un_se; un.un_blk = P.un_blk; un.un_order = P.un_order; un.up_un = P.up_un; un.multi = P.multi_blk;
   un.un_desc = reinterpret_cast<const int4*>(P.un_desc); un.un_mflag = P.un_mflag;
   un.pair_a = P.pair_a; un.pair_b = P.pair_b; un.Z = (const T*)P.slotZ; un.H = (const T*)P.slotH;
-  un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.upart = P.upart; un.nun = d.nun; un.nmulti = d.nmulti;
+  un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.CK = (const T*)P.slotCK; un.upart = P.upart;
+  un.nun = d.nun; un.nmulti = d.nmulti;
   un.pk_desc = reinterpret_cast<const int4*>(P.pk_desc); un.nun_main = d.nun_main; un.npack = d.npack;
   un.line_slot0 = P.line_slot0; un.fb = b;
   return un;
@@ -3168,6 +3334,7 @@ void launch_backsub(Problem& P) {
   a.slot_type = P.slot_type; a.V = P.featV; a.Vinv = P.featVinv; a.g = P.featg; a.x = P.x;
   a.W = (const T*)P.slotW; a.H = (const T*)P.slotH; a.G = (const T*)P.slotG; a.C = (const T*)P.slotC;
   a.sv = (T*)P.slotBS; a.df = P.dfeat; a.np = d.np; a.nf = d.nf; a.ne = d.ne; a.S = P.S; a.red = P.red;
+  a.CK = (const T*)P.slotCK; a.cam_k = d.nk ? P.cam_k : nullptr; a.kbase = d.nc + d.npl + d.nv;
   if (d.ne) { ++P.launches; k_backsub_slots<T><<<nblk(d.ne, 128), 128, 0, P.stream>>>(a); }
   ++P.launches;
   k_backsub<T><<<nblk(d.nf > 0 ? d.nf : 1, 128), 128, 0, P.stream>>>(a);
@@ -3181,7 +3348,8 @@ void launch_candidate(Problem& P) {
   a.cam = c.cam; a.pts = c.pts; a.lin = c.lin; a.pln = c.pln; a.vps = c.vps; a.x = P.x; a.df = P.dfeat;
   a.fixed = P.cam_fixed; a.cam2 = n.cam; a.pts2 = n.pts; a.lin2 = n.lin; a.pln2 = n.pln; a.vps2 = n.vps;
   a.nc = d.nc; a.np = d.np; a.nl = d.nl; a.npl = d.npl; a.nv = d.nv;
-  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl;
+  a.intr = c.intr; a.intr2 = n.intr; a.cam_k = P.cam_k; a.nk = d.nk; a.kbase = d.nc + d.npl + d.nv;
+  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl + d.nk;
   if (tot) { ++P.launches; k_candidate<<<nblk(tot, 128), 128, 0, P.stream>>>(a); }
 }
 
@@ -3553,6 +3721,7 @@ void fill_window_desc(Problem& P, void* out) {
   a.npl = d.npl; a.np = d.np;
   a.W = (T*)P.slotW; a.H = (T*)P.slotH; a.G = (T*)P.slotG; a.C = (T*)P.slotC; a.V = P.featV; a.g = P.featg;
   a.loss = make_loss(P.opt);
+  a.rslot_k = nullptr; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = nullptr;
   InvArgs<T>& ia = W.inv;
   ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
   ia.slot_feat = P.slot_feat; ia.Vinv = P.featVinv; ia.u = P.featu; ia.L = P.featL; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB;
@@ -3564,8 +3733,10 @@ void fill_window_desc(Problem& P, void* out) {
   k.V = P.featV; k.Vinv = P.featVinv; k.g = P.featg; k.x = P.x; k.W = (const T*)P.slotW; k.H = (const T*)P.slotH;
   k.G = (const T*)P.slotG; k.C = (const T*)P.slotC; k.df = P.dfeat; k.np = d.np; k.nf = d.nf; k.S = P.S; k.red = P.red;
   k.slot_feat = P.slot_feat; k.sv = (T*)P.slotBS; k.ne = d.ne;
+  k.CK = nullptr; k.cam_k = nullptr; k.kbase = 0;
   CandArgs& c = W.cand;
   c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
+  c.intr = nullptr; c.intr2 = nullptr; c.cam_k = nullptr; c.nk = 0; c.kbase = 0;   // windows: no refined intrinsics
   CostArgs& co = W.cost;
   co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64; co.order = P.cost_order;
   co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;

@@ -44,8 +44,7 @@ __device__ __forceinline__ double warp_max_d(double v) {
 
 // real (non-padding, non-held) dimensions of entity a as a 6-bit mask
 __device__ __forceinline__ unsigned real_mask(int64_t a, int64_t nc, const uint8_t* ent_type, const uint8_t* held) {
-  const int et = ent_type[a];
-  const int nd = et == ENT_CAM ? 6 : (et == ENT_PLANE ? 3 : 2);
+  const int nd = ent_dims(ent_type[a]);
   unsigned m = (1u << nd) - 1u;
   if (a < nc) m &= ~(unsigned)held[a];
   return m;
@@ -96,7 +95,7 @@ __global__ void k_pre_features(int64_t na, int64_t nc, const int32_t* __restrict
     float* x = X + (size_t)a * NF;
     x[21] = (float)log1p(cnt); x[22] = (float)s1; x[23] = (float)mx; x[24] = (float)s2;
     const int et = ent_type[a];
-    x[25] = et == 0; x[26] = et == 1; x[27] = et == 2;
+    x[25] = et == 0; x[26] = et == 1 || et == 3; x[27] = et == 2;   // an intrinsics block counts as a 3-wide group
     x[28] = x[29] = x[30] = x[31] = 0.f;
     mask[a] = (uint8_t)real_mask(a, nc, ent_type, held);
   }

@@ -24,6 +24,8 @@
 //   R7 wireframe line->point    Eq. 12 (pinhole pixels)
 // Lines and the wireframe terms live in undistorted pixel coordinates; only R1
 // and R3 use k1, k2.
+// With INTR (refined intrinsics, Section 3.1) a residual also gives its rows of the
+// Jacobian with respect to the additive increments of the camera's (f, k1, k2).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -96,8 +98,21 @@ struct ResJ {
   T Jc[4][6];
   T Jf[4][4];
   T Jg[4][3];
+  T Jk[4][3];   // w.r.t. the camera's (f, k1, k2), filled only when asked for (INTR)
   bool valid;
 };
+
+// d pi / d (f, k1, k2) of the distorted projection of x_cam: (s u, f r^2 u, f r^4 u), the same with v
+template <class T>
+__device__ __forceinline__ void project_dist_k(const Cam<T>& c, const T* xc, T Jk[2][3]) {
+  T iz = T(1) / xc[2];
+  T u = xc[0] * iz, v = xc[1] * iz;
+  T r2 = u * u + v * v;
+  T s = T(1) + c.k1 * r2 + c.k2 * r2 * r2;
+  T fr2 = c.f * r2, fr4 = c.f * r2 * r2;
+  Jk[0][0] = s * u; Jk[0][1] = fr2 * u; Jk[0][2] = fr4 * u;
+  Jk[1][0] = s * v; Jk[1][1] = fr2 * v; Jk[1][2] = fr4 * v;
+}
 
 // ---------------------------------------------------------------- camera / point pieces
 // rotation columns of the pose Jacobian for one row g of d(res)/d(x_cam):
@@ -304,7 +319,7 @@ __device__ __forceinline__ void plane_proj_line_dir(const T* n, T w, const T* d,
 
 // ---------------------------------------------------------------- the seven residuals
 // R1: pi(C, X) - x_ij
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_point(const Cam<T>& c, const T* X, const T* meas, ResJ<T>& o) {
   T p[3], xc[3], pi[2], J[2][3];
   matvec3(c.R, X, p);
@@ -322,11 +337,12 @@ __device__ void res_point(const Cam<T>& c, const T* X, const T* meas, ResJ<T>& o
 #pragma unroll
       for (int k = 0; k < 3; ++k) o.Jf[i][k] = J[i][0] * c.R[k] + J[i][1] * c.R[3 + k] + J[i][2] * c.R[6 + k];
     }
+    if (INTR) project_dist_k(c, xc, o.Jk);
   }
 }
 
 // R2: rho(pi_l(C, L), segment)
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_line(const Cam<T>& c, const T* L, const T* seg, ResJ<T>& o) {
   T dc[3], Rm[3], mc[3], l[3], G[4][3];
   line_to_cam(c, L, L + 3, dc, Rm, mc);
@@ -346,10 +362,17 @@ __device__ void res_line(const Cam<T>& c, const T* L, const T* seg, ResJ<T>& o) 
 #pragma unroll
     for (int k = 0; k < 4; ++k) o.Jf[i][k] = dot3(G[i], dmc[k]);
   }
+  if (INTR) {
+    // only l_2 = f m_c2 - ... depends on f (d l_2 / d f = m_c2), and d rho / d l_2 = (l0, l1) / |l_12|^2 at
+    // both endpoints; the line terms are undistorted
+    const T a = mc[2] / A2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { o.Jk[i][0] = l[i & 1] * a; o.Jk[i][1] = 0; o.Jk[i][2] = 0; }
+  }
 }
 
 // R3: pi(C, X) - pi(C, Proj_plane(X))  (Eq. 7)
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_plane_point(const Cam<T>& c, const T* X, const T* P, ResJ<T>& o) {
   const T* n = P;
   T w = P[3];
@@ -395,11 +418,20 @@ __device__ void res_plane_point(const Cam<T>& c, const T* X, const T* P, ResJ<T>
       o.Jg[i][1] = (e2 * g2n + cd * dot3(g2, b2));
       o.Jg[i][2] = g2n;
     }
+    if (INTR) {
+      T K1[2][3], K2[2][3];
+      project_dist_k(c, x1, K1);
+      project_dist_k(c, x2, K2);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o.Jk[i][k] = K1[i][k] - K2[i][k];
+    }
   }
 }
 
 // R4: rho(pi_l(C, L)) - rho(pi_l(C, Proj_plane(L)))  (Eq. 8)
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T* seg, ResJ<T>& o) {
   const T* n = P;
   T w = P[3];
@@ -456,10 +488,15 @@ __device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T*
 #pragma unroll
     for (int k = 0; k < 3; ++k) o.Jg[i][k] = -dot3(G2[i], dmcg[k]);
   }
+  if (INTR) {
+    const T a1 = mc1[2] / A1, a2 = mc2[2] / A2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { o.Jk[i][0] = l1[i & 1] * a1 - l2[i & 1] * a2; o.Jk[i][1] = 0; o.Jk[i][2] = 0; }
+  }
 }
 
 // R5: d x v (Eq. 6 as a 3-vector; |d| = 1)
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_vp(const T* L, const T* V, ResJ<T>& o) {
   const T* d = L;
   T dn = rsqrt_t(dot3(d, d));
@@ -485,11 +522,12 @@ __device__ void res_vp(const T* L, const T* V, ResJ<T>& o) {
     o.Jg[i][0] = g0[i]; o.Jg[i][1] = g1[i]; o.Jg[i][2] = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) o.Jc[i][k] = 0;
+    if (INTR) { o.Jk[i][0] = 0; o.Jk[i][1] = 0; o.Jk[i][2] = 0; }
   }
 }
 
 // R6: lhat . [pi_pinhole(C, X); 1], lhat = e1 x e2 scaled to |lhat_12| = 1 (Eq. 11)
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_p2l(const Cam<T>& c, const T* X, const T* seg, ResJ<T>& o) {
   T e1[3] = {seg[0], seg[1], T(1)}, e2[3] = {seg[2], seg[3], T(1)}, lh[3];
   cross3(e1, e2, lh);
@@ -507,11 +545,16 @@ __device__ void res_p2l(const Cam<T>& c, const T* X, const T* seg, ResJ<T>& o) {
     pose_row_point(p, g, o.Jc[0]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) o.Jf[0][k] = g[0] * c.R[k] + g[1] * c.R[3 + k] + g[2] * c.R[6 + k];
+    if (INTR) {
+      // pinhole pixels pp + f (u, v): d r / d f = lhat_12 . (u, v)
+      const T iz = T(1) / xc[2];
+      o.Jk[0][0] = (lh[0] * xc[0] + lh[1] * xc[1]) * iz; o.Jk[0][1] = 0; o.Jk[0][2] = 0;
+    }
   }
 }
 
 // R7: (l . [x;1]) / |l_12| with l = pi_l(C, L) (Eq. 12)
-template <class T, bool JAC>
+template <class T, bool JAC, bool INTR = false>
 __device__ void res_l2p(const Cam<T>& c, const T* L, const T* x, ResJ<T>& o) {
   T dc[3], Rm[3], mc[3], l[3];
   line_to_cam(c, L, L + 3, dc, Rm, mc);
@@ -528,6 +571,7 @@ __device__ void res_l2p(const Cam<T>& c, const T* L, const T* x, ResJ<T>& o) {
   T h0 = x[0] * in - q * l[0] * in3, h1 = x[1] * in - q * l[1] * in3, h2 = in;
   T G[3] = {h0 - c.px * h2, h1 - c.py * h2, c.f * h2};
   pose_row_line(c, dc, Rm, G, o.Jc[0]);
+  if (INTR) { o.Jk[0][0] = mc[2] * in; o.Jk[0][1] = 0; o.Jk[0][2] = 0; }   // d l_2 / d f = m_c2, d r / d l_2 = 1/|l_12|
   T u1[3], u3[3], r;
   line_frame(L, L + 3, u1, u3, r);
   T ddir[4][3], mdir[4][3];

@@ -282,14 +282,25 @@ struct SlotArgs {
   const uint8_t* fixed;
   int64_t nf, nc, npl;
   int* err;   // bit 0: two planes on one feature, bit 1: two VPs on one line
+  const int32_t* cam_k;   // refined intrinsics: per camera its intrinsics entity (else null)
+  int64_t kbase;          // A index of intrinsics entity 0
 };
 
-// distinct kept entities of a feature (cameras ascending, then its plane, then its VP)
+// intrinsics entity of residual j of a feature (-1: none)
+__device__ __forceinline__ int slot_intr(const SlotArgs& a, int32_t j) {
+  if (!a.cam_k) return -1;
+  const int c = a.cam[a.order[j]];
+  return c >= 0 ? a.cam_k[c] : -1;
+}
+
+// distinct kept entities of a feature (cameras ascending, then its plane, then its VP, then the intrinsics
+// entities of its cameras, ascending)
 __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
   const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.nf) return;
   int n = 0, prev = -1, plane = -1, vp = -1;
-  for (int32_t j = a.fres_off[f]; j < a.fres_off[f + 1]; ++j) {
+  const int32_t r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
+  for (int32_t j = r0; j < r1; ++j) {
     const int32_t i = a.order[j];
     const int c = a.cam[i];
     if (c >= 0 && a.fixed[c] != 0x3F && c != prev) { ++n; prev = c; }
@@ -301,12 +312,19 @@ __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
       if (vp >= 0 && vp != a.grp[i]) atomicOr(a.err, 2);
       vp = a.grp[i];
     }
+    // an intrinsics entity counts at the first residual that names it
+    const int kk = slot_intr(a, j);
+    if (kk >= 0) {
+      bool seen = false;
+      for (int32_t j2 = r0; j2 < j && !seen; ++j2) seen = slot_intr(a, j2) == kk;
+      n += seen ? 0 : 1;
+    }
   }
   nslot[f] = n + (plane >= 0) + (vp >= 0);
 }
 
 struct SlotFill {
-  int32_t *fslot_off, *slot_ent, *slot_feat, *feat_plane_slot, *rslot_c, *rslot_g;
+  int32_t *fslot_off, *slot_ent, *slot_feat, *feat_plane_slot, *rslot_c, *rslot_g, *rslot_k;
   uint8_t* slot_type;
 };
 
@@ -355,6 +373,31 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
   for (int32_t j = r0; j < r1; ++j) {
     const int k = a.kind[a.order[j]];
     o.rslot_g[j] = (k == R_PLANE_POINT || k == R_PLANE_LINE) ? plane_slot : (k == R_VP ? vp_slot : -1);
+  }
+  if (!a.cam_k) return;
+  // the intrinsics entities of the feature's cameras in ascending order (the slots of a feature are in entity
+  // order), then every residual's slot among them
+  const int32_t k0 = e;
+  int last = -1;
+  for (;;) {
+    int nxt = INT32_MAX;
+    for (int32_t j = r0; j < r1; ++j) {
+      const int kk = slot_intr(a, j);
+      if (kk > last && kk < nxt) nxt = kk;
+    }
+    if (nxt == INT32_MAX) break;
+    o.slot_ent[e] = (int32_t)(a.kbase + nxt);
+    o.slot_feat[e] = (int32_t)f;
+    o.slot_type[e] = ENT_INTR;
+    ++e;
+    last = nxt;
+  }
+  for (int32_t j = r0; j < r1; ++j) {
+    const int kk = slot_intr(a, j);
+    int32_t sk = -1;
+    for (int32_t q = k0; q < e && kk >= 0; ++q)
+      if (o.slot_ent[q] == (int32_t)(a.kbase + kk)) { sk = q; break; }
+    o.rslot_k[j] = sk;
   }
 }
 
@@ -464,6 +507,8 @@ __global__ void k_pair_count(const int32_t* __restrict__ fslot_off, int64_t nf, 
 struct PairGen {
   const int32_t *fslot_off, *slot_ent, *wpre, *nlow;
   const uint8_t* slot_type;
+  const int32_t* cam_k;   // refined intrinsics: per camera its entity (else null)
+  int64_t kbase;
   const int64_t *poff, *uptr;
   Bitmap bm;
   int64_t nf;
@@ -486,9 +531,16 @@ __global__ void k_pair_gen(PairGen g) {
       g.key[q] = (uint32_t)u;
       g.val[q] = (uint32_t)q;
       g.gi[q] = i;
-      // bit 31 marks a (camera slot, plane slot) pair of one feature: its direct J_cam^T w J_plane block is added
-      const bool cam_plane = i != j && g.slot_type[i] == ENT_CAM && g.slot_type[j] == ENT_PLANE;
-      g.gj[q] = (int32_t)((uint32_t)j | (cam_plane ? 0x80000000u : 0u));
+      // bits 30-31: the direct block of the pair's two entities that the feature's residuals add (camera-plane;
+      // camera and its own intrinsics entity; plane-intrinsics)
+      uint32_t code = 0;
+      if (i != j) {
+        const int ti = g.slot_type[i], tj = g.slot_type[j];
+        if (ti == ENT_CAM && tj == ENT_PLANE) code = PAIR_CP;
+        else if (ti == ENT_CAM && tj == ENT_INTR && g.cam_k && g.kbase + g.cam_k[a] == b) code = PAIR_CK;
+        else if (ti == ENT_PLANE && tj == ENT_INTR) code = PAIR_PK;
+      }
+      g.gj[q] = (int32_t)((uint32_t)j | (code << PAIR_SHIFT));
       atomicAdd(&g.ucnt[u], 1ull);
     }
   }
@@ -548,7 +600,7 @@ __global__ void k_unit_key(const int32_t* __restrict__ un_se, const int32_t* __r
     const int u = un_blk[w];
     const bool diag = pcol[up_full[u]] == up_row[u];
     const bool single = up_un[u + 1] - up_un[u] == 1;
-    const bool packable = !diag && single && n >= 1 && n <= PACK_MAX && pair_b[un_se[2 * w]] >= 0;
+    const bool packable = !diag && single && n >= 1 && n <= PACK_MAX && ((uint32_t)pair_b[un_se[2 * w]] >> PAIR_SHIFT) == 0u;
     key[w] = n > UNIT_LONG ? 0u : (packable ? 2u : 1u);
     val[w] = (uint32_t)w;
   }
@@ -655,9 +707,9 @@ __global__ void k_kind_key(const int8_t* __restrict__ kind, int64_t n, uint32_t*
   if (j < n) { key[j] = (uint32_t)kind[j]; val[j] = (uint32_t)j; }
 }
 
-__global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, uint8_t* __restrict__ t) {
+__global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, uint8_t* __restrict__ t) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a < na) t[a] = a < nc ? ENT_CAM : (a < nc + npl ? ENT_PLANE : ENT_VP);
+  if (a < na) t[a] = a < nc ? ENT_CAM : (a < nc + npl ? ENT_PLANE : (a < nc + npl + nv ? ENT_VP : ENT_INTR));
 }
 
 static ba_status read_i64(Problem& P, const int64_t* src, int64_t* dst) {
@@ -675,7 +727,25 @@ ba_status build_structure(Problem& P) {
   d.npl = (int64_t)P.h_pln.size() / 4;
   d.nv = (int64_t)P.h_vps.size() / 3;
   d.nf = d.np + d.nl;
-  d.na = d.nc + d.npl + d.nv;
+  // refined intrinsics (cam_dof 9): shared entities as set, else one per camera with the camera's values; every
+  // camera's f, k1, k2 become a copy of its entity's
+  if (P.opt.cam_dof == 9) {
+    if (!P.intr_set) {
+      P.h_intr.resize(3 * d.nc);
+      P.h_cam_k.resize(d.nc);
+      for (int64_t i = 0; i < d.nc; ++i) {
+        for (int k = 0; k < 3; ++k) P.h_intr[3 * i + k] = P.h_cam[12 * i + 7 + k];
+        P.h_cam_k[i] = (int32_t)i;
+      }
+    } else if ((int64_t)P.h_cam_k.size() != d.nc) {
+      return fail(P, BA_ERR_ARG, "ba_set_intrinsics: intr_of_cam has " + std::to_string(P.h_cam_k.size()) +
+                                     " entries for " + std::to_string(d.nc) + " cameras");
+    }
+    d.nk = (int64_t)P.h_intr.size() / 3;
+    for (int64_t i = 0; i < d.nc; ++i)
+      for (int k = 0; k < 3; ++k) P.h_cam[12 * i + 7 + k] = P.h_intr[3 * (size_t)P.h_cam_k[i] + k];
+  }
+  d.na = d.nc + d.npl + d.nv + d.nk;
   if (d.na > (int64_t)1 << 30 || d.nf > (int64_t)1 << 30) return fail(P, BA_ERR_ARG, "too many entities");
   // the pattern bitmap holds na x na bits
   const int64_t wpr = (d.na + 31) / 32;
@@ -792,7 +862,13 @@ ba_status build_structure(Problem& P) {
   int* err_d = S.get<int>(1);
   if (!err_d) return oom();
   CU(cudaMemsetAsync(err_d, 0, sizeof(int), P.stream));
-  SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d};
+  if (d.nk) {
+    P.cam_k = P.dnew<int32_t>(d.nc);
+    if (!P.cam_k) return oom();
+    CU(cudaMemcpyAsync(P.cam_k, P.h_cam_k.data(), sizeof(int32_t) * d.nc, cudaMemcpyHostToDevice, P.stream));
+  }
+  const int64_t kbase = d.nc + d.npl + d.nv;
+  SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d, P.cam_k, kbase};
   int64_t* soff = S.get<int64_t>(nf + 1);
   if (!soff) return oom();
   k_slot_count<<<grid_of(nf, NT), NT, 0, P.stream>>>(sa, cnt64);
@@ -811,7 +887,11 @@ ba_status build_structure(Problem& P) {
   P.feat_plane_slot = P.dnew<int32_t>(nf);
   P.rslot_c = P.dnew<int32_t>(nr); P.rslot_g = P.dnew<int32_t>(nr);
   if (!P.fslot_off || !P.slot_ent || !P.slot_feat || !P.slot_type || !P.feat_plane_slot || !P.rslot_c || !P.rslot_g) return oom();
-  SlotFill sf{P.fslot_off, P.slot_ent, P.slot_feat, P.feat_plane_slot, P.rslot_c, P.rslot_g, P.slot_type};
+  if (d.nk) {
+    P.rslot_k = P.dnew<int32_t>(nr);
+    if (!P.rslot_k) return oom();
+  }
+  SlotFill sf{P.fslot_off, P.slot_ent, P.slot_feat, P.feat_plane_slot, P.rslot_c, P.rslot_g, P.rslot_k, P.slot_type};
   k_slot_fill<<<grid_of(nf + 1, NT), NT, 0, P.stream>>>(sa, soff, sf);
   {
     int64_t v;
@@ -868,7 +948,7 @@ ba_status build_structure(Problem& P) {
   unsigned long long* ucnt = S.get<unsigned long long>(nbu + 1);
   if (!pkey || !pval || !pk2 || !pv2 || !gi || !gj || !ucnt) return oom();
   CU(cudaMemsetAsync(ucnt, 0, sizeof(unsigned long long) * (nbu + 1), P.stream));
-  PairGen pg{P.fslot_off, P.slot_ent, wpre, nlow, P.slot_type, poff, uptr, bm, nf, pkey, pval, gi, gj, ucnt};
+  PairGen pg{P.fslot_off, P.slot_ent, wpre, nlow, P.slot_type, P.cam_k, kbase, poff, uptr, bm, nf, pkey, pval, gi, gj, ucnt};
   if (nf) k_pair_gen<<<grid_of(nf, NT), NT, 0, P.stream>>>(pg);
   if ((s = radix_sort(P, S, pkey, pval, pk2, pv2, npair, bits_for(nbu)))) return s;
   P.pair_a = P.dnew<int32_t>(npair); P.pair_b = P.dnew<int32_t>(npair);
@@ -966,7 +1046,7 @@ ba_status build_structure(Problem& P) {
   }
   P.ent_type = P.dnew<uint8_t>(na);
   if (!P.ent_type) return oom();
-  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, P.ent_type);
+  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, d.nv, P.ent_type);
 
   // ---- parameters
 #define UP(dst, src) if ((s = upload(P, dst, src)) != BA_OK) return s
@@ -974,6 +1054,7 @@ ba_status build_structure(Problem& P) {
   for (int k = 0; k < 2; ++k) {
     auto& S_ = P.ps[k];
     UP(S_.cam, P.h_cam); UP(S_.pts, P.h_pts); UP(S_.lin, P.h_lin); UP(S_.pln, P.h_pln); UP(S_.vps, P.h_vps);
+    if (d.nk) UP(S_.intr, P.h_intr);
     S_.camD = P.dnew<double>(d.nc * CAM_STRIDE);
     S_.grpD = P.dnew<double>((d.npl + d.nv) * GRP_STRIDE);
     if (!S_.camD || !S_.grpD) return oom();

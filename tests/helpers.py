@@ -38,6 +38,8 @@ def padded_to_oracle_index(scene, lay):
         idx += list(range(6 * (nc + g), 6 * (nc + g) + 3))
     for v in range(nv):
         idx += list(range(6 * (nc + npl + v), 6 * (nc + npl + v) + 2))
+    for k in range(getattr(lay, "nk", 0)):
+        idx += list(range(6 * (nc + npl + nv + k), 6 * (nc + npl + nv + k) + 3))
     return np.array(idx, np.int64)
 
 
@@ -49,7 +51,8 @@ def oracle_delta_split(delta, lay):
     vp = delta[lay.vp_col[:, None] + np.arange(2)] if lay.nv else np.zeros((0, 2))
     point = delta[lay.point_col[:, None] + np.arange(3)] if lay.np_ else np.zeros((0, 3))
     line = delta[lay.line_col[:, None] + np.arange(4)] if lay.nl else np.zeros((0, 4))
-    return dict(cam=cam, plane=plane, vp=vp, point=point, line=line)
+    intr = delta[lay.intr_col[:, None] + np.arange(3)] if lay.nk else np.zeros((0, 3))
+    return dict(cam=cam, plane=plane, vp=vp, point=point, line=line, intr=intr)
 
 
 def oracle_setup(scene):
