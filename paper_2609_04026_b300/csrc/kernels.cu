@@ -2881,7 +2881,7 @@ __device__ void candidate_item(const CandArgs& a, int64_t i) {
 
 __global__ void k_candidate(CandArgs a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < a.nc + a.npl + a.nv + a.np + a.nl) candidate_item(a, i);
+  if (i < a.nc + a.npl + a.nv + a.np + a.nl + a.nk) candidate_item(a, i);
 }
 
 // ---- ln(1 + x) for the FP64 cost, table-driven after P. T. P. Tang, "Table-driven implementation of the
