@@ -202,6 +202,9 @@ def main():
     ap.add_argument("--windows", type=int, default=256)
     ap.add_argument("--no-fp64-ttc", action="store_true", help="skip the FP64 block-Jacobi time-to-converge")
     ap.add_argument("--no-mixed-error", action="store_true", help="skip the per-result mixed-vs-FP64 error")
+    ap.add_argument("--no-intr", action="store_true", help="skip the refined-intrinsics (cam_dof 9) workload")
+    ap.add_argument("--intr-models", type=int, default=20,
+                    help="camera models sharing refined intrinsics in that workload (0 = one per camera)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -433,6 +436,42 @@ def main():
                            "device time of the second launch of the kept graph (10 iterations each, every window "
                            "continuing from the first launch's state)"}
 
+    # ---------------- refined intrinsics (cam_dof 9, Section 3.1 K_c(i)) at the same scale: the scene generated
+    # with every camera belonging to one of --intr-models camera models (shared f, k1, k2 in the ground truth),
+    # the models' initial intrinsics perturbed by 1%; LM iterations per second of the step with the intrinsics
+    # entities in the reduced system, and how far the models' f moved towards the ground truth
+    intr = None
+    if not args.no_intr:
+        si = make_scene(scfg(args.config, seed=scfg(args.config).seed + rank, intr_refine=True,
+                             intr_groups=args.intr_models, intr_noise=0.01))
+        q = B.ba_create(B.ba_default_options(precision=prec, cam_dof=9, cuda_stream=stream.cuda_stream))
+        B.load_scene(q, si)
+        for _ in range(3):
+            B.ba_lm_step(q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ti = [B.ba_lm_step(q) for _ in range(5)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_i = e0.elapsed_time(e1)
+        nk = B.ba_intrinsics_count(q)
+        na_i, nbf_i = B.ba_reduced_size(q)
+        fk = B.ba_get_intrinsics(q, len(si["cams"]["q"]))
+        B.ba_destroy(q)
+        gt = si["gt"]["cams"]["intr"]
+        intr = {"lm_iters_per_s": round(5 / (ms_i / 1e3), 3), "ms_per_step": round(ms_i / 5, 3),
+                "intrinsics_entities": nk, "block_rows": na_i, "stored_blocks": nbf_i,
+                "pcg_iters": [r.pcg_iters for r in ti],
+                "kernels_ms": {k: round(float(np.mean([r.as_dict()["ms_kernel"][k] for r in ti])), 4)
+                               for k in ti[0].KERNELS},
+                "f_rel_error": {"initial": float(np.abs(si["cams"]["intr"][:, 0] - gt[:, 0]).max() / gt[:, 0].min()),
+                                "after_8_steps": float(np.abs(fk[:, 0] - gt[:, 0]).max() / gt[:, 0].min())},
+                "note": f"the {args.config} scene with {args.intr_models or 'per-camera'} camera models (seeded), "
+                        "intrinsics perturbed by 1%, cam_dof 9, same precision; 5 steps timed after 3 warm-up "
+                        "(full 6 x 6 storage of S: the typed storage does not take intrinsics columns)"}
+        del si
+
     # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
     # at the initial damping (the FP64 path itself is checked against the oracle at 2000 cameras by
     # tests/test_gpu_scale.py)
@@ -492,7 +531,7 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "time_to_converge": ttc, "time_to_converge_fp64_block_jacobi": ttc64,
                "time_to_equal_cost": equal,
-               "batched_windows": batched, "learned_precond": learned,
+               "batched_windows": batched, "refined_intrinsics": intr, "learned_precond": learned,
                "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
                "stage_rooflines": stages, "measured_fma_tflops": {"fp32": round(peak32, 2), "fp64": round(peak64, 3)},
                "mixed_error": mixed_err,
