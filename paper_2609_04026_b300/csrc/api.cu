@@ -414,6 +414,8 @@ static ba_status plan_pcg_typed(ba_problem* p, const TypedPlan& tp) {
     for (int k = 0; k < 3; ++k) gvi[3 * g + k] = (int32_t)(6 * (nc + g) + k);
   for (int64_t v = 0; v < d.nv; ++v)
     for (int k = 0; k < 2; ++k) gvi[3 * d.npl + 2 * v + k] = (int32_t)(6 * (nc + d.npl + v) + k);
+  for (int64_t q = 0; q < d.nk; ++q)
+    for (int k = 0; k < 3; ++k) gvi[3 * d.npl + 2 * d.nv + 3 * q + k] = (int32_t)(6 * (nc + d.npl + d.nv + q) + k);
   // shared memory: the fixed part (stage, group accumulators and operands) and one segment of 6 sums per
   // (warp, camera row it touches)
   const size_t seg = (mx ? sizeof(float) * 2 : sizeof(double)) * 6 * ((size_t)maxrows + 16);
@@ -458,7 +460,7 @@ static ba_status freeze(ba_problem* p) {
   p->frozen = true;
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
-  p->gv = (int)(3 * d.npl + 2 * d.nv);
+  p->gv = (int)(3 * d.npl + 2 * d.nv + 3 * d.nk);
   auto A = [&](void*& dst, size_t bytes) -> bool {
     dst = p->dalloc(bytes);
     return dst != nullptr;
@@ -533,8 +535,7 @@ static ba_status ensure_sstore(ba_problem* p, bool for_batch) {
   if (p->Sval) return BA_OK;
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
-  // refined intrinsics keep the full storage: the typed storage knows camera, plane and VP columns only
-  p->typed = !for_batch && d.nc > 0 && d.nk == 0 && 3 * d.npl + 2 * d.nv <= GV_MAX;
+  p->typed = !for_batch && d.nc > 0 && 3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
   ba_status s;
   if (p->typed) {
     TypedPlan tplan;
@@ -875,7 +876,10 @@ extern "C" ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, i
     }
   }
   SView hv;
-  if (p->typed) { hv.sel = hsel.data(); hv.col = pc.data(); hv.nc = d.nc; hv.npl = d.npl; hv.gg_val0 = p->gg_val0; }
+  if (p->typed) {
+    hv.sel = hsel.data(); hv.col = pc.data(); hv.nc = d.nc; hv.npl = d.npl; hv.gg_val0 = p->gg_val0;
+    hv.kb = d.nc + d.npl + d.nv;
+  }
   int64_t o = 0;
   if (row_ptr) row_ptr[0] = 0;
   for (int64_t a = 0; a < d.na; ++a) {

@@ -83,12 +83,13 @@ constexpr int PCG_FLAG_TIMEOUT = 8;   // DevScalars::flags bit: a bounded device
 // each of the three runs is padded to whole chunks of 32 blocks.  The camera-group blocks are stored only
 // there: a group row's camera part is the transpose, which the PCG forms from the camera rows (a scatter
 // into per-warp accumulators of the group values).  A group row keeps its few group-group blocks (6 x 6).
-constexpr int TY_CC = 0, TY_CP = 1, TY_CV = 2;
+constexpr int TY_CC = 0, TY_CP = 1, TY_CV = 2, TY_CK = 3;   // camera-intrinsics blocks: a fourth run (6 x 3)
 constexpr int TCHUNK = 32;             // blocks per chunk (one per lane)
-constexpr int GV_MAX = 1400;           // group values (3 per plane, 2 per VP) the typed storage supports
+constexpr int GV_MAX = 1400;           // group values (3 per plane, 2 per VP, 3 per intrinsics entity) the typed
+                                       // storage supports
 constexpr int GV_PAD = 4;              // dummy group values behind the real ones (targets of padding blocks)
 constexpr uint32_t SEL_MIRROR = 0x80000000u;   // sel[] flag: only the transposed copy of this block is stored
-__host__ __device__ __forceinline__ int ty_vals(int ty) { return ty == TY_CC ? 36 : (ty == TY_CP ? 18 : 12); }
+__host__ __device__ __forceinline__ int ty_vals(int ty) { return ty == TY_CC ? 36 : (ty == TY_CV ? 12 : 18); }
 
 // Where the blocks of the reduced system live, addressed by their position q in the full padded block-CSR
 // pattern (row_ptr / col).  Full storage (sel == null, batched windows): block q at 36 q, row-major 6 x 6.
@@ -98,10 +99,13 @@ struct SView {
   const int32_t* sel = nullptr;
   const int32_t* col = nullptr;
   int64_t nc = 0, npl = 0, gg_val0 = 0;
+  int64_t kb = 0;   // first intrinsics entity (nc + npl + nv)
 };
+// real width of a group entity's block: plane 3, VP 2, intrinsics 3
+__host__ __device__ __forceinline__ int sview_gw(const SView& v, int64_t g) { return (g < v.nc + v.npl || g >= v.kb) ? 3 : 2; }
 // width of the stored copy at typed offset o of a block in column c (the copy itself, not a mirror)
 __host__ __device__ __forceinline__ int sview_width(const SView& v, int64_t o, int64_t c) {
-  return (o < v.gg_val0 && c >= v.nc) ? (c < v.nc + v.npl ? 3 : 2) : 6;
+  return (o < v.gg_val0 && c >= v.nc) ? sview_gw(v, c) : 6;
 }
 // the padded 6 x 6 block at position q of row r (zeros beyond a narrow block's width; the transpose of the
 // stored copy when only the mirror is stored; all zeros for a padding position)
@@ -120,7 +124,7 @@ __host__ __device__ __forceinline__ void sview_load(const SView& v, const T* Sva
     for (int i = 0; i < 6; ++i)
       for (int j = 0; j < w; ++j) out[i * 6 + j] = (double)Sval[o + i * w + j];
   } else {
-    const int w = r < v.nc + v.npl ? 3 : 2;   // the stored copy is camera row col[q]'s block of group r
+    const int w = sview_gw(v, r);   // the stored copy is camera row col[q]'s block of group r
     for (int i = 0; i < w; ++i)
       for (int j = 0; j < 6; ++j) out[i * 6 + j] = (double)Sval[o + j * w + i];
   }

@@ -2040,7 +2040,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
 // ============================================================================
 template <class T>
 struct PcgTypedArgs {
-  int64_t na, nc, npl;
+  int64_t na, nc, npl, nv;
   int gv;                         // group values: 3 per plane, 2 per VP
   const int32_t *tcol, *row_chunk0, *gg_ptr, *gg_col, *cta_gs, *gv_idx;
   const int4* tchunk;             // per chunk {value offset, first block, camera row, type}
@@ -2203,7 +2203,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   };
   // group row g's group values: first value offset and count
   auto gval = [&](int g, int& k0, int& nd) {
-    if (g < a.npl) { k0 = 3 * g; nd = 3; } else { k0 = 3 * (int)a.npl + 2 * (g - (int)a.npl); nd = 2; }
+    if (g < a.npl) { k0 = 3 * g; nd = 3; }
+    else if (g < a.npl + a.nv) { k0 = 3 * (int)a.npl + 2 * (g - (int)a.npl); nd = 2; }
+    else { k0 = 3 * (int)a.npl + 2 * (int)a.nv + 3 * (g - (int)(a.npl + a.nv)); nd = 3; }   // intrinsics
   };
 
   auto issue = [&](int k) {
@@ -2287,7 +2289,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
         load_block36(buf + lane * 36, B);
 #pragma unroll
         for (int j = 0; j < 6; ++j) uc[j] = un[j];
-      } else if (cd.w == TY_CP) {
+      } else if (cd.w != TY_CV) {   // camera-plane or camera-intrinsics: 6 x 3
         T b18[18];
         load_vals<18>(buf + lane * 18, b18);
 #pragma unroll
@@ -2318,7 +2320,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
           for (int j = 0; j < 6; ++j) ds_madd(acc[i], B[i * 6 + j], uc[j]);
       } else {
         // camera-group block (6 x nd): the row part with the group's u, the transpose into the group values
-        const int nd = cd.w == TY_CP ? 3 : 2;
+        const int nd = cd.w == TY_CV ? 2 : 3;
         XV<T> xg[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -3253,7 +3255,7 @@ static void launch_pcg_typed(Problem& P) {
   const Dims& d = P.d;
   constexpr int NT = TypedCfg<T>::NT, NB = TypedCfg<T>::NBUF;
   PcgTypedArgs<T> a;
-  a.na = d.na; a.nc = d.nc; a.npl = d.npl; a.gv = P.gv;
+  a.na = d.na; a.nc = d.nc; a.npl = d.npl; a.nv = d.nv; a.gv = P.gv;
   a.tcol = P.tcol; a.row_chunk0 = P.row_chunk0; a.gg_ptr = P.gg_ptr; a.gg_col = P.gg_col; a.cta_gs = P.cta_gs;
   a.gv_idx = P.gv_idx; a.tchunk = P.tchunk; a.cta_part = reinterpret_cast<const int4*>(P.cta_part);
   a.carry = P.pcg_carry; a.part_g = P.part_g;

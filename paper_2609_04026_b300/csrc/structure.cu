@@ -1069,24 +1069,25 @@ ba_status build_structure(Problem& P) {
 
 // ---------------------------------------------------------------------------
 // typed storage of the reduced system (see TY_CC in ba_internal.cuh)
-// per row: its camera, plane and VP columns (columns of a row are in entity order: cameras, planes, VPs)
-__global__ void k_typed_count(int64_t na, int64_t nc, int64_t npl, const int32_t* __restrict__ row_ptr,
+// per row: its camera, plane, VP and intrinsics columns (columns of a row are in entity order: cameras,
+// planes, VPs, intrinsics entities)
+__global__ void k_typed_count(int64_t na, int64_t nc, int64_t npl, int64_t kb, const int32_t* __restrict__ row_ptr,
                               const int32_t* __restrict__ row_len, const int32_t* __restrict__ col,
                               int32_t* __restrict__ cnt) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= na) return;
-  int32_t n0 = 0, n1 = 0, n2 = 0;
+  int32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
   for (int32_t q = row_ptr[r]; q < row_ptr[r] + row_len[r]; ++q) {
     const int32_t c = col[q];
-    if (c < nc) ++n0; else if (c < nc + npl) ++n1; else ++n2;
+    if (c < nc) ++n0; else if (c < nc + npl) ++n1; else if (c < kb) ++n2; else ++n3;
   }
-  cnt[3 * r] = n0; cnt[3 * r + 1] = n1; cnt[3 * r + 2] = n2;
+  cnt[4 * r] = n0; cnt[4 * r + 1] = n1; cnt[4 * r + 2] = n2; cnt[4 * r + 3] = n3;
 }
 
 struct TypedFill {
-  int64_t na, nc, npl, gv;
+  int64_t na, nc, npl, kb, gv;
   const int32_t *row_ptr, *prow_end, *row_len, *col, *cnt;
-  const int32_t* rinfo;   // camera row: value and block offsets of its CC, CP, CV runs (6); group row: GG block 0
+  const int32_t* rinfo;   // camera row: value and block offsets of its CC, CP, CV, CK runs (8); group row: GG block 0
   int64_t gg_val0;
   int32_t *sel, *tcol, *gg_col;
 };
@@ -1095,8 +1096,9 @@ __global__ void k_typed_fill(TypedFill a) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= a.na) return;
   const int32_t q0 = a.row_ptr[r], len = a.row_len[r];
-  const int32_t* ri = a.rinfo + 6 * r;
-  const int32_t ncc = a.cnt[3 * r], ncp = a.cnt[3 * r + 1], ncv = a.cnt[3 * r + 2];
+  const int32_t* ri = a.rinfo + 8 * r;
+  const int32_t ncc = a.cnt[4 * r], ncp = a.cnt[4 * r + 1], ncv = a.cnt[4 * r + 2], nck = a.cnt[4 * r + 3];
+  const int32_t nv = (int32_t)(a.kb - a.nc - a.npl);
   if (r < a.nc) {
     for (int32_t k = 0; k < len; ++k) {
       const int32_t c = a.col[q0 + k];
@@ -1107,17 +1109,22 @@ __global__ void k_typed_fill(TypedFill a) {
         const int32_t kk = k - ncc;
         a.sel[q0 + k] = ri[2] + 18 * kk;
         a.tcol[ri[3] + kk] = 3 * (c - (int32_t)a.nc);
-      } else {
+      } else if (c < a.kb) {
         const int32_t kk = k - ncc - ncp;
         a.sel[q0 + k] = ri[4] + 12 * kk;
         a.tcol[ri[5] + kk] = 3 * (int32_t)a.npl + 2 * (c - (int32_t)(a.nc + a.npl));
+      } else {
+        const int32_t kk = k - ncc - ncp - ncv;
+        a.sel[q0 + k] = ri[6] + 18 * kk;
+        a.tcol[ri[7] + kk] = 3 * (int32_t)a.npl + 2 * nv + 3 * (c - (int32_t)a.kb);
       }
     }
-    // padding blocks of the three runs (zero values): a camera-camera pad gathers the row's own u, a
+    // padding blocks of the four runs (zero values): a camera-camera pad gathers the row's own u, a
     // camera-group pad points at the dummy group values
     for (int32_t k = ncc; k < (ncc + TCHUNK - 1) / TCHUNK * TCHUNK; ++k) a.tcol[ri[1] + k] = (int32_t)r;
     for (int32_t k = ncp; k < (ncp + TCHUNK - 1) / TCHUNK * TCHUNK; ++k) a.tcol[ri[3] + k] = (int32_t)a.gv;
     for (int32_t k = ncv; k < (ncv + TCHUNK - 1) / TCHUNK * TCHUNK; ++k) a.tcol[ri[5] + k] = (int32_t)a.gv;
+    for (int32_t k = nck; k < (nck + TCHUNK - 1) / TCHUNK * TCHUNK; ++k) a.tcol[ri[7] + k] = (int32_t)a.gv;
   } else {
     const int32_t g0 = ri[0];
     for (int32_t k = 0; k < len; ++k) {
@@ -1134,9 +1141,10 @@ __global__ void k_typed_fill(TypedFill a) {
           if (a.col[mid] < r) lo = mid + 1; else hi = mid;
         }
         const int32_t kc = lo - a.row_ptr[c];
-        const int32_t* rc = a.rinfo + 6 * (int64_t)c;
-        const int32_t cc = a.cnt[3 * (int64_t)c], cp = a.cnt[3 * (int64_t)c + 1];
-        const int32_t o = r < a.nc + a.npl ? rc[2] + 18 * (kc - cc) : rc[4] + 12 * (kc - cc - cp);
+        const int32_t* rc = a.rinfo + 8 * (int64_t)c;
+        const int32_t cc = a.cnt[4 * (int64_t)c], cp = a.cnt[4 * (int64_t)c + 1], cv = a.cnt[4 * (int64_t)c + 2];
+        const int32_t o = r < a.nc + a.npl ? rc[2] + 18 * (kc - cc)
+                          : (r < a.kb ? rc[4] + 12 * (kc - cc - cp) : rc[6] + 18 * (kc - cc - cp - cv));
         a.sel[q0 + k] = (int32_t)((uint32_t)o | SEL_MIRROR);
       }
     }
@@ -1152,6 +1160,7 @@ SView sview_of(const Problem& P) {
     v.nc = P.d.nc;
     v.npl = P.d.npl;
     v.gg_val0 = P.gg_val0;
+    v.kb = P.d.nc + P.d.npl + P.d.nv;
   }
   return v;
 }
@@ -1161,25 +1170,26 @@ ba_status build_typed_storage(Problem& P, TypedPlan& plan) {
   const int64_t na = d.na, nc = d.nc;
   constexpr int NT = 128;
   auto oom = [&]() { return fail(P, BA_ERR_OOM, "device allocation failed"); };
-  int32_t* cnt_d = P.dnew<int32_t>(3 * na);
+  const int64_t kb = nc + d.npl + d.nv;
+  int32_t* cnt_d = P.dnew<int32_t>(4 * na);
   if (!cnt_d) return oom();
-  k_typed_count<<<grid_of(na, NT), NT, 0, P.stream>>>(na, nc, d.npl, P.row_ptr, P.row_len, P.col, cnt_d);
-  std::vector<int32_t> cnt(3 * na);
+  k_typed_count<<<grid_of(na, NT), NT, 0, P.stream>>>(na, nc, d.npl, kb, P.row_ptr, P.row_len, P.col, cnt_d);
+  std::vector<int32_t> cnt(4 * na);
   CU(cudaMemcpyAsync(cnt.data(), cnt_d, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, P.stream));
   CU(cudaStreamSynchronize(P.stream));
-  // camera rows: three runs of whole chunks; group rows: their group-group blocks, unpadded
-  std::vector<int32_t> rinfo(6 * na, 0);
+  // camera rows: four runs of whole chunks; group rows: their group-group blocks, unpadded
+  std::vector<int32_t> rinfo(8 * na, 0);
   plan.row_chunk0.assign(nc + 1, 0);
   plan.chunks.clear();
   plan.chunk_w.clear();
   int64_t val = 0, blk = 0;
-  const int wt[3] = {36, 40, 28};   // products per block (and the scatter of a camera-group block)
+  const int wt[4] = {36, 40, 28, 40};   // products per block (and the scatter of a camera-group block)
   for (int64_t r = 0; r < nc; ++r) {
-    for (int t = 0; t < 3; ++t) {
-      const int64_t n = cnt[3 * r + t];
+    for (int t = 0; t < 4; ++t) {
+      const int64_t n = cnt[4 * r + t];
       const int64_t nch = (n + TCHUNK - 1) / TCHUNK;
-      rinfo[6 * r + 2 * t] = (int32_t)val;
-      rinfo[6 * r + 2 * t + 1] = (int32_t)blk;
+      rinfo[8 * r + 2 * t] = (int32_t)val;
+      rinfo[8 * r + 2 * t + 1] = (int32_t)blk;
       for (int64_t k = 0; k < nch; ++k) {
         plan.chunks.push_back(make_int4((int32_t)(val + k * TCHUNK * ty_vals(t)), (int32_t)(blk + k * TCHUNK), (int32_t)r, t));
         plan.chunk_w.push_back(wt[t] + (t == 0 && k == 0 ? 8 : 0));
@@ -1194,8 +1204,8 @@ ba_status build_typed_storage(Problem& P, TypedPlan& plan) {
   std::vector<int32_t> gg_ptr(ng + 1, 0);
   for (int64_t g = 0; g < ng; ++g) {
     const int64_t r = nc + g;
-    rinfo[6 * r] = gg_ptr[g];
-    gg_ptr[g + 1] = gg_ptr[g] + cnt[3 * r + 1] + cnt[3 * r + 2];
+    rinfo[8 * r] = gg_ptr[g];
+    gg_ptr[g + 1] = gg_ptr[g] + cnt[4 * r + 1] + cnt[4 * r + 2] + cnt[4 * r + 3];
   }
   P.gg_val0 = val;
   P.tvals = val + 36 * (int64_t)gg_ptr[ng];
@@ -1204,14 +1214,14 @@ ba_status build_typed_storage(Problem& P, TypedPlan& plan) {
   P.tcol = P.dnew<int32_t>(std::max<int64_t>(blk, 1));
   P.gg_ptr = P.dnew<int32_t>(ng + 1);
   P.gg_col = P.dnew<int32_t>(std::max<int32_t>(gg_ptr[ng], 1));
-  int32_t* rinfo_d = P.dnew<int32_t>(6 * na);
+  int32_t* rinfo_d = P.dnew<int32_t>(8 * na);
   int32_t* pend_d = P.dnew<int32_t>(na);
   if (!P.sel || !P.tcol || !P.gg_ptr || !P.gg_col || !rinfo_d || !pend_d) return oom();
   CU(cudaMemcpyAsync(rinfo_d, rinfo.data(), sizeof(int32_t) * rinfo.size(), cudaMemcpyHostToDevice, P.stream));
   CU(cudaMemcpyAsync(P.gg_ptr, gg_ptr.data(), sizeof(int32_t) * gg_ptr.size(), cudaMemcpyHostToDevice, P.stream));
   CU(cudaMemcpyAsync(pend_d, P.h_prow_ptr.data() + 1, sizeof(int32_t) * na, cudaMemcpyHostToDevice, P.stream));
-  TypedFill f{na, nc, d.npl, 3 * d.npl + 2 * d.nv, P.row_ptr, pend_d, P.row_len, P.col, cnt_d, rinfo_d, P.gg_val0,
-              P.sel, P.tcol, P.gg_col};
+  TypedFill f{na, nc, d.npl, kb, 3 * d.npl + 2 * d.nv + 3 * d.nk, P.row_ptr, pend_d, P.row_len, P.col, cnt_d, rinfo_d,
+              P.gg_val0, P.sel, P.tcol, P.gg_col};
   k_typed_fill<<<grid_of(na, NT), NT, 0, P.stream>>>(f);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(P.stream));
