@@ -469,7 +469,7 @@ def main():
                                 "after_8_steps": float(np.abs(fk[:, 0] - gt[:, 0]).max() / gt[:, 0].min())},
                 "note": f"the {args.config} scene with {args.intr_models or 'per-camera'} camera models (seeded), "
                         "intrinsics perturbed by 1%, cam_dof 9, same precision; 5 steps timed after 3 warm-up "
-                        "(full 6 x 6 storage of S: the typed storage does not take intrinsics columns)"}
+                        "(the typed storage of S when the group and intrinsics values fit, else the full 6 x 6)"}
         del si
 
     # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
