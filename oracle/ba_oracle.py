@@ -41,13 +41,17 @@ from torch.func import jacfwd, vmap
 torch.set_default_dtype(torch.float64)
 DT = torch.float64
 
-KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p")
+KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d")
 # residual dimension, feature type, group type per kind
-RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1}
+RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1,
+        "plane_point3d": 1, "plane_line3d": 2}
 FEAT = {"point": "point", "line": "line", "plane_point": "point", "plane_line": "line",
-        "vp": "line", "p2l": "point", "l2p": "line"}
-GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp"}
-HAS_CAM = {k: k != "vp" for k in KINDS}
+        "vp": "line", "p2l": "point", "l2p": "line", "plane_point3d": "point", "plane_line3d": "line"}
+GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp", "plane_point3d": "plane",
+         "plane_line3d": "plane"}
+HAS_CAM = {k: k not in ("vp", "plane_point3d", "plane_line3d") for k in KINDS}
+# kinds outside the pixel cost E_px: the angular VP term, and the direct 3D group distances
+NON_PIXEL = ("vp", "plane_point3d", "plane_line3d")
 FDOF = {"point": 3, "line": 4}
 GDOF = {"plane": 3, "vp": 2}
 CDOF = 6
@@ -63,6 +67,8 @@ class Options:
     w_vp: float = 5e3
     w_rel: float = 5e3        # inter-group relations (angular, like the VP term)
     cauchy_rel: float = 0.2
+    w_group3d: float = 1.0    # the direct 3D group distances (Section 3.2's alternative; Table 5 weighs it)
+    cauchy_3d: float = 1.0
     cauchy_px: float = 1.0
     cauchy_vp: float = 0.2
     lambda0: float = 1e-4
@@ -77,9 +83,11 @@ class Options:
     def weight(self, kind):
         return {"point": self.w_point, "line": self.w_line, "plane_point": self.w_group,
                 "plane_line": self.w_group, "vp": self.w_vp, "p2l": self.w_wire,
-                "l2p": self.w_wire}[kind]
+                "l2p": self.w_wire, "plane_point3d": self.w_group3d, "plane_line3d": self.w_group3d}[kind]
 
     def scale(self, kind):
+        if kind in ("plane_point3d", "plane_line3d"):
+            return self.cauchy_3d
         return self.cauchy_vp if kind == "vp" else self.cauchy_px
 
 
@@ -333,8 +341,23 @@ def res_l2p(dc, df, dg, cam, feat, grp, meas):              # Eq. 12
     return ((l[0] * meas[0] + l[1] * meas[1] + l[2]) / n12)[None], n12 > 1e-12
 
 
+def res_plane_point3d(dc, df, dg, cam, feat, grp, meas):    # Section 3.2: the direct point-to-plane distance
+    X = feat[:3] + df
+    P = plane_plus(grp, dg)
+    return ((P[:3] * X).sum(-1) + P[3])[None], torch.ones((), dtype=torch.bool)
+
+
+def res_plane_line3d(dc, df, dg, cam, feat, grp, meas):     # the same for a line: its direction's normal component
+    L = line_plus(feat, df)                                  # and the distance of its foot point d x m (|d| = 1)
+    P = plane_plus(grp, dg)
+    n = P[:3]
+    foot = torch.linalg.cross(L[:3], L[3:6])
+    return torch.stack([(n * L[:3]).sum(-1), (n * foot).sum(-1) + P[3]]), torch.ones((), dtype=torch.bool)
+
+
 RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
-          "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p}
+          "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p,
+          "plane_point3d": res_plane_point3d, "plane_line3d": res_plane_line3d}
 
 
 # ===========================================================================
@@ -503,11 +526,12 @@ def residuals(state, obs, kind, with_jac=False, chunk=200_000, with_intr=False):
 
 
 def cost(state, obs, opt: Options):
-    """(E, E_px): E = 1/2 sum w a^2 ln(1 + |r|^2/a^2); E_px omits the VP (angular) terms."""
+    """(E, E_px): E = 1/2 sum w a^2 ln(1 + |r|^2/a^2); E_px omits the VP (angular) terms and the direct 3D
+    group distances (not pixel terms)."""
     E = 0.0
     Epx = 0.0
     for k in KINDS:
-        if len(obs[k]["feat"]) == 0:
+        if k not in obs or len(obs[k]["feat"]) == 0:
             continue
         r, v = residuals(state, obs, k)
         a = opt.scale(k)
@@ -516,7 +540,7 @@ def cost(state, obs, opt: Options):
         e = torch.where(v, e, torch.zeros_like(e))
         tot = float(e.sum())
         E += tot
-        if k != "vp":
+        if k not in NON_PIXEL:
             Epx += tot
     rel = obs.get("relations")
     if rel is not None and len(rel["a"]):
@@ -575,8 +599,8 @@ def linearize(state, obs, opt: Options, lay: Layout):
     rows, cols, vals, rt = [], [], [], []
     row0 = 0
     for k in KINDS:
-        o = obs[k]
-        n = len(o["feat"])
+        o = obs.get(k)
+        n = len(o["feat"]) if o is not None else 0
         if n == 0:
             continue
         r, v, Jc, Jf, Jg, *Jk = residuals(state, obs, k, with_jac=True, with_intr=lay.nk > 0)

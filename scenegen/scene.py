@@ -29,6 +29,8 @@ Observation kinds (one record per residual):
   vp         (-1,  line,  vp,    no meas)                             Eq. 6
   p2l        (cam, point, line id of partner, meas 4 partner segment) Eq. 11
   l2p        (cam, line,  point id of partner, meas 2 undistorted pt) Eq. 12
+  plane_point3d (-1, point, plane, no meas)  direct 3D distance (Section 3.2's alternative, Table 5)
+  plane_line3d  (-1, line,  plane, no meas)  direct 3D distances of a line (direction, foot point)
 """
 from __future__ import annotations
 
@@ -40,8 +42,9 @@ import numpy as np
 IMG_W, IMG_H = 800.0, 600.0
 HALF = 3.0
 
-KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p")
-MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2}
+KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d")
+MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2,
+            "plane_point3d": 0, "plane_line3d": 0}
 
 
 @dataclasses.dataclass
@@ -75,6 +78,10 @@ class SceneConfig:
     intr_refine: bool = False
     intr_groups: int = 0
     intr_noise: float = 0.0
+    # form of the positional group constraints: "2d" the group-induced reprojection residuals (Eq. 7, Eq. 8),
+    # "3d" the direct 3D distances to the plane instead (the alternative of Section 3.2, compared in Table 5),
+    # "both" all of them; the observations are the same draws in every form
+    group_form: str = "2d"
     seed: int = 1
 
 
@@ -420,6 +427,21 @@ def make_scene(cfg: SceneConfig) -> dict:
                               meas=np.zeros((sel.sum(), 0)))
     sel = l_plane[lf] >= 0
     obs["plane_line"] = dict(cam=lc[sel], feat=lf[sel], other=l_plane[lf[sel]].astype(np.int32), meas=lm[sel])
+    # direct 3D group distances: one record per observed feature on a plane (no camera, no measurement)
+    pp3 = np.unique(pf[p_plane[pf] >= 0]).astype(np.int32)
+    ll3 = np.unique(lf[l_plane[lf] >= 0]).astype(np.int32)
+    obs["plane_point3d"] = dict(cam=neg(len(pp3)), feat=pp3, other=p_plane[pp3].astype(np.int32),
+                                meas=np.zeros((len(pp3), 0)))
+    obs["plane_line3d"] = dict(cam=neg(len(ll3)), feat=ll3, other=l_plane[ll3].astype(np.int32),
+                               meas=np.zeros((len(ll3), 0)))
+    if cfg.group_form == "2d":
+        for k_ in ("plane_point3d", "plane_line3d"):
+            obs[k_] = {kk: vv[:0] for kk, vv in obs[k_].items()}
+    elif cfg.group_form == "3d":
+        for k_ in ("plane_point", "plane_line"):
+            obs[k_] = {kk: vv[:0] for kk, vv in obs[k_].items()}
+    elif cfg.group_form != "both":
+        raise ValueError(cfg.group_form)
     vl = np.nonzero(l_vp >= 0)[0]
     obs["vp"] = dict(cam=neg(len(vl)), feat=vl.astype(np.int32), other=l_vp[vl].astype(np.int32),
                      meas=np.zeros((len(vl), 0)))

@@ -142,11 +142,19 @@ def test_noise_free_zero_cost_and_zero_step():
 
 
 # ---------------------------------------------------------------- Jacobians by finite differences
+@pytest.fixture(scope="module")
+def tiny_both():
+    """The tiny scene with both forms of the plane constraints (group-induced 2D and direct 3D)."""
+    s = make_scene(config("tiny", group_form="both"))
+    return s, O.state_from_scene(s), s["fixed"]
+
+
 @pytest.mark.parametrize("kind", O.KINDS)
-def test_jacobian_finite_differences(tiny, kind):
+def test_jacobian_finite_differences(tiny_both, kind):
     """Central differences through the retraction x (+) delta agree with the oracle's J."""
-    s, st, _ = tiny
+    s, st, _ = tiny_both
     o = s["obs"][kind]
+    assert len(o["feat"]) > 0
     n = min(40, len(o["feat"]))
     sub = {k: {kk: vv[:n] for kk, vv in o.items()} for k, o in s["obs"].items()}
     r, v, Jc, Jf, Jg = O.residuals(st, sub, kind, with_jac=True)
@@ -192,8 +200,9 @@ def test_first_order_group_residual():
 
 
 # ---------------------------------------------------------------- the Schur step equals the full solve
-def test_schur_equals_dense_full_solve(tiny):
-    s, st, fixed = tiny
+@pytest.mark.parametrize("form", ["2d", "both"])
+def test_schur_equals_dense_full_solve(tiny, tiny_both, form):
+    s, st, fixed = tiny if form == "2d" else tiny_both
     opt = O.Options(solver="dense")
     lay = O.Layout(st, fixed)
     lam = 1e-3
@@ -617,3 +626,41 @@ def test_refined_intrinsics_recovered_noise_free():
     assert E0 > 100 and info["E"] < 1e-12 * E0
     np.testing.assert_allclose(st2["intr"], true, rtol=0, atol=1e-7)
     np.testing.assert_allclose(st2["cams"][:, 7:10], true[s["intrinsics"]["of_cam"]], rtol=0, atol=1e-7)
+
+
+# ---------------------------------------------------------------- direct 3D group distances (Section 3.2, Table 5)
+def test_group3d_closed_forms():
+    """Point-to-plane distance n.X + w, and for a line its direction's normal component n.d and the distance of
+    its foot point d x m: hand-worked values (plane z = 1)."""
+    P = torch.tensor([0.0, 0.0, 1.0, -1.0])
+    z3 = torch.zeros(3)
+    r, _ = O.res_plane_point3d(torch.zeros(6), z3, z3, torch.zeros(12), torch.tensor([1.0, 2.0, 3.0, 0, 0, 0]), P,
+                               torch.zeros(4))
+    assert abs(float(r[0]) - 2.0) < 1e-15
+    # the x axis lifted to z = 5: d = (1,0,0), m = p x d = (0,5,0), foot (0,0,5): r = (0, 4)
+    L = torch.tensor([1.0, 0.0, 0.0, 0.0, 5.0, 0.0])
+    r, _ = O.res_plane_line3d(torch.zeros(6), torch.zeros(4), z3, torch.zeros(12), L, P, torch.zeros(4))
+    np.testing.assert_allclose(r.numpy(), [0.0, 4.0], atol=1e-14)
+    # a line through (0,0,1) with d = (0, 0.6, 0.8): foot (0, -0.48, 0.36) (the point of the line nearest the
+    # origin): r = (0.8, 0.36 - 1)
+    d = torch.tensor([0.0, 0.6, 0.8])
+    L = torch.cat([d, torch.linalg.cross(torch.tensor([0.0, 0.0, 1.0]), d)])
+    r, _ = O.res_plane_line3d(torch.zeros(6), torch.zeros(4), z3, torch.zeros(12), L, P, torch.zeros(4))
+    np.testing.assert_allclose(r.numpy(), [0.8, 0.36 - 1.0], atol=1e-14)
+
+
+def test_group3d_zero_on_ground_truth_and_outside_pixel_cost():
+    """The 3D distances vanish at the noise-free ground truth; they count in E and not in E_px (moving a plane
+    in a scene whose planes enter only through them changes E, not E_px); their weight scales their share."""
+    s = noise_free(config("tiny", group_form="3d"))
+    st = O.state_from_scene(s)
+    for k in ("plane_point3d", "plane_line3d"):
+        r, v = O.residuals(st, s["obs"], k)
+        assert float(r.abs().max()) < 1e-13
+    st2 = {k: v.copy() for k, v in st.items()}
+    st2["planes"][0, 3] += 0.05
+    E1, Epx1 = O.cost(st, s["obs"], O.Options())
+    E2, Epx2 = O.cost(st2, s["obs"], O.Options())
+    assert E2 > E1 + 1e-6 and Epx2 == Epx1
+    E10, _ = O.cost(st2, s["obs"], O.Options(w_group3d=10.0))
+    assert abs((E10 - Epx2) - 10 * (E2 - Epx2)) <= 1e-9 * E10
