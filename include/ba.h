@@ -74,7 +74,9 @@ typedef enum { BA_PLANE = 0, BA_VP = 1 } ba_group_kind;
 typedef enum { BA_REL_ORTHOGONAL = 0, BA_REL_PARALLEL = 1 } ba_relation_type;
 typedef enum {
   BA_OBS_POINT = 0, BA_OBS_LINE = 1, BA_OBS_PLANE_POINT = 2, BA_OBS_PLANE_LINE = 3,
-  BA_OBS_VP = 4, BA_OBS_P2L = 5, BA_OBS_L2P = 6
+  BA_OBS_VP = 4, BA_OBS_P2L = 5, BA_OBS_L2P = 6,
+  BA_OBS_PLANE_POINT3D = 7,   /* direct 3D point-to-plane distance n.X + w (no camera, no measurement) */
+  BA_OBS_PLANE_LINE3D = 8     /* direct 3D line-to-plane distances n.d and n.(d x m) + w (|d| = 1; no camera) */
 } ba_obs_kind;
 
 typedef struct ba_options {
@@ -114,6 +116,9 @@ typedef struct ba_options {
                                 = every window on a thread-block cluster of that many CTAs (256 threads each).  The
                                 autotuner may also run only the largest windows on clusters and the rest on single
                                 CTAs of the same launch */
+  double w_group3d;         /* loss weight of the direct 3D plane distances (1.0; the form Section 3.2 sets against
+                               the group-induced residuals, weighed 1 to 1000 in Table 5).  Not in E_px */
+  double cauchy_3d;         /* their Cauchy scale, in scene units (1.0) */
   int cam_dof;              /* 6 (default): camera blocks refine the pose, f, k1, k2 are held constant; 9: f, k1, k2
                                are refined too (Section 3.1, K_c(i)), as intrinsics entities of the reduced system
                                (3 values each, one per camera unless ba_set_intrinsics shares them); their
@@ -192,7 +197,7 @@ ba_status ba_add_relations(ba_problem* p, int64_t n, int mem, const int32_t* kin
  * replaces an earlier one; not allowed after freezing (BA_ERR_STATE). */
 ba_status ba_set_intrinsics(ba_problem* p, int64_t n_intr, int mem, const double* f_k1_k2,
                             const int32_t* intr_of_cam, int64_t n_cams);
-/* Residual records of one kind: cam (n; ignored for BA_OBS_VP, may be NULL), feature (n), other (n; group id or
+/* Residual records of one kind: cam (n; ignored for BA_OBS_VP and the 3D plane kinds, may be NULL), feature (n), other (n; group id or
  * partner feature id, may be NULL for kinds without one), meas (n x meas_dim(kind), may be NULL when 0). */
 ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int mem, const int32_t* cam,
                               const int32_t* feature, const int32_t* other, const double* meas);

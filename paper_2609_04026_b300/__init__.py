@@ -26,8 +26,10 @@ BA_PRECOND_BLOCK_JACOBI, BA_PRECOND_LEARNED = 0, 1
 BA_POINT, BA_LINE = 0, 1
 BA_PLANE, BA_VP = 0, 1
 BA_REL_ORTHOGONAL, BA_REL_PARALLEL = 0, 1
-OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6}
-MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2}
+OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6,
+             "plane_point3d": 7, "plane_line3d": 8}
+MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0}
+NO_CAM = (4, 7, 8)   # kinds without a camera (the VP term, the direct 3D plane distances)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -43,7 +45,7 @@ class ba_options(C.Structure):
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double),
                 ("w_rel", C.c_double), ("cauchy_rel", C.c_double), ("batch_ctas_per_window", C.c_int),
-                ("cam_dof", C.c_int)]
+                ("w_group3d", C.c_double), ("cauchy_3d", C.c_double), ("cam_dof", C.c_int)]
 
 
 class ba_step_report(C.Structure):
@@ -417,11 +419,11 @@ def load_scene(p, scene, device_tensors=False):
         ba_add_relations(p, conv(rel["ka"].astype(np.int32)), conv(rel["a"]), conv(rel["kb"].astype(np.int32)),
                          conv(rel["b"]), conv(rel["type"].astype(np.int32)))
     for name, k in OBS_KINDS.items():
-        o = scene["obs"][name]
-        if len(o["feat"]) == 0:
+        o = scene["obs"].get(name)
+        if o is None or len(o["feat"]) == 0:
             continue
         meas = o["meas"] if MEAS_DIM[k] else None
-        ba_add_observations(p, k, conv(o["cam"]) if k != 4 else None, conv(o["feat"]), conv(o["other"]),
+        ba_add_observations(p, k, conv(o["cam"]) if k not in NO_CAM else None, conv(o["feat"]), conv(o["other"]),
                             conv(meas) if meas is not None else None)
 
 

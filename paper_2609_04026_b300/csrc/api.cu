@@ -24,7 +24,7 @@
 
 using namespace ba;
 
-static const int kMeasDim[7] = {2, 4, 0, 4, 0, 4, 2};
+static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0};
 
 static ba_status set_err(ba_problem* p, ba_status s, const std::string& m) {
   if (p) p->err = m;
@@ -59,6 +59,8 @@ extern "C" void ba_default_options(ba_options* o) {
   o->w_rel = 5e3;
   o->cauchy_rel = 0.2;
   o->cam_dof = 6;
+  o->w_group3d = 1.0;
+  o->cauchy_3d = 1.0;
 }
 
 extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
@@ -218,12 +220,14 @@ extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int
                                          const int32_t* feature, const int32_t* other, const double* meas) {
   ba_status s = check_add(p, n);
   if (s) return s;
-  if (kind < 0 || kind > 6) return set_err(p, BA_ERR_ARG, "unknown observation kind");
+  if (kind < 0 || kind >= N_KINDS) return set_err(p, BA_ERR_ARG, "unknown observation kind");
   if (mem != BA_MEM_HOST && mem != BA_MEM_DEVICE) return set_err(p, BA_ERR_ARG, "mem must be BA_MEM_HOST or BA_MEM_DEVICE");
   if (n == 0) return BA_OK;
-  const bool needs_other = kind == BA_OBS_PLANE_POINT || kind == BA_OBS_PLANE_LINE || kind == BA_OBS_VP;
+  const bool needs_other = kind == BA_OBS_PLANE_POINT || kind == BA_OBS_PLANE_LINE || kind == BA_OBS_VP ||
+                           kind == BA_OBS_PLANE_POINT3D || kind == BA_OBS_PLANE_LINE3D;
+  const bool has_cam = res_has_cam(kind);
   const int md = kMeasDim[kind];
-  if (!feature || (kind != BA_OBS_VP && !cam) || (md && !meas)) return set_err(p, BA_ERR_ARG, "null array");
+  if (!feature || (has_cam && !cam) || (md && !meas)) return set_err(p, BA_ERR_ARG, "null array");
   if (needs_other && !other) return set_err(p, BA_ERR_ARG, "this observation kind needs the group id array");
   // the records go straight to device memory: the structure build validates and merges them there
   ba_problem::ObsBatch b;
@@ -239,7 +243,7 @@ extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int
     if (!dst || cudaMemcpyAsync(dst, src, bytes, dir, p->stream) != cudaSuccess) ok = false;
   };
   stage(b.feat, feature, (size_t)n);
-  if (kind != BA_OBS_VP) stage(b.cam, cam, (size_t)n);
+  if (has_cam) stage(b.cam, cam, (size_t)n);
   stage(b.other, other, (size_t)n);
   if (md) stage(b.meas, meas, (size_t)md * n);
   // the caller may reuse its buffers on return (also pinned ones, whose copies are asynchronous)

@@ -230,10 +230,10 @@ __global__ void k_convert(int64_t n, const double* __restrict__ a, float* __rest
 // K1: linearise and reduce per feature
 // ============================================================================
 struct LossW {
-  double w[7];
-  double a2[7];
-  double inv_a2[7];   // 1 / a^2: the scaled squared norm s / a^2 as a product
-  double half_wa2[7]; // w a^2 / 2, the factor of the Cauchy cost
+  double w[N_KINDS];
+  double a2[N_KINDS];
+  double inv_a2[N_KINDS];   // 1 / a^2: the scaled squared norm s / a^2 as a product
+  double half_wa2[N_KINDS]; // w a^2 / 2, the factor of the Cauchy cost
 };
 
 template <class T>
@@ -453,12 +453,14 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       if (kind == R_POINT) res_point<T, true, INTR>(c, F, meas, o);
       else if (kind == R_PLANE_POINT) { res_plane_point<T, true, INTR>(c, F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
       else if (kind == R_P2L) res_p2l<T, true, INTR>(c, F, meas, o);
+      else if (kind == R_PLANE_POINT3) { res_plane_point3<T, true>(F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
       else continue;
     } else {
       if (kind == R_LINE) res_line<T, true, INTR>(c, F, meas, o);
       else if (kind == R_PLANE_LINE) { res_plane_line<T, true, INTR>(c, F, a.grp + (size_t)GRP_STRIDE * gid, meas, o); has_plane = true; }
       else if (kind == R_VP) { res_vp<T, true, INTR>(F, a.grp + (size_t)GRP_STRIDE * (a.npl + gid), o); has_vp = true; }
       else if (kind == R_L2P) res_l2p<T, true, INTR>(c, F, meas, o);
+      else if (kind == R_PLANE_LINE3) { res_plane_line3<T, true>(F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
       else continue;
     }
     if (!o.valid) continue;
@@ -2994,13 +2996,15 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
       case R_VP: res_vp<double, false>(L, a.grpD + (size_t)GRP_STRIDE * (a.npl + gid), o); break;
       case R_P2L: res_p2l<double, false>(c, X, meas, o); break;
       case R_L2P: res_l2p<double, false>(c, L, meas, o); break;
+      case R_PLANE_POINT3: res_plane_point3<double, false>(X, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
+      case R_PLANE_LINE3: res_plane_line3<double, false>(L, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
     }
     if (o.valid) {
       double s = 0;
       for (int k = 0; k < rd; ++k) s += o.r[k] * o.r[k];
       const double e = a.loss.half_wa2[kind] * ln1p_tab(s * a.loss.inv_a2[kind]);
       v[0] = e;
-      v[1] = kind == R_VP ? 0.0 : e;
+      v[1] = res_pixel(kind) ? e : 0.0;
     }
   }
 }
@@ -3101,10 +3105,10 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 static LossW make_loss(const ba_options& o) {
   LossW L;
-  double w[7] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire};
-  for (int k = 0; k < 7; ++k) {
+  double w[N_KINDS] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire, o.w_group3d, o.w_group3d};
+  for (int k = 0; k < N_KINDS; ++k) {
     L.w[k] = w[k];
-    double s = (k == R_VP) ? o.cauchy_vp : o.cauchy_px;
+    double s = (k == R_VP) ? o.cauchy_vp : (res_has_cam(k) ? o.cauchy_px : o.cauchy_3d);
     L.a2[k] = s * s;
     L.inv_a2[k] = 1.0 / L.a2[k];
     L.half_wa2[k] = 0.5 * w[k] * L.a2[k];

@@ -22,6 +22,8 @@
 //   R5 VP angular               Eq. 6 written as the 3-vector d x v
 //   R6 wireframe point->line    Eq. 11 (pinhole pixels)
 //   R7 wireframe line->point    Eq. 12 (pinhole pixels)
+//   3D point-to-plane and line-to-plane distances: the direct 3D form of the plane constraint that Section 3.2
+//   sets against the group-induced residuals (Table 5 weighs it); no camera, not in the pixel cost
 // Lines and the wireframe terms live in undistorted pixel coordinates; only R1
 // and R3 use k1, k2.
 // With INTR (refined intrinsics, Section 3.1) a residual also gives its rows of the
@@ -32,11 +34,20 @@
 
 namespace ba {
 
-enum ResKind : int { R_POINT = 0, R_LINE = 1, R_PLANE_POINT = 2, R_PLANE_LINE = 3, R_VP = 4, R_P2L = 5, R_L2P = 6 };
+enum ResKind : int {
+  R_POINT = 0, R_LINE = 1, R_PLANE_POINT = 2, R_PLANE_LINE = 3, R_VP = 4, R_P2L = 5, R_L2P = 6,
+  R_PLANE_POINT3 = 7, R_PLANE_LINE3 = 8   // the direct 3D plane distances (no camera)
+};
+constexpr int N_KINDS = 9;
 
 __host__ __device__ constexpr int res_dim(int k) {
-  return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3 : 1;
+  return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3
+       : k == R_PLANE_LINE3 ? 2 : 1;
 }
+// kinds with a camera (the others: the VP term and the direct 3D plane distances)
+__host__ __device__ constexpr bool res_has_cam(int k) { return k != R_VP && k != R_PLANE_POINT3 && k != R_PLANE_LINE3; }
+// kinds in the pixel cost E_px
+__host__ __device__ constexpr bool res_pixel(int k) { return res_has_cam(k); }
 
 // per-camera data precomputed from the FP64 master parameters each time they change
 // layout (stride CAM_STRIDE): R row-major (9), t (3), f, k1, k2, ppx, ppy
@@ -524,6 +535,56 @@ __device__ void res_vp(const T* L, const T* V, ResJ<T>& o) {
     for (int k = 0; k < 6; ++k) o.Jc[i][k] = 0;
     if (INTR) { o.Jk[i][0] = 0; o.Jk[i][1] = 0; o.Jk[i][2] = 0; }
   }
+}
+
+// direct 3D distance of a point to the plane (n, w): n . X + w
+template <class T, bool JAC>
+__device__ void res_plane_point3(const T* X, const T* P, ResJ<T>& o) {
+  const T* n = P;
+  o.r[0] = dot3(n, X) + P[3];
+  o.valid = true;
+  if (!JAC) return;
+  const T* b1 = P + 4;
+  const T* b2 = P + 7;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) o.Jf[0][k] = n[k];
+  o.Jg[0][0] = dot3(X, b1); o.Jg[0][1] = dot3(X, b2); o.Jg[0][2] = T(1);   // n moves along b1, b2; w along 1
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o.Jc[0][k] = 0;
+}
+
+// direct 3D distances of a line (d, m), |d| = 1, to the plane: n . d and n . (d x m) + w (its foot point)
+template <class T, bool JAC>
+__device__ void res_plane_line3(const T* L, const T* P, ResJ<T>& o) {
+  const T* n = P;
+  const T* d = L;
+  const T* m = L + 3;
+  T foot[3];
+  cross3(d, m, foot);
+  o.r[0] = dot3(n, d);
+  o.r[1] = dot3(n, foot) + P[3];
+  o.valid = true;
+  if (!JAC) return;
+  T u1[3], u3[3], r;
+  line_frame(d, m, u1, u3, r);
+  T ddir[4][3], mdir[4][3];
+  line_dirs(d, u1, u3, r, ddir, mdir);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T a[3], b[3];
+    cross3(ddir[k], m, a);   // d foot = dd x m + d x dm
+    cross3(d, mdir[k], b);
+    o.Jf[0][k] = dot3(n, ddir[k]);
+    o.Jf[1][k] = n[0] * (a[0] + b[0]) + n[1] * (a[1] + b[1]) + n[2] * (a[2] + b[2]);
+  }
+  const T* b1 = P + 4;
+  const T* b2 = P + 7;
+  o.Jg[0][0] = dot3(d, b1); o.Jg[0][1] = dot3(d, b2); o.Jg[0][2] = 0;
+  o.Jg[1][0] = dot3(foot, b1); o.Jg[1][1] = dot3(foot, b2); o.Jg[1][2] = T(1);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.Jc[i][k] = 0;
 }
 
 // R6: lhat . [pi_pinhole(C, X); 1], lhat = e1 x e2 scaled to |lhat_12| = 1 (Eq. 11)

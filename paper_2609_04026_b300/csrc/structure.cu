@@ -305,7 +305,7 @@ __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
     const int c = a.cam[i];
     if (c >= 0 && a.fixed[c] != 0x3F && c != prev) { ++n; prev = c; }
     const int k = a.kind[i];
-    if (k == R_PLANE_POINT || k == R_PLANE_LINE) {
+    if (k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3) {
       if (plane >= 0 && plane != a.grp[i]) atomicOr(a.err, 1);
       plane = a.grp[i];
     } else if (k == R_VP) {
@@ -340,7 +340,7 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
     const int32_t i = a.order[j];
     const int c = a.cam[i];
     const int k = a.kind[i];
-    if (k == R_PLANE_POINT || k == R_PLANE_LINE) plane = a.grp[i];
+    if (k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3) plane = a.grp[i];
     if (k == R_VP) vp = a.grp[i];
     if (c >= 0 && a.fixed[c] != 0x3F) {
       if (c != prev) {
@@ -372,7 +372,8 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
   o.feat_plane_slot[f] = plane_slot;
   for (int32_t j = r0; j < r1; ++j) {
     const int k = a.kind[a.order[j]];
-    o.rslot_g[j] = (k == R_PLANE_POINT || k == R_PLANE_LINE) ? plane_slot : (k == R_VP ? vp_slot : -1);
+    const bool on_plane = k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3;
+    o.rslot_g[j] = on_plane ? plane_slot : (k == R_VP ? vp_slot : -1);
   }
   if (!a.cam_k) return;
   // the intrinsics entities of the feature's cameras in ascending order (the slots of a feature are in entity
@@ -625,17 +626,17 @@ __global__ void k_gather_obs(ObsGather a) {
   if (i >= a.n) return;
   const int64_t j = a.o + i;
   const int k = a.kind;
-  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L);
+  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L || k == R_PLANE_POINT3);
   int code = 0;
   const int32_t f = a.feat[i];
   if (f < 0 || f >= (is_point ? a.np : a.nl)) code = 1;
   int32_t c = -1;
-  if (!code && k != R_VP) {
+  if (!code && res_has_cam(k)) {
     c = a.cam[i];
     if (c < 0 || c >= a.nc) code = 2;
   }
   int32_t g = -1;
-  if (!code && (k == R_PLANE_POINT || k == R_PLANE_LINE)) {
+  if (!code && (k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3)) {
     g = a.other[i];
     if (g < 0 || g >= a.npl) code = 3;
   } else if (!code && k == R_VP) {
