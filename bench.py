@@ -203,6 +203,7 @@ def main():
     ap.add_argument("--no-fp64-ttc", action="store_true", help="skip the FP64 block-Jacobi time-to-converge")
     ap.add_argument("--no-mixed-error", action="store_true", help="skip the per-result mixed-vs-FP64 error")
     ap.add_argument("--no-intr", action="store_true", help="skip the refined-intrinsics (cam_dof 9) workload")
+    ap.add_argument("--no-group3d", action="store_true", help="skip the direct-3D group-distance workload")
     ap.add_argument("--intr-models", type=int, default=20,
                     help="camera models sharing refined intrinsics in that workload (0 = one per camera)")
     args = ap.parse_args()
@@ -472,6 +473,42 @@ def main():
                         "(the typed storage of S when the group and intrinsics values fit, else the full 6 x 6)"}
         del si
 
+    # ---------------- the plane constraints in the direct 3D form (Section 3.2's alternative, Table 5): the same
+    # scene with the group-induced residuals replaced by one point-to-plane or line-to-plane distance per feature
+    # on a plane (weight 100, Table 5's best on ScanNet++); per-iteration time against the 2D form above
+    g3 = None
+    if not args.no_group3d:
+        s3 = dict(scene)
+        ob = dict(scene["obs"])
+        for k2, k3 in (("plane_point", "plane_point3d"), ("plane_line", "plane_line3d")):
+            f_, i_ = np.unique(ob[k2]["feat"], return_index=True)
+            ob[k3] = dict(cam=np.full(len(f_), -1, np.int32), feat=f_.astype(np.int32),
+                          other=ob[k2]["other"][i_].astype(np.int32), meas=np.zeros((len(f_), 0)))
+            ob[k2] = {kk: vv[:0] for kk, vv in ob[k2].items()}
+        s3["obs"] = ob
+        q = B.ba_create(B.ba_default_options(precision=prec, w_group3d=100.0, cuda_stream=stream.cuda_stream))
+        B.load_scene(q, s3)
+        for _ in range(3):
+            B.ba_lm_step(q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t3 = [B.ba_lm_step(q) for _ in range(5)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = e0.elapsed_time(e1)
+        na3, nbf3 = B.ba_reduced_size(q)
+        B.ba_destroy(q)
+        nres3 = sum(int(len(o["feat"])) for o in ob.values())
+        g3 = {"lm_iters_per_s": round(5 / (ms3 / 1e3), 3), "ms_per_step": round(ms3 / 5, 3),
+              "ms_per_step_2d_form": round(ms / args.steps, 3), "residuals": nres3, "stored_blocks": nbf3,
+              "pcg_iters": [r.pcg_iters for r in t3],
+              "kernels_ms": {k: round(float(np.mean([r.as_dict()["ms_kernel"][k] for r in t3])), 4)
+                             for k in t3[0].KERNELS},
+              "note": "the benchmark scene with its plane-induced residuals (Eq. 7, Eq. 8) replaced by the direct "
+                      "3D distances, one per feature on a plane, w_group3d = 100; 5 steps timed after 3 warm-up"}
+        del s3, ob
+
     # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
     # at the initial damping (the FP64 path itself is checked against the oracle at 2000 cameras by
     # tests/test_gpu_scale.py)
@@ -531,7 +568,7 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "time_to_converge": ttc, "time_to_converge_fp64_block_jacobi": ttc64,
                "time_to_equal_cost": equal,
-               "batched_windows": batched, "refined_intrinsics": intr, "learned_precond": learned,
+               "batched_windows": batched, "refined_intrinsics": intr, "group_form_3d": g3, "learned_precond": learned,
                "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
                "stage_rooflines": stages, "measured_fma_tflops": {"fp32": round(peak32, 2), "fp64": round(peak64, 3)},
                "mixed_error": mixed_err,
