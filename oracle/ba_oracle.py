@@ -41,19 +41,26 @@ from torch.func import jacfwd, vmap
 torch.set_default_dtype(torch.float64)
 DT = torch.float64
 
-KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d")
+KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
+         "sphere_point", "cylinder_point", "cone_point")
 # residual dimension, feature type, group type per kind
 RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1,
-        "plane_point3d": 1, "plane_line3d": 2}
+        "plane_point3d": 1, "plane_line3d": 2, "sphere_point": 2, "cylinder_point": 2, "cone_point": 2}
 FEAT = {"point": "point", "line": "line", "plane_point": "point", "plane_line": "line",
-        "vp": "line", "p2l": "point", "l2p": "line", "plane_point3d": "point", "plane_line3d": "line"}
+        "vp": "line", "p2l": "point", "l2p": "line", "plane_point3d": "point", "plane_line3d": "line",
+        "sphere_point": "point", "cylinder_point": "point", "cone_point": "point"}
 GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp", "plane_point3d": "plane",
-         "plane_line3d": "plane"}
+         "plane_line3d": "plane", "sphere_point": "sphere", "cylinder_point": "cylinder", "cone_point": "cone"}
 HAS_CAM = {k: k not in ("vp", "plane_point3d", "plane_line3d") for k in KINDS}
 # kinds outside the pixel cost E_px: the angular VP term, and the direct 3D group distances
 NON_PIXEL = ("vp", "plane_point3d", "plane_line3d")
 FDOF = {"point": 3, "line": 4}
-GDOF = {"plane": 3, "vp": 2}
+GDOF = {"plane": 3, "vp": 2, "sphere": 4, "cylinder": 5, "cone": 6}
+# state key and stored width of every group kind (spheres (c, r); cylinders (d, m, r), the axis a Pluecker line
+# with |d| = 1; cones (apex, unit axis, half-angle))
+GKEY = {"plane": ("planes", 4), "vp": ("vps", 3), "sphere": ("spheres", 4), "cylinder": ("cylinders", 7),
+        "cone": ("cones", 7)}
+SURFACES = ("sphere", "cylinder", "cone")
 CDOF = 6
 
 
@@ -83,7 +90,8 @@ class Options:
     def weight(self, kind):
         return {"point": self.w_point, "line": self.w_line, "plane_point": self.w_group,
                 "plane_line": self.w_group, "vp": self.w_vp, "p2l": self.w_wire,
-                "l2p": self.w_wire, "plane_point3d": self.w_group3d, "plane_line3d": self.w_group3d}[kind]
+                "l2p": self.w_wire, "plane_point3d": self.w_group3d, "plane_line3d": self.w_group3d,
+                "sphere_point": self.w_group, "cylinder_point": self.w_group, "cone_point": self.w_group}[kind]
 
     def scale(self, kind):
         if kind in ("plane_point3d", "plane_line3d"):
@@ -214,6 +222,58 @@ def vp_plus(v, dv):
     v = v / torch.linalg.norm(v, dim=-1, keepdim=True)
     b1, b2 = tangent_basis(v)
     return s2_exp(v, dv[..., 0:1] * b1 + dv[..., 1:2] * b2)
+
+
+# ---- the other group types of Appendix B / Table 6 (positives in log space, as the table's parameterisations
+# ask for r > 0; the cone's half-angle additive)
+def sphere_plus(S, d):
+    """centre c <- c + d[0:3], radius r <- r exp(d[3])."""
+    return torch.cat([S[..., :3] + d[..., :3], S[..., 3:4] * torch.exp(d[..., 3:4])], -1)
+
+
+def cylinder_plus(C, d):
+    """axis (Pluecker, |d| = 1) by the line update of the features (4), radius r <- r exp(d[4])."""
+    return torch.cat([line_plus(C[..., :6], d[..., :4]), C[..., 6:7] * torch.exp(d[..., 4:5])], -1)
+
+
+def cone_plus(K, d):
+    """apex a <- a + d[0:3], axis on S^2 by d[3:5], half-angle alpha <- alpha + d[5]."""
+    return torch.cat([K[..., :3] + d[..., :3], vp_plus(K[..., 3:6], d[..., 3:5]), K[..., 6:7] + d[..., 5:6]], -1)
+
+
+GROUP_PLUS = {"sphere": sphere_plus, "cylinder": cylinder_plus, "cone": cone_plus}
+
+
+def sphere_project_point(S, X):
+    """Appendix B: radial projection c + r (X - c) / |X - c|."""
+    u = X - S[..., :3]
+    return S[..., :3] + S[..., 3:4] * u / torch.linalg.norm(u, dim=-1, keepdim=True)
+
+
+def cylinder_project_point(C, X):
+    """Appendix B: radially onto the surface, perpendicular to the axis (foot p0 = d x m, direction d)."""
+    d, m, r = C[..., :3], C[..., 3:6], C[..., 6:7]
+    p0 = torch.linalg.cross(d, m)
+    v = X - p0
+    h = (v * d).sum(-1, keepdim=True)
+    w = v - h * d
+    return p0 + h * d + r * w / torch.linalg.norm(w, dim=-1, keepdim=True)
+
+
+def cone_project_point(K, X):
+    """Appendix B: onto the cone surface along the direction perpendicular to its generatrix: with v = X - a,
+    the radial unit e of v about the axis and the generatrix g = cos(alpha) d + sin(alpha) e through the apex,
+    the projection is a + (v . g) g."""
+    a, d, al = K[..., :3], K[..., 3:6], K[..., 6:7]
+    v = X - a
+    h = (v * d).sum(-1, keepdim=True)
+    w = v - h * d
+    e = w / torch.linalg.norm(w, dim=-1, keepdim=True)
+    g = torch.cos(al) * d + torch.sin(al) * e
+    return a + (v * g).sum(-1, keepdim=True) * g
+
+
+GROUP_PROJECT = {"sphere": sphere_project_point, "cylinder": cylinder_project_point, "cone": cone_project_point}
 
 
 # ===========================================================================
@@ -355,9 +415,30 @@ def res_plane_line3d(dc, df, dg, cam, feat, grp, meas):     # the same for a lin
     return torch.stack([(n * L[:3]).sum(-1), (n * foot).sum(-1) + P[3]]), torch.ones((), dtype=torch.bool)
 
 
+def _res_surface_point(kind):
+    """The group-induced point residual of Eq. 7 with the projection of another group type (Appendix B):
+    pi(C, X) - pi(C, Proj_g(X))."""
+    plus, proj = GROUP_PLUS[kind], GROUP_PROJECT[kind]
+
+    def fn(dc, df, dg, cam, feat, grp, meas):
+        R, t = _pose(cam, dc)
+        X = feat[:3] + df
+        G = plus(grp[:7], dg)
+        x1, z1 = pi_point(R, t, cam, X)
+        x2, z2 = pi_point(R, t, cam, proj(G, X))
+        return x1 - x2, (z1 > 1e-6) & (z2 > 1e-6)
+    return fn
+
+
+res_sphere_point = _res_surface_point("sphere")
+res_cylinder_point = _res_surface_point("cylinder")
+res_cone_point = _res_surface_point("cone")
+
+
 RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
           "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p,
-          "plane_point3d": res_plane_point3d, "plane_line3d": res_plane_line3d}
+          "plane_point3d": res_plane_point3d, "plane_line3d": res_plane_line3d,
+          "sphere_point": res_sphere_point, "cylinder_point": res_cylinder_point, "cone_point": res_cone_point}
 
 
 # ===========================================================================
@@ -438,7 +519,15 @@ def state_from_scene(scene):
         lines=normalize_lines(scene["lines"]) if len(scene["lines"]) else np.zeros((0, 6)),
         planes=np.array(scene["planes"], np.float64).reshape(-1, 4),
         vps=np.array(scene["vps"], np.float64).reshape(-1, 3),
+        spheres=np.array(scene.get("spheres", np.zeros((0, 4))), np.float64).reshape(-1, 4),
+        cylinders=np.array(scene.get("cylinders", np.zeros((0, 7))), np.float64).reshape(-1, 7),
+        cones=np.array(scene.get("cones", np.zeros((0, 7))), np.float64).reshape(-1, 7),
     )
+    if len(st["cylinders"]):
+        # the axis as a Pluecker line with |d| = 1
+        st["cylinders"][:, :6] = normalize_lines(st["cylinders"][:, :6])
+    if len(st["cones"]):
+        st["cones"][:, 3:6] /= np.linalg.norm(st["cones"][:, 3:6], axis=1, keepdims=True)
     if len(st["planes"]):
         # the plane n.x + w = 0 is homogeneous in (n, w): rescale both so that |n| = 1
         st["planes"] /= np.linalg.norm(st["planes"][:, :3], axis=1, keepdims=True)
@@ -466,10 +555,10 @@ def _records(state, obs, kind):
     feat = torch.zeros((n, 6), dtype=DT)
     if n:
         feat[:, : src.shape[1]] = torch.from_numpy(src[o["feat"]])
-    grp = torch.zeros((n, 4), dtype=DT)
+    grp = torch.zeros((n, 8), dtype=DT)
     gk = GROUP.get(kind)
     if gk and n:
-        g = state["planes"] if gk == "plane" else state["vps"]
+        g = state[GKEY[gk][0]]
         grp[:, : g.shape[1]] = torch.from_numpy(g[o["other"]])
     meas = torch.zeros((n, 4), dtype=DT)
     m = np.asarray(o["meas"]).reshape(n, -1)
@@ -503,7 +592,8 @@ def residuals(state, obs, kind, with_jac=False, chunk=200_000, with_intr=False):
             if with_intr:
                 out = out + (torch.zeros((0, rd, 3)),)
         return out
-    dc = torch.zeros((n, 6)); df = torch.zeros((n, kf)); dg = torch.zeros((n, 3)); dk = torch.zeros((n, 3))
+    dc = torch.zeros((n, 6)); df = torch.zeros((n, kf)); dk = torch.zeros((n, 3))
+    dg = torch.zeros((n, GDOF[GROUP[kind]] if kind in GROUP else 3))
     rs, vs, Js = [], [], [[] for _ in range(nj)]
     fk = with_intrinsics_increment(fn) if with_intr else fn
     for s in range(0, n, chunk):
@@ -578,6 +668,13 @@ class Layout:
         o = int(free.sum())
         self.plane_col = o + 3 * np.arange(self.npl); o += 3 * self.npl
         self.vp_col = o + 2 * np.arange(self.nv); o += 2 * self.nv
+        # the other group types (Appendix B), after the VPs: spheres (4), cylinders (5), cones (6)
+        self.ngs = {}
+        self.gcol = {"plane": self.plane_col, "vp": self.vp_col}
+        for gk in SURFACES:
+            ng = state[GKEY[gk][0]].shape[0] if GKEY[gk][0] in state else 0
+            self.ngs[gk] = ng
+            self.gcol[gk] = o + GDOF[gk] * np.arange(ng); o += GDOF[gk] * ng
         self.nk = state["intr"].shape[0] if "intr" in state else 0
         self.cam_k = state["cam_k"] if self.nk else np.full(self.nc, -1, np.int64)
         self.intr_col = o + 3 * np.arange(self.nk); o += 3 * self.nk
@@ -589,6 +686,7 @@ class Layout:
         nfree = free.sum(1)
         self.a_blocks = ([(int(self.cam_cols[i][free[i]][0]), int(nfree[i])) for i in range(self.nc) if nfree[i]] +
                          [(int(c), 3) for c in self.plane_col] + [(int(c), 2) for c in self.vp_col] +
+                         [(int(c), GDOF[gk]) for gk in SURFACES for c in self.gcol[gk]] +
                          [(int(c), 3) for c in self.intr_col])
         self.f_blocks = [(int(c), 3) for c in self.point_col] + [(int(c), 4) for c in self.line_col]
 
@@ -625,7 +723,7 @@ def linearize(state, obs, opt: Options, lay: Layout):
         blocks.append((Jf.numpy(), fc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
         gk = GROUP.get(k)
         if gk:
-            gc = (lay.plane_col if gk == "plane" else lay.vp_col)[o["other"]]
+            gc = lay.gcol[gk][o["other"]]
             w = GDOF[gk]
             blocks.append((Jg.numpy()[:, :, :w], gc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
         for J, C0, ok in blocks:
@@ -760,6 +858,11 @@ def apply_step(state, delta, lay: Layout):
     if lay.nv:
         d = delta[lay.vp_col[:, None] + np.arange(2)]
         new["vps"] = vp_plus(torch.from_numpy(state["vps"]), torch.from_numpy(d)).numpy()
+    for gk in SURFACES:
+        if lay.ngs[gk]:
+            key = GKEY[gk][0]
+            d = delta[lay.gcol[gk][:, None] + np.arange(GDOF[gk])]
+            new[key] = GROUP_PLUS[gk](torch.from_numpy(state[key]), torch.from_numpy(d)).numpy()
     if lay.nk:
         # intrinsics: additive; every camera's copy follows its entity
         new["intr"] = state["intr"] + delta[lay.intr_col[:, None] + np.arange(3)]

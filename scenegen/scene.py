@@ -42,9 +42,10 @@ import numpy as np
 IMG_W, IMG_H = 800.0, 600.0
 HALF = 3.0
 
-KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d")
+KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
+         "sphere_point", "cylinder_point", "cone_point")
 MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2,
-            "plane_point3d": 0, "plane_line3d": 0}
+            "plane_point3d": 0, "plane_line3d": 0, "sphere_point": 0, "cylinder_point": 0, "cone_point": 0}
 
 
 @dataclasses.dataclass
@@ -82,6 +83,12 @@ class SceneConfig:
     # "3d" the direct 3D distances to the plane instead (the alternative of Section 3.2, compared in Table 5),
     # "both" all of them; the observations are the same draws in every form
     group_form: str = "2d"
+    # the other group types of Appendix B (spheres, cylinders, cones), each with surf_points points on its
+    # surface, drawn with a generator of their own after everything else (the rest of the scene is unchanged)
+    n_spheres: int = 0
+    n_cylinders: int = 0
+    n_cones: int = 0
+    surf_points: int = 60
     seed: int = 1
 
 
@@ -554,7 +561,98 @@ def make_scene(cfg: SceneConfig) -> dict:
     )
     if intrinsics is not None:
         scene["intrinsics"] = intrinsics
+    _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp)
     return scene
+
+
+def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
+    """Spheres (c, r), cylinders (Pluecker axis d, m with |d| = 1, r) and cones (apex, unit axis, half-angle)
+    inside the cube, points on their surfaces appended after the other points, with their point observations
+    and one group-induced record per view (kinds sphere_point, cylinder_point, cone_point)."""
+    obs = scene["obs"]
+    for k in ("sphere_point", "cylinder_point", "cone_point"):
+        obs[k] = dict(cam=np.zeros(0, np.int32), feat=np.zeros(0, np.int32), other=np.zeros(0, np.int32),
+                      meas=np.zeros((0, 0)))
+    counts = {"sphere": cfg.n_spheres, "cylinder": cfg.n_cylinders, "cone": cfg.n_cones}
+    gt = {"sphere": np.zeros((0, 4)), "cylinder": np.zeros((0, 7)), "cone": np.zeros((0, 7))}
+    init = {k: v.copy() for k, v in gt.items()}
+    if sum(counts.values()) == 0:
+        scene["spheres"], scene["cylinders"], scene["cones"] = init["sphere"], init["cylinder"], init["cone"]
+        scene["gt"].update(spheres=gt["sphere"], cylinders=gt["cylinder"], cones=gt["cone"])
+        return
+    rng = np.random.default_rng(cfg.seed * 31 + 777)
+    Nc = len(Rgt)
+    np0 = len(scene["points"])
+    new_P, new_gt, recs = [], [], []
+    for kind in ("sphere", "cylinder", "cone"):
+        rows, rows0 = [], []
+        for g in range(counts[kind]):
+            ctr = rng.uniform(-1.5, 1.5, 3)
+            d = _rand_unit(rng, 1)[0]
+            e1 = np.cross(d, [1.0, 0, 0] if abs(d[0]) < 0.9 else [0, 1.0, 0]); e1 /= np.linalg.norm(e1)
+            e2 = np.cross(d, e1)
+            th = rng.uniform(0, 2 * np.pi, cfg.surf_points)
+            ring = np.cos(th)[:, None] * e1 + np.sin(th)[:, None] * e2
+            if kind == "sphere":
+                r = rng.uniform(0.3, 0.8)
+                prm = np.concatenate([ctr, [r]])
+                X = ctr + r * _rand_unit(rng, cfg.surf_points)
+                prm0 = np.concatenate([ctr + rng.normal(0, 0.05, 3), [r * (1 + 0.05 * rng.normal())]])
+            elif kind == "cylinder":
+                r = rng.uniform(0.2, 0.5)
+                prm = np.concatenate([d, np.cross(ctr, d), [r]])
+                X = ctr + rng.uniform(-1, 1, cfg.surf_points)[:, None] * d + r * ring
+                d0 = _axis_angle_mat(_rand_unit(rng, 1), np.deg2rad(2.0) * rng.normal(size=1))[0] @ d
+                c0 = ctr + rng.normal(0, 0.05, 3)
+                prm0 = np.concatenate([d0, np.cross(c0, d0), [r * (1 + 0.05 * rng.normal())]])
+            else:
+                al = rng.uniform(0.3, 0.7)
+                prm = np.concatenate([ctr, d, [al]])
+                t_ = rng.uniform(0.5, 1.5, cfg.surf_points)
+                X = ctr + t_[:, None] * (np.cos(al) * d + np.sin(al) * ring)
+                d0 = _axis_angle_mat(_rand_unit(rng, 1), np.deg2rad(2.0) * rng.normal(size=1))[0] @ d
+                prm0 = np.concatenate([ctr + rng.normal(0, 0.05, 3), d0, [al + 0.02 * rng.normal()]])
+            rows.append(prm); rows0.append(prm0)
+            for x in X:
+                new_gt.append(x)
+                new_P.append(x + rng.normal(0, cfg.feat_noise, 3))
+                recs.append((kind, g))
+        if rows:
+            gt[kind] = np.array(rows); init[kind] = np.array(rows0)
+    new_gt = np.array(new_gt).reshape(-1, 3)
+    # views: every camera that sees the point in front and inside the image; a random track of the usual length
+    xc = np.einsum("cij,pj->pci", Rgt, new_gt) + tgt[None]
+    xy = _pix_dist(f[None], k1[None], k2[None], pp[None], xc)
+    vis = _visible(xy, xc[..., 2])
+    pc, pf, pm, gk, gc, gf, gg = [], [], [], {k: [] for k in counts}, {k: [] for k in counts}, None, None
+    cams_of = {"sphere": [], "cylinder": [], "cone": []}
+    for i in range(len(new_gt)):
+        cs = np.flatnonzero(vis[i])
+        if len(cs) < 2:
+            continue
+        n = int(min(len(cs), rng.integers(cfg.track_min, cfg.track_max + 1)))
+        cs = np.sort(rng.choice(cs, size=max(n, 2), replace=False))
+        m = xy[i, cs] + rng.normal(0, cfg.sigma_px, (len(cs), 2))
+        out = rng.random(len(cs)) < cfg.outlier_frac
+        m[out] = np.stack([rng.uniform(0, IMG_W, out.sum()), rng.uniform(0, IMG_H, out.sum())], 1)
+        fid = np0 + i
+        pc += cs.tolist(); pf += [fid] * len(cs); pm.append(m)
+        kind, g = recs[i]
+        cams_of[kind] += [(c, fid, g) for c in cs]
+    if pc:
+        o = obs["point"]
+        obs["point"] = dict(cam=np.concatenate([o["cam"], np.array(pc, np.int32)]),
+                            feat=np.concatenate([o["feat"], np.array(pf, np.int32)]),
+                            other=np.concatenate([o["other"], np.full(len(pc), -1, np.int32)]),
+                            meas=np.concatenate([o["meas"], np.concatenate(pm)]))
+    for kind in counts:
+        t = np.array(cams_of[kind], np.int64).reshape(-1, 3)
+        obs[kind + "_point"] = dict(cam=t[:, 0].astype(np.int32), feat=t[:, 1].astype(np.int32),
+                                    other=t[:, 2].astype(np.int32), meas=np.zeros((len(t), 0)))
+    scene["points"] = np.concatenate([scene["points"], np.array(new_P).reshape(-1, 3)])
+    scene["gt"]["points"] = np.concatenate([scene["gt"]["points"], new_gt])
+    scene["spheres"], scene["cylinders"], scene["cones"] = init["sphere"], init["cylinder"], init["cone"]
+    scene["gt"].update(spheres=gt["sphere"], cylinders=gt["cylinder"], cones=gt["cone"])
 
 
 def noise_free(cfg: SceneConfig) -> dict:
@@ -565,6 +663,8 @@ def noise_free(cfg: SceneConfig) -> dict:
     s["cams"] = {k: v.copy() for k, v in s["gt"]["cams"].items()}
     s["points"] = s["gt"]["points"].copy(); s["lines"] = s["gt"]["lines"].copy()
     s["planes"] = s["gt"]["planes"].copy(); s["vps"] = s["gt"]["vps"].copy()
+    for k in ("spheres", "cylinders", "cones"):
+        s[k] = s["gt"][k].copy()
     if "intrinsics" in s:
         ik = s["intrinsics"]
         nk = len(ik["values"])

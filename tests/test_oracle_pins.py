@@ -144,8 +144,9 @@ def test_noise_free_zero_cost_and_zero_step():
 # ---------------------------------------------------------------- Jacobians by finite differences
 @pytest.fixture(scope="module")
 def tiny_both():
-    """The tiny scene with both forms of the plane constraints (group-induced 2D and direct 3D)."""
-    s = make_scene(config("tiny", group_form="both"))
+    """The tiny scene with both forms of the plane constraints (group-induced 2D and direct 3D) and two spheres,
+    cylinders and cones (Appendix B)."""
+    s = make_scene(config("tiny", group_form="both", n_spheres=2, n_cylinders=2, n_cones=2))
     return s, O.state_from_scene(s), s["fixed"]
 
 
@@ -162,12 +163,13 @@ def test_jacobian_finite_differences(tiny_both, kind):
     kf = O.FDOF[O.FEAT[kind]]
     fn = O.RES_FN[kind]
     h = 1e-6
-    for blk, dim, J in ((0, 6, Jc), (1, kf, Jf), (2, 3, Jg)):
+    ng = Jg.shape[2]
+    for blk, dim, J in ((0, 6, Jc), (1, kf, Jf), (2, ng, Jg)):
         for j in range(dim):
             def ev(sgn):
                 out = []
                 for i in range(n):
-                    d = [torch.zeros(6), torch.zeros(kf), torch.zeros(3)]
+                    d = [torch.zeros(6), torch.zeros(kf), torch.zeros(ng)]
                     d[blk] = d[blk].clone(); d[blk][j] = sgn * h
                     out.append(fn(d[0], d[1], d[2], cam[i], feat[i], grp[i], meas[i])[0])
                 return torch.stack(out)
@@ -563,9 +565,10 @@ def test_intrinsics_derivatives_closed_form():
 def test_intrinsics_jacobian_finite_differences(kind):
     """Central differences of the residuals in (f, k1, k2) agree with the oracle's intrinsics Jacobian; the
     line kinds and the wireframe kinds do not depend on k1, k2 (undistorted pinhole pixels)."""
-    s = make_scene(config("tiny", intr_refine=True))
+    s = make_scene(config("tiny", intr_refine=True, n_spheres=1, n_cylinders=1, n_cones=1))
     st = O.state_from_scene(s)
     n = min(40, len(s["obs"][kind]["feat"]))
+    assert n > 0
     sub = {k: {kk: vv[:n] for kk, vv in o.items()} for k, o in s["obs"].items()}
     r, v, Jc, Jf, Jg, Jk = O.residuals(st, sub, kind, with_jac=True, with_intr=True)
     cam, feat, grp, meas = O._records(st, sub, kind)
@@ -575,12 +578,12 @@ def test_intrinsics_jacobian_finite_differences(kind):
     for j, h in ((0, 1e-1), (1, 1e-3), (2, 1e-3)):
         def ev(sgn):
             dk = torch.zeros(3); dk[j] = sgn * h
-            return torch.stack([fk(torch.zeros(6), torch.zeros(kf), torch.zeros(3), dk, cam[i], feat[i], grp[i],
-                                   meas[i])[0] for i in range(n)])
+            return torch.stack([fk(torch.zeros(6), torch.zeros(kf), torch.zeros(Jg.shape[2]), dk, cam[i], feat[i],
+                                   grp[i], meas[i])[0] for i in range(n)])
         fd = (ev(1) - ev(-1)) / (2 * h)
         scale = float(Jk[:, :, j].abs().max()) + 1e-12
         assert float((fd - Jk[:, :, j]).abs().max()) <= 2e-6 * scale + 1e-7, (kind, j)
-    if kind not in ("point", "plane_point"):
+    if kind not in ("point", "plane_point", "sphere_point", "cylinder_point", "cone_point"):
         assert float(Jk[:, :, 1:].abs().max()) == 0.0
 
 
@@ -664,3 +667,34 @@ def test_group3d_zero_on_ground_truth_and_outside_pixel_cost():
     assert E2 > E1 + 1e-6 and Epx2 == Epx1
     E10, _ = O.cost(st2, s["obs"], O.Options(w_group3d=10.0))
     assert abs((E10 - Epx2) - 10 * (E2 - Epx2)) <= 1e-9 * E10
+
+
+# ---------------------------------------------------------------- sphere, cylinder, cone (Appendix B, Table 6)
+@pytest.mark.parametrize("name,kind", [("sphere_projection", "sphere"), ("cylinder_projection", "cylinder"),
+                                       ("cone_projection", "cone")])
+def test_surface_projection_closed_forms(name, kind):
+    c = _case(name)
+    out = O.GROUP_PROJECT[kind](torch.tensor(c["group"]), torch.tensor(c["X"]))
+    np.testing.assert_allclose(out.numpy(), c["proj"], atol=1e-14)
+    # the projection is idempotent (a point of the surface is its own projection)
+    again = O.GROUP_PROJECT[kind](torch.tensor(c["group"]), out)
+    np.testing.assert_allclose(again.numpy(), c["proj"], atol=1e-13)
+
+
+def test_surface_groups_zero_on_ground_truth_and_retractions():
+    """Points on their spheres, cylinders and cones have zero group-induced residuals at the noise-free
+    ground truth; the retractions keep the radius positive (log space), the axes unit and the cylinder axis a
+    Pluecker line (d . m = 0)."""
+    s = noise_free(config("tiny", n_spheres=2, n_cylinders=2, n_cones=2))
+    st = O.state_from_scene(s)
+    for k in ("sphere_point", "cylinder_point", "cone_point"):
+        r, v = O.residuals(st, s["obs"], k)
+        assert len(r) > 100 and bool(v.all()) and float(r.abs().max()) < 1e-10, k
+    d = torch.tensor([0.3, -0.2, 0.1, -5.0, 0.2])
+    C = O.cylinder_plus(torch.tensor(st["cylinders"][0]), d)
+    assert float(C[6]) > 0 and abs(float(torch.linalg.norm(C[:3])) - 1) < 1e-14
+    assert abs(float((C[:3] * C[3:6]).sum())) < 1e-14
+    S = O.sphere_plus(torch.tensor(st["spheres"][0]), torch.tensor([0.0, 0, 0, -50.0]))
+    assert float(S[3]) > 0
+    K = O.cone_plus(torch.tensor(st["cones"][0]), torch.tensor([0.1, 0, 0, 0.4, -0.3, 0.01]))
+    assert abs(float(torch.linalg.norm(K[3:6])) - 1) < 1e-14
