@@ -70,13 +70,21 @@ typedef enum { BA_MEM_HOST = 0, BA_MEM_DEVICE = 1 } ba_mem;
 typedef enum { BA_FP64 = 0, BA_MIXED = 1 } ba_precision;
 typedef enum { BA_PRECOND_BLOCK_JACOBI = 0, BA_PRECOND_LEARNED = 1 } ba_precond;
 typedef enum { BA_POINT = 0, BA_LINE = 1 } ba_feature_kind;
-typedef enum { BA_PLANE = 0, BA_VP = 1 } ba_group_kind;
+typedef enum {
+  BA_PLANE = 0, BA_VP = 1,
+  BA_SPHERE = 2,     /* n x 4: centre c, radius r > 0 (Appendix B; radius updated in log space) */
+  BA_CYLINDER = 3,   /* n x 7: axis as a Pluecker line (d, m), m . d = 0 (rescaled to |d| = 1), radius r > 0 */
+  BA_CONE = 4        /* n x 7: apex a, axis direction d (normalised), half-angle in (0, pi/2) */
+} ba_group_kind;
 typedef enum { BA_REL_ORTHOGONAL = 0, BA_REL_PARALLEL = 1 } ba_relation_type;
 typedef enum {
   BA_OBS_POINT = 0, BA_OBS_LINE = 1, BA_OBS_PLANE_POINT = 2, BA_OBS_PLANE_LINE = 3,
   BA_OBS_VP = 4, BA_OBS_P2L = 5, BA_OBS_L2P = 6,
   BA_OBS_PLANE_POINT3D = 7,   /* direct 3D point-to-plane distance n.X + w (no camera, no measurement) */
-  BA_OBS_PLANE_LINE3D = 8     /* direct 3D line-to-plane distances n.d and n.(d x m) + w (|d| = 1; no camera) */
+  BA_OBS_PLANE_LINE3D = 8,    /* direct 3D line-to-plane distances n.d and n.(d x m) + w (|d| = 1; no camera) */
+  /* group-induced point residuals of the other group types (Eq. 7 with the projections of Appendix B): a point
+   * observed in a camera, other = the sphere / cylinder / cone id; no measurement */
+  BA_OBS_SPHERE_POINT = 9, BA_OBS_CYLINDER_POINT = 10, BA_OBS_CONE_POINT = 11
 } ba_obs_kind;
 
 typedef struct ba_options {
@@ -176,7 +184,10 @@ ba_status ba_add_cameras(ba_problem* p, int64_t n, int mem, const double* quat_t
                          const double* pp, const uint8_t* fixed);
 /* Features (Section 3.2): kind BA_POINT (n x 3) or BA_LINE (n x 6 Pluecker). */
 ba_status ba_add_features(ba_problem* p, int kind, int64_t n, int mem, const double* params);
-/* Groups (Section 3.2-3.3, Appendix B): kind BA_PLANE (n x 4) or BA_VP (n x 3). */
+/* Groups (Section 3.2-3.3, Appendix B, Table 6): kind BA_PLANE (n x 4), BA_VP (n x 3), BA_SPHERE (n x 4),
+ * BA_CYLINDER (n x 7) or BA_CONE (n x 7), layouts at ba_group_kind.  A feature may belong to at most one
+ * positional group (a plane, sphere, cylinder or cone).  Spheres, cylinders and cones keep the full 6 x 6
+ * storage of S and are not supported by ba_solve_batch or together with cam_dof = 9 (BA_ERR_ARG). */
 ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, const double* params);
 /* Inter-group relations (Section 3.2, Inter-Group Relations; Appendix C, Manhattan / Atlanta world): n
  * relations between two group directions, each a plane normal (kind BA_PLANE) or a VP direction (BA_VP).

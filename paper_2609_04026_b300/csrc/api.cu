@@ -24,7 +24,7 @@
 
 using namespace ba;
 
-static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0};
+static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0};
 
 static ba_status set_err(ba_problem* p, ba_status s, const std::string& m) {
   if (p) p->err = m;
@@ -173,7 +173,10 @@ extern "C" ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, 
   if (s) return s;
   if (kind == BA_PLANE) s = fetch(p, mem, params, 4 * n, p->h_pln);
   else if (kind == BA_VP) s = fetch(p, mem, params, 3 * n, p->h_vps);
-  else return set_err(p, BA_ERR_ARG, "group kind must be BA_PLANE or BA_VP");
+  else if (kind == BA_SPHERE) s = fetch(p, mem, params, 4 * n, p->h_sph);
+  else if (kind == BA_CYLINDER) s = fetch(p, mem, params, 7 * n, p->h_cyl);
+  else if (kind == BA_CONE) s = fetch(p, mem, params, 7 * n, p->h_cone);
+  else return set_err(p, BA_ERR_ARG, "group kind must be BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER or BA_CONE");
   return s;
 }
 
@@ -224,7 +227,7 @@ extern "C" ba_status ba_add_observations(ba_problem* p, int kind, int64_t n, int
   if (mem != BA_MEM_HOST && mem != BA_MEM_DEVICE) return set_err(p, BA_ERR_ARG, "mem must be BA_MEM_HOST or BA_MEM_DEVICE");
   if (n == 0) return BA_OK;
   const bool needs_other = kind == BA_OBS_PLANE_POINT || kind == BA_OBS_PLANE_LINE || kind == BA_OBS_VP ||
-                           kind == BA_OBS_PLANE_POINT3D || kind == BA_OBS_PLANE_LINE3D;
+                           kind == BA_OBS_PLANE_POINT3D || kind == BA_OBS_PLANE_LINE3D || kind >= BA_OBS_SPHERE_POINT;
   const bool has_cam = res_has_cam(kind);
   const int md = kMeasDim[kind];
   if (!feature || (has_cam && !cam) || (md && !meas)) return set_err(p, BA_ERR_ARG, "null array");
@@ -477,6 +480,7 @@ static ba_status freeze(ba_problem* p) {
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
   if (d.nk) ok &= A(p->slotCK, T * SC * (size_t)d.ne);
+  if (d.ngs()) ok &= A(p->slotCS, T * SCS * (size_t)d.ne);
   ok &= A(p->slotBS, T * SBS * (size_t)d.ne);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
@@ -497,12 +501,14 @@ static ba_status freeze(ba_problem* p) {
     ok &= A(p->ptsT, sizeof(float) * 3 * (size_t)d.np);
     ok &= A(p->linT, sizeof(float) * 6 * (size_t)d.nl);
     ok &= A(p->measT, sizeof(float) * 4 * (size_t)d.nr);
+    if (d.ngs()) ok &= A(p->srfT, sizeof(float) * SRF_STRIDE * (size_t)d.ngs());
   }
   if (!ok) return set_err(p, BA_ERR_OOM, "device allocation failed");
   // one-time zero fill of the slot and feature arrays
   CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
   if (d.nk) CUDA_OR(p, cudaMemsetAsync(p->slotCK, 0, T * SC * (size_t)d.ne, p->stream));
+  if (d.ngs()) CUDA_OR(p, cudaMemsetAsync(p->slotCS, 0, T * SCS * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
   if (mixed(p) && d.nr) {
@@ -539,7 +545,8 @@ static ba_status ensure_sstore(ba_problem* p, bool for_batch) {
   if (p->Sval) return BA_OK;
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
-  p->typed = !for_batch && d.nc > 0 && 3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
+  // spheres, cylinders and cones keep the full storage (their camera blocks are 4 to 6 wide)
+  p->typed = !for_batch && d.nc > 0 && d.ngs() == 0 && 3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
   ba_status s;
   if (p->typed) {
     TypedPlan tplan;
@@ -746,6 +753,23 @@ extern "C" ba_status ba_get_groups(ba_problem* p, int kind, int mem, double* par
   if (s) return s;
   if (kind == BA_PLANE) return put_out(p, mem, params, (const double*)p->ps[p->cur].pln, 4 * (size_t)p->d.npl);
   if (kind == BA_VP) return put_out(p, mem, params, (const double*)p->ps[p->cur].vps, 3 * (size_t)p->d.nv);
+  if (kind == BA_SPHERE || kind == BA_CYLINDER || kind == BA_CONE) {
+    // the surface records (SRF_STRIDE values) in the add layout: sphere 4, cylinder 7, cone 7 values
+    const Dims& d = p->d;
+    const int64_t g0 = kind == BA_SPHERE ? 0 : kind == BA_CYLINDER ? d.nsp : d.nsp + d.ncy;
+    const int64_t n = kind == BA_SPHERE ? d.nsp : kind == BA_CYLINDER ? d.ncy : d.nco;
+    const int w = kind == BA_SPHERE ? 4 : 7;
+    if (n == 0) return BA_OK;
+    std::vector<double> h(SRF_STRIDE * n), o(w * n);
+    ba_status st = put_out(p, BA_MEM_HOST, h.data(), (const double*)p->ps[p->cur].srf + SRF_STRIDE * g0, h.size());
+    if (st) return st;
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = 0; k < w; ++k) o[w * i + k] = h[SRF_STRIDE * i + k];
+    if (!params) return set_err(p, BA_ERR_ARG, "null output");
+    if (mem == BA_MEM_HOST) { std::memcpy(params, o.data(), o.size() * sizeof(double)); return BA_OK; }
+    CUDA_OR(p, cudaMemcpy(params, o.data(), o.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return BA_OK;
+  }
   return set_err(p, BA_ERR_ARG, "bad group kind");
 }
 
@@ -782,7 +806,7 @@ extern "C" ba_status ba_get_step_intrinsics(ba_problem* p, double* dk) {
   if (!dk) return set_err(p, BA_ERR_ARG, "null output");
   std::vector<double> x(6 * (size_t)d.nk);
   ba_status s;
-  if ((s = put_out(p, BA_MEM_HOST, x.data(), (const double*)p->x + 6 * (d.nc + d.npl + d.nv), x.size()))) return s;
+  if ((s = put_out(p, BA_MEM_HOST, x.data(), (const double*)p->x + 6 * d.kbase(), x.size()))) return s;
   for (int64_t k = 0; k < d.nk; ++k)
     for (int j = 0; j < 3; ++j) dk[3 * k + j] = x[6 * k + j];
   return BA_OK;
@@ -882,7 +906,7 @@ extern "C" ba_status ba_export_reduced_system(ba_problem* p, int32_t* row_ptr, i
   SView hv;
   if (p->typed) {
     hv.sel = hsel.data(); hv.col = pc.data(); hv.nc = d.nc; hv.npl = d.npl; hv.gg_val0 = p->gg_val0;
-    hv.kb = d.nc + d.npl + d.nv;
+    hv.kb = d.kbase();
   }
   int64_t o = 0;
   if (row_ptr) row_ptr[0] = 0;
@@ -1191,6 +1215,7 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
     ba_status s = freeze(p);
     if (!s && p->nrel) s = set_err(p, BA_ERR_ARG, "inter-group relations are not supported in batched windows");
     if (!s && p->d.nk) s = set_err(p, BA_ERR_ARG, "refined intrinsics (cam_dof 9) are not supported in batched windows");
+    if (!s && p->d.ngs()) s = set_err(p, BA_ERR_ARG, "spheres, cylinders and cones are not supported in batched windows");
     if (!s) s = ensure_sstore(p, true);
     if (s) return set_err(p0, s, "window " + std::to_string(i) + ": " + p->err);
     if (p->typed)

@@ -65,16 +65,22 @@ constexpr int SC = 20;  // camera slot: J_cam^T w J_plane (6 x 3, 18 values); in
                         // (3 x 3 in the first 9); with refined intrinsics a second camera record of this size
                         // holds J_cam^T w J_K (6 x 3) of the camera's own intrinsics entity
 constexpr int SBS = 6;  // back-substitution record per slot (6 values, unpadded: padding cost more than it saved)
+constexpr int SCS = 36; // camera slot of a feature on a sphere, cylinder or cone: J_cam^T w J_group (6 x 6, zero
+                        // beyond the group's dimensions)
 
-enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2, ENT_INTR = 3 };
-// real dimensions of an entity block: camera pose 6, plane 3, VP 2, intrinsics (f, k1, k2) 3
-__host__ __device__ __forceinline__ int ent_dims(int et) { return et == ENT_CAM ? 6 : (et == ENT_VP ? 2 : 3); }
+enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2, ENT_INTR = 3, ENT_SPHERE = 4, ENT_CYL = 5, ENT_CONE = 6 };
+// real dimensions of an entity block: camera pose 6, plane 3, VP 2, intrinsics (f, k1, k2) 3, sphere 4,
+// cylinder 5, cone 6
+__host__ __device__ __forceinline__ int ent_dims(int et) {
+  return et == ENT_CAM ? 6 : et == ENT_VP ? 2 : et == ENT_SPHERE ? 4 : et == ENT_CYL ? 5 : et == ENT_CONE ? 6 : 3;
+}
 // direct coupling carried by a slot pair (pair_b bits 30-31): none, camera-plane (the camera slot's C record),
 // camera-intrinsics (the camera slot's CK record, its own entity only), plane-intrinsics (the intrinsics slot's
 // C record, transposed)
-constexpr uint32_t PAIR_CP = 1u, PAIR_CK = 2u, PAIR_PK = 3u;
-constexpr int PAIR_SHIFT = 30;
-constexpr int32_t PAIR_SLOT = 0x3fffffff;
+// camera-surface (the camera slot's CS record: a sphere, cylinder or cone of the feature)
+constexpr uint32_t PAIR_CP = 1u, PAIR_CK = 2u, PAIR_PK = 3u, PAIR_CS = 4u;
+constexpr int PAIR_SHIFT = 29;
+constexpr int32_t PAIR_SLOT = 0x1fffffff;
 
 constexpr int PCG_FLAG_TIMEOUT = 8;   // DevScalars::flags bit: a bounded device-side wait of the PCG ran out
 
@@ -158,7 +164,11 @@ using Problem = ::ba_problem;
 
 struct Dims {
   int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
-  int64_t nk = 0;    // intrinsics entities (refined f, k1, k2; A indices nc + npl + nv + k)
+  int64_t nsp = 0, ncy = 0, nco = 0;   // spheres, cylinders, cones (A indices after the VPs, in that order)
+  int64_t nk = 0;    // intrinsics entities (refined f, k1, k2; A indices after the surface groups)
+  int64_t ngs() const { return nsp + ncy + nco; }            // surface groups
+  int64_t sbase() const { return nc + npl + nv; }            // A index of the first surface group
+  int64_t kbase() const { return nc + npl + nv + nsp + ncy + nco; }   // A index of intrinsics entity 0
   int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0;  // nbf stored blocks, nbp padded
   int64_t nun = 0, nmulti = 0;   // Schur work units of the grid path; blocks split over several units
   int64_t nun_main = 0, npack = 0;   // units a warp takes alone (the rest are packed), and the packs
@@ -208,6 +218,7 @@ struct ba_problem {
   std::vector<double> h_cam;      // n x 12: q(4) t(3) f k1 k2 ppx ppy
   std::vector<uint8_t> h_fixed;
   std::vector<double> h_pts, h_lin, h_pln, h_vps;
+  std::vector<double> h_sph, h_cyl, h_cone;   // spheres (4), cylinders (7), cones (7) as added
   std::vector<int32_t> h_rel;     // inter-group relations as added: 5 per relation (kind_a, a, kind_b, b, type)
   // shared intrinsics (ba_set_intrinsics): entity values (3 each) and every camera's entity
   std::vector<double> h_intr;
@@ -238,11 +249,13 @@ struct ba_problem {
     double *cam = nullptr, *pts = nullptr, *lin = nullptr, *pln = nullptr, *vps = nullptr;
     double* intr = nullptr;   // intrinsics entities (f, k1, k2), refined intrinsics only; each camera's f, k1, k2
                               // in cam is a copy of its entity's values
+    double* srf = nullptr;    // surface groups, SRF_STRIDE values each: sphere (c, r), cylinder (d, m, r), cone
+                              // (apex, axis, half-angle)
     double *camD = nullptr, *grpD = nullptr;   // rotation matrices / tangent bases (CAM_STRIDE / GRP_STRIDE)
   } ps[2];
   int cur = 0;
   // working-type (double or float) copies of the current parameters used by the linearisation
-  void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr;
+  void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr, *srfT = nullptr;
   uint8_t* cam_fixed = nullptr;
   int32_t* cam_k = nullptr;   // per camera its intrinsics entity (refined intrinsics only)
   // residuals, feature-major
@@ -305,6 +318,7 @@ struct ba_problem {
   // numeric arrays
   void *slotW = nullptr, *slotH = nullptr, *slotG = nullptr, *slotC = nullptr, *slotZ = nullptr, *slotB = nullptr;
   void* slotCK = nullptr;       // refined intrinsics: per camera slot J_cam^T w J_K of its own entity (SC)
+  void* slotCS = nullptr;       // surface groups: per camera slot J_cam^T w J_group of the feature's surface (SCS)
   void* slotBS = nullptr;       // back-substitution: per slot W da (4), G.da, da^T H da + 2 da^T C dplane
   double *featV = nullptr, *featg = nullptr, *featVinv = nullptr, *featu = nullptr, *featL = nullptr, *dfeat = nullptr;
   void *Sval = nullptr, *Minv = nullptr;

@@ -244,6 +244,9 @@ struct LinArgs {
   const int32_t *rslot_k, *fslot_off;   // refined intrinsics: per residual its intrinsics slot; slots per feature
   const uint8_t* slot_type;
   T* CK;                                // per camera slot J_cam^T w J_K of its own intrinsics entity
+  const T* srf;                         // surface groups (SRF_STRIDE values each; sphere, cylinder, cone)
+  T* CS;                                // per camera slot J_cam^T w J_group of the feature's surface group (SCS)
+  int64_t nsp, ncy;                     // spheres, cylinders (the surface ids of cones follow)
   const T* meas;
   const T *cam, *pts, *lin, *grp;
   int64_t npl, np;
@@ -296,9 +299,12 @@ __device__ __forceinline__ void load16(const T* __restrict__ src, T* dst) {
   for (int i = NT2; i < N; ++i) dst[i] = src[i];
 }
 
-template <class T, int KF, bool INTR = false>
+template <class T, int KF, bool INTR = false, bool SURF = false>
 __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
+  // width of the positional group's accumulators: 3 (plane), 6 when spheres, cylinders or cones may occur
+  constexpr int GW = SURF ? 6 : 3;
+  constexpr int GH = GW * (GW + 1) / 2;
   constexpr int NV = KF * (KF + 1) / 2;
   T V[NV], gf[KF];
 #pragma unroll
@@ -306,24 +312,28 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
   for (int i = 0; i < KF; ++i) gf[i] = 0;
   // current camera slot accumulators
-  T Wc[KF][6], Hc[21], Gc[6], Cc[6][3];
+  T Wc[KF][6], Hc[21], Gc[6], Cc[6][GW];
   int cur = -1;
-  // group slot accumulators: plane (3 dof), VP (2 dof, lines only)
-  T Wp[KF][3], Hp[6], Gp[3];
+  // group slot accumulators: the positional group (a plane, or a sphere / cylinder / cone: up to 6 dof), VP (2
+  // dof, lines only)
+  T Wp[KF][GW], Hp[GH], Gp[GW];
   T Wv[KF][2], Hv[3], Gv[2];
   int ps = -1, vs = -1;
 #pragma unroll
   for (int i = 0; i < KF; ++i) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Wp[i][j] = 0;
+    for (int j = 0; j < GW; ++j) Wp[i][j] = 0;
     Wv[i][0] = 0; Wv[i][1] = 0;
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) Hp[i] = 0;
-  Gp[0] = Gp[1] = Gp[2] = 0;
+  for (int i = 0; i < GH; ++i) Hp[i] = 0;
+#pragma unroll
+  for (int i = 0; i < GW; ++i) Gp[i] = 0;
   Hv[0] = Hv[1] = Hv[2] = 0;
   Gv[0] = Gv[1] = 0;
   const int plane_slot = a.feat_plane_slot[f];
+  // the positional group is a sphere, cylinder or cone (its camera couplings go to the 6 x 6 CS records)
+  const bool surf = SURF && plane_slot >= 0 && a.slot_type[plane_slot] >= ENT_SPHERE;
 
   T F[6];
   if (KF == 3) {
@@ -341,7 +351,15 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
     for (int i = 0; i < SG; ++i) gh[i] = i < HG_H ? Gc[i] : i < HG_H + 21 ? Hc[i - HG_H] : T(0);
     store16<T, SG>(a.G + (size_t)e * SG, gh);
-    if (plane_slot >= 0) {
+    if constexpr (SURF) {
+      if (surf) {
+        T cb[SCS];
+#pragma unroll
+        for (int i = 0; i < SCS; ++i) cb[i] = Cc[i / 6][i % 6];
+        store16<T, SCS>(a.CS + (size_t)e * SCS, cb);
+      }
+    }
+    if (!surf && plane_slot >= 0) {
       T cb[SC];
 #pragma unroll
       for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? Cc[i / 3][i % 3] : T(0);
@@ -358,7 +376,8 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       Gc[i] = 0;
-      Cc[i][0] = Cc[i][1] = Cc[i][2] = 0;
+#pragma unroll
+      for (int j = 0; j < GW; ++j) Cc[i][j] = 0;
     }
   };
   zero_cam();
@@ -447,6 +466,12 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
     Cam<T> c;
     if (camid >= 0) load_cam(a.cam + (size_t)CAM_STRIDE * camid, c);
     ResJ<T> o;
+    if constexpr (SURF) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o.Jg[i][k] = 0;   // a plane residual fills 3 of the 6 group columns
+    }
     int rd = res_dim(kind);
     bool has_plane = false, has_vp = false;
     if (KF == 3) {
@@ -454,6 +479,9 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       else if (kind == R_PLANE_POINT) { res_plane_point<T, true, INTR>(c, F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
       else if (kind == R_P2L) res_p2l<T, true, INTR>(c, F, meas, o);
       else if (kind == R_PLANE_POINT3) { res_plane_point3<T, true>(F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
+      else if (SURF && kind == R_SPHERE_POINT) { res_surface_point<T, true, 0>(c, F, a.srf + (size_t)SRF_STRIDE * gid, o); has_plane = true; }
+      else if (SURF && kind == R_CYL_POINT) { res_surface_point<T, true, 1>(c, F, a.srf + (size_t)SRF_STRIDE * (a.nsp + gid), o); has_plane = true; }
+      else if (SURF && kind == R_CONE_POINT) { res_surface_point<T, true, 2>(c, F, a.srf + (size_t)SRF_STRIDE * (a.nsp + a.ncy + gid), o); has_plane = true; }
       else continue;
     } else {
       if (kind == R_LINE) res_line<T, true, INTR>(c, F, meas, o);
@@ -484,13 +512,13 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (i >= rd) break;
-      T wf[KF], wc[6], wg[3];
+      T wf[KF], wc[6], wg[GW];
 #pragma unroll
       for (int k = 0; k < KF; ++k) wf[k] = om * o.Jf[i][k];
 #pragma unroll
       for (int k = 0; k < 6; ++k) wc[k] = om * o.Jc[i][k];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) wg[k] = om * o.Jg[i][k];
+      for (int k = 0; k < GW; ++k) wg[k] = om * o.Jg[i][k];
       const T ri = o.r[i];
       // V_f and g_f
 #pragma unroll
@@ -514,18 +542,18 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
           for (int p = 0; p < 6; ++p)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) Cc[p][q] += wc[p] * o.Jg[i][q];
+            for (int q = 0; q < GW; ++q) Cc[p][q] += wc[p] * o.Jg[i][q];
       }
       if (has_plane) {
 #pragma unroll
         for (int p = 0; p < KF; ++p)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) Wp[p][q] += wf[p] * o.Jg[i][q];
+          for (int q = 0; q < GW; ++q) Wp[p][q] += wf[p] * o.Jg[i][q];
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
+        for (int p = 0; p < GW; ++p) {
           Gp[p] += wg[p] * ri;
 #pragma unroll
-          for (int q = p; q < 3; ++q) Hp[up_idx(p, q, 3)] += wg[p] * o.Jg[i][q];
+          for (int q = p; q < GW; ++q) Hp[up_idx(p, q, GW)] += wg[p] * o.Jg[i][q];
         }
       }
       if (KF == 4 && has_vp) {
@@ -580,12 +608,13 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   }
   if (cur >= 0) flush(cur);
   // group slots, padded to the 6-wide block of the reduced system
-  auto put_group = [&](int e, int nd, const T* Wg, const T* Hg, const T* Gg) {
+  // W (stride ws per feature row) and the upper H (dimension hd) of a group slot; nd real dimensions
+  auto put_group = [&](int e, int nd, const T* Wg, int ws, const T* Hg, int hd, const T* Gg) {
     T wb[KF * 6], gh[SG];   // W; G (6), H (21), pad
 #pragma unroll
     for (int i = 0; i < KF; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) wb[i * 6 + j] = j < nd ? Wg[i * nd + j] : T(0);
+      for (int j = 0; j < 6; ++j) wb[i * 6 + j] = j < nd ? Wg[i * ws + j] : T(0);
 #pragma unroll
     for (int i = 0; i < SG; ++i) gh[i] = T(0);
 #pragma unroll
@@ -594,19 +623,19 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int j = i; j < 6; ++j)
-        if (j < nd) gh[HG_H + up_idx(i, j, 6)] = Hg[up_idx(i, j, nd)];
+        if (j < nd) gh[HG_H + up_idx(i, j, 6)] = Hg[up_idx(i, j, hd)];
     store16<T, KF * 6>(a.W + (size_t)e * SW, wb);
     store16<T, SG>(a.G + (size_t)e * SG, gh);
   };
   if (ps < 0) ps = plane_slot;  // a plane slot whose residuals were all invalid
-  if (ps >= 0) put_group(ps, 3, &Wp[0][0], Hp, Gp);
+  if (ps >= 0) put_group(ps, SURF ? ent_dims(a.slot_type[ps]) : 3, &Wp[0][0], GW, Hp, GW, Gp);
   if (KF == 4) {
     if (vs < 0) {
       // find the VP slot (if any) among this feature's residuals
       for (int rr = r0; rr < r1; ++rr)
         if (a.rkind[rr] == R_VP) { vs = a.rslot_g[rr]; break; }
     }
-    if (vs >= 0) put_group(vs, 2, &Wv[0][0], Hv, Gv);
+    if (vs >= 0) put_group(vs, 2, &Wv[0][0], 2, Hv, 2, Gv);
   }
   double vb[NV], gbf[KF];
 #pragma unroll
@@ -617,10 +646,10 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   store16<double, KF>(a.g + 4 * f, gbf);
 }
 
-template <class T, int KF, bool INTR = false>
+template <class T, int KF, bool INTR = false, bool SURF = false>
 __global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int64_t f1) {
   int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f < f1) linearize_feature<T, KF, INTR>(a, f);
+  if (f < f1) linearize_feature<T, KF, INTR, SURF>(a, f);
 }
 
 // ============================================================================
@@ -848,6 +877,7 @@ struct UnitArgs {
   const int4* pk_desc;      // per pack of small units: first unit (processing order), units, first pair, pairs
   const T *Z, *H, *B, *C;
   const T* CK;     // refined intrinsics: per camera slot J_cam^T w J_K of its own entity (or null)
+  const T* CS;     // surface groups: per camera slot J_cam^T w J_group of the feature's sphere / cylinder / cone
   double* upart;   // 48 per unit: 36 S, 6 b, 6 diag(H)
   int64_t nun, nmulti, nun_main, npack;
   int line_slot0;
@@ -1086,6 +1116,13 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
         for (int i = 0; i < 6; ++i)
 #pragma unroll
           for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+      } else if (code == PAIR_CS) {
+        // the camera's direct block with the feature's sphere, cylinder or cone (6 x 6, zeros beyond its dims)
+        const T* Cm = a.CS + (size_t)ea * SCS;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += Cm[i * 6 + j] - pair_dot(za, zb, i, j, line);
       } else if (code == PAIR_PK) {
         // plane-intrinsics: the intrinsics slot holds J_K^T w J_plane (3 x 3); this block is its transpose
         const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
@@ -2596,6 +2633,7 @@ struct BackArgs {
   const double *V, *Vinv, *g, *x;
   const T *W, *H, *G, *C;
   const T* CK;              // refined intrinsics: camera slots' blocks with their own entity (else null)
+  const T* CS;              // surface groups: camera slots' blocks with the feature's sphere / cylinder / cone
   const int32_t* cam_k;     // refined intrinsics: per camera its entity (else null)
   int64_t kbase;            // A index of intrinsics entity 0
   T* sv;        // per slot: W_e da (4, zero-padded), G_e . da, da^T H_e da + 2 da^T C_e dplane
@@ -2646,7 +2684,16 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
   }
   T cpl = 0;
   const int pslot = a.feat_plane_slot[f];
-  if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {   // camera-plane direct block of a plane feature
+  if (pslot >= 0 && a.slot_type[e] == ENT_CAM && a.slot_type[pslot] >= ENT_SPHERE) {
+    // camera-surface direct block of a feature on a sphere, cylinder or cone (6 x 6, zeros beyond its dims)
+    const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
+    T Cm[36];
+    load16<T, 36>(a.CS + (size_t)e * SCS, Cm);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) cpl += dv[i] * Cm[i * 6 + j] * (T)dp[j];
+  } else if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {   // camera-plane direct block of a plane feature
     const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
     const T dpl[3] = {(T)dp[0], (T)dp[1], (T)dp[2]};
     T Cm[18];
@@ -2792,11 +2839,42 @@ struct CandArgs {
   double* intr2;
   const int32_t* cam_k;
   int64_t nk, kbase;
+  // surface groups (else none): spheres, cylinders, cones (SRF_STRIDE values each), A index of the first
+  const double* srf;
+  double* srf2;
+  int64_t nsp, ncy, nco, sbase;
 };
 
-// items: cameras, planes, VPs, points, lines, then the intrinsics entities
+// the orthonormal update of a Pluecker line (d, m), |d| = 1: U <- U Exp(dl[0:3]), phi <- phi + dl[3]
+__device__ void line_retract(const double* L, const double* dl, double* o);
+
+// items: cameras, planes, VPs, points, lines, the intrinsics entities, then the surface groups
 __device__ void candidate_item(const CandArgs& a, int64_t i) {
   const int64_t n0 = a.nc, n1 = n0 + a.npl, n2 = n1 + a.nv, n3 = n2 + a.np;
+  if (i >= n3 + a.nl + a.nk) {
+    // sphere (c + dc, r exp(ds)), cylinder (line update of the axis, r exp(ds)), cone (a + da, axis on S^2,
+    // half-angle + d)
+    const int64_t g = i - n3 - a.nl - a.nk;
+    const double* G = a.srf + SRF_STRIDE * g;
+    double* o = a.srf2 + SRF_STRIDE * g;
+    const double* dl = a.x + 6 * (a.sbase + g);
+    for (int k = 0; k < SRF_STRIDE; ++k) o[k] = G[k];
+    if (g < a.nsp) {
+      for (int k = 0; k < 3; ++k) o[k] = G[k] + dl[k];
+      o[3] = G[3] * exp(dl[3]);
+    } else if (g < a.nsp + a.ncy) {
+      line_retract(G, dl, o);
+      o[6] = G[6] * exp(dl[4]);
+    } else {
+      for (int k = 0; k < 3; ++k) o[k] = G[k] + dl[k];
+      double b1[3], b2[3], v[3];
+      tangent_basis_d(G + 3, b1, b2);
+      for (int k = 0; k < 3; ++k) v[k] = dl[3] * b1[k] + dl[4] * b2[k];
+      s2_exp(G + 3, v, o + 3);
+      o[6] = G[6] + dl[5];
+    }
+    return;
+  }
   if (i >= n3 + a.nl) {
     // intrinsics entity: additive (f, k1, k2)
     const int64_t k = i - n3 - a.nl;
@@ -2861,31 +2939,34 @@ __device__ void candidate_item(const CandArgs& a, int64_t i) {
     int64_t f = i - n2;
     for (int k = 0; k < 3; ++k) a.pts2[3 * f + k] = a.pts[3 * f + k] + a.df[4 * f + k];
   } else {
-    int64_t l = i - n3;
-    const double* L = a.lin + 6 * l;
-    const double* dl = a.df + 4 * (a.np + l);
-    double u1[3], u3[3], r;
-    line_frame<double>(L, L + 3, u1, u3, r);
-    double E[9];
-    so3_exp(dl, E);
-    // U = [u1, d, u3] (columns); U' = U E
-    double U[9] = {u1[0], L[0], u3[0], u1[1], L[1], u3[1], u1[2], L[2], u3[2]};
-    double Un[9];
-    for (int rr = 0; rr < 3; ++rr)
-      for (int s = 0; s < 3; ++s) Un[3 * rr + s] = U[3 * rr] * E[s] + U[3 * rr + 1] * E[3 + s] + U[3 * rr + 2] * E[6 + s];
-    double phi = atan2(1.0, r) + dl[3];
-    double ct = cos(phi) / sin(phi);
-    double* o = a.lin2 + 6 * l;
-    for (int k = 0; k < 3; ++k) {
-      o[k] = Un[3 * k + 1];
-      o[3 + k] = ct * Un[3 * k + 0];
-    }
+    const int64_t l = i - n3;
+    line_retract(a.lin + 6 * l, a.df + 4 * (a.np + l), a.lin2 + 6 * l);
   }
+}
+
+__device__ void line_retract(const double* L, const double* dl, double* o) {
+  double u1[3], u3[3], r;
+  line_frame<double>(L, L + 3, u1, u3, r);
+  double E[9];
+  so3_exp(dl, E);
+  // U = [u1, d, u3] (columns); U' = U E
+  double U[9] = {u1[0], L[0], u3[0], u1[1], L[1], u3[1], u1[2], L[2], u3[2]};
+  double Un[9];
+  for (int rr = 0; rr < 3; ++rr)
+    for (int s = 0; s < 3; ++s) Un[3 * rr + s] = U[3 * rr] * E[s] + U[3 * rr + 1] * E[3 + s] + U[3 * rr + 2] * E[6 + s];
+  double phi = atan2(1.0, r) + dl[3];
+  double ct = cos(phi) / sin(phi);
+  double d[3], m[3];   // computed in full before writing: o may alias nothing the caller still reads
+  for (int k = 0; k < 3; ++k) {
+    d[k] = Un[3 * k + 1];
+    m[k] = ct * Un[3 * k + 0];
+  }
+  for (int k = 0; k < 3; ++k) { o[k] = d[k]; o[3 + k] = m[k]; }
 }
 
 __global__ void k_candidate(CandArgs a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < a.nc + a.npl + a.nv + a.np + a.nl + a.nk) candidate_item(a, i);
+  if (i < a.nc + a.npl + a.nv + a.np + a.nl + a.nk + a.nsp + a.ncy + a.nco) candidate_item(a, i);
 }
 
 // ---- ln(1 + x) for the FP64 cost, table-driven after P. T. P. Tang, "Table-driven implementation of the
@@ -2967,7 +3048,8 @@ struct CostArgs {
   const int8_t* rkind;
   const int32_t *rcam, *rfeat, *rgrp, *order;
   const double *meas, *camD, *grpD, *pts, *lin;
-  int64_t nr, np, npl;
+  const double* srf;   // surface groups (spheres, cylinders, cones)
+  int64_t nr, np, npl, nsp, ncy;
   LossW loss;
   DevScalars* S;
   double* red;
@@ -2998,6 +3080,9 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
       case R_L2P: res_l2p<double, false>(c, L, meas, o); break;
       case R_PLANE_POINT3: res_plane_point3<double, false>(X, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
       case R_PLANE_LINE3: res_plane_line3<double, false>(L, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
+      case R_SPHERE_POINT: res_surface_point<double, false, 0>(c, X, a.srf + (size_t)SRF_STRIDE * gid, o); break;
+      case R_CYL_POINT: res_surface_point<double, false, 1>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + gid), o); break;
+      case R_CONE_POINT: res_surface_point<double, false, 2>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + a.ncy + gid), o); break;
     }
     if (o.valid) {
       double s = 0;
@@ -3127,6 +3212,10 @@ void launch_prepare(Problem& P, bool candidate_only) {
   if (d.nc) { ++P.launches; k_derive_cams<T><<<nblk(d.nc, 128), 128, 0, P.stream>>>(d.nc, cs.cam, cs.camD, camW); }
   if (d.npl + d.nv) { ++P.launches; k_derive_groups<T><<<nblk(d.npl + d.nv, 128), 128, 0, P.stream>>>(d.npl, d.nv, cs.pln, cs.vps, cs.grpD, grpW); }
   if (!candidate_only && sizeof(T) == sizeof(float)) {
+    if (d.ngs()) {
+      ++P.launches;
+      k_convert<<<nblk(SRF_STRIDE * d.ngs(), 256), 256, 0, P.stream>>>(SRF_STRIDE * d.ngs(), cs.srf, (float*)P.srfT);
+    }
     if (d.np) { ++P.launches; k_convert<<<nblk(3 * d.np, 256), 256, 0, P.stream>>>(3 * d.np, cs.pts, (float*)P.ptsT); }
     if (d.nl) { ++P.launches; k_convert<<<nblk(6 * d.nl, 256), 256, 0, P.stream>>>(6 * d.nl, cs.lin, (float*)P.linT); }
   }
@@ -3150,6 +3239,14 @@ void launch_linearize(Problem& P) {
   a.V = P.featV; a.g = P.featg;
   a.loss = make_loss(P.opt);
   a.rslot_k = P.rslot_k; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = (T*)P.slotCK;
+  a.srf = dbl ? (const T*)cs.srf : (const T*)P.srfT; a.CS = (T*)P.slotCS; a.nsp = d.nsp; a.ncy = d.ncy;
+  if (d.ngs()) {
+    // spheres, cylinders, cones: the points' positional groups take up to 6 dimensions (refined intrinsics are
+    // refused together with them)
+    if (d.np) { ++P.launches; k_linearize<T, 3, false, true><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
+    if (d.nl) { ++P.launches; k_linearize<T, 4><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
+    return;
+  }
   if (d.nk) {
     // refined intrinsics: the feature's intrinsics slots and the camera slots' couplings with them too
     if (d.np) { ++P.launches; k_linearize<T, 3, true><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
@@ -3183,7 +3280,8 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   un.un_se = P.un_se; un.un_blk = P.un_blk; un.un_order = P.un_order; un.up_un = P.up_un; un.multi = P.multi_blk;
   un.un_desc = reinterpret_cast<const int4*>(P.un_desc); un.un_mflag = P.un_mflag;
   un.pair_a = P.pair_a; un.pair_b = P.pair_b; un.Z = (const T*)P.slotZ; un.H = (const T*)P.slotH;
-  un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.CK = (const T*)P.slotCK; un.upart = P.upart;
+  un.B = (const T*)P.slotB; un.C = (const T*)P.slotC; un.CK = (const T*)P.slotCK; un.CS = (const T*)P.slotCS;
+  un.upart = P.upart;
   un.nun = d.nun; un.nmulti = d.nmulti;
   un.pk_desc = reinterpret_cast<const int4*>(P.pk_desc); un.nun_main = d.nun_main; un.npack = d.npack;
   un.line_slot0 = P.line_slot0; un.fb = b;
@@ -3340,7 +3438,7 @@ void launch_backsub(Problem& P) {
   a.slot_type = P.slot_type; a.V = P.featV; a.Vinv = P.featVinv; a.g = P.featg; a.x = P.x;
   a.W = (const T*)P.slotW; a.H = (const T*)P.slotH; a.G = (const T*)P.slotG; a.C = (const T*)P.slotC;
   a.sv = (T*)P.slotBS; a.df = P.dfeat; a.np = d.np; a.nf = d.nf; a.ne = d.ne; a.S = P.S; a.red = P.red;
-  a.CK = (const T*)P.slotCK; a.cam_k = d.nk ? P.cam_k : nullptr; a.kbase = d.nc + d.npl + d.nv;
+  a.CK = (const T*)P.slotCK; a.cam_k = d.nk ? P.cam_k : nullptr; a.kbase = d.kbase(); a.CS = (const T*)P.slotCS;
   if (d.ne) { ++P.launches; k_backsub_slots<T><<<nblk(d.ne, 128), 128, 0, P.stream>>>(a); }
   ++P.launches;
   k_backsub<T><<<nblk(d.nf > 0 ? d.nf : 1, 128), 128, 0, P.stream>>>(a);
@@ -3354,8 +3452,9 @@ void launch_candidate(Problem& P) {
   a.cam = c.cam; a.pts = c.pts; a.lin = c.lin; a.pln = c.pln; a.vps = c.vps; a.x = P.x; a.df = P.dfeat;
   a.fixed = P.cam_fixed; a.cam2 = n.cam; a.pts2 = n.pts; a.lin2 = n.lin; a.pln2 = n.pln; a.vps2 = n.vps;
   a.nc = d.nc; a.np = d.np; a.nl = d.nl; a.npl = d.npl; a.nv = d.nv;
-  a.intr = c.intr; a.intr2 = n.intr; a.cam_k = P.cam_k; a.nk = d.nk; a.kbase = d.nc + d.npl + d.nv;
-  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl + d.nk;
+  a.intr = c.intr; a.intr2 = n.intr; a.cam_k = P.cam_k; a.nk = d.nk; a.kbase = d.kbase();
+  a.srf = c.srf; a.srf2 = n.srf; a.nsp = d.nsp; a.ncy = d.ncy; a.nco = d.nco; a.sbase = d.sbase();
+  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl + d.nk + d.ngs();
   if (tot) { ++P.launches; k_candidate<<<nblk(tot, 128), 128, 0, P.stream>>>(a); }
 }
 
@@ -3364,8 +3463,9 @@ void launch_cost(Problem& P, bool candidate) {
   auto& s = P.ps[candidate ? 1 - P.cur : P.cur];
   CostArgs a;
   a.rkind = P.rkind; a.rcam = P.rcam; a.rfeat = P.rfeat; a.rgrp = P.rgrp; a.meas = P.meas64; a.order = P.cost_order;
-  a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin;
-  a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
+  a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin; a.srf = s.srf;
+  a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.nsp = d.nsp; a.ncy = d.ncy;
+  a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
   a.candidate = candidate ? 1 : 0;
   ++P.launches;
   k_cost<<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
@@ -3728,6 +3828,7 @@ void fill_window_desc(Problem& P, void* out) {
   a.W = (T*)P.slotW; a.H = (T*)P.slotH; a.G = (T*)P.slotG; a.C = (T*)P.slotC; a.V = P.featV; a.g = P.featg;
   a.loss = make_loss(P.opt);
   a.rslot_k = nullptr; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = nullptr;
+  a.srf = nullptr; a.CS = nullptr; a.nsp = a.ncy = 0;
   InvArgs<T>& ia = W.inv;
   ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
   ia.slot_feat = P.slot_feat; ia.Vinv = P.featVinv; ia.u = P.featu; ia.L = P.featL; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB;
@@ -3739,13 +3840,15 @@ void fill_window_desc(Problem& P, void* out) {
   k.V = P.featV; k.Vinv = P.featVinv; k.g = P.featg; k.x = P.x; k.W = (const T*)P.slotW; k.H = (const T*)P.slotH;
   k.G = (const T*)P.slotG; k.C = (const T*)P.slotC; k.df = P.dfeat; k.np = d.np; k.nf = d.nf; k.S = P.S; k.red = P.red;
   k.slot_feat = P.slot_feat; k.sv = (T*)P.slotBS; k.ne = d.ne;
-  k.CK = nullptr; k.cam_k = nullptr; k.kbase = 0;
+  k.CK = nullptr; k.cam_k = nullptr; k.kbase = 0; k.CS = nullptr;
   CandArgs& c = W.cand;
   c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
   c.intr = nullptr; c.intr2 = nullptr; c.cam_k = nullptr; c.nk = 0; c.kbase = 0;   // windows: no refined intrinsics
+  c.srf = nullptr; c.srf2 = nullptr; c.nsp = c.ncy = c.nco = 0; c.sbase = 0;        // nor surface groups
   CostArgs& co = W.cost;
   co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64; co.order = P.cost_order;
   co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;
+  co.srf = nullptr; co.nsp = co.ncy = 0;
   W.dec = DecideArgs{P.S, P.opt.min_gain, P.opt.lambda_min, P.opt.lambda_max};
   for (int s = 0; s < 2; ++s) {
     W.cam[s] = P.ps[s].cam; W.pts[s] = P.ps[s].pts; W.lin_[s] = P.ps[s].lin; W.pln[s] = P.ps[s].pln;

@@ -22,6 +22,8 @@
 //   R5 VP angular               Eq. 6 written as the 3-vector d x v
 //   R6 wireframe point->line    Eq. 11 (pinhole pixels)
 //   R7 wireframe line->point    Eq. 12 (pinhole pixels)
+//   sphere / cylinder / cone point residuals: Eq. 7 with the projections of Appendix B (radial onto a sphere;
+//   radial about a cylinder's axis; onto a cone along the normal of its generatrix)
 //   3D point-to-plane and line-to-plane distances: the direct 3D form of the plane constraint that Section 3.2
 //   sets against the group-induced residuals (Table 5 weighs it); no camera, not in the pixel cost
 // Lines and the wireframe terms live in undistorted pixel coordinates; only R1
@@ -36,14 +38,18 @@ namespace ba {
 
 enum ResKind : int {
   R_POINT = 0, R_LINE = 1, R_PLANE_POINT = 2, R_PLANE_LINE = 3, R_VP = 4, R_P2L = 5, R_L2P = 6,
-  R_PLANE_POINT3 = 7, R_PLANE_LINE3 = 8   // the direct 3D plane distances (no camera)
+  R_PLANE_POINT3 = 7, R_PLANE_LINE3 = 8,   // the direct 3D plane distances (no camera)
+  R_SPHERE_POINT = 9, R_CYL_POINT = 10, R_CONE_POINT = 11   // group-induced point residuals of other group types
 };
-constexpr int N_KINDS = 9;
+constexpr int N_KINDS = 12;
 
 __host__ __device__ constexpr int res_dim(int k) {
   return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3
-       : k == R_PLANE_LINE3 ? 2 : 1;
+       : k == R_PLANE_LINE3 ? 2 : k >= R_SPHERE_POINT ? 2 : 1;
 }
+// surface group types (sphere, cylinder, cone): 8 raw values per group, increments of 4, 5 and 6
+constexpr int SRF_STRIDE = 8;
+__host__ __device__ constexpr int srf_dims(int ty) { return ty == 0 ? 4 : (ty == 1 ? 5 : 6); }
 // kinds with a camera (the others: the VP term and the direct 3D plane distances)
 __host__ __device__ constexpr bool res_has_cam(int k) { return k != R_VP && k != R_PLANE_POINT3 && k != R_PLANE_LINE3; }
 // kinds in the pixel cost E_px
@@ -108,7 +114,7 @@ struct ResJ {
   T r[4];
   T Jc[4][6];
   T Jf[4][4];
-  T Jg[4][3];
+  T Jg[4][6];   // w.r.t. the group's increments (plane 3, VP 2, sphere 4, cylinder 5, cone 6)
   T Jk[4][3];   // w.r.t. the camera's (f, k1, k2), filled only when asked for (INTR)
   bool valid;
 };
@@ -534,6 +540,184 @@ __device__ void res_vp(const T* L, const T* V, ResJ<T>& o) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) o.Jc[i][k] = 0;
     if (INTR) { o.Jk[i][0] = 0; o.Jk[i][1] = 0; o.Jk[i][2] = 0; }
+  }
+}
+
+// ---------------------------------------------------------------- sphere, cylinder, cone (Appendix B)
+// Projection Xp of X onto the surface and its directional derivative dXp for a change dX of X and a change of
+// the group along increment k (k < 0: none).  Sphere (c, r): Xp = c + r u/|u|, u = X - c; increments dc (3),
+// d log r.  Cylinder (axis d, m with |d| = 1, radius r): foot p0 = d x m, v = X - p0, Xp = p0 + (v.d) d + r w/|w|
+// with w the radial part of v; increments: the line update of the axis (4), d log r.  Cone (apex a, unit axis
+// d, half-angle al): v = X - a, e the radial unit of v, generatrix g = cos(al) d + sin(al) e, Xp = a + (v.g) g;
+// increments da (3), the axis along the tangent basis (2), d al.
+template <class T>
+struct SurfFrame {
+  T Xp[3];
+  T a[3], d[3], m[3], r, v[3], h, w[3], rho, e[3], g[3], t, ca, sa;   // the quantities the derivatives reuse
+  T u1[3], u3[3], lr, b1[3], b2[3];                                     // axis frames (cylinder; cone)
+};
+
+template <class T, int TY>
+__device__ __forceinline__ void surf_frame(const T* G, const T* X, SurfFrame<T>& s) {
+  if (TY == 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s.a[i] = G[i]; s.v[i] = X[i] - G[i]; }
+    s.r = G[3];
+    s.rho = sqrt_t(dot3(s.v, s.v));
+    const T ir = T(1) / s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s.e[i] = s.v[i] * ir; s.Xp[i] = s.a[i] + s.r * s.e[i]; }
+  } else if (TY == 1) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s.d[i] = G[i]; s.m[i] = G[3 + i]; }
+    s.r = G[6];
+    cross3(s.d, s.m, s.a);   // foot p0
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s.v[i] = X[i] - s.a[i];
+    s.h = dot3(s.v, s.d);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s.w[i] = s.v[i] - s.h * s.d[i];
+    s.rho = sqrt_t(dot3(s.w, s.w));
+    const T ir = T(1) / s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s.e[i] = s.w[i] * ir; s.Xp[i] = s.a[i] + s.h * s.d[i] + s.r * s.e[i]; }
+    line_frame(s.d, s.m, s.u1, s.u3, s.lr);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s.a[i] = G[i]; s.d[i] = G[3 + i]; s.v[i] = X[i] - G[i]; }
+    s.ca = cos((double)G[6]); s.sa = sin((double)G[6]);
+    s.h = dot3(s.v, s.d);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s.w[i] = s.v[i] - s.h * s.d[i];
+    s.rho = sqrt_t(dot3(s.w, s.w));
+    const T ir = T(1) / s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s.e[i] = s.w[i] * ir; s.g[i] = s.ca * s.d[i] + s.sa * s.e[i]; }
+    s.t = dot3(s.v, s.g);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s.Xp[i] = s.a[i] + s.t * s.g[i];
+    tangent_b1(s.d, s.b1);
+    cross3(s.d, s.b1, s.b2);
+  }
+}
+
+// dXp for a change dX of the point (grp = -1) or along group increment grp (dX ignored)
+template <class T, int TY>
+__device__ __forceinline__ void surf_dir(const SurfFrame<T>& s, const T* dX, int grp, T* o) {
+  if (TY == 0) {
+    // Xp = c + r e: de = (du - e (e.du)) / |u|, du = dX - dc
+    T du[3] = {T(0), T(0), T(0)}, dc[3] = {T(0), T(0), T(0)}, ds = 0;
+    if (grp < 0) { du[0] = dX[0]; du[1] = dX[1]; du[2] = dX[2]; }
+    else if (grp < 3) { dc[grp] = T(1); du[grp] = T(-1); }
+    else ds = T(1);
+    const T ed = dot3(s.e, du), ir = T(1) / s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i] = dc[i] + s.r * (du[i] - s.e[i] * ed) * ir + s.r * ds * s.e[i];
+  } else if (TY == 1) {
+    T dXv[3] = {T(0), T(0), T(0)}, zeta[3] = {T(0), T(0), T(0)}, mu[3] = {T(0), T(0), T(0)}, ds = 0;
+    if (grp < 0) { dXv[0] = dX[0]; dXv[1] = dX[1]; dXv[2] = dX[2]; }
+    else if (grp < 4) {
+      T dd[4][3], dm[4][3];
+      line_dirs(s.d, s.u1, s.u3, s.lr, dd, dm);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { zeta[i] = dd[grp][i]; mu[i] = dm[grp][i]; }
+    } else ds = T(1);
+    T dp0[3], t1[3], t2[3];
+    cross3(zeta, s.m, t1);
+    cross3(s.d, mu, t2);
+    T dv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { dp0[i] = t1[i] + t2[i]; dv[i] = dXv[i] - dp0[i]; }
+    const T dh = dot3(dv, s.d) + dot3(s.v, zeta);
+    T dw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dw[i] = dv[i] - dh * s.d[i] - s.h * zeta[i];
+    const T ed = dot3(s.e, dw), ir = T(1) / s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      o[i] = dp0[i] + dh * s.d[i] + s.h * zeta[i] + s.r * (dw[i] - s.e[i] * ed) * ir + s.r * ds * s.e[i];
+  } else {
+    T dXv[3] = {T(0), T(0), T(0)}, da[3] = {T(0), T(0), T(0)}, dd[3] = {T(0), T(0), T(0)}, dal = 0;
+    if (grp < 0) { dXv[0] = dX[0]; dXv[1] = dX[1]; dXv[2] = dX[2]; }
+    else if (grp < 3) da[grp] = T(1);
+    else if (grp == 3) { dd[0] = s.b1[0]; dd[1] = s.b1[1]; dd[2] = s.b1[2]; }
+    else if (grp == 4) { dd[0] = s.b2[0]; dd[1] = s.b2[1]; dd[2] = s.b2[2]; }
+    else dal = T(1);
+    T dv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dv[i] = dXv[i] - da[i];
+    const T dh = dot3(dv, s.d) + dot3(s.v, dd);
+    T dw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dw[i] = dv[i] - dh * s.d[i] - s.h * dd[i];
+    const T ed = dot3(s.e, dw), ir = T(1) / s.rho;
+    T dg[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T de = (dw[i] - s.e[i] * ed) * ir;
+      dg[i] = -s.sa * dal * s.d[i] + s.ca * dd[i] + s.ca * dal * s.e[i] + s.sa * de;
+    }
+    const T dt = dot3(dv, s.g) + dot3(s.v, dg);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i] = da[i] + dt * s.g[i] + s.t * dg[i];
+  }
+}
+
+// the group-induced point residual of a sphere (TY 0), cylinder (1) or cone (2): pi(C, X) - pi(C, Proj(X))
+template <class T, bool JAC, int TY, bool INTR = false>
+__device__ void res_surface_point(const Cam<T>& c, const T* X, const T* G, ResJ<T>& o) {
+  SurfFrame<T> s;
+  surf_frame<T, TY>(G, X, s);
+  T p1[3], p2[3], x1[3], x2[3], pi1[2], pi2[2], J1[2][3], J2[2][3];
+  matvec3(c.R, X, p1);
+  matvec3(c.R, s.Xp, p2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { x1[i] = p1[i] + c.t[i]; x2[i] = p2[i] + c.t[i]; }
+  o.valid = (double)x1[2] > 1e-6 && (double)x2[2] > 1e-6;
+  if (!o.valid) return;
+  project_dist<T, JAC>(c, x1, pi1, J1);
+  project_dist<T, JAC>(c, x2, pi2, J2);
+  o.r[0] = pi1[0] - pi2[0];
+  o.r[1] = pi1[1] - pi2[1];
+  if (!JAC) return;
+  constexpr int ND = srf_dims(TY);
+  T g1[2][3], g2[2][3];   // d pi / d X in world coordinates
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    T a6[6], b6[6];
+    pose_row_point(p1, J1[i], a6);
+    pose_row_point(p2, J2[i], b6);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.Jc[i][k] = a6[k] - b6[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      g1[i][k] = J1[i][0] * c.R[k] + J1[i][1] * c.R[3 + k] + J1[i][2] * c.R[6 + k];
+      g2[i][k] = J2[i][0] * c.R[k] + J2[i][1] * c.R[3 + k] + J2[i][2] * c.R[6 + k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T ek[3] = {T(0), T(0), T(0)}, dp[3];
+    ek[k] = T(1);
+    surf_dir<T, TY>(s, ek, -1, dp);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) o.Jf[i][k] = g1[i][k] - dot3(g2[i], dp);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T dp[3] = {T(0), T(0), T(0)};
+    if (k < ND) surf_dir<T, TY>(s, X, k, dp);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) o.Jg[i][k] = k < ND ? -dot3(g2[i], dp) : T(0);
+  }
+  if (INTR) {
+    T K1[2][3], K2[2][3];
+    project_dist_k(c, x1, K1);
+    project_dist_k(c, x2, K2);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o.Jk[i][k] = K1[i][k] - K2[i][k];
   }
 }
 

@@ -284,7 +284,20 @@ struct SlotArgs {
   int* err;   // bit 0: two planes on one feature, bit 1: two VPs on one line
   const int32_t* cam_k;   // refined intrinsics: per camera its intrinsics entity (else null)
   int64_t kbase;          // A index of intrinsics entity 0
+  int64_t sbase, nsp, ncy;   // A index of the first sphere; spheres, cylinders (cones follow)
 };
+
+// the positional group of residual record i as an A index (plane, sphere, cylinder, cone), or -1
+__device__ __forceinline__ int64_t pos_group(const SlotArgs& a, int k, int32_t g) {
+  if (k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3) return a.nc + g;
+  if (k == R_SPHERE_POINT) return a.sbase + g;
+  if (k == R_CYL_POINT) return a.sbase + a.nsp + g;
+  if (k == R_CONE_POINT) return a.sbase + a.nsp + a.ncy + g;
+  return -1;
+}
+__device__ __forceinline__ uint8_t pos_type(const SlotArgs& a, int64_t e) {
+  return e < a.sbase ? ENT_PLANE : e < a.sbase + a.nsp ? ENT_SPHERE : e < a.sbase + a.nsp + a.ncy ? ENT_CYL : ENT_CONE;
+}
 
 // intrinsics entity of residual j of a feature (-1: none)
 __device__ __forceinline__ int slot_intr(const SlotArgs& a, int32_t j) {
@@ -298,16 +311,18 @@ __device__ __forceinline__ int slot_intr(const SlotArgs& a, int32_t j) {
 __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
   const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.nf) return;
-  int n = 0, prev = -1, plane = -1, vp = -1;
+  int n = 0, prev = -1, vp = -1;
+  int64_t plane = -1;   // the positional group (A index)
   const int32_t r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   for (int32_t j = r0; j < r1; ++j) {
     const int32_t i = a.order[j];
     const int c = a.cam[i];
     if (c >= 0 && a.fixed[c] != 0x3F && c != prev) { ++n; prev = c; }
     const int k = a.kind[i];
-    if (k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3) {
-      if (plane >= 0 && plane != a.grp[i]) atomicOr(a.err, 1);
-      plane = a.grp[i];
+    const int64_t pg = pos_group(a, k, a.grp[i]);
+    if (pg >= 0) {
+      if (plane >= 0 && plane != pg) atomicOr(a.err, 1);
+      plane = pg;
     } else if (k == R_VP) {
       if (vp >= 0 && vp != a.grp[i]) atomicOr(a.err, 2);
       vp = a.grp[i];
@@ -335,12 +350,14 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
   if (f == a.nf) return;
   const int32_t r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   int32_t e = (int32_t)soff[f];
-  int prev = -1, plane = -1, vp = -1;
+  int prev = -1, vp = -1;
+  int64_t plane = -1;   // the positional group (A index)
   for (int32_t j = r0; j < r1; ++j) {
     const int32_t i = a.order[j];
     const int c = a.cam[i];
     const int k = a.kind[i];
-    if (k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3) plane = a.grp[i];
+    const int64_t pg = pos_group(a, k, a.grp[i]);
+    if (pg >= 0) plane = pg;
     if (k == R_VP) vp = a.grp[i];
     if (c >= 0 && a.fixed[c] != 0x3F) {
       if (c != prev) {
@@ -357,9 +374,9 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
   }
   const int32_t plane_slot = plane >= 0 ? e : -1;
   if (plane >= 0) {
-    o.slot_ent[e] = (int32_t)(a.nc + plane);
+    o.slot_ent[e] = (int32_t)plane;
     o.slot_feat[e] = (int32_t)f;
-    o.slot_type[e] = ENT_PLANE;
+    o.slot_type[e] = pos_type(a, plane);
     ++e;
   }
   const int32_t vp_slot = vp >= 0 ? e : -1;
@@ -372,7 +389,7 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
   o.feat_plane_slot[f] = plane_slot;
   for (int32_t j = r0; j < r1; ++j) {
     const int k = a.kind[a.order[j]];
-    const bool on_plane = k == R_PLANE_POINT || k == R_PLANE_LINE || k == R_PLANE_POINT3 || k == R_PLANE_LINE3;
+    const bool on_plane = pos_group(a, k, 0) >= 0;
     o.rslot_g[j] = on_plane ? plane_slot : (k == R_VP ? vp_slot : -1);
   }
   if (!a.cam_k) return;
@@ -540,6 +557,7 @@ __global__ void k_pair_gen(PairGen g) {
         if (ti == ENT_CAM && tj == ENT_PLANE) code = PAIR_CP;
         else if (ti == ENT_CAM && tj == ENT_INTR && g.cam_k && g.kbase + g.cam_k[a] == b) code = PAIR_CK;
         else if (ti == ENT_PLANE && tj == ENT_INTR) code = PAIR_PK;
+        else if (ti == ENT_CAM && tj >= ENT_SPHERE) code = PAIR_CS;
       }
       g.gj[q] = (int32_t)((uint32_t)j | (code << PAIR_SHIFT));
       atomicAdd(&g.ucnt[u], 1ull);
@@ -614,7 +632,7 @@ struct ObsGather {
   int64_t n, o;
   const int32_t *cam, *feat, *other;
   const double* meas;
-  int64_t np, nl, nc, npl, nv;
+  int64_t np, nl, nc, npl, nv, nsp, ncy, nco;
   int8_t* kind_d;
   int32_t *cam_d, *feat_d, *grp_d;
   double* meas_d;
@@ -626,7 +644,7 @@ __global__ void k_gather_obs(ObsGather a) {
   if (i >= a.n) return;
   const int64_t j = a.o + i;
   const int k = a.kind;
-  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L || k == R_PLANE_POINT3);
+  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L || k == R_PLANE_POINT3 || k >= R_SPHERE_POINT);
   int code = 0;
   const int32_t f = a.feat[i];
   if (f < 0 || f >= (is_point ? a.np : a.nl)) code = 1;
@@ -642,6 +660,9 @@ __global__ void k_gather_obs(ObsGather a) {
   } else if (!code && k == R_VP) {
     g = a.other[i];
     if (g < 0 || g >= a.nv) code = 4;
+  } else if (!code && k >= R_SPHERE_POINT) {
+    g = a.other[i];
+    if (g < 0 || g >= (k == R_SPHERE_POINT ? a.nsp : k == R_CYL_POINT ? a.ncy : a.nco)) code = 7;
   } else if (!code && (k == R_P2L || k == R_L2P) && a.other) {
     const int32_t q = a.other[i];
     if (q < 0 || q >= (k == R_P2L ? a.nl : a.np)) code = 5;
@@ -708,9 +729,19 @@ __global__ void k_kind_key(const int8_t* __restrict__ kind, int64_t n, uint32_t*
   if (j < n) { key[j] = (uint32_t)kind[j]; val[j] = (uint32_t)j; }
 }
 
-__global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, uint8_t* __restrict__ t) {
+__global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int64_t nsp, int64_t ncy, int64_t nco,
+                           uint8_t* __restrict__ t) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a < na) t[a] = a < nc ? ENT_CAM : (a < nc + npl ? ENT_PLANE : (a < nc + npl + nv ? ENT_VP : ENT_INTR));
+  if (a >= na) return;
+  int64_t b = nc;
+  uint8_t ty = ENT_CAM;
+  if (a >= b) ty = ENT_PLANE;
+  b += npl; if (a >= b) ty = ENT_VP;
+  b += nv; if (a >= b) ty = ENT_SPHERE;
+  b += nsp; if (a >= b) ty = ENT_CYL;
+  b += ncy; if (a >= b) ty = ENT_CONE;
+  b += nco; if (a >= b) ty = ENT_INTR;
+  t[a] = ty;
 }
 
 static ba_status read_i64(Problem& P, const int64_t* src, int64_t* dst) {
@@ -746,7 +777,12 @@ ba_status build_structure(Problem& P) {
     for (int64_t i = 0; i < d.nc; ++i)
       for (int k = 0; k < 3; ++k) P.h_cam[12 * i + 7 + k] = P.h_intr[3 * (size_t)P.h_cam_k[i] + k];
   }
-  d.na = d.nc + d.npl + d.nv + d.nk;
+  d.nsp = (int64_t)P.h_sph.size() / 4;
+  d.ncy = (int64_t)P.h_cyl.size() / 7;
+  d.nco = (int64_t)P.h_cone.size() / 7;
+  if (d.ngs() && d.nk) return fail(P, BA_ERR_ARG, "refined intrinsics (cam_dof 9) together with spheres, cylinders "
+                                                  "or cones are not supported");
+  d.na = d.nc + d.npl + d.nv + d.ngs() + d.nk;
   if (d.na > (int64_t)1 << 30 || d.nf > (int64_t)1 << 30) return fail(P, BA_ERR_ARG, "too many entities");
   // the pattern bitmap holds na x na bits
   const int64_t wpr = (d.na + 31) / 32;
@@ -779,6 +815,36 @@ ba_status build_structure(Problem& P) {
     for (int k = 0; k < 3; ++k) v[k] /= n;
   }
 
+  // ---- spheres (c, r > 0), cylinders (Pluecker axis rescaled to |d| = 1, r > 0), cones (apex, unit axis, half-angle
+  // in (0, pi/2)), SRF_STRIDE values each
+  std::vector<double> srf(SRF_STRIDE * (size_t)d.ngs(), 0.0);
+  for (int64_t i = 0; i < d.nsp; ++i) {
+    const double* S_ = &P.h_sph[4 * i];
+    if (!(S_[3] > 0) || !std::isfinite(S_[0] + S_[1] + S_[2] + S_[3]))
+      return fail(P, BA_ERR_ARG, "sphere " + std::to_string(i) + ": the radius must be positive and finite");
+    for (int k = 0; k < 4; ++k) srf[SRF_STRIDE * i + k] = S_[k];
+  }
+  for (int64_t i = 0; i < d.ncy; ++i) {
+    const double* C_ = &P.h_cyl[7 * i];
+    double* o = &srf[SRF_STRIDE * (d.nsp + i)];
+    const double n = std::sqrt(C_[0] * C_[0] + C_[1] * C_[1] + C_[2] * C_[2]);
+    if (!(n > 0) || !std::isfinite(n) || !(C_[6] > 0) || !std::isfinite(C_[6]))
+      return fail(P, BA_ERR_ARG, "cylinder " + std::to_string(i) + ": zero axis direction or a radius that is not positive");
+    for (int k = 0; k < 6; ++k) o[k] = C_[k] / n;
+    const double dm = o[0] * o[3] + o[1] * o[4] + o[2] * o[5];   // keep m perpendicular to d
+    for (int k = 0; k < 3; ++k) o[3 + k] -= dm * o[k];
+    o[6] = C_[6];
+  }
+  for (int64_t i = 0; i < d.nco; ++i) {
+    const double* K_ = &P.h_cone[7 * i];
+    double* o = &srf[SRF_STRIDE * (d.nsp + d.ncy + i)];
+    const double n = std::sqrt(K_[3] * K_[3] + K_[4] * K_[4] + K_[5] * K_[5]);
+    if (!(n > 0) || !std::isfinite(n) || !(K_[6] > 0 && K_[6] < 1.5707963267948966))
+      return fail(P, BA_ERR_ARG, "cone " + std::to_string(i) + ": zero axis or a half-angle outside (0, pi/2)");
+    for (int k = 0; k < 3; ++k) { o[k] = K_[k]; o[3 + k] = K_[3 + k] / n; }
+    o[6] = K_[6];
+  }
+
   // ---- residual records: validated and merged in input order on the device (below)
   int64_t nr = 0;
   for (auto& b : P.d_obs) nr += b.n;
@@ -804,7 +870,7 @@ ba_status build_structure(Problem& P) {
     CU(cudaMemcpyAsync(err, &none, sizeof(none), cudaMemcpyHostToDevice, P.stream));
     int64_t o = 0;
     for (auto& b : P.d_obs) {
-      ObsGather g{b.kind, b.md, b.n, o, b.cam, b.feat, b.other, b.meas, d.np, d.nl, d.nc, d.npl, d.nv,
+      ObsGather g{b.kind, b.md, b.n, o, b.cam, b.feat, b.other, b.meas, d.np, d.nl, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco,
                   kind_d, cam_d, feat_d, grp_d, meas_d, err};
       k_gather_obs<<<grid_of(b.n, NT), NT, 0, P.stream>>>(g);
       o += b.n;
@@ -828,6 +894,7 @@ ba_status build_structure(Problem& P) {
       if (code == 3) return fail(P, BA_ERR_ARG, "plane id out of range");
       if (code == 4) return fail(P, BA_ERR_ARG, "vp id out of range");
       if (code == 5) return fail(P, BA_ERR_ARG, "partner feature id out of range");
+      if (code == 7) return fail(P, BA_ERR_ARG, "sphere, cylinder or cone id out of range");
       return fail(P, BA_ERR_ARG, "non-finite measurement");
     }
     P.release_obs();
@@ -868,8 +935,9 @@ ba_status build_structure(Problem& P) {
     if (!P.cam_k) return oom();
     CU(cudaMemcpyAsync(P.cam_k, P.h_cam_k.data(), sizeof(int32_t) * d.nc, cudaMemcpyHostToDevice, P.stream));
   }
-  const int64_t kbase = d.nc + d.npl + d.nv;
-  SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d, P.cam_k, kbase};
+  const int64_t kbase = d.kbase();
+  SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d, P.cam_k, kbase,
+              d.sbase(), d.nsp, d.ncy};
   int64_t* soff = S.get<int64_t>(nf + 1);
   if (!soff) return oom();
   k_slot_count<<<grid_of(nf, NT), NT, 0, P.stream>>>(sa, cnt64);
@@ -879,7 +947,7 @@ ba_status build_structure(Problem& P) {
   int herr = 0;
   CU(cudaMemcpyAsync(&herr, err_d, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
   CU(cudaStreamSynchronize(P.stream));
-  if (herr & 1) return fail(P, BA_ERR_ARG, "a feature may be associated with at most one plane");
+  if (herr & 1) return fail(P, BA_ERR_ARG, "a feature may be associated with at most one plane, sphere, cylinder or cone");
   if (herr & 2) return fail(P, BA_ERR_ARG, "a line may be associated with at most one VP");
   if (ne > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many slots");
   d.ne = ne;
@@ -1047,7 +1115,7 @@ ba_status build_structure(Problem& P) {
   }
   P.ent_type = P.dnew<uint8_t>(na);
   if (!P.ent_type) return oom();
-  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, d.nv, P.ent_type);
+  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco, P.ent_type);
 
   // ---- parameters
 #define UP(dst, src) if ((s = upload(P, dst, src)) != BA_OK) return s
@@ -1056,6 +1124,7 @@ ba_status build_structure(Problem& P) {
     auto& S_ = P.ps[k];
     UP(S_.cam, P.h_cam); UP(S_.pts, P.h_pts); UP(S_.lin, P.h_lin); UP(S_.pln, P.h_pln); UP(S_.vps, P.h_vps);
     if (d.nk) UP(S_.intr, P.h_intr);
+    if (d.ngs()) UP(S_.srf, srf);
     S_.camD = P.dnew<double>(d.nc * CAM_STRIDE);
     S_.grpD = P.dnew<double>((d.npl + d.nv) * GRP_STRIDE);
     if (!S_.camD || !S_.grpD) return oom();
@@ -1161,7 +1230,7 @@ SView sview_of(const Problem& P) {
     v.nc = P.d.nc;
     v.npl = P.d.npl;
     v.gg_val0 = P.gg_val0;
-    v.kb = P.d.nc + P.d.npl + P.d.nv;
+    v.kb = P.d.kbase();
   }
   return v;
 }
@@ -1171,7 +1240,7 @@ ba_status build_typed_storage(Problem& P, TypedPlan& plan) {
   const int64_t na = d.na, nc = d.nc;
   constexpr int NT = 128;
   auto oom = [&]() { return fail(P, BA_ERR_OOM, "device allocation failed"); };
-  const int64_t kb = nc + d.npl + d.nv;
+  const int64_t kb = d.kbase();
   int32_t* cnt_d = P.dnew<int32_t>(4 * na);
   if (!cnt_d) return oom();
   k_typed_count<<<grid_of(na, NT), NT, 0, P.stream>>>(na, nc, d.npl, kb, P.row_ptr, P.row_len, P.col, cnt_d);

@@ -38,8 +38,13 @@ def padded_to_oracle_index(scene, lay):
         idx += list(range(6 * (nc + g), 6 * (nc + g) + 3))
     for v in range(nv):
         idx += list(range(6 * (nc + npl + v), 6 * (nc + npl + v) + 2))
+    o = nc + npl + nv
+    for gk in O.SURFACES:
+        for g in range(lay.ngs.get(gk, 0) if hasattr(lay, "ngs") else 0):
+            idx += list(range(6 * o, 6 * o + O.GDOF[gk]))
+            o += 1
     for k in range(getattr(lay, "nk", 0)):
-        idx += list(range(6 * (nc + npl + nv + k), 6 * (nc + npl + nv + k) + 3))
+        idx += list(range(6 * (o + k), 6 * (o + k) + 3))
     return np.array(idx, np.int64)
 
 
