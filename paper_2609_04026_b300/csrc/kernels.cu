@@ -3190,7 +3190,11 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 static LossW make_loss(const ba_options& o) {
   LossW L;
-  double w[N_KINDS] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire, o.w_group3d, o.w_group3d};
+  // per kind: points, lines, plane-induced (2), VP, wireframe (2), direct 3D plane distances (2), sphere /
+  // cylinder / cone-induced (3)
+  const double w[N_KINDS] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire,
+                             o.w_group3d, o.w_group3d, o.w_group, o.w_group, o.w_group};
+  static_assert(N_KINDS == 12, "a weight per residual kind");
   for (int k = 0; k < N_KINDS; ++k) {
     L.w[k] = w[k];
     double s = (k == R_VP) ? o.cauchy_vp : (res_has_cam(k) ? o.cauchy_px : o.cauchy_3d);
