@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--no-mixed-error", action="store_true", help="skip the per-result mixed-vs-FP64 error")
     ap.add_argument("--no-intr", action="store_true", help="skip the refined-intrinsics (cam_dof 9) workload")
     ap.add_argument("--no-group3d", action="store_true", help="skip the direct-3D group-distance workload")
+    ap.add_argument("--no-surfaces", action="store_true", help="skip the sphere / cylinder / cone workload")
     ap.add_argument("--intr-models", type=int, default=20,
                     help="camera models sharing refined intrinsics in that workload (0 = one per camera)")
     args = ap.parse_args()
@@ -509,6 +510,39 @@ def main():
                       "3D distances, one per feature on a plane, w_group3d = 100; 5 steps timed after 3 warm-up"}
         del s3, ob
 
+    # ---------------- spheres, cylinders and cones (Appendix B, Table 6): the medium scene (200 cameras) with 30 of
+    # each type, 300 points on each surface; LM iterations per second with the group-induced point residuals of
+    # the three types, against the same scene without them
+    srf = None
+    if not args.no_surfaces:
+        res_s = {}
+        for label, kw in (("without", {}), ("with", dict(n_spheres=30, n_cylinders=30, n_cones=30, surf_points=300))):
+            ss = make_scene(scfg("medium", seed=scfg("medium").seed + rank, **kw))
+            q = B.ba_create(B.ba_default_options(precision=prec, cuda_stream=stream.cuda_stream))
+            B.load_scene(q, ss)
+            E0 = B.ba_eval_cost(q)[0]
+            for _ in range(3):
+                B.ba_lm_step(q)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ts = [B.ba_lm_step(q) for _ in range(5)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_s = e0.elapsed_time(e1)
+            na_s, nbf_s = B.ba_reduced_size(q)
+            E1 = B.ba_eval_cost(q)[0]
+            B.ba_destroy(q)
+            res_s[label] = {"lm_iters_per_s": round(5 / (ms_s / 1e3), 3), "ms_per_step": round(ms_s / 5, 3),
+                            "residuals": sum(int(len(o["feat"])) for o in ss["obs"].values()),
+                            "block_rows": na_s, "stored_blocks": nbf_s, "pcg_iters": [r.pcg_iters for r in ts],
+                            "cost_after_8_steps_over_initial": round(E1 / E0, 5)}
+            if label == "with":
+                res_s[label]["surface_residuals"] = {k: int(len(ss["obs"][k]["feat"])) for k in
+                                                     ("sphere_point", "cylinder_point", "cone_point")}
+        srf = dict(res_s, note="the medium scene (200 cameras, 100k points, 20k lines) without and with 30 spheres, "
+                               "30 cylinders and 30 cones of 300 points each; 5 steps timed after 3 warm-up")
+
     # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
     # at the initial damping (the FP64 path itself is checked against the oracle at 2000 cameras by
     # tests/test_gpu_scale.py)
@@ -568,7 +602,7 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "time_to_converge": ttc, "time_to_converge_fp64_block_jacobi": ttc64,
                "time_to_equal_cost": equal,
-               "batched_windows": batched, "refined_intrinsics": intr, "group_form_3d": g3, "learned_precond": learned,
+               "batched_windows": batched, "refined_intrinsics": intr, "group_form_3d": g3, "surface_groups": srf, "learned_precond": learned,
                "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
                "stage_rooflines": stages, "measured_fma_tflops": {"fp32": round(peak32, 2), "fp64": round(peak64, 3)},
                "mixed_error": mixed_err,
