@@ -42,25 +42,31 @@ torch.set_default_dtype(torch.float64)
 DT = torch.float64
 
 KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
-         "sphere_point", "cylinder_point", "cone_point")
+         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point")
 # residual dimension, feature type, group type per kind
 RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1,
-        "plane_point3d": 1, "plane_line3d": 2, "sphere_point": 2, "cylinder_point": 2, "cone_point": 2}
+        "plane_point3d": 1, "plane_line3d": 2, "sphere_point": 2, "cylinder_point": 2, "cone_point": 2,
+        "ellipsoid_point": 2, "cuboid_point": 2}
 FEAT = {"point": "point", "line": "line", "plane_point": "point", "plane_line": "line",
         "vp": "line", "p2l": "point", "l2p": "line", "plane_point3d": "point", "plane_line3d": "line",
-        "sphere_point": "point", "cylinder_point": "point", "cone_point": "point"}
+        "sphere_point": "point", "cylinder_point": "point", "cone_point": "point", "ellipsoid_point": "point",
+        "cuboid_point": "point"}
 GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp", "plane_point3d": "plane",
-         "plane_line3d": "plane", "sphere_point": "sphere", "cylinder_point": "cylinder", "cone_point": "cone"}
+         "plane_line3d": "plane", "sphere_point": "sphere", "cylinder_point": "cylinder", "cone_point": "cone",
+         "ellipsoid_point": "ellipsoid", "cuboid_point": "cuboid"}
 HAS_CAM = {k: k not in ("vp", "plane_point3d", "plane_line3d") for k in KINDS}
 # kinds outside the pixel cost E_px: the angular VP term, and the direct 3D group distances
 NON_PIXEL = ("vp", "plane_point3d", "plane_line3d")
 FDOF = {"point": 3, "line": 4}
-GDOF = {"plane": 3, "vp": 2, "sphere": 4, "cylinder": 5, "cone": 6}
+GDOF = {"plane": 3, "vp": 2, "sphere": 4, "cylinder": 5, "cone": 6, "ellipsoid": 9, "cuboid": 9}
 # state key and stored width of every group kind (spheres (c, r); cylinders (d, m, r), the axis a Pluecker line
 # with |d| = 1; cones (apex, unit axis, half-angle))
 GKEY = {"plane": ("planes", 4), "vp": ("vps", 3), "sphere": ("spheres", 4), "cylinder": ("cylinders", 7),
-        "cone": ("cones", 7)}
+        "cone": ("cones", 7), "ellipsoid": ("ellipsoids", 15), "cuboid": ("cuboids", 15)}
 SURFACES = ("sphere", "cylinder", "cone")
+# the 9-parameter groups: two entities of A each, the first 6 increments (rotation and centre, or rotation and
+# three face offsets) and the last 3 (log semi-axes, or the other three offsets)
+SPLIT = ("ellipsoid", "cuboid")
 CDOF = 6
 
 
@@ -91,7 +97,8 @@ class Options:
         return {"point": self.w_point, "line": self.w_line, "plane_point": self.w_group,
                 "plane_line": self.w_group, "vp": self.w_vp, "p2l": self.w_wire,
                 "l2p": self.w_wire, "plane_point3d": self.w_group3d, "plane_line3d": self.w_group3d,
-                "sphere_point": self.w_group, "cylinder_point": self.w_group, "cone_point": self.w_group}[kind]
+                "sphere_point": self.w_group, "cylinder_point": self.w_group, "cone_point": self.w_group,
+                "ellipsoid_point": self.w_group, "cuboid_point": self.w_group}[kind]
 
     def scale(self, kind):
         if kind in ("plane_point3d", "plane_line3d"):
@@ -241,7 +248,21 @@ def cone_plus(K, d):
     return torch.cat([K[..., :3] + d[..., :3], vp_plus(K[..., 3:6], d[..., 3:5]), K[..., 6:7] + d[..., 5:6]], -1)
 
 
-GROUP_PLUS = {"sphere": sphere_plus, "cylinder": cylinder_plus, "cone": cone_plus}
+def ellipsoid_plus(E, d):
+    """(R, c, s) stored as R row-major (9), c (3), semi-axes s (3): R <- Exp(d[0:3]) R, c <- c + d[3:6],
+    s <- s exp(d[6:9])."""
+    R = so3_exp(d[..., :3]) @ E[..., :9].reshape(E.shape[:-1] + (3, 3))
+    return torch.cat([R.reshape(E.shape[:-1] + (9,)), E[..., 9:12] + d[..., 3:6], E[..., 12:15] * torch.exp(d[..., 6:9])], -1)
+
+
+def cuboid_plus(K, d):
+    """(R, d_0..d_5) stored as R row-major (9) and the six face offsets: R <- Exp(d[0:3]) R, offsets + d[3:9]."""
+    R = so3_exp(d[..., :3]) @ K[..., :9].reshape(K.shape[:-1] + (3, 3))
+    return torch.cat([R.reshape(K.shape[:-1] + (9,)), K[..., 9:15] + d[..., 3:9]], -1)
+
+
+GROUP_PLUS = {"sphere": sphere_plus, "cylinder": cylinder_plus, "cone": cone_plus, "ellipsoid": ellipsoid_plus,
+              "cuboid": cuboid_plus}
 
 
 def sphere_project_point(S, X):
@@ -273,7 +294,39 @@ def cone_project_point(K, X):
     return a + (v * g).sum(-1, keepdim=True) * g
 
 
-GROUP_PROJECT = {"sphere": sphere_project_point, "cylinder": cylinder_project_point, "cone": cone_project_point}
+def ellipsoid_project_point(E, X):
+    """Appendix B: scaled-radial projection: to the local frame x = R^T (X - c), scaled to the unit sphere,
+    normalised, scaled back, and back to the world frame."""
+    R = E[..., :9].reshape(E.shape[:-1] + (3, 3))
+    c, sx = E[..., 9:12], E[..., 12:15]
+    x = (R.transpose(-1, -2) @ (X - c)[..., None])[..., 0]
+    y = x / sx
+    y = y / torch.linalg.norm(y, dim=-1, keepdim=True)
+    return c + (R @ (sx * y)[..., None])[..., 0]
+
+
+def cuboid_faces(K):
+    """The six faces n_f . x + w_f = 0 of a cuboid (R, d): n_i = R e_i with w_i = -d_i, n_{i+3} = -R e_i with
+    w_{i+3} = -d_{i+3}; normals pointing out."""
+    R = K[..., :9].reshape(K.shape[:-1] + (3, 3))
+    Rt = R.transpose(-1, -2)                       # rows: the columns R e_i
+    normals = torch.cat([Rt, -Rt], -2)             # [6, 3]
+    return normals, -K[..., 9:15]
+
+
+def cuboid_project_point(K, X):
+    """Appendix B: onto the face nearest the point (smallest |signed distance|), along that face's normal."""
+    normals, w = cuboid_faces(K)
+    dist = (normals @ X[..., None])[..., 0] + w    # signed, outside positive
+    ad = dist.abs()
+    sel = (ad == ad.min(-1, keepdim=True).values).to(X.dtype)   # the nearest face (a tie is measure zero)
+    df = (dist * sel).sum(-1, keepdim=True)
+    nf = (normals * sel[..., None]).sum(-2)
+    return X - df * nf
+
+
+GROUP_PROJECT = {"sphere": sphere_project_point, "cylinder": cylinder_project_point, "cone": cone_project_point,
+                 "ellipsoid": ellipsoid_project_point, "cuboid": cuboid_project_point}
 
 
 # ===========================================================================
@@ -423,7 +476,7 @@ def _res_surface_point(kind):
     def fn(dc, df, dg, cam, feat, grp, meas):
         R, t = _pose(cam, dc)
         X = feat[:3] + df
-        G = plus(grp[:7], dg)
+        G = plus(grp[:GKEY[kind][1]], dg)
         x1, z1 = pi_point(R, t, cam, X)
         x2, z2 = pi_point(R, t, cam, proj(G, X))
         return x1 - x2, (z1 > 1e-6) & (z2 > 1e-6)
@@ -433,12 +486,15 @@ def _res_surface_point(kind):
 res_sphere_point = _res_surface_point("sphere")
 res_cylinder_point = _res_surface_point("cylinder")
 res_cone_point = _res_surface_point("cone")
+res_ellipsoid_point = _res_surface_point("ellipsoid")
+res_cuboid_point = _res_surface_point("cuboid")
 
 
 RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
           "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p,
           "plane_point3d": res_plane_point3d, "plane_line3d": res_plane_line3d,
-          "sphere_point": res_sphere_point, "cylinder_point": res_cylinder_point, "cone_point": res_cone_point}
+          "sphere_point": res_sphere_point, "cylinder_point": res_cylinder_point, "cone_point": res_cone_point,
+          "ellipsoid_point": res_ellipsoid_point, "cuboid_point": res_cuboid_point}
 
 
 # ===========================================================================
@@ -523,6 +579,12 @@ def state_from_scene(scene):
         cylinders=np.array(scene.get("cylinders", np.zeros((0, 7))), np.float64).reshape(-1, 7),
         cones=np.array(scene.get("cones", np.zeros((0, 7))), np.float64).reshape(-1, 7),
     )
+    # ellipsoids (q, c, s) and cuboids (q, d_0..d_5) as given; the state keeps R (row-major) for the quaternion
+    for key in ("ellipsoids", "cuboids"):
+        g = np.array(scene.get(key, np.zeros((0, 10))), np.float64).reshape(-1, 10)
+        q = g[:, :4] / np.linalg.norm(g[:, :4], axis=1, keepdims=True) if len(g) else g[:, :4]
+        R = quat_to_R(torch.from_numpy(q)).numpy().reshape(-1, 9)
+        st[key] = np.concatenate([R, g[:, 4:]], 1)
     if len(st["cylinders"]):
         # the axis as a Pluecker line with |d| = 1
         st["cylinders"][:, :6] = normalize_lines(st["cylinders"][:, :6])
@@ -555,7 +617,7 @@ def _records(state, obs, kind):
     feat = torch.zeros((n, 6), dtype=DT)
     if n:
         feat[:, : src.shape[1]] = torch.from_numpy(src[o["feat"]])
-    grp = torch.zeros((n, 8), dtype=DT)
+    grp = torch.zeros((n, 16), dtype=DT)
     gk = GROUP.get(kind)
     if gk and n:
         g = state[GKEY[gk][0]]
@@ -675,6 +737,13 @@ class Layout:
             ng = state[GKEY[gk][0]].shape[0] if GKEY[gk][0] in state else 0
             self.ngs[gk] = ng
             self.gcol[gk] = o + GDOF[gk] * np.arange(ng); o += GDOF[gk] * ng
+        # a 9-parameter group's first 6 increments, then (after all of its kind) its last 3
+        self.gcol2 = {}
+        for gk in SPLIT:
+            ng = state[GKEY[gk][0]].shape[0] if GKEY[gk][0] in state else 0
+            self.ngs[gk] = ng
+            self.gcol[gk] = o + 6 * np.arange(ng); o += 6 * ng
+            self.gcol2[gk] = o + 3 * np.arange(ng); o += 3 * ng
         self.nk = state["intr"].shape[0] if "intr" in state else 0
         self.cam_k = state["cam_k"] if self.nk else np.full(self.nc, -1, np.int64)
         self.intr_col = o + 3 * np.arange(self.nk); o += 3 * self.nk
@@ -687,6 +756,8 @@ class Layout:
         self.a_blocks = ([(int(self.cam_cols[i][free[i]][0]), int(nfree[i])) for i in range(self.nc) if nfree[i]] +
                          [(int(c), 3) for c in self.plane_col] + [(int(c), 2) for c in self.vp_col] +
                          [(int(c), GDOF[gk]) for gk in SURFACES for c in self.gcol[gk]] +
+                         [(int(c), w) for gk in SPLIT for cs, w in ((self.gcol[gk], 6), (self.gcol2[gk], 3))
+                          for c in cs] +
                          [(int(c), 3) for c in self.intr_col])
         self.f_blocks = [(int(c), 3) for c in self.point_col] + [(int(c), 4) for c in self.line_col]
 
@@ -722,7 +793,11 @@ def linearize(state, obs, opt: Options, lay: Layout):
         w = FDOF[ft]
         blocks.append((Jf.numpy(), fc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
         gk = GROUP.get(k)
-        if gk:
+        if gk in SPLIT:
+            for cols_, j0, w in ((lay.gcol[gk], 0, 6), (lay.gcol2[gk], 6, 3)):
+                gc = cols_[o["other"]]
+                blocks.append((Jg.numpy()[:, :, j0:j0 + w], gc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
+        elif gk:
             gc = lay.gcol[gk][o["other"]]
             w = GDOF[gk]
             blocks.append((Jg.numpy()[:, :, :w], gc[:, None] + np.arange(w)[None, :], np.ones((n, w), bool)))
@@ -858,10 +933,14 @@ def apply_step(state, delta, lay: Layout):
     if lay.nv:
         d = delta[lay.vp_col[:, None] + np.arange(2)]
         new["vps"] = vp_plus(torch.from_numpy(state["vps"]), torch.from_numpy(d)).numpy()
-    for gk in SURFACES:
+    for gk in SURFACES + SPLIT:
         if lay.ngs[gk]:
             key = GKEY[gk][0]
-            d = delta[lay.gcol[gk][:, None] + np.arange(GDOF[gk])]
+            if gk in SPLIT:
+                d = np.concatenate([delta[lay.gcol[gk][:, None] + np.arange(6)],
+                                    delta[lay.gcol2[gk][:, None] + np.arange(3)]], 1)
+            else:
+                d = delta[lay.gcol[gk][:, None] + np.arange(GDOF[gk])]
             new[key] = GROUP_PLUS[gk](torch.from_numpy(state[key]), torch.from_numpy(d)).numpy()
     if lay.nk:
         # intrinsics: additive; every camera's copy follows its entity

@@ -43,9 +43,10 @@ IMG_W, IMG_H = 800.0, 600.0
 HALF = 3.0
 
 KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
-         "sphere_point", "cylinder_point", "cone_point")
+         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point")
 MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2,
-            "plane_point3d": 0, "plane_line3d": 0, "sphere_point": 0, "cylinder_point": 0, "cone_point": 0}
+            "plane_point3d": 0, "plane_line3d": 0, "sphere_point": 0, "cylinder_point": 0, "cone_point": 0,
+            "ellipsoid_point": 0, "cuboid_point": 0}
 
 
 @dataclasses.dataclass
@@ -88,6 +89,8 @@ class SceneConfig:
     n_spheres: int = 0
     n_cylinders: int = 0
     n_cones: int = 0
+    n_ellipsoids: int = 0
+    n_cuboids: int = 0
     surf_points: int = 60
     seed: int = 1
 
@@ -570,21 +573,26 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
     inside the cube, points on their surfaces appended after the other points, with their point observations
     and one group-induced record per view (kinds sphere_point, cylinder_point, cone_point)."""
     obs = scene["obs"]
-    for k in ("sphere_point", "cylinder_point", "cone_point"):
-        obs[k] = dict(cam=np.zeros(0, np.int32), feat=np.zeros(0, np.int32), other=np.zeros(0, np.int32),
-                      meas=np.zeros((0, 0)))
-    counts = {"sphere": cfg.n_spheres, "cylinder": cfg.n_cylinders, "cone": cfg.n_cones}
-    gt = {"sphere": np.zeros((0, 4)), "cylinder": np.zeros((0, 7)), "cone": np.zeros((0, 7))}
+    kinds = ("sphere", "cylinder", "cone", "ellipsoid", "cuboid")
+    keys = {"sphere": "spheres", "cylinder": "cylinders", "cone": "cones", "ellipsoid": "ellipsoids", "cuboid": "cuboids"}
+    for k in kinds:
+        obs[k + "_point"] = dict(cam=np.zeros(0, np.int32), feat=np.zeros(0, np.int32), other=np.zeros(0, np.int32),
+                                 meas=np.zeros((0, 0)))
+    counts = {"sphere": cfg.n_spheres, "cylinder": cfg.n_cylinders, "cone": cfg.n_cones,
+              "ellipsoid": cfg.n_ellipsoids, "cuboid": cfg.n_cuboids}
+    gt = {"sphere": np.zeros((0, 4)), "cylinder": np.zeros((0, 7)), "cone": np.zeros((0, 7)),
+          "ellipsoid": np.zeros((0, 10)), "cuboid": np.zeros((0, 10))}
     init = {k: v.copy() for k, v in gt.items()}
     if sum(counts.values()) == 0:
-        scene["spheres"], scene["cylinders"], scene["cones"] = init["sphere"], init["cylinder"], init["cone"]
-        scene["gt"].update(spheres=gt["sphere"], cylinders=gt["cylinder"], cones=gt["cone"])
+        for k in kinds:
+            scene[keys[k]] = init[k]
+            scene["gt"][keys[k]] = gt[k]
         return
     rng = np.random.default_rng(cfg.seed * 31 + 777)
     Nc = len(Rgt)
     np0 = len(scene["points"])
     new_P, new_gt, recs = [], [], []
-    for kind in ("sphere", "cylinder", "cone"):
+    for kind in kinds:
         rows, rows0 = [], []
         for g in range(counts[kind]):
             ctr = rng.uniform(-1.5, 1.5, 3)
@@ -598,6 +606,27 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
                 prm = np.concatenate([ctr, [r]])
                 X = ctr + r * _rand_unit(rng, cfg.surf_points)
                 prm0 = np.concatenate([ctr + rng.normal(0, 0.05, 3), [r * (1 + 0.05 * rng.normal())]])
+            elif kind in ("ellipsoid", "cuboid"):
+                Rg = _axis_angle_mat(_rand_unit(rng, 1), rng.uniform(0, np.pi, 1))[0]   # local -> world
+                q = _mat_to_quat(Rg[None])[0]
+                R0g = _axis_angle_mat(_rand_unit(rng, 1), np.deg2rad(2.0) * rng.normal(size=1))[0] @ Rg
+                q0 = _mat_to_quat(R0g[None])[0]
+                if kind == "ellipsoid":
+                    sx = rng.uniform(0.3, 0.9, 3)
+                    prm = np.concatenate([q, ctr, sx])
+                    X = ctr + (_rand_unit(rng, cfg.surf_points) * sx) @ Rg.T
+                    prm0 = np.concatenate([q0, ctr + rng.normal(0, 0.05, 3), sx * (1 + 0.05 * rng.normal(size=3))])
+                else:
+                    hx = rng.uniform(0.3, 0.8, 3)
+                    a_ = Rg.T @ ctr                              # the centre along the face normals R e_i
+                    dd = np.concatenate([a_ + hx, hx - a_])      # faces n_i.x = d_i and -n_i.x = d_{i+3}
+                    prm = np.concatenate([q, dd])
+                    f_ = rng.integers(0, 6, cfg.surf_points)     # a face, then a point inside 90% of it
+                    loc = rng.uniform(-0.9, 0.9, (cfg.surf_points, 3)) * hx
+                    ax = f_ % 3
+                    loc[np.arange(cfg.surf_points), ax] = np.where(f_ < 3, hx[ax], -hx[ax])
+                    X = ctr + loc @ Rg.T
+                    prm0 = np.concatenate([q0, dd + rng.normal(0, 0.03, 6)])
             elif kind == "cylinder":
                 r = rng.uniform(0.2, 0.5)
                 prm = np.concatenate([d, np.cross(ctr, d), [r]])
@@ -625,7 +654,7 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
     xy = _pix_dist(f[None], k1[None], k2[None], pp[None], xc)
     vis = _visible(xy, xc[..., 2])
     pc, pf, pm, gk, gc, gf, gg = [], [], [], {k: [] for k in counts}, {k: [] for k in counts}, None, None
-    cams_of = {"sphere": [], "cylinder": [], "cone": []}
+    cams_of = {k: [] for k in kinds}
     for i in range(len(new_gt)):
         cs = np.flatnonzero(vis[i])
         if len(cs) < 2:
@@ -651,8 +680,9 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
                                     other=t[:, 2].astype(np.int32), meas=np.zeros((len(t), 0)))
     scene["points"] = np.concatenate([scene["points"], np.array(new_P).reshape(-1, 3)])
     scene["gt"]["points"] = np.concatenate([scene["gt"]["points"], new_gt])
-    scene["spheres"], scene["cylinders"], scene["cones"] = init["sphere"], init["cylinder"], init["cone"]
-    scene["gt"].update(spheres=gt["sphere"], cylinders=gt["cylinder"], cones=gt["cone"])
+    for k in kinds:
+        scene[keys[k]] = init[k]
+        scene["gt"][keys[k]] = gt[k]
 
 
 def noise_free(cfg: SceneConfig) -> dict:
@@ -663,7 +693,7 @@ def noise_free(cfg: SceneConfig) -> dict:
     s["cams"] = {k: v.copy() for k, v in s["gt"]["cams"].items()}
     s["points"] = s["gt"]["points"].copy(); s["lines"] = s["gt"]["lines"].copy()
     s["planes"] = s["gt"]["planes"].copy(); s["vps"] = s["gt"]["vps"].copy()
-    for k in ("spheres", "cylinders", "cones"):
+    for k in ("spheres", "cylinders", "cones", "ellipsoids", "cuboids"):
         s[k] = s["gt"][k].copy()
     if "intrinsics" in s:
         ik = s["intrinsics"]

@@ -146,7 +146,8 @@ def test_noise_free_zero_cost_and_zero_step():
 def tiny_both():
     """The tiny scene with both forms of the plane constraints (group-induced 2D and direct 3D) and two spheres,
     cylinders and cones (Appendix B)."""
-    s = make_scene(config("tiny", group_form="both", n_spheres=2, n_cylinders=2, n_cones=2))
+    s = make_scene(config("tiny", group_form="both", n_spheres=2, n_cylinders=2, n_cones=2, n_ellipsoids=2,
+                          n_cuboids=2))
     return s, O.state_from_scene(s), s["fixed"]
 
 
@@ -565,7 +566,8 @@ def test_intrinsics_derivatives_closed_form():
 def test_intrinsics_jacobian_finite_differences(kind):
     """Central differences of the residuals in (f, k1, k2) agree with the oracle's intrinsics Jacobian; the
     line kinds and the wireframe kinds do not depend on k1, k2 (undistorted pinhole pixels)."""
-    s = make_scene(config("tiny", intr_refine=True, n_spheres=1, n_cylinders=1, n_cones=1))
+    s = make_scene(config("tiny", intr_refine=True, n_spheres=1, n_cylinders=1, n_cones=1, n_ellipsoids=1,
+                          n_cuboids=1))
     st = O.state_from_scene(s)
     n = min(40, len(s["obs"][kind]["feat"]))
     assert n > 0
@@ -583,7 +585,8 @@ def test_intrinsics_jacobian_finite_differences(kind):
         fd = (ev(1) - ev(-1)) / (2 * h)
         scale = float(Jk[:, :, j].abs().max()) + 1e-12
         assert float((fd - Jk[:, :, j]).abs().max()) <= 2e-6 * scale + 1e-7, (kind, j)
-    if kind not in ("point", "plane_point", "sphere_point", "cylinder_point", "cone_point"):
+    if kind not in ("point", "plane_point", "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point",
+                    "cuboid_point"):
         assert float(Jk[:, :, 1:].abs().max()) == 0.0
 
 
@@ -698,3 +701,32 @@ def test_surface_groups_zero_on_ground_truth_and_retractions():
     assert float(S[3]) > 0
     K = O.cone_plus(torch.tensor(st["cones"][0]), torch.tensor([0.1, 0, 0, 0.4, -0.3, 0.01]))
     assert abs(float(torch.linalg.norm(K[3:6])) - 1) < 1e-14
+
+
+@pytest.mark.parametrize("name,kind", [("ellipsoid_projection", "ellipsoid"), ("cuboid_projection", "cuboid")])
+def test_nine_parameter_group_projections(name, kind):
+    """Ellipsoid (scaled-radial) and cuboid (nearest face) projections against hand-worked values, and their
+    idempotence."""
+    c = _case(name)
+    G = torch.tensor(c["group"], dtype=torch.float64)
+    for X, P in zip(c["X"], c["proj"]):
+        out = O.GROUP_PROJECT[kind](G, torch.tensor(X))
+        np.testing.assert_allclose(out.numpy(), P, atol=1e-14)
+        np.testing.assert_allclose(O.GROUP_PROJECT[kind](G, out).numpy(), P, atol=1e-13)
+
+
+def test_nine_parameter_groups_ground_truth_and_retractions():
+    """Points on their ellipsoids and cuboids have zero residuals at the noise-free ground truth; the
+    retractions keep R a rotation and the semi-axes positive; a 9-parameter group is two entities of A (6 + 3
+    columns)."""
+    s = noise_free(config("tiny", n_ellipsoids=2, n_cuboids=2))
+    st = O.state_from_scene(s)
+    for k in ("ellipsoid_point", "cuboid_point"):
+        r, v = O.residuals(st, s["obs"], k)
+        assert len(r) > 100 and bool(v.all()) and float(r.abs().max()) < 1e-10, k
+    E = O.ellipsoid_plus(torch.tensor(st["ellipsoids"][0]), torch.tensor([0.3, -0.2, 0.1, 0.1, 0, 0, -9.0, 0.1, 0.2]))
+    R = E[:9].reshape(3, 3)
+    assert float((R @ R.T - torch.eye(3)).abs().max()) < 1e-14 and float(E[12:15].min()) > 0
+    lay = O.Layout(st, s["fixed"])
+    assert np.all(np.diff(lay.gcol["ellipsoid"]) == 6) and np.all(np.diff(lay.gcol2["cuboid"]) == 3)
+    assert (6, 6) == (lay.gcol2["ellipsoid"][0] - lay.gcol["ellipsoid"][-1], lay.gcol["cuboid"][0] - lay.gcol2["ellipsoid"][-1] + 3)
