@@ -74,7 +74,10 @@ typedef enum {
   BA_PLANE = 0, BA_VP = 1,
   BA_SPHERE = 2,     /* n x 4: centre c, radius r > 0 (Appendix B; radius updated in log space) */
   BA_CYLINDER = 3,   /* n x 7: axis as a Pluecker line (d, m), m . d = 0 (rescaled to |d| = 1), radius r > 0 */
-  BA_CONE = 4        /* n x 7: apex a, axis direction d (normalised), half-angle in (0, pi/2) */
+  BA_CONE = 4,       /* n x 7: apex a, axis direction d (normalised), half-angle in (0, pi/2) */
+  BA_ELLIPSOID = 5,  /* n x 10: unit quaternion (w, x, y, z) of R (local -> world), centre c, semi-axes s > 0 */
+  BA_CUBOID = 6      /* n x 10: unit quaternion of R, face offsets d_0..d_5 (faces n_i . x = d_i and -n_i . x =
+                        d_{i+3} with n_i = R e_i); both 9-parameter groups are two entities of A each */
 } ba_group_kind;
 typedef enum { BA_REL_ORTHOGONAL = 0, BA_REL_PARALLEL = 1 } ba_relation_type;
 typedef enum {
@@ -84,7 +87,8 @@ typedef enum {
   BA_OBS_PLANE_LINE3D = 8,    /* direct 3D line-to-plane distances n.d and n.(d x m) + w (|d| = 1; no camera) */
   /* group-induced point residuals of the other group types (Eq. 7 with the projections of Appendix B): a point
    * observed in a camera, other = the sphere / cylinder / cone id; no measurement */
-  BA_OBS_SPHERE_POINT = 9, BA_OBS_CYLINDER_POINT = 10, BA_OBS_CONE_POINT = 11
+  BA_OBS_SPHERE_POINT = 9, BA_OBS_CYLINDER_POINT = 10, BA_OBS_CONE_POINT = 11,
+  BA_OBS_ELLIPSOID_POINT = 12, BA_OBS_CUBOID_POINT = 13
 } ba_obs_kind;
 
 typedef struct ba_options {
@@ -185,9 +189,11 @@ ba_status ba_add_cameras(ba_problem* p, int64_t n, int mem, const double* quat_t
 /* Features (Section 3.2): kind BA_POINT (n x 3) or BA_LINE (n x 6 Pluecker). */
 ba_status ba_add_features(ba_problem* p, int kind, int64_t n, int mem, const double* params);
 /* Groups (Section 3.2-3.3, Appendix B, Table 6): kind BA_PLANE (n x 4), BA_VP (n x 3), BA_SPHERE (n x 4),
- * BA_CYLINDER (n x 7) or BA_CONE (n x 7), layouts at ba_group_kind.  A feature may belong to at most one
- * positional group (a plane, sphere, cylinder or cone).  Spheres, cylinders and cones keep the full 6 x 6
- * storage of S and are not supported by ba_solve_batch or together with cam_dof = 9 (BA_ERR_ARG). */
+ * BA_CYLINDER (n x 7), BA_CONE (n x 7), BA_ELLIPSOID (n x 10) or BA_CUBOID (n x 10), layouts at ba_group_kind.
+ * A feature may belong to at most one positional group (a plane, sphere, cylinder, cone, ellipsoid or cuboid).
+ * The groups other than planes and VPs keep the full 6 x 6 storage of S and are not supported by
+ * ba_solve_batch or together with cam_dof = 9 (BA_ERR_ARG).  ba_get_groups returns the add layouts (a
+ * 9-parameter group's quaternion with w >= 0). */
 ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, const double* params);
 /* Inter-group relations (Section 3.2, Inter-Group Relations; Appendix C, Manhattan / Atlanta world): n
  * relations between two group directions, each a plane normal (kind BA_PLANE) or a VP direction (BA_VP).

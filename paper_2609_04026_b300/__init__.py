@@ -24,11 +24,12 @@ BA_MEM_HOST, BA_MEM_DEVICE = 0, 1
 BA_FP64, BA_MIXED = 0, 1
 BA_PRECOND_BLOCK_JACOBI, BA_PRECOND_LEARNED = 0, 1
 BA_POINT, BA_LINE = 0, 1
-BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER, BA_CONE = 0, 1, 2, 3, 4
+BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER, BA_CONE, BA_ELLIPSOID, BA_CUBOID = 0, 1, 2, 3, 4, 5, 6
 BA_REL_ORTHOGONAL, BA_REL_PARALLEL = 0, 1
 OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6,
-             "plane_point3d": 7, "plane_line3d": 8, "sphere_point": 9, "cylinder_point": 10, "cone_point": 11}
-MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0, 9: 0, 10: 0, 11: 0}
+             "plane_point3d": 7, "plane_line3d": 8, "sphere_point": 9, "cylinder_point": 10, "cone_point": 11,
+             "ellipsoid_point": 12, "cuboid_point": 13}
+MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0, 9: 0, 10: 0, 11: 0, 12: 0, 13: 0}
 NO_CAM = (4, 7, 8)   # kinds without a camera (the VP term, the direct 3D plane distances)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -334,7 +335,7 @@ def ba_get_features(p, kind, n):
     return out
 
 
-GROUP_WIDTH = {0: 4, 1: 3, 2: 4, 3: 7, 4: 7}   # BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER, BA_CONE
+GROUP_WIDTH = {0: 4, 1: 3, 2: 4, 3: 7, 4: 7, 5: 10, 6: 10}   # BA_PLANE ... BA_CUBOID
 
 
 def ba_get_groups(p, kind, n):
@@ -414,7 +415,8 @@ def load_scene(p, scene, device_tensors=False):
         ba_add_groups(p, BA_PLANE, conv(scene["planes"]))
     if len(scene["vps"]):
         ba_add_groups(p, BA_VP, conv(scene["vps"]))
-    for key, kind in (("spheres", BA_SPHERE), ("cylinders", BA_CYLINDER), ("cones", BA_CONE)):
+    for key, kind in (("spheres", BA_SPHERE), ("cylinders", BA_CYLINDER), ("cones", BA_CONE),
+                      ("ellipsoids", BA_ELLIPSOID), ("cuboids", BA_CUBOID)):
         if len(scene.get(key, ())):
             ba_add_groups(p, kind, conv(np.asarray(scene[key], np.float64)))
     ik = scene.get("intrinsics")

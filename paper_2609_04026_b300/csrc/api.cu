@@ -24,7 +24,7 @@
 
 using namespace ba;
 
-static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0};
+static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0, 0, 0};
 
 static ba_status set_err(ba_problem* p, ba_status s, const std::string& m) {
   if (p) p->err = m;
@@ -176,7 +176,9 @@ extern "C" ba_status ba_add_groups(ba_problem* p, int kind, int64_t n, int mem, 
   else if (kind == BA_SPHERE) s = fetch(p, mem, params, 4 * n, p->h_sph);
   else if (kind == BA_CYLINDER) s = fetch(p, mem, params, 7 * n, p->h_cyl);
   else if (kind == BA_CONE) s = fetch(p, mem, params, 7 * n, p->h_cone);
-  else return set_err(p, BA_ERR_ARG, "group kind must be BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER or BA_CONE");
+  else if (kind == BA_ELLIPSOID) s = fetch(p, mem, params, 10 * n, p->h_ell);
+  else if (kind == BA_CUBOID) s = fetch(p, mem, params, 10 * n, p->h_cub);
+  else return set_err(p, BA_ERR_ARG, "unknown group kind");
   return s;
 }
 
@@ -479,8 +481,8 @@ static ba_status freeze(ba_problem* p) {
   p->slotH = p->slotG ? (void*)((char*)p->slotG + T * HG_H) : nullptr;   // a view into the G|H records
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
-  if (d.nk) ok &= A(p->slotCK, T * SC * (size_t)d.ne);
-  if (d.ngs()) ok &= A(p->slotCS, T * SCS * (size_t)d.ne);
+  if (d.nk || d.nbx()) ok &= A(p->slotCK, T * SC * (size_t)d.ne);
+  if (d.ngs() || d.nbx()) ok &= A(p->slotCS, T * SCS * (size_t)d.ne);
   ok &= A(p->slotBS, T * SBS * (size_t)d.ne);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
   p->featV = p->dnew<double>(10 * d.nf); p->featVinv = p->dnew<double>(10 * d.nf);
@@ -502,13 +504,14 @@ static ba_status freeze(ba_problem* p) {
     ok &= A(p->linT, sizeof(float) * 6 * (size_t)d.nl);
     ok &= A(p->measT, sizeof(float) * 4 * (size_t)d.nr);
     if (d.ngs()) ok &= A(p->srfT, sizeof(float) * SRF_STRIDE * (size_t)d.ngs());
+    if (d.nbx()) ok &= A(p->bxT, sizeof(float) * BOX_STRIDE * (size_t)d.nbx());
   }
   if (!ok) return set_err(p, BA_ERR_OOM, "device allocation failed");
   // one-time zero fill of the slot and feature arrays
   CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
-  if (d.nk) CUDA_OR(p, cudaMemsetAsync(p->slotCK, 0, T * SC * (size_t)d.ne, p->stream));
-  if (d.ngs()) CUDA_OR(p, cudaMemsetAsync(p->slotCS, 0, T * SCS * (size_t)d.ne, p->stream));
+  if (d.nk || d.nbx()) CUDA_OR(p, cudaMemsetAsync(p->slotCK, 0, T * SC * (size_t)d.ne, p->stream));
+  if (d.ngs() || d.nbx()) CUDA_OR(p, cudaMemsetAsync(p->slotCS, 0, T * SCS * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
   if (mixed(p) && d.nr) {
@@ -546,7 +549,7 @@ static ba_status ensure_sstore(ba_problem* p, bool for_batch) {
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
   // spheres, cylinders and cones keep the full storage (their camera blocks are 4 to 6 wide)
-  p->typed = !for_batch && d.nc > 0 && d.ngs() == 0 && 3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
+  p->typed = !for_batch && d.nc > 0 && d.ngs() == 0 && d.nbx() == 0 && 3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
   ba_status s;
   if (p->typed) {
     TypedPlan tplan;
@@ -765,6 +768,40 @@ extern "C" ba_status ba_get_groups(ba_problem* p, int kind, int mem, double* par
     if (st) return st;
     for (int64_t i = 0; i < n; ++i)
       for (int k = 0; k < w; ++k) o[w * i + k] = h[SRF_STRIDE * i + k];
+    if (!params) return set_err(p, BA_ERR_ARG, "null output");
+    if (mem == BA_MEM_HOST) { std::memcpy(params, o.data(), o.size() * sizeof(double)); return BA_OK; }
+    CUDA_OR(p, cudaMemcpy(params, o.data(), o.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return BA_OK;
+  }
+  if (kind == BA_ELLIPSOID || kind == BA_CUBOID) {
+    // the 9-parameter records (R row-major, then 6 values) in the add layout: unit quaternion (w >= 0), 6 values
+    const Dims& d = p->d;
+    const int64_t g0 = kind == BA_ELLIPSOID ? 0 : d.nel, n = kind == BA_ELLIPSOID ? d.nel : d.ncu;
+    if (n == 0) return BA_OK;
+    std::vector<double> h(BOX_STRIDE * n), o(10 * n);
+    ba_status st = put_out(p, BA_MEM_HOST, h.data(), (const double*)p->ps[p->cur].bx + BOX_STRIDE * g0, h.size());
+    if (st) return st;
+    for (int64_t i = 0; i < n; ++i) {
+      const double* R = &h[BOX_STRIDE * i];
+      double q[4];
+      const double tr = R[0] + R[4] + R[8];
+      if (tr > 0) {
+        const double s4 = std::sqrt(tr + 1.0) * 2;
+        q[0] = 0.25 * s4; q[1] = (R[7] - R[5]) / s4; q[2] = (R[2] - R[6]) / s4; q[3] = (R[3] - R[1]) / s4;
+      } else if (R[0] > R[4] && R[0] > R[8]) {
+        const double s4 = std::sqrt(1.0 + R[0] - R[4] - R[8]) * 2;
+        q[0] = (R[7] - R[5]) / s4; q[1] = 0.25 * s4; q[2] = (R[1] + R[3]) / s4; q[3] = (R[2] + R[6]) / s4;
+      } else if (R[4] > R[8]) {
+        const double s4 = std::sqrt(1.0 + R[4] - R[0] - R[8]) * 2;
+        q[0] = (R[2] - R[6]) / s4; q[1] = (R[1] + R[3]) / s4; q[2] = 0.25 * s4; q[3] = (R[5] + R[7]) / s4;
+      } else {
+        const double s4 = std::sqrt(1.0 + R[8] - R[0] - R[4]) * 2;
+        q[0] = (R[3] - R[1]) / s4; q[1] = (R[2] + R[6]) / s4; q[2] = (R[5] + R[7]) / s4; q[3] = 0.25 * s4;
+      }
+      const double sg = q[0] < 0 ? -1.0 : 1.0;
+      for (int k = 0; k < 4; ++k) o[10 * i + k] = sg * q[k];
+      for (int k = 0; k < 6; ++k) o[10 * i + 4 + k] = h[BOX_STRIDE * i + 9 + k];
+    }
     if (!params) return set_err(p, BA_ERR_ARG, "null output");
     if (mem == BA_MEM_HOST) { std::memcpy(params, o.data(), o.size() * sizeof(double)); return BA_OK; }
     CUDA_OR(p, cudaMemcpy(params, o.data(), o.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -1215,7 +1252,8 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
     ba_status s = freeze(p);
     if (!s && p->nrel) s = set_err(p, BA_ERR_ARG, "inter-group relations are not supported in batched windows");
     if (!s && p->d.nk) s = set_err(p, BA_ERR_ARG, "refined intrinsics (cam_dof 9) are not supported in batched windows");
-    if (!s && p->d.ngs()) s = set_err(p, BA_ERR_ARG, "spheres, cylinders and cones are not supported in batched windows");
+    if (!s && (p->d.ngs() || p->d.nbx()))
+      s = set_err(p, BA_ERR_ARG, "spheres, cylinders, cones, ellipsoids and cuboids are not supported in batched windows");
     if (!s) s = ensure_sstore(p, true);
     if (s) return set_err(p0, s, "window " + std::to_string(i) + ": " + p->err);
     if (p->typed)

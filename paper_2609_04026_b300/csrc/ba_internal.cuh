@@ -68,17 +68,27 @@ constexpr int SBS = 6;  // back-substitution record per slot (6 values, unpadded
 constexpr int SCS = 36; // camera slot of a feature on a sphere, cylinder or cone: J_cam^T w J_group (6 x 6, zero
                         // beyond the group's dimensions)
 
-enum EntType : uint8_t { ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2, ENT_INTR = 3, ENT_SPHERE = 4, ENT_CYL = 5, ENT_CONE = 6 };
+enum EntType : uint8_t {
+  ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2, ENT_INTR = 3, ENT_SPHERE = 4, ENT_CYL = 5, ENT_CONE = 6,
+  ENT_ELL1 = 7, ENT_ELL2 = 8, ENT_CUB1 = 9, ENT_CUB2 = 10   // a 9-parameter group's first (6) and second (3) entity
+};
 // real dimensions of an entity block: camera pose 6, plane 3, VP 2, intrinsics (f, k1, k2) 3, sphere 4,
-// cylinder 5, cone 6
+// cylinder 5, cone 6, a 9-parameter group's first entity 6 and second 3
 __host__ __device__ __forceinline__ int ent_dims(int et) {
-  return et == ENT_CAM ? 6 : et == ENT_VP ? 2 : et == ENT_SPHERE ? 4 : et == ENT_CYL ? 5 : et == ENT_CONE ? 6 : 3;
+  return et == ENT_CAM ? 6 : et == ENT_VP ? 2 : et == ENT_SPHERE ? 4 : et == ENT_CYL ? 5
+       : (et == ENT_CONE || et == ENT_ELL1 || et == ENT_CUB1) ? 6 : 3;
 }
+// a positional group that is not a plane (its camera couplings take the 6 x 6 CS records)
+__host__ __device__ __forceinline__ bool ent_surface(int et) { return et >= ENT_SPHERE && et != ENT_ELL2 && et != ENT_CUB2; }
+__host__ __device__ __forceinline__ bool ent_second(int et) { return et == ENT_ELL2 || et == ENT_CUB2; }
 // direct coupling carried by a slot pair (pair_b bits 30-31): none, camera-plane (the camera slot's C record),
 // camera-intrinsics (the camera slot's CK record, its own entity only), plane-intrinsics (the intrinsics slot's
 // C record, transposed)
 // camera-surface (the camera slot's CS record: a sphere, cylinder or cone of the feature)
-constexpr uint32_t PAIR_CP = 1u, PAIR_CK = 2u, PAIR_PK = 3u, PAIR_CS = 4u;
+// a 9-parameter group's two entities (the second entity's C record holds J_1^T w J_2, 6 x 3); PAIR_CK also
+// carries a camera's block with a 9-parameter group's second entity (the camera slot's CK record; refined
+// intrinsics are refused together with the other group types)
+constexpr uint32_t PAIR_CP = 1u, PAIR_CK = 2u, PAIR_PK = 3u, PAIR_CS = 4u, PAIR_G12 = 5u;
 constexpr int PAIR_SHIFT = 29;
 constexpr int32_t PAIR_SLOT = 0x1fffffff;
 
@@ -165,10 +175,14 @@ using Problem = ::ba_problem;
 struct Dims {
   int64_t nc = 0, np = 0, nl = 0, npl = 0, nv = 0;
   int64_t nsp = 0, ncy = 0, nco = 0;   // spheres, cylinders, cones (A indices after the VPs, in that order)
-  int64_t nk = 0;    // intrinsics entities (refined f, k1, k2; A indices after the surface groups)
-  int64_t ngs() const { return nsp + ncy + nco; }            // surface groups
-  int64_t sbase() const { return nc + npl + nv; }            // A index of the first surface group
-  int64_t kbase() const { return nc + npl + nv + nsp + ncy + nco; }   // A index of intrinsics entity 0
+  int64_t nel = 0, ncu = 0;            // ellipsoids, cuboids: two entities each (all first entities of a kind,
+                                       // then its second ones), after the cones
+  int64_t nk = 0;    // intrinsics entities (refined f, k1, k2; A indices after the groups)
+  int64_t ngs() const { return nsp + ncy + nco; }            // sphere, cylinder and cone groups
+  int64_t nbx() const { return nel + ncu; }                  // 9-parameter groups
+  int64_t sbase() const { return nc + npl + nv; }            // A index of the first sphere
+  int64_t bbase() const { return sbase() + ngs(); }          // A index of the first ellipsoid's first entity
+  int64_t kbase() const { return bbase() + 2 * nbx(); }      // A index of intrinsics entity 0
   int64_t nf = 0, na = 0, nr = 0, ne = 0, nbu = 0, nbf = 0, nbp = 0, npair = 0;  // nbf stored blocks, nbp padded
   int64_t nun = 0, nmulti = 0;   // Schur work units of the grid path; blocks split over several units
   int64_t nun_main = 0, npack = 0;   // units a warp takes alone (the rest are packed), and the packs
@@ -219,6 +233,7 @@ struct ba_problem {
   std::vector<uint8_t> h_fixed;
   std::vector<double> h_pts, h_lin, h_pln, h_vps;
   std::vector<double> h_sph, h_cyl, h_cone;   // spheres (4), cylinders (7), cones (7) as added
+  std::vector<double> h_ell, h_cub;           // ellipsoids (q, c, s), cuboids (q, d_0..5): 10 each as added
   std::vector<int32_t> h_rel;     // inter-group relations as added: 5 per relation (kind_a, a, kind_b, b, type)
   // shared intrinsics (ba_set_intrinsics): entity values (3 each) and every camera's entity
   std::vector<double> h_intr;
@@ -251,11 +266,12 @@ struct ba_problem {
                               // in cam is a copy of its entity's values
     double* srf = nullptr;    // surface groups, SRF_STRIDE values each: sphere (c, r), cylinder (d, m, r), cone
                               // (apex, axis, half-angle)
+    double* bx = nullptr;     // ellipsoids then cuboids, BOX_STRIDE values each: R row-major, then (c, s) or d_0..5
     double *camD = nullptr, *grpD = nullptr;   // rotation matrices / tangent bases (CAM_STRIDE / GRP_STRIDE)
   } ps[2];
   int cur = 0;
   // working-type (double or float) copies of the current parameters used by the linearisation
-  void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr, *srfT = nullptr;
+  void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr, *srfT = nullptr, *bxT = nullptr;
   uint8_t* cam_fixed = nullptr;
   int32_t* cam_k = nullptr;   // per camera its intrinsics entity (refined intrinsics only)
   // residuals, feature-major

@@ -247,6 +247,8 @@ struct LinArgs {
   const T* srf;                         // surface groups (SRF_STRIDE values each; sphere, cylinder, cone)
   T* CS;                                // per camera slot J_cam^T w J_group of the feature's surface group (SCS)
   int64_t nsp, ncy;                     // spheres, cylinders (the surface ids of cones follow)
+  const T* bx;                          // ellipsoids then cuboids (BOX_STRIDE values each)
+  int64_t nel;                          // ellipsoids
   const T* meas;
   const T *cam, *pts, *lin, *grp;
   int64_t npl, np;
@@ -332,8 +334,20 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   Hv[0] = Hv[1] = Hv[2] = 0;
   Gv[0] = Gv[1] = 0;
   const int plane_slot = a.feat_plane_slot[f];
-  // the positional group is a sphere, cylinder or cone (its camera couplings go to the 6 x 6 CS records)
-  const bool surf = SURF && plane_slot >= 0 && a.slot_type[plane_slot] >= ENT_SPHERE;
+  // the positional group is a sphere, cylinder, cone or a 9-parameter group (its camera couplings go to the
+  // 6 x 6 CS records); a 9-parameter group's second entity has the next slot
+  const bool surf = SURF && plane_slot >= 0 && ent_surface(a.slot_type[plane_slot]);
+  const bool split = SURF && surf && plane_slot + 1 < a.fslot_off[f + 1] && ent_second(a.slot_type[plane_slot + 1]);
+  // the second entity's accumulators (W, H, G), its coupling with the first (J_1^T w J_2) and with the current
+  // camera (J_cam^T w J_2)
+  T W2[KF][3], H2[6], G2[3], X12[6][3], C2[6][3];
+  if constexpr (SURF) {
+#pragma unroll
+    for (int i = 0; i < KF; ++i) W2[i][0] = W2[i][1] = W2[i][2] = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { H2[i] = 0; X12[i][0] = X12[i][1] = X12[i][2] = 0; C2[i][0] = C2[i][1] = C2[i][2] = 0; }
+    G2[0] = G2[1] = G2[2] = 0;
+  }
 
   T F[6];
   if (KF == 3) {
@@ -357,6 +371,14 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
         for (int i = 0; i < SCS; ++i) cb[i] = Cc[i / 6][i % 6];
         store16<T, SCS>(a.CS + (size_t)e * SCS, cb);
+      }
+      if (split) {
+        T cb[SC];
+#pragma unroll
+        for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? C2[i / 3][i % 3] : T(0);
+        store16<T, SC>(a.CK + (size_t)e * SC, cb);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) C2[i][0] = C2[i][1] = C2[i][2] = 0;
       }
     }
     if (!surf && plane_slot >= 0) {
@@ -482,6 +504,8 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       else if (SURF && kind == R_SPHERE_POINT) { res_surface_point<T, true, 0>(c, F, a.srf + (size_t)SRF_STRIDE * gid, o); has_plane = true; }
       else if (SURF && kind == R_CYL_POINT) { res_surface_point<T, true, 1>(c, F, a.srf + (size_t)SRF_STRIDE * (a.nsp + gid), o); has_plane = true; }
       else if (SURF && kind == R_CONE_POINT) { res_surface_point<T, true, 2>(c, F, a.srf + (size_t)SRF_STRIDE * (a.nsp + a.ncy + gid), o); has_plane = true; }
+      else if (SURF && kind == R_ELL_POINT) { res_box_point<T, true, 3>(c, F, a.bx + (size_t)BOX_STRIDE * gid, o); has_plane = true; }
+      else if (SURF && kind == R_CUB_POINT) { res_box_point<T, true, 4>(c, F, a.bx + (size_t)BOX_STRIDE * (a.nel + gid), o); has_plane = true; }
       else continue;
     } else {
       if (kind == R_LINE) res_line<T, true, INTR>(c, F, meas, o);
@@ -554,6 +578,33 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
           Gp[p] += wg[p] * ri;
 #pragma unroll
           for (int q = p; q < GW; ++q) Hp[up_idx(p, q, GW)] += wg[p] * o.Jg[i][q];
+        }
+      }
+      if constexpr (SURF) {
+        if (has_plane && (kind == R_ELL_POINT || kind == R_CUB_POINT)) {
+          // the 9-parameter group's second entity
+          T w2[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) w2[k] = om * o.Jg2[i][k];
+#pragma unroll
+          for (int p = 0; p < KF; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) W2[p][q] += wf[p] * o.Jg2[i][q];
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            G2[p] += w2[p] * ri;
+#pragma unroll
+            for (int q = p; q < 3; ++q) H2[up_idx(p, q, 3)] += w2[p] * o.Jg2[i][q];
+          }
+#pragma unroll
+          for (int p = 0; p < 6; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) X12[p][q] += wg[p] * o.Jg2[i][q];
+          if (camslot)
+#pragma unroll
+            for (int p = 0; p < 6; ++p)
+#pragma unroll
+              for (int q = 0; q < 3; ++q) C2[p][q] += wc[p] * o.Jg2[i][q];
         }
       }
       if (KF == 4 && has_vp) {
@@ -629,6 +680,15 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   };
   if (ps < 0) ps = plane_slot;  // a plane slot whose residuals were all invalid
   if (ps >= 0) put_group(ps, SURF ? ent_dims(a.slot_type[ps]) : 3, &Wp[0][0], GW, Hp, GW, Gp);
+  if constexpr (SURF) {
+    if (split) {
+      put_group(plane_slot + 1, 3, &W2[0][0], 3, H2, 3, G2);
+      T cb[SC];
+#pragma unroll
+      for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? X12[i / 3][i % 3] : T(0);
+      store16<T, SC>(a.C + (size_t)(plane_slot + 1) * SC, cb);
+    }
+  }
   if (KF == 4) {
     if (vs < 0) {
       // find the VP slot (if any) among this feature's residuals
@@ -1123,6 +1183,13 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
         for (int i = 0; i < 6; ++i)
 #pragma unroll
           for (int j = 0; j < 6; ++j) acc[i * 6 + j] += Cm[i * 6 + j] - pair_dot(za, zb, i, j, line);
+      } else if (code == PAIR_G12) {
+        // a 9-parameter group's two entities: the second entity's slot holds J_1^T w J_2 (6 x 3)
+        const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
       } else if (code == PAIR_PK) {
         // plane-intrinsics: the intrinsics slot holds J_K^T w J_plane (3 x 3); this block is its transpose
         const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
@@ -2684,8 +2751,9 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
   }
   T cpl = 0;
   const int pslot = a.feat_plane_slot[f];
-  if (pslot >= 0 && a.slot_type[e] == ENT_CAM && a.slot_type[pslot] >= ENT_SPHERE) {
-    // camera-surface direct block of a feature on a sphere, cylinder or cone (6 x 6, zeros beyond its dims)
+  if (pslot >= 0 && a.slot_type[e] == ENT_CAM && ent_surface(a.slot_type[pslot])) {
+    // camera-surface direct block of a feature on a sphere, cylinder, cone or 9-parameter group (6 x 6, zeros
+    // beyond its dims), and a 9-parameter group's second entity (the camera slot's CK record, 6 x 3)
     const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
     T Cm[36];
     load16<T, 36>(a.CS + (size_t)e * SCS, Cm);
@@ -2693,6 +2761,24 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int j = 0; j < 6; ++j) cpl += dv[i] * Cm[i * 6 + j] * (T)dp[j];
+    if (pslot + 1 < a.fslot_off[f + 1] && ent_second(a.slot_type[pslot + 1])) {
+      const double* d2 = a.x + 6 * (size_t)a.slot_ent[pslot + 1];
+      T Ck[18];
+      load16<T, 18>(a.CK + (size_t)e * SC, Ck);
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cpl += dv[i] * Ck[i * 3 + j] * (T)d2[j];
+    }
+  } else if (ent_second(a.slot_type[e])) {
+    // a 9-parameter group's second entity: its coupling with the first (J_1^T w J_2, the slot's C record)
+    const double* d1 = a.x + 6 * (size_t)a.slot_ent[e - 1];
+    T Cm[18];
+    load16<T, 18>(a.C + (size_t)e * SC, Cm);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cpl += (T)d1[i] * Cm[i * 3 + j] * dv[j];
   } else if (pslot >= 0 && a.slot_type[e] == ENT_CAM) {   // camera-plane direct block of a plane feature
     const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
     const T dpl[3] = {(T)dp[0], (T)dp[1], (T)dp[2]};
@@ -2843,14 +2929,42 @@ struct CandArgs {
   const double* srf;
   double* srf2;
   int64_t nsp, ncy, nco, sbase;
+  // 9-parameter groups (else none): ellipsoids then cuboids (BOX_STRIDE values each), A index of the first
+  // ellipsoid's first entity
+  const double* bx;
+  double* bx2;
+  int64_t nel, ncu, bbase;
 };
 
 // the orthonormal update of a Pluecker line (d, m), |d| = 1: U <- U Exp(dl[0:3]), phi <- phi + dl[3]
 __device__ void line_retract(const double* L, const double* dl, double* o);
 
-// items: cameras, planes, VPs, points, lines, the intrinsics entities, then the surface groups
+// items: cameras, planes, VPs, points, lines, the intrinsics entities, the surface groups, then the
+// 9-parameter groups
 __device__ void candidate_item(const CandArgs& a, int64_t i) {
   const int64_t n0 = a.nc, n1 = n0 + a.npl, n2 = n1 + a.nv, n3 = n2 + a.np;
+  if (i >= n3 + a.nl + a.nk + a.nsp + a.ncy + a.nco) {
+    // ellipsoid (R <- Exp(dw) R, c + dc, s exp(ds)) or cuboid (R <- Exp(dw) R, offsets + dd): the first
+    // entity's increments (dw, then dc or d_0..2), the second's (ds or d_3..5)
+    const int64_t g = i - (n3 + a.nl + a.nk + a.nsp + a.ncy + a.nco);
+    const bool ell = g < a.nel;
+    const double* G = a.bx + BOX_STRIDE * g;
+    double* o = a.bx2 + BOX_STRIDE * g;
+    const int64_t e1 = ell ? a.bbase + g : a.bbase + 2 * a.nel + (g - a.nel);
+    const int64_t e2 = ell ? a.bbase + a.nel + g : a.bbase + 2 * a.nel + a.ncu + (g - a.nel);
+    const double* d1 = a.x + 6 * e1;
+    const double* d2 = a.x + 6 * e2;
+    double E[9];
+    so3_exp(d1, E);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) o[3 * r + c] = E[3 * r] * G[c] + E[3 * r + 1] * G[3 + c] + E[3 * r + 2] * G[6 + c];
+    for (int k = 0; k < 3; ++k) {
+      o[9 + k] = G[9 + k] + d1[3 + k];
+      o[12 + k] = ell ? G[12 + k] * exp(d2[k]) : G[12 + k] + d2[k];
+    }
+    o[15] = G[15];
+    return;
+  }
   if (i >= n3 + a.nl + a.nk) {
     // sphere (c + dc, r exp(ds)), cylinder (line update of the axis, r exp(ds)), cone (a + da, axis on S^2,
     // half-angle + d)
@@ -2966,7 +3080,7 @@ __device__ void line_retract(const double* L, const double* dl, double* o) {
 
 __global__ void k_candidate(CandArgs a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < a.nc + a.npl + a.nv + a.np + a.nl + a.nk + a.nsp + a.ncy + a.nco) candidate_item(a, i);
+  if (i < a.nc + a.npl + a.nv + a.np + a.nl + a.nk + a.nsp + a.ncy + a.nco + a.nel + a.ncu) candidate_item(a, i);
 }
 
 // ---- ln(1 + x) for the FP64 cost, table-driven after P. T. P. Tang, "Table-driven implementation of the
@@ -3049,13 +3163,17 @@ struct CostArgs {
   const int32_t *rcam, *rfeat, *rgrp, *order;
   const double *meas, *camD, *grpD, *pts, *lin;
   const double* srf;   // surface groups (spheres, cylinders, cones)
-  int64_t nr, np, npl, nsp, ncy;
+  const double* bx;    // 9-parameter groups (ellipsoids, cuboids)
+  int64_t nr, np, npl, nsp, ncy, nel;
   LossW loss;
   DevScalars* S;
   double* red;
   int candidate;
 };
 
+// EXT: the sphere ... cuboid kinds too (a separate instantiation, so that the common kinds' kernel keeps its
+// registers and code size)
+template <bool EXT = false>
 __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
   {
     const int kind = a.rkind[i];
@@ -3080,9 +3198,17 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
       case R_L2P: res_l2p<double, false>(c, L, meas, o); break;
       case R_PLANE_POINT3: res_plane_point3<double, false>(X, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
       case R_PLANE_LINE3: res_plane_line3<double, false>(L, a.grpD + (size_t)GRP_STRIDE * gid, o); break;
-      case R_SPHERE_POINT: res_surface_point<double, false, 0>(c, X, a.srf + (size_t)SRF_STRIDE * gid, o); break;
-      case R_CYL_POINT: res_surface_point<double, false, 1>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + gid), o); break;
-      case R_CONE_POINT: res_surface_point<double, false, 2>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + a.ncy + gid), o); break;
+      default:
+        if constexpr (EXT) {
+          switch (kind) {
+            case R_SPHERE_POINT: res_surface_point<double, false, 0>(c, X, a.srf + (size_t)SRF_STRIDE * gid, o); break;
+            case R_CYL_POINT: res_surface_point<double, false, 1>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + gid), o); break;
+            case R_CONE_POINT: res_surface_point<double, false, 2>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + a.ncy + gid), o); break;
+            case R_ELL_POINT: res_box_point<double, false, 3>(c, X, a.bx + (size_t)BOX_STRIDE * gid, o); break;
+            case R_CUB_POINT: res_box_point<double, false, 4>(c, X, a.bx + (size_t)BOX_STRIDE * (a.nel + gid), o); break;
+          }
+        }
+        break;
     }
     if (o.valid) {
       double s = 0;
@@ -3094,10 +3220,11 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
   }
 }
 
+template <bool EXT>
 __global__ void __launch_bounds__(256) k_cost(CostArgs a) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double v[2] = {0, 0};
-  if (t < a.nr) cost_residual(a, a.order[t], v);
+  if (t < a.nr) cost_residual<EXT>(a, a.order[t], v);
   double tot[2];
   if (grid_reduce<2>(v, a.red, &a.S->counter[4], tot) && threadIdx.x == 0) {
     if (a.candidate) { a.S->Enew = tot[0]; a.S->Epxnew = tot[1]; }
@@ -3191,10 +3318,10 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 static LossW make_loss(const ba_options& o) {
   LossW L;
   // per kind: points, lines, plane-induced (2), VP, wireframe (2), direct 3D plane distances (2), sphere /
-  // cylinder / cone-induced (3)
+  // cylinder / cone / ellipsoid / cuboid-induced (5)
   const double w[N_KINDS] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire,
-                             o.w_group3d, o.w_group3d, o.w_group, o.w_group, o.w_group};
-  static_assert(N_KINDS == 12, "a weight per residual kind");
+                             o.w_group3d, o.w_group3d, o.w_group, o.w_group, o.w_group, o.w_group, o.w_group};
+  static_assert(N_KINDS == 14, "a weight per residual kind");
   for (int k = 0; k < N_KINDS; ++k) {
     L.w[k] = w[k];
     double s = (k == R_VP) ? o.cauchy_vp : (res_has_cam(k) ? o.cauchy_px : o.cauchy_3d);
@@ -3220,6 +3347,10 @@ void launch_prepare(Problem& P, bool candidate_only) {
       ++P.launches;
       k_convert<<<nblk(SRF_STRIDE * d.ngs(), 256), 256, 0, P.stream>>>(SRF_STRIDE * d.ngs(), cs.srf, (float*)P.srfT);
     }
+    if (d.nbx()) {
+      ++P.launches;
+      k_convert<<<nblk(BOX_STRIDE * d.nbx(), 256), 256, 0, P.stream>>>(BOX_STRIDE * d.nbx(), cs.bx, (float*)P.bxT);
+    }
     if (d.np) { ++P.launches; k_convert<<<nblk(3 * d.np, 256), 256, 0, P.stream>>>(3 * d.np, cs.pts, (float*)P.ptsT); }
     if (d.nl) { ++P.launches; k_convert<<<nblk(6 * d.nl, 256), 256, 0, P.stream>>>(6 * d.nl, cs.lin, (float*)P.linT); }
   }
@@ -3244,7 +3375,8 @@ void launch_linearize(Problem& P) {
   a.loss = make_loss(P.opt);
   a.rslot_k = P.rslot_k; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = (T*)P.slotCK;
   a.srf = dbl ? (const T*)cs.srf : (const T*)P.srfT; a.CS = (T*)P.slotCS; a.nsp = d.nsp; a.ncy = d.ncy;
-  if (d.ngs()) {
+  a.bx = dbl ? (const T*)cs.bx : (const T*)P.bxT; a.nel = d.nel;
+  if (d.ngs() || d.nbx()) {
     // spheres, cylinders, cones: the points' positional groups take up to 6 dimensions (refined intrinsics are
     // refused together with them)
     if (d.np) { ++P.launches; k_linearize<T, 3, false, true><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
@@ -3458,7 +3590,8 @@ void launch_candidate(Problem& P) {
   a.nc = d.nc; a.np = d.np; a.nl = d.nl; a.npl = d.npl; a.nv = d.nv;
   a.intr = c.intr; a.intr2 = n.intr; a.cam_k = P.cam_k; a.nk = d.nk; a.kbase = d.kbase();
   a.srf = c.srf; a.srf2 = n.srf; a.nsp = d.nsp; a.ncy = d.ncy; a.nco = d.nco; a.sbase = d.sbase();
-  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl + d.nk + d.ngs();
+  a.bx = c.bx; a.bx2 = n.bx; a.nel = d.nel; a.ncu = d.ncu; a.bbase = d.bbase();
+  int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl + d.nk + d.ngs() + d.nbx();
   if (tot) { ++P.launches; k_candidate<<<nblk(tot, 128), 128, 0, P.stream>>>(a); }
 }
 
@@ -3467,12 +3600,13 @@ void launch_cost(Problem& P, bool candidate) {
   auto& s = P.ps[candidate ? 1 - P.cur : P.cur];
   CostArgs a;
   a.rkind = P.rkind; a.rcam = P.rcam; a.rfeat = P.rfeat; a.rgrp = P.rgrp; a.meas = P.meas64; a.order = P.cost_order;
-  a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin; a.srf = s.srf;
-  a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.nsp = d.nsp; a.ncy = d.ncy;
+  a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin; a.srf = s.srf; a.bx = s.bx;
+  a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.nsp = d.nsp; a.ncy = d.ncy; a.nel = d.nel;
   a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
   a.candidate = candidate ? 1 : 0;
   ++P.launches;
-  k_cost<<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
+  if (d.ngs() || d.nbx()) k_cost<true><<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
+  else k_cost<false><<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
 }
 
 void launch_decide(Problem& P) {
@@ -3832,7 +3966,7 @@ void fill_window_desc(Problem& P, void* out) {
   a.W = (T*)P.slotW; a.H = (T*)P.slotH; a.G = (T*)P.slotG; a.C = (T*)P.slotC; a.V = P.featV; a.g = P.featg;
   a.loss = make_loss(P.opt);
   a.rslot_k = nullptr; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = nullptr;
-  a.srf = nullptr; a.CS = nullptr; a.nsp = a.ncy = 0;
+  a.srf = nullptr; a.CS = nullptr; a.nsp = a.ncy = 0; a.bx = nullptr; a.nel = 0;
   InvArgs<T>& ia = W.inv;
   ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
   ia.slot_feat = P.slot_feat; ia.Vinv = P.featVinv; ia.u = P.featu; ia.L = P.featL; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB;
@@ -3849,10 +3983,11 @@ void fill_window_desc(Problem& P, void* out) {
   c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
   c.intr = nullptr; c.intr2 = nullptr; c.cam_k = nullptr; c.nk = 0; c.kbase = 0;   // windows: no refined intrinsics
   c.srf = nullptr; c.srf2 = nullptr; c.nsp = c.ncy = c.nco = 0; c.sbase = 0;        // nor surface groups
+  c.bx = nullptr; c.bx2 = nullptr; c.nel = c.ncu = 0; c.bbase = 0;
   CostArgs& co = W.cost;
   co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64; co.order = P.cost_order;
   co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;
-  co.srf = nullptr; co.nsp = co.ncy = 0;
+  co.srf = nullptr; co.nsp = co.ncy = 0; co.bx = nullptr; co.nel = 0;
   W.dec = DecideArgs{P.S, P.opt.min_gain, P.opt.lambda_min, P.opt.lambda_max};
   for (int s = 0; s < 2; ++s) {
     W.cam[s] = P.ps[s].cam; W.pts[s] = P.ps[s].pts; W.lin_[s] = P.ps[s].lin; W.pln[s] = P.ps[s].pln;

@@ -39,9 +39,10 @@ namespace ba {
 enum ResKind : int {
   R_POINT = 0, R_LINE = 1, R_PLANE_POINT = 2, R_PLANE_LINE = 3, R_VP = 4, R_P2L = 5, R_L2P = 6,
   R_PLANE_POINT3 = 7, R_PLANE_LINE3 = 8,   // the direct 3D plane distances (no camera)
-  R_SPHERE_POINT = 9, R_CYL_POINT = 10, R_CONE_POINT = 11   // group-induced point residuals of other group types
+  R_SPHERE_POINT = 9, R_CYL_POINT = 10, R_CONE_POINT = 11,  // group-induced point residuals of other group types
+  R_ELL_POINT = 12, R_CUB_POINT = 13                         // ... of the 9-parameter ellipsoid and cuboid
 };
-constexpr int N_KINDS = 12;
+constexpr int N_KINDS = 14;
 
 __host__ __device__ constexpr int res_dim(int k) {
   return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3
@@ -49,6 +50,9 @@ __host__ __device__ constexpr int res_dim(int k) {
 }
 // surface group types (sphere, cylinder, cone): 8 raw values per group, increments of 4, 5 and 6
 constexpr int SRF_STRIDE = 8;
+// 9-parameter groups (ellipsoid, cuboid): R row-major (9) then (c, s) or the six face offsets; two entities each
+// (rotation and c or d_0..2; then log s or d_3..5)
+constexpr int BOX_STRIDE = 16;
 __host__ __device__ constexpr int srf_dims(int ty) { return ty == 0 ? 4 : (ty == 1 ? 5 : 6); }
 // kinds with a camera (the others: the VP term and the direct 3D plane distances)
 __host__ __device__ constexpr bool res_has_cam(int k) { return k != R_VP && k != R_PLANE_POINT3 && k != R_PLANE_LINE3; }
@@ -114,7 +118,9 @@ struct ResJ {
   T r[4];
   T Jc[4][6];
   T Jf[4][4];
-  T Jg[4][6];   // w.r.t. the group's increments (plane 3, VP 2, sphere 4, cylinder 5, cone 6)
+  T Jg[4][6];   // w.r.t. the group's increments (plane 3, VP 2, sphere 4, cylinder 5, cone 6; a 9-parameter
+                // group's first entity 6)
+  T Jg2[4][3];  // w.r.t. a 9-parameter group's second entity (ellipsoid log semi-axes, cuboid d_3..5)
   T Jk[4][3];   // w.r.t. the camera's (f, k1, k2), filled only when asked for (INTR)
   bool valid;
 };
@@ -718,6 +724,160 @@ __device__ void res_surface_point(const Cam<T>& c, const T* X, const T* G, ResJ<
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k) o.Jk[i][k] = K1[i][k] - K2[i][k];
+  }
+}
+
+// ---------------------------------------------------------------- ellipsoid, cuboid (Appendix B)
+// Ellipsoid (R, c, s): local x = R^T (X - c), y = x / s, Xp = c + R (s y/|y|).  Cuboid (R, d): faces n_f . X + w_f
+// = 0 with n_i = R e_i, w_i = -d_i and n_{i+3} = -R e_i, w_{i+3} = -d_{i+3}; Xp = X - dist_f n_f on the face
+// nearest X.  Increments: R <- Exp(dw) R (3), then c (3) or d_0..2 (3) -- the first entity; log s (3) or
+// d_3..5 (3) -- the second.  dXp for a change dX (grp < 0) or along increment grp (0..8).
+template <class T>
+struct BoxFrame {
+  T Xp[3], R[9];
+  T v[3], x[3], y[3], yn, yh[3], xp[3], s[3];   // ellipsoid
+  T n[3], dist;                                   // cuboid: the nearest face
+  int face;
+};
+
+template <class T, int TY>
+__device__ __forceinline__ void box_frame(const T* G, const T* X, BoxFrame<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) b.R[i] = G[i];
+  if (TY == 3) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { b.v[i] = X[i] - G[9 + i]; b.s[i] = G[12 + i]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      b.x[i] = b.R[i] * b.v[0] + b.R[3 + i] * b.v[1] + b.R[6 + i] * b.v[2];   // R^T v
+      b.y[i] = b.x[i] / b.s[i];
+    }
+    b.yn = sqrt_t(dot3(b.y, b.y));
+    const T iy = T(1) / b.yn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { b.yh[i] = b.y[i] * iy; b.xp[i] = b.s[i] * b.yh[i]; }
+    matvec3(b.R, b.xp, b.Xp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b.Xp[i] += G[9 + i];
+  } else {
+    T best = T(0);
+    b.face = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int i = f % 3;
+      const T sg = f < 3 ? T(1) : T(-1);
+      const T dist = sg * (b.R[i] * X[0] + b.R[3 + i] * X[1] + b.R[6 + i] * X[2]) - G[9 + f];
+      if (f == 0 || fabs((double)dist) < fabs((double)best)) { best = dist; b.face = f; }
+    }
+    const int i = b.face % 3;
+    const T sg = b.face < 3 ? T(1) : T(-1);
+    b.n[0] = sg * b.R[i]; b.n[1] = sg * b.R[3 + i]; b.n[2] = sg * b.R[6 + i];
+    b.dist = best;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b.Xp[k] = X[k] - best * b.n[k];
+  }
+}
+
+template <class T, int TY>
+__device__ __forceinline__ void box_dir(const BoxFrame<T>& b, const T* X, const T* dX, int grp, T* o) {
+  if (TY == 3) {
+    T dxw[3] = {T(0), T(0), T(0)};   // the change of X - c, before the rotation's
+    T w[3] = {T(0), T(0), T(0)};     // rotation increment
+    T dc[3] = {T(0), T(0), T(0)}, dls[3] = {T(0), T(0), T(0)};
+    if (grp < 0) { dxw[0] = dX[0]; dxw[1] = dX[1]; dxw[2] = dX[2]; }
+    else if (grp < 3) w[grp] = T(1);
+    else if (grp < 6) { dc[grp - 3] = T(1); dxw[grp - 3] = T(-1); }
+    else dls[grp - 6] = T(1);
+    // dx = R^T (dX - dc) - R^T (w x v)
+    T wv[3];
+    cross3(w, b.v, wv);
+    T dv[3] = {dxw[0] - wv[0], dxw[1] - wv[1], dxw[2] - wv[2]};
+    T dx[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dx[i] = b.R[i] * dv[0] + b.R[3 + i] * dv[1] + b.R[6 + i] * dv[2];
+      dy[i] = dx[i] / b.s[i] - b.y[i] * dls[i];
+    }
+    const T yd = dot3(b.yh, dy), iy = T(1) / b.yn;
+    T dxp[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dxp[i] = b.s[i] * dls[i] * b.yh[i] + b.s[i] * (dy[i] - b.yh[i] * yd) * iy;
+    T Rdxp[3], Rxp[3], wR[3];
+    matvec3(b.R, dxp, Rdxp);
+    matvec3(b.R, b.xp, Rxp);
+    cross3(w, Rxp, wR);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i] = dc[i] + wR[i] + Rdxp[i];
+  } else {
+    if (grp < 0) {
+      const T nd = dot3(b.n, dX);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) o[i] = dX[i] - nd * b.n[i];
+    } else if (grp < 3) {
+      T w[3] = {T(0), T(0), T(0)}, dn[3];
+      w[grp] = T(1);
+      cross3(w, b.n, dn);
+      const T dd = dot3(dn, X);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) o[i] = -dd * b.n[i] - b.dist * dn[i];
+    } else {
+      // offset d_j, j = grp - 3: only the nearest face's offset moves Xp (dist_f = n_f . X - d_f)
+      const bool on = (grp - 3) == b.face;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) o[i] = on ? b.n[i] : T(0);
+    }
+  }
+}
+
+// the group-induced point residual of an ellipsoid (TY 3) or cuboid (TY 4): pi(C, X) - pi(C, Proj(X)); Jg holds
+// the first entity's 6 columns, Jg2 the second's 3
+template <class T, bool JAC, int TY>
+__device__ void res_box_point(const Cam<T>& c, const T* X, const T* G, ResJ<T>& o) {
+  BoxFrame<T> b;
+  box_frame<T, TY>(G, X, b);
+  T p1[3], p2[3], x1[3], x2[3], pi1[2], pi2[2], J1[2][3], J2[2][3];
+  matvec3(c.R, X, p1);
+  matvec3(c.R, b.Xp, p2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { x1[i] = p1[i] + c.t[i]; x2[i] = p2[i] + c.t[i]; }
+  o.valid = (double)x1[2] > 1e-6 && (double)x2[2] > 1e-6;
+  if (!o.valid) return;
+  project_dist<T, JAC>(c, x1, pi1, J1);
+  project_dist<T, JAC>(c, x2, pi2, J2);
+  o.r[0] = pi1[0] - pi2[0];
+  o.r[1] = pi1[1] - pi2[1];
+  if (!JAC) return;
+  T g1[2][3], g2[2][3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    T a6[6], b6[6];
+    pose_row_point(p1, J1[i], a6);
+    pose_row_point(p2, J2[i], b6);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.Jc[i][k] = a6[k] - b6[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      g1[i][k] = J1[i][0] * c.R[k] + J1[i][1] * c.R[3 + k] + J1[i][2] * c.R[6 + k];
+      g2[i][k] = J2[i][0] * c.R[k] + J2[i][1] * c.R[3 + k] + J2[i][2] * c.R[6 + k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T ek[3] = {T(0), T(0), T(0)}, dp[3];
+    ek[k] = T(1);
+    box_dir<T, TY>(b, X, ek, -1, dp);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) o.Jf[i][k] = g1[i][k] - dot3(g2[i], dp);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    T dp[3];
+    box_dir<T, TY>(b, X, X, k, dp);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const T v = -dot3(g2[i], dp);
+      if (k < 6) o.Jg[i][k] = v; else o.Jg2[i][k - 6] = v;
+    }
   }
 }
 

@@ -285,6 +285,7 @@ struct SlotArgs {
   const int32_t* cam_k;   // refined intrinsics: per camera its intrinsics entity (else null)
   int64_t kbase;          // A index of intrinsics entity 0
   int64_t sbase, nsp, ncy;   // A index of the first sphere; spheres, cylinders (cones follow)
+  int64_t bbase, nel, ncu;   // A index of the first ellipsoid entity; ellipsoids, cuboids
 };
 
 // the positional group of residual record i as an A index (plane, sphere, cylinder, cone), or -1
@@ -293,10 +294,20 @@ __device__ __forceinline__ int64_t pos_group(const SlotArgs& a, int k, int32_t g
   if (k == R_SPHERE_POINT) return a.sbase + g;
   if (k == R_CYL_POINT) return a.sbase + a.nsp + g;
   if (k == R_CONE_POINT) return a.sbase + a.nsp + a.ncy + g;
+  if (k == R_ELL_POINT) return a.bbase + g;
+  if (k == R_CUB_POINT) return a.bbase + 2 * a.nel + g;
+  return -1;
+}
+// a 9-parameter group's second entity (A index), or -1
+__device__ __forceinline__ int64_t pos_group2(const SlotArgs& a, int k, int32_t g) {
+  if (k == R_ELL_POINT) return a.bbase + a.nel + g;
+  if (k == R_CUB_POINT) return a.bbase + 2 * a.nel + a.ncu + g;
   return -1;
 }
 __device__ __forceinline__ uint8_t pos_type(const SlotArgs& a, int64_t e) {
-  return e < a.sbase ? ENT_PLANE : e < a.sbase + a.nsp ? ENT_SPHERE : e < a.sbase + a.nsp + a.ncy ? ENT_CYL : ENT_CONE;
+  return e < a.sbase ? ENT_PLANE : e < a.sbase + a.nsp ? ENT_SPHERE : e < a.sbase + a.nsp + a.ncy ? ENT_CYL
+       : e < a.bbase ? ENT_CONE : e < a.bbase + a.nel ? ENT_ELL1 : e < a.bbase + 2 * a.nel ? ENT_ELL2
+       : e < a.bbase + 2 * a.nel + a.ncu ? ENT_CUB1 : ENT_CUB2;
 }
 
 // intrinsics entity of residual j of a feature (-1: none)
@@ -312,7 +323,7 @@ __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
   const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.nf) return;
   int n = 0, prev = -1, vp = -1;
-  int64_t plane = -1;   // the positional group (A index)
+  int64_t plane = -1, second = -1;   // the positional group (A index) and a 9-parameter group's second entity
   const int32_t r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   for (int32_t j = r0; j < r1; ++j) {
     const int32_t i = a.order[j];
@@ -323,6 +334,7 @@ __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
     if (pg >= 0) {
       if (plane >= 0 && plane != pg) atomicOr(a.err, 1);
       plane = pg;
+      second = pos_group2(a, k, a.grp[i]);
     } else if (k == R_VP) {
       if (vp >= 0 && vp != a.grp[i]) atomicOr(a.err, 2);
       vp = a.grp[i];
@@ -335,7 +347,7 @@ __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
       n += seen ? 0 : 1;
     }
   }
-  nslot[f] = n + (plane >= 0) + (vp >= 0);
+  nslot[f] = n + (plane >= 0) + (second >= 0) + (vp >= 0);
 }
 
 struct SlotFill {
@@ -351,13 +363,13 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
   const int32_t r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   int32_t e = (int32_t)soff[f];
   int prev = -1, vp = -1;
-  int64_t plane = -1;   // the positional group (A index)
+  int64_t plane = -1, second = -1;   // the positional group (A index) and a 9-parameter group's second entity
   for (int32_t j = r0; j < r1; ++j) {
     const int32_t i = a.order[j];
     const int c = a.cam[i];
     const int k = a.kind[i];
     const int64_t pg = pos_group(a, k, a.grp[i]);
-    if (pg >= 0) plane = pg;
+    if (pg >= 0) { plane = pg; second = pos_group2(a, k, a.grp[i]); }
     if (k == R_VP) vp = a.grp[i];
     if (c >= 0 && a.fixed[c] != 0x3F) {
       if (c != prev) {
@@ -377,6 +389,12 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
     o.slot_ent[e] = (int32_t)plane;
     o.slot_feat[e] = (int32_t)f;
     o.slot_type[e] = pos_type(a, plane);
+    ++e;
+  }
+  if (second >= 0) {   // right after the first entity's slot (points have no VP slot)
+    o.slot_ent[e] = (int32_t)second;
+    o.slot_feat[e] = (int32_t)f;
+    o.slot_type[e] = pos_type(a, second);
     ++e;
   }
   const int32_t vp_slot = vp >= 0 ? e : -1;
@@ -557,7 +575,9 @@ __global__ void k_pair_gen(PairGen g) {
         if (ti == ENT_CAM && tj == ENT_PLANE) code = PAIR_CP;
         else if (ti == ENT_CAM && tj == ENT_INTR && g.cam_k && g.kbase + g.cam_k[a] == b) code = PAIR_CK;
         else if (ti == ENT_PLANE && tj == ENT_INTR) code = PAIR_PK;
-        else if (ti == ENT_CAM && tj >= ENT_SPHERE) code = PAIR_CS;
+        else if (ti == ENT_CAM && ent_second(tj)) code = PAIR_CK;
+        else if (ti == ENT_CAM && ent_surface(tj)) code = PAIR_CS;
+        else if ((ti == ENT_ELL1 && tj == ENT_ELL2) || (ti == ENT_CUB1 && tj == ENT_CUB2)) code = PAIR_G12;
       }
       g.gj[q] = (int32_t)((uint32_t)j | (code << PAIR_SHIFT));
       atomicAdd(&g.ucnt[u], 1ull);
@@ -632,7 +652,7 @@ struct ObsGather {
   int64_t n, o;
   const int32_t *cam, *feat, *other;
   const double* meas;
-  int64_t np, nl, nc, npl, nv, nsp, ncy, nco;
+  int64_t np, nl, nc, npl, nv, nsp, ncy, nco, nel, ncu;
   int8_t* kind_d;
   int32_t *cam_d, *feat_d, *grp_d;
   double* meas_d;
@@ -662,7 +682,8 @@ __global__ void k_gather_obs(ObsGather a) {
     if (g < 0 || g >= a.nv) code = 4;
   } else if (!code && k >= R_SPHERE_POINT) {
     g = a.other[i];
-    if (g < 0 || g >= (k == R_SPHERE_POINT ? a.nsp : k == R_CYL_POINT ? a.ncy : a.nco)) code = 7;
+    if (g < 0 || g >= (k == R_SPHERE_POINT ? a.nsp : k == R_CYL_POINT ? a.ncy : k == R_CONE_POINT ? a.nco
+                       : k == R_ELL_POINT ? a.nel : a.ncu)) code = 7;
   } else if (!code && (k == R_P2L || k == R_L2P) && a.other) {
     const int32_t q = a.other[i];
     if (q < 0 || q >= (k == R_P2L ? a.nl : a.np)) code = 5;
@@ -730,7 +751,7 @@ __global__ void k_kind_key(const int8_t* __restrict__ kind, int64_t n, uint32_t*
 }
 
 __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int64_t nsp, int64_t ncy, int64_t nco,
-                           uint8_t* __restrict__ t) {
+                           int64_t nel, int64_t ncu, uint8_t* __restrict__ t) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= na) return;
   int64_t b = nc;
@@ -740,7 +761,11 @@ __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int6
   b += nv; if (a >= b) ty = ENT_SPHERE;
   b += nsp; if (a >= b) ty = ENT_CYL;
   b += ncy; if (a >= b) ty = ENT_CONE;
-  b += nco; if (a >= b) ty = ENT_INTR;
+  b += nco; if (a >= b) ty = ENT_ELL1;
+  b += nel; if (a >= b) ty = ENT_ELL2;
+  b += nel; if (a >= b) ty = ENT_CUB1;
+  b += ncu; if (a >= b) ty = ENT_CUB2;
+  b += ncu; if (a >= b) ty = ENT_INTR;
   t[a] = ty;
 }
 
@@ -780,9 +805,12 @@ ba_status build_structure(Problem& P) {
   d.nsp = (int64_t)P.h_sph.size() / 4;
   d.ncy = (int64_t)P.h_cyl.size() / 7;
   d.nco = (int64_t)P.h_cone.size() / 7;
-  if (d.ngs() && d.nk) return fail(P, BA_ERR_ARG, "refined intrinsics (cam_dof 9) together with spheres, cylinders "
-                                                  "or cones are not supported");
-  d.na = d.nc + d.npl + d.nv + d.ngs() + d.nk;
+  d.nel = (int64_t)P.h_ell.size() / 10;
+  d.ncu = (int64_t)P.h_cub.size() / 10;
+  if ((d.ngs() || d.nbx()) && d.nk)
+    return fail(P, BA_ERR_ARG, "refined intrinsics (cam_dof 9) together with spheres, cylinders, cones, ellipsoids "
+                               "or cuboids are not supported");
+  d.na = d.nc + d.npl + d.nv + d.ngs() + 2 * d.nbx() + d.nk;
   if (d.na > (int64_t)1 << 30 || d.nf > (int64_t)1 << 30) return fail(P, BA_ERR_ARG, "too many entities");
   // the pattern bitmap holds na x na bits
   const int64_t wpr = (d.na + 31) / 32;
@@ -845,6 +873,28 @@ ba_status build_structure(Problem& P) {
     o[6] = K_[6];
   }
 
+  // ---- ellipsoids (q, c, s > 0) and cuboids (q, d_0..5): R row-major from the unit quaternion (w, x, y, z),
+  // BOX_STRIDE values each
+  std::vector<double> bx(BOX_STRIDE * (size_t)d.nbx(), 0.0);
+  for (int64_t i = 0; i < d.nbx(); ++i) {
+    const bool ell = i < d.nel;
+    const double* G_ = ell ? &P.h_ell[10 * i] : &P.h_cub[10 * (i - d.nel)];
+    double* o = &bx[BOX_STRIDE * i];
+    const double qn = std::sqrt(G_[0] * G_[0] + G_[1] * G_[1] + G_[2] * G_[2] + G_[3] * G_[3]);
+    bool bad = !(qn > 0) || !std::isfinite(qn);
+    for (int k = 4; k < 10; ++k) bad |= !std::isfinite(G_[k]);
+    if (ell) for (int k = 7; k < 10; ++k) bad |= !(G_[k] > 0);
+    if (bad)
+      return fail(P, BA_ERR_ARG, std::string(ell ? "ellipsoid " : "cuboid ") + std::to_string(ell ? i : i - d.nel) +
+                                     (ell ? ": zero quaternion or a semi-axis that is not positive" : ": zero quaternion"));
+    const double w = G_[0] / qn, x = G_[1] / qn, y = G_[2] / qn, z = G_[3] / qn;
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                         2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    for (int k = 0; k < 9; ++k) o[k] = R[k];
+    for (int k = 0; k < 6; ++k) o[9 + k] = G_[4 + k];
+  }
+
   // ---- residual records: validated and merged in input order on the device (below)
   int64_t nr = 0;
   for (auto& b : P.d_obs) nr += b.n;
@@ -870,7 +920,7 @@ ba_status build_structure(Problem& P) {
     CU(cudaMemcpyAsync(err, &none, sizeof(none), cudaMemcpyHostToDevice, P.stream));
     int64_t o = 0;
     for (auto& b : P.d_obs) {
-      ObsGather g{b.kind, b.md, b.n, o, b.cam, b.feat, b.other, b.meas, d.np, d.nl, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco,
+      ObsGather g{b.kind, b.md, b.n, o, b.cam, b.feat, b.other, b.meas, d.np, d.nl, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco, d.nel, d.ncu,
                   kind_d, cam_d, feat_d, grp_d, meas_d, err};
       k_gather_obs<<<grid_of(b.n, NT), NT, 0, P.stream>>>(g);
       o += b.n;
@@ -894,7 +944,7 @@ ba_status build_structure(Problem& P) {
       if (code == 3) return fail(P, BA_ERR_ARG, "plane id out of range");
       if (code == 4) return fail(P, BA_ERR_ARG, "vp id out of range");
       if (code == 5) return fail(P, BA_ERR_ARG, "partner feature id out of range");
-      if (code == 7) return fail(P, BA_ERR_ARG, "sphere, cylinder or cone id out of range");
+      if (code == 7) return fail(P, BA_ERR_ARG, "sphere, cylinder, cone, ellipsoid or cuboid id out of range");
       return fail(P, BA_ERR_ARG, "non-finite measurement");
     }
     P.release_obs();
@@ -937,7 +987,7 @@ ba_status build_structure(Problem& P) {
   }
   const int64_t kbase = d.kbase();
   SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d, P.cam_k, kbase,
-              d.sbase(), d.nsp, d.ncy};
+              d.sbase(), d.nsp, d.ncy, d.bbase(), d.nel, d.ncu};
   int64_t* soff = S.get<int64_t>(nf + 1);
   if (!soff) return oom();
   k_slot_count<<<grid_of(nf, NT), NT, 0, P.stream>>>(sa, cnt64);
@@ -947,7 +997,9 @@ ba_status build_structure(Problem& P) {
   int herr = 0;
   CU(cudaMemcpyAsync(&herr, err_d, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
   CU(cudaStreamSynchronize(P.stream));
-  if (herr & 1) return fail(P, BA_ERR_ARG, "a feature may be associated with at most one plane, sphere, cylinder or cone");
+  if (herr & 1)
+    return fail(P, BA_ERR_ARG, "a feature may be associated with at most one plane, sphere, cylinder, cone, ellipsoid "
+                               "or cuboid");
   if (herr & 2) return fail(P, BA_ERR_ARG, "a line may be associated with at most one VP");
   if (ne > (int64_t)INT32_MAX - 1) return fail(P, BA_ERR_ARG, "too many slots");
   d.ne = ne;
@@ -1115,7 +1167,8 @@ ba_status build_structure(Problem& P) {
   }
   P.ent_type = P.dnew<uint8_t>(na);
   if (!P.ent_type) return oom();
-  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco, P.ent_type);
+  if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco, d.nel, d.ncu,
+                                                            P.ent_type);
 
   // ---- parameters
 #define UP(dst, src) if ((s = upload(P, dst, src)) != BA_OK) return s
@@ -1125,6 +1178,7 @@ ba_status build_structure(Problem& P) {
     UP(S_.cam, P.h_cam); UP(S_.pts, P.h_pts); UP(S_.lin, P.h_lin); UP(S_.pln, P.h_pln); UP(S_.vps, P.h_vps);
     if (d.nk) UP(S_.intr, P.h_intr);
     if (d.ngs()) UP(S_.srf, srf);
+    if (d.nbx()) UP(S_.bx, bx);
     S_.camD = P.dnew<double>(d.nc * CAM_STRIDE);
     S_.grpD = P.dnew<double>((d.npl + d.nv) * GRP_STRIDE);
     if (!S_.camD || !S_.grpD) return oom();

@@ -1,6 +1,7 @@
-"""Spheres, cylinders and cones (Appendix B, Table 6) through the C ABI against the FP64 oracle: the
-group-induced point residual of Eq. 7 with each type's projection, its 4-, 5- and 6-wide group blocks in the
-reduced system, the log-space radius and the cone's half-angle.  FP64 path at 1e-9: cost (1e-12), S and b, the
+"""Spheres, cylinders, cones, ellipsoids and cuboids (Appendix B, Table 6) through the C ABI against the FP64
+oracle: the group-induced point residual of Eq. 7 with each type's projection, its 4-, 5- and 6-wide group
+blocks in the reduced system (a 9-parameter group as two entities, 6 + 3), the log-space radii and semi-axes,
+the cone's half-angle, the cuboid's nearest face.  FP64 path at 1e-9: cost (1e-12), S and b, the
 step and the predicted decrease, and an LM run with the oracle's decisions; the mixed step within 1e-5 (S, b)
 and 1e-3 (step) of FP64; refusals (batched windows, refined intrinsics, bad parameters)."""
 import numpy as np
@@ -32,8 +33,8 @@ _SC = {}
 
 def scene(name):
     if name not in _SC:
-        kw = dict(n_spheres=2, n_cylinders=2, n_cones=2) if name == "tiny" else \
-            dict(n_spheres=3, n_cylinders=3, n_cones=3, surf_points=150)
+        kw = dict(n_spheres=2, n_cylinders=2, n_cones=2, n_ellipsoids=2, n_cuboids=2) if name == "tiny" else \
+            dict(n_spheres=3, n_cylinders=3, n_cones=3, n_ellipsoids=3, n_cuboids=3, surf_points=150)
         _SC[name] = make_scene(config(name, **kw))
     return _SC[name]
 
@@ -96,7 +97,8 @@ def test_surface_lm_trajectory(B):
     try:
         reps = [B.ba_lm_step(p).as_dict() for _ in range(10)]
         got = {k: B.ba_get_groups(p, kind, len(s[k])) for k, kind in
-               (("spheres", B.BA_SPHERE), ("cylinders", B.BA_CYLINDER), ("cones", B.BA_CONE))}
+               (("spheres", B.BA_SPHERE), ("cylinders", B.BA_CYLINDER), ("cones", B.BA_CONE),
+                ("ellipsoids", B.BA_ELLIPSOID), ("cuboids", B.BA_CUBOID))}
     finally:
         B.ba_destroy(p)
     st, lay = oracle_setup(s)
@@ -111,6 +113,10 @@ def test_surface_lm_trajectory(B):
     assert sum(r["accepted"] for r in reps) >= 5
     for k in ("spheres", "cylinders", "cones"):
         assert rel(got[k], st[k]) <= FP64_TOL, (k, rel(got[k], st[k]))
+    for k in ("ellipsoids", "cuboids"):
+        # the library returns (quaternion, 6 values), the oracle keeps (R, 6 values)
+        R = O.quat_to_R(torch.from_numpy(got[k][:, :4])).numpy().reshape(-1, 9)
+        assert rel(np.concatenate([R, got[k][:, 4:]], 1), st[k]) <= FP64_TOL, k
 
 
 def test_surface_mixed_step_against_fp64(B):
