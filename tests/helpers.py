@@ -43,6 +43,12 @@ def padded_to_oracle_index(scene, lay):
         for g in range(lay.ngs.get(gk, 0) if hasattr(lay, "ngs") else 0):
             idx += list(range(6 * o, 6 * o + O.GDOF[gk]))
             o += 1
+    for gk in O.SPLIT:   # a 9-parameter kind: all first entities (6), then all second entities (3)
+        ng = lay.ngs.get(gk, 0) if hasattr(lay, "ngs") else 0
+        for w in (6, 3):
+            for g in range(ng):
+                idx += list(range(6 * o, 6 * o + w))
+                o += 1
     for k in range(getattr(lay, "nk", 0)):
         idx += list(range(6 * (o + k), 6 * (o + k) + 3))
     return np.array(idx, np.int64)
