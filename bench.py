@@ -512,13 +512,14 @@ def main():
                       "3D distances, one per feature on a plane, w_group3d = 100; 5 steps timed after 3 warm-up"}
         del s3, ob
 
-    # ---------------- spheres, cylinders and cones (Appendix B, Table 6): the medium scene (200 cameras) with 30 of
-    # each type, 300 points on each surface; LM iterations per second with the group-induced point residuals of
-    # the three types, against the same scene without them
+    # ---------------- spheres, cylinders, cones, ellipsoids, cuboids (Appendix B, Table 6): the medium scene (200
+    # cameras) with 30 of each type, 300 points on each surface; LM iterations per second with the group-induced
+    # point residuals of the five types, against the same scene without them
     srf = None
     if not args.no_surfaces:
         res_s = {}
-        for label, kw in (("without", {}), ("with", dict(n_spheres=30, n_cylinders=30, n_cones=30, surf_points=300))):
+        for label, kw in (("without", {}), ("with", dict(n_spheres=30, n_cylinders=30, n_cones=30, n_ellipsoids=30,
+                                                          n_cuboids=30, surf_points=300))):
             ss = make_scene(scfg("medium", seed=scfg("medium").seed + rank, **kw))
             q = B.ba_create(B.ba_default_options(precision=prec, cuda_stream=stream.cuda_stream))
             B.load_scene(q, ss)
@@ -541,9 +542,11 @@ def main():
                             "cost_after_8_steps_over_initial": round(E1 / E0, 5)}
             if label == "with":
                 res_s[label]["surface_residuals"] = {k: int(len(ss["obs"][k]["feat"])) for k in
-                                                     ("sphere_point", "cylinder_point", "cone_point")}
+                                                     ("sphere_point", "cylinder_point", "cone_point",
+                                                      "ellipsoid_point", "cuboid_point")}
         srf = dict(res_s, note="the medium scene (200 cameras, 100k points, 20k lines) without and with 30 spheres, "
-                               "30 cylinders and 30 cones of 300 points each; 5 steps timed after 3 warm-up")
+                               "cylinders, cones, ellipsoids and cuboids each, 300 points on each; 5 steps timed "
+                               "after 3 warm-up")
 
     # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
     # at the initial damping (the FP64 path itself is checked against the oracle at 2000 cameras by
