@@ -425,10 +425,20 @@ static ba_status plan_pcg_typed(ba_problem* p, const TypedPlan& tp) {
     for (int k = 0; k < 2; ++k) gvi[3 * d.npl + 2 * v + k] = (int32_t)(6 * (nc + d.npl + v) + k);
   for (int64_t q = 0; q < d.nk; ++q)
     for (int k = 0; k < 3; ++k) gvi[3 * d.npl + 2 * d.nv + 3 * q + k] = (int32_t)(6 * (nc + d.npl + d.nv + q) + k);
-  // shared memory: the fixed part (stage, group accumulators and operands) and one segment of 6 sums per
-  // (warp, camera row it touches)
+  // the owned values of every CTA (its whole camera rows and its group rows), kept in shared memory
+  int64_t nown = 0;
+  for (int64_t c = 0; c < G; ++c) {
+    const int32_t q0 = cta_part[4 * c], t0 = cta_part[4 * c + 2], t1 = cta_part[4 * c + 3];
+    const int32_t o0 = (t0 < t1 && tp.row_chunk0[t0] != q0) ? t0 + 1 : t0;
+    nown = std::max<int64_t>(nown, 6 * ((int64_t)std::max(0, t1 - o0) + (gs[c + 1] - gs[c])));
+  }
+  nown = std::max<int64_t>(nown, 2);
+  // shared memory: the fixed part (stage, group accumulators and operands), the owned vectors (6 doubles and 6
+  // values of the block inverses per owned value) and one segment of 6 sums per (warp, camera row it touches)
   const size_t seg = (mx ? sizeof(float) * 2 : sizeof(double)) * 6 * ((size_t)maxrows + 16);
-  const size_t smem = (mx ? pcg_typed_fixed_smem<float>(p->gv) : pcg_typed_fixed_smem<double>(p->gv)) + seg;
+  const size_t own = sizeof(double) * 6 * (size_t)nown + (((mx ? sizeof(float) : sizeof(double)) * 6 * (size_t)nown + 15) & ~(size_t)15);
+  const size_t smem = (mx ? pcg_typed_fixed_smem<float>(p->gv) : pcg_typed_fixed_smem<double>(p->gv)) + own + seg;
+  p->pcg_nown = (int)nown;
   if (smem > 227 * 1024)
     return set_err(p, BA_ERR_ARG, "reduced system too large or irregular for the PCG partition");
   const int per_sm = mx ? pcg_typed_blocks_per_sm<float>(smem) : pcg_typed_blocks_per_sm<double>(smem);

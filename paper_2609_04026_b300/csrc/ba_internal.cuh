@@ -329,6 +329,7 @@ struct ba_problem {
   int32_t *rp_ptr = nullptr, *rp_idx = nullptr, *rp_pos = nullptr;
   double *rel_lin = nullptr, *relH = nullptr, *relG = nullptr;
   int pcg_grid = 0;
+  int pcg_nown = 0;              // typed PCG: the most values any CTA owns (its shared-memory vector room)
   size_t pcg_smem = 0;
   cudaError_t pcg_err = cudaSuccess;
   // numeric arrays

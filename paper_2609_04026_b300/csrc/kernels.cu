@@ -2164,6 +2164,7 @@ struct PcgTypedArgs {
   int max_iters;
   float keep_frac;
   long long budget;
+  int nown;                       // shared-memory room for the owned values (the most any CTA owns)
 };
 
 // one operand value: the (hi, lo) split of an FP64 value for float S, the value itself for double S
@@ -2255,7 +2256,15 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   T* stage = reinterpret_cast<T*>(dyn);                                                    // [NW][NBUF][32 x 36]
   DotAcc<T>* gacc = reinterpret_cast<DotAcc<T>*>(dyn + typed_stage_bytes<T>());           // [NW][gvp]
   UGv<T>* ug = reinterpret_cast<UGv<T>*>(reinterpret_cast<unsigned char*>(gacc) + sizeof(DotAcc<T>) * NW * gvp);
-  DotAcc<T>* seg = reinterpret_cast<DotAcc<T>*>(dyn + typed_fixed_smem<T>(a.gv));         // [row segments][6]
+  // the owned values' vectors stay in shared memory across iterations: x, r, p, s, w, u (double) and the
+  // owned block rows' block-Jacobi inverses (36 per row); only u (which every CTA gathers), the carries and the
+  // group scatter go through global memory
+  double* sv = reinterpret_cast<double*>(dyn + typed_fixed_smem<T>(a.gv));
+  double *sx = sv, *sr = sv + a.nown, *sp = sv + 2 * a.nown, *ss = sv + 3 * a.nown, *sw = sv + 4 * a.nown,
+         *su = sv + 5 * a.nown;
+  T* sM = reinterpret_cast<T*>(sv + 6 * a.nown);                                           // [owned rows][36]
+  DotAcc<T>* seg = reinterpret_cast<DotAcc<T>*>(
+      reinterpret_cast<unsigned char*>(sM) + ((sizeof(T) * 6 * (size_t)a.nown + 15) & ~(size_t)15));   // [row segments][6]
   __shared__ __align__(8) uint64_t bars[NW][NBUF];
   __shared__ __align__(128) int cols[NW][NBUF][TCHUNK];
   __shared__ int wfirst[NW], wlast[NW], wbase[NW + 1];
@@ -2303,10 +2312,13 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   // the owned values: camera rows [o0, r1) and group rows [gs0, gs1) (6 per row)
   const int64_t cb0 = 6 * (int64_t)o0, cb1 = 6 * (int64_t)r1;
   const int64_t gb0 = 6 * (a.nc + gs0), gb1 = 6 * (a.nc + gs1);
+  // f(global index, local index) over the owned values
   auto owned = [&](auto&& f) {
-    for (int64_t k = cb0 + threadIdx.x; k < cb1; k += NT) f(k);
-    for (int64_t k = gb0 + threadIdx.x; k < gb1; k += NT) f(k);
+    for (int64_t k = cb0 + threadIdx.x; k < cb1; k += NT) f(k, (int)(k - cb0));
+    for (int64_t k = gb0 + threadIdx.x; k < gb1; k += NT) f(k, (int)(cb1 - cb0 + k - gb0));
   };
+  auto loc_cam = [&](int64_t k) { return (int)(k - cb0); };                 // an owned camera value
+  auto loc_grp = [&](int64_t k) { return (int)(cb1 - cb0 + k - gb0); };     // an owned group value
   // group row g's group values: first value offset and count
   auto gval = [&](int g, int& k0, int& nd) {
     if (g < a.npl) { k0 = 3 * g; nd = 3; }
@@ -2475,12 +2487,21 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
         if (wfirst[w] <= rr && rr <= wlast[w])
 #pragma unroll
           for (int i = 0; i < 6; ++i) acc_add(y[i], seg[6 * (wbase[w] + rr - wfirst[w]) + i]);
-      double* dst = rr < o0 ? a.carry + 6 * (size_t)c : a.w + 6 * (size_t)rr;
+      if (rr < o0) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        const double yv = y[i].value();
-        dst[i] = yv;
-        v += yv * __ldcg(&a.u[6 * (size_t)rr + i]);
+        for (int i = 0; i < 6; ++i) {
+          const double yv = y[i].value();
+          a.carry[6 * (size_t)c + i] = yv;
+          v += yv * __ldcg(&a.u[6 * (size_t)rr + i]);
+        }
+      } else {
+        const int l0 = loc_cam(6 * (int64_t)rr);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const double yv = y[i].value();
+          sw[l0 + i] = yv;
+          v += yv * su[l0 + i];
+        }
       }
     }
     // the group values of this CTA's scatter, warps in order; their dot with u in the working precision
@@ -2538,10 +2559,10 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       if (lane == 0) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-          const size_t o = 6 * ((size_t)a.nc + g) + i;
+          const int l = loc_grp(6 * ((int64_t)a.nc + g) + i);
           const double yv = y[i].value();
-          a.w[o] = yv;
-          v += yv * __ldcg(&a.u[o]);
+          sw[l] = yv;
+          v += yv * su[l];
         }
       }
     }
@@ -2552,13 +2573,14 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   auto add_carries = [&]() {
     if (tail_cut && threadIdx.x < 6) {
       const int rrow = r1 - 1;
-      double v = a.w[6 * (size_t)rrow + threadIdx.x];
+      const int l = loc_cam(6 * (int64_t)rrow + threadIdx.x);
+      double v = sw[l];
       for (int c2 = c + 1; c2 < G; ++c2) {
         const int4 pn = a.cta_part[c2];
         if (pn.x == pn.y || pn.z != rrow) break;
         v += __ldcg(&a.carry[6 * (size_t)c2 + threadIdx.x]);
       }
-      a.w[6 * (size_t)rrow + threadIdx.x] = v;
+      sw[l] = v;
     }
     // a warp per owned group value, its lanes over the CTAs (a fixed order: strided lane sums, then the
     // warp's shuffle tree)
@@ -2570,20 +2592,20 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       double v = 0;
       for (int c2 = lane; c2 < G; c2 += 32) v += __ldcg(&a.part_g[(size_t)(k0 + d) * G + c2]);
       v = warp_sum(v);
-      if (lane == 0) a.w[6 * ((size_t)a.nc + g) + d] += v;
+      if (lane == 0) sw[loc_grp(6 * ((int64_t)a.nc + g) + d)] += v;
     }
   };
   auto precondition = [&](double& ru, double& rr_) {
     double v0 = 0, v1 = 0;
-    owned([&](int64_t k) {
-      const int64_t rw = k / 6;
-      const int i = (int)(k - 6 * rw);
-      const T* M = a.Minv + (size_t)rw * BS2 + 6 * i;
-      const double* rv = a.r + 6 * (size_t)rw;
+    owned([&](int64_t k, int l) {
+      const int i = (int)(k % 6);
+      const T* M = sM + 6 * (size_t)l;        // row i of the block (the owned rows are whole)
+      const double* rv = sr + (l - i);
       T zs = 0;
 #pragma unroll
       for (int j = 0; j < 6; ++j) zs += M[j] * (T)rv[j];
       const double z = (double)zs, ri = rv[i];
+      su[l] = z;
       a.u[k] = z;
       if (a.uhl) a.uhl[k] = split2(z);
       v0 += ri * z;
@@ -2599,8 +2621,14 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
     return grid_barrier(a.S, (unsigned)G, a.budget);
   };
 
-  // ---- start: x = 0, r = b, u = M^-1 r, w = S u
-  owned([&](int64_t k) { a.x[k] = 0; a.r[k] = a.b[k]; });
+  // ---- start: x = 0, r = b, the owned rows' block inverses into shared memory, u = M^-1 r, w = S u
+  owned([&](int64_t k, int l) {
+    sx[l] = 0;
+    sr[l] = a.b[k];
+    const T* M = a.Minv + (size_t)(k / 6) * BS2 + 6 * (k % 6);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sM[6 * (size_t)l + j] = M[j];
+  });
   __syncthreads();
   double ru, rrl, wu;
   precondition(ru, rrl);
@@ -2649,13 +2677,13 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   int par = 1;
   while (!done) {
     const bool first = it == 0;
-    owned([&](int64_t k) {
-      const double pk = first ? a.u[k] : a.u[k] + beta * a.p[k];
-      const double sk = first ? a.w[k] : a.w[k] + beta * a.s[k];
-      a.p[k] = pk;
-      a.s[k] = sk;
-      a.x[k] += alpha * pk;
-      a.r[k] -= alpha * sk;
+    owned([&](int64_t, int l) {
+      const double pk = first ? su[l] : su[l] + beta * sp[l];
+      const double sk = first ? sw[l] : sw[l] + beta * ss[l];
+      sp[l] = pk;
+      ss[l] = sk;
+      sx[l] += alpha * pk;
+      sr[l] -= alpha * sk;
     });
     __syncthreads();
     precondition(ru, rrl);
@@ -2680,6 +2708,8 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
     par ^= 1;
   }
   drain();
+  __syncthreads();
+  owned([&](int64_t k, int l) { a.x[k] = sx[l]; });   // the solution of the owned values
   if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
   if (c == 0 && threadIdx.x == 0) {
     a.S->iters = it;
@@ -3503,6 +3533,7 @@ static void launch_pcg_typed(Problem& P) {
   a.tol = P.opt.pcg_rel_tol; a.max_iters = P.opt.pcg_max_iters;
   a.keep_frac = P.pcg_keep_frac;
   a.budget = P.opt.wait_budget_cycles > 0 ? P.opt.wait_budget_cycles : 1;
+  a.nown = P.pcg_nown;
   void* args[] = {&a};
   ++P.launches;
   // the grid barrier's arrival count starts at zero (a launch that gave up at a barrier may leave it set)
