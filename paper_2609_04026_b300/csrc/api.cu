@@ -106,6 +106,9 @@ extern "C" void ba_destroy(ba_problem* p) {
   if (p->hS) cudaFreeHost(p->hS);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  if (p->side) { cudaStreamSynchronize(p->side); cudaStreamDestroy(p->side); }
+  for (auto& e : p->sev)
+    if (e) cudaEventDestroy(e);
   cudaGetLastError();
   delete p;
 }
@@ -540,6 +543,9 @@ static ba_status freeze(ba_problem* p) {
   p->hS->max_iters = p->opt.pcg_max_iters;
   CUDA_OR(p, cudaMemcpyAsync(p->S, p->hS, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
   for (auto& e : p->ev) CUDA_OR(p, cudaEventCreate(&e));
+  // the second stream of the candidate's linearisation (beside the FP64 cost pass)
+  CUDA_OR(p, cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  for (auto& e : p->sev) CUDA_OR(p, cudaEventCreate(&e));
   // cost at the initial parameters
   CUDA_OR(p, ensure_ln1p_table(p->stream));
   if (mixed(p)) launch_prepare<float>(*p, false); else launch_prepare<double>(*p, false);
@@ -605,6 +611,7 @@ static ba_status build_reduced_t(ba_problem* p, double lambda, bool* relin) {
     launch_linearize<T>(*p);
     launch_rel_linearize(*p);
     p->have_lin = true;
+    p->spec_lin = false;
     if (relin) *relin = true;
   }
   MARK(0);
@@ -643,6 +650,7 @@ template <class T>
 static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
   const double lam = p->hS->lambda;
   bool relin = false;
+  const bool relin_spec = p->have_lin && p->spec_lin;   // this step's Jacobians were made by the previous step
   p->launches = 0;
   CUDA_OR(p, cudaEventRecord(p->ev[0], p->stream));
   ba_status s = build_reduced_t<T>(p, lam, &relin);
@@ -651,11 +659,29 @@ static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
   launch_candidate(*p);
   launch_prepare<T>(*p, true);
   MARK(7);
+  // The next step linearises at the candidate whenever this one accepts it (most steps): do it now, on the
+  // second stream, while the FP64 cost pass (FP64 pipe) evaluates the candidate; a rejection discards it.
+  const bool spec = p->side != nullptr;
+  if (spec) {
+    CUDA_OR(p, cudaEventRecord(p->sev[0], p->stream));
+    CUDA_OR(p, cudaStreamWaitEvent(p->side, p->sev[0], 0));
+    cudaStream_t main_stream = p->stream;
+    p->stream = p->side;
+    p->cur ^= 1;   // the candidate's parameter set
+    cudaEventRecord(p->sev[1], p->stream);
+    launch_prepare<T>(*p, false, true);
+    launch_linearize<T>(*p);
+    launch_rel_linearize(*p);
+    cudaEventRecord(p->sev[2], p->stream);
+    p->cur ^= 1;
+    p->stream = main_stream;
+  }
   launch_cost(*p, true);
   launch_rel_cost(*p, true);
   MARK(8);
   launch_decide(*p);
   MARK(9);
+  if (spec) CUDA_OR(p, cudaStreamWaitEvent(p->stream, p->sev[2], 0));
   if ((s = sync_scalars(p))) return s;
   DevScalars& h = *p->hS;
   ba_step_report r;
@@ -663,29 +689,38 @@ static ba_status lm_step_t(ba_problem* p, ba_step_report* rep) {
   r.cost = h.E; r.cost_px = h.Epx; r.cost_new = h.Enew; r.cost_px_new = h.Epxnew;
   r.pred = h.pred; r.gain = h.gain; r.lambda = lam;
   r.pcg_iters = h.iters; r.pcg_rel = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
-  r.accepted = h.accepted; r.relinearized = relin ? 1 : 0;
+  r.accepted = h.accepted; r.relinearized = (relin || relin_spec) ? 1 : 0;
   r.n_launches = p->launches;
   r.precond_fallbacks = -1;
   if (p->opt.precond == BA_PRECOND_LEARNED && p->pre_ready)
     CUDA_OR(p, cudaMemcpy(&r.precond_fallbacks, p->pre_fallbacks, sizeof(int), cudaMemcpyDeviceToHost));
   for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&r.ms_kernel[k], p->ev[k], p->ev[k + 1]);
+  if (p->spec_lin && relin_spec) r.ms_kernel[0] = p->spec_ms;   // made during the previous step
+  float spec_ms = 0.f;
+  if (spec) cudaEventElapsedTime(&spec_ms, p->sev[1], p->sev[2]);
   r.ms_linearize = r.ms_kernel[0];
   r.ms_schur = r.ms_kernel[1] + r.ms_kernel[2] + r.ms_kernel[3] + r.ms_kernel[4];
   r.ms_pcg = r.ms_kernel[5];
   r.ms_update = r.ms_kernel[6] + r.ms_kernel[7] + r.ms_kernel[8] + r.ms_kernel[9];
+  p->spec_lin = spec;
+  p->spec_ms = spec_ms;
   if (h.accepted) {
     double rel = std::fabs(h.Epx - h.Epxnew) / std::max(h.Epx, 1e-300);
     r.converged = rel < p->opt.rel_cost_tol ? 1 : 0;
     p->cur ^= 1;
-    p->have_lin = false;
+    p->have_lin = spec;   // the candidate's linearisation is the new point's
     p->have_reduced = false;
     // the accepted cost becomes the current cost
     h.E = h.Enew; h.Epx = h.Epxnew;
     CUDA_OR(p, cudaMemcpyAsync(&p->S->E, &h.E, 2 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-  } else if (lam >= p->opt.lambda_max) {
-    // rejected at the largest damping: no step lowers the cost at the working precision (the analogue of
-    // a trust region shrunk to its minimum radius), so the iteration has converged
-    r.converged = 1;
+  } else {
+    // the slot records now hold the candidate's linearisation: the next step linearises the current point again
+    if (spec) p->have_lin = false;
+    if (lam >= p->opt.lambda_max) {
+      // rejected at the largest damping: no step lowers the cost at the working precision (the analogue of
+      // a trust region shrunk to its minimum radius), so the iteration has converged
+      r.converged = 1;
+    }
   }
   if (rep) *rep = r;
   if (!std::isfinite(h.E)) return set_err(p, BA_ERR_NUMERIC, "non-finite cost");

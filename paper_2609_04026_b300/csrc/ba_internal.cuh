@@ -190,7 +190,7 @@ struct Dims {
 };
 
 // kernel launchers (kernels.cu); T = double (FP64 path) or float (mixed path)
-template <class T> void launch_prepare(Problem& P, bool candidate_only);
+template <class T> void launch_prepare(Problem& P, bool candidate_only, bool working_only = false);
 template <class T> void launch_linearize(Problem& P);
 template <class T> void launch_invert(Problem& P, double lambda);
 template <class T> void launch_schur(Problem& P, double lambda);
@@ -372,6 +372,12 @@ struct ba_problem {
   ba::DevScalars* hS = nullptr; // pinned host mirror
 
   cudaEvent_t ev[16] = {};
+  // the candidate's linearisation, made on a second stream beside the FP64 cost pass of the step that forms the
+  // candidate; valid for the next step when the candidate is accepted
+  cudaStream_t side = nullptr;
+  cudaEvent_t sev[4] = {};   // fork, side start, side end (timing), join
+  bool spec_lin = false;      // the last step linearised its candidate
+  float spec_ms = 0.f;        // device time of that linearisation (on the side stream, overlapping the cost)
   int launches = 0;              // kernel launches since the start of the current step
 };
 

@@ -185,7 +185,8 @@ __device__ void derive_cam(const double* __restrict__ src, double* __restrict__ 
   quat_to_R(c, o);
   o[9] = c[4]; o[10] = c[5]; o[11] = c[6];
   o[12] = c[7]; o[13] = c[8]; o[14] = c[9]; o[15] = c[10]; o[16] = c[11];
-  for (int k = 0; k < 17; ++k) D[CAM_STRIDE * i + k] = o[k];
+  if (D)
+    for (int k = 0; k < 17; ++k) D[CAM_STRIDE * i + k] = o[k];
   if (W)
     for (int k = 0; k < 17; ++k) W[CAM_STRIDE * i + k] = (T)o[k];
 }
@@ -209,7 +210,8 @@ __device__ void derive_group(int64_t npl, const double* __restrict__ pln, const 
     o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = 0;
   }
   tangent_basis_d(o, o + 4, o + 7);
-  for (int k = 0; k < 10; ++k) D[GRP_STRIDE * i + k] = o[k];
+  if (D)
+    for (int k = 0; k < 10; ++k) D[GRP_STRIDE * i + k] = o[k];
   if (W)
     for (int k = 0; k < 10; ++k) W[GRP_STRIDE * i + k] = (T)o[k];
 }
@@ -3250,11 +3252,17 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
   }
 }
 
+// a grid of a few CTAs per SM striding over the residuals: the FP64 pipe bounds this pass, and the SMs keep
+// room for the candidate's linearisation that runs beside it on another stream
 template <bool EXT>
 __global__ void __launch_bounds__(256) k_cost(CostArgs a) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double v[2] = {0, 0};
-  if (t < a.nr) cost_residual<EXT>(a, a.order[t], v);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.nr; t += (int64_t)gridDim.x * blockDim.x) {
+    double w[2] = {0, 0};
+    cost_residual<EXT>(a, a.order[t], w);
+    v[0] += w[0];
+    v[1] += w[1];
+  }
   double tot[2];
   if (grid_reduce<2>(v, a.red, &a.S->counter[4], tot) && threadIdx.x == 0) {
     if (a.candidate) { a.S->Enew = tot[0]; a.S->Epxnew = tot[1]; }
@@ -3364,14 +3372,19 @@ static LossW make_loss(const ba_options& o) {
 
 
 template <class T>
-void launch_prepare(Problem& P, bool candidate_only) {
+void launch_prepare(Problem& P, bool candidate_only, bool working_only) {
   const Dims& d = P.d;
   auto& cs = P.ps[candidate_only ? 1 - P.cur : P.cur];
   T* camW = candidate_only ? nullptr : (T*)P.camT;
   T* grpW = candidate_only ? nullptr : (T*)P.grpT;
   if (sizeof(T) == sizeof(double)) { camW = nullptr; grpW = nullptr; }
-  if (d.nc) { ++P.launches; k_derive_cams<T><<<nblk(d.nc, 128), 128, 0, P.stream>>>(d.nc, cs.cam, cs.camD, camW); }
-  if (d.npl + d.nv) { ++P.launches; k_derive_groups<T><<<nblk(d.npl + d.nv, 128), 128, 0, P.stream>>>(d.npl, d.nv, cs.pln, cs.vps, cs.grpD, grpW); }
+  // working_only: the float working copies alone (the derived FP64 data of this set exist already and may be
+  // read by a kernel of another stream meanwhile)
+  double* camD = working_only ? nullptr : cs.camD;
+  double* grpD = working_only ? nullptr : cs.grpD;
+  if (working_only && !camW) return;
+  if (d.nc) { ++P.launches; k_derive_cams<T><<<nblk(d.nc, 128), 128, 0, P.stream>>>(d.nc, cs.cam, camD, camW); }
+  if (d.npl + d.nv) { ++P.launches; k_derive_groups<T><<<nblk(d.npl + d.nv, 128), 128, 0, P.stream>>>(d.npl, d.nv, cs.pln, cs.vps, grpD, grpW); }
   if (!candidate_only && sizeof(T) == sizeof(float)) {
     if (d.ngs()) {
       ++P.launches;
@@ -3636,8 +3649,14 @@ void launch_cost(Problem& P, bool candidate) {
   a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
   a.candidate = candidate ? 1 : 0;
   ++P.launches;
-  if (d.ngs() || d.nbx()) k_cost<true><<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
-  else k_cost<false><<<nblk(d.nr > 0 ? d.nr : 1, 256), 256, 0, P.stream>>>(a);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  const unsigned grid = (unsigned)std::min<int64_t>(nblk(d.nr > 0 ? d.nr : 1, 256), 2 * (int64_t)sms);
+  if (d.ngs() || d.nbx()) k_cost<true><<<grid, 256, 0, P.stream>>>(a);
+  else k_cost<false><<<grid, 256, 0, P.stream>>>(a);
 }
 
 void launch_decide(Problem& P) {
@@ -4126,7 +4145,7 @@ template int windows_per_sm<float>(int, size_t);
 template int windows_per_sm<double>(int, size_t);
 
 #define INST(T)                                         \
-  template void launch_prepare<T>(Problem&, bool);      \
+  template void launch_prepare<T>(Problem&, bool, bool); \
   template void launch_linearize<T>(Problem&);          \
   template void launch_invert<T>(Problem&, double);     \
   template void launch_schur<T>(Problem&, double);      \
