@@ -42,27 +42,27 @@ torch.set_default_dtype(torch.float64)
 DT = torch.float64
 
 KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
-         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point")
+         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point", "wf3d")
 # residual dimension, feature type, group type per kind
 RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1,
         "plane_point3d": 1, "plane_line3d": 2, "sphere_point": 2, "cylinder_point": 2, "cone_point": 2,
-        "ellipsoid_point": 2, "cuboid_point": 2}
+        "ellipsoid_point": 2, "cuboid_point": 2, "wf3d": 3}
 FEAT = {"point": "point", "line": "line", "plane_point": "point", "plane_line": "line",
         "vp": "line", "p2l": "point", "l2p": "line", "plane_point3d": "point", "plane_line3d": "line",
         "sphere_point": "point", "cylinder_point": "point", "cone_point": "point", "ellipsoid_point": "point",
-        "cuboid_point": "point"}
+        "cuboid_point": "point", "wf3d": "line"}
 GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp", "plane_point3d": "plane",
          "plane_line3d": "plane", "sphere_point": "sphere", "cylinder_point": "cylinder", "cone_point": "cone",
-         "ellipsoid_point": "ellipsoid", "cuboid_point": "cuboid"}
-HAS_CAM = {k: k not in ("vp", "plane_point3d", "plane_line3d") for k in KINDS}
-# kinds outside the pixel cost E_px: the angular VP term, and the direct 3D group distances
-NON_PIXEL = ("vp", "plane_point3d", "plane_line3d")
+         "ellipsoid_point": "ellipsoid", "cuboid_point": "cuboid", "wf3d": "jpoint"}
+HAS_CAM = {k: k not in ("vp", "plane_point3d", "plane_line3d", "wf3d") for k in KINDS}
+# kinds outside the pixel cost E_px: the angular VP term, and the direct 3D distances
+NON_PIXEL = ("vp", "plane_point3d", "plane_line3d", "wf3d")
 FDOF = {"point": 3, "line": 4}
-GDOF = {"plane": 3, "vp": 2, "sphere": 4, "cylinder": 5, "cone": 6, "ellipsoid": 9, "cuboid": 9}
+GDOF = {"plane": 3, "vp": 2, "sphere": 4, "cylinder": 5, "cone": 6, "ellipsoid": 9, "cuboid": 9, "jpoint": 3}
 # state key and stored width of every group kind (spheres (c, r); cylinders (d, m, r), the axis a Pluecker line
 # with |d| = 1; cones (apex, unit axis, half-angle))
 GKEY = {"plane": ("planes", 4), "vp": ("vps", 3), "sphere": ("spheres", 4), "cylinder": ("cylinders", 7),
-        "cone": ("cones", 7), "ellipsoid": ("ellipsoids", 15), "cuboid": ("cuboids", 15)}
+        "cone": ("cones", 7), "ellipsoid": ("ellipsoids", 15), "cuboid": ("cuboids", 15), "jpoint": ("points", 3)}
 SURFACES = ("sphere", "cylinder", "cone")
 # the 9-parameter groups: two entities of A each, the first 6 increments (rotation and centre, or rotation and
 # three face offsets) and the last 3 (log semi-axes, or the other three offsets)
@@ -82,6 +82,7 @@ class Options:
     cauchy_rel: float = 0.2
     w_group3d: float = 1.0    # the direct 3D group distances (Section 3.2's alternative; Table 5 weighs it)
     cauchy_3d: float = 1.0
+    w_wire3d: float = 1.0     # the 3D wireframe endpoint distance (the form Fig. 3b compares; scale cauchy_3d)
     cauchy_px: float = 1.0
     cauchy_vp: float = 0.2
     lambda0: float = 1e-4
@@ -98,10 +99,10 @@ class Options:
                 "plane_line": self.w_group, "vp": self.w_vp, "p2l": self.w_wire,
                 "l2p": self.w_wire, "plane_point3d": self.w_group3d, "plane_line3d": self.w_group3d,
                 "sphere_point": self.w_group, "cylinder_point": self.w_group, "cone_point": self.w_group,
-                "ellipsoid_point": self.w_group, "cuboid_point": self.w_group}[kind]
+                "ellipsoid_point": self.w_group, "cuboid_point": self.w_group, "wf3d": self.w_wire3d}[kind]
 
     def scale(self, kind):
-        if kind in ("plane_point3d", "plane_line3d"):
+        if kind in ("plane_point3d", "plane_line3d", "wf3d"):
             return self.cauchy_3d
         return self.cauchy_vp if kind == "vp" else self.cauchy_px
 
@@ -490,11 +491,17 @@ res_ellipsoid_point = _res_surface_point("ellipsoid")
 res_cuboid_point = _res_surface_point("cuboid")
 
 
+def res_wf3d(dc, df, dg, cam, feat, grp, meas):   # 3D wireframe endpoint distance: X x d - m (|d| = 1)
+    L = line_plus(feat, df)
+    X = grp[:3] + dg
+    return torch.linalg.cross(X, L[:3]) - L[3:6], torch.ones((), dtype=torch.bool)
+
+
 RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
           "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p,
           "plane_point3d": res_plane_point3d, "plane_line3d": res_plane_line3d,
           "sphere_point": res_sphere_point, "cylinder_point": res_cylinder_point, "cone_point": res_cone_point,
-          "ellipsoid_point": res_ellipsoid_point, "cuboid_point": res_cuboid_point}
+          "ellipsoid_point": res_ellipsoid_point, "cuboid_point": res_cuboid_point, "wf3d": res_wf3d}
 
 
 # ===========================================================================
@@ -595,6 +602,10 @@ def state_from_scene(scene):
         st["planes"] /= np.linalg.norm(st["planes"][:, :3], axis=1, keepdims=True)
     if len(st["vps"]):
         st["vps"] /= np.linalg.norm(st["vps"], axis=1, keepdims=True)
+    w3 = scene.get("obs", {}).get("wf3d")
+    if w3 is not None and len(w3["other"]):
+        # the 3D wireframe distance couples a point with a line feature: its points join the reduced system
+        st["jpoints"] = np.unique(np.asarray(w3["other"], np.int64))
     ik = scene.get("intrinsics")
     if ik is not None:
         # refined intrinsics (Section 3.1, K_c(i): image i uses the intrinsics of its camera model c(i)): the
@@ -747,8 +758,15 @@ class Layout:
         self.nk = state["intr"].shape[0] if "intr" in state else 0
         self.cam_k = state["cam_k"] if self.nk else np.full(self.nc, -1, np.int64)
         self.intr_col = o + 3 * np.arange(self.nk); o += 3 * self.nk
+        # points coupled with a line feature by the 3D wireframe distance: entities of A (after the intrinsics),
+        # the other points features
+        self.jpoints = np.asarray(state.get("jpoints", np.zeros(0, np.int64)), np.int64)
+        self.point_col = np.full(self.np_, -1, np.int64)
+        self.point_col[self.jpoints] = o + 3 * np.arange(len(self.jpoints)); o += 3 * len(self.jpoints)
         self.na = o
-        self.point_col = o + 3 * np.arange(self.np_); o += 3 * self.np_
+        rest = np.setdiff1d(np.arange(self.np_), self.jpoints)
+        self.point_col[rest] = o + 3 * np.arange(len(rest)); o += 3 * len(rest)
+        self.gcol["jpoint"] = self.point_col
         self.line_col = o + 4 * np.arange(self.nl); o += 4 * self.nl
         self.n = o
         # entity blocks of A (for block-Jacobi): (start, size); a camera's free columns are contiguous
@@ -758,8 +776,9 @@ class Layout:
                          [(int(c), GDOF[gk]) for gk in SURFACES for c in self.gcol[gk]] +
                          [(int(c), w) for gk in SPLIT for cs, w in ((self.gcol[gk], 6), (self.gcol2[gk], 3))
                           for c in cs] +
-                         [(int(c), 3) for c in self.intr_col])
-        self.f_blocks = [(int(c), 3) for c in self.point_col] + [(int(c), 4) for c in self.line_col]
+                         [(int(c), 3) for c in self.intr_col] +
+                         [(int(self.point_col[j]), 3) for j in self.jpoints])
+        self.f_blocks = [(int(c), 3) for c in self.point_col[rest]] + [(int(c), 4) for c in self.line_col]
 
 
 def linearize(state, obs, opt: Options, lay: Layout):

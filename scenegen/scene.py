@@ -31,6 +31,7 @@ Observation kinds (one record per residual):
   l2p        (cam, line,  point id of partner, meas 2 undistorted pt) Eq. 12
   plane_point3d (-1, point, plane, no meas)  direct 3D distance (Section 3.2's alternative, Table 5)
   plane_line3d  (-1, line,  plane, no meas)  direct 3D distances of a line (direction, foot point)
+  wf3d          (-1, line,  point, no meas)  3D wireframe endpoint distance X x d - m (Fig. 3b's form)
 """
 from __future__ import annotations
 
@@ -43,10 +44,10 @@ IMG_W, IMG_H = 800.0, 600.0
 HALF = 3.0
 
 KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
-         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point")
+         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point", "wf3d")
 MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2,
             "plane_point3d": 0, "plane_line3d": 0, "sphere_point": 0, "cylinder_point": 0, "cone_point": 0,
-            "ellipsoid_point": 0, "cuboid_point": 0}
+            "ellipsoid_point": 0, "cuboid_point": 0, "wf3d": 0}
 
 
 @dataclasses.dataclass
@@ -84,6 +85,10 @@ class SceneConfig:
     # "3d" the direct 3D distances to the plane instead (the alternative of Section 3.2, compared in Table 5),
     # "both" all of them; the observations are the same draws in every form
     group_form: str = "2d"
+    # form of the wireframe constraints: "2d" the cross-feature reprojection residuals (Eq. 11, Eq. 12), "3d"
+    # the 3D endpoint distance of each edge instead (the form Fig. 3b compares; it couples the point with the
+    # line), "both"
+    wire_form: str = "2d"
     # the other group types of Appendix B (spheres, cylinders, cones), each with surf_points points on its
     # surface, drawn with a generator of their own after everything else (the rest of the scene is unchanged)
     n_spheres: int = 0
@@ -481,6 +486,20 @@ def make_scene(cfg: SceneConfig) -> dict:
         obs[name] = dict(cam=np.array(d["cam"], np.int32), feat=np.array(d["feat"], np.int32),
                          other=np.array(d["other"], np.int32),
                          meas=np.array(d["meas"], np.float64).reshape(-1, md))
+    # the 3D endpoint distance of every edge whose point and line are both observed (line = the feature, point =
+    # the other id); no camera, no measurement
+    seen_p = set(int(x) for x in pf) if len(pf) else set()
+    seen_l = set(int(x) for x in lf) if len(lf) else set()
+    e3 = np.array([(k, j) for j, k in edges if j in seen_p and k in seen_l], np.int64).reshape(-1, 2)
+    obs["wf3d"] = dict(cam=np.full(len(e3), -1, np.int32), feat=e3[:, 0].astype(np.int32),
+                       other=e3[:, 1].astype(np.int32), meas=np.zeros((len(e3), 0)))
+    if cfg.wire_form == "2d":
+        obs["wf3d"] = {kk: vv[:0] for kk, vv in obs["wf3d"].items()}
+    elif cfg.wire_form == "3d":
+        for k_ in ("p2l", "l2p"):
+            obs[k_] = {kk: vv[:0] for kk, vv in obs[k_].items()}
+    elif cfg.wire_form != "both":
+        raise ValueError(cfg.wire_form)
 
     # ---- ground truth and perturbed initial values
     qgt = _mat_to_quat(Rgt)

@@ -146,8 +146,8 @@ def test_noise_free_zero_cost_and_zero_step():
 def tiny_both():
     """The tiny scene with both forms of the plane constraints (group-induced 2D and direct 3D) and two spheres,
     cylinders and cones (Appendix B)."""
-    s = make_scene(config("tiny", group_form="both", n_spheres=2, n_cylinders=2, n_cones=2, n_ellipsoids=2,
-                          n_cuboids=2))
+    s = make_scene(config("tiny", group_form="both", wire_form="both", n_spheres=2, n_cylinders=2, n_cones=2,
+                          n_ellipsoids=2, n_cuboids=2))
     return s, O.state_from_scene(s), s["fixed"]
 
 
@@ -730,3 +730,26 @@ def test_nine_parameter_groups_ground_truth_and_retractions():
     lay = O.Layout(st, s["fixed"])
     assert np.all(np.diff(lay.gcol["ellipsoid"]) == 6) and np.all(np.diff(lay.gcol2["cuboid"]) == 3)
     assert (6, 6) == (lay.gcol2["ellipsoid"][0] - lay.gcol["ellipsoid"][-1], lay.gcol["cuboid"][0] - lay.gcol2["ellipsoid"][-1] + 3)
+
+
+# ---------------------------------------------------------------- the 3D wireframe endpoint distance (Fig. 3b)
+def test_wf3d_closed_form_and_layout():
+    """X x d - m: a point at the origin and the line y = 1 along x (d = (1,0,0), m = p x d = (0,0,-1)) are at
+    distance 1, r = (0, 0, 1); a point on the line gives 0.  The points it couples with a line feature are
+    entities of A (their columns among the reduced system's), the others stay features."""
+    L = torch.tensor([1.0, 0.0, 0.0, 0.0, 0.0, -1.0])
+    z = torch.zeros(3)
+    r, _ = O.res_wf3d(torch.zeros(6), torch.zeros(4), z, torch.zeros(12), L, torch.zeros(8), torch.zeros(4))
+    np.testing.assert_allclose(r.numpy(), [0.0, 0.0, 1.0], atol=1e-15)
+    r, _ = O.res_wf3d(torch.zeros(6), torch.zeros(4), z, torch.zeros(12), L,
+                      torch.tensor([3.0, 1.0, 0.0, 0, 0, 0, 0, 0]), torch.zeros(4))
+    assert float(r.abs().max()) < 1e-15
+    s = make_scene(config("tiny", wire_form="3d"))
+    st = O.state_from_scene(s)
+    lay = O.Layout(st, s["fixed"])
+    jp = set(s["obs"]["wf3d"]["other"].tolist())
+    assert len(jp) > 10 and all(lay.point_col[j] < lay.na for j in jp)
+    assert all(lay.point_col[j] >= lay.na for j in range(lay.np_) if j not in jp)
+    noise = noise_free(config("tiny", wire_form="3d"))
+    r, v = O.residuals(O.state_from_scene(noise), noise["obs"], "wf3d")
+    assert float(r.abs().max()) < 1e-13
