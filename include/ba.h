@@ -88,7 +88,12 @@ typedef enum {
   /* group-induced point residuals of the other group types (Eq. 7 with the projections of Appendix B): a point
    * observed in a camera, other = the sphere / cylinder / cone id; no measurement */
   BA_OBS_SPHERE_POINT = 9, BA_OBS_CYLINDER_POINT = 10, BA_OBS_CONE_POINT = 11,
-  BA_OBS_ELLIPSOID_POINT = 12, BA_OBS_CUBOID_POINT = 13
+  BA_OBS_ELLIPSOID_POINT = 12, BA_OBS_CUBOID_POINT = 13,
+  /* 3D wireframe endpoint distance X x d - m of a point X to a line (d, m), |d| = 1 (the form Section 3.3 sets
+   * against Eq. 11 / Eq. 12): feature = the line id, other = the point id; no camera, no measurement.  Every
+   * point it names becomes a 3-value entity of the reduced system (its residuals are not eliminated with
+   * it); not together with cam_dof = 9 or the sphere ... cuboid groups, nor in ba_solve_batch (BA_ERR_ARG) */
+  BA_OBS_WIREFRAME3D = 14
 } ba_obs_kind;
 
 typedef struct ba_options {
@@ -137,6 +142,8 @@ typedef struct ba_options {
                                increments are additive, and the principal point stays constant.  Problems with
                                refined intrinsics keep the full 6 x 6 storage of S and are not supported by
                                ba_solve_batch (BA_ERR_ARG there) */
+  double w_wire3d;          /* loss weight of the 3D wireframe endpoint distance (1.0; Cauchy scale cauchy_3d).
+                               Not in E_px */
 } ba_options;
 
 /* Per-LM-step report. */

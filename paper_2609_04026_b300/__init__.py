@@ -28,9 +28,9 @@ BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER, BA_CONE, BA_ELLIPSOID, BA_CUBOID = 0, 1
 BA_REL_ORTHOGONAL, BA_REL_PARALLEL = 0, 1
 OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6,
              "plane_point3d": 7, "plane_line3d": 8, "sphere_point": 9, "cylinder_point": 10, "cone_point": 11,
-             "ellipsoid_point": 12, "cuboid_point": 13}
-MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0, 9: 0, 10: 0, 11: 0, 12: 0, 13: 0}
-NO_CAM = (4, 7, 8)   # kinds without a camera (the VP term, the direct 3D plane distances)
+             "ellipsoid_point": 12, "cuboid_point": 13, "wf3d": 14}
+MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0, 9: 0, 10: 0, 11: 0, 12: 0, 13: 0, 14: 0}
+NO_CAM = (4, 7, 8, 14)   # kinds without a camera (the VP term, the direct 3D plane and wireframe distances)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -46,7 +46,8 @@ class ba_options(C.Structure):
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("wait_budget_cycles", C.c_longlong), ("mixed_lambda_floor", C.c_double),
                 ("w_rel", C.c_double), ("cauchy_rel", C.c_double), ("batch_ctas_per_window", C.c_int),
-                ("w_group3d", C.c_double), ("cauchy_3d", C.c_double), ("cam_dof", C.c_int)]
+                ("w_group3d", C.c_double), ("cauchy_3d", C.c_double), ("cam_dof", C.c_int),
+                ("w_wire3d", C.c_double)]
 
 
 class ba_step_report(C.Structure):

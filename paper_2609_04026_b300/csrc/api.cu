@@ -24,7 +24,7 @@
 
 using namespace ba;
 
-static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0, 0, 0};
+static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0, 0, 0, 0};
 
 static ba_status set_err(ba_problem* p, ba_status s, const std::string& m) {
   if (p) p->err = m;
@@ -61,6 +61,7 @@ extern "C" void ba_default_options(ba_options* o) {
   o->cam_dof = 6;
   o->w_group3d = 1.0;
   o->cauchy_3d = 1.0;
+  o->w_wire3d = 1.0;
 }
 
 extern "C" ba_status ba_create(const ba_options* opts, ba_problem** out) {
@@ -494,7 +495,7 @@ static ba_status freeze(ba_problem* p) {
   p->slotH = p->slotG ? (void*)((char*)p->slotG + T * HG_H) : nullptr;   // a view into the G|H records
   ok &= A(p->slotB, T * SB * (size_t)d.ne);
   ok &= A(p->slotC, T * SC * (size_t)d.ne);
-  if (d.nk || d.nbx()) ok &= A(p->slotCK, T * SC * (size_t)d.ne);
+  if (d.nk || d.nbx() || d.njp) ok &= A(p->slotCK, T * SC * (size_t)d.ne);
   if (d.ngs() || d.nbx()) ok &= A(p->slotCS, T * SCS * (size_t)d.ne);
   ok &= A(p->slotBS, T * SBS * (size_t)d.ne);
   ok &= A(p->Minv, T * BS2 * (size_t)d.na);
@@ -504,7 +505,7 @@ static ba_status freeze(ba_problem* p) {
   ok &= p->featV && p->featVinv && p->featg && p->featu && p->dfeat && p->featL;
   double** vecs[] = {&p->bvec, &p->Dg, &p->x, &p->r, &p->z, &p->p, &p->Ap, &p->sdiag, &p->svec};
   for (double** v : vecs) { *v = p->dnew<double>(6 * d.na); ok &= *v != nullptr; }
-  int64_t maxb = std::max<int64_t>({(d.nr + 255) / 256, (d.nf + 127) / 128, (d.na * 32 + 255) / 256, (d.na + 127) / 128,
+  int64_t maxb = std::max<int64_t>({(d.nr + 255) / 256, (d.nfp + 127) / 128, (d.na * 32 + 255) / 256, (d.na + 127) / 128,
                                     4 * 148 * 4, 1});
   p->red = p->dnew<double>(2 * maxb + 16);
   p->S = p->dnew<DevScalars>(1);
@@ -523,7 +524,7 @@ static ba_status freeze(ba_problem* p) {
   // one-time zero fill of the slot and feature arrays
   CUDA_OR(p, cudaMemsetAsync(p->slotW, 0, T * SW * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->slotC, 0, T * SC * (size_t)d.ne, p->stream));
-  if (d.nk || d.nbx()) CUDA_OR(p, cudaMemsetAsync(p->slotCK, 0, T * SC * (size_t)d.ne, p->stream));
+  if (d.nk || d.nbx() || d.njp) CUDA_OR(p, cudaMemsetAsync(p->slotCK, 0, T * SC * (size_t)d.ne, p->stream));
   if (d.ngs() || d.nbx()) CUDA_OR(p, cudaMemsetAsync(p->slotCS, 0, T * SCS * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
@@ -565,7 +566,8 @@ static ba_status ensure_sstore(ba_problem* p, bool for_batch) {
   const Dims& d = p->d;
   const size_t T = mixed(p) ? sizeof(float) : sizeof(double);
   // spheres, cylinders and cones keep the full storage (their camera blocks are 4 to 6 wide)
-  p->typed = !for_batch && d.nc > 0 && d.ngs() == 0 && d.nbx() == 0 && 3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
+  p->typed = !for_batch && d.nc > 0 && d.ngs() == 0 && d.nbx() == 0 && d.njp == 0 &&
+             3 * d.npl + 2 * d.nv + 3 * d.nk <= GV_MAX;
   ba_status s;
   if (p->typed) {
     TypedPlan tplan;
@@ -1022,7 +1024,17 @@ extern "C" ba_status ba_compute_step(ba_problem* p, double* dcam, double* dplane
   if (dcam) for (int64_t i = 0; i < d.nc; ++i) for (int k = 0; k < 6; ++k) dcam[6 * i + k] = x[6 * i + k];
   if (dplane) for (int64_t i = 0; i < d.npl; ++i) for (int k = 0; k < 3; ++k) dplane[3 * i + k] = x[6 * (d.nc + i) + k];
   if (dvp) for (int64_t i = 0; i < d.nv; ++i) for (int k = 0; k < 2; ++k) dvp[2 * i + k] = x[6 * (d.nc + d.npl + i) + k];
-  if (dpoint) for (int64_t i = 0; i < d.np; ++i) for (int k = 0; k < 3; ++k) dpoint[3 * i + k] = df[4 * i + k];
+  if (dpoint) {
+    // a point that a 3D wireframe distance names is an entity of A: its increment is part of x
+    std::vector<int32_t> jq(d.njp ? d.np : 0, -1);
+    if (d.njp) {
+      CUDA_OR(p, cudaMemcpyAsync(jq.data(), p->jq, sizeof(int32_t) * d.np, cudaMemcpyDeviceToHost, p->stream));
+      CUDA_OR(p, cudaStreamSynchronize(p->stream));
+    }
+    for (int64_t i = 0; i < d.np; ++i)
+      for (int k = 0; k < 3; ++k)
+        dpoint[3 * i + k] = (d.njp && jq[i] >= 0) ? x[6 * (d.jbase() + jq[i]) + k] : df[4 * i + k];
+  }
   if (dline) for (int64_t i = 0; i < d.nl; ++i) for (int k = 0; k < 4; ++k) dline[4 * i + k] = df[4 * (d.np + i) + k];
   if (pcg_iters) *pcg_iters = p->hS->iters;
   if (pcg_rel) *pcg_rel = p->hS->bnorm2 > 0 ? std::sqrt(p->hS->rr / p->hS->bnorm2) : 0.0;
@@ -1297,6 +1309,7 @@ extern "C" ba_status ba_solve_batch(ba_problem* const* windows, int n, int lm_it
     ba_status s = freeze(p);
     if (!s && p->nrel) s = set_err(p, BA_ERR_ARG, "inter-group relations are not supported in batched windows");
     if (!s && p->d.nk) s = set_err(p, BA_ERR_ARG, "refined intrinsics (cam_dof 9) are not supported in batched windows");
+    if (!s && p->d.njp) s = set_err(p, BA_ERR_ARG, "3D wireframe distances are not supported in batched windows");
     if (!s && (p->d.ngs() || p->d.nbx()))
       s = set_err(p, BA_ERR_ARG, "spheres, cylinders, cones, ellipsoids and cuboids are not supported in batched windows");
     if (!s) s = ensure_sstore(p, true);

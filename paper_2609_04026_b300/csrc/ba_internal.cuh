@@ -70,7 +70,8 @@ constexpr int SCS = 36; // camera slot of a feature on a sphere, cylinder or con
 
 enum EntType : uint8_t {
   ENT_CAM = 0, ENT_PLANE = 1, ENT_VP = 2, ENT_INTR = 3, ENT_SPHERE = 4, ENT_CYL = 5, ENT_CONE = 6,
-  ENT_ELL1 = 7, ENT_ELL2 = 8, ENT_CUB1 = 9, ENT_CUB2 = 10   // a 9-parameter group's first (6) and second (3) entity
+  ENT_ELL1 = 7, ENT_ELL2 = 8, ENT_CUB1 = 9, ENT_CUB2 = 10,  // a 9-parameter group's first (6) and second (3) entity
+  ENT_JPT = 11   // a point that the 3D wireframe distance couples with a line feature (3)
 };
 // real dimensions of an entity block: camera pose 6, plane 3, VP 2, intrinsics (f, k1, k2) 3, sphere 4,
 // cylinder 5, cone 6, a 9-parameter group's first entity 6 and second 3
@@ -88,6 +89,9 @@ __host__ __device__ __forceinline__ bool ent_second(int et) { return et == ENT_E
 // a 9-parameter group's two entities (the second entity's C record holds J_1^T w J_2, 6 x 3); PAIR_CK also
 // carries a camera's block with a 9-parameter group's second entity (the camera slot's CK record; refined
 // intrinsics are refused together with the other group types)
+// The residuals of a point that the 3D wireframe distance makes an entity of A form a zero-dimension feature
+// (zero Z records): its camera-point pairs carry PAIR_CK (the camera slot's CK record holds J_cam^T w J_point),
+// its plane-point pair PAIR_PK (the point slot's C record holds J_point^T w J_plane)
 constexpr uint32_t PAIR_CP = 1u, PAIR_CK = 2u, PAIR_PK = 3u, PAIR_CS = 4u, PAIR_G12 = 5u;
 constexpr int PAIR_SHIFT = 29;
 constexpr int32_t PAIR_SLOT = 0x1fffffff;
@@ -178,6 +182,11 @@ struct Dims {
   int64_t nel = 0, ncu = 0;            // ellipsoids, cuboids: two entities each (all first entities of a kind,
                                        // then its second ones), after the cones
   int64_t nk = 0;    // intrinsics entities (refined f, k1, k2; A indices after the groups)
+  // the 3D wireframe distance: the points it names are entities of A (after the intrinsics); the residuals of
+  // such a point form a zero-dimension feature of their own (one per point, after the points and lines)
+  int64_t njp = 0;
+  int64_t nfp = 0;   // features including those zero-dimension ones (nf: points and lines)
+  int64_t jbase() const { return nc + npl + nv + nsp + ncy + nco + 2 * (nel + ncu) + nk; }
   int64_t ngs() const { return nsp + ncy + nco; }            // sphere, cylinder and cone groups
   int64_t nbx() const { return nel + ncu; }                  // 9-parameter groups
   int64_t sbase() const { return nc + npl + nv; }            // A index of the first sphere
@@ -274,6 +283,8 @@ struct ba_problem {
   void *camT = nullptr, *ptsT = nullptr, *linT = nullptr, *grpT = nullptr, *srfT = nullptr, *bxT = nullptr;
   uint8_t* cam_fixed = nullptr;
   int32_t* cam_k = nullptr;   // per camera its intrinsics entity (refined intrinsics only)
+  int32_t* jq = nullptr;      // per point its index among the wireframe-coupled points, or -1
+  int32_t* jp_pt = nullptr;   // per wireframe-coupled point its point id
   // residuals, feature-major
   int8_t* rkind = nullptr;
   int32_t *rcam = nullptr, *rfeat = nullptr, *rgrp = nullptr, *rslot_c = nullptr, *rslot_g = nullptr;

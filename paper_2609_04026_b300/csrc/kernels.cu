@@ -254,6 +254,8 @@ struct LinArgs {
   const T* meas;
   const T *cam, *pts, *lin, *grp;
   int64_t npl, np;
+  const int32_t* jp_pt;                 // 3D wireframe distance: per coupled point its point id
+  int64_t nf;                           // points and lines (the coupled points' features follow)
   T *W, *H, *G, *C;
   double *V, *g;
   LossW loss;
@@ -303,8 +305,12 @@ __device__ __forceinline__ void load16(const T* __restrict__ src, T* dst) {
   for (int i = NT2; i < N; ++i) dst[i] = src[i];
 }
 
-template <class T, int KF, bool INTR = false, bool SURF = false>
+// INTR: refined intrinsics (the residuals' intrinsics Jacobians, the intrinsics slots, the camera slots' couplings
+// with their entities); WF: lines with 3D wireframe distances (their points' slots); SURF: the point kinds of
+// spheres ... cuboids
+template <class T, int KF, bool INTR = false, bool SURF = false, bool WF = false>
 __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
+  constexpr bool XK = INTR || WF;   // the 3-dimension extra slots (intrinsics entities or coupled points)
   const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
   // width of the positional group's accumulators: 3 (plane), 6 when spheres, cylinders or cones may occur
   constexpr int GW = SURF ? 6 : 3;
@@ -445,13 +451,13 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
     store16<T, SG>(a.G + (size_t)e * SG, gh);
     store16<T, SC>(a.C + (size_t)e * SC, cb);
   };
-  if constexpr (INTR) {
+  if constexpr (XK) {
     zero_k();
     zero_ck();
-    // the feature's intrinsics slots start from zero (they are summed into below)
+    // the feature's extra slots start from zero (they are summed into below)
     const T z[SG > SC ? SG : SC] = {};
     for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e)
-      if (a.slot_type[e] == ENT_INTR) {
+      if (a.slot_type[e] == ENT_INTR || a.slot_type[e] == ENT_JPT) {
         store16<T, KF * 6>(a.W + (size_t)e * SW, z);
         store16<T, SG>(a.G + (size_t)e * SG, z);
         store16<T, SC>(a.C + (size_t)e * SC, z);
@@ -475,7 +481,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       zero_cam();
       cur = sc;
     }
-    if constexpr (INTR) {
+    if constexpr (XK) {
       const int sk = a.rslot_k[rr];
       if (sk != curk) {
         if (curk >= 0) add_k(curk);
@@ -515,6 +521,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       else if (kind == R_VP) { res_vp<T, true, INTR>(F, a.grp + (size_t)GRP_STRIDE * (a.npl + gid), o); has_vp = true; }
       else if (kind == R_L2P) res_l2p<T, true, INTR>(c, F, meas, o);
       else if (kind == R_PLANE_LINE3) { res_plane_line3<T, true>(F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
+      else if (WF && kind == R_WF3D) res_wf3d<T, true>(F, a.pts + 3 * (size_t)gid, o);
       else continue;
     }
     if (!o.valid) continue;
@@ -621,7 +628,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
           for (int q = p; q < 2; ++q) Hv[up_idx(p, q, 2)] += wg[p] * o.Jg[i][q];
         }
       }
-      if constexpr (INTR) {
+      if constexpr (XK) {
         if (curk >= 0) {
           T wk[3];
 #pragma unroll
@@ -650,7 +657,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       }
     }
   }
-  if constexpr (INTR) {
+  if constexpr (XK) {
     if (cur >= 0) {
       T cb[SC];
 #pragma unroll
@@ -708,10 +715,166 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
   store16<double, KF>(a.g + 4 * f, gbf);
 }
 
-template <class T, int KF, bool INTR = false, bool SURF = false>
+template <class T, int KF, bool INTR = false, bool SURF = false, bool WF = false>
 __global__ void __launch_bounds__(128) k_linearize(LinArgs<T> a, int64_t f0, int64_t f1) {
   int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f < f1) linearize_feature<T, KF, INTR, SURF>(a, f);
+  if (f < f1) linearize_feature<T, KF, INTR, SURF, WF>(a, f);
+}
+
+// The residuals of a point that the 3D wireframe distance makes an entity of A (a zero-dimension feature: no
+// W, V or g): per camera slot its G, H, the coupling with the point (CK record) and with the plane (C record);
+// the point slot's G, H and its coupling with the plane (C record, J_point^T w J_plane, 3 x 3); the plane
+// slot's G, H.  Point kinds with a camera or the direct plane distance (the other group types are refused
+// together with this distance).
+template <class T>
+__device__ void linearize_jpoint(const LinArgs<T>& a, int64_t q) {
+  const int64_t f = a.nf + q;
+  const int r0 = a.fres_off[f], r1 = a.fres_off[f + 1];
+  const T* X = a.pts + 3 * (size_t)a.jp_pt[q];
+  const T F[3] = {X[0], X[1], X[2]};
+  T Hc[21], Gc[6], Cc[6][3], CKc[6][3];
+  T Hk[6], Gk[3], KP[3][3], Hp[6], Gp[3];
+  int cur = -1, ps = -1, sk = -1;
+  auto zero_cam = [&]() {
+#pragma unroll
+    for (int i = 0; i < 21; ++i) Hc[i] = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      Gc[i] = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { Cc[i][j] = 0; CKc[i][j] = 0; }
+    }
+  };
+  auto flush = [&](int e) {
+    T gh[SG];
+#pragma unroll
+    for (int i = 0; i < SG; ++i) gh[i] = i < HG_H ? Gc[i] : i < HG_H + 21 ? Hc[i - HG_H] : T(0);
+    store16<T, SG>(a.G + (size_t)e * SG, gh);
+    T cb[SC];
+#pragma unroll
+    for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? Cc[i / 3][i % 3] : T(0);
+    store16<T, SC>(a.C + (size_t)e * SC, cb);
+#pragma unroll
+    for (int i = 0; i < SC; ++i) cb[i] = i < 18 ? CKc[i / 3][i % 3] : T(0);
+    store16<T, SC>(a.CK + (size_t)e * SC, cb);
+  };
+  zero_cam();
+#pragma unroll
+  for (int i = 0; i < 6; ++i) { Hk[i] = 0; Hp[i] = 0; }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { Gk[i] = 0; Gp[i] = 0; KP[i][0] = KP[i][1] = KP[i][2] = 0; }
+  for (int rr = r0; rr < r1; ++rr) {
+    const int kind = a.rkind[rr];
+    const int sc = a.rslot_c[rr];
+    if (sc != cur) {
+      if (cur >= 0) flush(cur);
+      zero_cam();
+      cur = sc;
+    }
+    sk = a.rslot_k[rr];
+    const int camid = a.rcam[rr];
+    const int gid = a.rgrp[rr];
+    T meas[4];
+    load16<T, 4>(a.meas + 4 * (size_t)rr, meas);
+    Cam<T> c;
+    if (camid >= 0) load_cam(a.cam + (size_t)CAM_STRIDE * camid, c);
+    ResJ<T> o;
+    bool has_plane = false;
+    if (kind == R_POINT) res_point<T, true>(c, F, meas, o);
+    else if (kind == R_PLANE_POINT) { res_plane_point<T, true>(c, F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
+    else if (kind == R_P2L) res_p2l<T, true>(c, F, meas, o);
+    else if (kind == R_PLANE_POINT3) { res_plane_point3<T, true>(F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
+    else continue;
+    if (!o.valid) continue;
+    if (camid >= 0) {
+      const unsigned held = a.cam_mask[camid];
+      if (held)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 6; ++k)
+            if ((held >> k) & 1u) o.Jc[i][k] = 0;
+    }
+    const int rd = res_dim(kind);
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < rd) s += o.r[i] * o.r[i];
+    const T om = (T)a.loss.w[kind] / (T(1) + s * (T)a.loss.inv_a2[kind]);
+    if (has_plane) ps = a.rslot_g[rr];
+    const bool camslot = sc >= 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= rd) break;
+      T wx[3], wc[6], wg[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { wx[k] = om * o.Jf[i][k]; wg[k] = om * o.Jg[i][k]; }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wc[k] = om * o.Jc[i][k];
+      const T ri = o.r[i];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        Gk[p] += wx[p] * ri;
+#pragma unroll
+        for (int q2 = p; q2 < 3; ++q2) Hk[up_idx(p, q2, 3)] += wx[p] * o.Jf[i][q2];
+      }
+      if (camslot) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          Gc[p] += wc[p] * ri;
+#pragma unroll
+          for (int q2 = p; q2 < 6; ++q2) Hc[up_idx(p, q2, 6)] += wc[p] * o.Jc[i][q2];
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) CKc[p][q2] += wc[p] * o.Jf[i][q2];
+        }
+        if (has_plane)
+#pragma unroll
+          for (int p = 0; p < 6; ++p)
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) Cc[p][q2] += wc[p] * o.Jg[i][q2];
+      }
+      if (has_plane) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          Gp[p] += wg[p] * ri;
+#pragma unroll
+          for (int q2 = p; q2 < 3; ++q2) Hp[up_idx(p, q2, 3)] += wg[p] * o.Jg[i][q2];
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) KP[p][q2] += wx[p] * o.Jg[i][q2];
+        }
+      }
+    }
+  }
+  if (cur >= 0) flush(cur);
+  // the point slot (the feature's last) and the plane slot: G and the upper H in the 6-wide layout
+  auto put3 = [&](int e, const T* Gg, const T* Hg) {
+    T gh[SG];
+#pragma unroll
+    for (int i = 0; i < SG; ++i) gh[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      gh[i] = Gg[i];
+#pragma unroll
+      for (int j = i; j < 3; ++j) gh[HG_H + up_idx(i, j, 6)] = Hg[up_idx(i, j, 3)];
+    }
+    store16<T, SG>(a.G + (size_t)e * SG, gh);
+  };
+  if (sk < 0 && r1 > r0) sk = a.fslot_off[f + 1] - 1;
+  if (sk >= 0) {
+    put3(sk, Gk, Hk);
+    T cb[SC];
+#pragma unroll
+    for (int i = 0; i < SC; ++i) cb[i] = i < 9 ? KP[i / 3][i % 3] : T(0);
+    store16<T, SC>(a.C + (size_t)sk * SC, cb);
+  }
+  if (ps < 0) ps = a.feat_plane_slot[f];
+  if (ps >= 0) put3(ps, Gp, Hp);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_linearize_jpoint(LinArgs<T> a, int64_t njp) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < njp) linearize_jpoint<T>(a, q);
 }
 
 // ============================================================================
@@ -903,8 +1066,19 @@ __global__ void __launch_bounds__(128) k_whiten(InvArgs<T> a) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= a.ne) return;
   const int64_t f = a.slot_feat[e];
-  if (f < a.np) whiten_from_store<T, 3>(a, e, f);
-  else whiten_from_store<T, 4>(a, e, f);
+  if (f >= a.nf) {
+    // a slot of a wireframe-coupled point's residuals (a zero-dimension feature): Z = 0, the b part -G
+    const T z[SW] = {};
+    store16<T, SW>(a.Z + (size_t)e * SW, z);
+    T G[6];
+    load16<T, 6>(a.G + (size_t)e * SG, G);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a.B[(size_t)e * SB + j] = -G[j];
+  } else if (f < a.np) {
+    whiten_from_store<T, 3>(a, e, f);
+  } else {
+    whiten_from_store<T, 4>(a, e, f);
+  }
 }
 
 // ============================================================================
@@ -1292,7 +1466,7 @@ __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_packs(UnitArgs<T
   for (int t = lane; t < n * 2 * CH; t += 32) {
     const int p = t / (2 * CH), r = t - p * 2 * CH;
     const int which = r / CH, ch = r - which * CH;
-    const int e = which == 0 ? sa_[p] : sb_[p];
+    const int e = which == 0 ? sa_[p] : (sb_[p] & PAIR_SLOT);   // packed pairs carry no direct-block code
     cp_async16(reinterpret_cast<char*>(stage + p * ST + which * SW) + 16 * ch,
                reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * ch);
   }
@@ -2735,6 +2909,7 @@ struct BackArgs {
   const T* CS;              // surface groups: camera slots' blocks with the feature's sphere / cylinder / cone
   const int32_t* cam_k;     // refined intrinsics: per camera its entity (else null)
   int64_t kbase;            // A index of intrinsics entity 0
+  int64_t nfp;              // features including the wireframe-coupled points' (zero-dimension, after nf)
   T* sv;        // per slot: W_e da (4, zero-padded), G_e . da, da^T H_e da + 2 da^T C_e dplane
   double* df;
   int64_t np, nf, ne;
@@ -2821,7 +2996,29 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
   }
-  if (a.cam_k) {
+  if (f >= a.nf) {
+    // a wireframe-coupled point's residuals: a camera slot's direct block with the point (the CK record, the
+    // point slot is the feature's last), the point slot's with the plane (its C record, 3 x 3)
+    if (a.slot_type[e] == ENT_CAM) {
+      const double* dk = a.x + 6 * (size_t)a.slot_ent[a.fslot_off[f + 1] - 1];
+      const T dkv[3] = {(T)dk[0], (T)dk[1], (T)dk[2]};
+      T Ck[18];
+      load16<T, 18>(a.CK + (size_t)e * SC, Ck);
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cpl += dv[i] * Ck[i * 3 + j] * dkv[j];
+    } else if (a.slot_type[e] == ENT_JPT && pslot >= 0) {
+      const double* dp = a.x + 6 * (size_t)a.slot_ent[pslot];
+      const T dpl[3] = {(T)dp[0], (T)dp[1], (T)dp[2]};
+      T Cm[18];
+      load16<T, 18>(a.C + (size_t)e * SC, Cm);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cpl += dv[i] * Cm[i * 3 + j] * dpl[j];
+    }
+  } else if (a.cam_k) {
     // refined intrinsics: a camera slot's direct block with its own entity, an intrinsics slot's with the plane
     if (a.slot_type[e] == ENT_CAM) {
       const double* dk = a.x + 6 * (size_t)(a.kbase + a.cam_k[a.slot_ent[e]]);
@@ -2899,6 +3096,13 @@ __global__ void __launch_bounds__(128) k_backsub(BackArgs<T> a) {
   if (f < a.nf) {
     if (f < a.np) backsub_feature<T, 3>(a, f, v[0], v[1]);
     else backsub_feature<T, 4>(a, f, v[0], v[1]);
+  } else if (f < a.nfp) {
+    // a wireframe-coupled point's residuals: their slots' shares of g.delta and delta^T H delta alone
+    for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
+      const T* so = a.sv + (size_t)e * SBS;
+      v[0] += (double)so[4];
+      v[1] += (double)so[5];
+    }
   }
   double tot[2];
   if (grid_reduce<2>(v, a.red, &a.S->counter[3], tot) && threadIdx.x == 0) {
@@ -2966,6 +3170,10 @@ struct CandArgs {
   const double* bx;
   double* bx2;
   int64_t nel, ncu, bbase;
+  // 3D wireframe distance (else null): per point its index among the coupled points (-1: a feature), A index of
+  // the first coupled point
+  const int32_t* jq;
+  int64_t jbase;
 };
 
 // the orthonormal update of a Pluecker line (d, m), |d| = 1: U <- U Exp(dl[0:3]), phi <- phi + dl[3]
@@ -3083,7 +3291,8 @@ __device__ void candidate_item(const CandArgs& a, int64_t i) {
     s2_exp(V, v, a.vps2 + 3 * g);
   } else if (i < n3) {
     int64_t f = i - n2;
-    for (int k = 0; k < 3; ++k) a.pts2[3 * f + k] = a.pts[3 * f + k] + a.df[4 * f + k];
+    const double* dl = (a.jq && a.jq[f] >= 0) ? a.x + 6 * (a.jbase + a.jq[f]) : a.df + 4 * f;
+    for (int k = 0; k < 3; ++k) a.pts2[3 * f + k] = a.pts[3 * f + k] + dl[k];
   } else {
     const int64_t l = i - n3;
     line_retract(a.lin + 6 * l, a.df + 4 * (a.np + l), a.lin2 + 6 * l);
@@ -3238,6 +3447,7 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
             case R_CONE_POINT: res_surface_point<double, false, 2>(c, X, a.srf + (size_t)SRF_STRIDE * (a.nsp + a.ncy + gid), o); break;
             case R_ELL_POINT: res_box_point<double, false, 3>(c, X, a.bx + (size_t)BOX_STRIDE * gid, o); break;
             case R_CUB_POINT: res_box_point<double, false, 4>(c, X, a.bx + (size_t)BOX_STRIDE * (a.nel + gid), o); break;
+            case R_WF3D: res_wf3d<double, false>(L, a.pts + 3 * (size_t)gid, o); break;
           }
         }
         break;
@@ -3356,10 +3566,11 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 static LossW make_loss(const ba_options& o) {
   LossW L;
   // per kind: points, lines, plane-induced (2), VP, wireframe (2), direct 3D plane distances (2), sphere /
-  // cylinder / cone / ellipsoid / cuboid-induced (5)
+  // cylinder / cone / ellipsoid / cuboid-induced (5), the 3D wireframe endpoint distance
   const double w[N_KINDS] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire,
-                             o.w_group3d, o.w_group3d, o.w_group, o.w_group, o.w_group, o.w_group, o.w_group};
-  static_assert(N_KINDS == 14, "a weight per residual kind");
+                             o.w_group3d, o.w_group3d, o.w_group, o.w_group, o.w_group, o.w_group, o.w_group,
+                             o.w_wire3d};
+  static_assert(N_KINDS == 15, "a weight per residual kind");
   for (int k = 0; k < N_KINDS; ++k) {
     L.w[k] = w[k];
     double s = (k == R_VP) ? o.cauchy_vp : (res_has_cam(k) ? o.cauchy_px : o.cauchy_3d);
@@ -3419,6 +3630,16 @@ void launch_linearize(Problem& P) {
   a.rslot_k = P.rslot_k; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = (T*)P.slotCK;
   a.srf = dbl ? (const T*)cs.srf : (const T*)P.srfT; a.CS = (T*)P.slotCS; a.nsp = d.nsp; a.ncy = d.ncy;
   a.bx = dbl ? (const T*)cs.bx : (const T*)P.bxT; a.nel = d.nel;
+  a.jp_pt = P.jp_pt; a.nf = d.nf;
+  if (d.njp) {
+    // 3D wireframe distances: the lines' coupled-point slots, then the coupled points' own residuals
+    // (refined intrinsics and the other group types are refused together with them)
+    if (d.np) { ++P.launches; k_linearize<T, 3><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
+    if (d.nl) { ++P.launches; k_linearize<T, 4, false, false, true><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
+    ++P.launches;
+    k_linearize_jpoint<T><<<nblk(d.njp, 128), 128, 0, P.stream>>>(a, d.njp);
+    return;
+  }
   if (d.ngs() || d.nbx()) {
     // spheres, cylinders, cones: the points' positional groups take up to 6 dimensions (refined intrinsics are
     // refused together with them)
@@ -3621,7 +3842,8 @@ void launch_backsub(Problem& P) {
   a.CK = (const T*)P.slotCK; a.cam_k = d.nk ? P.cam_k : nullptr; a.kbase = d.kbase(); a.CS = (const T*)P.slotCS;
   if (d.ne) { ++P.launches; k_backsub_slots<T><<<nblk(d.ne, 128), 128, 0, P.stream>>>(a); }
   ++P.launches;
-  k_backsub<T><<<nblk(d.nf > 0 ? d.nf : 1, 128), 128, 0, P.stream>>>(a);
+  a.nfp = d.nfp;
+  k_backsub<T><<<nblk(d.nfp > 0 ? d.nfp : 1, 128), 128, 0, P.stream>>>(a);
 }
 
 void launch_candidate(Problem& P) {
@@ -3635,6 +3857,7 @@ void launch_candidate(Problem& P) {
   a.intr = c.intr; a.intr2 = n.intr; a.cam_k = P.cam_k; a.nk = d.nk; a.kbase = d.kbase();
   a.srf = c.srf; a.srf2 = n.srf; a.nsp = d.nsp; a.ncy = d.ncy; a.nco = d.nco; a.sbase = d.sbase();
   a.bx = c.bx; a.bx2 = n.bx; a.nel = d.nel; a.ncu = d.ncu; a.bbase = d.bbase();
+  a.jq = d.njp ? P.jq : nullptr; a.jbase = d.jbase();
   int64_t tot = d.nc + d.npl + d.nv + d.np + d.nl + d.nk + d.ngs() + d.nbx();
   if (tot) { ++P.launches; k_candidate<<<nblk(tot, 128), 128, 0, P.stream>>>(a); }
 }
@@ -3655,7 +3878,7 @@ void launch_cost(Problem& P, bool candidate) {
     sms = 148;
   }
   const unsigned grid = (unsigned)std::min<int64_t>(nblk(d.nr > 0 ? d.nr : 1, 256), 2 * (int64_t)sms);
-  if (d.ngs() || d.nbx()) k_cost<true><<<grid, 256, 0, P.stream>>>(a);
+  if (d.ngs() || d.nbx() || d.njp) k_cost<true><<<grid, 256, 0, P.stream>>>(a);
   else k_cost<false><<<grid, 256, 0, P.stream>>>(a);
 }
 
@@ -4017,6 +4240,7 @@ void fill_window_desc(Problem& P, void* out) {
   a.loss = make_loss(P.opt);
   a.rslot_k = nullptr; a.fslot_off = P.fslot_off; a.slot_type = P.slot_type; a.CK = nullptr;
   a.srf = nullptr; a.CS = nullptr; a.nsp = a.ncy = 0; a.bx = nullptr; a.nel = 0;
+  a.jp_pt = nullptr; a.nf = d.nf;
   InvArgs<T>& ia = W.inv;
   ia.fslot_off = P.fslot_off; ia.V = P.featV; ia.g = P.featg; ia.W = (const T*)P.slotW; ia.G = (const T*)P.slotG;
   ia.slot_feat = P.slot_feat; ia.Vinv = P.featVinv; ia.u = P.featu; ia.L = P.featL; ia.Z = (T*)P.slotZ; ia.B = (T*)P.slotB;
@@ -4028,12 +4252,13 @@ void fill_window_desc(Problem& P, void* out) {
   k.V = P.featV; k.Vinv = P.featVinv; k.g = P.featg; k.x = P.x; k.W = (const T*)P.slotW; k.H = (const T*)P.slotH;
   k.G = (const T*)P.slotG; k.C = (const T*)P.slotC; k.df = P.dfeat; k.np = d.np; k.nf = d.nf; k.S = P.S; k.red = P.red;
   k.slot_feat = P.slot_feat; k.sv = (T*)P.slotBS; k.ne = d.ne;
-  k.CK = nullptr; k.cam_k = nullptr; k.kbase = 0; k.CS = nullptr;
+  k.CK = nullptr; k.cam_k = nullptr; k.kbase = 0; k.CS = nullptr; k.nfp = d.nf;
   CandArgs& c = W.cand;
   c.x = P.x; c.df = P.dfeat; c.fixed = P.cam_fixed; c.nc = d.nc; c.np = d.np; c.nl = d.nl; c.npl = d.npl; c.nv = d.nv;
   c.intr = nullptr; c.intr2 = nullptr; c.cam_k = nullptr; c.nk = 0; c.kbase = 0;   // windows: no refined intrinsics
   c.srf = nullptr; c.srf2 = nullptr; c.nsp = c.ncy = c.nco = 0; c.sbase = 0;        // nor surface groups
   c.bx = nullptr; c.bx2 = nullptr; c.nel = c.ncu = 0; c.bbase = 0;
+  c.jq = nullptr; c.jbase = 0;                                                      // nor 3D wireframe distances
   CostArgs& co = W.cost;
   co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64; co.order = P.cost_order;
   co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;

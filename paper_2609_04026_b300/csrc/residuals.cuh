@@ -40,13 +40,14 @@ enum ResKind : int {
   R_POINT = 0, R_LINE = 1, R_PLANE_POINT = 2, R_PLANE_LINE = 3, R_VP = 4, R_P2L = 5, R_L2P = 6,
   R_PLANE_POINT3 = 7, R_PLANE_LINE3 = 8,   // the direct 3D plane distances (no camera)
   R_SPHERE_POINT = 9, R_CYL_POINT = 10, R_CONE_POINT = 11,  // group-induced point residuals of other group types
-  R_ELL_POINT = 12, R_CUB_POINT = 13                         // ... of the 9-parameter ellipsoid and cuboid
+  R_ELL_POINT = 12, R_CUB_POINT = 13,                        // ... of the 9-parameter ellipsoid and cuboid
+  R_WF3D = 14                                                // 3D wireframe endpoint distance (line, point)
 };
-constexpr int N_KINDS = 14;
+constexpr int N_KINDS = 15;
 
 __host__ __device__ constexpr int res_dim(int k) {
   return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3
-       : k == R_PLANE_LINE3 ? 2 : k >= R_SPHERE_POINT ? 2 : 1;
+       : k == R_PLANE_LINE3 ? 2 : k == R_WF3D ? 3 : k >= R_SPHERE_POINT ? 2 : 1;
 }
 // surface group types (sphere, cylinder, cone): 8 raw values per group, increments of 4, 5 and 6
 constexpr int SRF_STRIDE = 8;
@@ -55,7 +56,9 @@ constexpr int SRF_STRIDE = 8;
 constexpr int BOX_STRIDE = 16;
 __host__ __device__ constexpr int srf_dims(int ty) { return ty == 0 ? 4 : (ty == 1 ? 5 : 6); }
 // kinds with a camera (the others: the VP term and the direct 3D plane distances)
-__host__ __device__ constexpr bool res_has_cam(int k) { return k != R_VP && k != R_PLANE_POINT3 && k != R_PLANE_LINE3; }
+__host__ __device__ constexpr bool res_has_cam(int k) {
+  return k != R_VP && k != R_PLANE_POINT3 && k != R_PLANE_LINE3 && k != R_WF3D;
+}
 // kinds in the pixel cost E_px
 __host__ __device__ constexpr bool res_pixel(int k) { return res_has_cam(k); }
 
@@ -879,6 +882,38 @@ __device__ void res_box_point(const Cam<T>& c, const T* X, const T* G, ResJ<T>& 
       if (k < 6) o.Jg[i][k] = v; else o.Jg2[i][k - 6] = v;
     }
   }
+}
+
+// 3D wireframe endpoint distance of point X to line L = (d, m), |d| = 1: X x d - m (its norm is the distance).
+// Jf: the line's 4 increments (X x dd - dm); Jk: the point's (a 3-entity of A): d/dX (X x d) = -[d]x
+template <class T, bool JAC>
+__device__ void res_wf3d(const T* L, const T* X, ResJ<T>& o) {
+  const T* d = L;
+  const T* m = L + 3;
+  T xd[3];
+  cross3(X, d, xd);
+  o.r[0] = xd[0] - m[0]; o.r[1] = xd[1] - m[1]; o.r[2] = xd[2] - m[2];
+  o.valid = true;
+  if (!JAC) return;
+  T u1[3], u3[3], r;
+  line_frame(d, m, u1, u3, r);
+  T dd[4][3], dm[4][3];
+  line_dirs(d, u1, u3, r, dd, dm);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T c[3];
+    cross3(X, dd[k], c);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.Jf[i][k] = c[i] - dm[k][i];
+  }
+  // (X + e_k) x d - X x d = e_k x d
+  o.Jk[0][0] = 0;     o.Jk[0][1] = d[2];  o.Jk[0][2] = -d[1];
+  o.Jk[1][0] = -d[2]; o.Jk[1][1] = 0;     o.Jk[1][2] = d[0];
+  o.Jk[2][0] = d[1];  o.Jk[2][1] = -d[0]; o.Jk[2][2] = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.Jc[i][k] = 0;
 }
 
 // direct 3D distance of a point to the plane (n, w): n . X + w

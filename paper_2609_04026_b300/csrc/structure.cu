@@ -276,6 +276,29 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int32_t* 
   if (j < n) b[j] = (int32_t)a[j];
 }
 
+// the points that a 3D wireframe distance names (mark[p] = 1), their ranks (ascending point id) and the
+// feature key of every record: a named point's residuals are a zero-dimension feature after the points and
+// lines (nf_real + rank); the records themselves keep the point id
+__global__ void k_mark_jpt(const int8_t* __restrict__ kind, const int32_t* __restrict__ grp, int64_t n,
+                           int64_t* __restrict__ mark) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n && kind[j] == R_WF3D) mark[grp[j]] = 1;   // every writer stores the same value
+}
+__global__ void k_jq(const int64_t* __restrict__ mark, const int64_t* __restrict__ rank, int64_t np,
+                     int32_t* __restrict__ jq, int32_t* __restrict__ jp_pt) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  jq[p] = mark[p] ? (int32_t)rank[p] : -1;
+  if (mark[p]) jp_pt[rank[p]] = (int32_t)p;
+}
+__global__ void k_fkey(const int32_t* __restrict__ feat, const int32_t* __restrict__ jq, int64_t np, int64_t nf_real,
+                       int64_t n, int32_t* __restrict__ fkey) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int32_t f = feat[j];
+  fkey[j] = (f < np && jq[f] >= 0) ? (int32_t)(nf_real + jq[f]) : f;
+}
+
 struct SlotArgs {
   const int32_t *order, *fres_off, *cam, *grp;
   const int8_t* kind;
@@ -286,6 +309,8 @@ struct SlotArgs {
   int64_t kbase;          // A index of intrinsics entity 0
   int64_t sbase, nsp, ncy;   // A index of the first sphere; spheres, cylinders (cones follow)
   int64_t bbase, nel, ncu;   // A index of the first ellipsoid entity; ellipsoids, cuboids
+  const int32_t* jq;         // per point its index among the wireframe-coupled points (or -1), or null
+  int64_t jbase, nf_real;    // A index of the first wireframe-coupled point; points and lines
 };
 
 // the positional group of residual record i as an A index (plane, sphere, cylinder, cone), or -1
@@ -310,15 +335,24 @@ __device__ __forceinline__ uint8_t pos_type(const SlotArgs& a, int64_t e) {
        : e < a.bbase + 2 * a.nel + a.ncu ? ENT_CUB1 : ENT_CUB2;
 }
 
-// intrinsics entity of residual j of a feature (-1: none)
-__device__ __forceinline__ int slot_intr(const SlotArgs& a, int32_t j) {
-  if (!a.cam_k) return -1;
-  const int c = a.cam[a.order[j]];
-  return c >= 0 ? a.cam_k[c] : -1;
+// the extra 3-dimension entity (A index) that residual j of feature f names besides its camera and groups, or
+// -1: its camera's intrinsics entity (refined intrinsics); the point of a 3D wireframe distance (a line's
+// residual); the point itself for a residual of a wireframe-coupled point (a zero-dimension feature)
+__device__ __forceinline__ int64_t slot_extra(const SlotArgs& a, int64_t f, int32_t j) {
+  const int32_t i = a.order[j];
+  if (a.cam_k) {
+    const int c = a.cam[i];
+    return c >= 0 ? a.kbase + a.cam_k[c] : -1;
+  }
+  if (a.jq) {
+    if (f >= a.nf_real) return a.jbase + (f - a.nf_real);
+    if (a.kind[i] == R_WF3D) return a.jbase + a.jq[a.grp[i]];
+  }
+  return -1;
 }
 
 // distinct kept entities of a feature (cameras ascending, then its plane, then its VP, then the intrinsics
-// entities of its cameras, ascending)
+// entities of its cameras or its wireframe-coupled points, ascending)
 __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
   const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.nf) return;
@@ -339,11 +373,11 @@ __global__ void k_slot_count(SlotArgs a, int64_t* __restrict__ nslot) {
       if (vp >= 0 && vp != a.grp[i]) atomicOr(a.err, 2);
       vp = a.grp[i];
     }
-    // an intrinsics entity counts at the first residual that names it
-    const int kk = slot_intr(a, j);
+    // an extra entity counts at the first residual that names it
+    const int64_t kk = slot_extra(a, f, j);
     if (kk >= 0) {
       bool seen = false;
-      for (int32_t j2 = r0; j2 < j && !seen; ++j2) seen = slot_intr(a, j2) == kk;
+      for (int32_t j2 = r0; j2 < j && !seen; ++j2) seen = slot_extra(a, f, j2) == kk;
       n += seen ? 0 : 1;
     }
   }
@@ -410,29 +444,29 @@ __global__ void k_slot_fill(SlotArgs a, const int64_t* __restrict__ soff, SlotFi
     const bool on_plane = pos_group(a, k, 0) >= 0;
     o.rslot_g[j] = on_plane ? plane_slot : (k == R_VP ? vp_slot : -1);
   }
-  if (!a.cam_k) return;
-  // the intrinsics entities of the feature's cameras in ascending order (the slots of a feature are in entity
-  // order), then every residual's slot among them
+  if (!a.cam_k && !a.jq) return;
+  // the extra entities (intrinsics of the feature's cameras, or wireframe-coupled points) in ascending order
+  // (the slots of a feature are in entity order), then every residual's slot among them
   const int32_t k0 = e;
-  int last = -1;
+  int64_t last = -1;
   for (;;) {
-    int nxt = INT32_MAX;
+    int64_t nxt = INT64_MAX;
     for (int32_t j = r0; j < r1; ++j) {
-      const int kk = slot_intr(a, j);
+      const int64_t kk = slot_extra(a, f, j);
       if (kk > last && kk < nxt) nxt = kk;
     }
-    if (nxt == INT32_MAX) break;
-    o.slot_ent[e] = (int32_t)(a.kbase + nxt);
+    if (nxt == INT64_MAX) break;
+    o.slot_ent[e] = (int32_t)nxt;
     o.slot_feat[e] = (int32_t)f;
-    o.slot_type[e] = ENT_INTR;
+    o.slot_type[e] = nxt >= a.jbase ? ENT_JPT : ENT_INTR;
     ++e;
     last = nxt;
   }
   for (int32_t j = r0; j < r1; ++j) {
-    const int kk = slot_intr(a, j);
+    const int64_t kk = slot_extra(a, f, j);
     int32_t sk = -1;
     for (int32_t q = k0; q < e && kk >= 0; ++q)
-      if (o.slot_ent[q] == (int32_t)(a.kbase + kk)) { sk = q; break; }
+      if (o.slot_ent[q] == (int32_t)kk) { sk = q; break; }
     o.rslot_k[j] = sk;
   }
 }
@@ -545,6 +579,7 @@ struct PairGen {
   const uint8_t* slot_type;
   const int32_t* cam_k;   // refined intrinsics: per camera its entity (else null)
   int64_t kbase;
+  int64_t nf_real;        // points and lines; later features are zero-dimension ones
   const int64_t *poff, *uptr;
   Bitmap bm;
   int64_t nf;
@@ -573,6 +608,10 @@ __global__ void k_pair_gen(PairGen g) {
       if (i != j) {
         const int ti = g.slot_type[i], tj = g.slot_type[j];
         if (ti == ENT_CAM && tj == ENT_PLANE) code = PAIR_CP;
+        else if (tj == ENT_JPT) {
+          // a wireframe-coupled point: direct blocks with the camera and plane of its own residuals only
+          if (f >= g.nf_real) code = ti == ENT_CAM ? PAIR_CK : ti == ENT_PLANE ? PAIR_PK : 0u;
+        }
         else if (ti == ENT_CAM && tj == ENT_INTR && g.cam_k && g.kbase + g.cam_k[a] == b) code = PAIR_CK;
         else if (ti == ENT_PLANE && tj == ENT_INTR) code = PAIR_PK;
         else if (ti == ENT_CAM && ent_second(tj)) code = PAIR_CK;
@@ -639,7 +678,11 @@ __global__ void k_unit_key(const int32_t* __restrict__ un_se, const int32_t* __r
     const int u = un_blk[w];
     const bool diag = pcol[up_full[u]] == up_row[u];
     const bool single = up_un[u + 1] - up_un[u] == 1;
-    const bool packable = !diag && single && n >= 1 && n <= PACK_MAX && ((uint32_t)pair_b[un_se[2 * w]] >> PAIR_SHIFT) == 0u;
+    // every pair of a packable unit carries no direct block (a block may mix pairs with and without one: the
+    // camera-point block of a wireframe-coupled point has the lines' pairs and its own residuals' pair)
+    bool nodirect = n >= 1 && n <= PACK_MAX;
+    for (int k = 0; nodirect && k < n; ++k) nodirect = ((uint32_t)pair_b[un_se[2 * w] + k] >> PAIR_SHIFT) == 0u;
+    const bool packable = !diag && single && nodirect;
     key[w] = n > UNIT_LONG ? 0u : (packable ? 2u : 1u);
     val[w] = (uint32_t)w;
   }
@@ -664,7 +707,8 @@ __global__ void k_gather_obs(ObsGather a) {
   if (i >= a.n) return;
   const int64_t j = a.o + i;
   const int k = a.kind;
-  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L || k == R_PLANE_POINT3 || k >= R_SPHERE_POINT);
+  const bool is_point = (k == R_POINT || k == R_PLANE_POINT || k == R_P2L || k == R_PLANE_POINT3 ||
+                         (k >= R_SPHERE_POINT && k <= R_CUB_POINT));
   int code = 0;
   const int32_t f = a.feat[i];
   if (f < 0 || f >= (is_point ? a.np : a.nl)) code = 1;
@@ -680,10 +724,13 @@ __global__ void k_gather_obs(ObsGather a) {
   } else if (!code && k == R_VP) {
     g = a.other[i];
     if (g < 0 || g >= a.nv) code = 4;
-  } else if (!code && k >= R_SPHERE_POINT) {
+  } else if (!code && k >= R_SPHERE_POINT && k <= R_CUB_POINT) {
     g = a.other[i];
     if (g < 0 || g >= (k == R_SPHERE_POINT ? a.nsp : k == R_CYL_POINT ? a.ncy : k == R_CONE_POINT ? a.nco
                        : k == R_ELL_POINT ? a.nel : a.ncu)) code = 7;
+  } else if (!code && k == R_WF3D) {
+    g = a.other[i];
+    if (g < 0 || g >= a.np) code = 5;
   } else if (!code && (k == R_P2L || k == R_L2P) && a.other) {
     const int32_t q = a.other[i];
     if (q < 0 || q >= (k == R_P2L ? a.nl : a.np)) code = 5;
@@ -751,7 +798,7 @@ __global__ void k_kind_key(const int8_t* __restrict__ kind, int64_t n, uint32_t*
 }
 
 __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int64_t nsp, int64_t ncy, int64_t nco,
-                           int64_t nel, int64_t ncu, uint8_t* __restrict__ t) {
+                           int64_t nel, int64_t ncu, int64_t nk, uint8_t* __restrict__ t) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= na) return;
   int64_t b = nc;
@@ -766,6 +813,7 @@ __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int6
   b += nel; if (a >= b) ty = ENT_CUB1;
   b += ncu; if (a >= b) ty = ENT_CUB2;
   b += ncu; if (a >= b) ty = ENT_INTR;
+  b += nk; if (a >= b) ty = ENT_JPT;
   t[a] = ty;
 }
 
@@ -813,7 +861,7 @@ ba_status build_structure(Problem& P) {
   d.na = d.nc + d.npl + d.nv + d.ngs() + 2 * d.nbx() + d.nk;
   if (d.na > (int64_t)1 << 30 || d.nf > (int64_t)1 << 30) return fail(P, BA_ERR_ARG, "too many entities");
   // the pattern bitmap holds na x na bits
-  const int64_t wpr = (d.na + 31) / 32;
+  int64_t wpr = (d.na + 31) / 32;
   if ((double)d.na * (double)wpr * 8.0 > 16e9)
     return fail(P, BA_ERR_ARG, "too many cameras and groups for the reduced-system pattern (" + std::to_string(d.na) + ")");
 
@@ -903,7 +951,9 @@ ba_status build_structure(Problem& P) {
 
   Scratch S(&P.alloc, P.stream);
   const int NT = 256;
-  const int64_t na = d.na, nf = d.nf;
+  int64_t na = d.na, nf = d.nf;
+  bool any_wf = false;
+  for (auto& b : P.d_obs) any_wf |= b.kind == R_WF3D && b.n > 0;
   ba_status s;
   auto oom = [&]() { return fail(P, BA_ERR_OOM, "device allocation failed"); };
 
@@ -951,13 +1001,44 @@ ba_status build_structure(Problem& P) {
   }
   if (d.nc) CU(cudaMemcpyAsync(fixed_d, P.h_fixed.data(), d.nc, cudaMemcpyHostToDevice, P.stream));
 
+  // ---- points named by a 3D wireframe distance: entities of A after the intrinsics (ascending point id);
+  // their residuals are keyed to a zero-dimension feature each, after the points and lines
+  d.njp = 0;
+  int32_t* fkey_d = feat_d;
+  if (any_wf) {
+    if (d.nk || d.ngs() || d.nbx())
+      return fail(P, BA_ERR_ARG, "3D wireframe distances together with refined intrinsics or with spheres, cylinders, "
+                                 "cones, ellipsoids or cuboids are not supported");
+    int64_t *mark = S.get<int64_t>(d.np + 1), *rank = S.get<int64_t>(d.np + 1);
+    fkey_d = S.get<int32_t>(nr);
+    if (!mark || !rank || !fkey_d) return oom();
+    CU(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (d.np + 1), P.stream));
+    k_mark_jpt<<<grid_of(nr, NT), NT, 0, P.stream>>>(kind_d, grp_d, nr, mark);
+    if ((s = scan_excl(P, S, mark, rank, d.np))) return s;
+    if ((s = read_i64(P, rank + d.np, &d.njp))) return s;
+    P.jq = P.dnew<int32_t>(d.np);
+    P.jp_pt = P.dnew<int32_t>(d.njp);
+    if (!P.jq || !P.jp_pt) return oom();
+    if (d.np) k_jq<<<grid_of(d.np, NT), NT, 0, P.stream>>>(mark, rank, d.np, P.jq, P.jp_pt);
+    k_fkey<<<grid_of(nr, NT), NT, 0, P.stream>>>(feat_d, P.jq, d.np, d.nf, nr, fkey_d);
+    d.na += d.njp;
+    na = d.na;
+    if (d.na > (int64_t)1 << 30) return fail(P, BA_ERR_ARG, "too many entities");
+    wpr = (d.na + 31) / 32;
+    if ((double)d.na * (double)wpr * 8.0 > 16e9)
+      return fail(P, BA_ERR_ARG, "too many cameras, groups and wireframe-coupled points for the reduced-system "
+                                 "pattern (" + std::to_string(d.na) + ")");
+  }
+  d.nfp = d.nf + d.njp;
+  nf = d.nfp;
+
   // ---- feature-major order: stable sort by camera, then stable sort by feature
   uint32_t *key = S.get<uint32_t>(nr), *order = S.get<uint32_t>(nr), *k2 = S.get<uint32_t>(nr), *v2 = S.get<uint32_t>(nr);
   if (!key || !order || !k2 || !v2) return oom();
   if (nr) {
     k_iota_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(cam_d, nr, 1, key, order);
     if ((s = radix_sort(P, S, key, order, k2, v2, nr, bits_for(d.nc + 1)))) return s;
-    k_gather_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(feat_d, order, nr, key);
+    k_gather_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(fkey_d, order, nr, key);
     if ((s = radix_sort(P, S, key, order, k2, v2, nr, bits_for(nf)))) return s;
   }
   // residual offsets per feature
@@ -965,7 +1046,7 @@ ba_status build_structure(Problem& P) {
   int64_t* off64 = S.get<int64_t>(std::max(nf, na) + 1);
   if (!cnt64 || !off64) return oom();
   CU(cudaMemsetAsync(cnt64, 0, sizeof(int64_t) * (nf + 1), P.stream));
-  if (nr) k_count<<<grid_of(nr, NT), NT, 0, P.stream>>>(feat_d, nr, (unsigned long long*)cnt64);
+  if (nr) k_count<<<grid_of(nr, NT), NT, 0, P.stream>>>(fkey_d, nr, (unsigned long long*)cnt64);
   if ((s = scan_excl(P, S, cnt64, off64, nf))) return s;
   P.fres_off = P.dnew<int32_t>(nf + 1);
   if (!P.fres_off) return oom();
@@ -987,7 +1068,7 @@ ba_status build_structure(Problem& P) {
   }
   const int64_t kbase = d.kbase();
   SlotArgs sa{(const int32_t*)order, P.fres_off, cam_d, grp_d, kind_d, fixed_d, nf, d.nc, d.npl, err_d, P.cam_k, kbase,
-              d.sbase(), d.nsp, d.ncy, d.bbase(), d.nel, d.ncu};
+              d.sbase(), d.nsp, d.ncy, d.bbase(), d.nel, d.ncu, P.jq, d.jbase(), d.nf};
   int64_t* soff = S.get<int64_t>(nf + 1);
   if (!soff) return oom();
   k_slot_count<<<grid_of(nf, NT), NT, 0, P.stream>>>(sa, cnt64);
@@ -1008,7 +1089,7 @@ ba_status build_structure(Problem& P) {
   P.feat_plane_slot = P.dnew<int32_t>(nf);
   P.rslot_c = P.dnew<int32_t>(nr); P.rslot_g = P.dnew<int32_t>(nr);
   if (!P.fslot_off || !P.slot_ent || !P.slot_feat || !P.slot_type || !P.feat_plane_slot || !P.rslot_c || !P.rslot_g) return oom();
-  if (d.nk) {
+  if (d.nk || d.njp) {
     P.rslot_k = P.dnew<int32_t>(nr);
     if (!P.rslot_k) return oom();
   }
@@ -1069,7 +1150,7 @@ ba_status build_structure(Problem& P) {
   unsigned long long* ucnt = S.get<unsigned long long>(nbu + 1);
   if (!pkey || !pval || !pk2 || !pv2 || !gi || !gj || !ucnt) return oom();
   CU(cudaMemsetAsync(ucnt, 0, sizeof(unsigned long long) * (nbu + 1), P.stream));
-  PairGen pg{P.fslot_off, P.slot_ent, wpre, nlow, P.slot_type, P.cam_k, kbase, poff, uptr, bm, nf, pkey, pval, gi, gj, ucnt};
+  PairGen pg{P.fslot_off, P.slot_ent, wpre, nlow, P.slot_type, P.cam_k, kbase, d.nf, poff, uptr, bm, nf, pkey, pval, gi, gj, ucnt};
   if (nf) k_pair_gen<<<grid_of(nf, NT), NT, 0, P.stream>>>(pg);
   if ((s = radix_sort(P, S, pkey, pval, pk2, pv2, npair, bits_for(nbu)))) return s;
   P.pair_a = P.dnew<int32_t>(npair); P.pair_b = P.dnew<int32_t>(npair);
@@ -1168,7 +1249,7 @@ ba_status build_structure(Problem& P) {
   P.ent_type = P.dnew<uint8_t>(na);
   if (!P.ent_type) return oom();
   if (na) k_ent_type<<<grid_of(na, NT), NT, 0, P.stream>>>(na, d.nc, d.npl, d.nv, d.nsp, d.ncy, d.nco, d.nel, d.ncu,
-                                                            P.ent_type);
+                                                            d.nk, P.ent_type);
 
   // ---- parameters
 #define UP(dst, src) if ((s = upload(P, dst, src)) != BA_OK) return s

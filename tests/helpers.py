@@ -49,8 +49,11 @@ def padded_to_oracle_index(scene, lay):
             for g in range(ng):
                 idx += list(range(6 * o, 6 * o + w))
                 o += 1
-    for k in range(getattr(lay, "nk", 0)):
+    nk = getattr(lay, "nk", 0)
+    for k in range(nk):
         idx += list(range(6 * (o + k), 6 * (o + k) + 3))
+    for j in range(len(getattr(lay, "jpoints", ()))):   # points that the 3D wireframe distance names
+        idx += list(range(6 * (o + nk + j), 6 * (o + nk + j) + 3))
     return np.array(idx, np.int64)
 
 
