@@ -207,6 +207,7 @@ def main():
     ap.add_argument("--no-intr", action="store_true", help="skip the refined-intrinsics (cam_dof 9) workload")
     ap.add_argument("--no-group3d", action="store_true", help="skip the direct-3D group-distance workload")
     ap.add_argument("--no-surfaces", action="store_true", help="skip the sphere / cylinder / cone workload")
+    ap.add_argument("--no-wire3d", action="store_true", help="skip the 3D wireframe-distance workload")
     ap.add_argument("--intr-models", type=int, default=20,
                     help="camera models sharing refined intrinsics in that workload (0 = one per camera)")
     args = ap.parse_args()
@@ -548,6 +549,37 @@ def main():
                                "cylinders, cones, ellipsoids and cuboids each, 300 points on each; 5 steps timed "
                                "after 3 warm-up")
 
+    # ---------------- the wireframe constraints in the 3D form (Section 3.3 / Fig. 3b): the medium scene with its
+    # projected wireframe residuals (Eq. 11, Eq. 12), with the 3D endpoint distances instead (the named points
+    # become entities of the reduced system), and with both; LM iterations per second and the cost after 8 steps
+    wf = None
+    if not args.no_wire3d:
+        res_w = {}
+        for form in ("2d", "3d", "both"):
+            sw = make_scene(scfg("medium", seed=scfg("medium").seed + rank, wire_form=form))
+            q = B.ba_create(B.ba_default_options(precision=prec, cuda_stream=stream.cuda_stream))
+            B.load_scene(q, sw)
+            E0 = B.ba_eval_cost(q)[0]
+            for _ in range(3):
+                B.ba_lm_step(q)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tw = [B.ba_lm_step(q) for _ in range(5)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_w = e0.elapsed_time(e1)
+            na_w, nbf_w = B.ba_reduced_size(q)
+            E1 = B.ba_eval_cost(q)[0]
+            B.ba_destroy(q)
+            res_w[form] = {"lm_iters_per_s": round(5 / (ms_w / 1e3), 3), "ms_per_step": round(ms_w / 5, 3),
+                           "wireframe_residuals": {k: int(len(sw["obs"][k]["feat"])) for k in ("p2l", "l2p", "wf3d")},
+                           "block_rows": na_w, "stored_blocks": nbf_w, "pcg_iters": [r.pcg_iters for r in tw],
+                           "cost_after_8_steps_over_initial": round(E1 / E0, 5)}
+        wf = dict(res_w, note="the medium scene (200 cameras, 100k points, 20k lines) with the projected wireframe "
+                              "residuals (2d), the 3D endpoint distances (3d: every named point an entity of the "
+                              "reduced system) or both; 5 steps timed after 3 warm-up")
+
     # ---------------- the mixed path's error per result against the FP64 path, one step from the seeded start
     # at the initial damping (the FP64 path itself is checked against the oracle at 2000 cameras by
     # tests/test_gpu_scale.py)
@@ -607,7 +639,8 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "time_to_converge": ttc, "time_to_converge_fp64_block_jacobi": ttc64,
                "time_to_equal_cost": equal,
-               "batched_windows": batched, "refined_intrinsics": intr, "group_form_3d": g3, "surface_groups": srf, "learned_precond": learned,
+               "batched_windows": batched, "refined_intrinsics": intr, "group_form_3d": g3, "surface_groups": srf,
+               "wireframe_3d": wf, "learned_precond": learned,
                "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
                "stage_rooflines": stages, "measured_fma_tflops": {"fp32": round(peak32, 2), "fp64": round(peak64, 3)},
                "mixed_error": mixed_err,
