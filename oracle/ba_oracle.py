@@ -42,18 +42,18 @@ torch.set_default_dtype(torch.float64)
 DT = torch.float64
 
 KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
-         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point", "wf3d")
+         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point", "wf3d", "cuboid_line")
 # residual dimension, feature type, group type per kind
 RDIM = {"point": 2, "line": 4, "plane_point": 2, "plane_line": 4, "vp": 3, "p2l": 1, "l2p": 1,
         "plane_point3d": 1, "plane_line3d": 2, "sphere_point": 2, "cylinder_point": 2, "cone_point": 2,
-        "ellipsoid_point": 2, "cuboid_point": 2, "wf3d": 3}
+        "ellipsoid_point": 2, "cuboid_point": 2, "wf3d": 3, "cuboid_line": 4}
 FEAT = {"point": "point", "line": "line", "plane_point": "point", "plane_line": "line",
         "vp": "line", "p2l": "point", "l2p": "line", "plane_point3d": "point", "plane_line3d": "line",
         "sphere_point": "point", "cylinder_point": "point", "cone_point": "point", "ellipsoid_point": "point",
-        "cuboid_point": "point", "wf3d": "line"}
+        "cuboid_point": "point", "wf3d": "line", "cuboid_line": "line"}
 GROUP = {"plane_point": "plane", "plane_line": "plane", "vp": "vp", "plane_point3d": "plane",
          "plane_line3d": "plane", "sphere_point": "sphere", "cylinder_point": "cylinder", "cone_point": "cone",
-         "ellipsoid_point": "ellipsoid", "cuboid_point": "cuboid", "wf3d": "jpoint"}
+         "ellipsoid_point": "ellipsoid", "cuboid_point": "cuboid", "wf3d": "jpoint", "cuboid_line": "cuboid"}
 HAS_CAM = {k: k not in ("vp", "plane_point3d", "plane_line3d", "wf3d") for k in KINDS}
 # kinds outside the pixel cost E_px: the angular VP term, and the direct 3D distances
 NON_PIXEL = ("vp", "plane_point3d", "plane_line3d", "wf3d")
@@ -99,7 +99,8 @@ class Options:
                 "plane_line": self.w_group, "vp": self.w_vp, "p2l": self.w_wire,
                 "l2p": self.w_wire, "plane_point3d": self.w_group3d, "plane_line3d": self.w_group3d,
                 "sphere_point": self.w_group, "cylinder_point": self.w_group, "cone_point": self.w_group,
-                "ellipsoid_point": self.w_group, "cuboid_point": self.w_group, "wf3d": self.w_wire3d}[kind]
+                "ellipsoid_point": self.w_group, "cuboid_point": self.w_group, "wf3d": self.w_wire3d,
+                "cuboid_line": self.w_group}[kind]
 
     def scale(self, kind):
         if kind in ("plane_point3d", "plane_line3d", "wf3d"):
@@ -326,6 +327,29 @@ def cuboid_project_point(K, X):
     return X - df * nf
 
 
+def cuboid_centre(K):
+    """The centre of a cuboid (R, d): along R e_i its faces lie at d_i and at -d_{i+3}, so the centre is
+    sum_i R e_i (d_i - d_{i+3}) / 2."""
+    R = K[..., :9].reshape(K.shape[:-1] + (3, 3))
+    return (R @ ((K[..., 9:12] - K[..., 12:15]) / 2)[..., None])[..., 0]
+
+
+def cuboid_line_face(K, L):
+    """Appendix B: the face (n, w) a line is projected onto: the point of the infinite line closest to the
+    cuboid's centre, then the face nearest that point (smallest |signed distance|).  The choice is piecewise
+    constant, so no derivative flows through it."""
+    normals, w = cuboid_faces(K)
+    d, m = L[..., :3], L[..., 3:6]
+    dd = (d * d).sum(-1, keepdim=True)
+    p0 = torch.linalg.cross(d, m) / dd                       # the line's point closest to the origin
+    c = cuboid_centre(K)
+    pc = p0 + (((c - p0) * d).sum(-1, keepdim=True) / dd) * d
+    dist = (normals @ pc[..., None])[..., 0] + w
+    ad = dist.abs()
+    sel = (ad == ad.min(-1, keepdim=True).values).to(L.dtype)   # a tie is measure zero
+    return torch.cat([(normals * sel[..., None]).sum(-2), (w * sel).sum(-1, keepdim=True)], -1)
+
+
 GROUP_PROJECT = {"sphere": sphere_project_point, "cylinder": cylinder_project_point, "cone": cone_project_point,
                  "ellipsoid": ellipsoid_project_point, "cuboid": cuboid_project_point}
 
@@ -469,6 +493,15 @@ def res_plane_line3d(dc, df, dg, cam, feat, grp, meas):     # the same for a lin
     return torch.stack([(n * L[:3]).sum(-1), (n * foot).sum(-1) + P[3]]), torch.ones((), dtype=torch.bool)
 
 
+def res_cuboid_line(dc, df, dg, cam, feat, grp, meas):    # Eq. 8 with the cuboid's face (Appendix B)
+    R, t = _pose(cam, dc)
+    L = line_plus(feat, df)
+    P = cuboid_line_face(cuboid_plus(grp[:15], dg), L)
+    r1, n1 = rho(pi_line(R, t, cam, L), meas)
+    r2, n2 = rho(pi_line(R, t, cam, plane_project_line(P, L)), meas)
+    return r1 - r2, (n1 > 1e-12) & (n2 > 1e-12)
+
+
 def _res_surface_point(kind):
     """The group-induced point residual of Eq. 7 with the projection of another group type (Appendix B):
     pi(C, X) - pi(C, Proj_g(X))."""
@@ -501,7 +534,8 @@ RES_FN = {"point": res_point, "line": res_line, "plane_point": res_plane_point,
           "plane_line": res_plane_line, "vp": res_vp, "p2l": res_p2l, "l2p": res_l2p,
           "plane_point3d": res_plane_point3d, "plane_line3d": res_plane_line3d,
           "sphere_point": res_sphere_point, "cylinder_point": res_cylinder_point, "cone_point": res_cone_point,
-          "ellipsoid_point": res_ellipsoid_point, "cuboid_point": res_cuboid_point, "wf3d": res_wf3d}
+          "ellipsoid_point": res_ellipsoid_point, "cuboid_point": res_cuboid_point, "wf3d": res_wf3d,
+          "cuboid_line": res_cuboid_line}
 
 
 # ===========================================================================

@@ -32,6 +32,8 @@ Observation kinds (one record per residual):
   plane_point3d (-1, point, plane, no meas)  direct 3D distance (Section 3.2's alternative, Table 5)
   plane_line3d  (-1, line,  plane, no meas)  direct 3D distances of a line (direction, foot point)
   wf3d          (-1, line,  point, no meas)  3D wireframe endpoint distance X x d - m (Fig. 3b's form)
+  sphere_point .. cuboid_point (cam, point, group, no meas)  Eq. 7 with the other group types (Appendix B)
+  cuboid_line   (cam, line, cuboid, meas 4 segment)  Eq. 8 onto the cuboid's face nearest the line
 """
 from __future__ import annotations
 
@@ -44,10 +46,10 @@ IMG_W, IMG_H = 800.0, 600.0
 HALF = 3.0
 
 KINDS = ("point", "line", "plane_point", "plane_line", "vp", "p2l", "l2p", "plane_point3d", "plane_line3d",
-         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point", "wf3d")
+         "sphere_point", "cylinder_point", "cone_point", "ellipsoid_point", "cuboid_point", "wf3d", "cuboid_line")
 MEAS_DIM = {"point": 2, "line": 4, "plane_point": 0, "plane_line": 4, "vp": 0, "p2l": 4, "l2p": 2,
             "plane_point3d": 0, "plane_line3d": 0, "sphere_point": 0, "cylinder_point": 0, "cone_point": 0,
-            "ellipsoid_point": 0, "cuboid_point": 0, "wf3d": 0}
+            "ellipsoid_point": 0, "cuboid_point": 0, "wf3d": 0, "cuboid_line": 4}
 
 
 @dataclasses.dataclass
@@ -97,6 +99,9 @@ class SceneConfig:
     n_ellipsoids: int = 0
     n_cuboids: int = 0
     surf_points: int = 60
+    # lines on the cuboids' faces (Appendix B's line projection onto the face nearest the line), per cuboid,
+    # drawn with a generator of their own after the surface points
+    surf_lines: int = 0
     seed: int = 1
 
 
@@ -597,6 +602,8 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
     for k in kinds:
         obs[k + "_point"] = dict(cam=np.zeros(0, np.int32), feat=np.zeros(0, np.int32), other=np.zeros(0, np.int32),
                                  meas=np.zeros((0, 0)))
+    obs["cuboid_line"] = dict(cam=np.zeros(0, np.int32), feat=np.zeros(0, np.int32), other=np.zeros(0, np.int32),
+                              meas=np.zeros((0, 4)))
     counts = {"sphere": cfg.n_spheres, "cylinder": cfg.n_cylinders, "cone": cfg.n_cones,
               "ellipsoid": cfg.n_ellipsoids, "cuboid": cfg.n_cuboids}
     gt = {"sphere": np.zeros((0, 4)), "cylinder": np.zeros((0, 7)), "cone": np.zeros((0, 7)),
@@ -611,6 +618,7 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
     Nc = len(Rgt)
     np0 = len(scene["points"])
     new_P, new_gt, recs = [], [], []
+    cub_geo = []   # per cuboid (R local -> world, centre, half extents)
     for kind in kinds:
         rows, rows0 = [], []
         for g in range(counts[kind]):
@@ -646,6 +654,7 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
                     loc[np.arange(cfg.surf_points), ax] = np.where(f_ < 3, hx[ax], -hx[ax])
                     X = ctr + loc @ Rg.T
                     prm0 = np.concatenate([q0, dd + rng.normal(0, 0.03, 6)])
+                    cub_geo.append((Rg, ctr, hx))
             elif kind == "cylinder":
                 r = rng.uniform(0.2, 0.5)
                 prm = np.concatenate([d, np.cross(ctr, d), [r]])
@@ -702,6 +711,71 @@ def _add_surfaces(scene, cfg, Rgt, tgt, f, k1, k2, pp):
     for k in kinds:
         scene[keys[k]] = init[k]
         scene["gt"][keys[k]] = gt[k]
+    if cfg.surf_lines > 0 and cub_geo:
+        _add_cuboid_lines(scene, cfg, cub_geo, Rgt, tgt, f, pp)
+
+
+def _add_cuboid_lines(scene, cfg, cub_geo, Rgt, tgt, f, pp):
+    """surf_lines lines on faces of every cuboid (an in-face axis 70% of the time, else a random in-face
+    direction, centred inside the middle half of the face), appended after the other lines with their line
+    observations (segment endpoints, pinhole pixels) and one cuboid_line record per view."""
+    rng = np.random.default_rng(cfg.seed * 37 + 4242)
+    obs = scene["obs"]
+    E1, E2, gid = [], [], []
+    for g, (Rg, ctr, hx) in enumerate(cub_geo):
+        for _ in range(cfg.surf_lines):
+            fc = int(rng.integers(0, 6))
+            a = fc % 3
+            b, c = [k for k in range(3) if k != a]
+            dl = np.zeros(3)
+            if rng.random() < 0.7:
+                dl[b if rng.random() < 0.5 else c] = 1.0
+            else:
+                th = rng.uniform(0, 2 * np.pi)
+                dl[b], dl[c] = np.cos(th), np.sin(th)
+            loc = np.zeros(3)
+            loc[b], loc[c] = rng.uniform(-0.5, 0.5) * hx[b], rng.uniform(-0.5, 0.5) * hx[c]
+            loc[a] = hx[a] if fc < 3 else -hx[a]
+            ln = rng.uniform(0.5, 0.9) * min(hx[b], hx[c])
+            E1.append(ctr + Rg @ (loc - 0.5 * ln * dl))
+            E2.append(ctr + Rg @ (loc + 0.5 * ln * dl))
+            gid.append(g)
+    E1, E2, gid = np.array(E1), np.array(E2), np.array(gid, np.int64)
+    nl0 = len(scene["lines"])
+    xc1 = np.einsum("cij,pj->pci", Rgt, E1) + tgt[None]
+    xc2 = np.einsum("cij,pj->pci", Rgt, E2) + tgt[None]
+    a1 = _pix_pinhole(f[None], pp[None], xc1)
+    a2 = _pix_pinhole(f[None], pp[None], xc2)
+    vis = _visible(a1, xc1[..., 2]) & _visible(a2, xc2[..., 2])
+    lc, lf, lm, lg = [], [], [], []
+    for i in range(len(E1)):
+        cs = np.flatnonzero(vis[i])
+        if len(cs) < 2:
+            continue
+        n = int(min(len(cs), rng.integers(cfg.track_min, cfg.track_max + 1)))
+        cs = np.sort(rng.choice(cs, size=max(n, 2), replace=False))
+        m = np.concatenate([a1[i, cs], a2[i, cs]], 1) + rng.normal(0, cfg.sigma_px, (len(cs), 4))
+        out = rng.random(len(cs)) < cfg.outlier_frac
+        m[out] = np.stack([rng.uniform(0, IMG_W, out.sum()), rng.uniform(0, IMG_H, out.sum()),
+                           rng.uniform(0, IMG_W, out.sum()), rng.uniform(0, IMG_H, out.sum())], 1)
+        lc += cs.tolist(); lf += [nl0 + i] * len(cs); lm.append(m); lg += [int(gid[i])] * len(cs)
+    d = E2 - E1
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    gt_l = np.concatenate([d, np.cross(E1, d)], 1)
+    e1 = E1 + rng.normal(0, cfg.feat_noise, E1.shape)
+    e2 = E2 + rng.normal(0, cfg.feat_noise, E2.shape)
+    d0 = e2 - e1
+    d0 /= np.linalg.norm(d0, axis=1, keepdims=True)
+    init_l = np.concatenate([d0, np.cross(e1, d0)], 1)
+    scene["lines"] = np.concatenate([scene["lines"], init_l])
+    scene["gt"]["lines"] = np.concatenate([scene["gt"]["lines"], gt_l])
+    if lc:
+        cam = np.array(lc, np.int32); fid = np.array(lf, np.int32); meas = np.concatenate(lm)
+        o = obs["line"]
+        obs["line"] = dict(cam=np.concatenate([o["cam"], cam]), feat=np.concatenate([o["feat"], fid]),
+                           other=np.concatenate([o["other"], np.full(len(cam), -1, np.int32)]),
+                           meas=np.concatenate([o["meas"], meas]))
+        obs["cuboid_line"] = dict(cam=cam, feat=fid, other=np.array(lg, np.int32), meas=meas)
 
 
 def noise_free(cfg: SceneConfig) -> dict:

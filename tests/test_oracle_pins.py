@@ -147,7 +147,7 @@ def tiny_both():
     """The tiny scene with both forms of the plane constraints (group-induced 2D and direct 3D) and two spheres,
     cylinders and cones (Appendix B)."""
     s = make_scene(config("tiny", group_form="both", wire_form="both", n_spheres=2, n_cylinders=2, n_cones=2,
-                          n_ellipsoids=2, n_cuboids=2))
+                          n_ellipsoids=2, n_cuboids=2, surf_lines=4))
     return s, O.state_from_scene(s), s["fixed"]
 
 
@@ -567,7 +567,7 @@ def test_intrinsics_jacobian_finite_differences(kind):
     """Central differences of the residuals in (f, k1, k2) agree with the oracle's intrinsics Jacobian; the
     line kinds and the wireframe kinds do not depend on k1, k2 (undistorted pinhole pixels)."""
     s = make_scene(config("tiny", intr_refine=True, n_spheres=1, n_cylinders=1, n_cones=1, n_ellipsoids=1,
-                          n_cuboids=1))
+                          n_cuboids=1, surf_lines=4))
     st = O.state_from_scene(s)
     n = min(40, len(s["obs"][kind]["feat"]))
     assert n > 0
@@ -753,3 +753,47 @@ def test_wf3d_closed_form_and_layout():
     noise = noise_free(config("tiny", wire_form="3d"))
     r, v = O.residuals(O.state_from_scene(noise), noise["obs"], "wf3d")
     assert float(r.abs().max()) < 1e-13
+
+
+# ---------------------------------------------------------------- lines on cuboids (Appendix B)
+@pytest.mark.parametrize("R,off,d,p,n_exp,w_exp,m_exp", [
+    # unit cube at the origin; a line along x through (0, 0.3, 1.2), 0.2 above the top face z = 1: that face
+    # (n = e_z, w = -1), and the projected line through (0, 0.3, 1): m' = (0, 0.3, 1) x e_x = (0, 1, -0.3)
+    (np.eye(3), [1, 1, 1, 1, 1, 1], [1, 0, 0], [0, 0.3, 1.2], [0, 0, 1], -1, [0, 1, -0.3]),
+    # faces x = 2 and x = 0 (d_0 = 2, d_3 = 0): centre (1, 0, 0); a line along y through (2.1, 0, 0.5), whose
+    # point nearest the centre is (2.1, 0, 0.5), 0.1 outside face 0: n = e_x, w = -2, m' = (2, 0, 0.5) x e_y
+    (np.eye(3), [2, 1, 1, 0, 1, 1], [0, 1, 0], [2.1, 0, 0.5], [1, 0, 0], -2, [-0.5, 0, 2]),
+    # the unit cube turned 90 degrees about z (R e_0 = e_y, R e_1 = -e_x): a line along z through
+    # (-1.1, 0.2, 0) is nearest face 1, n = R e_1 = -e_x at -x = 1: w = -1, m' = (-1, 0.2, 0) x e_z = (0.2, 1, 0)
+    ([[0, -1, 0], [1, 0, 0], [0, 0, 1]], [1, 1, 1, 1, 1, 1], [0, 0, 1], [-1.1, 0.2, 0], [-1, 0, 0], -1, [0.2, 1, 0]),
+])
+def test_cuboid_line_face_and_projection(R, off, d, p, n_exp, w_exp, m_exp):
+    """Hand-worked face choice (the point of the line nearest the cuboid's centre, then the nearest face) and the
+    plane projection of the line onto it (Appendix B)."""
+    K = torch.tensor(np.concatenate([np.asarray(R, float).ravel(), np.asarray(off, float)]))
+    d = torch.tensor(d, dtype=torch.float64)
+    L = torch.cat([d, torch.linalg.cross(torch.tensor(p, dtype=torch.float64), d)])
+    P = O.cuboid_line_face(K, L)
+    np.testing.assert_allclose(P[:3].numpy(), n_exp, atol=1e-15)
+    assert abs(float(P[3]) - w_exp) < 1e-15
+    Lp = O.plane_project_line(P, L)
+    np.testing.assert_allclose(Lp[:3].numpy(), d.numpy(), atol=1e-15)
+    np.testing.assert_allclose(Lp[3:].numpy(), m_exp, atol=1e-14)
+
+
+def test_cuboid_line_zero_at_ground_truth_and_centre():
+    """On the noise-free scene every line on a cuboid face has a zero residual (its face is the nearest one), and
+    the centre of a generated cuboid is where scenegen put it."""
+    cfg = config("tiny", n_cuboids=2, surf_lines=6)
+    s = noise_free(cfg)
+    r, v = O.residuals(O.state_from_scene(s), s["obs"], "cuboid_line")
+    assert r.shape[0] > 10 and bool(v.all())
+    assert float(r.abs().max()) < 1e-10
+    K = torch.tensor(O.state_from_scene(s)["cuboids"][0])
+    faces_n, faces_w = O.cuboid_faces(K)
+    c = O.cuboid_centre(K)
+    # the centre lies halfway between opposite faces
+    for i in range(3):
+        a = float((faces_n[i] * c).sum() + faces_w[i])
+        b = float((faces_n[i + 3] * c).sum() + faces_w[i + 3])
+        assert abs(a - b) < 1e-12 and a < 0
