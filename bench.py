@@ -520,7 +520,7 @@ def main():
     if not args.no_surfaces:
         res_s = {}
         for label, kw in (("without", {}), ("with", dict(n_spheres=30, n_cylinders=30, n_cones=30, n_ellipsoids=30,
-                                                          n_cuboids=30, surf_points=300))):
+                                                          n_cuboids=30, surf_points=300, surf_lines=100))):
             ss = make_scene(scfg("medium", seed=scfg("medium").seed + rank, **kw))
             q = B.ba_create(B.ba_default_options(precision=prec, cuda_stream=stream.cuda_stream))
             B.load_scene(q, ss)
@@ -544,10 +544,10 @@ def main():
             if label == "with":
                 res_s[label]["surface_residuals"] = {k: int(len(ss["obs"][k]["feat"])) for k in
                                                      ("sphere_point", "cylinder_point", "cone_point",
-                                                      "ellipsoid_point", "cuboid_point")}
+                                                      "ellipsoid_point", "cuboid_point", "cuboid_line")}
         srf = dict(res_s, note="the medium scene (200 cameras, 100k points, 20k lines) without and with 30 spheres, "
-                               "cylinders, cones, ellipsoids and cuboids each, 300 points on each; 5 steps timed "
-                               "after 3 warm-up")
+                               "cylinders, cones, ellipsoids and cuboids each, 300 points on each and 100 lines on "
+                               "the faces of each cuboid; 5 steps timed after 3 warm-up")
 
     # ---------------- the wireframe constraints in the 3D form (Section 3.3 / Fig. 3b): the medium scene with its
     # projected wireframe residuals (Eq. 11, Eq. 12), with the 3D endpoint distances instead (the named points

@@ -93,7 +93,10 @@ typedef enum {
    * against Eq. 11 / Eq. 12): feature = the line id, other = the point id; no camera, no measurement.  Every
    * point it names becomes a 3-value entity of the reduced system (its residuals are not eliminated with
    * it); not together with cam_dof = 9 or the sphere ... cuboid groups, nor in ba_solve_batch (BA_ERR_ARG) */
-  BA_OBS_WIREFRAME3D = 14
+  BA_OBS_WIREFRAME3D = 14,
+  /* Eq. 8 for a line on a cuboid: the line projected onto the cuboid's face nearest the line's point closest to
+   * the cuboid's centre (Appendix B); other = the cuboid id, meas: 4 (the segment, as BA_OBS_PLANE_LINE) */
+  BA_OBS_CUBOID_LINE = 15
 } ba_obs_kind;
 
 typedef struct ba_options {

@@ -28,8 +28,8 @@ BA_PLANE, BA_VP, BA_SPHERE, BA_CYLINDER, BA_CONE, BA_ELLIPSOID, BA_CUBOID = 0, 1
 BA_REL_ORTHOGONAL, BA_REL_PARALLEL = 0, 1
 OBS_KINDS = {"point": 0, "line": 1, "plane_point": 2, "plane_line": 3, "vp": 4, "p2l": 5, "l2p": 6,
              "plane_point3d": 7, "plane_line3d": 8, "sphere_point": 9, "cylinder_point": 10, "cone_point": 11,
-             "ellipsoid_point": 12, "cuboid_point": 13, "wf3d": 14}
-MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0, 9: 0, 10: 0, 11: 0, 12: 0, 13: 0, 14: 0}
+             "ellipsoid_point": 12, "cuboid_point": 13, "wf3d": 14, "cuboid_line": 15}
+MEAS_DIM = {0: 2, 1: 4, 2: 0, 3: 4, 4: 0, 5: 4, 6: 2, 7: 0, 8: 0, 9: 0, 10: 0, 11: 0, 12: 0, 13: 0, 14: 0, 15: 4}
 NO_CAM = (4, 7, 8, 14)   # kinds without a camera (the VP term, the direct 3D plane and wireframe distances)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -24,7 +24,7 @@
 
 using namespace ba;
 
-static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0, 0, 0, 0};
+static const int kMeasDim[N_KINDS] = {2, 4, 0, 4, 0, 4, 2, 0, 0, 0, 0, 0, 0, 0, 0, 4};
 
 static ba_status set_err(ba_problem* p, ba_status s, const std::string& m) {
   if (p) p->err = m;

@@ -522,6 +522,10 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
       else if (kind == R_L2P) res_l2p<T, true, INTR>(c, F, meas, o);
       else if (kind == R_PLANE_LINE3) { res_plane_line3<T, true>(F, a.grp + (size_t)GRP_STRIDE * gid, o); has_plane = true; }
       else if (WF && kind == R_WF3D) res_wf3d<T, true>(F, a.pts + 3 * (size_t)gid, o);
+      else if (SURF && kind == R_CUB_LINE) {
+        res_box_line<T, true>(c, F, a.bx + (size_t)BOX_STRIDE * (a.nel + gid), meas, o);
+        has_plane = true;
+      }
       else continue;
     }
     if (!o.valid) continue;
@@ -590,7 +594,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
         }
       }
       if constexpr (SURF) {
-        if (has_plane && (kind == R_ELL_POINT || kind == R_CUB_POINT)) {
+        if (has_plane && (kind == R_ELL_POINT || kind == R_CUB_POINT || kind == R_CUB_LINE)) {
           // the 9-parameter group's second entity
           T w2[3];
 #pragma unroll
@@ -3448,6 +3452,7 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
             case R_ELL_POINT: res_box_point<double, false, 3>(c, X, a.bx + (size_t)BOX_STRIDE * gid, o); break;
             case R_CUB_POINT: res_box_point<double, false, 4>(c, X, a.bx + (size_t)BOX_STRIDE * (a.nel + gid), o); break;
             case R_WF3D: res_wf3d<double, false>(L, a.pts + 3 * (size_t)gid, o); break;
+            case R_CUB_LINE: res_box_line<double, false>(c, L, a.bx + (size_t)BOX_STRIDE * (a.nel + gid), meas, o); break;
           }
         }
         break;
@@ -3566,11 +3571,11 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 static LossW make_loss(const ba_options& o) {
   LossW L;
   // per kind: points, lines, plane-induced (2), VP, wireframe (2), direct 3D plane distances (2), sphere /
-  // cylinder / cone / ellipsoid / cuboid-induced (5), the 3D wireframe endpoint distance
+  // cylinder / cone / ellipsoid / cuboid-induced (5), the 3D wireframe endpoint distance, lines on cuboids
   const double w[N_KINDS] = {o.w_point, o.w_line, o.w_group, o.w_group, o.w_vp, o.w_wire, o.w_wire,
                              o.w_group3d, o.w_group3d, o.w_group, o.w_group, o.w_group, o.w_group, o.w_group,
-                             o.w_wire3d};
-  static_assert(N_KINDS == 15, "a weight per residual kind");
+                             o.w_wire3d, o.w_group};
+  static_assert(N_KINDS == 16, "a weight per residual kind");
   for (int k = 0; k < N_KINDS; ++k) {
     L.w[k] = w[k];
     double s = (k == R_VP) ? o.cauchy_vp : (res_has_cam(k) ? o.cauchy_px : o.cauchy_3d);
@@ -3644,7 +3649,12 @@ void launch_linearize(Problem& P) {
     // spheres, cylinders, cones: the points' positional groups take up to 6 dimensions (refined intrinsics are
     // refused together with them)
     if (d.np) { ++P.launches; k_linearize<T, 3, false, true><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
-    if (d.nl) { ++P.launches; k_linearize<T, 4><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
+    if (d.nl) {
+      ++P.launches;
+      // lines on cuboids take the 6-wide group accumulators and the cuboid's second entity too
+      if (d.ncu) k_linearize<T, 4, false, true><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf);
+      else k_linearize<T, 4><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf);
+    }
     return;
   }
   if (d.nk) {

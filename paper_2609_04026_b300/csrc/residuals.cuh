@@ -41,13 +41,14 @@ enum ResKind : int {
   R_PLANE_POINT3 = 7, R_PLANE_LINE3 = 8,   // the direct 3D plane distances (no camera)
   R_SPHERE_POINT = 9, R_CYL_POINT = 10, R_CONE_POINT = 11,  // group-induced point residuals of other group types
   R_ELL_POINT = 12, R_CUB_POINT = 13,                        // ... of the 9-parameter ellipsoid and cuboid
-  R_WF3D = 14                                                // 3D wireframe endpoint distance (line, point)
+  R_WF3D = 14,                                               // 3D wireframe endpoint distance (line, point)
+  R_CUB_LINE = 15                                            // Eq. 8 onto a cuboid's face (Appendix B)
 };
-constexpr int N_KINDS = 15;
+constexpr int N_KINDS = 16;
 
 __host__ __device__ constexpr int res_dim(int k) {
   return k == R_POINT ? 2 : k == R_LINE ? 4 : k == R_PLANE_POINT ? 2 : k == R_PLANE_LINE ? 4 : k == R_VP ? 3
-       : k == R_PLANE_LINE3 ? 2 : k == R_WF3D ? 3 : k >= R_SPHERE_POINT ? 2 : 1;
+       : k == R_PLANE_LINE3 ? 2 : k == R_WF3D ? 3 : k == R_CUB_LINE ? 4 : k >= R_SPHERE_POINT ? 2 : 1;
 }
 // surface group types (sphere, cylinder, cone): 8 raw values per group, increments of 4, 5 and 6
 constexpr int SRF_STRIDE = 8;
@@ -457,10 +458,11 @@ __device__ void res_plane_point(const Cam<T>& c, const T* X, const T* P, ResJ<T>
 }
 
 // R4: rho(pi_l(C, L)) - rho(pi_l(C, Proj_plane(L)))  (Eq. 8)
-template <class T, bool JAC, bool INTR = false>
-__device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T* seg, ResJ<T>& o) {
-  const T* n = P;
-  T w = P[3];
+// Eq. 8 for the plane (n, w): r, Jc, Jf (and Jk); the group columns through gdir(k, dn, dw), the plane change of
+// column k (normal change dn, offset change dw), stored by gput(i, k, value), for NG columns
+template <class T, bool JAC, bool INTR, int NG, class GDir, class GPut>
+__device__ __forceinline__ void plane_line_core(const Cam<T>& c, const T* L, const T* n, T w, const T* seg, ResJ<T>& o,
+                                                GDir gdir, GPut gput) {
   const T* d = L;
   const T* m = L + 3;
   T dp[3], mp[3];
@@ -490,17 +492,13 @@ __device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T*
     plane_proj_line_dir(n, w, d, m, ddir[k], mdir[k], zero3, T(0), ddp, dmp);
     dmc_dir(c, ddp, dmp, dmc2[k]);
   }
-  T dmcg[3][3];
-  {
-    const T* b1 = P + 4;
-    const T* b2 = P + 7;
-    T ddp[3], dmp[3];
-    plane_proj_line_dir(n, w, d, m, zero3, zero3, b1, T(0), ddp, dmp);
-    dmc_dir(c, ddp, dmp, dmcg[0]);
-    plane_proj_line_dir(n, w, d, m, zero3, zero3, b2, T(0), ddp, dmp);
-    dmc_dir(c, ddp, dmp, dmcg[1]);
-    plane_proj_line_dir(n, w, d, m, zero3, zero3, zero3, T(1), ddp, dmp);
-    dmc_dir(c, ddp, dmp, dmcg[2]);
+  T dmcg[NG][3];
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    T dn[3], dw, ddp[3], dmp[3];
+    gdir(k, dn, dw);
+    plane_proj_line_dir(n, w, d, m, zero3, zero3, dn, dw, ddp, dmp);
+    dmc_dir(c, ddp, dmp, dmcg[k]);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -512,13 +510,27 @@ __device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T*
 #pragma unroll
     for (int k = 0; k < 4; ++k) o.Jf[i][k] = dot3(G1[i], dmc1[k]) - dot3(G2[i], dmc2[k]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) o.Jg[i][k] = -dot3(G2[i], dmcg[k]);
+    for (int k = 0; k < NG; ++k) gput(i, k, -dot3(G2[i], dmcg[k]));
   }
   if (INTR) {
     const T a1 = mc1[2] / A1, a2 = mc2[2] / A2;
 #pragma unroll
     for (int i = 0; i < 4; ++i) { o.Jk[i][0] = l1[i & 1] * a1 - l2[i & 1] * a2; o.Jk[i][1] = 0; o.Jk[i][2] = 0; }
   }
+}
+
+// R4: Eq. 8 with the plane (n, w) and its tangent basis b1, b2 (P + 4, P + 7): group columns b1, b2 (normal), w
+template <class T, bool JAC, bool INTR = false>
+__device__ void res_plane_line(const Cam<T>& c, const T* L, const T* P, const T* seg, ResJ<T>& o) {
+  plane_line_core<T, JAC, INTR, 3>(
+      c, L, P, P[3], seg, o,
+      [&](int k, T* dn, T& dw) {
+        const T* b = k == 0 ? P + 4 : P + 7;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dn[i] = k < 2 ? b[i] : T(0);
+        dw = k == 2 ? T(1) : T(0);
+      },
+      [&](int i, int k, T v) { o.Jg[i][k] = v; });
 }
 
 // R5: d x v (Eq. 6 as a 3-vector; |d| = 1)
@@ -882,6 +894,76 @@ __device__ void res_box_point(const Cam<T>& c, const T* X, const T* G, ResJ<T>& 
       if (k < 6) o.Jg[i][k] = v; else o.Jg2[i][k - 6] = v;
     }
   }
+}
+
+// Lines on a cuboid (R, d): Eq. 8 onto the face nearest the line's point closest to the cuboid's centre
+// c0 = sum_i R e_i (d_i - d_{i+3}) / 2 (no derivative through that choice).  Group columns: the rotation
+// (dn = e_k x n) and the face's own offset (w = -d_f); Jg holds the first entity's 6 columns (rotation, d_0..2),
+// Jg2 the second's 3 (d_3..5)
+template <class T, bool JAC>
+__device__ void res_box_line(const Cam<T>& c, const T* L, const T* G, const T* seg, ResJ<T>& o) {
+  const T* R = G;   // row-major: column i is (R[i], R[3 + i], R[6 + i])
+  const T* d = L;
+  const T* m = L + 3;
+  T c0[3], h[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) h[i] = T(0.5) * (G[9 + i] - G[12 + i]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) c0[r] = R[3 * r] * h[0] + R[3 * r + 1] * h[1] + R[3 * r + 2] * h[2];
+  const T idd = T(1) / dot3(d, d);
+  T p0[3], pc[3];
+  cross3(d, m, p0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) p0[i] *= idd;
+  T v[3] = {c0[0] - p0[0], c0[1] - p0[1], c0[2] - p0[2]};
+  const T s = dot3(v, d) * idd;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pc[i] = p0[i] + s * d[i];
+  T best = T(0);
+  int face = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int i = f % 3;
+    const T sg = f < 3 ? T(1) : T(-1);
+    const T dist = sg * (R[i] * pc[0] + R[3 + i] * pc[1] + R[6 + i] * pc[2]) - G[9 + f];
+    if (f == 0 || fabs((double)dist) < fabs((double)best)) { best = dist; face = f; }
+  }
+  const int fi = face % 3;
+  const T sg = face < 3 ? T(1) : T(-1);
+  const T n[3] = {sg * R[fi], sg * R[3 + fi], sg * R[6 + fi]};
+  const T w = -G[9 + face];
+  if (JAC) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) o.Jg[i][k] = T(0);
+      o.Jg2[i][0] = o.Jg2[i][1] = o.Jg2[i][2] = T(0);
+    }
+  }
+  plane_line_core<T, JAC, false, 4>(
+      c, L, n, w, seg, o,
+      [&](int k, T* dn, T& dw) {
+        if (k < 3) {
+          T e[3] = {T(0), T(0), T(0)};
+          e[k] = T(1);
+          cross3(e, n, dn);
+          dw = T(0);
+        } else {
+          dn[0] = dn[1] = dn[2] = T(0);
+          dw = T(-1);
+        }
+      },
+      [&](int i, int k, T val) {
+        if (k < 3) {
+          o.Jg[i][k] = val;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {   // compile-time indices: the arrays stay in registers
+            if (face == q) o.Jg[i][3 + q] = val;
+            if (face == 3 + q) o.Jg2[i][q] = val;
+          }
+        }
+      });
 }
 
 // 3D wireframe endpoint distance of point X to line L = (d, m), |d| = 1: X x d - m (its norm is the distance).

@@ -320,13 +320,13 @@ __device__ __forceinline__ int64_t pos_group(const SlotArgs& a, int k, int32_t g
   if (k == R_CYL_POINT) return a.sbase + a.nsp + g;
   if (k == R_CONE_POINT) return a.sbase + a.nsp + a.ncy + g;
   if (k == R_ELL_POINT) return a.bbase + g;
-  if (k == R_CUB_POINT) return a.bbase + 2 * a.nel + g;
+  if (k == R_CUB_POINT || k == R_CUB_LINE) return a.bbase + 2 * a.nel + g;
   return -1;
 }
 // a 9-parameter group's second entity (A index), or -1
 __device__ __forceinline__ int64_t pos_group2(const SlotArgs& a, int k, int32_t g) {
   if (k == R_ELL_POINT) return a.bbase + a.nel + g;
-  if (k == R_CUB_POINT) return a.bbase + 2 * a.nel + a.ncu + g;
+  if (k == R_CUB_POINT || k == R_CUB_LINE) return a.bbase + 2 * a.nel + a.ncu + g;
   return -1;
 }
 __device__ __forceinline__ uint8_t pos_type(const SlotArgs& a, int64_t e) {
@@ -724,7 +724,7 @@ __global__ void k_gather_obs(ObsGather a) {
   } else if (!code && k == R_VP) {
     g = a.other[i];
     if (g < 0 || g >= a.nv) code = 4;
-  } else if (!code && k >= R_SPHERE_POINT && k <= R_CUB_POINT) {
+  } else if (!code && ((k >= R_SPHERE_POINT && k <= R_CUB_POINT) || k == R_CUB_LINE)) {
     g = a.other[i];
     if (g < 0 || g >= (k == R_SPHERE_POINT ? a.nsp : k == R_CYL_POINT ? a.ncy : k == R_CONE_POINT ? a.nco
                        : k == R_ELL_POINT ? a.nel : a.ncu)) code = 7;

@@ -1,7 +1,8 @@
 """Spheres, cylinders, cones, ellipsoids and cuboids (Appendix B, Table 6) through the C ABI against the FP64
 oracle: the group-induced point residual of Eq. 7 with each type's projection, its 4-, 5- and 6-wide group
 blocks in the reduced system (a 9-parameter group as two entities, 6 + 3), the log-space radii and semi-axes,
-the cone's half-angle, the cuboid's nearest face.  FP64 path at 1e-9: cost (1e-12), S and b, the
+the cone's half-angle, the cuboid's nearest face, and lines on cuboids (Eq. 8 onto the face nearest the line's
+point closest to the cuboid's centre).  FP64 path at 1e-9: cost (1e-12), S and b, the
 step and the predicted decrease, and an LM run with the oracle's decisions; the mixed step within 1e-5 (S, b)
 and 1e-3 (step) of FP64; refusals (batched windows, refined intrinsics, bad parameters)."""
 import numpy as np
@@ -33,8 +34,9 @@ _SC = {}
 
 def scene(name):
     if name not in _SC:
-        kw = dict(n_spheres=2, n_cylinders=2, n_cones=2, n_ellipsoids=2, n_cuboids=2) if name == "tiny" else \
-            dict(n_spheres=3, n_cylinders=3, n_cones=3, n_ellipsoids=3, n_cuboids=3, surf_points=150)
+        kw = dict(n_spheres=2, n_cylinders=2, n_cones=2, n_ellipsoids=2, n_cuboids=2, surf_lines=6) \
+            if name == "tiny" else \
+            dict(n_spheres=3, n_cylinders=3, n_cones=3, n_ellipsoids=3, n_cuboids=3, surf_points=150, surf_lines=30)
         _SC[name] = make_scene(config(name, **kw))
     return _SC[name]
 
@@ -134,7 +136,7 @@ def test_surface_mixed_step_against_fp64(B):
     (v0, b0, s0), (v1, b1, s1) = outs
     assert rel(v1, v0) <= 1e-5, rel(v1, v0)
     assert rel(b1, b0) <= 1e-5, rel(b1, b0)
-    for k in ("cam", "point"):
+    for k in ("cam", "point", "line"):
         assert rel(s1[k], s0[k]) <= 1e-3, (k, rel(s1[k], s0[k]))
 
 
