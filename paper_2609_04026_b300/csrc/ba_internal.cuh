@@ -311,6 +311,7 @@ struct ba_problem {
   // {first unit in processing order, units, first pair, pairs}, the pairs contiguous
   int32_t* pk_desc = nullptr;
   double* upart = nullptr;
+  int* unit_ctr = nullptr;   // the Schur unit kernel's work counter (reset before each launch)
   int line_slot0 = 0;           // first slot of a line feature
   // persistent PCG partition: CTA c owns block rows [cta_row0[c], cta_row0[c+1]); row r's stored blocks are
   // cut into chunks [chunk_beg[q], chunk_beg[q+1]) for q in [row_chunk0[r], row_chunk0[r+1])

@@ -236,7 +236,14 @@ struct LossW {
   double a2[N_KINDS];
   double inv_a2[N_KINDS];   // 1 / a^2: the scaled squared norm s / a^2 as a product
   double half_wa2[N_KINDS]; // w a^2 / 2, the factor of the Cauchy cost
+  float wf[N_KINDS], inv_a2f[N_KINDS];   // the float path's copies (no FP64 conversion per residual)
 };
+// the IRLS weight w / (1 + s / a^2) of a residual in the working type
+template <class T>
+__device__ __forceinline__ T irls_weight(const LossW& L, int kind, T s) {
+  if constexpr (sizeof(T) == 4) return L.wf[kind] / (1.0f + s * L.inv_a2f[kind]);
+  else return L.w[kind] / (1.0 + s * L.inv_a2[kind]);
+}
 
 template <class T>
 struct LinArgs {
@@ -542,7 +549,7 @@ __device__ void linearize_feature(const LinArgs<T>& a, int64_t f) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (i < rd) s += o.r[i] * o.r[i];
-    const T om = (T)a.loss.w[kind] / (T(1) + s * (T)a.loss.inv_a2[kind]);
+    const T om = irls_weight<T>(a.loss, kind, s);
     if (has_plane) ps = a.rslot_g[rr];
     if (has_vp) vs = a.rslot_g[rr];
     const bool camslot = sc >= 0;
@@ -804,7 +811,7 @@ __device__ void linearize_jpoint(const LinArgs<T>& a, int64_t q) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (i < rd) s += o.r[i] * o.r[i];
-    const T om = (T)a.loss.w[kind] / (T(1) + s * (T)a.loss.inv_a2[kind]);
+    const T om = irls_weight<T>(a.loss, kind, s);
     if (has_plane) ps = a.rslot_g[rr];
     const bool camslot = sc >= 0;
 #pragma unroll
@@ -1119,6 +1126,7 @@ struct UnitArgs {
   const T* CK;     // refined intrinsics: per camera slot J_cam^T w J_K of its own entity (or null)
   const T* CS;     // surface groups: per camera slot J_cam^T w J_group of the feature's sphere / cylinder / cone
   double* upart;   // 48 per unit: 36 S, 6 b, 6 diag(H)
+  int* ctr;        // grid path: the next unit a warp takes (zero at launch)
   int64_t nun, nmulti, nun_main, npack;
   int line_slot0;
   BlockArgs<T> fb;
@@ -1301,96 +1309,106 @@ __device__ __forceinline__ void load_rec(const T* src, T (&z)[24], bool line) {
   }
 }
 
+// the running sums of one work unit in a lane: the 6 x 6 term (and, for a diagonal block, b and diag(H))
 template <class T>
-__device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
-  constexpr int ST = UnitSmem<T>::stride, RS = UnitSmem<T>::red;
-  constexpr int CH = SW * (int)sizeof(T) / 16;   // 16-byte pieces of one Z record
-  T* stage = reinterpret_cast<T*>(smem);
-  int* sa_ = reinterpret_cast<int*>(smem + sizeof(T) * 32 * ST);
-  int* sb_ = sa_ + 32;
-  // the unit's descriptor (two independent loads instead of a chain through the block's arrays)
-  const int4 dsc = a.un_desc[g];
-  const int mf = a.un_mflag[g];
-  const int s0 = dsc.x, s1 = dsc.y, fpos = dsc.z, w = dsc.w;
-  const bool diag = (mf & 1) != 0;
-  const bool direct = (mf & 2) != 0;   // an off-diagonal block that fits this unit: written to S here
+struct UnitAcc {
   T acc[36], bacc[6], hacc[6];
+  __device__ __forceinline__ void zero() {
 #pragma unroll
-  for (int e = 0; e < 36; ++e) acc[e] = 0;
+    for (int e = 0; e < 36; ++e) acc[e] = 0;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) { bacc[i] = 0; hacc[i] = 0; }
-  for (int base = s0; base < s1; base += 32) {
-    const int n = min(32, s1 - base);
-    if (lane < n) { sa_[lane] = a.pair_a[base + lane]; sb_[lane] = a.pair_b[base + lane]; }
-    __syncwarp();
-    for (int t = lane; t < n * 2 * CH; t += 32) {
-      const int p = t / (2 * CH), r = t - p * 2 * CH;
-      const int which = r / CH, ch = r - which * CH;
-      const int e = which == 0 ? sa_[p] : (sb_[p] & PAIR_SLOT);
-      cp_async16(reinterpret_cast<char*>(stage + p * ST + which * SW) + 16 * ch,
-                 reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * ch);
-    }
-    cp_async_wait_all();
-    __syncwarp();
-    if (lane < n) {
-      const int ea = sa_[lane];
-      const unsigned code = (unsigned)sb_[lane] >> PAIR_SHIFT;
-      const bool line = ea >= a.line_slot0;
-      T za[24], zb[24];
-      load_rec(stage + lane * ST, za, line);
-      load_rec(stage + lane * ST + SW, zb, line);
-      if (diag) {
-        const T* H = a.H + (size_t)ea * SH;
-        const T* Bv = a.B + (size_t)ea * SB;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          bacc[i] += Bv[i];
-          hacc[i] += H[up_idx(i, i, 6)];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] - pair_dot(za, zb, i, j, line);
-        }
-      } else if (code == PAIR_CP || code == PAIR_CK) {
-        // the camera's direct block with the plane, or with its own intrinsics entity (6 x 3)
-        const T* Cm = (code == PAIR_CP ? a.C : a.CK) + (size_t)ea * SC;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
-      } else if (code == PAIR_CS) {
-        // the camera's direct block with the feature's sphere, cylinder or cone (6 x 6, zeros beyond its dims)
-        const T* Cm = a.CS + (size_t)ea * SCS;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += Cm[i * 6 + j] - pair_dot(za, zb, i, j, line);
-      } else if (code == PAIR_G12) {
-        // a 9-parameter group's two entities: the second entity's slot holds J_1^T w J_2 (6 x 3)
-        const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
-      } else if (code == PAIR_PK) {
-        // plane-intrinsics: the intrinsics slot holds J_K^T w J_plane (3 x 3); this block is its transpose
-        const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (i < 3 && j < 3 ? Cm[j * 3 + i] : T(0)) - pair_dot(za, zb, i, j, line);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 36; ++e) acc[e] -= pair_dot(za, zb, e / 6, e % 6, line);
-      }
-    }
-    __syncwarp();   // the next stage overwrites the staged records
+    for (int i = 0; i < 6; ++i) { bacc[i] = 0; hacc[i] = 0; }
   }
-  // cross-lane sums in lane order
-  T* red = stage;
+};
+
+// the pair indices of the stage [base, base + n) into sa_ / sb_ and the 16-byte copies of both Z records of
+// every pair into the stage buffer (cp.async; the caller waits)
+template <class T>
+__device__ __forceinline__ void unit_stage_issue(const UnitArgs<T>& a, int base, int n, T* stage, int* sa_, int* sb_,
+                                                 int lane) {
+  constexpr int ST = UnitSmem<T>::stride;
+  constexpr int CH = SW * (int)sizeof(T) / 16;   // 16-byte pieces of one Z record
+  if (lane < n) { sa_[lane] = a.pair_a[base + lane]; sb_[lane] = a.pair_b[base + lane]; }
+  __syncwarp();
+  for (int t = lane; t < n * 2 * CH; t += 32) {
+    const int p = t / (2 * CH), r = t - p * 2 * CH;
+    const int which = r / CH, ch = r - which * CH;
+    const int e = which == 0 ? sa_[p] : (sb_[p] & PAIR_SLOT);
+    cp_async16(reinterpret_cast<char*>(stage + p * ST + which * SW) + 16 * ch,
+               reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * ch);
+  }
+}
+
+// lane's term of its pair (lane < n) of a staged stage, added to its running sums
+template <class T>
+__device__ __forceinline__ void unit_stage_compute(const UnitArgs<T>& a, bool diag, int n, const T* stage,
+                                                   const int* sa_, const int* sb_, int lane, UnitAcc<T>& u) {
+  constexpr int ST = UnitSmem<T>::stride;
+  if (lane >= n) return;
+  T* acc = u.acc;
+  const int ea = sa_[lane];
+  const unsigned code = (unsigned)sb_[lane] >> PAIR_SHIFT;
+  const bool line = ea >= a.line_slot0;
+  T za[24], zb[24];
+  load_rec(stage + lane * ST, za, line);
+  load_rec(stage + lane * ST + SW, zb, line);
+  if (diag) {
+    const T* H = a.H + (size_t)ea * SH;
+    const T* Bv = a.B + (size_t)ea * SB;
 #pragma unroll
-  for (int e = 0; e < 36; ++e) red[lane * RS + e] = acc[e];
+    for (int i = 0; i < 6; ++i) {
+      u.bacc[i] += Bv[i];
+      u.hacc[i] += H[up_idx(i, i, 6)];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] - pair_dot(za, zb, i, j, line);
+    }
+  } else if (code == PAIR_CP || code == PAIR_CK) {
+    // the camera's direct block with the plane, or with its own intrinsics entity (6 x 3)
+    const T* Cm = (code == PAIR_CP ? a.C : a.CK) + (size_t)ea * SC;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+  } else if (code == PAIR_CS) {
+    // the camera's direct block with the feature's sphere, cylinder or cone (6 x 6, zeros beyond its dims)
+    const T* Cm = a.CS + (size_t)ea * SCS;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += Cm[i * 6 + j] - pair_dot(za, zb, i, j, line);
+  } else if (code == PAIR_G12) {
+    // a 9-parameter group's two entities: the second entity's slot holds J_1^T w J_2 (6 x 3)
+    const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+  } else if (code == PAIR_PK) {
+    // plane-intrinsics: the intrinsics slot holds J_K^T w J_plane (3 x 3); this block is its transpose
+    const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (i < 3 && j < 3 ? Cm[j * 3 + i] : T(0)) - pair_dot(za, zb, i, j, line);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 36; ++e) acc[e] -= pair_dot(za, zb, e / 6, e % 6, line);
+  }
+}
+
+// the unit's cross-lane sums in lane order (red: 32 x RS values of shared memory, free to overwrite), written to
+// S directly (a block this unit covers alone) or as FP64 partials of the unit
+template <class T>
+__device__ __forceinline__ void unit_finish_warp(const UnitArgs<T>& a, int fpos, int w, int mf, T* red, int lane,
+                                                 const UnitAcc<T>& u) {
+  constexpr int RS = UnitSmem<T>::red;
+  const bool diag = (mf & 1) != 0;
+  const bool direct = (mf & 2) != 0;
+#pragma unroll
+  for (int e = 0; e < 36; ++e) red[lane * RS + e] = u.acc[e];
   if (diag)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) { red[lane * RS + 36 + i] = bacc[i]; red[lane * RS + 42 + i] = hacc[i]; }
+    for (int i = 0; i < 6; ++i) { red[lane * RS + 36 + i] = u.bacc[i]; red[lane * RS + 42 + i] = u.hacc[i]; }
   __syncwarp();
   const int ne = diag ? 48 : 36;
   const int mpos = mf >> 2;
@@ -1408,21 +1426,130 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
       if (i < tt.w) a.fb.Sval[tt.off + j * tt.w + i] = v;
     }
   }
-  __syncwarp();   // the next unit of this warp reuses the shared memory
+  __syncwarp();
+}
+
+template <class T>
+__device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
+  constexpr int ST = UnitSmem<T>::stride;
+  T* stage = reinterpret_cast<T*>(smem);
+  int* sa_ = reinterpret_cast<int*>(smem + sizeof(T) * 32 * ST);
+  int* sb_ = sa_ + 32;
+  // the unit's descriptor (two independent loads instead of a chain through the block's arrays)
+  const int4 dsc = a.un_desc[g];
+  const int mf = a.un_mflag[g];
+  const int s0 = dsc.x, s1 = dsc.y, fpos = dsc.z, w = dsc.w;
+  const bool diag = (mf & 1) != 0;
+  UnitAcc<T> u;
+  u.zero();
+  for (int base = s0; base < s1; base += 32) {
+    const int n = min(32, s1 - base);
+    unit_stage_issue<T>(a, base, n, stage, sa_, sb_, lane);
+    cp_async_wait_all();
+    __syncwarp();
+    unit_stage_compute<T>(a, diag, n, stage, sa_, sb_, lane, u);
+    __syncwarp();   // the next stage overwrites the staged records
+  }
+  unit_finish_warp<T>(a, fpos, w, mf, stage, lane, u);   // the stage area takes the cross-lane sums
+}
+
+// Grid path: persistent warps, each taking the next unit of the processing order from a counter, with the
+// stages of its units in a two-deep pipeline: the copies of the next stage (of this unit or of the next) are
+// in flight while the current stage is summed, so a warp waits for a stage's gather only when the sums of
+// the previous one took less time.  Every unit's sums are those of unit_warp.
+template <class T>
+struct UnitPipeSmem {
+  static constexpr size_t buf = UnitSmem<T>::bytes;   // a stage buffer and its pair indices
+  static constexpr size_t bytes = 2 * buf;
+};
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <class T>
+__device__ void unit_pipe_warp(const UnitArgs<T>& a, char* smem, int lane) {
+  constexpr int ST = UnitSmem<T>::stride;
+  constexpr size_t BUF = UnitPipeSmem<T>::buf;
+  auto stage_of = [&](int b) { return reinterpret_cast<T*>(smem + b * BUF); };
+  auto sa_of = [&](int b) { return reinterpret_cast<int*>(smem + b * BUF + sizeof(T) * 32 * ST); };
+  auto take = [&]() {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(a.ctr, 1);
+    return __shfl_sync(0xffffffffu, v, 0);
+  };
+  int g = take();
+  if (g >= a.nun_main) return;
+  int4 dsc = a.un_desc[g];
+  int mf = a.un_mflag[g];
+  int base = dsc.x;
+  int buf = 0;
+  UnitAcc<T> u;
+  u.zero();
+  unit_stage_issue<T>(a, base, min(32, dsc.y - base), stage_of(0), sa_of(0), sa_of(0) + 32, lane);
+  cp_async_commit();
+  for (;;) {
+    // the next stage: the rest of this unit, else the first of the warp's next unit
+    const bool last = base + 32 >= dsc.y;
+    int ng = g, nbase = base + 32;
+    int4 nd = dsc;
+    int nmf = mf;
+    if (last) {
+      ng = take();
+      if (ng < a.nun_main) { nd = a.un_desc[ng]; nmf = a.un_mflag[ng]; nbase = nd.x; }
+    }
+    const bool more = ng < a.nun_main;
+    if (more) {
+      __syncwarp();   // the other buffer's last readers are done
+      unit_stage_issue<T>(a, nbase, min(32, nd.y - nbase), stage_of(buf ^ 1), sa_of(buf ^ 1), sa_of(buf ^ 1) + 32, lane);
+      cp_async_commit();
+      cp_async_wait_prev();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncwarp();
+    const int* sa_ = sa_of(buf);
+    unit_stage_compute<T>(a, (mf & 1) != 0, min(32, dsc.y - base), stage_of(buf), sa_, sa_ + 32, lane, u);
+    __syncwarp();
+    if (last) {
+      unit_finish_warp<T>(a, dsc.z, dsc.w, mf, stage_of(buf), lane, u);
+      u.zero();
+      if (!more) break;
+      g = ng; dsc = nd; mf = nmf;
+    }
+    base = nbase;
+    buf ^= 1;
+  }
 }
 
 template <class T>
 struct UnitWarps { static constexpr int n = sizeof(T) == 4 ? 4 : 2; };
 
-// grid path: a warp per unit, in the unit order (long units first)
+// grid path: persistent warps over the units in the unit order (long units first), pipelined stages
 template <class T>
 __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_units(UnitArgs<T> a) {
   constexpr int NW = UnitWarps<T>::n;
-  __shared__ __align__(16) char smem[NW][UnitSmem<T>::bytes];
+  extern __shared__ __align__(16) char unit_dyn[];   // NW x UnitPipeSmem<T>::bytes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g = blockIdx.x * (int64_t)NW + warp;
-  if (g >= a.nun_main) return;   // the whole warp leaves together
-  unit_warp<T>(a, (int)g, smem[warp], lane);
+  unit_pipe_warp<T>(a, unit_dyn + (size_t)warp * UnitPipeSmem<T>::bytes, lane);
+}
+
+// persistent grid of the unit kernel: the CTAs that are resident at once (opted in to its shared memory)
+template <class T>
+int schur_units_grid(int device, int64_t nun_main) {
+  constexpr int NW = UnitWarps<T>::n;
+  static int per_sm[2][64] = {};
+  const int ti = sizeof(T) == 4 ? 0 : 1;
+  if (device < 0 || device >= 64) device = 0;
+  const size_t smem = (size_t)NW * UnitPipeSmem<T>::bytes;
+  if (!per_sm[ti][device]) {
+    cudaFuncSetAttribute(k_schur_units<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur_units<T>, NW * 32, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaGetLastError();
+    per_sm[ti][device] = std::max(1, nb) * std::max(1, sms);
+  }
+  return (int)std::min<int64_t>(per_sm[ti][device], (nun_main + NW - 1) / NW);
 }
 
 // Small units, several to a warp: a pack holds whole off-diagonal blocks of a few pairs each (not
@@ -3582,6 +3709,8 @@ static LossW make_loss(const ba_options& o) {
     L.a2[k] = s * s;
     L.inv_a2[k] = 1.0 / L.a2[k];
     L.half_wa2[k] = 0.5 * w[k] * L.a2[k];
+    L.wf[k] = (float)L.w[k];
+    L.inv_a2f[k] = (float)L.inv_a2[k];
   }
   return L;
 }
@@ -3694,7 +3823,7 @@ UnitArgs<T> unit_args(Problem& P, double lambda) {
   un.upart = P.upart;
   un.nun = d.nun; un.nmulti = d.nmulti;
   un.pk_desc = reinterpret_cast<const int4*>(P.pk_desc); un.nun_main = d.nun_main; un.npack = d.npack;
-  un.line_slot0 = P.line_slot0; un.fb = b;
+  un.line_slot0 = P.line_slot0; un.fb = b; un.ctr = P.unit_ctr;
   return un;
 }
 
@@ -3705,7 +3834,9 @@ void launch_schur(Problem& P, double lambda) {
   constexpr int NW = UnitWarps<T>::n;
   if (d.nun_main) {
     ++P.launches;
-    k_schur_units<T><<<nblk(d.nun_main, NW), NW * 32, 0, P.stream>>>(un);
+    cudaMemsetAsync(P.unit_ctr, 0, sizeof(int), P.stream);
+    k_schur_units<T><<<schur_units_grid<T>(P.device, d.nun_main), NW * 32, (size_t)NW * UnitPipeSmem<T>::bytes,
+                       P.stream>>>(un);
   }
   if (d.npack) {
     ++P.launches;

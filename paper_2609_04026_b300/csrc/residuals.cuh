@@ -189,7 +189,7 @@ __device__ __forceinline__ void project_pin(const Cam<T>& c, const T* xc, T* pi,
 template <class T>
 __device__ __forceinline__ void tangent_b1(const T* n, T* b1) {
   T a[3] = {T(0), T(0), T(0)};
-  if (fabs((double)n[0]) < 0.9) a[0] = T(1); else a[1] = T(1);
+  if (fabs(n[0]) < T(0.9)) a[0] = T(1); else a[1] = T(1);
   T an = dot3(a, n);
   b1[0] = a[0] - an * n[0]; b1[1] = a[1] - an * n[1]; b1[2] = a[2] - an * n[2];
   T s = rsqrt_t(dot3(b1, b1));
@@ -199,7 +199,7 @@ __device__ __forceinline__ void tangent_b1(const T* n, T* b1) {
 template <class T>
 __device__ __forceinline__ void line_frame(const T* d, const T* m, T* u1, T* u3, T& r) {
   r = sqrt_t(dot3(m, m));
-  if ((double)r < 1e-12) {
+  if (r < T(1e-12)) {
     tangent_b1(d, u1);
   } else {
     T ir = T(1) / r;
@@ -351,7 +351,7 @@ __device__ void res_point(const Cam<T>& c, const T* X, const T* meas, ResJ<T>& o
   T p[3], xc[3], pi[2], J[2][3];
   matvec3(c.R, X, p);
   xc[0] = p[0] + c.t[0]; xc[1] = p[1] + c.t[1]; xc[2] = p[2] + c.t[2];
-  o.valid = (double)xc[2] > 1e-6;
+  o.valid = xc[2] > T(1e-6);
   if (!o.valid) return;
   project_dist<T, JAC>(c, xc, pi, J);
   o.r[0] = pi[0] - meas[0];
@@ -375,7 +375,7 @@ __device__ void res_line(const Cam<T>& c, const T* L, const T* seg, ResJ<T>& o) 
   line_to_cam(c, L, L + 3, dc, Rm, mc);
   image_line(c, mc, l);
   T A2 = rho_line<T, JAC>(c, l, seg, o.r, G);
-  o.valid = (double)A2 > 1e-24;
+  o.valid = A2 > T(1e-24);
   if (!JAC || !o.valid) return;
   T u1[3], u3[3], r;
   line_frame(L, L + 3, u1, u3, r);
@@ -410,7 +410,7 @@ __device__ void res_plane_point(const Cam<T>& c, const T* X, const T* P, ResJ<T>
   matvec3(c.R, Xp, p2);
 #pragma unroll
   for (int i = 0; i < 3; ++i) { x1[i] = p1[i] + c.t[i]; x2[i] = p2[i] + c.t[i]; }
-  o.valid = (double)x1[2] > 1e-6 && (double)x2[2] > 1e-6;
+  o.valid = x1[2] > T(1e-6) && x2[2] > T(1e-6);
   if (!o.valid) return;
   project_dist<T, JAC>(c, x1, pi1, J1);
   project_dist<T, JAC>(c, x2, pi2, J2);
@@ -475,7 +475,7 @@ __device__ __forceinline__ void plane_line_core(const Cam<T>& c, const T* L, con
   image_line(c, mc2, l2);
   T A1 = rho_line<T, JAC>(c, l1, seg, r1, G1);
   T A2 = rho_line<T, JAC>(c, l2, seg, r2, G2);
-  o.valid = (double)A1 > 1e-24 && (double)A2 > 1e-24;
+  o.valid = A1 > T(1e-24) && A2 > T(1e-24);
   if (!o.valid) return;
 #pragma unroll
   for (int i = 0; i < 4; ++i) o.r[i] = r1[i] - r2[i];
@@ -694,7 +694,7 @@ __device__ void res_surface_point(const Cam<T>& c, const T* X, const T* G, ResJ<
   matvec3(c.R, s.Xp, p2);
 #pragma unroll
   for (int i = 0; i < 3; ++i) { x1[i] = p1[i] + c.t[i]; x2[i] = p2[i] + c.t[i]; }
-  o.valid = (double)x1[2] > 1e-6 && (double)x2[2] > 1e-6;
+  o.valid = x1[2] > T(1e-6) && x2[2] > T(1e-6);
   if (!o.valid) return;
   project_dist<T, JAC>(c, x1, pi1, J1);
   project_dist<T, JAC>(c, x2, pi2, J2);
@@ -782,7 +782,7 @@ __device__ __forceinline__ void box_frame(const T* G, const T* X, BoxFrame<T>& b
       const int i = f % 3;
       const T sg = f < 3 ? T(1) : T(-1);
       const T dist = sg * (b.R[i] * X[0] + b.R[3 + i] * X[1] + b.R[6 + i] * X[2]) - G[9 + f];
-      if (f == 0 || fabs((double)dist) < fabs((double)best)) { best = dist; b.face = f; }
+      if (f == 0 || fabs(dist) < fabs(best)) { best = dist; b.face = f; }
     }
     const int i = b.face % 3;
     const T sg = b.face < 3 ? T(1) : T(-1);
@@ -855,7 +855,7 @@ __device__ void res_box_point(const Cam<T>& c, const T* X, const T* G, ResJ<T>& 
   matvec3(c.R, b.Xp, p2);
 #pragma unroll
   for (int i = 0; i < 3; ++i) { x1[i] = p1[i] + c.t[i]; x2[i] = p2[i] + c.t[i]; }
-  o.valid = (double)x1[2] > 1e-6 && (double)x2[2] > 1e-6;
+  o.valid = x1[2] > T(1e-6) && x2[2] > T(1e-6);
   if (!o.valid) return;
   project_dist<T, JAC>(c, x1, pi1, J1);
   project_dist<T, JAC>(c, x2, pi2, J2);
@@ -926,7 +926,7 @@ __device__ void res_box_line(const Cam<T>& c, const T* L, const T* G, const T* s
     const int i = f % 3;
     const T sg = f < 3 ? T(1) : T(-1);
     const T dist = sg * (R[i] * pc[0] + R[3 + i] * pc[1] + R[6 + i] * pc[2]) - G[9 + f];
-    if (f == 0 || fabs((double)dist) < fabs((double)best)) { best = dist; face = f; }
+    if (f == 0 || fabs(dist) < fabs(best)) { best = dist; face = f; }
   }
   const int fi = face % 3;
   const T sg = face < 3 ? T(1) : T(-1);
@@ -1058,7 +1058,7 @@ __device__ void res_p2l(const Cam<T>& c, const T* X, const T* seg, ResJ<T>& o) {
   T p[3], xc[3], pi[2], J[2][3];
   matvec3(c.R, X, p);
   xc[0] = p[0] + c.t[0]; xc[1] = p[1] + c.t[1]; xc[2] = p[2] + c.t[2];
-  o.valid = (double)xc[2] > 1e-6;
+  o.valid = xc[2] > T(1e-6);
   if (!o.valid) return;
   project_pin<T, JAC>(c, xc, pi, J);
   o.r[0] = lh[0] * pi[0] + lh[1] * pi[1] + lh[2];
@@ -1082,7 +1082,7 @@ __device__ void res_l2p(const Cam<T>& c, const T* L, const T* x, ResJ<T>& o) {
   line_to_cam(c, L, L + 3, dc, Rm, mc);
   image_line(c, mc, l);
   T A2 = l[0] * l[0] + l[1] * l[1];
-  o.valid = (double)A2 > 1e-24;
+  o.valid = A2 > T(1e-24);
   if (!o.valid) return;
   T in = rsqrt_t(A2);
   T q = l[0] * x[0] + l[1] * x[1] + l[2];

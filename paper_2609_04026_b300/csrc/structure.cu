@@ -665,13 +665,16 @@ __global__ void k_multi_fill(const int64_t* __restrict__ flag, const int64_t* __
   if (u < nbu && flag[u]) list[off[u]] = (int32_t)u;
 }
 
-// processing class of a unit: 0 long (scheduled first), 1 other, 2 packable (a whole off-diagonal block
-// of 1..PACK_MAX pairs, not a camera-plane block: its sums go straight to S)
+// processing class of a unit (bits 30-31): 0 long (scheduled first), 1 other, 2 packable (a whole
+// off-diagonal block of 1..PACK_MAX pairs, not a camera-plane block: its sums go straight to S).  Classes 0 and
+// 1 run in the locality order of their block's row (bits 0-29, the row's rank), so that the units that read
+// the slot records of the same features run close together in time and find them in L2; packable units keep
+// block order (the packs take consecutive units).  The order changes no sum.
 __global__ void k_unit_key(const int32_t* __restrict__ un_se, const int32_t* __restrict__ un_blk,
                            const int32_t* __restrict__ up_un, const int32_t* __restrict__ up_row,
                            const int32_t* __restrict__ up_full, const int32_t* __restrict__ pcol,
-                           const int32_t* __restrict__ pair_b, int64_t nun, uint32_t* __restrict__ key,
-                           uint32_t* __restrict__ val) {
+                           const int32_t* __restrict__ pair_b, const int32_t* __restrict__ rank, int64_t nun,
+                           uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (w < nun) {
     const int n = un_se[2 * w + 1] - un_se[2 * w];
@@ -683,7 +686,8 @@ __global__ void k_unit_key(const int32_t* __restrict__ un_se, const int32_t* __r
     bool nodirect = n >= 1 && n <= PACK_MAX;
     for (int k = 0; nodirect && k < n; ++k) nodirect = ((uint32_t)pair_b[un_se[2 * w] + k] >> PAIR_SHIFT) == 0u;
     const bool packable = !diag && single && nodirect;
-    key[w] = n > UNIT_LONG ? 0u : (packable ? 2u : 1u);
+    const uint32_t cls = n > UNIT_LONG ? 0u : (packable ? 2u : 1u);
+    key[w] = (cls << 30) | (cls == 2u ? 0u : (uint32_t)rank[up_row[u]]);
     val[w] = (uint32_t)w;
   }
 }
@@ -820,6 +824,51 @@ __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int6
 static ba_status read_i64(Problem& P, const int64_t* src, int64_t* dst) {
   CU(cudaMemcpyAsync(dst, src, sizeof(int64_t), cudaMemcpyDeviceToHost, P.stream));
   CU(cudaStreamSynchronize(P.stream));
+  return BA_OK;
+}
+
+// A locality order of the block rows: reverse Cuthill-McKee over the camera-camera pattern of S (breadth-first
+// from a camera of least degree, neighbours by ascending degree, every component in turn, reversed), the other
+// rows after the cameras in index order.  Covisible cameras get nearby ranks.  rank[a] = position of row a.
+static ba_status row_locality_rank(Problem& P, std::vector<int32_t>& rank) {
+  const Dims& d = P.d;
+  const int64_t na = d.na, nc = d.nc;
+  rank.assign(na, 0);
+  for (int64_t a = 0; a < na; ++a) rank[a] = (int32_t)a;
+  if (nc < 3) return BA_OK;
+  const int64_t ncol = P.h_prow_ptr[nc];
+  std::vector<int32_t> col(ncol);
+  CU(cudaMemcpyAsync(col.data(), P.col, sizeof(int32_t) * ncol, cudaMemcpyDeviceToHost, P.stream));
+  CU(cudaStreamSynchronize(P.stream));
+  std::vector<int32_t> deg(nc, 0);
+  auto nbrs = [&](int64_t a, auto&& f) {
+    for (int64_t q = P.h_prow_ptr[a]; q < P.h_prow_ptr[a + 1]; ++q) {
+      const int32_t b = col[q];
+      if (b < nc && b != a) f(b);
+    }
+  };
+  for (int64_t a = 0; a < nc; ++a) nbrs(a, [&](int32_t) { ++deg[a]; });
+  std::vector<int32_t> order;
+  order.reserve(nc);
+  std::vector<char> seen(nc, 0);
+  std::vector<int32_t> byd(nc);
+  std::iota(byd.begin(), byd.end(), 0);
+  std::stable_sort(byd.begin(), byd.end(), [&](int32_t x, int32_t y) { return deg[x] < deg[y]; });
+  std::vector<int32_t> next;
+  for (int32_t st : byd) {
+    if (seen[st]) continue;
+    seen[st] = 1;
+    size_t head = order.size();
+    order.push_back(st);
+    while (head < order.size()) {
+      const int32_t a = order[head++];
+      next.clear();
+      nbrs(a, [&](int32_t b) { if (!seen[b]) { seen[b] = 1; next.push_back(b); } });
+      std::stable_sort(next.begin(), next.end(), [&](int32_t x, int32_t y) { return deg[x] < deg[y]; });
+      order.insert(order.end(), next.begin(), next.end());
+    }
+  }
+  for (int64_t i = 0; i < nc; ++i) rank[order[nc - 1 - i]] = (int32_t)i;
   return BA_OK;
 }
 
@@ -1171,8 +1220,8 @@ ba_status build_structure(Problem& P) {
     if ((s = read_i64(P, ustart + nbu, &nun))) return s;
     d.nun = nun;
     P.up_un = P.dnew<int32_t>(nbu + 1); P.un_se = P.dnew<int32_t>(2 * nun); P.un_blk = P.dnew<int32_t>(nun);
-    P.un_order = P.dnew<int32_t>(nun); P.upart = P.dnew<double>(48 * nun);
-    if (!P.up_un || !P.un_se || !P.un_blk || !P.un_order || !P.upart) return oom();
+    P.un_order = P.dnew<int32_t>(nun); P.upart = P.dnew<double>(48 * nun); P.unit_ctr = P.dnew<int>(1);
+    if (!P.up_un || !P.un_se || !P.un_blk || !P.un_order || !P.upart || !P.unit_ctr) return oom();
     k_unit_fill<<<grid_of(nbu + 1, NT), NT, 0, P.stream>>>(ucnt, pstart, ustart, nbu, P.up_row, P.up_full, P.col,
                                                             P.up_un, P.un_se, P.un_blk, mflag);
     if ((s = scan_excl(P, S, mflag, moff, nbu))) return s;
@@ -1185,9 +1234,14 @@ ba_status build_structure(Problem& P) {
     uint32_t *uk = S.get<uint32_t>(nun), *uk2 = S.get<uint32_t>(nun), *uv2 = S.get<uint32_t>(nun);
     if (!uk || !uk2 || !uv2) return oom();
     if (nun) {
+      std::vector<int32_t> hrank;
+      if ((s = row_locality_rank(P, hrank))) return s;
+      int32_t* rank_d = S.get<int32_t>(na);
+      if (!rank_d) return oom();
+      CU(cudaMemcpyAsync(rank_d, hrank.data(), sizeof(int32_t) * na, cudaMemcpyHostToDevice, P.stream));
       k_unit_key<<<grid_of(nun, NT), NT, 0, P.stream>>>(P.un_se, P.un_blk, P.up_un, P.up_row, P.up_full, P.col,
-                                                       P.pair_b, nun, uk, (uint32_t*)P.un_order);
-      if ((s = radix_sort(P, S, uk, (uint32_t*)P.un_order, uk2, uv2, nun, 8))) return s;
+                                                       P.pair_b, rank_d, nun, uk, (uint32_t*)P.un_order);
+      if ((s = radix_sort(P, S, uk, (uint32_t*)P.un_order, uk2, uv2, nun, 32))) return s;
     }
     if (nbp >= ((int64_t)1 << 29)) return fail(P, BA_ERR_ARG, "too many blocks in the reduced system");
     P.un_desc = P.dnew<int32_t>(4 * nun);
@@ -1204,7 +1258,7 @@ ba_status build_structure(Problem& P) {
       std::vector<uint32_t> hk(nun);
       CU(cudaMemcpyAsync(hk.data(), uk, sizeof(uint32_t) * nun, cudaMemcpyDeviceToHost, P.stream));
       CU(cudaStreamSynchronize(P.stream));
-      const int64_t nmain = std::lower_bound(hk.begin(), hk.end(), 2u) - hk.begin();
+      const int64_t nmain = std::lower_bound(hk.begin(), hk.end(), 2u << 30) - hk.begin();
       const int64_t nsm = nun - nmain;
       if (nsm > 0) {
         std::vector<int32_t> hd(4 * nsm);
