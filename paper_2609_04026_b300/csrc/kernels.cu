@@ -1323,13 +1323,38 @@ struct UnitAcc {
 
 // the pair indices of the stage [base, base + n) into sa_ / sb_ and the 16-byte copies of both Z records of
 // every pair into the stage buffer (cp.async; the caller waits)
+// A diagonal block's pairs are (e, e): their stage holds the Z record once and, after it, the slot's direct
+// block H (for float the whole G|H record, whose start is 16-byte aligned; for double H and its pad, from
+// offset HG_H); DiagStage gives the copy's source offset from H, its 16-byte pieces and where H lands
 template <class T>
-__device__ __forceinline__ void unit_stage_issue(const UnitArgs<T>& a, int base, int n, T* stage, int* sa_, int* sb_,
-                                                 int lane) {
+struct DiagStage {
+  static constexpr int src = sizeof(T) == 4 ? -HG_H : 0;        // from a.H + e * SH
+  static constexpr int pieces = sizeof(T) == 4 ? SG * 4 / 16 : 22 * 8 / 16;
+  static constexpr int h_at = SW + (sizeof(T) == 4 ? HG_H : 0);  // H in the staged pair
+  static_assert(SW + pieces * 16 / (int)sizeof(T) <= UnitSmem<T>::stride, "a diagonal pair fits its stage slot");
+};
+
+template <class T>
+__device__ __forceinline__ void unit_stage_issue(const UnitArgs<T>& a, bool diag, int base, int n, T* stage, int* sa_,
+                                                 int* sb_, int lane) {
   constexpr int ST = UnitSmem<T>::stride;
   constexpr int CH = SW * (int)sizeof(T) / 16;   // 16-byte pieces of one Z record
+  constexpr int DP = DiagStage<T>::pieces;
   if (lane < n) { sa_[lane] = a.pair_a[base + lane]; sb_[lane] = a.pair_b[base + lane]; }
   __syncwarp();
+  if (diag) {
+    for (int t = lane; t < n * (CH + DP); t += 32) {
+      const int p = t / (CH + DP), r = t - p * (CH + DP);
+      const int e = sa_[p];
+      if (r < CH)
+        cp_async16(reinterpret_cast<char*>(stage + p * ST) + 16 * r,
+                   reinterpret_cast<const char*>(a.Z + (size_t)e * SW) + 16 * r);
+      else
+        cp_async16(reinterpret_cast<char*>(stage + p * ST + SW) + 16 * (r - CH),
+                   reinterpret_cast<const char*>(a.H + (size_t)e * SH + DiagStage<T>::src) + 16 * (r - CH));
+    }
+    return;
+  }
   for (int t = lane; t < n * 2 * CH; t += 32) {
     const int p = t / (2 * CH), r = t - p * 2 * CH;
     const int which = r / CH, ch = r - which * CH;
@@ -1340,9 +1365,20 @@ __device__ __forceinline__ void unit_stage_issue(const UnitArgs<T>& a, int base,
 }
 
 // lane's term of its pair (lane < n) of a staged stage, added to its running sums
+// a diagonal pair's b part (the slot's B record), loaded before the stage's copies are waited for
+template <class T>
+__device__ __forceinline__ void unit_diag_b(const UnitArgs<T>& a, bool diag, int n, const int* sa_, int lane, T (&bv)[6]) {
+  if (diag && lane < n) {
+    const T* Bv = a.B + (size_t)sa_[lane] * SB;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) bv[i] = Bv[i];
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void unit_stage_compute(const UnitArgs<T>& a, bool diag, int n, const T* stage,
-                                                   const int* sa_, const int* sb_, int lane, UnitAcc<T>& u) {
+                                                   const int* sa_, const int* sb_, int lane, const T (&bv)[6],
+                                                   UnitAcc<T>& u) {
   constexpr int ST = UnitSmem<T>::stride;
   if (lane >= n) return;
   T* acc = u.acc;
@@ -1351,18 +1387,22 @@ __device__ __forceinline__ void unit_stage_compute(const UnitArgs<T>& a, bool di
   const bool line = ea >= a.line_slot0;
   T za[24], zb[24];
   load_rec(stage + lane * ST, za, line);
-  load_rec(stage + lane * ST + SW, zb, line);
   if (diag) {
-    const T* H = a.H + (size_t)ea * SH;
-    const T* Bv = a.B + (size_t)ea * SB;
+    // the pair (e, e): one staged Z record, the staged H after it
+#pragma unroll
+    for (int k = 0; k < 24; ++k) zb[k] = za[k];
+    const T* H = stage + lane * ST + DiagStage<T>::h_at;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      u.bacc[i] += Bv[i];
+      u.bacc[i] += bv[i];
       u.hacc[i] += H[up_idx(i, i, 6)];
 #pragma unroll
       for (int j = 0; j < 6; ++j) acc[i * 6 + j] += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] - pair_dot(za, zb, i, j, line);
     }
-  } else if (code == PAIR_CP || code == PAIR_CK) {
+    return;
+  }
+  load_rec(stage + lane * ST + SW, zb, line);
+  if (code == PAIR_CP || code == PAIR_CK) {
     // the camera's direct block with the plane, or with its own intrinsics entity (6 x 3)
     const T* Cm = (code == PAIR_CP ? a.C : a.CK) + (size_t)ea * SC;
 #pragma unroll
@@ -1444,10 +1484,12 @@ __device__ void unit_warp(const UnitArgs<T>& a, int g, char* smem, int lane) {
   u.zero();
   for (int base = s0; base < s1; base += 32) {
     const int n = min(32, s1 - base);
-    unit_stage_issue<T>(a, base, n, stage, sa_, sb_, lane);
+    unit_stage_issue<T>(a, diag, base, n, stage, sa_, sb_, lane);
+    T bv[6];
+    unit_diag_b<T>(a, diag, n, sa_, lane, bv);
     cp_async_wait_all();
     __syncwarp();
-    unit_stage_compute<T>(a, diag, n, stage, sa_, sb_, lane, u);
+    unit_stage_compute<T>(a, diag, n, stage, sa_, sb_, lane, bv, u);
     __syncwarp();   // the next stage overwrites the staged records
   }
   unit_finish_warp<T>(a, fpos, w, mf, stage, lane, u);   // the stage area takes the cross-lane sums
@@ -1485,7 +1527,7 @@ __device__ void unit_pipe_warp(const UnitArgs<T>& a, char* smem, int lane) {
   int buf = 0;
   UnitAcc<T> u;
   u.zero();
-  unit_stage_issue<T>(a, base, min(32, dsc.y - base), stage_of(0), sa_of(0), sa_of(0) + 32, lane);
+  unit_stage_issue<T>(a, (mf & 1) != 0, base, min(32, dsc.y - base), stage_of(0), sa_of(0), sa_of(0) + 32, lane);
   cp_async_commit();
   for (;;) {
     // the next stage: the rest of this unit, else the first of the warp's next unit
@@ -1498,9 +1540,12 @@ __device__ void unit_pipe_warp(const UnitArgs<T>& a, char* smem, int lane) {
       if (ng < a.nun_main) { nd = a.un_desc[ng]; nmf = a.un_mflag[ng]; nbase = nd.x; }
     }
     const bool more = ng < a.nun_main;
+    T bv[6];
+    unit_diag_b<T>(a, (mf & 1) != 0, min(32, dsc.y - base), sa_of(buf), lane, bv);
     if (more) {
       __syncwarp();   // the other buffer's last readers are done
-      unit_stage_issue<T>(a, nbase, min(32, nd.y - nbase), stage_of(buf ^ 1), sa_of(buf ^ 1), sa_of(buf ^ 1) + 32, lane);
+      unit_stage_issue<T>(a, (nmf & 1) != 0, nbase, min(32, nd.y - nbase), stage_of(buf ^ 1), sa_of(buf ^ 1),
+                          sa_of(buf ^ 1) + 32, lane);
       cp_async_commit();
       cp_async_wait_prev();
     } else {
@@ -1508,7 +1553,7 @@ __device__ void unit_pipe_warp(const UnitArgs<T>& a, char* smem, int lane) {
     }
     __syncwarp();
     const int* sa_ = sa_of(buf);
-    unit_stage_compute<T>(a, (mf & 1) != 0, min(32, dsc.y - base), stage_of(buf), sa_, sa_ + 32, lane, u);
+    unit_stage_compute<T>(a, (mf & 1) != 0, min(32, dsc.y - base), stage_of(buf), sa_, sa_ + 32, lane, bv, u);
     __syncwarp();
     if (last) {
       unit_finish_warp<T>(a, dsc.z, dsc.w, mf, stage_of(buf), lane, u);
