@@ -2542,7 +2542,23 @@ __device__ __forceinline__ void ds_madd(DotAcc<float>& a, float b, const XV<floa
   a.hi = sm;
   a.lo += err + fmaf(b, x.l, pe);
 }
+__device__ __forceinline__ void ds_madd(DotAcc<float>& a, float b, const XV<float>& x);
 __device__ __forceinline__ void ds_madd(DotAcc<double>& a, double b, const XV<double>& x) { a.s = fma(b, x.v, a.s); }
+// acc += sum_j b[j * bs] x[j] over N terms of one stored block: for float the block's short dot product in
+// float FMA (head and tail parts of x; its rounding is a few units of the block's own float entries, the
+// order of their storage rounding) added to the double-single sum once; for double plain FMA
+template <int N>
+__device__ __forceinline__ void blk_dot(DotAcc<float>& acc, const float* b, int bs, const XV<float>* x) {
+  float h = 0.f, l = 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j) { h = fmaf(b[j * bs], x[j].h, h); l = fmaf(b[j * bs], x[j].l, l); }
+  two_sum_acc(acc.hi, acc.lo, h, l);
+}
+template <int N>
+__device__ __forceinline__ void blk_dot(DotAcc<double>& acc, const double* b, int bs, const XV<double>* x) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc.s = fma(b[j * bs], x[j].v, acc.s);
+}
 
 __device__ __forceinline__ void load_xv(const PcgTypedArgs<float>& a, size_t i, XV<float>& x) { x.set(__ldcg(&a.uhl[i])); }
 __device__ __forceinline__ void load_xv(const PcgTypedArgs<double>& a, size_t i, XV<double>& x) { x.v = __ldcg(&a.u[i]); }
@@ -2785,9 +2801,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       }
       if (cd.w == TY_CC) {
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) ds_madd(acc[i], B[i * 6 + j], uc[j]);
+        for (int i = 0; i < 6; ++i) blk_dot<6>(acc[i], B + i * 6, 1, uc);
       } else {
         // camera-group block (6 x nd): the row part with the group's u, the transpose into the group values
         const int nd = cd.w == TY_CV ? 2 : 3;
@@ -2800,26 +2814,20 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
         }
         if (nd == 3) {
 #pragma unroll
-          for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) ds_madd(acc[i], B[i * 3 + j], xg[j]);
+          for (int i = 0; i < 6; ++i) blk_dot<3>(acc[i], B + i * 3, 1, xg);
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             DotAcc<T> y;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) ds_madd(y, B[i * 3 + j], ur[i]);
+            blk_dot<6>(y, B + j, 3, ur);
             acc_add(ga[col + j], y);
           }
         } else {
 #pragma unroll
-          for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) ds_madd(acc[i], B[i * 2 + j], xg[j]);
+          for (int i = 0; i < 6; ++i) blk_dot<2>(acc[i], B + i * 2, 1, xg);
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             DotAcc<T> y;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) ds_madd(y, B[i * 2 + j], ur[i]);
+            blk_dot<6>(y, B + j, 2, ur);
             acc_add(ga[col + j], y);
           }
         }
