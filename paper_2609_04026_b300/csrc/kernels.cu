@@ -1770,24 +1770,24 @@ __device__ __forceinline__ void block_dot6(const double* __restrict__ B, const d
     for (int j = 0; j < 6; ++j) acc[i].s = fma(B[i * 6 + j], x[j], acc[i].s);
 }
 
+// one block's 6 row products with the (head, tail) operand: each row's 6-term dot product in float FMA (its
+// rounding is a few units of the block's own float entries, the order of their storage rounding), added to
+// the double-single row sum once
 __device__ __forceinline__ void block_dot6_split(const float* __restrict__ B, const float* xh, const float* xl,
                                                  DotAcc<float> (&acc)[6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    float hi = acc[i].hi, lo = acc[i].lo;
+    float h = 0.f, l = 0.f;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      const float b = B[i * 6 + j];
-      const float ph = b * xh[j];
-      const float pe = fmaf(b, xh[j], -ph);      // exact error of the product
-      const float s = hi + ph;                   // TwoSum(hi, ph)
-      const float bp = s - hi;
-      const float err = (hi - (s - bp)) + (ph - bp);
-      hi = s;
-      lo += err + fmaf(b, xl[j], pe);
+      h = fmaf(B[i * 6 + j], xh[j], h);
+      l = fmaf(B[i * 6 + j], xl[j], l);
     }
-    acc[i].hi = hi;
-    acc[i].lo = lo;
+    const float sm = acc[i].hi + h;   // TwoSum(hi, h), the tails added to the error
+    const float bp = sm - acc[i].hi;
+    const float er = (acc[i].hi - (sm - bp)) + (h - bp);
+    acc[i].hi = sm;
+    acc[i].lo = acc[i].lo + l + er;
   }
 }
 
