@@ -528,15 +528,8 @@ static ba_status freeze(ba_problem* p) {
   if (d.ngs() || d.nbx()) CUDA_OR(p, cudaMemsetAsync(p->slotCS, 0, T * SCS * (size_t)d.ne, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->dfeat, 0, sizeof(double) * 4 * (size_t)d.nf, p->stream));
   CUDA_OR(p, cudaMemsetAsync(p->x, 0, sizeof(double) * 6 * (size_t)d.na, p->stream));
-  if (mixed(p) && d.nr) {
-    // float copy of the measurements for the mixed-precision linearisation
-    std::vector<double> hm(4 * (size_t)d.nr);
-    CUDA_OR(p, cudaMemcpyAsync(hm.data(), p->meas64, sizeof(double) * hm.size(), cudaMemcpyDeviceToHost, p->stream));
-    CUDA_OR(p, cudaStreamSynchronize(p->stream));
-    std::vector<float> hf(hm.begin(), hm.end());
-    CUDA_OR(p, cudaMemcpyAsync(p->measT, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, p->stream));
-    CUDA_OR(p, cudaStreamSynchronize(p->stream));
-  }
+  // float copy of the measurements for the mixed-precision linearisation, on the device
+  if (mixed(p) && d.nr) CUDA_OR(p, launch_convert(p->stream, 4 * d.nr, p->meas64, (float*)p->measT));
   CUDA_OR(p, cudaMallocHost((void**)&p->hS, sizeof(DevScalars)));
   std::memset(p->hS, 0, sizeof(DevScalars));
   p->hS->lambda = p->opt.lambda0;

@@ -222,6 +222,7 @@ cudaError_t ensure_ln1p_table(cudaStream_t st);   // the FP64 cost's logarithm t
 cudaError_t launch_ln1p_eval(cudaStream_t st, int64_t n, const double* x, double* y);
 cudaError_t fma_probe(int precision, double* tflops, cudaStream_t st);   // FP32 / FP64 FMA throughput
 void launch_decide(Problem& P);
+cudaError_t launch_convert(cudaStream_t st, int64_t n, const double* a, float* b);   // b = (float)a
 
 }  // namespace ba
 

@@ -228,6 +228,12 @@ __global__ void k_convert(int64_t n, const double* __restrict__ a, float* __rest
   if (i < n) b[i] = (float)a[i];
 }
 
+cudaError_t launch_convert(cudaStream_t st, int64_t n, const double* a, float* b) {
+  if (n <= 0) return cudaSuccess;
+  k_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, b);
+  return cudaGetLastError();
+}
+
 // ============================================================================
 // K1: linearise and reduce per feature
 // ============================================================================
