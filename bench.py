@@ -188,6 +188,19 @@ def oracle_step_time(scene, frac):
 
 
 # ------------------------------------------------------------------------------------------ main
+def replica_rate(ms_local, steps, world, dist, device):
+    """N independent replicas (one problem per rank, no data-path collective): the slowest rank's time of its
+    timed steps (a MAX all-reduce over the ranks) and the whole job's LM iterations per second, every rank's
+    steps divided by that time."""
+    import torch
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,11 +272,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = smi.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = replica_rate(ev0.elapsed_time(ev1), args.steps, world, dist, "cuda")
     na, nbf = B.ba_reduced_size(p)
     B.ba_build_reduced(p, float(B.ba_get_lm_state(p)[0]))
     rp_, cols_, _, _ = B.ba_export_reduced_system(p, values=False)
@@ -277,7 +286,6 @@ def main():
     pcg_iters = [r.pcg_iters for r in timed]
     pcg_rel = [float("%.3g" % r.pcg_rel) for r in timed]
     dims_S = {"block_rows": na, "stored_blocks": nbf, "block_density": round(nbf / max(na * na, 1), 4)}
-    value = world * args.steps / (ms / 1e3)
 
     # ---------------- roofline of the dominant kernel stage (live CUDA-event times of the timed steps)
     dims = pair_counts(scene)
