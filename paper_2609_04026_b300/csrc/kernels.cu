@@ -1163,19 +1163,18 @@ struct PartSum<float> {
   __device__ __forceinline__ float rounded() const { return hi + lo; }
 };
 
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// entry (i, j) of Z_a^T Z_b (rows at stride 6; three rows for a point, four for a line), with explicit
-// operations so that every kernel forms it identically
+// acc - (Z_a^T Z_b)_ij (rows at stride 6), the products fused into the running sum (three FMAs for a point's records, four for a
+// line's), so that every kernel forms it identically
 template <class T>
-__device__ __forceinline__ T pair_dot(const T* za, const T* zb, int i, int j, bool line) {
-  T t = mul_rn(za[i], zb[j]);
-  t = fma(za[6 + i], zb[6 + j], t);
-  t = fma(za[12 + i], zb[12 + j], t);
-  if (line) t = fma(za[18 + i], zb[18 + j], t);
-  return t;
+__device__ __forceinline__ T pair_sub(T acc, const T* za, const T* zb, int i, int j, bool line) {
+  acc = fma(-za[i], zb[j], acc);
+  acc = fma(-za[6 + i], zb[6 + j], acc);
+  acc = fma(-za[12 + i], zb[12 + j], acc);
+  if (line) acc = fma(-za[18 + i], zb[18 + j], acc);
+  return acc;
 }
+
 
 // direct term of entry (i, j) for a pair of a diagonal block or a camera-plane pair
 template <class T>
@@ -1403,7 +1402,7 @@ __device__ __forceinline__ void unit_stage_compute(const UnitArgs<T>& a, bool di
       u.bacc[i] += bv[i];
       u.hacc[i] += H[up_idx(i, i, 6)];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)] - pair_dot(za, zb, i, j, line);
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] = pair_sub(acc[i * 6 + j] + H[i <= j ? up_idx(i, j, 6) : up_idx(j, i, 6)], za, zb, i, j, line);
     }
     return;
   }
@@ -1414,31 +1413,31 @@ __device__ __forceinline__ void unit_stage_compute(const UnitArgs<T>& a, bool di
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] = pair_sub(acc[i * 6 + j] + (j < 3 ? Cm[i * 3 + j] : T(0)), za, zb, i, j, line);
   } else if (code == PAIR_CS) {
     // the camera's direct block with the feature's sphere, cylinder or cone (6 x 6, zeros beyond its dims)
     const T* Cm = a.CS + (size_t)ea * SCS;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += Cm[i * 6 + j] - pair_dot(za, zb, i, j, line);
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] = pair_sub(acc[i * 6 + j] + Cm[i * 6 + j], za, zb, i, j, line);
   } else if (code == PAIR_G12) {
     // a 9-parameter group's two entities: the second entity's slot holds J_1^T w J_2 (6 x 3)
     const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (j < 3 ? Cm[i * 3 + j] : T(0)) - pair_dot(za, zb, i, j, line);
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] = pair_sub(acc[i * 6 + j] + (j < 3 ? Cm[i * 3 + j] : T(0)), za, zb, i, j, line);
   } else if (code == PAIR_PK) {
     // plane-intrinsics: the intrinsics slot holds J_K^T w J_plane (3 x 3); this block is its transpose
     const T* Cm = a.C + (size_t)(sb_[lane] & PAIR_SLOT) * SC;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[i * 6 + j] += (i < 3 && j < 3 ? Cm[j * 3 + i] : T(0)) - pair_dot(za, zb, i, j, line);
+      for (int j = 0; j < 6; ++j) acc[i * 6 + j] = pair_sub(acc[i * 6 + j] + (i < 3 && j < 3 ? Cm[j * 3 + i] : T(0)), za, zb, i, j, line);
   } else {
 #pragma unroll
-    for (int e = 0; e < 36; ++e) acc[e] -= pair_dot(za, zb, e / 6, e % 6, line);
+    for (int e = 0; e < 36; ++e) acc[e] = pair_sub(acc[e], za, zb, e / 6, e % 6, line);
   }
 }
 
@@ -1661,7 +1660,7 @@ __global__ void __launch_bounds__(UnitWarps<T>::n * 32) k_schur_packs(UnitArgs<T
     load_rec(stage + lane * ST, za, line);
     load_rec(stage + lane * ST + SW, zb, line);
 #pragma unroll
-    for (int e = 0; e < 36; ++e) acc[e] = T(0) - pair_dot(za, zb, e / 6, e % 6, line);
+    for (int e = 0; e < 36; ++e) acc[e] = pair_sub(T(0), za, zb, e / 6, e % 6, line);
   }
   __syncwarp();   // the staged records are overwritten by the terms
   T* red = stage;
