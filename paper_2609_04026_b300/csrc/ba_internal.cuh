@@ -196,6 +196,8 @@ struct Dims {
   int64_t nun = 0, nmulti = 0;   // Schur work units of the grid path; blocks split over several units
   int64_t nun_main = 0, npack = 0;   // units a warp takes alone (the rest are packed), and the packs
   int64_t n_points_res_end = 0;  // residuals of points are [0, this); lines follow
+  int64_t nr_cost = 0;   // entries of the cost order the grid cost pass visits (a point's plane-induced record
+                         // evaluated with its point record is not visited on its own)
 };
 
 // kernel launchers (kernels.cu); T = double (FP64 path) or float (mixed path)
@@ -292,6 +294,8 @@ struct ba_problem {
   int32_t* rslot_k = nullptr;   // per residual the slot of its camera's intrinsics entity (or -1)
   double* meas64 = nullptr;
   int32_t* cost_order = nullptr;   // residual indices sorted by kind (feature-major inside a kind)
+  int32_t* cost_partner = nullptr; // per point record, the plane-induced record of the same point and camera
+                                   // that the cost pass evaluates with it (pi(C, X) once), or -1
   void* measT = nullptr;
   int32_t *fres_off = nullptr, *fslot_off = nullptr;
   int32_t *slot_ent = nullptr, *slot_feat = nullptr;

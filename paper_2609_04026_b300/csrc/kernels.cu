@@ -3591,6 +3591,7 @@ cudaError_t launch_ln1p_eval(cudaStream_t st, int64_t n, const double* x, double
 struct CostArgs {
   const int8_t* rkind;
   const int32_t *rcam, *rfeat, *rgrp, *order;
+  const int32_t* partner;   // per point record its plane-induced partner (or -1), or null: every record alone
   const double *meas, *camD, *grpD, *pts, *lin;
   const double* srf;   // surface groups (spheres, cylinders, cones)
   const double* bx;    // 9-parameter groups (ellipsoids, cuboids)
@@ -3603,8 +3604,50 @@ struct CostArgs {
 
 // EXT: the sphere ... cuboid kinds too (a separate instantiation, so that the common kinds' kernel keeps its
 // registers and code size)
+// the Cauchy term of one residual's squared norm s (its share of E and of E_px)
+__device__ __forceinline__ void cost_term(const CostArgs& a, int kind, double s, double (&v)[2]) {
+  const double e = a.loss.half_wa2[kind] * ln1p_tab(s * a.loss.inv_a2[kind]);
+  v[0] += e;
+  if (res_pixel(kind)) v[1] += e;
+}
+
+// a point record and its plane-induced partner (Eq. 1 and Eq. 7 for the same point and camera): pi(C, X)
+// once, each residual formed with the operations of res_point and res_plane_point
+__device__ void cost_point_pair(const CostArgs& a, int64_t i, int64_t j, double (&v)[2]) {
+  const int cid = a.rcam[i];
+  const double* X = a.pts + 3 * (size_t)a.rfeat[i];
+  const double* meas = a.meas + 4 * i;
+  const double* P = a.grpD + (size_t)GRP_STRIDE * a.rgrp[j];
+  Cam<double> c;
+  load_cam(a.camD + (size_t)CAM_STRIDE * cid, c);
+  double p1[3], x1[3], pi1[2], J1[2][3];
+  matvec3(c.R, X, p1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) x1[k] = p1[k] + c.t[k];
+  if (!(x1[2] > 1e-6)) return;   // both residuals invalid
+  project_dist<double, false>(c, x1, pi1, J1);
+  const double r0 = pi1[0] - meas[0], r1 = pi1[1] - meas[1];
+  cost_term(a, R_POINT, r0 * r0 + r1 * r1, v);
+  double Xp[3], cd, p2[3], x2[3], pi2[2], J2[2][3];
+  plane_proj_point(P, P[3], X, Xp, cd);
+  matvec3(c.R, Xp, p2);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) x2[k] = p2[k] + c.t[k];
+  if (!(x2[2] > 1e-6)) return;
+  project_dist<double, false>(c, x2, pi2, J2);
+  const double q0 = pi1[0] - pi2[0], q1 = pi1[1] - pi2[1];
+  cost_term(a, R_PLANE_POINT, q0 * q0 + q1 * q1, v);
+}
+
 template <bool EXT = false>
 __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
+  if (a.partner && a.rkind[i] == R_POINT) {
+    const int32_t j = a.partner[i];
+    if (j >= 0) {
+      cost_point_pair(a, i, j, v);
+      return;
+    }
+  }
   {
     const int kind = a.rkind[i];
     const int cid = a.rcam[i];
@@ -3645,9 +3688,7 @@ __device__ void cost_residual(const CostArgs& a, int64_t i, double (&v)[2]) {
     if (o.valid) {
       double s = 0;
       for (int k = 0; k < rd; ++k) s += o.r[k] * o.r[k];
-      const double e = a.loss.half_wa2[kind] * ln1p_tab(s * a.loss.inv_a2[kind]);
-      v[0] = e;
-      v[1] = res_pixel(kind) ? e : 0.0;
+      cost_term(a, kind, s, v);
     }
   }
 }
@@ -4067,7 +4108,8 @@ void launch_cost(Problem& P, bool candidate) {
   CostArgs a;
   a.rkind = P.rkind; a.rcam = P.rcam; a.rfeat = P.rfeat; a.rgrp = P.rgrp; a.meas = P.meas64; a.order = P.cost_order;
   a.camD = s.camD; a.grpD = s.grpD; a.pts = s.pts; a.lin = s.lin; a.srf = s.srf; a.bx = s.bx;
-  a.nr = d.nr; a.np = d.np; a.npl = d.npl; a.nsp = d.nsp; a.ncy = d.ncy; a.nel = d.nel;
+  a.nr = d.nr_cost; a.np = d.np; a.npl = d.npl; a.nsp = d.nsp; a.ncy = d.ncy; a.nel = d.nel;
+  a.partner = P.cost_partner;
   a.loss = make_loss(P.opt); a.S = P.S; a.red = P.red;
   a.candidate = candidate ? 1 : 0;
   ++P.launches;
@@ -4461,6 +4503,7 @@ void fill_window_desc(Problem& P, void* out) {
   CostArgs& co = W.cost;
   co.rkind = P.rkind; co.rcam = P.rcam; co.rfeat = P.rfeat; co.rgrp = P.rgrp; co.meas = P.meas64; co.order = P.cost_order;
   co.nr = d.nr; co.np = d.np; co.npl = d.npl; co.loss = make_loss(P.opt); co.S = P.S; co.red = P.red; co.candidate = 1;
+  co.partner = nullptr;   // windows evaluate every record on its own
   co.srf = nullptr; co.nsp = co.ncy = 0; co.bx = nullptr; co.nel = 0;
   W.dec = DecideArgs{P.S, P.opt.min_gain, P.opt.lambda_min, P.opt.lambda_max};
   for (int s = 0; s < 2; ++s) {

@@ -796,9 +796,42 @@ __global__ void k_permute(Permute a) {
   a.rmeas[j] = a.meas[i];
 }
 
-__global__ void k_kind_key(const int8_t* __restrict__ kind, int64_t n, uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+// The cost pass evaluates a point record together with the plane-induced record of the same point and camera
+// (both project X into that camera): the first point record of each (feature, camera) run takes the run's
+// first plane-induced record as its partner.  Records are feature-major and camera-sorted, so a run is
+// contiguous.
+__global__ void k_cost_partner(const int8_t* __restrict__ kind, const int32_t* __restrict__ cam,
+                               const int32_t* __restrict__ feat, int64_t n, int32_t* __restrict__ partner,
+                               uint8_t* __restrict__ attached, unsigned long long* __restrict__ nattached) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  partner[k] = -1;
+  if (kind[k] != R_POINT) return;
+  const int32_t f = feat[k], c = cam[k];
+  int64_t b0 = k, b1 = k + 1;
+  while (b0 > 0 && feat[b0 - 1] == f && cam[b0 - 1] == c) --b0;
+  while (b1 < n && feat[b1] == f && cam[b1] == c) ++b1;
+  for (int64_t j = b0; j < k; ++j)
+    if (kind[j] == R_POINT) return;   // not the run's first point record
+  for (int64_t j = b0; j < b1; ++j)
+    if (kind[j] == R_PLANE_POINT) {
+      partner[k] = (int32_t)j;
+      attached[j] = 1;
+      atomicAdd(nattached, 1ull);
+      return;
+    }
+}
+
+// cost order key: the kind, a point record with a partner before one without (the lanes of a warp then do the
+// same work), attached plane-induced records last (the grid pass does not visit them)
+__global__ void k_kind_key(const int8_t* __restrict__ kind, const int32_t* __restrict__ partner,
+                           const uint8_t* __restrict__ attached, int64_t n, uint32_t* __restrict__ key,
+                           uint32_t* __restrict__ val) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j < n) { key[j] = (uint32_t)kind[j]; val[j] = (uint32_t)j; }
+  if (j < n) {
+    key[j] = attached[j] ? 255u : 2u * (uint32_t)kind[j] + (partner[j] >= 0 ? 0u : 1u);
+    val[j] = (uint32_t)j;
+  }
 }
 
 __global__ void k_ent_type(int64_t na, int64_t nc, int64_t npl, int64_t nv, int64_t nsp, int64_t ncy, int64_t nco,
@@ -1297,8 +1330,21 @@ ba_status build_structure(Problem& P) {
   P.cost_order = P.dnew<int32_t>(nr);
   if (!P.cost_order) return oom();
   if (nr) {
-    k_kind_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(P.rkind, nr, key, (uint32_t*)P.cost_order);
+    uint8_t* attached = S.get<uint8_t>(nr);
+    unsigned long long* natt = S.get<unsigned long long>(1);
+    P.cost_partner = P.dnew<int32_t>(nr);
+    if (!attached || !natt || !P.cost_partner) return oom();
+    CU(cudaMemsetAsync(attached, 0, nr, P.stream));
+    CU(cudaMemsetAsync(natt, 0, sizeof(unsigned long long), P.stream));
+    k_cost_partner<<<grid_of(nr, NT), NT, 0, P.stream>>>(P.rkind, P.rcam, P.rfeat, nr, P.cost_partner, attached, natt);
+    k_kind_key<<<grid_of(nr, NT), NT, 0, P.stream>>>(P.rkind, P.cost_partner, attached, nr, key, (uint32_t*)P.cost_order);
     if ((s = radix_sort(P, S, key, (uint32_t*)P.cost_order, k2, v2, nr, 8))) return s;
+    unsigned long long h = 0;
+    CU(cudaMemcpyAsync(&h, natt, sizeof(h), cudaMemcpyDeviceToHost, P.stream));
+    CU(cudaStreamSynchronize(P.stream));
+    d.nr_cost = nr - (int64_t)h;
+  } else {
+    d.nr_cost = 0;
   }
   P.ent_type = P.dnew<uint8_t>(na);
   if (!P.ent_type) return oom();
