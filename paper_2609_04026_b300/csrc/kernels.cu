@@ -3239,15 +3239,32 @@ __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
 template <class T, int K>
 __device__ void backsub_feature(const BackArgs<T>& a, int64_t f, double& gTd, double& dHd) {
   double t[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) t[i] = a.g[4 * f + i];
   double gd = 0, hh = 0;
-  for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
-    const T* so = a.sv + (size_t)e * SBS;
+  if constexpr (sizeof(T) == 4) {
+    // the slots' float values summed in double-single (TwoSum, as exact as an FP64 sum of them) and converted
+    // once: a conversion per slot and component would cost an FP64-pipe operation on this part
+    float hs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, ls[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
+      const T* so = a.sv + (size_t)e * SBS;
 #pragma unroll
-    for (int i = 0; i < K; ++i) t[i] += (double)so[i];
-    gd += (double)so[4];
-    hh += (double)so[5];
+      for (int i = 0; i < 6; ++i) {
+        if (i < K || i >= 4) two_sum_acc(hs[i], ls[i], so[i], 0.f);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) t[i] = a.g[4 * f + i] + ((double)hs[i] + (double)ls[i]);
+    gd = (double)hs[4] + (double)ls[4];
+    hh = (double)hs[5] + (double)ls[5];
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) t[i] = a.g[4 * f + i];
+    for (int e = a.fslot_off[f]; e < a.fslot_off[f + 1]; ++e) {
+      const T* so = a.sv + (size_t)e * SBS;
+#pragma unroll
+      for (int i = 0; i < K; ++i) t[i] += (double)so[i];
+      gd += (double)so[4];
+      hh += (double)so[5];
+    }
   }
   double dfv[K];
   const double* Vi = a.Vinv + 10 * f;
