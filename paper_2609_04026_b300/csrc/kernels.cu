@@ -3908,7 +3908,8 @@ void launch_linearize(Problem& P) {
     if (d.nl) { ++P.launches; k_linearize<T, 4, true><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
     return;
   }
-  if (d.np) { ++P.launches; k_linearize<T, 3><<<nblk(d.np, 128), 128, 0, P.stream>>>(a, 0, d.np); }
+  // a warp per CTA: at 217 registers a thread, an SM holds 9 warps of one-warp CTAs against 8 of 128-thread ones
+  if (d.np) { ++P.launches; k_linearize<T, 3><<<nblk(d.np, 32), 32, 0, P.stream>>>(a, 0, d.np); }
   if (d.nl) { ++P.launches; k_linearize<T, 4><<<nblk(d.nl, 128), 128, 0, P.stream>>>(a, d.np, d.nf); }
 }
 
