@@ -128,6 +128,10 @@ def s_type_counts(rp, cols, nc, npl):
             "cc_upper": int((cam_r & (c < nc) & (c >= r)).sum()), "gg_upper": int((~cam_r & (c >= r)).sum())}
 
 
+# measured DRAM traffic of one PCG iteration of the typed kernel on the 2000-camera workload, mixed path
+PCG_DRAM_BYTES_PER_ITER_LARGE = (8.45e9 + 9.27e6) / 121
+
+
 def pcg_bytes_per_iter(t, T, na):
     """Algorithmic bytes of one PCG iteration on the typed storage: every stored block's values at its real
     width (camera-camera 36, camera-plane 18, camera-VP 12, group-group 36) and its 4-byte column index, and
@@ -317,7 +321,16 @@ def main():
                              "4-byte column index; + block rows x 6 x 8 bytes x 10 vector accesses)")
     stages["pcg"]["frac_of_symmetric_minimum"] = round(
         dims["pcg_iters_mean"] * sym_iter / (kern["pcg"] / 1e3) / 1e9 / hbm_peak, 4)
-    stages["pcg"]["traffic"] = None   # the DRAM counters of the current kernel are in profiles/
+    # DRAM bytes of the PCG kernel from one ncu capture of the 2000-camera workload (profiles/pcg_dram_large.md:
+    # 8.46 GB read + written by a 121-iteration launch), per iteration times this run's mean iterations; only
+    # for that workload and precision
+    if args.config == "large" and prec == B.BA_MIXED:
+        stages["pcg"]["traffic"] = round(PCG_DRAM_BYTES_PER_ITER_LARGE * dims["pcg_iters_mean"])
+        stages["pcg"]["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu "
+                                         "capture (8.46 GB over 121 iterations) scaled by the mean iterations; below "
+                                         "the algorithmic bytes because ~60 MB of S stays in L2 between iterations")
+    else:
+        stages["pcg"]["traffic"] = None
     dom = max(kern, key=kern.get)
     roof = dict(stages[dom]) if dom in stages else {
         "bound": None, "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
