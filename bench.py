@@ -129,7 +129,7 @@ def s_type_counts(rp, cols, nc, npl):
 
 
 # measured DRAM traffic of one PCG iteration of the typed kernel on the 2000-camera workload, mixed path
-PCG_DRAM_BYTES_PER_ITER_LARGE = (8.45e9 + 9.27e6) / 121
+PCG_DRAM_BYTES_PER_ITER_LARGE = (8.44e9 + 9.07e6) / 121
 
 
 def pcg_bytes_per_iter(t, T, na):
@@ -322,12 +322,12 @@ def main():
     stages["pcg"]["frac_of_symmetric_minimum"] = round(
         dims["pcg_iters_mean"] * sym_iter / (kern["pcg"] / 1e3) / 1e9 / hbm_peak, 4)
     # DRAM bytes of the PCG kernel from one ncu capture of the 2000-camera workload (profiles/pcg_dram_large.md:
-    # 8.46 GB read + written by a 121-iteration launch), per iteration times this run's mean iterations; only
+    # 8.45 GB read + written by a 121-iteration launch), per iteration times this run's mean iterations; only
     # for that workload and precision
     if args.config == "large" and prec == B.BA_MIXED:
         stages["pcg"]["traffic"] = round(PCG_DRAM_BYTES_PER_ITER_LARGE * dims["pcg_iters_mean"])
         stages["pcg"]["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu "
-                                         "capture (8.46 GB over 121 iterations) scaled by the mean iterations; below "
+                                         "capture (8.45 GB over 121 iterations) scaled by the mean iterations; below "
                                          "the algorithmic bytes because ~60 MB of S stays in L2 between iterations")
     else:
         stages["pcg"]["traffic"] = None

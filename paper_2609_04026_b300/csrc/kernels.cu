@@ -2565,8 +2565,24 @@ __device__ __forceinline__ void blk_dot(DotAcc<double>& acc, const double* b, in
   for (int j = 0; j < N; ++j) acc.s = fma(b[j * bs], x[j].v, acc.s);
 }
 
-__device__ __forceinline__ void load_xv(const PcgTypedArgs<float>& a, size_t i, XV<float>& x) { x.set(__ldcg(&a.uhl[i])); }
-__device__ __forceinline__ void load_xv(const PcgTypedArgs<double>& a, size_t i, XV<double>& x) { x.v = __ldcg(&a.u[i]); }
+// the 6 values of block row r in three 16-byte loads (every vector starts on a 256-byte boundary and a block row
+// on a 48-byte one): half the L2 sector requests of six 8-byte gathers
+__device__ __forceinline__ void load_xv6(const PcgTypedArgs<float>& a, size_t r, XV<float> (&x)[6]) {
+  const float4* q = reinterpret_cast<const float4*>(a.uhl + 6 * r);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 t = __ldcg(q + k);
+    x[2 * k].h = t.x; x[2 * k].l = t.y; x[2 * k + 1].h = t.z; x[2 * k + 1].l = t.w;
+  }
+}
+__device__ __forceinline__ void load_xv6(const PcgTypedArgs<double>& a, size_t r, XV<double> (&x)[6]) {
+  const double2* q = reinterpret_cast<const double2*>(a.u + 6 * r);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double2 t = __ldcg(q + k);
+    x[2 * k].v = t.x; x[2 * k + 1].v = t.y;
+  }
+}
 
 // n contiguous values of a lane's block from the stage buffer (16-byte aligned for 36 and 12 floats and for
 // every double block; 8-byte aligned for 18 floats)
@@ -2702,7 +2718,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   auto issue = [&](int k) {
     const int q = c0 + k;
     const int bi = k % NBUF;
-    const int4 cd = a.tchunk[q];
+    const int4 cd = __ldg(&a.tchunk[q]);
     const unsigned vb = (unsigned)(TCHUNK * ty_vals(cd.w) * sizeof(T));
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(&bars[warp][bi], vb + 4u * TCHUNK);
@@ -2724,9 +2740,25 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   // w = S u over the owned values (camera rows complete after the carries, group rows after the partials);
   // returns this CTA's share of (w, u)
   auto spmv = [&](double& wu) {
-    for (int k = threadIdx.x; k < gvp; k += NT) {
-      if constexpr (sizeof(T) == 4) ug[k] = k < a.gv ? __ldcg(&a.uhl[a.gv_idx[k]]) : make_float2(0.f, 0.f);
-      else ug[k] = k < a.gv ? __ldcg(&a.u[a.gv_idx[k]]) : 0.0;
+    // the group values of u, eight per thread at a time: the (read-only, L1-resident) indices, then the eight
+    // gathers issued together, so that a thread waits for two round trips per eight values rather than two per value
+    constexpr int UGB = 8;
+    for (int k0 = threadIdx.x; k0 < gvp; k0 += UGB * NT) {
+      int gi[UGB];
+#pragma unroll
+      for (int t = 0; t < UGB; ++t) {
+        const int k = k0 + t * NT;
+        gi[t] = k < a.gv ? __ldg(&a.gv_idx[k]) : -1;
+      }
+      UGv<T> gvv[UGB];
+#pragma unroll
+      for (int t = 0; t < UGB; ++t) {
+        if constexpr (sizeof(T) == 4) gvv[t] = gi[t] >= 0 ? __ldcg(&a.uhl[gi[t]]) : make_float2(0.f, 0.f);
+        else gvv[t] = gi[t] >= 0 ? __ldcg(&a.u[gi[t]]) : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < UGB; ++t)
+        if (k0 + t * NT < gvp) ug[k0 + t * NT] = gvv[t];
     }
     for (int k = lane; k < gvp; k += 32) ga[k] = DotAcc<T>();
     if (lane == 0 && !prefetched)
@@ -2735,12 +2767,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
     __syncthreads();
     DotAcc<T> acc[6];
     int row = wfirst[warp];
-    int rend = nk > 0 ? a.row_chunk0[row + 1] : 0;
+    int rend = nk > 0 ? __ldg(&a.row_chunk0[row + 1]) : 0;
     XV<T> ur[6];   // u of the current camera row
-    auto load_ur = [&]() {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) load_xv(a, 6 * (size_t)row + i, ur[i]);
-    };
+    auto load_ur = [&]() { load_xv6(a, (size_t)row, ur); };
     auto flush = [&]() {
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -2754,11 +2783,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
     if (nk > 0) {
       load_ur();
       arrive(0);
-      cdn = a.tchunk[c0];
+      cdn = __ldg(&a.tchunk[c0]);
       if (cdn.w == TY_CC) {
-        const int cl = cols[warp][0][lane];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) load_xv(a, 6 * (size_t)cl + j, un[j]);
+        load_xv6(a, (size_t)cols[warp][0][lane], un);
       }
     }
     for (int k = 0; k < nk; ++k) {
@@ -2767,7 +2794,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       while (q >= rend) {
         flush();
         ++row;
-        rend = a.row_chunk0[row + 1];
+        rend = __ldg(&a.row_chunk0[row + 1]);
         load_ur();
       }
       const int bi = k % NBUF;
@@ -2797,11 +2824,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       if (lane == 0 && k + NBUF < nk) issue(k + NBUF);
       if (k + 1 < nk) {
         arrive(k + 1);
-        cdn = a.tchunk[q + 1];
+        cdn = __ldg(&a.tchunk[q + 1]);
         if (cdn.w == TY_CC) {
-          const int cl = cols[warp][(k + 1) % NBUF][lane];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) load_xv(a, 6 * (size_t)cl + j, un[j]);
+          load_xv6(a, (size_t)cols[warp][(k + 1) % NBUF][lane], un);
         }
       }
       if (cd.w == TY_CC) {
@@ -2895,14 +2920,13 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
     // every row's blocks summed in block order
     __syncthreads();
     DotAcc<T>* ggy = gacc;
-    const int kb0 = a.gg_ptr[gs0], kb1 = a.gg_ptr[gs1];
+    const int kb0 = __ldg(&a.gg_ptr[gs0]), kb1 = __ldg(&a.gg_ptr[gs1]);
     for (int kb = kb0 + threadIdx.x; kb < kb1; kb += NT) {
       T Bk[36];
       load_block36(a.Sv + a.gg_val0 + 36 * (size_t)kb, Bk);   // 16-byte aligned: gg_val0 is a chunk boundary
-      const int cl = a.gg_col[kb];
+      const int cl = __ldg(&a.gg_col[kb]);
       XV<T> uv[6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) load_xv(a, 6 * (size_t)cl + j, uv[j]);
+      load_xv6(a, (size_t)cl, uv);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         DotAcc<T> y;
@@ -2941,7 +2965,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       const int l = loc_cam(6 * (int64_t)rrow + threadIdx.x);
       double v = sw[l];
       for (int c2 = c + 1; c2 < G; ++c2) {
-        const int4 pn = a.cta_part[c2];
+        const int4 pn = __ldg(&a.cta_part[c2]);
         if (pn.x == pn.y || pn.z != rrow) break;
         v += __ldcg(&a.carry[6 * (size_t)c2 + threadIdx.x]);
       }
@@ -2954,8 +2978,17 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
       int k0, nd;
       gval(g, k0, nd);
       if (d >= nd) continue;
+      // the lane's CTAs in batches of eight loads issued together, summed in CTA order
+      constexpr int CB = 8;
+      const double* pg = a.part_g + (size_t)(k0 + d) * G;
       double v = 0;
-      for (int c2 = lane; c2 < G; c2 += 32) v += __ldcg(&a.part_g[(size_t)(k0 + d) * G + c2]);
+      for (int cb = lane; cb < G; cb += CB * 32) {
+        double pv[CB];
+#pragma unroll
+        for (int t = 0; t < CB; ++t) pv[t] = cb + 32 * t < G ? __ldcg(&pg[cb + 32 * t]) : 0.0;
+#pragma unroll
+        for (int t = 0; t < CB; ++t) v += pv[t];
+      }
       v = warp_sum(v);
       if (lane == 0) sw[loc_grp(6 * ((int64_t)a.nc + g) + d)] += v;
     }
