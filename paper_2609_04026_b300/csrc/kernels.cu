@@ -2195,12 +2195,15 @@ template <>
 struct UVal<float> {
   float xh[6], xl[6];
   __device__ __forceinline__ void gather(const PcgStreamArgs<float>& a, int col) {
-    const float2* pb = a.uhl + 6 * (size_t)col;
+    // three 16-byte loads: the vector is 256-byte aligned and a block row starts on a 48-byte boundary
+    const float4* pb = reinterpret_cast<const float4*>(a.uhl + 6 * (size_t)col);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const float2 v = __ldcg(&pb[j]);
-      xh[j] = v.x;
-      xl[j] = v.y;
+    for (int j = 0; j < 3; ++j) {
+      const float4 v = __ldcg(&pb[j]);
+      xh[2 * j] = v.x;
+      xl[2 * j] = v.y;
+      xh[2 * j + 1] = v.z;
+      xl[2 * j + 1] = v.w;
     }
   }
   __device__ __forceinline__ void product(const float (&B)[36], DotAcc<float> (&acc)[6]) const {
@@ -2211,9 +2214,13 @@ template <>
 struct UVal<double> {
   double xv[6];
   __device__ __forceinline__ void gather(const PcgStreamArgs<double>& a, int col) {
-    const double* pb = a.u + 6 * (size_t)col;
+    const double2* pb = reinterpret_cast<const double2*>(a.u + 6 * (size_t)col);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) xv[j] = __ldcg(&pb[j]);
+    for (int j = 0; j < 3; ++j) {
+      const double2 v = __ldcg(&pb[j]);
+      xv[2 * j] = v.x;
+      xv[2 * j + 1] = v.y;
+    }
   }
   __device__ __forceinline__ void product(const double (&B)[36], DotAcc<double> (&acc)[6]) const {
     block_dot6(B, xv, acc);
@@ -3145,10 +3152,15 @@ template <class T>
 __device__ void backsub_slot(const BackArgs<T>& a, int64_t e) {
   const int64_t f = a.slot_feat[e];
   const int K = f < a.np ? 3 : 4;
-  const double* da = a.x + 6 * (size_t)a.slot_ent[e];
+  // the entity's increments in three 16-byte loads (x is 256-byte aligned, a block row 48 bytes)
+  const double2* da = reinterpret_cast<const double2*>(a.x + 6 * (size_t)a.slot_ent[e]);
   T dv[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) dv[j] = (T)da[j];
+  for (int j = 0; j < 3; ++j) {
+    const double2 v = da[j];
+    dv[2 * j] = (T)v.x;
+    dv[2 * j + 1] = (T)v.y;
+  }
   T W[24];
   if (K == 3) {   // a point's W has three rows
     load16<T, 18>(a.W + (size_t)e * SW, W);
