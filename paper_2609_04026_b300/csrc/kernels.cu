@@ -1960,6 +1960,40 @@ __device__ __forceinline__ bool grid_barrier(DevScalars* S, unsigned G, long lon
   return ok_sh != 0;
 }
 
+// ---- the typed PCG's grid barrier: one arrival counter that only grows within a launch (reset on the host
+// before it), so that the k-th barrier of a launch is passed once the counter reaches k x G.  The last arrival
+// needs one atomic round trip and the waiters one load to see it (no reset of the count, no generation word).
+// A CTA that must end the solve (a copy wait or this wait ran out) adds BAR_ABORT: every CTA then leaves at its
+// current or next barrier with false, and PCG_FLAG_TIMEOUT is recorded for the host.
+constexpr unsigned long long BAR_ABORT = 1ull << 40;
+__device__ __forceinline__ bool grid_barrier_count(DevScalars* S, unsigned long long target, bool abort_cta,
+                                                   long long budget) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();   // the CTA's writes before its arrival
+    const unsigned long long add = abort_cta ? BAR_ABORT + 1ull : 1ull;
+    unsigned long long v = atomicAdd(&S->bar_arrive, add) + add;
+    int ok = 1;
+    if (v < target) {
+      volatile unsigned long long* cp = &S->bar_arrive;
+      const long long t0 = clock64();
+      while ((v = *cp) < target)
+        if (clock64() - t0 > budget) {
+          ok = 0;
+          atomicOr(&S->flags, PCG_FLAG_TIMEOUT);
+          atomicAdd(&S->bar_arrive, BAR_ABORT);
+          break;
+        }
+    }
+    __threadfence();   // the other CTAs' writes before their arrivals
+    if (v >= BAR_ABORT) ok = 0;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
 // SOA: S in the padded interleaved storage, chunks of exactly 32 blocks (one per lane, coalesced
 // loads); otherwise contiguous blocks and chunks of up to PCG_CHUNK blocks strided over the lanes
 template <class T, int NT, bool SOA>
@@ -3021,9 +3055,11 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_typed(PcgTypedArgs<T> a) {
   };
   auto slot = [&](int par, int k) { return a.part + (size_t)par * 3 * G + (size_t)k * G; };
   // a copy wait that ran out (in any warp) is recorded before the barrier; the barrier's answer is uniform
+  unsigned long long bar_target = 0;   // arrivals that complete this CTA's next barrier
   auto sync = [&]() -> bool {
     if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
-    return grid_barrier(a.S, (unsigned)G, a.budget);
+    bar_target += (unsigned long long)G;
+    return grid_barrier_count(a.S, bar_target, timed_out, a.budget);
   };
 
   // ---- start: x = 0, r = b, the owned rows' block inverses into shared memory, u = M^-1 r, w = S u
@@ -4073,8 +4109,8 @@ static void launch_pcg_typed(Problem& P) {
   a.nown = P.pcg_nown;
   void* args[] = {&a};
   ++P.launches;
-  // the grid barrier's arrival count starts at zero (a launch that gave up at a barrier may leave it set)
-  P.pcg_err = cudaMemsetAsync(&P.S->bar_count, 0, sizeof(unsigned), P.stream);
+  // the grid barriers' arrival counter starts at zero in every launch
+  P.pcg_err = cudaMemsetAsync(&P.S->bar_arrive, 0, sizeof(unsigned long long), P.stream);
   if (P.pcg_err != cudaSuccess) return;
   P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_typed<T, NT, NB>, dim3(P.pcg_grid), dim3(NT), args,
                                           P.pcg_smem, P.stream);
