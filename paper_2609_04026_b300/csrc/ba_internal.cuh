@@ -171,7 +171,7 @@ struct DevScalars {
                              // bit 2: a block-Jacobi block fell back to its diagonal; bit 3: PCG wait timeout
   unsigned int counter[8];   // arrival counters of the last-block reductions
   unsigned int bar_count, bar_gen;   // grid barrier of the persistent PCG (count reset before every launch)
-  unsigned long long bar_arrive;     // arrivals at the typed PCG's barriers in this launch (reset before it)
+  unsigned long long bar_arrive;     // arrivals at the typed and stream PCGs' barriers in this launch (reset before it)
 };
 
 // the frozen problem structure (built once, K0) plus every device array

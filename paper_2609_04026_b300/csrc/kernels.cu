@@ -1960,8 +1960,8 @@ __device__ __forceinline__ bool grid_barrier(DevScalars* S, unsigned G, long lon
   return ok_sh != 0;
 }
 
-// ---- the typed PCG's grid barrier: one arrival counter that only grows within a launch (reset on the host
-// before it), so that the k-th barrier of a launch is passed once the counter reaches k x G.  The last arrival
+// ---- the typed and stream PCGs' grid barrier: one arrival counter that only grows within a launch (reset on
+// the host before it), so that the k-th barrier of a launch is passed once the counter reaches k x G.  The last arrival
 // needs one atomic round trip and the waiters one load to see it (no reset of the count, no generation word).
 // A CTA that must end the solve (a copy wait or this wait ran out) adds BAR_ABORT: every CTA then leaves at its
 // current or next barrier with false, and PCG_FLAG_TIMEOUT is recorded for the host.
@@ -2450,9 +2450,11 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_stream(PcgStreamArgs<T> a) {
   cta_sum2<NT>(ru, rrl, cta_out);
   if (threadIdx.x == 0) { slot(0, 0)[c] = cta_out[0]; slot(0, 1)[c] = cta_out[1]; }
   // a copy wait that ran out (in any warp) is recorded before the barrier; the barrier's answer is uniform
+  unsigned long long bar_target = 0;   // arrivals that complete this CTA's next barrier
   auto sync = [&]() -> bool {
     if (timed_out) atomicOr(&a.S->flags, PCG_FLAG_TIMEOUT);
-    return grid_barrier(a.S, (unsigned)G, a.budget);
+    bar_target += (unsigned long long)G;
+    return grid_barrier_count(a.S, bar_target, timed_out, a.budget);
   };
   bool go = sync();
   if (go) {
@@ -4135,7 +4137,8 @@ void launch_pcg(Problem& P) {
   a.budget = P.opt.wait_budget_cycles > 0 ? P.opt.wait_budget_cycles : 1;
   void* args[] = {&a};
   ++P.launches;
-  P.pcg_err = cudaMemsetAsync(&P.S->bar_count, 0, sizeof(unsigned), P.stream);
+  // the grid barriers' arrival counter starts at zero in every launch
+  P.pcg_err = cudaMemsetAsync(&P.S->bar_arrive, 0, sizeof(unsigned long long), P.stream);
   if (P.pcg_err != cudaSuccess) return;
   P.pcg_err = cudaLaunchCooperativeKernel((const void*)k_pcg_stream<T, NT, NB>, dim3(P.pcg_grid), dim3(NT), args,
                                           P.pcg_smem + stream_stage_bytes<T>(), P.stream);
